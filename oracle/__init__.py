@@ -1,0 +1,286 @@
+"""Test infrastructure: the plain FP64 CPU oracle.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may import this package.  It shares no code with the CUDA path; the only
+thing both sides take from a common module are the seeded sample points
+(``paper_2105_02007_gb300.inputs``), which hold none of the method's
+arithmetic.
+
+The compiled part (``mlq_oracle.c``) implements the per-sample forward solve
+exactly as the paper defines it (see that file's header).  This module adds a
+ctypes loader, numpy wrappers and the estimators of Sec. 4:
+
+  single level  QoI^SL_L = Q_L(F_L)                                   (eq. SL)
+  multilevel    QoI^ML_L = sum_l Q_{L-l}(F_l - F_{l-1}), F_{-1} = 0   (eq. StandardML)
+
+Parity status per function (each is pinned by ``tests/test_oracle_pins.py``
+unless noted):
+  mesh2d, mesh3d, assemble, kl_build, centroid_table, solve, solve_batch,
+  mc_estimate, mlmc_estimate, qmc_estimate: pinned.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mlq_oracle.c")
+_LIB = os.path.join(_HERE, "libmlq_oracle.so")
+_lib = None
+
+_i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_i64p = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP if available).  Returns the path."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", _SRC, "-o", _LIB + ".tmp", "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = ctypes.CDLL(_LIB)
+    c = ctypes
+    lib.mlqo_mesh2d.argtypes = [c.c_int, _f64p, _i32p]
+    lib.mlqo_mesh3d.argtypes = [c.c_int, c.c_int, c.c_int, c.c_double, c.c_double, c.c_double, _f64p, _i32p]
+    lib.mlqo_pattern_nnz.argtypes = [c.c_int, c.c_int64, c.c_int64, _i32p]
+    lib.mlqo_pattern_nnz.restype = c.c_int64
+    lib.mlqo_assemble.argtypes = [c.c_int, c.c_int64, _f64p, c.c_int64, _i32p, c.c_void_p, c.c_double,
+                                  c.c_double, _i64p, _i32p, _f64p, _f64p]
+    lib.mlqo_kl_build.argtypes = [c.c_int, c.c_int64, _f64p, c.c_int64, _i32p, c.c_double, c.c_double,
+                                  c.c_int, _f64p, _f64p, c.c_void_p, c.c_void_p]
+    lib.mlqo_centroid_table.argtypes = [c.c_int, _i32p, _f64p, _f64p, c.c_int, _f64p, c.c_int64, _i32p,
+                                        _f64p]
+    lib.mlqo_solve.argtypes = [c.c_int, c.c_int64, _f64p, c.c_int64, _i32p, _f64p, _f64p, c.c_double,
+                               c.c_int, c.c_double, c.c_int64, _f64p, _f64p, c.POINTER(c.c_double),
+                               c.POINTER(c.c_int64), c.POINTER(c.c_int32)]
+    lib.mlqo_solve_batch.argtypes = [c.c_int, c.c_int64, _f64p, c.c_int64, _i32p, c.c_int, _f64p, c.c_void_p,
+                                     c.c_int64, _f64p, _f64p, c.c_double, c.c_int, c.c_double, c.c_int64,
+                                     _f64p, c.c_void_p, c.c_int, _f64p, _i64p, _i32p]
+    lib.mlqo_max_threads.restype = c.c_int
+    _lib = lib
+    return lib
+
+
+def max_threads() -> int:
+    return int(_load().mlqo_max_threads())
+
+
+# --------------------------------------------------------------------------
+# meshes (Sec. 3.1)
+# --------------------------------------------------------------------------
+class Mesh:
+    """A structured simplicial mesh: dims, box lengths, nodes, elements."""
+
+    def __init__(self, dim, dims, lengths, xyz, conn):
+        self.dim = dim
+        self.dims = tuple(int(v) for v in dims)
+        self.lengths = tuple(float(v) for v in lengths)
+        self.xyz = xyz
+        self.conn = conn
+
+    @property
+    def n(self) -> int:
+        return self.xyz.shape[0]
+
+    @property
+    def ne(self) -> int:
+        return self.conn.shape[0]
+
+
+def mesh2d(m: int) -> Mesh:
+    """Unit square, m x m nodes, two triangles per square (see mlq_oracle.c)."""
+    xy = np.zeros((m * m, 2))
+    conn = np.zeros((2 * (m - 1) ** 2, 3), dtype=np.int32)
+    assert _load().mlqo_mesh2d(m, xy, conn) == 0
+    return Mesh(2, (m,), (1.0, 1.0), xy, conn)
+
+
+def mesh3d(mx: int, my: int, mz: int, lx: float = 1.0, ly: float = 1.0, lz: float = 0.25) -> Mesh:
+    """Box [0,lx]x[0,ly]x[0,lz], mx*my*mz nodes, six Kuhn tetrahedra per cube."""
+    xyz = np.zeros((mx * my * mz, 3))
+    conn = np.zeros((6 * (mx - 1) * (my - 1) * (mz - 1), 4), dtype=np.int32)
+    assert _load().mlqo_mesh3d(mx, my, mz, lx, ly, lz, xyz, conn) == 0
+    return Mesh(3, (mx, my, mz), (lx, ly, lz), xyz, conn)
+
+
+# --------------------------------------------------------------------------
+# matrices (Sec. 3.1, eq. AdmV)
+# --------------------------------------------------------------------------
+def assemble(mesh: Mesh, theta=None, s_l: float = 1.0, s_t: float = 0.2):
+    """CSR (rp, ci, M values, K values) of the consistent mass matrix and the
+    stiffness matrix of D = s_t I + (s_l - s_t) f f^T, f = (cos t, sin t[, 0])."""
+    lib = _load()
+    nnz = lib.mlqo_pattern_nnz(mesh.dim, mesh.n, mesh.ne, mesh.conn)
+    rp = np.zeros(mesh.n + 1, dtype=np.int64)
+    ci = np.zeros(nnz, dtype=np.int32)
+    mv = np.zeros(nnz)
+    kv = np.zeros(nnz)
+    th = None
+    if theta is not None:
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        assert th.shape == (mesh.ne,)
+    ptr = th.ctypes.data_as(ctypes.c_void_p) if th is not None else None
+    assert lib.mlqo_assemble(mesh.dim, mesh.n, mesh.xyz, mesh.ne, mesh.conn, ptr, s_l, s_t, rp, ci, mv, kv) == 0
+    return rp, ci, mv, kv
+
+
+def csr_to_dense(rp, ci, val, n):
+    A = np.zeros((n, n))
+    for i in range(n):
+        A[i, ci[rp[i]:rp[i + 1]]] = val[rp[i]:rp[i + 1]]
+    return A
+
+
+# --------------------------------------------------------------------------
+# KL expansion (Sec. 2.3)
+# --------------------------------------------------------------------------
+def kl_build(mesh: Mesh, sigma2: float, ell: float, K: int, return_factor: bool = False):
+    """Modes v_k (n x K, v_i^T M v_j = lambda_i delta_ij) and eigenvalues
+    lambda (K) of the rank-K pivoted-Cholesky KL expansion of the covariance
+    sigma2 exp(-|x-y|^2/ell) (eqs. approxEig, redEig)."""
+    lib = _load()
+    modes = np.zeros((mesh.n, K))
+    lam = np.zeros(K)
+    L = np.zeros((mesh.n, K)) if return_factor else None
+    piv = np.zeros(K, dtype=np.int64) if return_factor else None
+    st = lib.mlqo_kl_build(mesh.dim, mesh.n, mesh.xyz, mesh.ne, mesh.conn, sigma2, ell, K, modes, lam,
+                           L.ctypes.data_as(ctypes.c_void_p) if L is not None else None,
+                           piv.ctypes.data_as(ctypes.c_void_p) if piv is not None else None)
+    assert st == 0, st
+    if return_factor:
+        return modes, lam, L, piv
+    return modes, lam
+
+
+def centroid_table(fine: Mesh, modes_f: np.ndarray, coarse: Mesh) -> np.ndarray:
+    """Phi[e, k] = fine P1 interpolant of mode k at the centroid of coarse
+    element e: the midpoint-rule transfer of Sec. 4."""
+    K = modes_f.shape[1]
+    phi = np.zeros((coarse.ne, K))
+    fd = np.array(fine.dims, dtype=np.int32)
+    fl = np.array(fine.lengths, dtype=np.float64)
+    assert _load().mlqo_centroid_table(fine.dim, fd, fl, np.ascontiguousarray(modes_f), K, coarse.xyz,
+                                       coarse.ne, coarse.conn, phi) == 0
+    return phi
+
+
+# --------------------------------------------------------------------------
+# forward solve
+# --------------------------------------------------------------------------
+DEFAULT_MODEL = dict(s_l=1.0, s_t=0.2, a=0.1, eps=0.01, gamma=0.5)
+
+
+def _model_vec(model):
+    m = dict(DEFAULT_MODEL)
+    if model:
+        m.update(model)
+    return np.array([m["s_l"], m["s_t"], m["a"], m["eps"], m["gamma"]], dtype=np.float64)
+
+
+def initial_state(mesh: Mesh, radius: float = 0.1):
+    """v = 1 inside the ball of the given radius around the origin, else 0;
+    w = 0."""
+    r2 = np.sum(mesh.xyz ** 2, axis=1)
+    v = np.where(r2 <= radius * radius, 1.0, 0.0)
+    return v, np.zeros(mesh.n)
+
+
+def solve(mesh: Mesh, theta, dt: float, nsteps: int, v0=None, w0=None, model=None, rtol: float = 1e-13,
+          maxit: int | None = None):
+    """One sample with angle field theta (per element).  Returns
+    (Q, v_final, w_final, total CG iterations, status)."""
+    lib = _load()
+    if v0 is None:
+        v0, w0 = initial_state(mesh)
+    v = np.array(v0, dtype=np.float64)
+    w = np.zeros(mesh.n) if w0 is None else np.array(w0, dtype=np.float64)
+    q = ctypes.c_double()
+    it = ctypes.c_int64()
+    st = ctypes.c_int32()
+    maxit = 10 * mesh.n if maxit is None else maxit
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    assert lib.mlqo_solve(mesh.dim, mesh.n, mesh.xyz, mesh.ne, mesh.conn, th, _model_vec(model), dt, nsteps,
+                          rtol, maxit, v, w, ctypes.byref(q), ctypes.byref(it), ctypes.byref(st)) == 0
+    return q.value, v, w, it.value, st.value
+
+
+def solve_batch(mesh: Mesh, phi: np.ndarray, xi: np.ndarray, dt: float, nsteps: int, v0=None, w0=None,
+                theta_mean=None, model=None, rtol: float = 1e-13, maxit: int | None = None,
+                nthreads: int = 0):
+    """S samples: theta_e = theta_mean_e + sum_k phi[e,k] xi[s,k] (eq. KLlowrank).
+    Returns (Q[S], iters[S], status[S])."""
+    lib = _load()
+    xi = np.ascontiguousarray(xi, dtype=np.float64)
+    S, K = xi.shape
+    assert phi.shape == (mesh.ne, K)
+    if v0 is None:
+        v0, w0 = initial_state(mesh)
+    v0 = np.ascontiguousarray(v0, dtype=np.float64)
+    w0a = None if w0 is None else np.ascontiguousarray(w0, dtype=np.float64)
+    tm = None if theta_mean is None else np.ascontiguousarray(theta_mean, dtype=np.float64)
+    q = np.zeros(S)
+    it = np.zeros(S, dtype=np.int64)
+    st = np.zeros(S, dtype=np.int32)
+    maxit = 10 * mesh.n if maxit is None else maxit
+    assert lib.mlqo_solve_batch(mesh.dim, mesh.n, mesh.xyz, mesh.ne, mesh.conn, K, np.ascontiguousarray(phi),
+                                tm.ctypes.data_as(ctypes.c_void_p) if tm is not None else None, S, xi,
+                                _model_vec(model), dt, nsteps, rtol, maxit, v0,
+                                w0a.ctypes.data_as(ctypes.c_void_p) if w0a is not None else None, nthreads,
+                                q, it, st) == 0
+    return q, it, st
+
+
+# --------------------------------------------------------------------------
+# estimators (Sec. 4)
+# --------------------------------------------------------------------------
+def mc_estimate(q: np.ndarray):
+    """Plain Monte Carlo mean and its statistical RMSE sqrt(var/N)."""
+    q = np.asarray(q, dtype=np.float64)
+    n = q.size
+    mean = float(np.sum(q) / n)
+    var = float(np.sum((q - mean) ** 2) / (n - 1)) if n > 1 else 0.0
+    return mean, var, (var / n) ** 0.5
+
+
+def mlmc_estimate(y_levels):
+    """eq. StandardML with MC rules: sum over levels of the sample mean of
+    Y_l = F_l - F_{l-1} (F_{-1} = 0).  Returns (estimate, V_l list, RMSE_stat)
+    with RMSE_stat = sqrt(sum_l V_l / N_l)."""
+    est = 0.0
+    var = []
+    mse = 0.0
+    for y in y_levels:
+        m, v, _ = mc_estimate(y)
+        est += m
+        var.append(v)
+        mse += v / np.asarray(y).size
+    return est, var, mse ** 0.5
+
+
+def qmc_estimate(q_by_shift: np.ndarray):
+    """Randomly shifted lattice rule: rows = shifts, columns = points.  The
+    estimate is the mean of the per-shift means; its RMSE the standard
+    deviation of those means over sqrt(R)."""
+    q = np.asarray(q_by_shift, dtype=np.float64)
+    R = q.shape[0]
+    means = q.mean(axis=1)
+    est = float(means.mean())
+    rmse = float(np.std(means, ddof=1) / np.sqrt(R)) if R > 1 else 0.0
+    return est, rmse

@@ -1,0 +1,383 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each check is chosen so that a plausible slip in the oracle (a dropped term,
+a wrong sign or index, a transposed operand) fails at least one of them:
+
+* mesh volumes and the mass-matrix total (Sec. 3.1);
+* closed-form interior stencils: textbook 5-point / 7-point Laplacians and a
+  hand-derived constant-fibre stencil (Sec. 3.1 with eq. AdmV);
+* Lemma 2.1 (eigenvalues of G are g and |V|) read off the assembled matrix;
+* KL: M-orthogonality and the eigenvalue identities of eqs. approxEig/redEig,
+  and agreement with a dense generalised eigen-solver at full rank;
+* midpoint-rule transfer (Sec. 4) exact on linear fields;
+* the time-block solve against dense LU, the exact scalar recurrence for
+  spatially uniform states, per-block conservation, mirror symmetry;
+* the multilevel telescoping identity (eq. StandardML).
+"""
+import numpy as np
+import pytest
+import scipy.linalg
+
+import oracle as O
+from paper_2105_02007_gb300 import inputs
+
+SL, ST = 1.0, 0.2
+
+
+def simplex_volumes(mesh):
+    X = mesh.xyz[mesh.conn]                      # (ne, d+1, d)
+    J = X[:, 1:, :] - X[:, :1, :]
+    d = mesh.dim
+    return np.linalg.det(J) / (2.0 if d == 2 else 6.0)
+
+
+# --------------------------------------------------------------------------
+# meshes and matrices
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("m", [2, 5, 17])
+def test_mesh2d_counts_orientation_area(m):
+    mesh = O.mesh2d(m)
+    assert mesh.n == m * m and mesh.ne == 2 * (m - 1) ** 2
+    vol = simplex_volumes(mesh)
+    assert np.all(vol > 0)                       # counter-clockwise, non-degenerate
+    assert abs(vol.sum() - 1.0) < 1e-14
+
+
+def test_mesh3d_counts_volume():
+    mesh = O.mesh3d(4, 5, 3, 1.0, 1.0, 0.25)
+    assert mesh.n == 60 and mesh.ne == 6 * 3 * 4 * 2
+    vol = np.abs(simplex_volumes(mesh))
+    assert np.all(vol > 0)
+    assert abs(vol.sum() - 0.25) < 1e-14
+    # every tetrahedron of a cube has the same volume h^3/6
+    assert np.allclose(vol, vol[0], rtol=1e-13)
+
+
+@pytest.mark.parametrize("mesh_fn,area", [(lambda: O.mesh2d(9), 1.0),
+                                          (lambda: O.mesh3d(5, 5, 3, 1.0, 1.0, 0.25), 0.25)])
+def test_mass_total_and_stiffness_kernel(mesh_fn, area):
+    mesh = mesh_fn()
+    rng = np.random.default_rng(1)
+    rp, ci, mv, kv = O.assemble(mesh, rng.normal(size=mesh.ne), SL, ST)
+    M = O.csr_to_dense(rp, ci, mv, mesh.n)
+    K = O.csr_to_dense(rp, ci, kv, mesh.n)
+    assert abs(M.sum() - area) < 1e-15 * 10
+    assert np.max(np.abs(K.sum(axis=1))) < 1e-13          # K 1 = 0
+    assert np.max(np.abs(K - K.T)) < 1e-14                # symmetric
+    assert np.linalg.eigvalsh(K).min() > -1e-12           # positive semi-definite
+    assert np.linalg.eigvalsh(M).min() > 0                # mass SPD
+
+
+def test_mass_interior_stencil_2d():
+    m = 9
+    h = 1.0 / (m - 1)
+    mesh = O.mesh2d(m)
+    rp, ci, mv, _ = O.assemble(mesh)
+    M = O.csr_to_dense(rp, ci, mv, mesh.n)
+    i = 4 + m * 4
+    assert abs(M[i, i] - h * h / 2) < 1e-16
+    for off in (1, -1, m, -m, m + 1, -m - 1):
+        assert abs(M[i, i + off] - h * h / 12) < 1e-17
+    assert np.count_nonzero(M[i]) == 7
+
+
+def test_isotropic_stiffness_is_textbook_laplacian():
+    m = 7
+    mesh = O.mesh2d(m)
+    rp, ci, _, kv = O.assemble(mesh, None, 1.0, 1.0)
+    K = O.csr_to_dense(rp, ci, kv, mesh.n)
+    i = 3 + m * 3
+    expect = {0: 4.0, 1: -1.0, -1: -1.0, m: -1.0, -m: -1.0}
+    for j in range(mesh.n):
+        assert abs(K[i, j] - expect.get(j - i, 0.0)) < 1e-14
+    # 3D Kuhn tetrahedra: the 7-point Laplacian scaled by h
+    m3 = 5
+    h = 1.0 / (m3 - 1)
+    mesh3 = O.mesh3d(m3, m3, m3, 1.0, 1.0, 1.0)
+    rp, ci, _, kv = O.assemble(mesh3, None, 1.0, 1.0)
+    K3 = O.csr_to_dense(rp, ci, kv, mesh3.n)
+    i = 2 + m3 * (2 + m3 * 2)
+    exp3 = {0: 6 * h, 1: -h, -1: -h, m3: -h, -m3: -h, m3 * m3: -h, -m3 * m3: -h}
+    for j in range(mesh3.n):
+        assert abs(K3[i, j] - exp3.get(j - i, 0.0)) < 1e-14
+
+
+@pytest.mark.parametrize("th", [0.0, np.pi / 2, 0.3, -1.1])
+def test_constant_fibre_stencil_closed_form(th):
+    # For constant D = [[d11,d12],[d12,d22]] the P1 stencil of this
+    # triangulation (derived by hand from the six triangles around a node):
+    # centre 2(d11+d22-d12), E/W -(d11-d12), N/S -(d22-d12), NE/SW -d12.
+    m = 7
+    mesh = O.mesh2d(m)
+    rp, ci, _, kv = O.assemble(mesh, np.full(mesh.ne, th), SL, ST)
+    K = O.csr_to_dense(rp, ci, kv, mesh.n)
+    c, s = np.cos(th), np.sin(th)
+    d11 = ST + (SL - ST) * c * c
+    d22 = ST + (SL - ST) * s * s
+    d12 = (SL - ST) * c * s
+    i = 3 + m * 3
+    expect = {0: 2 * (d11 + d22 - d12), 1: -(d11 - d12), -1: -(d11 - d12), m: -(d22 - d12),
+              -m: -(d22 - d12), m + 1: -d12, -m - 1: -d12}
+    for j in range(mesh.n):
+        assert abs(K[i, j] - expect.get(j - i, 0.0)) < 1e-14
+
+
+@pytest.mark.parametrize("th", [0.0, 0.7, -2.0])
+def test_lemma_2_1_eigenvalues_of_conductivity(th):
+    # Lemma 2.1: G f = |V| f and G f_perp = g f_perp.  For constant D the P1
+    # stiffness applied to u = (a.x)^2/2 at an interior node equals
+    # -(a^T D a) times that node's lumped mass h^2, so a = f gives s_l and
+    # a = f_perp gives s_t.
+    m = 9
+    h = 1.0 / (m - 1)
+    mesh = O.mesh2d(m)
+    rp, ci, _, kv = O.assemble(mesh, np.full(mesh.ne, th), SL, ST)
+    K = O.csr_to_dense(rp, ci, kv, mesh.n)
+    i = 4 + m * 4
+    f = np.array([np.cos(th), np.sin(th)])
+    fp = np.array([-np.sin(th), np.cos(th)])
+    for a, lam in ((f, SL), (fp, ST)):
+        u = 0.5 * (mesh.xyz @ a) ** 2
+        assert abs((K @ u)[i] + lam * h * h) < 1e-13
+
+
+# --------------------------------------------------------------------------
+# KL expansion
+# --------------------------------------------------------------------------
+def _dense_cov(mesh, sigma2, ell):
+    d2 = ((mesh.xyz[:, None, :] - mesh.xyz[None, :, :]) ** 2).sum(-1)
+    return sigma2 * np.exp(-d2 / ell)
+
+
+def test_kl_m_orthogonality_and_trace():
+    mesh = O.mesh2d(17)
+    K = 12
+    modes, lam, L, piv = O.kl_build(mesh, 0.09, 0.04, K, return_factor=True)
+    rp, ci, mv, _ = O.assemble(mesh)
+    M = O.csr_to_dense(rp, ci, mv, mesh.n)
+    G = modes.T @ M @ modes
+    assert np.allclose(G, np.diag(lam), atol=1e-14 * lam.max() * 50)
+    assert np.all(np.diff(lam) <= 0) and lam[-1] > 0
+    assert abs(lam.sum() - np.trace(L.T @ M @ L)) < 1e-13
+    # pivoted Cholesky reproduces C at the pivots and never overshoots it
+    C = _dense_cov(mesh, 0.09, 0.04)
+    R = C - L @ L.T
+    assert np.max(np.abs(R[np.ix_(piv, piv)])) < 1e-12
+    assert np.linalg.eigvalsh(R).min() > -1e-12
+    # first pivot: all diagonals equal, tie broken towards node 0
+    assert piv[0] == 0
+    # truncated eigenvalue sum grows with K, bounded by tr(C M)
+    trCM = float(np.sum(C * M))
+    prev = 0.0
+    for k in (2, 6, 12, 24):
+        s = O.kl_build(mesh, 0.09, 0.04, k)[1].sum()
+        assert prev < s <= trCM * (1 + 1e-12)
+        prev = s
+    # KL modes solve M C_K M v = lambda M v with C_K = L L^T (eq. approxEig)
+    CK = L @ L.T
+    for k in range(K):
+        res = M @ CK @ M @ modes[:, k] - lam[k] * M @ modes[:, k]
+        assert np.linalg.norm(res) < 1e-12 * np.linalg.norm(lam[k] * M @ modes[:, k]) * 1e3
+
+
+def test_kl_full_rank_matches_dense_generalised_eigensolver():
+    mesh = O.mesh2d(4)
+    n = mesh.n
+    modes, lam = O.kl_build(mesh, 0.09, 0.5, n)
+    rp, ci, mv, _ = O.assemble(mesh)
+    M = O.csr_to_dense(rp, ci, mv, n)
+    C = _dense_cov(mesh, 0.09, 0.5)
+    ref = scipy.linalg.eigh(M @ C @ M, M, eigvals_only=True)[::-1]
+    big = ref > 1e-9 * ref[0]
+    assert np.allclose(lam[big], ref[big], rtol=1e-8)
+
+
+def test_kl_sign_convention():
+    mesh = O.mesh2d(9)
+    modes, _ = O.kl_build(mesh, 0.09, 0.04, 6)
+    for k in range(6):
+        j = int(np.argmax(np.abs(modes[:, k])))
+        assert modes[j, k] > 0
+
+
+# --------------------------------------------------------------------------
+# midpoint-rule transfer
+# --------------------------------------------------------------------------
+def test_centroid_table_finest_is_vertex_mean():
+    mesh = O.mesh2d(9)
+    rng = np.random.default_rng(3)
+    f = rng.normal(size=(mesh.n, 3))
+    phi = O.centroid_table(mesh, f, mesh)
+    assert np.allclose(phi, f[mesh.conn].mean(axis=1), atol=1e-14)
+
+
+def test_centroid_table_exact_on_linear_fields():
+    fine = O.mesh2d(17)
+    coarse = O.mesh2d(5)
+    f = np.stack([1.0 + 0 * fine.xyz[:, 0], fine.xyz[:, 0], 2 * fine.xyz[:, 1] - fine.xyz[:, 0]], axis=1)
+    phi = O.centroid_table(fine, f, coarse)
+    cen = coarse.xyz[coarse.conn].mean(axis=1)
+    ref = np.stack([np.ones(coarse.ne), cen[:, 0], 2 * cen[:, 1] - cen[:, 0]], axis=1)
+    assert np.allclose(phi, ref, atol=1e-14)
+    fine3 = O.mesh3d(9, 9, 5)
+    coarse3 = O.mesh3d(5, 5, 3)
+    f3 = np.stack([fine3.xyz[:, 0] - 3 * fine3.xyz[:, 2], fine3.xyz[:, 1]], axis=1)
+    phi3 = O.centroid_table(fine3, f3, coarse3)
+    c3 = coarse3.xyz[coarse3.conn].mean(axis=1)
+    assert np.allclose(phi3, np.stack([c3[:, 0] - 3 * c3[:, 2], c3[:, 1]], axis=1), atol=1e-14)
+
+
+def test_centroid_of_nested_coarse_triangle_is_central_fine_child():
+    # In red refinement the coarse centroid is the centroid of the central
+    # child, so the transfer equals the fine element's own midpoint value.
+    fine = O.mesh2d(9)
+    coarse = O.mesh2d(5)
+    rng = np.random.default_rng(5)
+    f = rng.normal(size=(fine.n, 1))
+    phi_c = O.centroid_table(fine, f, coarse)[:, 0]
+    phi_f = O.centroid_table(fine, f, fine)[:, 0]
+    cen_c = coarse.xyz[coarse.conn].mean(axis=1)
+    cen_f = fine.xyz[fine.conn].mean(axis=1)
+    for e in range(coarse.ne):
+        j = int(np.argmin(((cen_f - cen_c[e]) ** 2).sum(1)))
+        assert np.allclose(cen_f[j], cen_c[e], atol=1e-15)
+        assert abs(phi_c[e] - phi_f[j]) < 1e-14
+
+
+# --------------------------------------------------------------------------
+# forward solve
+# --------------------------------------------------------------------------
+def _dense_imex(mesh, theta, dt, nsteps, v, w, a=0.1, eps=0.01, gamma=0.5):
+    rp, ci, mv, kv = O.assemble(mesh, theta, SL, ST)
+    M = O.csr_to_dense(rp, ci, mv, mesh.n)
+    K = O.csr_to_dense(rp, ci, kv, mesh.n)
+    lu = scipy.linalg.lu_factor(M + dt * K)
+    v, w = v.copy(), w.copy()
+    for _ in range(nsteps):
+        R = v * (v - a) * (1 - v) - w
+        vn = scipy.linalg.lu_solve(lu, M @ (v + dt * R))
+        w = w + dt * eps * (v - gamma * w)
+        v = vn
+    return float(M.sum(axis=0) @ v), v, w
+
+
+@pytest.mark.parametrize("m,dt,nsteps", [(3, 0.05, 20), (5, 0.1, 30)])
+def test_solve_matches_dense_lu(m, dt, nsteps):
+    mesh = O.mesh2d(m)
+    rng = np.random.default_rng(m)
+    theta = rng.normal(scale=0.8, size=mesh.ne)
+    v0 = rng.uniform(0, 1, size=mesh.n)
+    w0 = rng.uniform(0, 0.1, size=mesh.n)
+    q, v, w, _, st = O.solve(mesh, theta, dt, nsteps, v0, w0)
+    qd, vd, wd = _dense_imex(mesh, theta, dt, nsteps, v0, w0)
+    assert st == 0
+    assert abs(q - qd) < 1e-12 * abs(qd)
+    assert np.max(np.abs(v - vd)) < 1e-11
+    assert np.max(np.abs(w - wd)) < 1e-14
+
+
+def test_solve_3d_matches_dense_lu():
+    mesh = O.mesh3d(3, 3, 3, 1.0, 1.0, 0.25)
+    rng = np.random.default_rng(7)
+    theta = rng.normal(size=mesh.ne)
+    v0 = rng.uniform(0, 1, size=mesh.n)
+    w0 = np.zeros(mesh.n)
+    q, v, _, _, st = O.solve(mesh, theta, 0.05, 10, v0, w0)
+    qd, vd, _ = _dense_imex(mesh, theta, 0.05, 10, v0, w0)
+    assert st == 0 and abs(q - qd) < 1e-12 * abs(qd) and np.max(np.abs(v - vd)) < 1e-11
+
+
+def test_uniform_state_follows_scalar_recurrence():
+    # K 1 = 0 and M (c 1) = c M 1: a spatially constant state evolves by the
+    # scalar IMEX recurrence regardless of the fibre field.
+    mesh = O.mesh2d(9)
+    rng = np.random.default_rng(11)
+    theta = rng.normal(size=mesh.ne)
+    v, w = 0.6, 0.05
+    dt, n = 0.05, 40
+    q, vf, wf, _, st = O.solve(mesh, theta, dt, n, np.full(mesh.n, v), np.full(mesh.n, w))
+    for _ in range(n):
+        R = v * (v - 0.1) * (1 - v) - w
+        v, w = v + dt * R, w + dt * 0.01 * (v - 0.5 * w)
+    assert st == 0
+    assert np.max(np.abs(vf - v)) < 1e-13 and np.max(np.abs(wf - w)) < 1e-15
+    assert abs(q - v) < 1e-13                     # area of the unit square is 1
+
+
+def test_one_block_conserves_mass_weighted_integral():
+    # 1^T (M + dt K) = 1^T M, so m^T v+ = m^T (v + dt R) up to the residual.
+    mesh = O.mesh2d(17)
+    rng = np.random.default_rng(13)
+    theta = rng.normal(size=mesh.ne)
+    v0 = rng.uniform(0, 1, size=mesh.n)
+    w0 = rng.uniform(0, 0.2, size=mesh.n)
+    dt = 0.05
+    q, *_ = O.solve(mesh, theta, dt, 1, v0, w0)
+    rp, ci, mv, _ = O.assemble(mesh)
+    mlump = O.csr_to_dense(rp, ci, mv, mesh.n).sum(axis=0)
+    R = v0 * (v0 - 0.1) * (1 - v0) - w0
+    assert abs(q - mlump @ (v0 + dt * R)) < 1e-13 * abs(q)
+
+
+def test_mirror_symmetry():
+    # Swapping x and y maps the mesh onto itself (lower <-> upper triangles)
+    # and the fibre angle t onto pi/2 - t; the quarter-disc start is symmetric.
+    m = 17
+    mesh = O.mesh2d(m)
+    rng = np.random.default_rng(17)
+    theta = rng.normal(scale=0.5, size=mesh.ne)
+    mirror = np.empty_like(theta)
+    for j in range(m - 1):
+        for i in range(m - 1):
+            c, cm = i + (m - 1) * j, j + (m - 1) * i
+            mirror[2 * cm + 1] = np.pi / 2 - theta[2 * c]
+            mirror[2 * cm + 0] = np.pi / 2 - theta[2 * c + 1]
+    q1 = O.solve(mesh, theta, 0.1, 30)[0]
+    q2 = O.solve(mesh, mirror, 0.1, 30)[0]
+    assert abs(q1 - q2) < 1e-11 * abs(q1)
+
+
+def test_batch_equals_single_and_kl_synthesis():
+    mesh = O.mesh2d(9)
+    modes, _ = O.kl_build(mesh, 0.09, 0.04, 4)
+    phi = O.centroid_table(mesh, modes, mesh)
+    xi = inputs.gaussian_xi(0, 0, 0, 3, 4)
+    q, it, st = O.solve_batch(mesh, phi, xi, 0.1, 10, nthreads=2)
+    for s in range(3):
+        theta = np.array([sum(phi[e, k] * xi[s, k] for k in range(4)) for e in range(mesh.ne)])
+        qs = O.solve(mesh, theta, 0.1, 10)[0]
+        assert abs(qs - q[s]) <= 1e-15 * abs(q[s])
+    assert np.all(st == 0) and np.all(it > 0)
+
+
+def test_maxiter_status():
+    mesh = O.mesh2d(9)
+    q, v, w, it, st = O.solve(mesh, np.zeros(mesh.ne), 0.1, 3, maxit=1)
+    assert st == 1 and it == 3
+
+
+# --------------------------------------------------------------------------
+# estimators
+# --------------------------------------------------------------------------
+def test_mlmc_telescoping_on_common_samples():
+    # sum_l (F_l - F_{l-1}) = F_L for every sample (eq. StandardML with the
+    # same points on all levels), so the ML estimate equals the SL one.
+    fine = O.mesh2d(17)
+    modes, _ = O.kl_build(fine, 0.09, 0.04, 4)
+    xi = inputs.gaussian_xi(0, 0, 0, 5, 4)
+    meshes = [O.mesh2d(5), O.mesh2d(9), fine]
+    dts = [0.2, 0.1, 0.05]
+    q = [O.solve_batch(mm, O.centroid_table(fine, modes, mm), xi, dt, int(round(1.0 / dt)))[0]
+         for mm, dt in zip(meshes, dts)]
+    y = [q[0]] + [q[l] - q[l - 1] for l in (1, 2)]
+    assert np.allclose(sum(y), q[2], rtol=1e-14, atol=0)
+    est, var, _ = O.mlmc_estimate(y)
+    assert abs(est - O.mc_estimate(q[2])[0]) < 1e-15
+
+
+def test_mc_and_qmc_estimators_plain_definitions():
+    q = np.array([1.0, 2.0, 4.0, 7.0])
+    mean, var, rmse = O.mc_estimate(q)
+    assert mean == 3.5 and abs(var - 7.0) < 1e-15 and abs(rmse - np.sqrt(7.0 / 4)) < 1e-15
+    est, r = O.qmc_estimate(np.array([[1.0, 3.0], [2.0, 4.0], [3.0, 5.0]]))
+    assert est == 3.0 and abs(r - 1.0 / np.sqrt(3)) < 1e-15
