@@ -1,0 +1,181 @@
+/*
+ * mlq.h -- C ABI of libmlq, a GB300 (sm_103a) implementation of the batched
+ * per-sample forward solve inside multilevel quadrature for the stochastic
+ * monodomain equation (Ben Bader, Harbrecht, Krause, Multerer, Quaglino,
+ * Schmidlin, "Space-time multilevel quadrature methods and their application
+ * for cardiac electrophysiology", arXiv 2105.02007).
+ *
+ * Conventions for every call:
+ *   - Every function returns an mlq_status (0 = MLQ_OK, negative = error);
+ *     mlq_strerror() gives a message.  No exception or exit() crosses the ABI.
+ *   - Host arrays are owned by the caller and only read (or written, for
+ *     outputs) during the call; the library copies what it keeps.
+ *   - Arrays documented as "host or device" may be either; the library asks
+ *     the CUDA driver which one a pointer is.  Device pointers must be on the
+ *     context's device; the caller keeps ownership.
+ *   - A context is used from one host thread at a time.
+ *   - Per-sample failures (iteration cap, NaN/Inf) come back in status[] and
+ *     never abort the other samples of a batch.
+ *
+ * Mesh convention (structured, shared with callers that build Phi tables):
+ *   2D, unit square, m x m nodes: node (i,j) = i + m*j at (i/(m-1), j/(m-1));
+ *   square (i,j), c = i + (m-1)*j, holds element 2c   = (i,j)(i+1,j)(i+1,j+1)
+ *                                      and element 2c+1 = (i,j)(i+1,j+1)(i,j+1).
+ *   Red refinement maps the m-node mesh to the (2m-1)-node mesh: the levels
+ *   are nested (Sec. 3.1 of the paper: nested meshes with h_l ~ 2^-l).
+ */
+#ifndef MLQ_H
+#define MLQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mlq_ctx mlq_ctx; /* opaque; owns the device state it allocates */
+
+typedef enum {
+    MLQ_OK = 0,
+    MLQ_EINVAL = -1,       /* bad argument (null pointer, size, unknown level) */
+    MLQ_ENOMEM = -2,       /* device or host allocation failed */
+    MLQ_ECUDA = -3,        /* a CUDA runtime call failed; see mlq_last_cuda_error */
+    MLQ_ENOTREADY = -4,    /* serving: the request has not finished */
+    MLQ_ETIMEOUT = -5,     /* a bounded wait ran out */
+    MLQ_EUNSUPPORTED = -6  /* valid request this build does not implement */
+} mlq_status;
+
+typedef enum { MLQ_FP64 = 0, MLQ_MIXED = 1 } mlq_precision;
+
+/* per-sample outcome written to status[] */
+typedef enum {
+    MLQ_S_CONVERGED = 0, /* every time block reached its tolerance */
+    MLQ_S_MAXITER = 1,   /* some block hit max_iter (the sample still finished) */
+    MLQ_S_NONFINITE = 2, /* NaN/Inf met: the sample stopped, its QoI is NaN */
+    MLQ_S_CANCELLED = 3
+} mlq_sample_status;
+
+/* Monodomain model with FitzHugh-Nagumo kinetics (eq. monodomain and
+ * eq. ionic_term; the two-variable nondimensional form):
+ *   dv/dt - div(D grad v) = v (v - a)(1 - v) - w,   dw/dt = eps (v - gamma w),
+ *   D = s_t I + (s_l - s_t) f f^T,  f = (cos t, sin t)             (eq. AdmV)
+ * with homogeneous Neumann boundary conditions on [0, T].
+ * Defaults: s_l 1.0, s_t 0.2, a 0.1, eps 0.01, gamma 0.5, T 10. */
+typedef struct {
+    double s_l, s_t, a, eps, gamma, T;
+} mlq_model;
+
+/* Solver options.
+ *   precision  MLQ_FP64: FP64 Jacobi-PCG per time block, stopping at
+ *                        ||r|| <= rtol ||b||.
+ *              MLQ_MIXED: FP32 Jacobi-PCG (FP32 stencil apply and vector
+ *                        updates, FP64 cross-thread dot sums) inside an FP64
+ *                        iterative-refinement loop whose FP64 residual stops
+ *                        at ||b - A v|| <= rtol ||b||; each FP32 solve stops
+ *                        at rtol_inner times its starting residual.
+ *   max_iter   cap on CG iterations per solve (per refinement sweep).
+ *   max_sweeps cap on refinement sweeps per block (MLQ_MIXED only).
+ *   cluster    CTAs per sample (1,2,4,8,16); 0 = chosen per level.
+ *   threads    threads per CTA (128..1024, multiple of 32); 0 = chosen. */
+typedef struct {
+    int precision;
+    double rtol;
+    double rtol_inner;
+    int max_iter;
+    int max_sweeps;
+    int cluster;
+    int threads;
+} mlq_options;
+
+/* Fill *opt / *model with the defaults listed above (rtol 1e-13 for FP64,
+ * rtol 1e-12 and rtol_inner 1e-5 for MIXED, max_iter 100000, max_sweeps 20). */
+int mlq_default_options(mlq_options *opt, int precision);
+int mlq_default_model(mlq_model *model);
+
+/* Create a context on CUDA device `device` issuing work on `cuda_stream`
+ * (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream; NULL = the
+ * legacy default stream).  opt may be NULL (FP64 defaults). */
+int mlq_create(mlq_ctx **out, int device, void *cuda_stream, const mlq_options *opt);
+int mlq_destroy(mlq_ctx *ctx);
+int mlq_set_options(mlq_ctx *ctx, const mlq_options *opt);
+int mlq_set_model(mlq_ctx *ctx, const mlq_model *model);
+
+/* Declare level `level` (0..15) of the nested hierarchy {T_l} (Sec. 3.1):
+ * a structured 2D mesh of m x m nodes on the unit square (dim = 2; dims[0] = m;
+ * lengths ignored) with time step dt and nsteps time blocks (nsteps dt = T).
+ * dim = 3 returns MLQ_EUNSUPPORTED in this build. */
+int mlq_add_level(mlq_ctx *ctx, int level, int dim, const int32_t *dims, const double *lengths, double dt,
+                  int32_t nsteps);
+
+/* Initial state of a level (host arrays of n nodes; w0 may be NULL = 0).
+ * Without this call a level starts from v = 1 where x^2 + y^2 <= radius^2,
+ * else 0, w = 0, with radius = 0.1 (mlq_set_initial_disk changes radius). */
+int mlq_set_initial_state(mlq_ctx *ctx, int level, const double *v0, const double *w0);
+int mlq_set_initial_disk(mlq_ctx *ctx, int level, double radius);
+
+/* KL mode table of a level: the fibre angle on element e is
+ *   theta_e = theta_mean[e] + sum_k phi[e*K + k] xi[k]         (eq. KLlowrank)
+ * phi: host, n_elem x K, row-major, FP64 (n_elem from the mesh convention);
+ * theta_mean: host, n_elem, may be NULL (= 0).  K <= 256.  The table holds the
+ * fine-level modes transferred to this level by the midpoint rule (Sec. 4,
+ * intergrid transfer): see mlq_centroid_table. */
+int mlq_set_kl(mlq_ctx *ctx, int level, int K, const double *phi, const double *theta_mean);
+
+/* Host helper: KL modes of the covariance c(x,y) = sigma2 exp(-|x-y|^2 / ell)
+ * on the structured 2D mesh of m x m nodes (dims[0] = m), by K steps of
+ * pivoted Cholesky C ~ L L^T (eq. approxEig) and the reduced K x K
+ * eigenproblem L^T M L v~ = lambda v~ with the P1 mass matrix M (eq. redEig).
+ * modes_out: host, n x K row-major, v_k = L v~_k (so v_i^T M v_j =
+ * lambda_i delta_ij), largest-magnitude entry positive; lambda_out: host, K,
+ * descending. */
+int mlq_build_kl(int dim, const int32_t *dims, const double *lengths, double sigma2, double ell, int K,
+                 double *modes_out, double *lambda_out);
+
+/* Host helper: midpoint-rule transfer (Sec. 4) of nodal modes on the fine
+ * structured mesh (fine_dims[0] = mf) to a coarse nested mesh (coarse_dims[0]
+ * = mc): phi_out[e*K + k] = fine P1 interpolant of mode k at the centroid of
+ * coarse element e.  modes_f: host, mf^2 x K; phi_out: host, n_elem_c x K. */
+int mlq_centroid_table(int dim, const int32_t *fine_dims, const double *modes_f, int K,
+                       const int32_t *coarse_dims, double *phi_out);
+
+/* Solve S samples (0 <= S <= 65535) on `level`.  xi: host or device, S x K row-major FP64
+ * (sample s uses xi[s*K .. s*K+K-1]).  For each sample: synthesise theta
+ * (eq. KLlowrank), set up A = M + dt K(theta), run the nsteps time blocks,
+ * and return the QoI Q = integral of v_h(T) = m^T v (m = M 1).
+ * with_coarse != 0 also solves the same samples on level-1 (same xi) and
+ * returns Y = Q_l - Q_{l-1} (eq. StandardML's level difference).
+ * Outputs (host or device, FP64 / int32, length S; any may be NULL):
+ *   q_fine, q_coarse, y, status (mlq_sample_status, worst of both members),
+ *   iters (CG iterations summed over blocks and sweeps, fine member).
+ * Blocks until the results are written. */
+int mlq_solve(mlq_ctx *ctx, int level, int64_t S, const double *xi, int with_coarse, double *q_fine,
+              double *q_coarse, double *y, int32_t *status, int32_t *iters);
+
+/* Multilevel Monte Carlo estimate (eq. StandardML with MC rules) over levels
+ * 0..L (L <= 5): level l draws N[l] samples (2 <= N[l] <= 65535) xi[l] (host or device, N[l] x K_l) and
+ * contributes the sample mean of Y_l = Q_l - Q_{l-1} (Q_{-1} = 0).  All
+ * levels run concurrently.  Outputs (host): mean_out = sum_l mean(Y_l);
+ * var_out[l] = unbiased sample variance of Y_l (may be NULL); rmse_out =
+ * sqrt(sum_l var_l / N_l) (may be NULL); y_out[l] (host or device, N[l],
+ * may be NULL or contain NULLs) the per-sample Y_l. */
+int mlq_estimate(mlq_ctx *ctx, int L, const int64_t *N, const double *const *xi, double *mean_out,
+                 double *var_out, double *rmse_out, double *const *y_out);
+
+/* Bytes of device workspace a solve of S samples on `level` (and level-1
+ * when with_coarse) uses; the context allocates and caches it. */
+int mlq_workspace_bytes(mlq_ctx *ctx, int level, int64_t S, int with_coarse, size_t *bytes);
+
+/* Count of kernel launches the context has issued since creation. */
+int mlq_launch_count(mlq_ctx *ctx, int64_t *count);
+
+/* Launch shape chosen for a level: cluster size and threads per CTA. */
+int mlq_level_launch(mlq_ctx *ctx, int level, int *cluster, int *threads);
+
+const char *mlq_strerror(int status);
+const char *mlq_last_cuda_error(mlq_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MLQ_H */

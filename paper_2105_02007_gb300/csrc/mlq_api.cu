@@ -1,0 +1,728 @@
+// mlq_api.cu -- host runtime and C ABI of libmlq (see include/mlq.h).
+//
+// A context owns: the model and solver options, the level table (structured
+// meshes of the nested hierarchy, KL mode tables in device memory, launch
+// shapes), a device workspace that grows on demand, and a small pool of
+// CUDA streams on which the members of a multilevel estimate run
+// concurrently.  All compute happens in the kernels of mlq_kernels.cuh.
+#include "mlq.h"
+#include "mlq_kernels.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace {
+
+constexpr int kMaxLevels = 16;
+constexpr int kMaxK = 256;
+constexpr int kStreams = 12;
+
+struct Level {
+    bool defined = false;
+    int dim = 2;
+    int m = 0;          // nodes per side
+    int n = 0, ne = 0;  // nodes, elements
+    double h = 0.0, dt = 0.0;
+    int nsteps = 0;
+    int K = 0;
+    double *d_phi = nullptr;         // ne x K
+    double *d_theta_mean = nullptr;  // ne or null
+    double *d_v0 = nullptr, *d_w0 = nullptr;
+    double radius = 0.1;
+    mlq::FastDiv divm{};
+};
+
+struct Member {
+    int level = 0;
+    int64_t S = 0;
+    const double *d_xi = nullptr;
+    // workspace pieces
+    double *cs2 = nullptr, *A64 = nullptr, *v = nullptr, *w = nullptr, *b = nullptr, *q = nullptr;
+    void *Ai = nullptr, *r = nullptr, *s = nullptr, *wc = nullptr, *p = nullptr, *x = nullptr;
+    int32_t *iters = nullptr, *status = nullptr;
+};
+
+}  // namespace
+
+struct mlq_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    mlq_options opt{};
+    mlq_model model{};
+    Level levels[kMaxLevels];
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaStream_t pool[kStreams] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[kStreams] = {};
+    int64_t launches = 0;
+    std::string cuda_error;
+    int max_cluster = 8;
+};
+
+namespace {
+
+#define MLQ_CUDA(ctx, call)                                                                  \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            (ctx)->cuda_error = std::string(#call) + ": " + cudaGetErrorString(e_);          \
+            return e_ == cudaErrorMemoryAllocation ? MLQ_ENOMEM : MLQ_ECUDA;                 \
+        }                                                                                    \
+    } while (0)
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+bool fastdiv_make(uint32_t d, uint32_t nmax, mlq::FastDiv *out)
+{
+    // mul = ceil(2^40 / d); exact for n * d < 2^40.  Verify on the range.
+    if (d == 0) return false;
+    if ((uint64_t)nmax * d >= (1ull << 40)) return false;
+    out->d = d;
+    out->mul = ((1ull << 40) + d - 1) / d;
+    for (uint32_t t = 0; t < nmax; ++t)
+        if (out->div(t) != t / d) return false;
+    return true;
+}
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// launch shape of a level: cluster size and threads per CTA
+void choose_launch(const mlq_ctx *ctx, const Level &L, int *cs, int *threads)
+{
+    int c = ctx->opt.cluster;
+    if (c <= 0) {
+        // aim at ~4k nodes per CTA
+        c = 1;
+        while (c < ctx->max_cluster && (L.n + c - 1) / c > 4096) c *= 2;
+    }
+    c = std::min(c, ctx->max_cluster);
+    int t = ctx->opt.threads;
+    if (t <= 0) {
+        const int per = (L.n + c - 1) / c;
+        t = per >= 2048 ? 512 : (per >= 768 ? 256 : 128);
+    }
+    *cs = c;
+    *threads = t;
+}
+
+size_t tile_bytes(const Level &L, int cs)
+{
+    const int rows = (L.m + cs - 1) / cs + 2;
+    return (size_t)std::min(rows, L.m) * L.m * sizeof(double);
+}
+
+template <typename TI, int CS>
+cudaError_t launch_slab(const mlq::SolveArgs<TI> &a, int nclusters, int threads, size_t smem, cudaStream_t st)
+{
+    auto kern = mlq::slab_solve_kernel<TI, CS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (CS > 8) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(nclusters * CS));
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+template <typename TI>
+cudaError_t launch_slab_cs(int cs, const mlq::SolveArgs<TI> &a, int nclusters, int threads, size_t smem,
+                           cudaStream_t st)
+{
+    switch (cs) {
+    case 1: return launch_slab<TI, 1>(a, nclusters, threads, smem, st);
+    case 2: return launch_slab<TI, 2>(a, nclusters, threads, smem, st);
+    case 4: return launch_slab<TI, 4>(a, nclusters, threads, smem, st);
+    case 8: return launch_slab<TI, 8>(a, nclusters, threads, smem, st);
+    case 16: return launch_slab<TI, 16>(a, nclusters, threads, smem, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// Bytes of workspace for one member (level, S samples).
+size_t member_bytes(const mlq_ctx *ctx, const Level &L, int64_t S)
+{
+    const bool mixed = ctx->opt.precision == MLQ_MIXED;
+    const size_t ti = mixed ? 4 : 8;
+    const size_t sn = (size_t)S * L.n;
+    size_t t = 0;
+    auto add = [&](size_t bytes) { t += align_up(bytes, 256); };
+    add((size_t)S * L.ne * 2 * 8);          // cs2
+    add(sn * mlq::kSlots2D * 8);            // A64
+    if (mixed) add(sn * mlq::kSlots2D * 4); // A32
+    add(sn * 8);                            // v
+    add(2 * sn * 8);                        // w
+    add(sn * 8);                            // b
+    add(2 * sn * ti);                       // r
+    add(2 * sn * ti);                       // s
+    add(2 * sn * ti);                       // wc
+    add(sn * ti);                           // p
+    add(sn * ti);                           // x
+    add((size_t)S * 8);                     // q
+    add((size_t)S * 4);                     // iters
+    add((size_t)S * 4);                     // status
+    return t;
+}
+
+void member_carve(const mlq_ctx *ctx, const Level &L, Member &mb, char *&cur)
+{
+    const bool mixed = ctx->opt.precision == MLQ_MIXED;
+    const size_t ti = mixed ? 4 : 8;
+    const size_t sn = (size_t)mb.S * L.n;
+    auto take = [&](size_t bytes) {
+        char *p = cur;
+        cur += align_up(bytes, 256);
+        return (void *)p;
+    };
+    mb.cs2 = (double *)take((size_t)mb.S * L.ne * 2 * 8);
+    mb.A64 = (double *)take(sn * mlq::kSlots2D * 8);
+    mb.Ai = mixed ? take(sn * mlq::kSlots2D * 4) : (void *)mb.A64;
+    mb.v = (double *)take(sn * 8);
+    mb.w = (double *)take(2 * sn * 8);
+    mb.b = (double *)take(sn * 8);
+    mb.r = take(2 * sn * ti);
+    mb.s = take(2 * sn * ti);
+    mb.wc = take(2 * sn * ti);
+    mb.p = take(sn * ti);
+    mb.x = take(sn * ti);
+    mb.q = (double *)take((size_t)mb.S * 8);
+    mb.iters = (int32_t *)take((size_t)mb.S * 4);
+    mb.status = (int32_t *)take((size_t)mb.S * 4);
+}
+
+int ensure_workspace(mlq_ctx *ctx, size_t bytes)
+{
+    if (bytes <= ctx->ws_bytes) return MLQ_OK;
+    if (ctx->ws) {
+        MLQ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        MLQ_CUDA(ctx, cudaFree(ctx->ws));
+        ctx->ws = nullptr;
+        ctx->ws_bytes = 0;
+    }
+    MLQ_CUDA(ctx, cudaMalloc(&ctx->ws, bytes));
+    ctx->ws_bytes = bytes;
+    return MLQ_OK;
+}
+
+template <typename TI>
+int launch_member_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream_t st)
+{
+    const bool mixed = sizeof(TI) == 4;
+    // K1: KL synthesis (theta -> cos 2t, sin 2t)
+    {
+        dim3 blk(256), grd((unsigned)((L.ne + 255) / 256), (unsigned)mb.S);
+        mlq::kl_synthesis_kernel<<<grd, blk, 0, st>>>(L.d_phi, L.d_theta_mean, mb.d_xi, L.K, L.ne, (int)mb.S,
+                                                        mb.cs2);
+        MLQ_CUDA(ctx, cudaGetLastError());
+        ctx->launches++;
+    }
+    // K2: stencil of A = M + dt K(theta)
+    {
+        dim3 blk(256), grd((unsigned)((L.n + 255) / 256), (unsigned)mb.S);
+        mlq::stencil_setup_kernel<<<grd, blk, 0, st>>>(mb.cs2, L.m, L.h, L.dt, ctx->model.s_l, ctx->model.s_t,
+                                                         (int)mb.S, mb.A64, mixed ? (float *)mb.Ai : nullptr);
+        MLQ_CUDA(ctx, cudaGetLastError());
+        ctx->launches++;
+    }
+    // K3-K6: all time blocks
+    mlq::SolveArgs<TI> a{};
+    a.m = L.m;
+    a.n = L.n;
+    a.divm = L.divm;
+    a.h2 = L.h * L.h;
+    a.dt = L.dt;
+    a.nsteps = L.nsteps;
+    a.a = ctx->model.a;
+    a.eps = ctx->model.eps;
+    a.gam = ctx->model.gamma;
+    a.rtol_out = ctx->opt.rtol;
+    a.rtol_in = ctx->opt.rtol_inner;
+    a.max_iter = ctx->opt.max_iter;
+    a.max_sweeps = mixed ? ctx->opt.max_sweeps : 1;
+    a.A64 = mb.A64;
+    a.Ai = (const TI *)mb.Ai;
+    a.v = mb.v;
+    a.w = mb.w;
+    a.b = mb.b;
+    a.r = (TI *)mb.r;
+    a.s = (TI *)mb.s;
+    a.wc = (TI *)mb.wc;
+    a.p = (TI *)mb.p;
+    a.x = (TI *)mb.x;
+    a.v0 = L.d_v0;
+    a.w0 = L.d_w0;
+    a.radius2 = L.radius * L.radius;
+    a.S = (int)mb.S;
+    a.q = mb.q;
+    a.iters = mb.iters;
+    a.status = mb.status;
+    int cs, threads;
+    choose_launch(ctx, L, &cs, &threads);
+    const size_t smem = tile_bytes(L, cs);
+    MLQ_CUDA(ctx, launch_slab_cs<TI>(cs, a, (int)mb.S, threads, smem, st));
+    ctx->launches++;
+    return MLQ_OK;
+}
+
+int launch_member(mlq_ctx *ctx, const Member &mb, cudaStream_t st)
+{
+    const Level &L = ctx->levels[mb.level];
+    if (ctx->opt.precision == MLQ_MIXED) return launch_member_t<float>(ctx, L, mb, st);
+    return launch_member_t<double>(ctx, L, mb, st);
+}
+
+int check_level(const mlq_ctx *ctx, int level)
+{
+    if (level < 0 || level >= kMaxLevels || !ctx->levels[level].defined) return MLQ_EINVAL;
+    if (!ctx->levels[level].d_phi) return MLQ_EINVAL;
+    return MLQ_OK;
+}
+
+int copy_out(mlq_ctx *ctx, void *dst, const void *src, size_t bytes, cudaStream_t st)
+{
+    if (!dst || bytes == 0) return MLQ_OK;
+    MLQ_CUDA(ctx, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
+    return MLQ_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int mlq_default_options(mlq_options *opt, int precision)
+{
+    if (!opt || (precision != MLQ_FP64 && precision != MLQ_MIXED)) return MLQ_EINVAL;
+    opt->precision = precision;
+    opt->rtol = precision == MLQ_FP64 ? 1e-13 : 1e-12;
+    opt->rtol_inner = 1e-5;
+    opt->max_iter = 100000;
+    opt->max_sweeps = 20;
+    opt->cluster = 0;
+    opt->threads = 0;
+    return MLQ_OK;
+}
+
+int mlq_default_model(mlq_model *m)
+{
+    if (!m) return MLQ_EINVAL;
+    m->s_l = 1.0;
+    m->s_t = 0.2;
+    m->a = 0.1;
+    m->eps = 0.01;
+    m->gamma = 0.5;
+    m->T = 10.0;
+    return MLQ_OK;
+}
+
+static int validate_options(const mlq_options *o)
+{
+    if (o->precision != MLQ_FP64 && o->precision != MLQ_MIXED) return MLQ_EINVAL;
+    if (!(o->rtol > 0.0) || !(o->rtol_inner > 0.0) || o->max_iter < 0 || o->max_sweeps < 1) return MLQ_EINVAL;
+    if (o->cluster != 0 && o->cluster != 1 && o->cluster != 2 && o->cluster != 4 && o->cluster != 8 &&
+        o->cluster != 16)
+        return MLQ_EINVAL;
+    if (o->threads != 0 && (o->threads < 64 || o->threads > 512 || o->threads % 32)) return MLQ_EINVAL;
+    return MLQ_OK;
+}
+
+int mlq_create(mlq_ctx **out, int device, void *cuda_stream, const mlq_options *opt)
+{
+    if (!out) return MLQ_EINVAL;
+    *out = nullptr;
+    mlq_options o;
+    if (opt) o = *opt;
+    else mlq_default_options(&o, MLQ_FP64);
+    if (validate_options(&o) != MLQ_OK) return MLQ_EINVAL;
+    mlq_ctx *ctx = new (std::nothrow) mlq_ctx();
+    if (!ctx) return MLQ_ENOMEM;
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->opt = o;
+    mlq_default_model(&ctx->model);
+    auto fail = [&](int code) {
+        mlq_destroy(ctx);
+        return code;
+    };
+    if (cudaSetDevice(device) != cudaSuccess) return fail(MLQ_ECUDA);
+    for (int k = 0; k < kStreams; ++k) {
+        if (cudaStreamCreateWithFlags(&ctx->pool[k], cudaStreamNonBlocking) != cudaSuccess) return fail(MLQ_ECUDA);
+        if (cudaEventCreateWithFlags(&ctx->ev_join[k], cudaEventDisableTiming) != cudaSuccess)
+            return fail(MLQ_ECUDA);
+    }
+    if (cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess) return fail(MLQ_ECUDA);
+    // largest cluster that can be resident with our largest shapes
+    int nonportable = 0;
+    cudaDeviceGetAttribute(&nonportable, cudaDevAttrClusterLaunch, device);
+    ctx->max_cluster = 8;
+    {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(16);
+        cfg.blockDim = dim3(512);
+        cfg.dynamicSmemBytes = 48 * 1024;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 16;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        auto kern = mlq::slab_solve_kernel<float, 16>;
+        int ncl = 0;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 48 * 1024) == cudaSuccess &&
+            cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg) == cudaSuccess && ncl > 0)
+            ctx->max_cluster = 16;
+        cudaGetLastError();
+    }
+    (void)nonportable;
+    if (o.cluster > ctx->max_cluster) return fail(MLQ_EUNSUPPORTED);
+    *out = ctx;
+    return MLQ_OK;
+}
+
+int mlq_destroy(mlq_ctx *ctx)
+{
+    if (!ctx) return MLQ_EINVAL;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (int k = 0; k < kStreams; ++k) {
+        if (ctx->pool[k]) {
+            cudaStreamSynchronize(ctx->pool[k]);
+            cudaStreamDestroy(ctx->pool[k]);
+        }
+        if (ctx->ev_join[k]) cudaEventDestroy(ctx->ev_join[k]);
+    }
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    for (auto &L : ctx->levels) {
+        cudaFree(L.d_phi);
+        cudaFree(L.d_theta_mean);
+        cudaFree(L.d_v0);
+        cudaFree(L.d_w0);
+    }
+    cudaFree(ctx->ws);
+    delete ctx;
+    return MLQ_OK;
+}
+
+int mlq_set_options(mlq_ctx *ctx, const mlq_options *opt)
+{
+    if (!ctx || !opt || validate_options(opt) != MLQ_OK) return MLQ_EINVAL;
+    if (opt->cluster > ctx->max_cluster) return MLQ_EUNSUPPORTED;
+    ctx->opt = *opt;
+    return MLQ_OK;
+}
+
+int mlq_set_model(mlq_ctx *ctx, const mlq_model *m)
+{
+    if (!ctx || !m) return MLQ_EINVAL;
+    if (!(m->s_l > 0.0) || !(m->s_t > 0.0) || !(m->T > 0.0)) return MLQ_EINVAL;
+    ctx->model = *m;
+    return MLQ_OK;
+}
+
+int mlq_add_level(mlq_ctx *ctx, int level, int dim, const int32_t *dims, const double *lengths, double dt,
+                  int32_t nsteps)
+{
+    (void)lengths;
+    if (!ctx || !dims || level < 0 || level >= kMaxLevels) return MLQ_EINVAL;
+    if (dim == 3) return MLQ_EUNSUPPORTED;
+    if (dim != 2) return MLQ_EINVAL;
+    const int m = dims[0];
+    if (m < 2 || m > 8193 || !(dt > 0.0) || nsteps < 0) return MLQ_EINVAL;
+    Level &L = ctx->levels[level];
+    cudaFree(L.d_phi);
+    cudaFree(L.d_theta_mean);
+    cudaFree(L.d_v0);
+    cudaFree(L.d_w0);
+    L = Level();
+    L.dim = 2;
+    L.m = m;
+    L.n = m * m;
+    L.ne = 2 * (m - 1) * (m - 1);
+    L.h = 1.0 / (double)(m - 1);
+    L.dt = dt;
+    L.nsteps = nsteps;
+    if (!fastdiv_make((uint32_t)m, (uint32_t)L.n, &L.divm)) return MLQ_EINVAL;
+    L.defined = true;
+    return MLQ_OK;
+}
+
+int mlq_set_initial_state(mlq_ctx *ctx, int level, const double *v0, const double *w0)
+{
+    if (!ctx || !v0 || level < 0 || level >= kMaxLevels || !ctx->levels[level].defined) return MLQ_EINVAL;
+    Level &L = ctx->levels[level];
+    MLQ_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (!L.d_v0) MLQ_CUDA(ctx, cudaMalloc(&L.d_v0, sizeof(double) * L.n));
+    MLQ_CUDA(ctx, cudaMemcpy(L.d_v0, v0, sizeof(double) * L.n, cudaMemcpyDefault));
+    if (w0) {
+        if (!L.d_w0) MLQ_CUDA(ctx, cudaMalloc(&L.d_w0, sizeof(double) * L.n));
+        MLQ_CUDA(ctx, cudaMemcpy(L.d_w0, w0, sizeof(double) * L.n, cudaMemcpyDefault));
+    } else if (L.d_w0) {
+        cudaFree(L.d_w0);
+        L.d_w0 = nullptr;
+    }
+    return MLQ_OK;
+}
+
+int mlq_set_initial_disk(mlq_ctx *ctx, int level, double radius)
+{
+    if (!ctx || level < 0 || level >= kMaxLevels || !ctx->levels[level].defined || !(radius >= 0.0))
+        return MLQ_EINVAL;
+    Level &L = ctx->levels[level];
+    cudaFree(L.d_v0);
+    cudaFree(L.d_w0);
+    L.d_v0 = L.d_w0 = nullptr;
+    L.radius = radius;
+    return MLQ_OK;
+}
+
+int mlq_set_kl(mlq_ctx *ctx, int level, int K, const double *phi, const double *theta_mean)
+{
+    if (!ctx || !phi || K < 1 || K > kMaxK || level < 0 || level >= kMaxLevels || !ctx->levels[level].defined)
+        return MLQ_EINVAL;
+    Level &L = ctx->levels[level];
+    MLQ_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaFree(L.d_phi);
+    cudaFree(L.d_theta_mean);
+    L.d_phi = L.d_theta_mean = nullptr;
+    MLQ_CUDA(ctx, cudaMalloc(&L.d_phi, sizeof(double) * (size_t)L.ne * K));
+    MLQ_CUDA(ctx, cudaMemcpy(L.d_phi, phi, sizeof(double) * (size_t)L.ne * K, cudaMemcpyDefault));
+    if (theta_mean) {
+        MLQ_CUDA(ctx, cudaMalloc(&L.d_theta_mean, sizeof(double) * (size_t)L.ne));
+        MLQ_CUDA(ctx, cudaMemcpy(L.d_theta_mean, theta_mean, sizeof(double) * (size_t)L.ne, cudaMemcpyDefault));
+    }
+    L.K = K;
+    return MLQ_OK;
+}
+
+int mlq_workspace_bytes(mlq_ctx *ctx, int level, int64_t S, int with_coarse, size_t *bytes)
+{
+    if (!ctx || !bytes || S < 0) return MLQ_EINVAL;
+    if (check_level(ctx, level) != MLQ_OK) return MLQ_EINVAL;
+    size_t t = member_bytes(ctx, ctx->levels[level], S);
+    if (with_coarse) {
+        if (check_level(ctx, level - 1) != MLQ_OK) return MLQ_EINVAL;
+        t += member_bytes(ctx, ctx->levels[level - 1], S);
+    }
+    t += align_up((size_t)S * ctx->levels[level].K * 8, 256);  // xi staging
+    t += align_up((size_t)S * 8, 256) + align_up((size_t)S * 4, 256) + 256;  // y, status, sums
+    *bytes = t;
+    return MLQ_OK;
+}
+
+int mlq_solve(mlq_ctx *ctx, int level, int64_t S, const double *xi, int with_coarse, double *q_fine,
+              double *q_coarse, double *y, int32_t *status, int32_t *iters)
+{
+    if (!ctx || !xi || S < 0 || S > 65535) return MLQ_EINVAL;
+    if (check_level(ctx, level) != MLQ_OK) return MLQ_EINVAL;
+    if (with_coarse) {
+        if (check_level(ctx, level - 1) != MLQ_OK) return MLQ_EINVAL;
+        if (ctx->levels[level - 1].K != ctx->levels[level].K) return MLQ_EINVAL;
+    }
+    if (S == 0) return MLQ_OK;
+    MLQ_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int K = ctx->levels[level].K;
+    size_t need = 0;
+    mlq_workspace_bytes(ctx, level, S, with_coarse, &need);
+    int st = ensure_workspace(ctx, need);
+    if (st != MLQ_OK) return st;
+    char *cur = (char *)ctx->ws;
+    Member mf, mc;
+    mf.level = level;
+    mf.S = S;
+    member_carve(ctx, ctx->levels[level], mf, cur);
+    if (with_coarse) {
+        mc.level = level - 1;
+        mc.S = S;
+        member_carve(ctx, ctx->levels[level - 1], mc, cur);
+    }
+    double *ybuf = (double *)cur;
+    cur += align_up((size_t)S * 8, 256);
+    double *sums = (double *)cur;
+    cur += 256;
+    int32_t *stbuf = (int32_t *)cur;
+    cur += align_up((size_t)S * 4, 256);
+    // xi on the device
+    const double *d_xi = xi;
+    if (!is_device_ptr(xi)) {
+        double *dx = (double *)cur;
+        MLQ_CUDA(ctx, cudaMemcpyAsync(dx, xi, sizeof(double) * S * K, cudaMemcpyHostToDevice, ctx->stream));
+        d_xi = dx;
+    }
+    mf.d_xi = d_xi;
+    mc.d_xi = d_xi;
+    // fork: fine on pool[0], coarse on pool[1]
+    MLQ_CUDA(ctx, cudaEventRecord(ctx->ev_fork, ctx->stream));
+    const int nm = with_coarse ? 2 : 1;
+    for (int k = 0; k < nm; ++k) {
+        MLQ_CUDA(ctx, cudaStreamWaitEvent(ctx->pool[k], ctx->ev_fork, 0));
+        st = launch_member(ctx, k == 0 ? mf : mc, ctx->pool[k]);
+        if (st != MLQ_OK) return st;
+        MLQ_CUDA(ctx, cudaEventRecord(ctx->ev_join[k], ctx->pool[k]));
+        MLQ_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_join[k], 0));
+    }
+    // K7
+    mlq::level_sums_kernel<<<1, 1024, 0, ctx->stream>>>(mf.q, with_coarse ? mc.q : nullptr, S, ybuf, sums);
+    MLQ_CUDA(ctx, cudaGetLastError());
+    ctx->launches++;
+    mlq::merge_status_kernel<<<(unsigned)((S + 255) / 256), 256, 0, ctx->stream>>>(
+        mf.status, with_coarse ? mc.status : nullptr, S, stbuf);
+    MLQ_CUDA(ctx, cudaGetLastError());
+    ctx->launches++;
+    if ((st = copy_out(ctx, q_fine, mf.q, S * 8, ctx->stream)) != MLQ_OK) return st;
+    if (with_coarse && (st = copy_out(ctx, q_coarse, mc.q, S * 8, ctx->stream)) != MLQ_OK) return st;
+    if ((st = copy_out(ctx, y, ybuf, S * 8, ctx->stream)) != MLQ_OK) return st;
+    if ((st = copy_out(ctx, status, stbuf, S * 4, ctx->stream)) != MLQ_OK) return st;
+    if ((st = copy_out(ctx, iters, mf.iters, S * 4, ctx->stream)) != MLQ_OK) return st;
+    MLQ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return MLQ_OK;
+}
+
+int mlq_estimate(mlq_ctx *ctx, int L, const int64_t *N, const double *const *xi, double *mean_out,
+                 double *var_out, double *rmse_out, double *const *y_out)
+{
+    if (!ctx || !N || !xi || !mean_out || L < 0 || L >= kMaxLevels) return MLQ_EINVAL;
+    if (2 * (L + 1) > kStreams) return MLQ_EUNSUPPORTED;
+    for (int l = 0; l <= L; ++l) {
+        if (check_level(ctx, l) != MLQ_OK || N[l] < 2 || N[l] > 65535 || !xi[l]) return MLQ_EINVAL;
+        if (ctx->levels[l].K != ctx->levels[0].K) return MLQ_EINVAL;
+    }
+    MLQ_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int K = ctx->levels[0].K;
+    size_t need = 4096;
+    for (int l = 0; l <= L; ++l) {
+        need += member_bytes(ctx, ctx->levels[l], N[l]);
+        if (l > 0) need += member_bytes(ctx, ctx->levels[l - 1], N[l]);
+        need += align_up((size_t)N[l] * 8, 256) * 2 + align_up((size_t)N[l] * K * 8, 256);
+    }
+    int st = ensure_workspace(ctx, need);
+    if (st != MLQ_OK) return st;
+    char *cur = (char *)ctx->ws;
+    std::vector<Member> fine(L + 1), coarse(L + 1);
+    std::vector<double *> ybuf(L + 1);
+    double *sums = (double *)cur;
+    cur += align_up(sizeof(double) * 2 * (L + 1), 256);
+    for (int l = 0; l <= L; ++l) {
+        fine[l].level = l;
+        fine[l].S = N[l];
+        member_carve(ctx, ctx->levels[l], fine[l], cur);
+        if (l > 0) {
+            coarse[l].level = l - 1;
+            coarse[l].S = N[l];
+            member_carve(ctx, ctx->levels[l - 1], coarse[l], cur);
+        }
+        ybuf[l] = (double *)cur;
+        cur += align_up((size_t)N[l] * 8, 256);
+        const double *d_xi = xi[l];
+        if (!is_device_ptr(xi[l])) {
+            double *dx = (double *)cur;
+            cur += align_up((size_t)N[l] * K * 8, 256);
+            MLQ_CUDA(ctx, cudaMemcpyAsync(dx, xi[l], sizeof(double) * N[l] * K, cudaMemcpyHostToDevice,
+                                          ctx->stream));
+            d_xi = dx;
+        }
+        fine[l].d_xi = coarse[l].d_xi = d_xi;
+    }
+    MLQ_CUDA(ctx, cudaEventRecord(ctx->ev_fork, ctx->stream));
+    // largest levels first so that they start first
+    int sid = 0;
+    for (int l = L; l >= 0; --l) {
+        for (int k = 0; k < (l > 0 ? 2 : 1); ++k) {
+            cudaStream_t s = ctx->pool[sid];
+            MLQ_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_fork, 0));
+            st = launch_member(ctx, k == 0 ? fine[l] : coarse[l], s);
+            if (st != MLQ_OK) return st;
+            MLQ_CUDA(ctx, cudaEventRecord(ctx->ev_join[sid], s));
+            MLQ_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_join[sid], 0));
+            ++sid;
+        }
+    }
+    for (int l = 0; l <= L; ++l) {
+        mlq::level_sums_kernel<<<1, 1024, 0, ctx->stream>>>(fine[l].q, l > 0 ? coarse[l].q : nullptr, N[l],
+                                                              ybuf[l], sums + 2 * l);
+        MLQ_CUDA(ctx, cudaGetLastError());
+        ctx->launches++;
+        if (y_out && y_out[l]) {
+            if ((st = copy_out(ctx, y_out[l], ybuf[l], (size_t)N[l] * 8, ctx->stream)) != MLQ_OK) return st;
+        }
+    }
+    std::vector<double> hs(2 * (L + 1));
+    MLQ_CUDA(ctx, cudaMemcpyAsync(hs.data(), sums, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+    MLQ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    double mean = 0.0, mse = 0.0;
+    for (int l = 0; l <= L; ++l) {
+        const double nl = (double)N[l];
+        const double v = hs[2 * l + 1] / (nl - 1.0);
+        mean += hs[2 * l] / nl;
+        mse += v / nl;
+        if (var_out) var_out[l] = v;
+    }
+    *mean_out = mean;
+    if (rmse_out) *rmse_out = std::sqrt(mse);
+    return MLQ_OK;
+}
+
+int mlq_launch_count(mlq_ctx *ctx, int64_t *count)
+{
+    if (!ctx || !count) return MLQ_EINVAL;
+    *count = ctx->launches;
+    return MLQ_OK;
+}
+
+int mlq_level_launch(mlq_ctx *ctx, int level, int *cluster, int *threads)
+{
+    if (!ctx || !cluster || !threads || level < 0 || level >= kMaxLevels || !ctx->levels[level].defined)
+        return MLQ_EINVAL;
+    choose_launch(ctx, ctx->levels[level], cluster, threads);
+    return MLQ_OK;
+}
+
+const char *mlq_strerror(int s)
+{
+    switch (s) {
+    case MLQ_OK: return "ok";
+    case MLQ_EINVAL: return "invalid argument";
+    case MLQ_ENOMEM: return "out of memory";
+    case MLQ_ECUDA: return "CUDA runtime error";
+    case MLQ_ENOTREADY: return "not ready";
+    case MLQ_ETIMEOUT: return "timed out";
+    case MLQ_EUNSUPPORTED: return "not supported by this build";
+    default: return "unknown status";
+    }
+}
+
+const char *mlq_last_cuda_error(mlq_ctx *ctx)
+{
+    return ctx ? ctx->cuda_error.c_str() : "";
+}
+
+}  // extern "C"

@@ -1,0 +1,207 @@
+// mlq_kl.cpp -- host-side setup of libmlq: KL modes (Sec. 2.3) and the
+// midpoint-rule transfer of the fibre field to coarser levels (Sec. 4).
+//
+// Runs once per configuration, before any sample is solved, so it is plain
+// C++ on the host.  The per-sample synthesis from these modes (eq. KLlowrank)
+// is kernel K1.
+#include "mlq.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <vector>
+
+namespace {
+
+struct Grid2 {
+    int m;
+    double h;
+    double x(int64_t node) const { return (double)(node % m) / (double)(m - 1); }
+    double y(int64_t node) const { return (double)(node / m) / (double)(m - 1); }
+};
+
+// y = M x for the P1 mass matrix of the structured triangulation, using the
+// closed-form entries: every triangle adds h^2/12 to the diagonal of each of
+// its vertices and h^2/24 to each of its edges.
+void mass_apply(const Grid2 &g, const double *x, double *y, int ncol)
+{
+    const int m = g.m, mc = m - 1;
+    const double d = g.h * g.h / 12.0, e = g.h * g.h / 24.0;
+    for (int j = 0; j < m; ++j)
+        for (int i = 0; i < m; ++i) {
+            const int64_t P = i + (int64_t)m * j;
+            const int cij = (i < mc && j < mc), cim = (i >= 1 && j < mc), cmm = (i >= 1 && j >= 1),
+                      cjm = (i < mc && j >= 1);
+            const int ninc = 2 * cij + cim + 2 * cmm + cjm;
+            for (int c = 0; c < ncol; ++c) {
+                double acc = ninc * d * x[P * ncol + c];
+                if (i + 1 < m) acc += e * (cij + cjm) * x[(P + 1) * ncol + c];
+                if (i > 0) acc += e * (cim + cmm) * x[(P - 1) * ncol + c];
+                if (j + 1 < m) acc += e * (cij + cim) * x[(P + m) * ncol + c];
+                if (j > 0) acc += e * (cjm + cmm) * x[(P - m) * ncol + c];
+                if (i + 1 < m && j + 1 < m) acc += e * 2 * cij * x[(P + m + 1) * ncol + c];
+                if (i > 0 && j > 0) acc += e * 2 * cmm * x[(P - m - 1) * ncol + c];
+                y[P * ncol + c] = acc;
+            }
+        }
+}
+
+// Symmetric eigen-decomposition by cyclic Jacobi rotations; the eigenvectors
+// are the columns of Q (row-major).
+void sym_eigen(int K, std::vector<double> A, std::vector<double> &lam, std::vector<double> &Q)
+{
+    Q.assign((size_t)K * K, 0.0);
+    for (int k = 0; k < K; ++k) Q[(size_t)k * K + k] = 1.0;
+    auto at = [&](int r, int c) -> double & { return A[(size_t)r * K + c]; };
+    for (int sweep = 0; sweep < 64; ++sweep) {
+        double off = 0.0, diag = 0.0;
+        for (int r = 0; r < K; ++r)
+            for (int c = 0; c < K; ++c) (r == c ? diag : off) += at(r, c) * at(r, c);
+        if (off <= 1e-32 * diag) break;
+        for (int p = 0; p + 1 < K; ++p)
+            for (int q = p + 1; q < K; ++q) {
+                const double apq = at(p, q);
+                if (apq == 0.0) continue;
+                const double theta = (at(q, q) - at(p, p)) / (2.0 * apq);
+                const double t = std::copysign(1.0, theta) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < K; ++k) {  // columns p, q
+                    const double x = at(k, p), y = at(k, q);
+                    at(k, p) = c * x - s * y;
+                    at(k, q) = s * x + c * y;
+                }
+                for (int k = 0; k < K; ++k) {  // rows p, q
+                    const double x = at(p, k), y = at(q, k);
+                    at(p, k) = c * x - s * y;
+                    at(q, k) = s * x + c * y;
+                }
+                for (int k = 0; k < K; ++k) {
+                    const double x = Q[(size_t)k * K + p], y = Q[(size_t)k * K + q];
+                    Q[(size_t)k * K + p] = c * x - s * y;
+                    Q[(size_t)k * K + q] = s * x + c * y;
+                }
+            }
+    }
+    lam.resize(K);
+    for (int k = 0; k < K; ++k) lam[k] = at(k, k);
+}
+
+// Value at point (px, py) of the P1 interpolant of K nodal fields on the
+// m x m structured triangulation.
+void p1_at(const Grid2 &g, const double *f, int K, double px, double py, double *out)
+{
+    const int m = g.m;
+    const double sx = px * (m - 1), sy = py * (m - 1);
+    int i = std::min(std::max((int)std::floor(sx), 0), m - 2);
+    int j = std::min(std::max((int)std::floor(sy), 0), m - 2);
+    const double u = sx - i, w = sy - j;
+    const int64_t a = i + (int64_t)m * j;
+    // lower triangle (u >= w): (i,j) (i+1,j) (i+1,j+1); upper: (i,j) (i+1,j+1) (i,j+1)
+    double wa, wb, wc;
+    int64_t nb, nc;
+    if (u >= w) {
+        wa = 1.0 - u; wb = u - w; wc = w;
+        nb = a + 1; nc = a + m + 1;
+    } else {
+        wa = 1.0 - w; wb = u; wc = w - u;
+        nb = a + m + 1; nc = a + m;
+    }
+    for (int k = 0; k < K; ++k) out[k] = wa * f[a * K + k] + wb * f[nb * K + k] + wc * f[nc * K + k];
+}
+
+}  // namespace
+
+extern "C" {
+
+int mlq_build_kl(int dim, const int32_t *dims, const double *lengths, double sigma2, double ell, int K,
+                 double *modes_out, double *lambda_out)
+{
+    (void)lengths;
+    if (dim == 3) return MLQ_EUNSUPPORTED;
+    if (dim != 2 || !dims || !modes_out || !lambda_out || !(sigma2 > 0.0) || !(ell > 0.0)) return MLQ_EINVAL;
+    const int m = dims[0];
+    if (m < 2) return MLQ_EINVAL;
+    const int64_t n = (int64_t)m * m;
+    if (K < 1 || K > n || K > 4096) return MLQ_EINVAL;
+    Grid2 g{m, 1.0 / (m - 1)};
+    std::vector<double> xs(n), ys(n);
+    for (int64_t t = 0; t < n; ++t) {
+        xs[t] = g.x(t);
+        ys[t] = g.y(t);
+    }
+    auto cov = [&](int64_t a, int64_t b) {
+        const double dx = xs[a] - xs[b], dy = ys[a] - ys[b];
+        return sigma2 * std::exp(-(dx * dx + dy * dy) / ell);
+    };
+    // pivoted Cholesky: L (n x K, row-major), residual diagonal r
+    std::vector<double> L((size_t)n * K, 0.0), r(n, sigma2);
+    for (int k = 0; k < K; ++k) {
+        int64_t piv = std::max_element(r.begin(), r.end()) - r.begin();  // first maximum
+        const double lp = std::sqrt(r[piv]);
+        if (!(lp > 0.0)) return MLQ_EINVAL;
+        for (int64_t t = 0; t < n; ++t) {
+            double c = cov(t, piv);
+            for (int q = 0; q < k; ++q) c -= L[(size_t)t * K + q] * L[(size_t)piv * K + q];
+            L[(size_t)t * K + k] = c / lp;
+        }
+        for (int64_t t = 0; t < n; ++t) r[t] -= L[(size_t)t * K + k] * L[(size_t)t * K + k];
+    }
+    // B = L^T (M L)
+    std::vector<double> ML((size_t)n * K);
+    mass_apply(g, L.data(), ML.data(), K);
+    std::vector<double> B((size_t)K * K, 0.0);
+    for (int a = 0; a < K; ++a)
+        for (int c = a; c < K; ++c) {
+            double s = 0.0;
+            for (int64_t t = 0; t < n; ++t) s += L[(size_t)t * K + a] * ML[(size_t)t * K + c];
+            B[(size_t)a * K + c] = s;
+        }
+    for (int a = 0; a < K; ++a)
+        for (int c = 0; c < a; ++c) B[(size_t)a * K + c] = B[(size_t)c * K + a];
+    std::vector<double> lam, Q;
+    sym_eigen(K, B, lam, Q);
+    std::vector<int> ord(K);
+    for (int k = 0; k < K; ++k) ord[k] = k;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) { return lam[a] > lam[c]; });
+    for (int k = 0; k < K; ++k) {
+        const int src = ord[k];
+        lambda_out[k] = lam[src];
+        double big = 0.0;
+        int64_t arg = 0;
+        for (int64_t t = 0; t < n; ++t) {
+            double s = 0.0;
+            for (int q = 0; q < K; ++q) s += L[(size_t)t * K + q] * Q[(size_t)q * K + src];
+            modes_out[(size_t)t * K + k] = s;
+            if (std::fabs(s) > big) {
+                big = std::fabs(s);
+                arg = t;
+            }
+        }
+        if (modes_out[(size_t)arg * K + k] < 0.0)
+            for (int64_t t = 0; t < n; ++t) modes_out[(size_t)t * K + k] = -modes_out[(size_t)t * K + k];
+    }
+    return MLQ_OK;
+}
+
+int mlq_centroid_table(int dim, const int32_t *fine_dims, const double *modes_f, int K, const int32_t *coarse_dims,
+                       double *phi_out)
+{
+    if (dim == 3) return MLQ_EUNSUPPORTED;
+    if (dim != 2 || !fine_dims || !coarse_dims || !modes_f || !phi_out || K < 1) return MLQ_EINVAL;
+    const int mf = fine_dims[0], mc = coarse_dims[0];
+    if (mf < 2 || mc < 2) return MLQ_EINVAL;
+    Grid2 gf{mf, 1.0 / (mf - 1)};
+    const double H = 1.0 / (mc - 1);
+    for (int j = 0; j + 1 < mc; ++j)
+        for (int i = 0; i + 1 < mc; ++i) {
+            const int64_t c = i + (int64_t)(mc - 1) * j;
+            // centroids of the lower and upper triangle of square (i, j)
+            const double xl = (i + 2.0 / 3.0) * H, yl = (j + 1.0 / 3.0) * H;
+            const double xu = (i + 1.0 / 3.0) * H, yu = (j + 2.0 / 3.0) * H;
+            p1_at(gf, modes_f, K, xl, yl, phi_out + (2 * c) * K);
+            p1_at(gf, modes_f, K, xu, yu, phi_out + (2 * c + 1) * K);
+        }
+    return MLQ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,243 @@
+"""Thin ctypes binding of libmlq (include/mlq.h): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels; this module never
+computes the method.  Arrays may be numpy arrays (host) or torch CUDA tensors
+(device); outputs are returned as numpy arrays unless device tensors are
+passed in.  If the compiled library is missing this module raises at import
+time: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libmlq.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libmlq is not built ({LIB_PATH} missing); run paper_2105_02007_gb300.build.build()")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+MLQ_FP64, MLQ_MIXED = 0, 1
+S_CONVERGED, S_MAXITER, S_NONFINITE, S_CANCELLED = 0, 1, 2, 3
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("rtol", ctypes.c_double), ("rtol_inner", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("max_sweeps", ctypes.c_int), ("cluster", ctypes.c_int),
+                ("threads", ctypes.c_int)]
+
+
+class Model(ctypes.Structure):
+    _fields_ = [("s_l", ctypes.c_double), ("s_t", ctypes.c_double), ("a", ctypes.c_double),
+                ("eps", ctypes.c_double), ("gamma", ctypes.c_double), ("T", ctypes.c_double)]
+
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_lib.mlq_default_options.argtypes = [ctypes.POINTER(Options), ctypes.c_int]
+_lib.mlq_default_model.argtypes = [ctypes.POINTER(Model)]
+_lib.mlq_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, _vp, ctypes.POINTER(Options)]
+_lib.mlq_destroy.argtypes = [_vp]
+_lib.mlq_set_options.argtypes = [_vp, ctypes.POINTER(Options)]
+_lib.mlq_set_model.argtypes = [_vp, ctypes.POINTER(Model)]
+_lib.mlq_add_level.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_double, ctypes.c_int32]
+_lib.mlq_set_initial_state.argtypes = [_vp, ctypes.c_int, _vp, _vp]
+_lib.mlq_set_initial_disk.argtypes = [_vp, ctypes.c_int, ctypes.c_double]
+_lib.mlq_set_kl.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp]
+_lib.mlq_build_kl.argtypes = [ctypes.c_int, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, _vp, _vp]
+_lib.mlq_centroid_table.argtypes = [ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp]
+_lib.mlq_solve.argtypes = [_vp, ctypes.c_int, _i64, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
+_lib.mlq_estimate.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.mlq_workspace_bytes.argtypes = [_vp, ctypes.c_int, _i64, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
+_lib.mlq_launch_count.argtypes = [_vp, ctypes.POINTER(_i64)]
+_lib.mlq_level_launch.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+_lib.mlq_strerror.restype = ctypes.c_char_p
+_lib.mlq_strerror.argtypes = [ctypes.c_int]
+_lib.mlq_last_cuda_error.restype = ctypes.c_char_p
+_lib.mlq_last_cuda_error.argtypes = [_vp]
+
+EXPORTED = ["mlq_default_options", "mlq_default_model", "mlq_create", "mlq_destroy", "mlq_set_options",
+            "mlq_set_model", "mlq_add_level", "mlq_set_initial_state", "mlq_set_initial_disk", "mlq_set_kl",
+            "mlq_build_kl", "mlq_centroid_table", "mlq_solve", "mlq_estimate", "mlq_workspace_bytes",
+            "mlq_launch_count", "mlq_level_launch", "mlq_strerror", "mlq_last_cuda_error"]
+
+
+class MLQError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str = ""):
+        msg = f"{where}: {_lib.mlq_strerror(code).decode()} ({code})"
+        if detail:
+            msg += f": {detail}"
+        super().__init__(msg)
+        self.code = code
+
+
+def _check(code: int, where: str, ctx=None):
+    if code != 0:
+        detail = _lib.mlq_last_cuda_error(ctx).decode() if ctx else ""
+        raise MLQError(code, where, detail)
+
+
+def _host(a, dtype):
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr, arr.ctypes.data_as(_vp)
+
+
+def _ptr(a, dtype):
+    """Pointer to a numpy array (made contiguous) or a torch tensor (host or
+    CUDA).  Returns (keepalive, pointer)."""
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        assert a.is_contiguous()
+        return a, _vp(a.data_ptr())
+    return _host(a, dtype)
+
+
+def default_options(precision: int = MLQ_FP64, **kw) -> Options:
+    o = Options()
+    _check(_lib.mlq_default_options(ctypes.byref(o), precision), "mlq_default_options")
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def default_model(**kw) -> Model:
+    m = Model()
+    _check(_lib.mlq_default_model(ctypes.byref(m)), "mlq_default_model")
+    for k, v in kw.items():
+        setattr(m, k, v)
+    return m
+
+
+def build_kl(m: int, sigma2: float, ell: float, K: int):
+    """KL modes (n x K) and eigenvalues (K) on the m x m structured mesh."""
+    dims = np.array([m, 0, 0], dtype=np.int32)
+    modes = np.zeros((m * m, K))
+    lam = np.zeros(K)
+    _check(_lib.mlq_build_kl(2, dims.ctypes.data_as(_vp), None, sigma2, ell, K, modes.ctypes.data_as(_vp),
+                             lam.ctypes.data_as(_vp)), "mlq_build_kl")
+    return modes, lam
+
+
+def centroid_table(m_fine: int, modes_f: np.ndarray, m_coarse: int) -> np.ndarray:
+    """Midpoint-rule transfer of fine nodal modes to the coarse elements."""
+    K = modes_f.shape[1]
+    fd = np.array([m_fine, 0, 0], dtype=np.int32)
+    cd = np.array([m_coarse, 0, 0], dtype=np.int32)
+    mf, pm = _host(modes_f, np.float64)
+    phi = np.zeros((2 * (m_coarse - 1) ** 2, K))
+    _check(_lib.mlq_centroid_table(2, fd.ctypes.data_as(_vp), pm, K, cd.ctypes.data_as(_vp),
+                                   phi.ctypes.data_as(_vp)), "mlq_centroid_table")
+    return phi
+
+
+class Context:
+    """One libmlq context on a CUDA device, issuing work on a CUDA stream."""
+
+    def __init__(self, device: int = 0, precision: int = MLQ_FP64, stream=None, **opts):
+        self._h = _vp()
+        self.options = default_options(precision, **opts)
+        sp = _vp(stream) if stream else None
+        _check(_lib.mlq_create(ctypes.byref(self._h), device, sp, ctypes.byref(self.options)), "mlq_create")
+        self.levels = {}
+
+    def close(self):
+        if self._h:
+            _lib.mlq_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_options(self, **kw):
+        for k, v in kw.items():
+            setattr(self.options, k, v)
+        _check(_lib.mlq_set_options(self._h, ctypes.byref(self.options)), "mlq_set_options", self._h)
+
+    def set_model(self, **kw):
+        _check(_lib.mlq_set_model(self._h, ctypes.byref(default_model(**kw))), "mlq_set_model", self._h)
+
+    def add_level(self, level: int, m: int, dt: float, nsteps: int, dim: int = 2):
+        dims = np.array([m, 0, 0], dtype=np.int32)
+        _check(_lib.mlq_add_level(self._h, level, dim, dims.ctypes.data_as(_vp), None, dt, nsteps),
+               "mlq_add_level", self._h)
+        self.levels[level] = dict(m=m, dt=dt, nsteps=nsteps, n=m * m, ne=2 * (m - 1) ** 2)
+
+    def set_initial_state(self, level: int, v0, w0=None):
+        v, pv = _host(v0, np.float64)
+        w, pw = (None, None) if w0 is None else _host(w0, np.float64)
+        _check(_lib.mlq_set_initial_state(self._h, level, pv, pw), "mlq_set_initial_state", self._h)
+
+    def set_initial_disk(self, level: int, radius: float):
+        _check(_lib.mlq_set_initial_disk(self._h, level, radius), "mlq_set_initial_disk", self._h)
+
+    def set_kl(self, level: int, phi: np.ndarray, theta_mean=None):
+        p, pp = _host(phi, np.float64)
+        t, pt = (None, None) if theta_mean is None else _host(theta_mean, np.float64)
+        _check(_lib.mlq_set_kl(self._h, level, p.shape[1], pp, pt), "mlq_set_kl", self._h)
+        self.levels[level]["K"] = p.shape[1]
+
+    def solve(self, level: int, xi, with_coarse: bool = False, out=None):
+        """Solve the samples xi (S x K) on `level` (and level-1).  Returns a
+        dict of numpy arrays q_fine, q_coarse, y, status, iters, or fills the
+        given device tensors in `out`."""
+        xk, px = _ptr(xi, np.float64)
+        S = int(xi.shape[0])
+        if out is None:
+            res = dict(q_fine=np.zeros(S), q_coarse=np.zeros(S) if with_coarse else None,
+                       y=np.zeros(S), status=np.zeros(S, dtype=np.int32), iters=np.zeros(S, dtype=np.int32))
+        else:
+            res = out
+        ptrs = {k: (None if v is None else _ptr(v, np.float64 if k in ("q_fine", "q_coarse", "y") else np.int32)[1])
+                for k, v in res.items()}
+        _check(_lib.mlq_solve(self._h, level, S, px, int(bool(with_coarse)), ptrs.get("q_fine"),
+                              ptrs.get("q_coarse"), ptrs.get("y"), ptrs.get("status"), ptrs.get("iters")),
+               "mlq_solve", self._h)
+        return res
+
+    def estimate(self, xis, return_y: bool = False):
+        """MLMC over levels 0..L with xis[l] (N_l x K).  Returns (mean,
+        var_l, rmse[, y_l])."""
+        L = len(xis) - 1
+        keep = [_ptr(x, np.float64) for x in xis]
+        N = np.array([int(x.shape[0]) for x in xis], dtype=np.int64)
+        xp = (_vp * (L + 1))(*[k[1] for k in keep])
+        mean = ctypes.c_double()
+        var = np.zeros(L + 1)
+        rmse = ctypes.c_double()
+        ys = [np.zeros(int(n)) for n in N] if return_y else None
+        yp = (_vp * (L + 1))(*[y.ctypes.data_as(_vp) for y in ys]) if return_y else None
+        _check(_lib.mlq_estimate(self._h, L, N.ctypes.data_as(_vp), xp, ctypes.byref(mean),
+                                 var.ctypes.data_as(_vp), ctypes.byref(rmse), yp), "mlq_estimate", self._h)
+        if return_y:
+            return mean.value, var, rmse.value, ys
+        return mean.value, var, rmse.value
+
+    def workspace_bytes(self, level: int, S: int, with_coarse: bool = False) -> int:
+        b = ctypes.c_size_t()
+        _check(_lib.mlq_workspace_bytes(self._h, level, S, int(with_coarse), ctypes.byref(b)),
+               "mlq_workspace_bytes", self._h)
+        return b.value
+
+    def launch_count(self) -> int:
+        c = _i64()
+        _check(_lib.mlq_launch_count(self._h, ctypes.byref(c)), "mlq_launch_count")
+        return c.value
+
+    def level_launch(self, level: int):
+        c, t = ctypes.c_int(), ctypes.c_int()
+        _check(_lib.mlq_level_launch(self._h, level, ctypes.byref(c), ctypes.byref(t)), "mlq_level_launch")
+        return c.value, t.value
