@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark: multilevel Monte Carlo for the stochastic monodomain equation.
+
+Workload (one "step" = one complete MLMC estimate, every level's fine and
+coarse members):
+  unit square, nested P1 triangulations on 17^2, 33^2, 65^2, 129^2, 257^2
+  nodes; dt_l = 0.1 * 2^-l over T = 10 (100 ... 1600 time blocks);
+  4096 / 1024 / 256 / 64 / 16 samples per level; FitzHugh-Nagumo kinetics
+  (s_l 1, s_t 0.2, a 0.1, eps 0.01, gamma 0.5); initial quarter disc of
+  radius 0.1; fibre angle = Gaussian KL field, 16 modes of
+  0.09 exp(-|x-y|^2/0.04) on the finest mesh; xi ~ N(0,1) from Philox,
+  seed = rank; QoI = integral of v at T.  Mixed precision (FP32 inner PCG in
+  FP64 refinement to 1e-12), all levels running concurrently.
+
+Metric: DOF-steps/s (node x time block x sample, fine and coarse members
+both counted); time-to-RMSE = wall time of one estimate.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mlq|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+LEVEL_M = [17, 33, 65, 129, 257]
+LEVEL_N = [4096, 1024, 256, 64, 16]
+K_MODES = 16
+SIGMA2, ELL = 0.09, 0.04
+T_END = 10.0
+WORKLOAD = "MLMC 2D monodomain, 5 nested levels 17^2..257^2, N=4096/1024/256/64/16, K=16"
+METRIC = "MLMC DOF-steps/s (time-to-RMSE of one estimate alongside)"
+UNIT = "DOF-steps/s"
+# algorithmic bytes the method moves per DOF (2D, mixed FP32 inner PCG):
+# per CG iteration 4 stencil coefficients (16 B) + SpMV operand/result (8 B)
+# + vector updates (32 B); per time block the reaction/load/residual pass
+# with FP64 state (~64 B).  FP64 doubles both.
+BYTES_PER_DOF_ITER = {"mixed": 56.0, "fp64": 112.0}
+BYTES_PER_DOF_STEP = {"mixed": 64.0, "fp64": 64.0}
+
+
+def level_dt(l):
+    return 0.1 * 0.5 ** l
+
+
+def level_steps(l):
+    return int(round(T_END / level_dt(l)))
+
+
+def dof_steps_per_estimate():
+    tot = 0
+    for l, N in enumerate(LEVEL_N):
+        tot += N * LEVEL_M[l] ** 2 * level_steps(l)
+        if l > 0:
+            tot += N * LEVEL_M[l - 1] ** 2 * level_steps(l - 1)
+    return tot
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (bounded sample of the same workload)
+# ---------------------------------------------------------------------------
+def oracle_sample(slab_fraction: float, max_samples: int, seed: int = 0):
+    """Run the FP64 CPU oracle on a bounded sample of the workload: per level,
+    the first min(N_l, max_samples) samples of both members over the first
+    ceil(slab_fraction * steps) time blocks.  Returns (DOF-steps/s, seconds,
+    threads used, description)."""
+    import oracle as O
+    from paper_2105_02007_gb300 import inputs
+
+    fine = O.mesh2d(LEVEL_M[-1])
+    modes, _ = O.kl_build(fine, SIGMA2, ELL, K_MODES)
+    meshes = [O.mesh2d(m) for m in LEVEL_M[:-1]] + [fine]
+    phis = [O.centroid_table(fine, modes, mm) for mm in meshes]
+    threads = O.max_threads()
+    work = []
+    for l in range(len(LEVEL_M)):
+        s = min(LEVEL_N[l], max_samples)
+        xi = inputs.gaussian_xi(seed, l, 0, s, K_MODES)
+        for lm in ([l, l - 1] if l > 0 else [l]):
+            steps = max(1, int(np.ceil(slab_fraction * level_steps(lm))))
+            work.append((lm, xi, steps))
+    t0 = time.perf_counter()
+    dof = 0
+    for lm, xi, steps in work:
+        O.solve_batch(meshes[lm], phis[lm], xi, level_dt(lm), steps, nthreads=threads)
+        dof += xi.shape[0] * LEVEL_M[lm] ** 2 * steps
+    el = time.perf_counter() - t0
+    desc = (f"every level's fine and coarse member, first min(N_l,{max_samples}) samples, first "
+            f"{slab_fraction:.3g} of the time blocks (>=1), FP64 CSR Jacobi-PCG, OpenMP over samples")
+    return dof / el, el, threads, desc
+
+
+# ---------------------------------------------------------------------------
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def load_traffic(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if it matches."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))
+        return d.get(kernel_key)
+    except Exception:
+        return None
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    vals = []
+    for k in range(args.warmup + args.steps):
+        rate, el, threads, desc = oracle_sample(1.0 / 400.0, 4, seed=0)
+        if k >= args.warmup:
+            vals.append((rate, el))
+    rate = sum(v[0] for v in vals) / len(vals)
+    ms = 1000.0 * sum(v[1] for v in vals) / len(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": desc},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mlq", choices=["mlq", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=1, help="timed FP64 comparison estimates (0: skip)")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        dist = dist_mod
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2105_02007_gb300 import build, inputs
+
+    build.build()
+    from paper_2105_02007_gb300 import mlq
+
+    stream = torch.cuda.Stream()
+    prec = mlq.MLQ_MIXED if args.precision == "mixed" else mlq.MLQ_FP64
+    modes, _ = mlq.build_kl(LEVEL_M[-1], SIGMA2, ELL, K_MODES)
+    phis = [mlq.centroid_table(LEVEL_M[-1], modes, m) for m in LEVEL_M]
+
+    def make_ctx(p):
+        ctx = mlq.Context(local, p, stream=stream.cuda_stream)
+        for l, m in enumerate(LEVEL_M):
+            ctx.add_level(l, m, level_dt(l), level_steps(l))
+            ctx.set_kl(l, phis[l])
+        return ctx
+
+    ctx = make_ctx(prec)
+    xi_host = [inputs.gaussian_xi(rank, l, 0, LEVEL_N[l], K_MODES) for l in range(len(LEVEL_M))]
+    xi_dev = [torch.from_numpy(x).to(f"cuda:{local}") for x in xi_host]
+    xi_pin = [torch.from_numpy(x).pin_memory() for x in xi_host]
+    torch.cuda.synchronize()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=f"cuda:{local}")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # ---- warm-up
+    for _ in range(args.warmup):
+        ctx.estimate(xi_dev)
+    # ---- timed region: K estimates, inputs resident in HBM
+    ctx.set_profiling(True)
+    clocks = ClockSampler(local)
+    launches0 = ctx.launch_count()
+    step_ms, profiles, results = [], [], []
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.zero_()                                   # evict L2 between estimates
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = ctx.estimate(xi_dev)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            results.append(res)
+            profiles.append(ctx.member_profile())
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = ctx.launch_count() - launches0
+    ctx.set_profiling(False)
+    ms = sum(step_ms) / len(step_ms)
+    ms_all = ms
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_all = float(t.item())
+    dof = dof_steps_per_estimate()
+    value = world * dof / (ms_all / 1000.0)
+
+    # ---- end to end through the public call, host buffers (pinned) in and
+    #      per-sample results out, copies inside the timed region
+    e2e_vals = []
+    h2d = sum(x.numel() * 8 for x in xi_pin)
+    d2h = sum(LEVEL_N) * 8 + 16 * len(LEVEL_N)
+    for _ in range(args.e2e_steps):
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.estimate(xi_pin, return_y=True)
+        torch.cuda.synchronize()
+        e2e_vals.append(time.perf_counter() - t0)
+    e2e_s = max(e2e_vals) if e2e_vals else None
+
+    # ---- roofline of the dominant kernel (largest slab-kernel time)
+    peaks = load_peaks()
+    members = profiles[-1]
+    dom = max(members, key=lambda d: d["kernel_ms"])
+    dom_ms = statistics.mean(max(p, key=lambda d: d["kernel_ms"])["kernel_ms"] for p in profiles)
+    pkey = args.precision
+    alg_bytes = (dom["cg_iterations"] * dom["nodes"] * BYTES_PER_DOF_ITER[pkey]
+                 + dom["samples"] * dom["steps"] * dom["nodes"] * BYTES_PER_DOF_STEP[pkey])
+    achieved = alg_bytes / (dom_ms / 1000.0) / 1e9
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    kname = (f"slab_solve_{'smem' if dom['resident'] else 'global'}_kernel<"
+             f"{'float' if pkey == 'mixed' else 'double'},{dom['cluster']}>")
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": load_traffic(kname), "kernel": kname,
+            "launch": f"level {dom['level']} {'coarse' if dom['coarse'] else 'fine'} member, "
+                      f"{dom['samples']} samples x {dom['nodes']} nodes x {dom['steps']} blocks, "
+                      f"{dom['cg_iterations']} CG iterations",
+            "kernel_ms": dom_ms, "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800"}
+    mean, var, rmse = results[-1]
+
+    # ---- plain FP64 on the same inputs, for the same estimate
+    fp64 = None
+    if args.fp64_steps > 0 and prec == mlq.MLQ_MIXED:
+        c64 = make_ctx(mlq.MLQ_FP64)
+        c64.estimate(xi_dev)
+        t64 = []
+        for _ in range(args.fp64_steps):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                r64 = c64.estimate(xi_dev)
+                e1.record(stream)
+            e1.synchronize()
+            t64.append(e0.elapsed_time(e1))
+        ms64 = statistics.mean(t64)
+        fp64 = {"value": dof / (ms64 / 1000.0), "unit": UNIT, "ms_per_step": ms64, "estimate": r64[0],
+                "rmse": r64[2], "rel_diff_estimate_vs_mixed": abs(r64[0] - mean) / abs(r64[0]),
+                "mixed_speedup": ms64 / ms}
+        c64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, el, threads, desc = oracle_sample(1.0 / 50.0, 16)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc, "seconds": el}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if pkey == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "levels": LEVEL_M, "samples": LEVEL_N, "K": K_MODES,
+                       "dof_steps_per_step": dof, "precision": pkey, "l2": "256 MiB buffer zeroed before each "
+                       "timed estimate (inside the timed region, on the same stream)",
+                       "parallelism": f"replicas x{world}, seed = rank"},
+            "time_to_rmse_s": ms_all / 1000.0, "estimate": mean, "rmse": rmse, "var_l": list(var),
+            "e2e": {"value": world * dof / e2e_s if e2e_s else None, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "clocks": clk, "roofline": roof,
+            "cpu_baseline": cpu, "fp64": fp64,
+            "members": [{k: d[k] for k in ("level", "coarse", "cluster", "resident", "samples", "kernel_ms",
+                                            "cg_iterations")} for d in members],
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    ctx.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -77,7 +77,11 @@ typedef struct {
  *   max_iter   cap on CG iterations per solve (per refinement sweep).
  *   max_sweeps cap on refinement sweeps per block (MLQ_MIXED only).
  *   cluster    CTAs per sample (1,2,4,8,16); 0 = chosen per level.
- *   threads    threads per CTA (128..1024, multiple of 32); 0 = chosen. */
+ *   threads    threads per CTA (64..512, multiple of 32); 0 = chosen.
+ *   storage    where a sample's PCG vectors live: 0 = shared memory of its
+ *              cluster when they fit, else global memory; 1 = shared memory
+ *              (a solve whose level does not fit returns MLQ_EUNSUPPORTED);
+ *              2 = global memory. */
 typedef struct {
     int precision;
     double rtol;
@@ -86,6 +90,7 @@ typedef struct {
     int max_sweeps;
     int cluster;
     int threads;
+    int storage;
 } mlq_options;
 
 /* Fill *opt / *model with the defaults listed above (rtol 1e-13 for FP64,
@@ -166,11 +171,31 @@ int mlq_estimate(mlq_ctx *ctx, int L, const int64_t *N, const double *const *xi,
  * when with_coarse) uses; the context allocates and caches it. */
 int mlq_workspace_bytes(mlq_ctx *ctx, int level, int64_t S, int with_coarse, size_t *bytes);
 
+/* Per-member timing.  With profiling on, every solve / estimate records CUDA
+ * events on the stream of each member (a level's fine or coarse batch)
+ * around its slab-solver kernel; mlq_member_profile then returns, for the
+ * last call, one record per member (up to max_members; *count = members of
+ * that call).  The records stay valid until the next solve / estimate.
+ * Profiling adds two event records per member and one small device-to-host
+ * copy per member when queried. */
+typedef struct {
+    double kernel_ms;       /* slab-solver kernel duration (CUDA events) */
+    int level, coarse;      /* level of the mesh; 1 = coarse member of a pair */
+    int cluster, resident;  /* launch shape used */
+    int64_t samples, nodes, steps;
+    int64_t cg_iterations;  /* CG iterations summed over samples, blocks, sweeps */
+} mlq_member_stats;
+int mlq_set_profiling(mlq_ctx *ctx, int enable);
+int mlq_member_profile(mlq_ctx *ctx, int max_members, int *count, mlq_member_stats *out);
+
 /* Count of kernel launches the context has issued since creation. */
 int mlq_launch_count(mlq_ctx *ctx, int64_t *count);
 
-/* Launch shape chosen for a level: cluster size and threads per CTA. */
-int mlq_level_launch(mlq_ctx *ctx, int level, int *cluster, int *threads);
+/* Launch shape chosen for a level under the context's options: cluster size
+ * (CTAs per sample), threads per CTA, and *resident = 1 when the sample's PCG
+ * vectors live in the cluster's shared memory (0: in global memory).
+ * resident may be NULL. */
+int mlq_level_launch(mlq_ctx *ctx, int level, int *cluster, int *threads, int *resident);
 
 const char *mlq_strerror(int status);
 const char *mlq_last_cuda_error(mlq_ctx *ctx);

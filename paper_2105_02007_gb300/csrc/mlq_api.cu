@@ -62,6 +62,15 @@ struct mlq_ctx {
     int64_t launches = 0;
     std::string cuda_error;
     int max_cluster = 8;
+    int smem_optin = 48 * 1024;
+    // optional per-member timing of the slab kernel (CUDA events on the
+    // member's stream) and iteration totals of the last solve/estimate
+    bool profile = false;
+    cudaEvent_t ev_t0[kStreams] = {}, ev_t1[kStreams] = {};
+    int nmembers = 0;
+    int prof_level[kStreams] = {}, prof_coarse[kStreams] = {}, prof_cs[kStreams] = {}, prof_resident[kStreams] = {};
+    int64_t prof_samples[kStreams] = {}, prof_nodes[kStreams] = {}, prof_steps[kStreams] = {};
+    const int32_t *prof_iters_dev[kStreams] = {};
 };
 
 namespace {
@@ -100,35 +109,62 @@ bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// launch shape of a level: cluster size and threads per CTA
-void choose_launch(const mlq_ctx *ctx, const Level &L, int *cs, int *threads)
-{
-    int c = ctx->opt.cluster;
-    if (c <= 0) {
-        // aim at ~4k nodes per CTA
-        c = 1;
-        while (c < ctx->max_cluster && (L.n + c - 1) / c > 4096) c *= 2;
-    }
-    c = std::min(c, ctx->max_cluster);
-    int t = ctx->opt.threads;
-    if (t <= 0) {
-        const int per = (L.n + c - 1) / c;
-        t = per >= 2048 ? 512 : (per >= 768 ? 256 : 128);
-    }
-    *cs = c;
-    *threads = t;
-}
-
 size_t tile_bytes(const Level &L, int cs)
 {
     const int rows = (L.m + cs - 1) / cs + 2;
     return (size_t)std::min(rows, L.m) * L.m * sizeof(double);
 }
 
-template <typename TI, int CS>
-cudaError_t launch_slab(const mlq::SolveArgs<TI> &a, int nclusters, int threads, size_t smem, cudaStream_t st)
+// Launch shape of a level: cluster size, threads per CTA, and whether the
+// sample's PCG vectors fit in the cluster's shared memory (preferred).
+struct Shape {
+    int cs, threads;
+    bool resident;
+    size_t smem;
+};
+
+Shape choose_launch(const mlq_ctx *ctx, const Level &L)
 {
-    auto kern = mlq::slab_solve_kernel<TI, CS>;
+    const int ti = ctx->opt.precision == MLQ_MIXED ? 4 : 8;
+    const int limit = ctx->smem_optin - 2048;  // room for the static reduction buffers
+    Shape sh{0, 0, false, 0};
+    auto fits = [&](int c) {
+        if (c > L.m) return false;
+        return mlq::smem_plan(L.m, c, ti).total <= limit;
+    };
+    const bool allow = ctx->opt.storage != 2;
+    if (ctx->opt.cluster > 0) {
+        sh.cs = ctx->opt.cluster;
+        sh.resident = allow && fits(sh.cs);
+    } else {
+        for (int c = 1; allow && c <= ctx->max_cluster; c *= 2) {
+            if (fits(c) && (L.n + c - 1) / c <= 4608) {
+                sh.cs = c;
+                sh.resident = true;
+                break;
+            }
+        }
+        if (!sh.resident) {
+            int c = 1;
+            while (c < ctx->max_cluster && (L.n + c - 1) / c > 4096) c *= 2;
+            sh.cs = c;
+        }
+    }
+    int t = ctx->opt.threads;
+    if (t <= 0) {
+        const int per = (L.n + sh.cs - 1) / sh.cs;
+        t = per >= 2048 ? 512 : (per >= 768 ? 256 : 128);
+    }
+    sh.threads = t;
+    sh.smem = sh.resident ? (size_t)mlq::smem_plan(L.m, sh.cs, ti).total : tile_bytes(L, sh.cs);
+    return sh;
+}
+
+template <typename TI, int CS>
+cudaError_t launch_slab(const mlq::SolveArgs<TI> &a, int nclusters, int threads, size_t smem, bool resident,
+                        cudaStream_t st)
+{
+    auto kern = resident ? mlq::slab_solve_smem_kernel<TI, CS> : mlq::slab_solve_kernel<TI, CS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (CS > 8) {
@@ -152,14 +188,14 @@ cudaError_t launch_slab(const mlq::SolveArgs<TI> &a, int nclusters, int threads,
 
 template <typename TI>
 cudaError_t launch_slab_cs(int cs, const mlq::SolveArgs<TI> &a, int nclusters, int threads, size_t smem,
-                           cudaStream_t st)
+                           bool resident, cudaStream_t st)
 {
     switch (cs) {
-    case 1: return launch_slab<TI, 1>(a, nclusters, threads, smem, st);
-    case 2: return launch_slab<TI, 2>(a, nclusters, threads, smem, st);
-    case 4: return launch_slab<TI, 4>(a, nclusters, threads, smem, st);
-    case 8: return launch_slab<TI, 8>(a, nclusters, threads, smem, st);
-    case 16: return launch_slab<TI, 16>(a, nclusters, threads, smem, st);
+    case 1: return launch_slab<TI, 1>(a, nclusters, threads, smem, resident, st);
+    case 2: return launch_slab<TI, 2>(a, nclusters, threads, smem, resident, st);
+    case 4: return launch_slab<TI, 4>(a, nclusters, threads, smem, resident, st);
+    case 8: return launch_slab<TI, 8>(a, nclusters, threads, smem, resident, st);
+    case 16: return launch_slab<TI, 16>(a, nclusters, threads, smem, resident, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -230,7 +266,7 @@ int ensure_workspace(mlq_ctx *ctx, size_t bytes)
 }
 
 template <typename TI>
-int launch_member_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream_t st)
+int launch_member_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream_t st, int slot)
 {
     const bool mixed = sizeof(TI) == 4;
     // K1: KL synthesis (theta -> cos 2t, sin 2t)
@@ -281,19 +317,33 @@ int launch_member_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream_t
     a.q = mb.q;
     a.iters = mb.iters;
     a.status = mb.status;
-    int cs, threads;
-    choose_launch(ctx, L, &cs, &threads);
-    const size_t smem = tile_bytes(L, cs);
-    MLQ_CUDA(ctx, launch_slab_cs<TI>(cs, a, (int)mb.S, threads, smem, st));
+    const Shape sh = choose_launch(ctx, L);
+    if (ctx->opt.storage == 1 && !sh.resident) return MLQ_EUNSUPPORTED;
+    const bool timed = ctx->profile && slot >= 0 && slot < kStreams;
+    if (timed) MLQ_CUDA(ctx, cudaEventRecord(ctx->ev_t0[slot], st));
+    MLQ_CUDA(ctx, launch_slab_cs<TI>(sh.cs, a, (int)mb.S, sh.threads, sh.smem, sh.resident, st));
+    if (timed) MLQ_CUDA(ctx, cudaEventRecord(ctx->ev_t1[slot], st));
     ctx->launches++;
     return MLQ_OK;
 }
 
-int launch_member(mlq_ctx *ctx, const Member &mb, cudaStream_t st)
+int launch_member(mlq_ctx *ctx, const Member &mb, cudaStream_t st, int slot, int coarse)
 {
     const Level &L = ctx->levels[mb.level];
-    if (ctx->opt.precision == MLQ_MIXED) return launch_member_t<float>(ctx, L, mb, st);
-    return launch_member_t<double>(ctx, L, mb, st);
+    if (ctx->profile && slot >= 0 && slot < kStreams) {
+        const Shape sh = choose_launch(ctx, L);
+        ctx->prof_level[slot] = mb.level;
+        ctx->prof_coarse[slot] = coarse;
+        ctx->prof_cs[slot] = sh.cs;
+        ctx->prof_resident[slot] = sh.resident;
+        ctx->prof_samples[slot] = mb.S;
+        ctx->prof_nodes[slot] = L.n;
+        ctx->prof_steps[slot] = L.nsteps;
+        ctx->prof_iters_dev[slot] = mb.iters;
+        ctx->nmembers = std::max(ctx->nmembers, slot + 1);
+    }
+    if (ctx->opt.precision == MLQ_MIXED) return launch_member_t<float>(ctx, L, mb, st, slot);
+    return launch_member_t<double>(ctx, L, mb, st, slot);
 }
 
 int check_level(const mlq_ctx *ctx, int level)
@@ -327,6 +377,7 @@ int mlq_default_options(mlq_options *opt, int precision)
     opt->max_sweeps = 20;
     opt->cluster = 0;
     opt->threads = 0;
+    opt->storage = 0;
     return MLQ_OK;
 }
 
@@ -350,6 +401,7 @@ static int validate_options(const mlq_options *o)
         o->cluster != 16)
         return MLQ_EINVAL;
     if (o->threads != 0 && (o->threads < 64 || o->threads > 512 || o->threads % 32)) return MLQ_EINVAL;
+    if (o->storage < 0 || o->storage > 2) return MLQ_EINVAL;
     return MLQ_OK;
 }
 
@@ -378,9 +430,13 @@ int mlq_create(mlq_ctx **out, int device, void *cuda_stream, const mlq_options *
             return fail(MLQ_ECUDA);
     }
     if (cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess) return fail(MLQ_ECUDA);
+    for (int k = 0; k < kStreams; ++k)
+        if (cudaEventCreate(&ctx->ev_t0[k]) != cudaSuccess || cudaEventCreate(&ctx->ev_t1[k]) != cudaSuccess)
+            return fail(MLQ_ECUDA);
     // largest cluster that can be resident with our largest shapes
     int nonportable = 0;
     cudaDeviceGetAttribute(&nonportable, cudaDevAttrClusterLaunch, device);
+    cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     ctx->max_cluster = 8;
     {
         cudaLaunchConfig_t cfg{};
@@ -419,6 +475,8 @@ int mlq_destroy(mlq_ctx *ctx)
             cudaStreamDestroy(ctx->pool[k]);
         }
         if (ctx->ev_join[k]) cudaEventDestroy(ctx->ev_join[k]);
+        if (ctx->ev_t0[k]) cudaEventDestroy(ctx->ev_t0[k]);
+        if (ctx->ev_t1[k]) cudaEventDestroy(ctx->ev_t1[k]);
     }
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     for (auto &L : ctx->levels) {
@@ -549,6 +607,7 @@ int mlq_solve(mlq_ctx *ctx, int level, int64_t S, const double *xi, int with_coa
     }
     if (S == 0) return MLQ_OK;
     MLQ_CUDA(ctx, cudaSetDevice(ctx->device));
+    ctx->nmembers = 0;
     const int K = ctx->levels[level].K;
     size_t need = 0;
     mlq_workspace_bytes(ctx, level, S, with_coarse, &need);
@@ -584,7 +643,7 @@ int mlq_solve(mlq_ctx *ctx, int level, int64_t S, const double *xi, int with_coa
     const int nm = with_coarse ? 2 : 1;
     for (int k = 0; k < nm; ++k) {
         MLQ_CUDA(ctx, cudaStreamWaitEvent(ctx->pool[k], ctx->ev_fork, 0));
-        st = launch_member(ctx, k == 0 ? mf : mc, ctx->pool[k]);
+        st = launch_member(ctx, k == 0 ? mf : mc, ctx->pool[k], k, k);
         if (st != MLQ_OK) return st;
         MLQ_CUDA(ctx, cudaEventRecord(ctx->ev_join[k], ctx->pool[k]));
         MLQ_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_join[k], 0));
@@ -616,6 +675,7 @@ int mlq_estimate(mlq_ctx *ctx, int L, const int64_t *N, const double *const *xi,
         if (ctx->levels[l].K != ctx->levels[0].K) return MLQ_EINVAL;
     }
     MLQ_CUDA(ctx, cudaSetDevice(ctx->device));
+    ctx->nmembers = 0;
     const int K = ctx->levels[0].K;
     size_t need = 4096;
     for (int l = 0; l <= L; ++l) {
@@ -658,7 +718,7 @@ int mlq_estimate(mlq_ctx *ctx, int L, const int64_t *N, const double *const *xi,
         for (int k = 0; k < (l > 0 ? 2 : 1); ++k) {
             cudaStream_t s = ctx->pool[sid];
             MLQ_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_fork, 0));
-            st = launch_member(ctx, k == 0 ? fine[l] : coarse[l], s);
+            st = launch_member(ctx, k == 0 ? fine[l] : coarse[l], s, sid, k);
             if (st != MLQ_OK) return st;
             MLQ_CUDA(ctx, cudaEventRecord(ctx->ev_join[sid], s));
             MLQ_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_join[sid], 0));
@@ -691,6 +751,44 @@ int mlq_estimate(mlq_ctx *ctx, int L, const int64_t *N, const double *const *xi,
     return MLQ_OK;
 }
 
+int mlq_set_profiling(mlq_ctx *ctx, int enable)
+{
+    if (!ctx) return MLQ_EINVAL;
+    ctx->profile = enable != 0;
+    return MLQ_OK;
+}
+
+int mlq_member_profile(mlq_ctx *ctx, int max_members, int *count, mlq_member_stats *out)
+{
+    if (!ctx || !count || (max_members > 0 && !out)) return MLQ_EINVAL;
+    if (!ctx->profile) return MLQ_EINVAL;
+    MLQ_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int nm = std::min(ctx->nmembers, max_members);
+    *count = ctx->nmembers;
+    std::vector<int32_t> it;
+    for (int k = 0; k < nm; ++k) {
+        mlq_member_stats &o = out[k];
+        float ms = 0.0f;
+        MLQ_CUDA(ctx, cudaEventSynchronize(ctx->ev_t1[k]));
+        MLQ_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_t0[k], ctx->ev_t1[k]));
+        o.kernel_ms = ms;
+        o.level = ctx->prof_level[k];
+        o.coarse = ctx->prof_coarse[k];
+        o.cluster = ctx->prof_cs[k];
+        o.resident = ctx->prof_resident[k];
+        o.samples = ctx->prof_samples[k];
+        o.nodes = ctx->prof_nodes[k];
+        o.steps = ctx->prof_steps[k];
+        it.resize((size_t)o.samples);
+        MLQ_CUDA(ctx, cudaMemcpy(it.data(), ctx->prof_iters_dev[k], sizeof(int32_t) * o.samples,
+                                 cudaMemcpyDeviceToHost));
+        int64_t tot = 0;
+        for (int32_t x : it) tot += x;
+        o.cg_iterations = tot;
+    }
+    return MLQ_OK;
+}
+
 int mlq_launch_count(mlq_ctx *ctx, int64_t *count)
 {
     if (!ctx || !count) return MLQ_EINVAL;
@@ -698,11 +796,14 @@ int mlq_launch_count(mlq_ctx *ctx, int64_t *count)
     return MLQ_OK;
 }
 
-int mlq_level_launch(mlq_ctx *ctx, int level, int *cluster, int *threads)
+int mlq_level_launch(mlq_ctx *ctx, int level, int *cluster, int *threads, int *resident)
 {
     if (!ctx || !cluster || !threads || level < 0 || level >= kMaxLevels || !ctx->levels[level].defined)
         return MLQ_EINVAL;
-    choose_launch(ctx, ctx->levels[level], cluster, threads);
+    const Shape sh = choose_launch(ctx, ctx->levels[level]);
+    *cluster = sh.cs;
+    *threads = sh.threads;
+    if (resident) *resident = sh.resident ? 1 : 0;
     return MLQ_OK;
 }
 

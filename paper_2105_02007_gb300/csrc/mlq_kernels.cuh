@@ -514,6 +514,297 @@ __global__ void __launch_bounds__(512, 1) slab_solve_kernel(SolveArgs<TI> g)
 }
 
 // ---------------------------------------------------------------------------
+// Shared-memory-resident variant of the slab solver.
+//
+// Same algorithm and the same cluster decomposition as slab_solve_kernel, but
+// every PCG vector of a CTA's rows lives in its shared memory for the whole
+// run, and the halo rows of the next iterate are recomputed from the
+// neighbouring CTAs' shared memory over DSMEM (distributed shared memory of
+// the thread-block cluster).  The CG loop then touches global memory only for
+// the read-only stencil coefficients (L1 resident).  The FP64 state (v, w, b)
+// stays in global memory: it is read once per refinement sweep.
+//
+// Shared layout, identical in every CTA of the cluster (so that a neighbour's
+// array is the same offset in its window):
+//   utile  (rows_max + 2) * m   TI   tile rows [lo, hi) of the next iterate
+//   R0 R1 W0 W1 S0 S1 P X       nmax TI each, own nodes, local index
+//   ytile  (rows_max + 2) * m   FP64, aliases S0..X (dead while a block's
+//          load vector is formed)
+// ---------------------------------------------------------------------------
+struct SmemPlan {
+    int nmax;       // rows_max * m
+    int tile;       // (rows_max + 2) * m, capped at m * m
+    int off_vec;    // byte offset of R0
+    int vec_bytes;  // bytes per own-node vector (16-byte multiple)
+    int off_y;      // byte offset of ytile
+    int total;      // dynamic shared bytes
+};
+
+__host__ __device__ inline int align16(int b) { return (b + 15) & ~15; }
+
+__host__ __device__ inline SmemPlan smem_plan(int m, int cs, int ti_bytes)
+{
+    SmemPlan pl;
+    const int rows = (m + cs - 1) / cs;
+    pl.nmax = rows * m;
+    pl.tile = (rows + 2 < m ? rows + 2 : m) * m;
+    pl.off_vec = align16(pl.tile * ti_bytes);
+    pl.vec_bytes = align16(pl.nmax * ti_bytes);
+    pl.off_y = pl.off_vec + 4 * pl.vec_bytes;
+    const int end_vec = pl.off_vec + 8 * pl.vec_bytes;
+    const int end_y = pl.off_y + align16(pl.tile * 8);
+    pl.total = end_vec > end_y ? end_vec : end_y;
+    return pl;
+}
+
+template <typename TI, int CS>
+__global__ void __launch_bounds__(512, 1) slab_solve_smem_kernel(SolveArgs<TI> g)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double warp_buf[32][4];
+    __shared__ double slots[2][4];
+
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int sample = blockIdx.x / CS;
+    const int m = g.m, n = g.n;
+    const int r0 = (int)(((int64_t)m * rank) / CS), r1 = (int)(((int64_t)m * (rank + 1)) / CS);
+    const int lo = r0 > 0 ? r0 - 1 : 0, hi = r1 < m ? r1 + 1 : m;
+    const int own0 = r0 * m, own1 = r1 * m, tile0 = lo * m, tile1 = hi * m;
+    const int nown = own1 - own0;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const SmemPlan pl = smem_plan(m, CS, (int)sizeof(TI));
+
+    TI *utile = reinterpret_cast<TI *>(smem_raw);
+    TI *vec0 = reinterpret_cast<TI *>(smem_raw + pl.off_vec);
+    const int vstride = pl.vec_bytes / (int)sizeof(TI);
+    TI *Rv = vec0;                 // R0, R1 at Rv, Rv + vstride
+    TI *Wv = vec0 + 2 * vstride;   // W0, W1
+    TI *Sv = vec0 + 4 * vstride;   // S0, S1
+    TI *P = vec0 + 6 * vstride;
+    TI *X = vec0 + 7 * vstride;
+    double *ytile = reinterpret_cast<double *>(smem_raw + pl.off_y);
+    const int ushift = own0 - tile0;  // tile index of own local index 0
+
+    // neighbours' windows (their arrays sit at the same offsets)
+    const bool has_lo = rank > 0, has_hi = rank + 1 < CS;
+    const int r0_lo = has_lo ? (int)(((int64_t)m * (rank - 1)) / CS) : 0;
+    TI *vec_lo = has_lo ? cl.map_shared_rank(vec0, rank - 1) : nullptr;
+    TI *vec_hi = has_hi ? cl.map_shared_rank(vec0, rank + 1) : nullptr;
+    // local index, in the neighbour's numbering, of our halo rows' first node
+    const int lo_base = (r0 - 1 - r0_lo) * m;  // row r0-1 in rank-1
+    const int hi_base = 0;                     // row r1 is rank+1's first row
+
+    const size_t so = (size_t)sample * n;
+    const double *A64 = g.A64 + (size_t)sample * kSlots2D * n;
+    const TI *Ai = g.Ai + (size_t)sample * kSlots2D * n;
+    const TI *Dinv = Ai + 4 * (size_t)n;
+    double *v = g.v + so;
+    double *wb0 = g.w + so;
+    const size_t SN = (size_t)g.S * n;
+    double *b = g.b + so;
+    int par = 0;
+
+    for (int node = own0 + tid; node < own1; node += nt) {
+        double v0, w0;
+        if (g.v0) {
+            v0 = g.v0[node];
+            w0 = g.w0 ? g.w0[node] : 0.0;
+        } else {
+            const int j = (int)g.divm.div((uint32_t)node), i = node - j * m;
+            const double xx = (double)i / (double)(m - 1), yy = (double)j / (double)(m - 1);
+            v0 = (xx * xx + yy * yy <= g.radius2) ? 1.0 : 0.0;
+            w0 = 0.0;
+        }
+        v[node] = v0;
+        wb0[node] = w0;
+    }
+    cl.sync();
+
+    int wpar = 0;
+    int64_t total_iters = 0;
+    int32_t status = S_CONVERGED;
+    const bool mixed = sizeof(TI) == 4;
+    const double dt = g.dt;
+
+    for (int step = 0; step < g.nsteps; ++step) {
+        // ---- block load: y = v + dt R(v, w) on the tile, b = M y, w update,
+        //      r0 = b - A v into R0 (own rows)
+        const double *wcur = wb0 + wpar * SN;
+        double *wnext = wb0 + (wpar ^ 1) * SN;
+        for (int node = tile0 + tid; node < tile1; node += nt) {
+            const double vv = ldcg(v + node), ww = ldcg(wcur + node);
+            const double R = vv * (vv - g.a) * (1.0 - vv) - ww;
+            ytile[node - tile0] = vv + dt * R;
+        }
+        __syncthreads();
+        double acc[2] = {0.0, 0.0};
+        for (int node = own0 + tid; node < own1; node += nt) {
+            const int j = (int)g.divm.div((uint32_t)node), i = node - j * m;
+            const double bb = mass_apply(m, i, j, g.h2, ytile, node - tile0);
+            b[node] = bb;
+            const double vv = v[node], ww = wcur[node];
+            wnext[node] = ww + dt * g.eps * (vv - g.gam * ww);
+            const double rr = bb - stencil_apply_global(A64, n, m, node, i, j, v);
+            Rv[node - own0] = (TI)rr;
+            acc[0] += bb * bb;
+            acc[1] += rr * rr;
+        }
+        cluster_sum<2, CS>(acc, warp_buf, slots, par);
+        par ^= 1;
+        wpar ^= 1;
+        const double bnorm2 = acc[0];
+        double rnorm2 = acc[1];
+        if (!(isfinite(bnorm2) && isfinite(rnorm2))) {
+            status = S_NONFINITE;
+            break;
+        }
+        const double tol_out2 = g.rtol_out * g.rtol_out * bnorm2;
+
+        bool nonfinite = false, solved = false;
+        for (int sweep = 0; sweep < g.max_sweeps; ++sweep) {
+            if (sweep > 0) {
+                double racc[2] = {0.0, 0.0};
+                for (int node = own0 + tid; node < own1; node += nt) {
+                    const int j = (int)g.divm.div((uint32_t)node), i = node - j * m;
+                    const double rr = b[node] - stencil_apply_global(A64, n, m, node, i, j, v);
+                    Rv[node - own0] = (TI)rr;
+                    racc[0] += rr * rr;
+                }
+                cluster_sum<2, CS>(racc, warp_buf, slots, par);
+                par ^= 1;
+                rnorm2 = racc[0];
+                if (!isfinite(rnorm2)) { nonfinite = true; break; }
+            }
+            if (rnorm2 <= tol_out2) { solved = true; break; }
+            const double tol_in2 = mixed ? g.rtol_in * g.rtol_in * rnorm2 : tol_out2;
+
+            // ---- inner PCG init: u0 = r0 d^-1 on the tile, w0 = A u0, x = 0
+            for (int l = tid; l < nown; l += nt) utile[l + ushift] = Rv[l] * Dinv[own0 + l];
+            if (has_lo)
+                for (int i = tid; i < m; i += nt)
+                    utile[i] = vec_lo[lo_base + i] * Dinv[tile0 + i];
+            if (has_hi)
+                for (int i = tid; i < m; i += nt)
+                    utile[own1 - tile0 + i] = vec_hi[hi_base + i] * Dinv[own1 + i];
+            __syncthreads();
+            double iacc[3] = {0.0, 0.0, 0.0};
+            for (int l = tid; l < nown; l += nt) {
+                const int node = own0 + l;
+                const int j = (int)g.divm.div((uint32_t)node), i = node - j * m;
+                const TI u0 = utile[l + ushift];
+                const TI w0 = stencil_apply<TI, TI>(Ai, n, m, node, i, j, utile, l + ushift);
+                Wv[l] = w0;
+                X[l] = (TI)0;
+                const TI r0v = Rv[l];
+                iacc[0] += (double)(r0v * u0);
+                iacc[1] += (double)(w0 * u0);
+                iacc[2] += (double)(r0v * r0v);
+            }
+            cluster_sum<3, CS>(iacc, warp_buf, slots, par);
+            par ^= 1;
+            double gamma = iacc[0], delta = iacc[1], rr = iacc[2];
+            double gamma_prev = 1.0, alpha_prev = 1.0;
+            int it = 0;
+            while (true) {
+                if (!isfinite(rr) || !isfinite(gamma) || !isfinite(delta)) { nonfinite = true; break; }
+                if (rr <= tol_in2) { solved = !mixed; break; }
+                if (it >= g.max_iter) { status = status == S_CONVERGED ? S_MAXITER : status; break; }
+                double alpha, beta;
+                if (it == 0) {
+                    beta = 0.0;
+                    alpha = gamma / delta;
+                } else {
+                    beta = gamma / gamma_prev;
+                    alpha = gamma / (delta - beta * gamma / alpha_prev);
+                }
+                const TI ta = (TI)alpha, tb = (TI)beta;
+                const int cur = it & 1, nxt = cur ^ 1;
+                TI *Rc = Rv + cur * vstride, *Rn = Rv + nxt * vstride;
+                TI *Wc = Wv + cur * vstride, *Wn = Wv + nxt * vstride;
+                TI *Sc = Sv + cur * vstride, *Sp = Sv + nxt * vstride;
+                double pacc[3] = {0.0, 0.0, 0.0};
+                // own rows
+                for (int l = tid; l < nown; l += nt) {
+                    const TI ri = Rc[l], wi = Wc[l];
+                    const TI si = it == 0 ? wi : wi + tb * Sp[l];
+                    const TI rn = ri - ta * si;
+                    const TI di = Dinv[own0 + l];
+                    const TI un = rn * di;
+                    utile[l + ushift] = un;
+                    const TI ui = ri * di;
+                    const TI pi = it == 0 ? ui : ui + tb * P[l];
+                    X[l] += ta * pi;
+                    P[l] = pi;
+                    Sc[l] = si;
+                    Rn[l] = rn;
+                    pacc[0] += (double)(rn * un);
+                    pacc[2] += (double)(rn * rn);
+                }
+                // halo rows: the neighbours' r_i, w_i, s_{i-1} over DSMEM
+                if (has_lo) {
+                    const TI *rr_ = vec_lo + cur * vstride, *ww_ = vec_lo + (2 + cur) * vstride;
+                    const TI *ss_ = vec_lo + (4 + nxt) * vstride;
+                    for (int i = tid; i < m; i += nt) {
+                        const int k = lo_base + i;
+                        const TI si = it == 0 ? ww_[k] : ww_[k] + tb * ss_[k];
+                        utile[i] = (rr_[k] - ta * si) * Dinv[tile0 + i];
+                    }
+                }
+                if (has_hi) {
+                    const TI *rr_ = vec_hi + cur * vstride, *ww_ = vec_hi + (2 + cur) * vstride;
+                    const TI *ss_ = vec_hi + (4 + nxt) * vstride;
+                    for (int i = tid; i < m; i += nt) {
+                        const int k = hi_base + i;
+                        const TI si = it == 0 ? ww_[k] : ww_[k] + tb * ss_[k];
+                        utile[own1 - tile0 + i] = (rr_[k] - ta * si) * Dinv[own1 + i];
+                    }
+                }
+                __syncthreads();
+                for (int l = tid; l < nown; l += nt) {
+                    const int node = own0 + l;
+                    const int j = (int)g.divm.div((uint32_t)node), i = node - j * m;
+                    const TI wn = stencil_apply<TI, TI>(Ai, n, m, node, i, j, utile, l + ushift);
+                    Wn[l] = wn;
+                    pacc[1] += (double)(wn * utile[l + ushift]);
+                }
+                cluster_sum<3, CS>(pacc, warp_buf, slots, par);
+                par ^= 1;
+                gamma_prev = gamma;
+                alpha_prev = alpha;
+                gamma = pacc[0];
+                delta = pacc[1];
+                rr = pacc[2];
+                ++it;
+            }
+            total_iters += it;
+            if (nonfinite) break;
+            for (int l = tid; l < nown; l += nt) v[own0 + l] = v[own0 + l] + (double)X[l];
+            cl.sync();
+            if (!mixed) break;
+        }
+        if (nonfinite) {
+            status = S_NONFINITE;
+            break;
+        }
+        if (!solved && status == S_CONVERGED) status = S_MAXITER;
+    }
+
+    double qacc[1] = {0.0};
+    for (int node = own0 + tid; node < own1; node += nt) {
+        const int j = (int)g.divm.div((uint32_t)node), i = node - j * m;
+        qacc[0] += lumped_mass(m, i, j, g.h2) * v[node];
+    }
+    cluster_sum<1, CS>(qacc, warp_buf, slots, par);
+    if (rank == 0 && tid == 0) {
+        g.q[sample] = status == S_NONFINITE ? __longlong_as_double(0x7ff8000000000000LL) : qacc[0];
+        g.iters[sample] = (int32_t)(total_iters > 0x7fffffff ? 0x7fffffff : total_iters);
+        g.status[sample] = status;
+    }
+    cl.sync();
+}
+
+// ---------------------------------------------------------------------------
 // K7: Y = Q_l - Q_{l-1} and per-level sums in FP64.  One block, two passes
 // (mean, then centred squares); the tree is fixed by blockDim, so the sums do
 // not depend on how samples were batched.

@@ -28,12 +28,18 @@ S_CONVERGED, S_MAXITER, S_NONFINITE, S_CANCELLED = 0, 1, 2, 3
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("rtol", ctypes.c_double), ("rtol_inner", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("max_sweeps", ctypes.c_int), ("cluster", ctypes.c_int),
-                ("threads", ctypes.c_int)]
+                ("threads", ctypes.c_int), ("storage", ctypes.c_int)]
 
 
 class Model(ctypes.Structure):
     _fields_ = [("s_l", ctypes.c_double), ("s_t", ctypes.c_double), ("a", ctypes.c_double),
                 ("eps", ctypes.c_double), ("gamma", ctypes.c_double), ("T", ctypes.c_double)]
+
+
+class MemberStats(ctypes.Structure):
+    _fields_ = [("kernel_ms", ctypes.c_double), ("level", ctypes.c_int), ("coarse", ctypes.c_int),
+                ("cluster", ctypes.c_int), ("resident", ctypes.c_int), ("samples", ctypes.c_int64),
+                ("nodes", ctypes.c_int64), ("steps", ctypes.c_int64), ("cg_iterations", ctypes.c_int64)]
 
 
 _vp = ctypes.c_void_p
@@ -54,7 +60,10 @@ _lib.mlq_solve.argtypes = [_vp, ctypes.c_int, _i64, _vp, ctypes.c_int, _vp, _vp,
 _lib.mlq_estimate.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.mlq_workspace_bytes.argtypes = [_vp, ctypes.c_int, _i64, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
 _lib.mlq_launch_count.argtypes = [_vp, ctypes.POINTER(_i64)]
-_lib.mlq_level_launch.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+_lib.mlq_level_launch.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                  ctypes.POINTER(ctypes.c_int)]
+_lib.mlq_set_profiling.argtypes = [_vp, ctypes.c_int]
+_lib.mlq_member_profile.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(MemberStats)]
 _lib.mlq_strerror.restype = ctypes.c_char_p
 _lib.mlq_strerror.argtypes = [ctypes.c_int]
 _lib.mlq_last_cuda_error.restype = ctypes.c_char_p
@@ -63,7 +72,8 @@ _lib.mlq_last_cuda_error.argtypes = [_vp]
 EXPORTED = ["mlq_default_options", "mlq_default_model", "mlq_create", "mlq_destroy", "mlq_set_options",
             "mlq_set_model", "mlq_add_level", "mlq_set_initial_state", "mlq_set_initial_disk", "mlq_set_kl",
             "mlq_build_kl", "mlq_centroid_table", "mlq_solve", "mlq_estimate", "mlq_workspace_bytes",
-            "mlq_launch_count", "mlq_level_launch", "mlq_strerror", "mlq_last_cuda_error"]
+            "mlq_launch_count", "mlq_level_launch", "mlq_strerror", "mlq_last_cuda_error", "mlq_set_profiling",
+            "mlq_member_profile"]
 
 
 class MLQError(RuntimeError):
@@ -232,12 +242,25 @@ class Context:
                "mlq_workspace_bytes", self._h)
         return b.value
 
+    def set_profiling(self, enable: bool = True):
+        _check(_lib.mlq_set_profiling(self._h, int(enable)), "mlq_set_profiling", self._h)
+
+    def member_profile(self):
+        """Per-member slab-kernel timings and CG iteration totals of the last
+        solve / estimate (profiling must be on)."""
+        buf = (MemberStats * 16)()
+        cnt = ctypes.c_int()
+        _check(_lib.mlq_member_profile(self._h, 16, ctypes.byref(cnt), buf), "mlq_member_profile", self._h)
+        return [{f: getattr(buf[k], f) for f, _ in MemberStats._fields_} for k in range(min(cnt.value, 16))]
+
     def launch_count(self) -> int:
         c = _i64()
         _check(_lib.mlq_launch_count(self._h, ctypes.byref(c)), "mlq_launch_count")
         return c.value
 
-    def level_launch(self, level: int):
-        c, t = ctypes.c_int(), ctypes.c_int()
-        _check(_lib.mlq_level_launch(self._h, level, ctypes.byref(c), ctypes.byref(t)), "mlq_level_launch")
-        return c.value, t.value
+    def level_launch(self, level: int, with_resident: bool = False):
+        """(cluster, threads[, resident]) chosen for a level."""
+        c, t, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(_lib.mlq_level_launch(self._h, level, ctypes.byref(c), ctypes.byref(t), ctypes.byref(r)),
+               "mlq_level_launch")
+        return (c.value, t.value, bool(r.value)) if with_resident else (c.value, t.value)

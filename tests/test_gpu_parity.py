@@ -51,9 +51,10 @@ def c1():
     return dict(mesh=mesh, phi=phi, xi=xi, q=q)
 
 
+@pytest.mark.parametrize("storage", [1, 2])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_c1_full_config_parity(mlq, c1, prec):
-    with mlq.Context(0, prec) as ctx:
+def test_c1_full_config_parity(mlq, c1, prec, storage):
+    with mlq.Context(0, prec, storage=storage) as ctx:
         ctx.add_level(0, 33, 0.05, 200)
         ctx.set_kl(0, c1["phi"])
         r = ctx.solve(0, c1["xi"])
@@ -66,10 +67,11 @@ def test_c1_full_config_parity(mlq, c1, prec):
 # Launch shapes: cluster sizes 1..16 with ragged row bands, block sizes,
 # random initial states (every node active), a mean angle field.
 # --------------------------------------------------------------------------
+@pytest.mark.parametrize("storage", [1, 2])
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("m,cluster,threads", [(17, 1, 64), (17, 2, 128), (17, 4, 96), (23, 8, 64),
                                                (33, 16, 128), (9, 4, 64)])
-def test_launch_shapes_random_state(mlq, prec, m, cluster, threads):
+def test_launch_shapes_random_state(mlq, prec, m, cluster, threads, storage):
     mesh = O.mesh2d(m)
     rng = np.random.default_rng(m * 100 + cluster)
     K = 6
@@ -82,7 +84,7 @@ def test_launch_shapes_random_state(mlq, prec, m, cluster, threads):
     q_ref, _, st = O.solve_batch(mesh, phi, xi, 0.1, 15, v0=v0, w0=w0, theta_mean=tm)
     assert np.all(st == 0)
     try:
-        ctx = mlq.Context(0, prec, cluster=cluster, threads=threads)
+        ctx = mlq.Context(0, prec, cluster=cluster, threads=threads, storage=storage)
     except mlq.MLQError as e:
         if e.code == -6:
             pytest.skip("cluster size not available on this device")
@@ -91,7 +93,7 @@ def test_launch_shapes_random_state(mlq, prec, m, cluster, threads):
         ctx.add_level(0, m, 0.1, 15)
         ctx.set_kl(0, phi, tm)
         ctx.set_initial_state(0, v0, w0)
-        assert ctx.level_launch(0) == (cluster, threads)
+        assert ctx.level_launch(0, True) == (cluster, threads, storage == 1)
         r = ctx.solve(0, xi)
     assert np.all(r["status"] == 0)
     assert rel(r["q_fine"], q_ref) < TOL[prec]
@@ -228,9 +230,10 @@ def modes257():
     return fine, O.kl_build(fine, 0.09, 0.04, 16)[0]
 
 
+@pytest.mark.parametrize("storage", [0, 2])
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("m,dt", [(129, 0.0125), (257, 0.00625)])
-def test_full_size_meshes_sampled(mlq, modes257, prec, m, dt):
+def test_full_size_meshes_sampled(mlq, modes257, prec, m, dt, storage):
     steps = 8 if m == 257 else 16
     fine, modes = modes257
     mesh = fine if m == 257 else O.mesh2d(m)
@@ -238,7 +241,7 @@ def test_full_size_meshes_sampled(mlq, modes257, prec, m, dt):
     xi = inputs.gaussian_xi(0, 4, 0, 2, 16)
     q_ref, _, st = O.solve_batch(mesh, phi, xi, dt, steps, nthreads=2)
     assert np.all(st == 0)
-    with mlq.Context(0, prec) as ctx:
+    with mlq.Context(0, prec, storage=storage) as ctx:
         ctx.add_level(0, m, dt, steps)
         ctx.set_kl(0, phi)
         r = ctx.solve(0, xi)
