@@ -187,17 +187,48 @@ def run_reference(args):
     return 0
 
 
+def run_case(spec: str):
+    """One member solve for profiling: --case level=L,samples=S,steps=N[,precision=mixed|fp64].
+    Prints the slab-kernel time and iteration totals."""
+    kv = dict(item.split("=") for item in spec.split(","))
+    level = int(kv.get("level", 4))
+    S = int(kv.get("samples", 1))
+    steps = int(kv.get("steps", 4))
+    prec_name = kv.get("precision", "mixed")
+    from paper_2105_02007_gb300 import build, inputs
+
+    build.build()
+    from paper_2105_02007_gb300 import mlq
+
+    prec = mlq.MLQ_MIXED if prec_name == "mixed" else mlq.MLQ_FP64
+    modes, _ = mlq.build_kl(LEVEL_M[-1], SIGMA2, ELL, K_MODES)
+    phi = mlq.centroid_table(LEVEL_M[-1], modes, LEVEL_M[level])
+    with mlq.Context(0, prec) as ctx:
+        ctx.add_level(level, LEVEL_M[level], level_dt(level), steps)
+        ctx.set_kl(level, phi)
+        ctx.set_profiling(True)
+        xi = inputs.gaussian_xi(0, level, 0, S, K_MODES)
+        res = ctx.solve(level, xi)
+        prof = ctx.member_profile()[0]
+    print(json.dumps({"case": spec, "kernel_ms": prof["kernel_ms"], "cg_iterations": prof["cg_iterations"],
+                      "cluster": prof["cluster"], "resident": prof["resident"], "q0": float(res["q_fine"][0])}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mlq", choices=["mlq", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--fp64-steps", type=int, default=1, help="timed FP64 comparison estimates (0: skip)")
+    ap.add_argument("--fp64-steps", type=int, default=0, help="timed FP64 comparison estimates (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default=None, help="profile one member solve, e.g. level=4,samples=1,steps=4")
     args = ap.parse_args()
+    if args.case:
+        return run_case(args.case)
     if args.impl == "reference":
         return run_reference(args)
 

@@ -78,10 +78,10 @@ typedef struct {
  *   max_sweeps cap on refinement sweeps per block (MLQ_MIXED only).
  *   cluster    CTAs per sample (1,2,4,8,16); 0 = chosen per level.
  *   threads    threads per CTA (64..512, multiple of 32); 0 = chosen.
- *   storage    where a sample's PCG vectors live: 0 = shared memory of its
- *              cluster when they fit, else global memory; 1 = shared memory
- *              (a solve whose level does not fit returns MLQ_EUNSUPPORTED);
- *              2 = global memory. */
+ *   storage    where a sample's PCG vectors live: 0 = on chip (registers and
+ *              shared memory of its cluster) when they fit, else global
+ *              memory; 1 = on chip (a solve whose level does not fit returns
+ *              MLQ_EUNSUPPORTED); 2 = global memory. */
 typedef struct {
     int precision;
     double rtol;
@@ -192,8 +192,9 @@ int mlq_member_profile(mlq_ctx *ctx, int max_members, int *count, mlq_member_sta
 int mlq_launch_count(mlq_ctx *ctx, int64_t *count);
 
 /* Launch shape chosen for a level under the context's options: cluster size
- * (CTAs per sample), threads per CTA, and *resident = 1 when the sample's PCG
- * vectors live in the cluster's shared memory (0: in global memory).
+ * (CTAs per sample), threads per CTA, and *resident: 2 = the sample's PCG
+ * vectors live in registers with the stencil rows in shared memory (mixed
+ * path), 1 = vectors in the cluster's shared memory, 0 = in global memory.
  * resident may be NULL. */
 int mlq_level_launch(mlq_ctx *ctx, int level, int *cluster, int *threads, int *resident);
 

@@ -109,19 +109,17 @@ bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-size_t tile_bytes(const Level &L, int cs)
-{
-    const int rows = (L.m + cs - 1) / cs + 2;
-    return (size_t)std::min(rows, L.m) * L.m * sizeof(double);
-}
-
 // Launch shape of a level: cluster size, threads per CTA, and whether the
 // sample's PCG vectors fit in the cluster's shared memory (preferred).
 struct Shape {
     int cs, threads;
     bool resident;
     size_t smem;
+    int npt;  // > 0: register-resident mixed kernel with this many nodes per thread
 };
+
+// nodes-per-thread variants compiled for the register-resident kernel
+constexpr int kNpt[] = {4, 8, 12};
 
 Shape choose_launch(const mlq_ctx *ctx, const Level &L)
 {
@@ -130,7 +128,7 @@ Shape choose_launch(const mlq_ctx *ctx, const Level &L)
     Shape sh{0, 0, false, 0};
     auto fits = [&](int c) {
         if (c > L.m) return false;
-        return mlq::smem_plan(L.m, c, ti).total <= limit;
+        return mlq::smem_plan(L.m, c, ti, true).total <= limit;
     };
     const bool allow = ctx->opt.storage != 2;
     if (ctx->opt.cluster > 0) {
@@ -156,7 +154,30 @@ Shape choose_launch(const mlq_ctx *ctx, const Level &L)
         t = per >= 2048 ? 512 : (per >= 768 ? 256 : 128);
     }
     sh.threads = t;
-    sh.smem = sh.resident ? (size_t)mlq::smem_plan(L.m, sh.cs, ti).total : tile_bytes(L, sh.cs);
+    sh.smem = (size_t)mlq::smem_plan(L.m, sh.cs, ti, sh.resident).total;
+    sh.npt = 0;
+    // mixed path: registers for the vectors when the stencil rows fit
+    if (sh.resident && ti == 4 && ctx->opt.storage != 2) {
+        const mlq::RegPlan rp = mlq::reg_plan(L.m, sh.cs);
+        if (rp.total <= limit) {
+            const int nmax = rp.nmax;
+            int best = 0, bt = 0;
+            for (int npt : kNpt) {
+                int th = ctx->opt.threads > 0 ? ctx->opt.threads : ((nmax + npt - 1) / npt + 31) / 32 * 32;
+                if (th < 32) th = 32;
+                if (th > (npt >= 12 ? 384 : 512) || (int64_t)th * npt < nmax) continue;
+                best = npt;
+                bt = th;
+                if (ctx->opt.threads <= 0 && npt >= 12) break;
+                if (ctx->opt.threads > 0) break;
+            }
+            if (best > 0) {
+                sh.npt = best;
+                sh.threads = bt;
+                sh.smem = (size_t)rp.total;
+            }
+        }
+    }
     return sh;
 }
 
@@ -164,7 +185,7 @@ template <typename TI, int CS>
 cudaError_t launch_slab(const mlq::SolveArgs<TI> &a, int nclusters, int threads, size_t smem, bool resident,
                         cudaStream_t st)
 {
-    auto kern = resident ? mlq::slab_solve_smem_kernel<TI, CS> : mlq::slab_solve_kernel<TI, CS>;
+    auto kern = resident ? mlq::slab_solve_kernel<TI, CS, true> : mlq::slab_solve_kernel<TI, CS, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (CS > 8) {
@@ -184,6 +205,56 @@ cudaError_t launch_slab(const mlq::SolveArgs<TI> &a, int nclusters, int threads,
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+template <int CS, int NPT>
+cudaError_t launch_reg(const mlq::SolveArgs<float> &a, int nclusters, int threads, size_t smem, cudaStream_t st)
+{
+    auto kern = mlq::slab_solve_reg_kernel<CS, NPT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (CS > 8) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(nclusters * CS));
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+template <int CS>
+cudaError_t launch_reg_npt(int npt, const mlq::SolveArgs<float> &a, int ncl, int threads, size_t smem,
+                           cudaStream_t st)
+{
+    switch (npt) {
+    case 4: return launch_reg<CS, 4>(a, ncl, threads, smem, st);
+    case 8: return launch_reg<CS, 8>(a, ncl, threads, smem, st);
+    case 12: return launch_reg<CS, 12>(a, ncl, threads, smem, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_reg_any(int cs, int npt, const mlq::SolveArgs<float> &a, int ncl, int threads, size_t smem,
+                           cudaStream_t st)
+{
+    switch (cs) {
+    case 1: return launch_reg_npt<1>(npt, a, ncl, threads, smem, st);
+    case 2: return launch_reg_npt<2>(npt, a, ncl, threads, smem, st);
+    case 4: return launch_reg_npt<4>(npt, a, ncl, threads, smem, st);
+    case 8: return launch_reg_npt<8>(npt, a, ncl, threads, smem, st);
+    case 16: return launch_reg_npt<16>(npt, a, ncl, threads, smem, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 template <typename TI>
@@ -321,7 +392,14 @@ int launch_member_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream_t
     if (ctx->opt.storage == 1 && !sh.resident) return MLQ_EUNSUPPORTED;
     const bool timed = ctx->profile && slot >= 0 && slot < kStreams;
     if (timed) MLQ_CUDA(ctx, cudaEventRecord(ctx->ev_t0[slot], st));
-    MLQ_CUDA(ctx, launch_slab_cs<TI>(sh.cs, a, (int)mb.S, sh.threads, sh.smem, sh.resident, st));
+    if constexpr (sizeof(TI) == 4) {
+        if (sh.npt > 0)
+            MLQ_CUDA(ctx, launch_reg_any(sh.cs, sh.npt, a, (int)mb.S, sh.threads, sh.smem, st));
+        else
+            MLQ_CUDA(ctx, launch_slab_cs<TI>(sh.cs, a, (int)mb.S, sh.threads, sh.smem, sh.resident, st));
+    } else {
+        MLQ_CUDA(ctx, launch_slab_cs<TI>(sh.cs, a, (int)mb.S, sh.threads, sh.smem, sh.resident, st));
+    }
     if (timed) MLQ_CUDA(ctx, cudaEventRecord(ctx->ev_t1[slot], st));
     ctx->launches++;
     return MLQ_OK;
@@ -335,7 +413,7 @@ int launch_member(mlq_ctx *ctx, const Member &mb, cudaStream_t st, int slot, int
         ctx->prof_level[slot] = mb.level;
         ctx->prof_coarse[slot] = coarse;
         ctx->prof_cs[slot] = sh.cs;
-        ctx->prof_resident[slot] = sh.resident;
+        ctx->prof_resident[slot] = sh.npt > 0 ? 2 : (sh.resident ? 1 : 0);
         ctx->prof_samples[slot] = mb.S;
         ctx->prof_nodes[slot] = L.n;
         ctx->prof_steps[slot] = L.nsteps;
@@ -450,7 +528,7 @@ int mlq_create(mlq_ctx **out, int device, void *cuda_stream, const mlq_options *
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        auto kern = mlq::slab_solve_kernel<float, 16>;
+        auto kern = mlq::slab_solve_kernel<float, 16, true>;
         int ncl = 0;
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 48 * 1024) == cudaSuccess &&
@@ -803,7 +881,7 @@ int mlq_level_launch(mlq_ctx *ctx, int level, int *cluster, int *threads, int *r
     const Shape sh = choose_launch(ctx, ctx->levels[level]);
     *cluster = sh.cs;
     *threads = sh.threads;
-    if (resident) *resident = sh.resident ? 1 : 0;
+    if (resident) *resident = sh.npt > 0 ? 2 : (sh.resident ? 1 : 0);
     return MLQ_OK;
 }
 

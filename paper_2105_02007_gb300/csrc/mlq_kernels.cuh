@@ -189,11 +189,22 @@ struct SolveArgs {
 template <typename T>
 __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
 
-// Sum NV doubles over the block and then over the cluster.  Every thread of
-// every CTA returns the same values: per-CTA partials are combined in rank
-// order, so the result does not depend on timing.
-template <int NV, int CS>
-__device__ __forceinline__ void cluster_sum(double (&v)[NV], double (*warp_buf)[4], double (*slots)[4], int par)
+// ---------------------------------------------------------------------------
+// Cluster-wide sums.
+//
+// Each thread passes NV partial sums in its own precision TA (FP32 in the
+// mixed path).  They are summed over the warp in TA and converted to FP64;
+// warp 0 adds the per-warp values with a butterfly over its lanes (FP64),
+// giving the CTA's total; with CS > 1 the CTA totals are exchanged over DSMEM
+// after a cluster barrier and added with a butterfly over CS lanes.  Every
+// CTA therefore gets bit-identical totals, independent of timing.  Thread 0
+// hands the totals to `fin`; its writes to shared memory are visible to the
+// whole CTA on return.
+//   wsl: [32][4] doubles (per-warp values), csl: [2][4] doubles (CTA totals,
+//   alternating by `par` so that a slow reader never sees the next round).
+// ---------------------------------------------------------------------------
+template <int NV, int CS, typename TA, typename F>
+__device__ __forceinline__ void cluster_reduce(TA (&v)[NV], double (*wsl)[4], double (*csl)[4], int par, F &&fin)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
 #pragma unroll
@@ -203,25 +214,75 @@ __device__ __forceinline__ void cluster_sum(double (&v)[NV], double (*warp_buf)[
     }
     if (lane == 0) {
 #pragma unroll
-        for (int k = 0; k < NV; ++k) warp_buf[warp][k] = v[k];
+        for (int k = 0; k < NV; ++k) wsl[warp][k] = (double)v[k];
     }
     __syncthreads();
-    if (threadIdx.x < NV) {
-        double t = 0.0;
-        for (int w = 0; w < nwarp; ++w) t += warp_buf[w][threadIdx.x];
-        slots[par][threadIdx.x] = t;
+    double acc[NV];
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] = lane < nwarp ? wsl[lane][k] : 0.0;
+        for (int o = 1; o < nwarp; o <<= 1) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+        }
     }
-    cg::cluster_group cl = cg::this_cluster();
-    cl.sync();
+    if constexpr (CS == 1) {
+        if (threadIdx.x == 0) fin(acc);
+    } else {
+        if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = 0.0;
+            for (int k = 0; k < NV; ++k) csl[par][k] = acc[k];
+        }
+        cg::cluster_group cl = cg::this_cluster();
+        cl.sync();
+        if (warp == 0) {
+            double t[NV];
+            const double *rs = lane < CS ? cl.map_shared_rank(&csl[par][0], lane) : nullptr;
 #pragma unroll
-    for (int r = 0; r < CS; ++r) {
-        const double *rs = cl.map_shared_rank(&slots[par][0], r);
+            for (int k = 0; k < NV; ++k) t[k] = lane < CS ? rs[k] : 0.0;
 #pragma unroll
-        for (int k = 0; k < NV; ++k) v[k] += rs[k];
+            for (int o = 1; o < CS; o <<= 1) {
+#pragma unroll
+                for (int k = 0; k < NV; ++k) t[k] += __shfl_xor_sync(0xffffffffu, t[k], o);
+            }
+            if (lane == 0) fin(t);
+        }
     }
+    __syncthreads();
 }
+
+// 1/d in FP64 from an FP32 reciprocal and one Newton-Raphson step
+// r <- r + r (1 - d r) (the error squares: ~2^-46 relative), for d well
+// inside the FP32 range; used for the PCG scalars of the normalised inner
+// problem, whose magnitudes are bounded away from FP32 limits.
+__device__ __forceinline__ double rcp_newton(double d)
+{
+    double r = (double)(1.0f / (float)d);
+    return fma(r, fma(-d, r, 1.0), r);
+}
+
+// Walks the nodes own0 + tid, own0 + tid + nt, ... keeping (i, j) without
+// a division per node.
+struct NodeWalk {
+    int i, j, di, dj, m;
+    __device__ __forceinline__ void init(int node, int nt, int m_)
+    {
+        m = m_;
+        j = node / m;
+        i = node - j * m;
+        dj = nt / m;
+        di = nt - dj * m;
+    }
+    __device__ __forceinline__ void next()
+    {
+        i += di;
+        j += dj;
+        if (i >= m) {
+            i -= m;
+            ++j;
+        }
+    }
+};
 
 // Stencil apply at own node P = (i, j) (tile index l) for a vector held in a
 // shared-memory tile; coefficients from the sample's stored stencil.
@@ -288,248 +349,33 @@ __device__ __forceinline__ double lumped_mass(int m, int i, int j, double h2)
     return (double)ninc * h2 / 6.0;
 }
 
-// One cluster of CS CTAs per sample.  CTA `rank` owns rows [r0, r1) of the
-// m x m grid; its shared tile holds rows [lo, hi) = own rows plus one halo row
-// on each side.  Per time block (multiple time blocks, Sec. 3.3):
-//   S1  y = v + dt R(v, w) on the tile, b = M y, w <- w + dt eps (v - gam w),
-//       r = b - A v                                         (eq. mono_disc)
-//   refinement sweeps: inner Jacobi-PCG on A d = r (Chronopoulos-Gear form:
-//       one cluster barrier per iteration), v += d, new FP64 residual.
-// In the FP64 path (TI = double) one sweep runs to rtol ||b||.
-template <typename TI, int CS>
-__global__ void __launch_bounds__(512, 1) slab_solve_kernel(SolveArgs<TI> g)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double warp_buf[32][4];
-    __shared__ double slots[2][4];
-
-    cg::cluster_group cl = cg::this_cluster();
-    const int rank = (int)cl.block_rank();
-    const int sample = blockIdx.x / CS;
-    const int m = g.m, n = g.n;
-    const int r0 = (int)(((int64_t)m * rank) / CS), r1 = (int)(((int64_t)m * (rank + 1)) / CS);
-    const int lo = r0 > 0 ? r0 - 1 : 0, hi = r1 < m ? r1 + 1 : m;
-    const int own0 = r0 * m, own1 = r1 * m, tile0 = lo * m, tile1 = hi * m;
-    const int tid = threadIdx.x, nt = blockDim.x;
-
-    double *ytile = reinterpret_cast<double *>(smem_raw);   // FP64 tile (block S1)
-    TI *utile = reinterpret_cast<TI *>(smem_raw);           // inner-precision tile (PCG)
-
-    const size_t so = (size_t)sample * n;
-    const size_t SN = (size_t)g.S * n;  // stride between the two halves of a double buffer
-    const double *A64 = g.A64 + (size_t)sample * kSlots2D * n;
-    const TI *Ai = g.Ai + (size_t)sample * kSlots2D * n;
-    const TI *Dinv = Ai + 4 * (size_t)n;
-    double *v = g.v + so;
-    double *wb0 = g.w + so;
-    double *b = g.b + so;
-    TI *rb0 = g.r + so;
-    TI *sb0 = g.s + so;
-    TI *wc0 = g.wc + so;
-    TI *p = g.p + so;
-    TI *x = g.x + so;
-    int par = 0;  // parity of the reduction slots
-
-    // initial state
-    for (int node = own0 + tid; node < own1; node += nt) {
-        double v0, w0;
-        if (g.v0) {
-            v0 = g.v0[node];
-            w0 = g.w0 ? g.w0[node] : 0.0;
-        } else {
-            const int j = (int)g.divm.div((uint32_t)node), i = node - j * m;
-            const double xx = (double)i / (double)(m - 1), yy = (double)j / (double)(m - 1);
-            v0 = (xx * xx + yy * yy <= g.radius2) ? 1.0 : 0.0;
-            w0 = 0.0;
-        }
-        v[node] = v0;
-        wb0[node] = w0;
-    }
-    cl.sync();
-
-    int wpar = 0;
-    int64_t total_iters = 0;
-    int32_t status = S_CONVERGED;
-    const bool mixed = sizeof(TI) == 4;
-    const double dt = g.dt;
-
-    for (int step = 0; step < g.nsteps; ++step) {
-        // ---- S1: reaction, consistent-mass load, recovery update, residual
-        for (int node = tile0 + tid; node < tile1; node += nt) {
-            const double vv = ldcg(v + node), ww = ldcg(wb0 + wpar * SN + node);
-            const double R = vv * (vv - g.a) * (1.0 - vv) - ww;
-            ytile[node - tile0] = vv + dt * R;
-        }
-        __syncthreads();
-        double acc[2] = {0.0, 0.0};  // |b|^2, |r|^2
-        double *wcur = wb0 + wpar * SN, *wnext = wb0 + (wpar ^ 1) * SN;
-        for (int node = own0 + tid; node < own1; node += nt) {
-            const int j = (int)g.divm.div((uint32_t)node), i = node - j * m;
-            const double bb = mass_apply(m, i, j, g.h2, ytile, node - tile0);
-            b[node] = bb;
-            const double vv = v[node], ww = wcur[node];
-            wnext[node] = ww + dt * g.eps * (vv - g.gam * ww);
-            const double rr = bb - stencil_apply_global(A64, n, m, node, i, j, v);
-            rb0[node] = (TI)rr;
-            acc[0] += bb * bb;
-            acc[1] += rr * rr;
-        }
-        cluster_sum<2, CS>(acc, warp_buf, slots, par);
-        par ^= 1;
-        wpar ^= 1;
-        const double bnorm2 = acc[0];
-        double rnorm2 = acc[1];
-        if (!(isfinite(bnorm2) && isfinite(rnorm2))) {
-            status = S_NONFINITE;
-            break;
-        }
-        const double tol_out2 = g.rtol_out * g.rtol_out * bnorm2;
-
-        bool nonfinite = false, solved = false;
-        for (int sweep = 0; sweep < g.max_sweeps; ++sweep) {
-            if (sweep > 0) {
-                // ---- FP64 residual of the refined iterate
-                double racc[2] = {0.0, 0.0};
-                for (int node = own0 + tid; node < own1; node += nt) {
-                    const int j = (int)g.divm.div((uint32_t)node), i = node - j * m;
-                    const double rr = b[node] - stencil_apply_global(A64, n, m, node, i, j, v);
-                    rb0[node] = (TI)rr;
-                    racc[0] += rr * rr;
-                }
-                cluster_sum<2, CS>(racc, warp_buf, slots, par);
-                par ^= 1;
-                rnorm2 = racc[0];
-                if (!isfinite(rnorm2)) { nonfinite = true; break; }
-            }
-            if (rnorm2 <= tol_out2) { solved = true; break; }
-            const double tol_in2 = mixed ? g.rtol_in * g.rtol_in * rnorm2 : tol_out2;
-
-            // ---- inner PCG init: u0 = r0 / d on the tile, w0 = A u0
-            for (int node = tile0 + tid; node < tile1; node += nt)
-                utile[node - tile0] = ldcg(rb0 + node) * Dinv[node];
-            __syncthreads();
-            double iacc[3] = {0.0, 0.0, 0.0};  // gamma, delta, |r|^2
-            for (int node = own0 + tid; node < own1; node += nt) {
-                const int j = (int)g.divm.div((uint32_t)node), i = node - j * m;
-                const int l = node - tile0;
-                const TI u0 = utile[l];
-                const TI w0 = stencil_apply<TI, TI>(Ai, n, m, node, i, j, utile, l);
-                wc0[node] = w0;
-                x[node] = (TI)0;
-                const TI r0v = rb0[node];
-                iacc[0] += (double)(r0v * u0);
-                iacc[1] += (double)(w0 * u0);
-                iacc[2] += (double)(r0v * r0v);
-            }
-            cluster_sum<3, CS>(iacc, warp_buf, slots, par);
-            par ^= 1;
-            double gamma = iacc[0], delta = iacc[1], rr = iacc[2];
-            double gamma_prev = 1.0, alpha_prev = 1.0;
-            int it = 0;
-            while (true) {
-                if (!isfinite(rr) || !isfinite(gamma) || !isfinite(delta)) { nonfinite = true; break; }
-                if (rr <= tol_in2) { solved = !mixed; break; }
-                if (it >= g.max_iter) { status = status == S_CONVERGED ? S_MAXITER : status; break; }
-                double alpha, beta;
-                if (it == 0) {
-                    beta = 0.0;
-                    alpha = gamma / delta;
-                } else {
-                    beta = gamma / gamma_prev;
-                    alpha = gamma / (delta - beta * gamma / alpha_prev);
-                }
-                const TI ta = (TI)alpha, tb = (TI)beta;
-                const int cur = it & 1, nxt = cur ^ 1;
-                const TI *rcur = rb0 + cur * SN, *wcurv = wc0 + cur * SN, *sprev = sb0 + nxt * SN;
-                TI *rnext = rb0 + nxt * SN, *scur = sb0 + cur * SN, *wnextv = wc0 + nxt * SN;
-                double pacc[3] = {0.0, 0.0, 0.0};
-                // s_i = w_i + beta s_{i-1};  r_{i+1} = r_i - alpha s_i;  u_{i+1} = r_{i+1}/d
-                // (own rows and halo rows: the halo is recomputed from the
-                // neighbours' previous-iteration vectors, double-buffered)
-                for (int node = tile0 + tid; node < tile1; node += nt) {
-                    const TI ri = ldcg(rcur + node), wi = ldcg(wcurv + node);
-                    const TI sp = it == 0 ? (TI)0 : ldcg(sprev + node);
-                    const TI si = wi + tb * sp;
-                    const TI rn = ri - ta * si;
-                    const TI di = Dinv[node];
-                    const TI un = rn * di;
-                    utile[node - tile0] = un;
-                    if (node >= own0 && node < own1) {
-                        const TI ui = ri * di;
-                        const TI pi = it == 0 ? ui : ui + tb * p[node];
-                        x[node] = x[node] + ta * pi;
-                        p[node] = pi;
-                        scur[node] = si;
-                        rnext[node] = rn;
-                        pacc[0] += (double)(rn * un);
-                        pacc[2] += (double)(rn * rn);
-                    }
-                }
-                __syncthreads();
-                for (int node = own0 + tid; node < own1; node += nt) {
-                    const int j = (int)g.divm.div((uint32_t)node), i = node - j * m;
-                    const int l = node - tile0;
-                    const TI wn = stencil_apply<TI, TI>(Ai, n, m, node, i, j, utile, l);
-                    wnextv[node] = wn;
-                    pacc[1] += (double)(wn * utile[l]);
-                }
-                cluster_sum<3, CS>(pacc, warp_buf, slots, par);
-                par ^= 1;
-                gamma_prev = gamma;
-                alpha_prev = alpha;
-                gamma = pacc[0];
-                delta = pacc[1];
-                rr = pacc[2];
-                ++it;
-            }
-            total_iters += it;
-            if (nonfinite) break;
-            // ---- v += d
-            for (int node = own0 + tid; node < own1; node += nt)
-                v[node] = v[node] + (double)x[node];
-            cl.sync();
-            if (!mixed) break;  // FP64: a single sweep solves to rtol ||b||
-        }
-        if (nonfinite) {
-            status = S_NONFINITE;
-            break;
-        }
-        if (!solved && status == S_CONVERGED) status = S_MAXITER;
-    }
-
-    // ---- QoI: Q = m^T v, m = M 1
-    double qacc[1] = {0.0};
-    for (int node = own0 + tid; node < own1; node += nt) {
-        const int j = (int)g.divm.div((uint32_t)node), i = node - j * m;
-        qacc[0] += lumped_mass(m, i, j, g.h2) * v[node];
-    }
-    cluster_sum<1, CS>(qacc, warp_buf, slots, par);
-    if (rank == 0 && tid == 0) {
-        g.q[sample] = status == S_NONFINITE ? __longlong_as_double(0x7ff8000000000000LL) : qacc[0];
-        g.iters[sample] = (int32_t)(total_iters > 0x7fffffff ? 0x7fffffff : total_iters);
-        g.status[sample] = status;
-    }
-    // keep every CTA's shared memory alive until all remote reads are done
-    cl.sync();
-}
-
 // ---------------------------------------------------------------------------
-// Shared-memory-resident variant of the slab solver.
+// Slab solver: every time block of one sample in one cluster of CS CTAs.
 //
-// Same algorithm and the same cluster decomposition as slab_solve_kernel, but
-// every PCG vector of a CTA's rows lives in its shared memory for the whole
-// run, and the halo rows of the next iterate are recomputed from the
-// neighbouring CTAs' shared memory over DSMEM (distributed shared memory of
-// the thread-block cluster).  The CG loop then touches global memory only for
-// the read-only stencil coefficients (L1 resident).  The FP64 state (v, w, b)
-// stays in global memory: it is read once per refinement sweep.
+// CTA `rank` owns rows [r0, r1) of the m x m grid.  Per time block (multiple
+// time blocks of the paper's Sec. 3.3, one backward-Euler step each):
+//   load   y = v + dt R(v, w) on the rows [r0-1, r1+1), b = M y,
+//          w <- w + dt eps (v - gam w), r = b - A v            (eq. mono_disc)
+//   sweeps inner Jacobi-PCG on A d = r from d = 0, then v += d and a new FP64
+//          residual; the mixed path repeats until ||b - A v|| <= rtol ||b||,
+//          the FP64 path runs one sweep to that tolerance.
+// The PCG is the Chronopoulos-Gear form (one reduction per iteration):
+//   s_i = w_i + b_i s_{i-1},  r_{i+1} = r_i - a_i s_i,  u_{i+1} = D^-1 r_{i+1},
+//   w_{i+1} = A u_{i+1},  g = (r, u),  d = (w, u),
+//   b_i = g_i / g_{i-1},  a_i = g_i / (d_i - b_i g_i / a_{i-1}).
+// The halo rows of u_{i+1} are recomputed from the neighbours' r_i, w_i,
+// s_{i-1} (double-buffered), so an iteration needs one cluster barrier.
 //
-// Shared layout, identical in every CTA of the cluster (so that a neighbour's
-// array is the same offset in its window):
-//   utile  (rows_max + 2) * m   TI   tile rows [lo, hi) of the next iterate
+// RES = true: the PCG vectors of a CTA's rows live in its shared memory and
+// the neighbours' rows are read over DSMEM; RES = false: they live in global
+// memory (halo rows through L2).  The FP64 state v, w, b is in global memory.
+//
+// Shared layout (RES), identical in every CTA of the cluster:
+//   utile  (rows_max + 2) * m   TI   rows [lo, hi) of the next iterate
 //   R0 R1 W0 W1 S0 S1 P X       nmax TI each, own nodes, local index
-//   ytile  (rows_max + 2) * m   FP64, aliases S0..X (dead while a block's
-//          load vector is formed)
+//   ytile  (rows_max + 2) * m   FP64, aliases S0..X (dead while a block's load
+//          vector is formed)
+// Without RES only utile / ytile (aliased) are in shared memory.
 // ---------------------------------------------------------------------------
 struct SmemPlan {
     int nmax;       // rows_max * m
@@ -542,12 +388,19 @@ struct SmemPlan {
 
 __host__ __device__ inline int align16(int b) { return (b + 15) & ~15; }
 
-__host__ __device__ inline SmemPlan smem_plan(int m, int cs, int ti_bytes)
+__host__ __device__ inline SmemPlan smem_plan(int m, int cs, int ti_bytes, bool resident)
 {
     SmemPlan pl;
     const int rows = (m + cs - 1) / cs;
     pl.nmax = rows * m;
     pl.tile = (rows + 2 < m ? rows + 2 : m) * m;
+    if (!resident) {
+        pl.off_vec = 0;
+        pl.vec_bytes = 0;
+        pl.off_y = 0;
+        pl.total = align16(pl.tile * 8);
+        return pl;
+    }
     pl.off_vec = align16(pl.tile * ti_bytes);
     pl.vec_bytes = align16(pl.nmax * ti_bytes);
     pl.off_y = pl.off_vec + 4 * pl.vec_bytes;
@@ -557,12 +410,27 @@ __host__ __device__ inline SmemPlan smem_plan(int m, int cs, int ti_bytes)
     return pl;
 }
 
-template <typename TI, int CS>
-__global__ void __launch_bounds__(512, 1) slab_solve_smem_kernel(SolveArgs<TI> g)
+// control words written by thread 0, read by every thread
+struct Ctl {
+    double alpha, beta;
+    double s0, s1;      // broadcast sums (load / residual phases)
+    int code;           // 0 continue, 1 converged, 2 max_iter, 3 non-finite
+};
+
+template <bool RES, typename T>
+__device__ __forceinline__ T ld_halo(const T *p)
+{
+    if constexpr (RES) return *p;   // neighbour's shared memory over DSMEM
+    else return __ldcg(p);          // another CTA's rows: bypass L1
+}
+
+template <typename TI, int CS, bool RES>
+__global__ void __launch_bounds__(512, 1) slab_solve_kernel(SolveArgs<TI> g)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double warp_buf[32][4];
-    __shared__ double slots[2][4];
+    __shared__ double wsl[32][4];
+    __shared__ double csl[2][4];
+    __shared__ Ctl ctl;
 
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
@@ -573,36 +441,61 @@ __global__ void __launch_bounds__(512, 1) slab_solve_smem_kernel(SolveArgs<TI> g
     const int own0 = r0 * m, own1 = r1 * m, tile0 = lo * m, tile1 = hi * m;
     const int nown = own1 - own0;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const SmemPlan pl = smem_plan(m, CS, (int)sizeof(TI));
+    const bool has_lo = rank > 0, has_hi = rank + 1 < CS;
+    const SmemPlan pl = smem_plan(m, CS, (int)sizeof(TI), RES);
 
     TI *utile = reinterpret_cast<TI *>(smem_raw);
-    TI *vec0 = reinterpret_cast<TI *>(smem_raw + pl.off_vec);
-    const int vstride = pl.vec_bytes / (int)sizeof(TI);
-    TI *Rv = vec0;                 // R0, R1 at Rv, Rv + vstride
-    TI *Wv = vec0 + 2 * vstride;   // W0, W1
-    TI *Sv = vec0 + 4 * vstride;   // S0, S1
-    TI *P = vec0 + 6 * vstride;
-    TI *X = vec0 + 7 * vstride;
     double *ytile = reinterpret_cast<double *>(smem_raw + pl.off_y);
-    const int ushift = own0 - tile0;  // tile index of own local index 0
-
-    // neighbours' windows (their arrays sit at the same offsets)
-    const bool has_lo = rank > 0, has_hi = rank + 1 < CS;
-    const int r0_lo = has_lo ? (int)(((int64_t)m * (rank - 1)) / CS) : 0;
-    TI *vec_lo = has_lo ? cl.map_shared_rank(vec0, rank - 1) : nullptr;
-    TI *vec_hi = has_hi ? cl.map_shared_rank(vec0, rank + 1) : nullptr;
-    // local index, in the neighbour's numbering, of our halo rows' first node
-    const int lo_base = (r0 - 1 - r0_lo) * m;  // row r0-1 in rank-1
-    const int hi_base = 0;                     // row r1 is rank+1's first row
+    const int ushift = own0 - tile0;
 
     const size_t so = (size_t)sample * n;
+    const size_t SN = (size_t)g.S * n;
     const double *A64 = g.A64 + (size_t)sample * kSlots2D * n;
     const TI *Ai = g.Ai + (size_t)sample * kSlots2D * n;
     const TI *Dinv = Ai + 4 * (size_t)n;
     double *v = g.v + so;
     double *wb0 = g.w + so;
-    const size_t SN = (size_t)g.S * n;
     double *b = g.b + so;
+
+    // PCG vectors: own rows (local index) and the neighbours' boundary rows
+    TI *R, *W, *Sv, *P, *X;
+    const TI *Rlo = nullptr, *Wlo = nullptr, *Slo = nullptr, *Rhi = nullptr, *Whi = nullptr, *Shi = nullptr;
+    size_t vs;  // stride between the two halves of a double buffer
+    if constexpr (RES) {
+        TI *vec0 = reinterpret_cast<TI *>(smem_raw + pl.off_vec);
+        vs = (size_t)(pl.vec_bytes / (int)sizeof(TI));
+        R = vec0;
+        W = vec0 + 2 * vs;
+        Sv = vec0 + 4 * vs;
+        P = vec0 + 6 * vs;
+        X = vec0 + 7 * vs;
+        if (has_lo) {
+            const int r0_lo = (int)(((int64_t)m * (rank - 1)) / CS);
+            const TI *nb = cl.map_shared_rank(vec0, rank - 1) + (r0 - 1 - r0_lo) * m;
+            Rlo = nb;
+            Wlo = nb + 2 * vs;
+            Slo = nb + 4 * vs;
+        }
+        if (has_hi) {
+            const TI *nb = cl.map_shared_rank(vec0, rank + 1);
+            Rhi = nb;
+            Whi = nb + 2 * vs;
+            Shi = nb + 4 * vs;
+        }
+    } else {
+        vs = SN;
+        R = g.r + so + own0;
+        W = g.wc + so + own0;
+        Sv = g.s + so + own0;
+        P = g.p + so + own0;
+        X = g.x + so + own0;
+        Rlo = g.r + so + tile0;
+        Wlo = g.wc + so + tile0;
+        Slo = g.s + so + tile0;
+        Rhi = g.r + so + own1;
+        Whi = g.wc + so + own1;
+        Shi = g.s + so + own1;
+    }
     int par = 0;
 
     for (int node = own0 + tid; node < own1; node += nt) {
@@ -611,7 +504,7 @@ __global__ void __launch_bounds__(512, 1) slab_solve_smem_kernel(SolveArgs<TI> g
             v0 = g.v0[node];
             w0 = g.w0 ? g.w0[node] : 0.0;
         } else {
-            const int j = (int)g.divm.div((uint32_t)node), i = node - j * m;
+            const int j = node / m, i = node - j * m;
             const double xx = (double)i / (double)(m - 1), yy = (double)j / (double)(m - 1);
             v0 = (xx * xx + yy * yy <= g.radius2) ? 1.0 : 0.0;
             w0 = 0.0;
@@ -622,39 +515,45 @@ __global__ void __launch_bounds__(512, 1) slab_solve_smem_kernel(SolveArgs<TI> g
     cl.sync();
 
     int wpar = 0;
-    int64_t total_iters = 0;
+    int64_t total_iters = 0;     // thread 0's count
     int32_t status = S_CONVERGED;
-    const bool mixed = sizeof(TI) == 4;
+    constexpr bool mixed = sizeof(TI) == 4;
     const double dt = g.dt;
 
     for (int step = 0; step < g.nsteps; ++step) {
-        // ---- block load: y = v + dt R(v, w) on the tile, b = M y, w update,
-        //      r0 = b - A v into R0 (own rows)
+        // ---- block load
         const double *wcur = wb0 + wpar * SN;
         double *wnext = wb0 + (wpar ^ 1) * SN;
         for (int node = tile0 + tid; node < tile1; node += nt) {
             const double vv = ldcg(v + node), ww = ldcg(wcur + node);
-            const double R = vv * (vv - g.a) * (1.0 - vv) - ww;
-            ytile[node - tile0] = vv + dt * R;
+            const double Rr = vv * (vv - g.a) * (1.0 - vv) - ww;
+            ytile[node - tile0] = vv + dt * Rr;
         }
         __syncthreads();
-        double acc[2] = {0.0, 0.0};
-        for (int node = own0 + tid; node < own1; node += nt) {
-            const int j = (int)g.divm.div((uint32_t)node), i = node - j * m;
-            const double bb = mass_apply(m, i, j, g.h2, ytile, node - tile0);
-            b[node] = bb;
-            const double vv = v[node], ww = wcur[node];
-            wnext[node] = ww + dt * g.eps * (vv - g.gam * ww);
-            const double rr = bb - stencil_apply_global(A64, n, m, node, i, j, v);
-            Rv[node - own0] = (TI)rr;
-            acc[0] += bb * bb;
-            acc[1] += rr * rr;
+        {
+            double acc[2] = {0.0, 0.0};
+            NodeWalk nw;
+            nw.init(own0 + tid, nt, m);
+            for (int l = tid; l < nown; l += nt, nw.next()) {
+                const int node = own0 + l;
+                const double bb = mass_apply(m, nw.i, nw.j, g.h2, ytile, node - tile0);
+                b[node] = bb;
+                const double vv = v[node], ww = wcur[node];
+                wnext[node] = ww + dt * g.eps * (vv - g.gam * ww);
+                const double rr = bb - stencil_apply_global(A64, n, m, node, nw.i, nw.j, v);
+                R[l] = (TI)rr;
+                acc[0] += bb * bb;
+                acc[1] += rr * rr;
+            }
+            cluster_reduce<2, CS>(acc, wsl, csl, par, [&](double(&t)[2]) {
+                ctl.s0 = t[0];
+                ctl.s1 = t[1];
+            });
+            par ^= 1;
         }
-        cluster_sum<2, CS>(acc, warp_buf, slots, par);
-        par ^= 1;
         wpar ^= 1;
-        const double bnorm2 = acc[0];
-        double rnorm2 = acc[1];
+        const double bnorm2 = ctl.s0;
+        double rnorm2 = ctl.s1;
         if (!(isfinite(bnorm2) && isfinite(rnorm2))) {
             status = S_NONFINITE;
             break;
@@ -664,67 +563,87 @@ __global__ void __launch_bounds__(512, 1) slab_solve_smem_kernel(SolveArgs<TI> g
         bool nonfinite = false, solved = false;
         for (int sweep = 0; sweep < g.max_sweeps; ++sweep) {
             if (sweep > 0) {
-                double racc[2] = {0.0, 0.0};
-                for (int node = own0 + tid; node < own1; node += nt) {
-                    const int j = (int)g.divm.div((uint32_t)node), i = node - j * m;
-                    const double rr = b[node] - stencil_apply_global(A64, n, m, node, i, j, v);
-                    Rv[node - own0] = (TI)rr;
+                double racc[1] = {0.0};
+                NodeWalk nw;
+                nw.init(own0 + tid, nt, m);
+                for (int l = tid; l < nown; l += nt, nw.next()) {
+                    const int node = own0 + l;
+                    const double rr = b[node] - stencil_apply_global(A64, n, m, node, nw.i, nw.j, v);
+                    R[l] = (TI)rr;
                     racc[0] += rr * rr;
                 }
-                cluster_sum<2, CS>(racc, warp_buf, slots, par);
+                cluster_reduce<1, CS>(racc, wsl, csl, par, [&](double(&t)[1]) { ctl.s1 = t[0]; });
                 par ^= 1;
-                rnorm2 = racc[0];
+                rnorm2 = ctl.s1;
                 if (!isfinite(rnorm2)) { nonfinite = true; break; }
             }
             if (rnorm2 <= tol_out2) { solved = true; break; }
             const double tol_in2 = mixed ? g.rtol_in * g.rtol_in * rnorm2 : tol_out2;
 
-            // ---- inner PCG init: u0 = r0 d^-1 on the tile, w0 = A u0, x = 0
-            for (int l = tid; l < nown; l += nt) utile[l + ushift] = Rv[l] * Dinv[own0 + l];
+            // ---- inner PCG init: u0 = D^-1 r0 on the tile, w0 = A u0, x = 0
+            for (int l = tid; l < nown; l += nt) utile[l + ushift] = R[l] * Dinv[own0 + l];
             if (has_lo)
-                for (int i = tid; i < m; i += nt)
-                    utile[i] = vec_lo[lo_base + i] * Dinv[tile0 + i];
+                for (int i = tid; i < m; i += nt) utile[i] = ld_halo<RES>(Rlo + i) * Dinv[tile0 + i];
             if (has_hi)
                 for (int i = tid; i < m; i += nt)
-                    utile[own1 - tile0 + i] = vec_hi[hi_base + i] * Dinv[own1 + i];
+                    utile[own1 - tile0 + i] = ld_halo<RES>(Rhi + i) * Dinv[own1 + i];
             __syncthreads();
-            double iacc[3] = {0.0, 0.0, 0.0};
-            for (int l = tid; l < nown; l += nt) {
-                const int node = own0 + l;
-                const int j = (int)g.divm.div((uint32_t)node), i = node - j * m;
-                const TI u0 = utile[l + ushift];
-                const TI w0 = stencil_apply<TI, TI>(Ai, n, m, node, i, j, utile, l + ushift);
-                Wv[l] = w0;
-                X[l] = (TI)0;
-                const TI r0v = Rv[l];
-                iacc[0] += (double)(r0v * u0);
-                iacc[1] += (double)(w0 * u0);
-                iacc[2] += (double)(r0v * r0v);
-            }
-            cluster_sum<3, CS>(iacc, warp_buf, slots, par);
-            par ^= 1;
-            double gamma = iacc[0], delta = iacc[1], rr = iacc[2];
-            double gamma_prev = 1.0, alpha_prev = 1.0;
+            // thread 0's recurrence state: eta_i = (p_i, A p_i) = delta_i - beta_i^2 eta_{i-1}
+            double gamma_prev = 1.0, eta_prev = 1.0;
             int it = 0;
-            while (true) {
-                if (!isfinite(rr) || !isfinite(gamma) || !isfinite(delta)) { nonfinite = true; break; }
-                if (rr <= tol_in2) { solved = !mixed; break; }
-                if (it >= g.max_iter) { status = status == S_CONVERGED ? S_MAXITER : status; break; }
-                double alpha, beta;
-                if (it == 0) {
-                    beta = 0.0;
-                    alpha = gamma / delta;
-                } else {
-                    beta = gamma / gamma_prev;
-                    alpha = gamma / (delta - beta * gamma / alpha_prev);
+            auto decide = [&](double gamma, double delta, double rr) {
+                // runs on thread 0 only
+                double alpha = 0.0, beta = 0.0;
+                int code;
+                if (!isfinite(rr) || !isfinite(gamma) || !isfinite(delta)) code = 3;
+                else if (rr <= tol_in2) code = 1;
+                else if (it >= g.max_iter) code = 2;
+                else {
+                    code = 0;
+                    double eta = delta;
+                    if (it > 0) {
+                        beta = gamma / gamma_prev;
+                        eta = delta - beta * beta * eta_prev;
+                    }
+                    alpha = gamma / eta;
+                    gamma_prev = gamma;
+                    eta_prev = eta;
                 }
-                const TI ta = (TI)alpha, tb = (TI)beta;
+                ctl.alpha = alpha;
+                ctl.beta = beta;
+                ctl.code = code;
+            };
+            {
+                TI iacc[3] = {(TI)0, (TI)0, (TI)0};
+                NodeWalk nw;
+                nw.init(own0 + tid, nt, m);
+                for (int l = tid; l < nown; l += nt, nw.next()) {
+                    const TI u0 = utile[l + ushift];
+                    const TI w0 = stencil_apply<TI, TI>(Ai, n, m, own0 + l, nw.i, nw.j, utile, l + ushift);
+                    W[l] = w0;
+                    X[l] = (TI)0;
+                    const TI r0v = R[l];
+                    iacc[0] += r0v * u0;
+                    iacc[1] += w0 * u0;
+                    iacc[2] += r0v * r0v;
+                }
+                cluster_reduce<3, CS>(iacc, wsl, csl, par, [&](double(&t)[3]) { decide(t[0], t[1], t[2]); });
+                par ^= 1;
+            }
+            while (true) {
+                const int code = ctl.code;
+                if (code != 0) {
+                    if (code == 3) nonfinite = true;
+                    else if (code == 1) solved = !mixed;
+                    else status = status == S_CONVERGED ? S_MAXITER : status;
+                    break;
+                }
+                const TI ta = (TI)ctl.alpha, tb = (TI)ctl.beta;
                 const int cur = it & 1, nxt = cur ^ 1;
-                TI *Rc = Rv + cur * vstride, *Rn = Rv + nxt * vstride;
-                TI *Wc = Wv + cur * vstride, *Wn = Wv + nxt * vstride;
-                TI *Sc = Sv + cur * vstride, *Sp = Sv + nxt * vstride;
-                double pacc[3] = {0.0, 0.0, 0.0};
-                // own rows
+                TI *Rc = R + cur * vs, *Rn = R + nxt * vs;
+                TI *Wc = W + cur * vs, *Wn = W + nxt * vs;
+                TI *Sc = Sv + cur * vs, *Sp = Sv + nxt * vs;
+                TI pacc[3] = {(TI)0, (TI)0, (TI)0};
                 for (int l = tid; l < nown; l += nt) {
                     const TI ri = Rc[l], wi = Wc[l];
                     const TI si = it == 0 ? wi : wi + tb * Sp[l];
@@ -738,44 +657,38 @@ __global__ void __launch_bounds__(512, 1) slab_solve_smem_kernel(SolveArgs<TI> g
                     P[l] = pi;
                     Sc[l] = si;
                     Rn[l] = rn;
-                    pacc[0] += (double)(rn * un);
-                    pacc[2] += (double)(rn * rn);
+                    pacc[0] += rn * un;
+                    pacc[2] += rn * rn;
                 }
-                // halo rows: the neighbours' r_i, w_i, s_{i-1} over DSMEM
                 if (has_lo) {
-                    const TI *rr_ = vec_lo + cur * vstride, *ww_ = vec_lo + (2 + cur) * vstride;
-                    const TI *ss_ = vec_lo + (4 + nxt) * vstride;
+                    const TI *rr_ = Rlo + cur * vs, *ww_ = Wlo + cur * vs, *ss_ = Slo + nxt * vs;
                     for (int i = tid; i < m; i += nt) {
-                        const int k = lo_base + i;
-                        const TI si = it == 0 ? ww_[k] : ww_[k] + tb * ss_[k];
-                        utile[i] = (rr_[k] - ta * si) * Dinv[tile0 + i];
+                        const TI wi = ld_halo<RES>(ww_ + i);
+                        const TI si = it == 0 ? wi : wi + tb * ld_halo<RES>(ss_ + i);
+                        utile[i] = (ld_halo<RES>(rr_ + i) - ta * si) * Dinv[tile0 + i];
                     }
                 }
                 if (has_hi) {
-                    const TI *rr_ = vec_hi + cur * vstride, *ww_ = vec_hi + (2 + cur) * vstride;
-                    const TI *ss_ = vec_hi + (4 + nxt) * vstride;
+                    const TI *rr_ = Rhi + cur * vs, *ww_ = Whi + cur * vs, *ss_ = Shi + nxt * vs;
                     for (int i = tid; i < m; i += nt) {
-                        const int k = hi_base + i;
-                        const TI si = it == 0 ? ww_[k] : ww_[k] + tb * ss_[k];
-                        utile[own1 - tile0 + i] = (rr_[k] - ta * si) * Dinv[own1 + i];
+                        const TI wi = ld_halo<RES>(ww_ + i);
+                        const TI si = it == 0 ? wi : wi + tb * ld_halo<RES>(ss_ + i);
+                        utile[own1 - tile0 + i] = (ld_halo<RES>(rr_ + i) - ta * si) * Dinv[own1 + i];
                     }
                 }
                 __syncthreads();
-                for (int l = tid; l < nown; l += nt) {
-                    const int node = own0 + l;
-                    const int j = (int)g.divm.div((uint32_t)node), i = node - j * m;
-                    const TI wn = stencil_apply<TI, TI>(Ai, n, m, node, i, j, utile, l + ushift);
-                    Wn[l] = wn;
-                    pacc[1] += (double)(wn * utile[l + ushift]);
+                {
+                    NodeWalk nw;
+                    nw.init(own0 + tid, nt, m);
+                    for (int l = tid; l < nown; l += nt, nw.next()) {
+                        const TI wn = stencil_apply<TI, TI>(Ai, n, m, own0 + l, nw.i, nw.j, utile, l + ushift);
+                        Wn[l] = wn;
+                        pacc[1] += wn * utile[l + ushift];
+                    }
                 }
-                cluster_sum<3, CS>(pacc, warp_buf, slots, par);
-                par ^= 1;
-                gamma_prev = gamma;
-                alpha_prev = alpha;
-                gamma = pacc[0];
-                delta = pacc[1];
-                rr = pacc[2];
                 ++it;
+                cluster_reduce<3, CS>(pacc, wsl, csl, par, [&](double(&t)[3]) { decide(t[0], t[1], t[2]); });
+                par ^= 1;
             }
             total_iters += it;
             if (nonfinite) break;
@@ -791,13 +704,396 @@ __global__ void __launch_bounds__(512, 1) slab_solve_smem_kernel(SolveArgs<TI> g
     }
 
     double qacc[1] = {0.0};
+    {
+        NodeWalk nw;
+        nw.init(own0 + tid, nt, m);
+        for (int l = tid; l < nown; l += nt, nw.next()) qacc[0] += lumped_mass(m, nw.i, nw.j, g.h2) * v[own0 + l];
+    }
+    cluster_reduce<1, CS>(qacc, wsl, csl, par, [&](double(&t)[1]) { ctl.s0 = t[0]; });
+    if (rank == 0 && tid == 0) {
+        g.q[sample] = status == S_NONFINITE ? __longlong_as_double(0x7ff8000000000000LL) : ctl.s0;
+        g.iters[sample] = (int32_t)(total_iters > 0x7fffffff ? 0x7fffffff : total_iters);
+        g.status[sample] = status;
+    }
+    // keep every CTA's shared memory alive until all remote reads are done
+    cl.sync();
+}
+
+// ---------------------------------------------------------------------------
+// Register-resident slab solver (mixed path: FP32 inner PCG).
+//
+// Same algorithm and decomposition as slab_solve_kernel, laid out for the
+// SM: thread t of a CTA owns the nodes l = t + k*nt (k < NPT) of the CTA's
+// rows and keeps their PCG vectors r, w, s, p, x (and D^-1) in registers for
+// the whole run.  The seven stencil entries of every owned node sit in
+// shared memory as two float4 (diag, E, N, NE) and (W, S, SW, D^-1); the
+// iterate u goes through a zero-padded shared tile, so the stencil apply has
+// no boundary branches (missing neighbours have zero coefficients).  The
+// first and last own row of r, w, s are exported, double-buffered, for the
+// neighbouring CTAs, which rebuild their halo rows of u from them over DSMEM.
+//
+// Shared layout (bytes), identical in every CTA of the cluster:
+//   c0, c1   nmax float4 each
+//   utile    1 + (rows_max + 2) * m + 1 floats (rows r0-1 .. r1, padded)
+//   ex       [2 parity][2 rows: first, last][3: r, w, s][m] floats
+//   ytile    (rows_max + 2) * m doubles (the block's load vector y)
+// ---------------------------------------------------------------------------
+struct RegPlan {
+    int nmax, rows;
+    int off_c1, off_u, off_ex, off_y, total;
+    int usize;
+};
+
+__host__ __device__ inline RegPlan reg_plan(int m, int cs)
+{
+    RegPlan pl;
+    pl.rows = (m + cs - 1) / cs;
+    pl.nmax = pl.rows * m;
+    pl.off_c1 = pl.nmax * 16;
+    pl.off_u = pl.off_c1 + pl.nmax * 16;
+    pl.usize = 1 + (pl.rows + 2) * m + 1;
+    pl.off_ex = pl.off_u + align16(pl.usize * 4);
+    pl.off_y = pl.off_ex + align16(2 * 2 * 3 * m * 4);
+    const int ty = (pl.rows + 2 < m ? pl.rows + 2 : m) * m;
+    pl.total = pl.off_y + align16(ty * 8);
+    return pl;
+}
+
+template <int CS, int NPT>
+__global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1) slab_solve_reg_kernel(SolveArgs<float> g)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double wsl[32][4];
+    __shared__ double csl[2][4];
+    __shared__ Ctl ctl;
+
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int sample = blockIdx.x / CS;
+    const int m = g.m, n = g.n;
+    const int r0 = (int)(((int64_t)m * rank) / CS), r1 = (int)(((int64_t)m * (rank + 1)) / CS);
+    const int lo = r0 > 0 ? r0 - 1 : 0, hi = r1 < m ? r1 + 1 : m;
+    const int own0 = r0 * m, own1 = r1 * m, tile0 = lo * m, tile1 = hi * m;
+    const int nown = own1 - own0;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const bool has_lo = rank > 0, has_hi = rank + 1 < CS;
+    const RegPlan pl = reg_plan(m, CS);
+
+    float4 *c0 = reinterpret_cast<float4 *>(smem_raw);
+    float4 *c1 = reinterpret_cast<float4 *>(smem_raw + pl.off_c1);
+    float *ut = reinterpret_cast<float *>(smem_raw + pl.off_u);
+    float *ex = reinterpret_cast<float *>(smem_raw + pl.off_ex);   // [par][row][var][m]
+    double *ytile = reinterpret_cast<double *>(smem_raw + pl.off_y);
+    const int UB = 1 + m;                 // tile index of own local index 0
+    const int Uhi = 1 + m + nown;         // tile index of the upper halo row
+    // neighbours' exports: rank-1's last row is our lower halo, rank+1's
+    // first row our upper halo
+    const float *ex_lo = has_lo ? cl.map_shared_rank(ex, rank - 1) : nullptr;
+    const float *ex_hi = has_hi ? cl.map_shared_rank(ex, rank + 1) : nullptr;
+    auto exi = [m](int par, int row, int var) { return ((par * 2 + row) * 3 + var) * m; };
+
+    const size_t so = (size_t)sample * n;
+    const size_t SN = (size_t)g.S * n;
+    const double *A64 = g.A64 + (size_t)sample * kSlots2D * n;
+    const float *Ai = g.Ai + (size_t)sample * kSlots2D * n;
+    double *v = g.v + so;
+    double *wb0 = g.w + so;
+    double *b = g.b + so;
+
+    // ---- one-time setup: stencil rows into shared memory, zero the u tile
+    float dinv[NPT];
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int l = tid + k * nt;
+        dinv[k] = 0.0f;
+        if (l < nown) {
+            const int node = own0 + l;
+            const int j = node / m, i = node - j * m;
+            c0[l] = make_float4(Ai[node], Ai[n + node], Ai[2 * n + node], Ai[3 * n + node]);
+            const float wv = i > 0 ? Ai[n + node - 1] : 0.0f;
+            const float sv = j > 0 ? Ai[2 * n + node - m] : 0.0f;
+            const float swv = (i > 0 && j > 0) ? Ai[3 * n + node - m - 1] : 0.0f;
+            dinv[k] = Ai[4 * n + node];
+            c1[l] = make_float4(wv, sv, swv, dinv[k]);
+        }
+    }
+    for (int t = tid; t < pl.usize; t += nt) ut[t] = 0.0f;
     for (int node = own0 + tid; node < own1; node += nt) {
-        const int j = (int)g.divm.div((uint32_t)node), i = node - j * m;
+        double v0, w0;
+        if (g.v0) {
+            v0 = g.v0[node];
+            w0 = g.w0 ? g.w0[node] : 0.0;
+        } else {
+            const int j = node / m, i = node - j * m;
+            const double xx = (double)i / (double)(m - 1), yy = (double)j / (double)(m - 1);
+            v0 = (xx * xx + yy * yy <= g.radius2) ? 1.0 : 0.0;
+            w0 = 0.0;
+        }
+        v[node] = v0;
+        wb0[node] = w0;
+    }
+    cl.sync();
+
+    float r[NPT], w[NPT], sv[NPT], p[NPT], x[NPT];
+    int wpar = 0, par = 0;
+    int64_t total_iters = 0;
+    int32_t status = S_CONVERGED;
+    const double dt = g.dt;
+    const int last0 = nown - m;   // local index of the first node of the last own row
+
+    for (int step = 0; step < g.nsteps; ++step) {
+        // ---- block load
+        const double *wcur = wb0 + wpar * SN;
+        double *wnext = wb0 + (wpar ^ 1) * SN;
+        for (int node = tile0 + tid; node < tile1; node += nt) {
+            const double vv = ldcg(v + node), ww = ldcg(wcur + node);
+            const double Rr = vv * (vv - g.a) * (1.0 - vv) - ww;
+            ytile[node - tile0] = vv + dt * Rr;
+        }
+        __syncthreads();
+        {
+            double acc[2] = {0.0, 0.0};
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                const int l = tid + k * nt;
+                if (l < nown) {
+                    const int node = own0 + l;
+                    const int j = node / m, i = node - j * m;
+                    const double bb = mass_apply(m, i, j, g.h2, ytile, node - tile0);
+                    b[node] = bb;
+                    const double vv = v[node], ww = wcur[node];
+                    wnext[node] = ww + dt * g.eps * (vv - g.gam * ww);
+                    const double rr = bb - stencil_apply_global(A64, n, m, node, i, j, v);
+                    r[k] = (float)rr;
+                    acc[0] += bb * bb;
+                    acc[1] += rr * rr;
+                    if (l < m) ex[exi(0, 0, 0) + l] = r[k];
+                    if (l >= last0) ex[exi(0, 1, 0) + l - last0] = r[k];
+                }
+            }
+            cluster_reduce<2, CS>(acc, wsl, csl, par, [&](double(&t)[2]) {
+                ctl.s0 = t[0];
+                ctl.s1 = t[1];
+            });
+            par ^= 1;
+        }
+        wpar ^= 1;
+        const double bnorm2 = ctl.s0;
+        double rnorm2 = ctl.s1;
+        if (!(isfinite(bnorm2) && isfinite(rnorm2))) {
+            status = S_NONFINITE;
+            break;
+        }
+        const double tol_out2 = g.rtol_out * g.rtol_out * bnorm2;
+
+        bool nonfinite = false, solved = false;
+        for (int sweep = 0; sweep < g.max_sweeps; ++sweep) {
+            if (sweep > 0) {
+                // FP64 residual b - A v of the refined iterate, exported as r_0
+                double racc[1] = {0.0};
+#pragma unroll
+                for (int k = 0; k < NPT; ++k) {
+                    const int l = tid + k * nt;
+                    if (l < nown) {
+                        const int node = own0 + l;
+                        const int j = node / m, i = node - j * m;
+                        const double rr = b[node] - stencil_apply_global(A64, n, m, node, i, j, v);
+                        r[k] = (float)rr;
+                        racc[0] += rr * rr;
+                        if (l < m) ex[exi(0, 0, 0) + l] = r[k];
+                        if (l >= last0) ex[exi(0, 1, 0) + l - last0] = r[k];
+                    }
+                }
+                cluster_reduce<1, CS>(racc, wsl, csl, par, [&](double(&t)[1]) { ctl.s1 = t[0]; });
+                par ^= 1;
+                rnorm2 = ctl.s1;
+                if (!isfinite(rnorm2)) { nonfinite = true; break; }
+            }
+            if (rnorm2 <= tol_out2) { solved = true; break; }
+            // The inner problem is solved for r / ||r|| (and the correction
+            // scaled back): FP32 squares of late-sweep residuals would
+            // otherwise underflow.  The neighbours apply the same factor to
+            // the r_0 rows they import.
+            const double rnorm = sqrt(rnorm2);
+            const float rscale = (float)(1.0 / rnorm);
+            const double tol_in2 = g.rtol_in * g.rtol_in;
+
+            // ---- init: u0 = D^-1 r0 (own + halo), w0 = A u0, x = 0
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                const int l = tid + k * nt;
+                r[k] *= rscale;
+                if (l < nown) ut[UB + l] = r[k] * dinv[k];
+            }
+            if (has_lo)
+                for (int i = tid; i < m; i += nt)
+                    ut[1 + i] = (ex_lo[exi(0, 1, 0) + i] * rscale) * Ai[4 * n + tile0 + i];
+            if (has_hi)
+                for (int i = tid; i < m; i += nt)
+                    ut[Uhi + i] = (ex_hi[exi(0, 0, 0) + i] * rscale) * Ai[4 * n + own1 + i];
+            __syncthreads();
+            // thread 0's recurrence state: eta_i = (p_i, A p_i) = delta_i - beta_i^2 eta_{i-1}
+            double gamma_prev = 1.0, eta_prev = 1.0;
+            int it = 0;
+            auto decide = [&](double gamma, double delta, double rr) {
+                double alpha = 0.0, beta = 0.0;
+                int code;
+                if (!isfinite(rr) || !isfinite(gamma) || !isfinite(delta)) code = 3;
+                else if (rr <= tol_in2) code = 1;
+                else if (it >= g.max_iter) code = 2;
+                else {
+                    code = 0;
+                    double eta = delta;
+                    if (it > 0) {
+                        beta = gamma * rcp_newton(gamma_prev);
+                        eta = delta - beta * beta * eta_prev;
+                    }
+                    alpha = gamma * rcp_newton(eta);
+                    gamma_prev = gamma;
+                    eta_prev = eta;
+                }
+                ctl.alpha = alpha;
+                ctl.beta = beta;
+                ctl.code = code;
+            };
+            {
+                float iacc[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+                for (int k = 0; k < NPT; ++k) {
+                    const int l = tid + k * nt;
+                    x[k] = 0.0f;
+                    p[k] = 0.0f;
+                    sv[k] = 0.0f;
+                    if (l < nown) {
+                        const int t = UB + l;
+                        const float4 a = c0[l], bq = c1[l];
+                        const float u0 = ut[t];
+                        float wn = a.x * u0;
+                        wn = fmaf(a.y, ut[t + 1], wn);
+                        wn = fmaf(bq.x, ut[t - 1], wn);
+                        wn = fmaf(a.z, ut[t + m], wn);
+                        wn = fmaf(bq.y, ut[t - m], wn);
+                        wn = fmaf(a.w, ut[t + m + 1], wn);
+                        wn = fmaf(bq.z, ut[t - m - 1], wn);
+                        w[k] = wn;
+                        iacc[0] = fmaf(r[k], u0, iacc[0]);
+                        iacc[1] = fmaf(wn, u0, iacc[1]);
+                        iacc[2] = fmaf(r[k], r[k], iacc[2]);
+                        if (l < m) ex[exi(0, 0, 1) + l] = wn;
+                        if (l >= last0) ex[exi(0, 1, 1) + l - last0] = wn;
+                    }
+                }
+                cluster_reduce<3, CS>(iacc, wsl, csl, par, [&](double(&t)[3]) { decide(t[0], t[1], t[2]); });
+                par ^= 1;
+            }
+            while (true) {
+                const int code = ctl.code;
+                if (code != 0) {
+                    if (code == 3) nonfinite = true;
+                    else if (code == 2) status = status == S_CONVERGED ? S_MAXITER : status;
+                    break;
+                }
+                const float ta = (float)ctl.alpha, tb = (float)ctl.beta;
+                const int cur = it & 1, nxt = cur ^ 1;
+                float pacc[3] = {0.0f, 0.0f, 0.0f};
+                float un[NPT];
+                // own nodes: s_i, r_{i+1}, u_{i+1}, p_i, x_{i+1}
+#pragma unroll
+                for (int k = 0; k < NPT; ++k) {
+                    const int l = tid + k * nt;
+                    un[k] = 0.0f;
+                    if (l < nown) {
+                        const float si = it == 0 ? w[k] : fmaf(tb, sv[k], w[k]);
+                        const float rn = fmaf(-ta, si, r[k]);
+                        const float uk = rn * dinv[k];
+                        ut[UB + l] = uk;
+                        const float ui = r[k] * dinv[k];
+                        p[k] = it == 0 ? ui : fmaf(tb, p[k], ui);
+                        x[k] = fmaf(ta, p[k], x[k]);
+                        sv[k] = si;
+                        r[k] = rn;
+                        un[k] = uk;
+                        pacc[0] = fmaf(rn, uk, pacc[0]);
+                        pacc[2] = fmaf(rn, rn, pacc[2]);
+                        if (l < m) {
+                            ex[exi(nxt, 0, 0) + l] = rn;
+                            ex[exi(nxt, 0, 2) + l] = si;
+                        }
+                        if (l >= last0) {
+                            ex[exi(nxt, 1, 0) + l - last0] = rn;
+                            ex[exi(nxt, 1, 2) + l - last0] = si;
+                        }
+                    }
+                }
+                // halo rows from the neighbours' exports of r_i, w_i, s_{i-1}
+                if (has_lo) {
+                    const float *er = ex_lo + exi(cur, 1, 0), *ew = ex_lo + exi(cur, 1, 1),
+                                *es = ex_lo + exi(cur, 1, 2);
+                    for (int i = tid; i < m; i += nt) {
+                        // at it = 0 the exported r_0 rows are still unscaled
+                        const float ri = it == 0 ? er[i] * rscale : er[i];
+                        const float si = it == 0 ? ew[i] : fmaf(tb, es[i], ew[i]);
+                        ut[1 + i] = fmaf(-ta, si, ri) * Ai[4 * n + tile0 + i];
+                    }
+                }
+                if (has_hi) {
+                    const float *er = ex_hi + exi(cur, 0, 0), *ew = ex_hi + exi(cur, 0, 1),
+                                *es = ex_hi + exi(cur, 0, 2);
+                    for (int i = tid; i < m; i += nt) {
+                        const float ri = it == 0 ? er[i] * rscale : er[i];
+                        const float si = it == 0 ? ew[i] : fmaf(tb, es[i], ew[i]);
+                        ut[Uhi + i] = fmaf(-ta, si, ri) * Ai[4 * n + own1 + i];
+                    }
+                }
+                __syncthreads();
+                // w_{i+1} = A u_{i+1}
+#pragma unroll
+                for (int k = 0; k < NPT; ++k) {
+                    const int l = tid + k * nt;
+                    if (l < nown) {
+                        const int t = UB + l;
+                        const float4 a = c0[l], bq = c1[l];
+                        float wn = a.x * un[k];
+                        wn = fmaf(a.y, ut[t + 1], wn);
+                        wn = fmaf(bq.x, ut[t - 1], wn);
+                        wn = fmaf(a.z, ut[t + m], wn);
+                        wn = fmaf(bq.y, ut[t - m], wn);
+                        wn = fmaf(a.w, ut[t + m + 1], wn);
+                        wn = fmaf(bq.z, ut[t - m - 1], wn);
+                        w[k] = wn;
+                        pacc[1] = fmaf(wn, un[k], pacc[1]);
+                        if (l < m) ex[exi(nxt, 0, 1) + l] = wn;
+                        if (l >= last0) ex[exi(nxt, 1, 1) + l - last0] = wn;
+                    }
+                }
+                ++it;
+                cluster_reduce<3, CS>(pacc, wsl, csl, par, [&](double(&t)[3]) { decide(t[0], t[1], t[2]); });
+                par ^= 1;
+            }
+            total_iters += it;
+            if (nonfinite) break;
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                const int l = tid + k * nt;
+                if (l < nown) v[own0 + l] = fma((double)x[k], rnorm, v[own0 + l]);
+            }
+            cl.sync();
+        }
+        if (nonfinite) {
+            status = S_NONFINITE;
+            break;
+        }
+        if (!solved && status == S_CONVERGED) status = S_MAXITER;
+    }
+
+    double qacc[1] = {0.0};
+    for (int node = own0 + tid; node < own1; node += nt) {
+        const int j = node / m, i = node - j * m;
         qacc[0] += lumped_mass(m, i, j, g.h2) * v[node];
     }
-    cluster_sum<1, CS>(qacc, warp_buf, slots, par);
+    cluster_reduce<1, CS>(qacc, wsl, csl, par, [&](double(&t)[1]) { ctl.s0 = t[0]; });
     if (rank == 0 && tid == 0) {
-        g.q[sample] = status == S_NONFINITE ? __longlong_as_double(0x7ff8000000000000LL) : qacc[0];
+        g.q[sample] = status == S_NONFINITE ? __longlong_as_double(0x7ff8000000000000LL) : ctl.s0;
         g.iters[sample] = (int32_t)(total_iters > 0x7fffffff ? 0x7fffffff : total_iters);
         g.status[sample] = status;
     }

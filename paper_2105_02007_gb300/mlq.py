@@ -259,8 +259,9 @@ class Context:
         return c.value
 
     def level_launch(self, level: int, with_resident: bool = False):
-        """(cluster, threads[, resident]) chosen for a level."""
+        """(cluster, threads[, resident]) chosen for a level; resident is 2 for
+        the register-resident kernel, 1 for shared-memory vectors, 0 global."""
         c, t, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(_lib.mlq_level_launch(self._h, level, ctypes.byref(c), ctypes.byref(t), ctypes.byref(r)),
                "mlq_level_launch")
-        return (c.value, t.value, bool(r.value)) if with_resident else (c.value, t.value)
+        return (c.value, t.value, r.value) if with_resident else (c.value, t.value)

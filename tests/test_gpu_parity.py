@@ -93,7 +93,8 @@ def test_launch_shapes_random_state(mlq, prec, m, cluster, threads, storage):
         ctx.add_level(0, m, 0.1, 15)
         ctx.set_kl(0, phi, tm)
         ctx.set_initial_state(0, v0, w0)
-        assert ctx.level_launch(0, True) == (cluster, threads, storage == 1)
+        c_, t_, res_ = ctx.level_launch(0, True)
+        assert (c_, t_) == (cluster, threads) and (res_ > 0) == (storage == 1)
         r = ctx.solve(0, xi)
     assert np.all(r["status"] == 0)
     assert rel(r["q_fine"], q_ref) < TOL[prec]
