@@ -188,6 +188,16 @@ typedef struct {
 int mlq_set_profiling(mlq_ctx *ctx, int enable);
 int mlq_member_profile(mlq_ctx *ctx, int max_members, int *count, mlq_member_stats *out);
 
+/* Autotuner (mixed path).  Times every register-resident launch shape of
+ * `level` that fits the device (cluster size x nodes per thread) on a probe
+ * run of probe_steps time blocks with the given S samples xi (host or
+ * device), after one warm-up pass, and keeps the fastest for later solves of
+ * this level (until the level is redefined or an explicit cluster/threads
+ * option is set).  Outputs (may be NULL): chosen cluster size, threads per
+ * CTA, and the probe time in milliseconds.  MLQ_EUNSUPPORTED in FP64 mode. */
+int mlq_autotune(mlq_ctx *ctx, int level, int64_t S, const double *xi, int probe_steps, int *cluster_out,
+                 int *threads_out, double *ms_out);
+
 /* Count of kernel launches the context has issued since creation. */
 int mlq_launch_count(mlq_ctx *ctx, int64_t *count);
 

@@ -17,7 +17,11 @@ CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libmlq.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["mlq_api.cu", "mlq_kl.cpp"]
+# (source, extra flags, object name): the slab-solver kernels are compiled
+# once per cluster size / inner precision so that the objects build in parallel
+SOURCES = ([("mlq_api.cu", [], "mlq_api"), ("mlq_kl.cpp", [], "mlq_kl")]
+           + [("mlq_reg_inst.cu", [f"-DMLQ_CS={cs}"], f"mlq_reg_cs{cs}") for cs in (1, 2, 4, 8, 16)]
+           + [("mlq_slab_inst.cu", [f"-DMLQ_F64={f}"], f"mlq_slab_f{64 if f else 32}") for f in (0, 1)])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -41,16 +45,17 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 
-    def compile_one(src: str) -> str:
-        obj = os.path.join(LIBDIR, src + ".o")
-        cmd = [nvcc] + common + ["-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(item) -> str:
+        src, flags, name = item
+        obj = os.path.join(LIBDIR, name + ".o")
+        cmd = [nvcc] + common + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cu"):
             cmd[1:1] = ARCH + ["-lineinfo", "-Xptxas", "-v" if verbose else "-O3"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
         if verbose:
-            sys.stderr.write(r.stderr)
+            sys.stderr.write(f"== {name}\n" + r.stderr)
         return obj
 
     with ThreadPoolExecutor(len(SOURCES)) as ex:

@@ -6,7 +6,8 @@
 // CUDA streams on which the members of a multilevel estimate run
 // concurrently.  All compute happens in the kernels of mlq_kernels.cuh.
 #include "mlq.h"
-#include "mlq_kernels.cuh"
+#include "mlq_aux.cuh"
+#include "mlq_launch.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -34,6 +35,7 @@ struct Level {
     double *d_v0 = nullptr, *d_w0 = nullptr;
     double radius = 0.1;
     mlq::FastDiv divm{};
+    int tuned_cs = 0, tuned_npt = 0, tuned_threads = 0;  // set by mlq_autotune (mixed path)
 };
 
 struct Member {
@@ -109,8 +111,8 @@ bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// Launch shape of a level: cluster size, threads per CTA, and whether the
-// sample's PCG vectors fit in the cluster's shared memory (preferred).
+// Launch shape of a level: cluster size, threads per CTA, and where the
+// sample's PCG vectors live.
 struct Shape {
     int cs, threads;
     bool resident;
@@ -119,18 +121,87 @@ struct Shape {
 };
 
 // nodes-per-thread variants compiled for the register-resident kernel
-constexpr int kNpt[] = {4, 8, 12};
+constexpr int kNpt[] = {4, 8, 12, 17};
+inline int npt_max_threads(int npt) { return npt >= 12 ? (npt >= 16 ? 512 : 384) : 512; }
 
-Shape choose_launch(const mlq_ctx *ctx, const Level &L)
+int max_active_clusters_reg(mlq_ctx *ctx, int cs, int npt, int threads, size_t smem);
+
+// Register-kernel candidates of a level: for each cluster size whose shared
+// layout fits, the smallest nodes-per-thread variant that covers a CTA's rows.
+std::vector<Shape> reg_candidates(const mlq_ctx *ctx, const Level &L)
+{
+    std::vector<Shape> out;
+    const int limit = ctx->smem_optin - 2048;
+    for (int c = 1; c <= ctx->max_cluster; c *= 2) {
+        if (c > L.m) break;
+        const mlq::RegPlan rp = mlq::reg_plan(L.m, c);
+        if (rp.total > limit) continue;
+        for (int npt : kNpt) {
+            int th = ((rp.nmax + npt - 1) / npt + 31) / 32 * 32;
+            if (th < 32) th = 32;
+            if (th > npt_max_threads(npt)) continue;
+            out.push_back(Shape{c, th, true, (size_t)rp.total, npt});
+            break;
+        }
+    }
+    return out;
+}
+
+Shape choose_launch(mlq_ctx *ctx, const Level &L, int64_t S = 0)
 {
     const int ti = ctx->opt.precision == MLQ_MIXED ? 4 : 8;
     const int limit = ctx->smem_optin - 2048;  // room for the static reduction buffers
-    Shape sh{0, 0, false, 0};
+    const bool allow = ctx->opt.storage != 2;
+    // mixed path: the register-resident kernel when a shape fits
+    if (ti == 4 && allow) {
+        if (L.tuned_cs > 0 && ctx->opt.cluster <= 0 && ctx->opt.threads <= 0) {
+            const mlq::RegPlan rp = mlq::reg_plan(L.m, L.tuned_cs);
+            return Shape{L.tuned_cs, L.tuned_threads, true, (size_t)rp.total, L.tuned_npt};
+        }
+        std::vector<Shape> cand = reg_candidates(ctx, L);
+        if (ctx->opt.cluster > 0 || ctx->opt.threads > 0) {
+            // honour explicit overrides when a register shape matches them
+            for (const Shape &c : cand) {
+                if (ctx->opt.cluster > 0 && c.cs != ctx->opt.cluster) continue;
+                Shape sh = c;
+                if (ctx->opt.threads > 0) {
+                    const mlq::RegPlan rp = mlq::reg_plan(L.m, c.cs);
+                    bool ok = false;
+                    for (int npt : kNpt)
+                        if ((int64_t)ctx->opt.threads * npt >= rp.nmax && ctx->opt.threads <= npt_max_threads(npt)) {
+                            sh.npt = npt;
+                            sh.threads = ctx->opt.threads;
+                            ok = true;
+                            break;
+                        }
+                    if (!ok) continue;
+                }
+                return sh;
+            }
+        } else if (!cand.empty()) {
+            // cost model: waves of co-resident clusters x per-iteration time,
+            // t_iter ~ 0.8 us + 0.3 us log2(cluster) + 0.3 ns per node of a CTA
+            double best = 1e300;
+            Shape pick = cand[0];
+            for (const Shape &c : cand) {
+                const int act = max_active_clusters_reg(ctx, c.cs, c.npt, c.threads, c.smem);
+                if (act <= 0) continue;
+                const double waves = S > 0 ? (double)((S + act - 1) / act) : 1.0;
+                const int nodes = mlq::reg_plan(L.m, c.cs).nmax;
+                const double t = waves * (0.8 + 0.3 * std::log2((double)c.cs) + 3e-4 * nodes);
+                if (t < best) {
+                    best = t;
+                    pick = c;
+                }
+            }
+            return pick;
+        }
+    }
+    Shape sh{0, 0, false, 0, 0};
     auto fits = [&](int c) {
         if (c > L.m) return false;
         return mlq::smem_plan(L.m, c, ti, true).total <= limit;
     };
-    const bool allow = ctx->opt.storage != 2;
     if (ctx->opt.cluster > 0) {
         sh.cs = ctx->opt.cluster;
         sh.resident = allow && fits(sh.cs);
@@ -155,105 +226,32 @@ Shape choose_launch(const mlq_ctx *ctx, const Level &L)
     }
     sh.threads = t;
     sh.smem = (size_t)mlq::smem_plan(L.m, sh.cs, ti, sh.resident).total;
-    sh.npt = 0;
-    // mixed path: registers for the vectors when the stencil rows fit
-    if (sh.resident && ti == 4 && ctx->opt.storage != 2) {
-        const mlq::RegPlan rp = mlq::reg_plan(L.m, sh.cs);
-        if (rp.total <= limit) {
-            const int nmax = rp.nmax;
-            int best = 0, bt = 0;
-            for (int npt : kNpt) {
-                int th = ctx->opt.threads > 0 ? ctx->opt.threads : ((nmax + npt - 1) / npt + 31) / 32 * 32;
-                if (th < 32) th = 32;
-                if (th > (npt >= 12 ? 384 : 512) || (int64_t)th * npt < nmax) continue;
-                best = npt;
-                bt = th;
-                if (ctx->opt.threads <= 0 && npt >= 12) break;
-                if (ctx->opt.threads > 0) break;
-            }
-            if (best > 0) {
-                sh.npt = best;
-                sh.threads = bt;
-                sh.smem = (size_t)rp.total;
-            }
-        }
-    }
     return sh;
-}
-
-template <typename TI, int CS>
-cudaError_t launch_slab(const mlq::SolveArgs<TI> &a, int nclusters, int threads, size_t smem, bool resident,
-                        cudaStream_t st)
-{
-    auto kern = resident ? mlq::slab_solve_kernel<TI, CS, true> : mlq::slab_solve_kernel<TI, CS, false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    if (CS > 8) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
-    }
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3((unsigned)(nclusters * CS));
-    cfg.blockDim = dim3((unsigned)threads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CS;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, a);
-}
-
-template <int CS, int NPT>
-cudaError_t launch_reg(const mlq::SolveArgs<float> &a, int nclusters, int threads, size_t smem, cudaStream_t st)
-{
-    auto kern = mlq::slab_solve_reg_kernel<CS, NPT>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    if (CS > 8) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
-    }
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3((unsigned)(nclusters * CS));
-    cfg.blockDim = dim3((unsigned)threads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CS;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, a);
-}
-
-template <int CS>
-cudaError_t launch_reg_npt(int npt, const mlq::SolveArgs<float> &a, int ncl, int threads, size_t smem,
-                           cudaStream_t st)
-{
-    switch (npt) {
-    case 4: return launch_reg<CS, 4>(a, ncl, threads, smem, st);
-    case 8: return launch_reg<CS, 8>(a, ncl, threads, smem, st);
-    case 12: return launch_reg<CS, 12>(a, ncl, threads, smem, st);
-    default: return cudaErrorInvalidValue;
-    }
 }
 
 cudaError_t launch_reg_any(int cs, int npt, const mlq::SolveArgs<float> &a, int ncl, int threads, size_t smem,
                            cudaStream_t st)
 {
     switch (cs) {
-    case 1: return launch_reg_npt<1>(npt, a, ncl, threads, smem, st);
-    case 2: return launch_reg_npt<2>(npt, a, ncl, threads, smem, st);
-    case 4: return launch_reg_npt<4>(npt, a, ncl, threads, smem, st);
-    case 8: return launch_reg_npt<8>(npt, a, ncl, threads, smem, st);
-    case 16: return launch_reg_npt<16>(npt, a, ncl, threads, smem, st);
+    case 1: return mlq::launch_reg_cs1(npt, a, ncl, threads, smem, st);
+    case 2: return mlq::launch_reg_cs2(npt, a, ncl, threads, smem, st);
+    case 4: return mlq::launch_reg_cs4(npt, a, ncl, threads, smem, st);
+    case 8: return mlq::launch_reg_cs8(npt, a, ncl, threads, smem, st);
+    case 16: return mlq::launch_reg_cs16(npt, a, ncl, threads, smem, st);
     default: return cudaErrorInvalidValue;
+    }
+}
+
+int max_active_clusters_reg(mlq_ctx *ctx, int cs, int npt, int threads, size_t smem)
+{
+    (void)ctx;
+    switch (cs) {
+    case 1: return mlq::active_reg_cs1(npt, threads, smem);
+    case 2: return mlq::active_reg_cs2(npt, threads, smem);
+    case 4: return mlq::active_reg_cs4(npt, threads, smem);
+    case 8: return mlq::active_reg_cs8(npt, threads, smem);
+    case 16: return mlq::active_reg_cs16(npt, threads, smem);
+    default: return 0;
     }
 }
 
@@ -261,14 +259,8 @@ template <typename TI>
 cudaError_t launch_slab_cs(int cs, const mlq::SolveArgs<TI> &a, int nclusters, int threads, size_t smem,
                            bool resident, cudaStream_t st)
 {
-    switch (cs) {
-    case 1: return launch_slab<TI, 1>(a, nclusters, threads, smem, resident, st);
-    case 2: return launch_slab<TI, 2>(a, nclusters, threads, smem, resident, st);
-    case 4: return launch_slab<TI, 4>(a, nclusters, threads, smem, resident, st);
-    case 8: return launch_slab<TI, 8>(a, nclusters, threads, smem, resident, st);
-    case 16: return launch_slab<TI, 16>(a, nclusters, threads, smem, resident, st);
-    default: return cudaErrorInvalidValue;
-    }
+    if constexpr (sizeof(TI) == 4) return mlq::launch_slab_f32(cs, resident, a, nclusters, threads, smem, st);
+    else return mlq::launch_slab_f64(cs, resident, a, nclusters, threads, smem, st);
 }
 
 // Bytes of workspace for one member (level, S samples).
@@ -388,7 +380,7 @@ int launch_member_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream_t
     a.q = mb.q;
     a.iters = mb.iters;
     a.status = mb.status;
-    const Shape sh = choose_launch(ctx, L);
+    const Shape sh = choose_launch(ctx, L, mb.S);
     if (ctx->opt.storage == 1 && !sh.resident) return MLQ_EUNSUPPORTED;
     const bool timed = ctx->profile && slot >= 0 && slot < kStreams;
     if (timed) MLQ_CUDA(ctx, cudaEventRecord(ctx->ev_t0[slot], st));
@@ -409,7 +401,7 @@ int launch_member(mlq_ctx *ctx, const Member &mb, cudaStream_t st, int slot, int
 {
     const Level &L = ctx->levels[mb.level];
     if (ctx->profile && slot >= 0 && slot < kStreams) {
-        const Shape sh = choose_launch(ctx, L);
+        const Shape sh = choose_launch(ctx, L, mb.S);
         ctx->prof_level[slot] = mb.level;
         ctx->prof_coarse[slot] = coarse;
         ctx->prof_cs[slot] = sh.cs;
@@ -515,27 +507,8 @@ int mlq_create(mlq_ctx **out, int device, void *cuda_stream, const mlq_options *
     int nonportable = 0;
     cudaDeviceGetAttribute(&nonportable, cudaDevAttrClusterLaunch, device);
     cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-    ctx->max_cluster = 8;
-    {
-        cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3(16);
-        cfg.blockDim = dim3(512);
-        cfg.dynamicSmemBytes = 48 * 1024;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = 16;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        auto kern = mlq::slab_solve_kernel<float, 16, true>;
-        int ncl = 0;
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 48 * 1024) == cudaSuccess &&
-            cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg) == cudaSuccess && ncl > 0)
-            ctx->max_cluster = 16;
-        cudaGetLastError();
-    }
+    ctx->max_cluster = mlq::active_reg_cs16(8, 512, 48 * 1024) > 0 ? 16 : 8;
+    cudaGetLastError();
     (void)nonportable;
     if (o.cluster > ctx->max_cluster) return fail(MLQ_EUNSUPPORTED);
     *out = ctx;
@@ -864,6 +837,78 @@ int mlq_member_profile(mlq_ctx *ctx, int max_members, int *count, mlq_member_sta
         for (int32_t x : it) tot += x;
         o.cg_iterations = tot;
     }
+    return MLQ_OK;
+}
+
+int mlq_autotune(mlq_ctx *ctx, int level, int64_t S, const double *xi, int probe_steps, int *cluster_out,
+                 int *threads_out, double *ms_out)
+{
+    if (!ctx || !xi || S < 1 || probe_steps < 1) return MLQ_EINVAL;
+    if (check_level(ctx, level) != MLQ_OK) return MLQ_EINVAL;
+    if (ctx->opt.precision != MLQ_MIXED || ctx->opt.storage == 2) return MLQ_EUNSUPPORTED;
+    Level &L = ctx->levels[level];
+    std::vector<Shape> cand = reg_candidates(ctx, L);
+    if (cand.empty()) return MLQ_EUNSUPPORTED;
+    // also try the next nodes-per-thread variant of each cluster size
+    const size_t nbase = cand.size();
+    for (size_t k = 0; k < nbase; ++k) {
+        const Shape c = cand[k];
+        for (int npt : kNpt) {
+            if (npt <= c.npt) continue;
+            const mlq::RegPlan rp = mlq::reg_plan(L.m, c.cs);
+            int th = ((rp.nmax + npt - 1) / npt + 31) / 32 * 32;
+            if (th < 32) th = 32;
+            if (th > npt_max_threads(npt)) continue;
+            cand.push_back(Shape{c.cs, th, true, c.smem, npt});
+            break;
+        }
+    }
+    const int saved_steps = L.nsteps;
+    const int saved_cs = L.tuned_cs, saved_npt = L.tuned_npt, saved_th = L.tuned_threads;
+    const mlq_options saved_opt = ctx->opt;
+    ctx->opt.cluster = 0;
+    ctx->opt.threads = 0;
+    L.nsteps = probe_steps;
+    cudaEvent_t e0, e1;
+    MLQ_CUDA(ctx, cudaEventCreate(&e0));
+    MLQ_CUDA(ctx, cudaEventCreate(&e1));
+    double best = 1e300;
+    Shape pick = cand[0];
+    int st = MLQ_OK;
+    for (int pass = 0; pass < 2 && st == MLQ_OK; ++pass) {  // pass 0 warms up
+        for (const Shape &c : cand) {
+            L.tuned_cs = c.cs;
+            L.tuned_npt = c.npt;
+            L.tuned_threads = c.threads;
+            if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) { st = MLQ_ECUDA; break; }
+            st = mlq_solve(ctx, level, S, xi, 0, nullptr, nullptr, nullptr, nullptr, nullptr);
+            if (st != MLQ_OK) break;
+            cudaEventRecord(e1, ctx->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (pass == 1 && ms < best) {
+                best = ms;
+                pick = c;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    L.nsteps = saved_steps;
+    ctx->opt = saved_opt;
+    if (st != MLQ_OK) {
+        L.tuned_cs = saved_cs;
+        L.tuned_npt = saved_npt;
+        L.tuned_threads = saved_th;
+        return st;
+    }
+    L.tuned_cs = pick.cs;
+    L.tuned_npt = pick.npt;
+    L.tuned_threads = pick.threads;
+    if (cluster_out) *cluster_out = pick.cs;
+    if (threads_out) *threads_out = pick.threads;
+    if (ms_out) *ms_out = best;
     return MLQ_OK;
 }
 

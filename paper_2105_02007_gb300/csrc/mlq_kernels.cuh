@@ -1,17 +1,10 @@
-// mlq_kernels.cuh -- device code of libmlq (sm_103a).
+// mlq_kernels.cuh -- device code of the slab solvers of libmlq (sm_103a).
 //
-// Hot path of the per-sample forward solve of the stochastic monodomain
-// equation, batched over samples:
-//   K1 kl_synthesis_kernel    theta_e = theta_mean_e + sum_k Phi[e,k] xi_k
-//                             (eq. KLlowrank), epilogue (cos 2t, sin 2t)
-//   K2 stencil_setup_kernel   A = M + dt K(theta) as a stored 7-point stencil
-//                             (Sec. 3.1 mass/stiffness, eq. AdmV conductivity)
-//   K3-K6 slab_solve_kernel   all time blocks of one sample in one cluster of
-//                             CTAs: FHN reaction and consistent-mass load
-//                             (eq. mono_disc), Jacobi-PCG per block (multiple
-//                             time blocks, Sec. 3.3), FP64 refinement
-//   K7 level_sums_kernel      Y = Q_l - Q_{l-1} and per-level FP64 sums
-//                             (eq. StandardML)
+// The per-sample forward solve of the stochastic monodomain equation: all
+// time blocks of one sample run inside one cluster of CTAs -- FHN reaction
+// and consistent-mass load (eq. mono_disc), Jacobi-PCG per block (multiple
+// time blocks, Sec. 3.3) with FP64 iterative refinement in the mixed path,
+// and the QoI m^T v.  The set-up and reduction kernels are in mlq_aux.cuh.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -44,120 +37,6 @@ struct FastDiv {
         return (uint32_t)(((uint64_t)n * mul) >> 40);
     }
 };
-
-// ---------------------------------------------------------------------------
-// K1: KL synthesis.  One thread per (element, sample); Phi rows are shared
-// by all samples (L1/L2 resident), xi rows by all elements.
-// out[(s*ne + e)*2 + {0,1}] = (cos 2 theta, sin 2 theta).
-// ---------------------------------------------------------------------------
-__global__ void kl_synthesis_kernel(const double *__restrict__ phi, const double *__restrict__ theta_mean,
-                                    const double *__restrict__ xi, int K, int ne, int S,
-                                    double *__restrict__ out)
-{
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = blockIdx.y;
-    if (e >= ne || s >= S) return;
-    const double *pr = phi + (size_t)e * K;
-    const double *xr = xi + (size_t)s * K;
-    double t = theta_mean ? theta_mean[e] : 0.0;
-    for (int k = 0; k < K; ++k) t = fma(pr[k], xr[k], t);
-    double sn, cs;
-    sincos(2.0 * t, &sn, &cs);
-    out[((size_t)s * ne + e) * 2 + 0] = cs;
-    out[((size_t)s * ne + e) * 2 + 1] = sn;
-}
-
-// ---------------------------------------------------------------------------
-// K2: stencil of A = M + dt K(theta) on the structured triangulation.
-//
-// With D = sbar I + (ds/2) [[c2, s2], [s2, -c2]], sbar = (s_l+s_t)/2,
-// ds = s_l - s_t, (c2, s2) = (cos 2t, sin 2t):
-//   d11 = sbar + ds/2 c2,  d22 = sbar - ds/2 c2,  d12 = ds/2 s2.
-// P1 element stiffness (|e| = h^2/2, h cancels in 2D):
-//   lower (a,b,c) = (i,j)(i+1,j)(i+1,j+1), gradients (-1,0),(1,-1),(0,1) / h
-//   upper (a,c,d) = (i,j)(i+1,j+1)(i,j+1), gradients (0,-1),(1,0),(-1,1) / h
-//   K_xy = (1/2) g_x^T D g_y.
-// Consistent mass per element: h^2/12 on the diagonal, h^2/24 off it.
-// ---------------------------------------------------------------------------
-struct DTensor {
-    double d11, d12, d22;
-};
-
-__device__ __forceinline__ DTensor dtensor(const double *cs, double sbar, double hds)
-{
-    DTensor D;
-    D.d11 = sbar + hds * cs[0];
-    D.d22 = sbar - hds * cs[0];
-    D.d12 = hds * cs[1];
-    return D;
-}
-
-__global__ void stencil_setup_kernel(const double *__restrict__ cs2, int m, double h, double dt, double s_l,
-                                     double s_t, int S, double *__restrict__ A64, float *__restrict__ A32)
-{
-    const int n = m * m;
-    const int node = blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = blockIdx.y;
-    if (node >= n || s >= S) return;
-    const int i = node % m, j = node / m;
-    const int ne = 2 * (m - 1) * (m - 1);
-    const double *c = cs2 + (size_t)s * ne * 2;
-    const double sbar = 0.5 * (s_l + s_t), hds = 0.5 * (s_l - s_t);
-    const double mdiag = h * h / 12.0, moff = h * h / 24.0;
-    const int mc = m - 1; // cells per side
-    double diag = 0.0, east = 0.0, north = 0.0, ne_ = 0.0;
-    auto lower = [&](int ci, int cj) { return 2 * (ci + mc * cj); };
-    auto upper = [&](int ci, int cj) { return 2 * (ci + mc * cj) + 1; };
-    const bool cell_ij = (i < mc && j < mc);         // square (i, j)
-    const bool cell_im = (i >= 1 && j < mc);         // square (i-1, j)
-    const bool cell_mm = (i >= 1 && j >= 1);         // square (i-1, j-1)
-    const bool cell_jm = (i < mc && j >= 1);         // square (i, j-1)
-    if (cell_ij) {
-        // lower(i,j): P = a; E = b; NE = c
-        DTensor D = dtensor(c + 2 * lower(i, j), sbar, hds);
-        diag += 0.5 * D.d11 * dt + mdiag;
-        east += -0.5 * (D.d11 - D.d12) * dt + moff;
-        ne_ += -0.5 * D.d12 * dt + moff;
-        // upper(i,j): P = a; NE = c; N = d
-        D = dtensor(c + 2 * upper(i, j), sbar, hds);
-        diag += 0.5 * D.d22 * dt + mdiag;
-        ne_ += -0.5 * D.d12 * dt + moff;
-        north += 0.5 * (D.d12 - D.d22) * dt + moff;
-    }
-    if (cell_im) {
-        // lower(i-1,j): a = (i-1,j), P = b, N = c
-        DTensor D = dtensor(c + 2 * lower(i - 1, j), sbar, hds);
-        diag += 0.5 * (D.d11 - 2.0 * D.d12 + D.d22) * dt + mdiag;
-        north += 0.5 * (D.d12 - D.d22) * dt + moff;
-    }
-    if (cell_mm) {
-        // lower(i-1,j-1): P = c; upper(i-1,j-1): P = c
-        DTensor D = dtensor(c + 2 * lower(i - 1, j - 1), sbar, hds);
-        diag += 0.5 * D.d22 * dt + mdiag;
-        D = dtensor(c + 2 * upper(i - 1, j - 1), sbar, hds);
-        diag += 0.5 * D.d11 * dt + mdiag;
-    }
-    if (cell_jm) {
-        // upper(i,j-1): a = (i,j-1), E = c, P = d
-        DTensor D = dtensor(c + 2 * upper(i, j - 1), sbar, hds);
-        diag += 0.5 * (D.d11 - 2.0 * D.d12 + D.d22) * dt + mdiag;
-        east += -0.5 * (D.d11 - D.d12) * dt + moff;
-    }
-    double *a = A64 + (size_t)s * kSlots2D * n;
-    a[node] = diag;
-    a[n + node] = east;
-    a[2 * n + node] = north;
-    a[3 * n + node] = ne_;
-    a[4 * n + node] = 1.0 / diag;
-    if (A32) {
-        float *f = A32 + (size_t)s * kSlots2D * n;
-        f[node] = (float)diag;
-        f[n + node] = (float)east;
-        f[2 * n + node] = (float)north;
-        f[3 * n + node] = (float)ne_;
-        f[4 * n + node] = 1.0f / (float)diag;
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Slab solver.
@@ -724,24 +603,28 @@ __global__ void __launch_bounds__(512, 1) slab_solve_kernel(SolveArgs<TI> g)
 //
 // Same algorithm and decomposition as slab_solve_kernel, laid out for the
 // SM: thread t of a CTA owns the nodes l = t + k*nt (k < NPT) of the CTA's
-// rows and keeps their PCG vectors r, w, s, p, x (and D^-1) in registers for
-// the whole run.  The seven stencil entries of every owned node sit in
-// shared memory as two float4 (diag, E, N, NE) and (W, S, SW, D^-1); the
-// iterate u goes through a zero-padded shared tile, so the stencil apply has
-// no boundary branches (missing neighbours have zero coefficients).  The
-// first and last own row of r, w, s are exported, double-buffered, for the
-// neighbouring CTAs, which rebuild their halo rows of u from them over DSMEM.
+// rows and keeps their PCG vectors r, w, s, p, x in registers for the whole
+// run.  Shared memory holds, per node, the stencil row (diag, E, N, NE) as a
+// float4 and D^-1; the W, S, SW entries of a row are the E, N, NE entries of
+// the neighbouring nodes (A is symmetric), so the float4 array also covers
+// the row below the CTA's band.  The iterate u goes through a zero-padded
+// shared tile, so the stencil apply has no boundary branches (missing
+// neighbours have zero coefficients).  The first and last own row of r, w, s
+// are exported, double-buffered, for the neighbouring CTAs, which rebuild
+// their halo rows of u from them over DSMEM.  The block load vector
+// b = M (v + dt R(v, w)) is formed from the FP64 state in global memory,
+// evaluating y = v + dt R at each stencil point.
 //
 // Shared layout (bytes), identical in every CTA of the cluster:
-//   c0, c1   nmax float4 each
-//   utile    1 + (rows_max + 2) * m + 1 floats (rows r0-1 .. r1, padded)
-//   ex       [2 parity][2 rows: first, last][3: r, w, s][m] floats
-//   ytile    (rows_max + 2) * m doubles (the block's load vector y)
+//   c0     1 + (rows_max + 1) * m  float4   (pad, row r0-1, own rows)
+//   dinv   rows_max * m            float
+//   utile  1 + (rows_max + 2) * m + 1 float  (pad, rows r0-1 .. r1, pad)
+//   ex     [2 parity][2 rows: first, last][3: r, w, s][m] floats
 // ---------------------------------------------------------------------------
 struct RegPlan {
     int nmax, rows;
-    int off_c1, off_u, off_ex, off_y, total;
-    int usize;
+    int off_dinv, off_u, off_ex, total;
+    int csize, usize;
 };
 
 __host__ __device__ inline RegPlan reg_plan(int m, int cs)
@@ -749,18 +632,44 @@ __host__ __device__ inline RegPlan reg_plan(int m, int cs)
     RegPlan pl;
     pl.rows = (m + cs - 1) / cs;
     pl.nmax = pl.rows * m;
-    pl.off_c1 = pl.nmax * 16;
-    pl.off_u = pl.off_c1 + pl.nmax * 16;
+    pl.csize = 1 + (pl.rows + 1) * m;
+    pl.off_dinv = align16(pl.csize * 16);
+    pl.off_u = pl.off_dinv + align16(pl.nmax * 4);
     pl.usize = 1 + (pl.rows + 2) * m + 1;
     pl.off_ex = pl.off_u + align16(pl.usize * 4);
-    pl.off_y = pl.off_ex + align16(2 * 2 * 3 * m * 4);
-    const int ty = (pl.rows + 2 < m ? pl.rows + 2 : m) * m;
-    pl.total = pl.off_y + align16(ty * 8);
+    pl.total = pl.off_ex + align16(2 * 2 * 3 * m * 4);
     return pl;
 }
 
+// y = v + dt R(v, w) at node q (FP64 state in global memory, through L2)
+__device__ __forceinline__ double load_y(const double *v, const double *w, int q, double dt, double a)
+{
+    const double vv = __ldcg(v + q), ww = __ldcg(w + q);
+    return vv + dt * (vv * (vv - a) * (1.0 - vv) - ww);
+}
+
+// b_P = (M y)_P with y evaluated at the stencil points (see mass_apply)
+__device__ __forceinline__ double mass_apply_y(int m, int i, int j, double h2, const double *v, const double *w,
+                                               int node, double dt, double a)
+{
+    const int mc = m - 1;
+    const bool cij = (i < mc && j < mc), cim = (i >= 1 && j < mc), cmm = (i >= 1 && j >= 1),
+               cjm = (i < mc && j >= 1);
+    const int ninc = 2 * cij + cim + 2 * cmm + cjm;
+    double acc = (double)ninc * (h2 / 12.0) * load_y(v, w, node, dt, a);
+    const double e = h2 / 24.0;
+    if (i + 1 < m) acc += e * (double)(cij + cjm) * load_y(v, w, node + 1, dt, a);
+    if (i > 0) acc += e * (double)(cim + cmm) * load_y(v, w, node - 1, dt, a);
+    if (j + 1 < m) acc += e * (double)(cij + cim) * load_y(v, w, node + m, dt, a);
+    if (j > 0) acc += e * (double)(cjm + cmm) * load_y(v, w, node - m, dt, a);
+    if (i + 1 < m && j + 1 < m) acc += e * (double)(2 * cij) * load_y(v, w, node + m + 1, dt, a);
+    if (i > 0 && j > 0) acc += e * (double)(2 * cmm) * load_y(v, w, node - m - 1, dt, a);
+    return acc;
+}
+
 template <int CS, int NPT>
-__global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1) slab_solve_reg_kernel(SolveArgs<float> g)
+__global__ void __launch_bounds__(NPT >= 12 ? (NPT >= 16 ? 512 : 384) : 512, 1)
+    slab_solve_reg_kernel(SolveArgs<float> g)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double wsl[32][4];
@@ -772,22 +681,18 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1) slab_solve_reg_kerne
     const int sample = blockIdx.x / CS;
     const int m = g.m, n = g.n;
     const int r0 = (int)(((int64_t)m * rank) / CS), r1 = (int)(((int64_t)m * (rank + 1)) / CS);
-    const int lo = r0 > 0 ? r0 - 1 : 0, hi = r1 < m ? r1 + 1 : m;
-    const int own0 = r0 * m, own1 = r1 * m, tile0 = lo * m, tile1 = hi * m;
+    const int own0 = r0 * m, own1 = r1 * m;
     const int nown = own1 - own0;
     const int tid = threadIdx.x, nt = blockDim.x;
     const bool has_lo = rank > 0, has_hi = rank + 1 < CS;
     const RegPlan pl = reg_plan(m, CS);
 
-    float4 *c0 = reinterpret_cast<float4 *>(smem_raw);
-    float4 *c1 = reinterpret_cast<float4 *>(smem_raw + pl.off_c1);
-    float *ut = reinterpret_cast<float *>(smem_raw + pl.off_u);
-    float *ex = reinterpret_cast<float *>(smem_raw + pl.off_ex);   // [par][row][var][m]
-    double *ytile = reinterpret_cast<double *>(smem_raw + pl.off_y);
-    const int UB = 1 + m;                 // tile index of own local index 0
-    const int Uhi = 1 + m + nown;         // tile index of the upper halo row
-    // neighbours' exports: rank-1's last row is our lower halo, rank+1's
-    // first row our upper halo
+    float4 *c0 = reinterpret_cast<float4 *>(smem_raw);                 // index 1 + m + l for own l
+    float *dv = reinterpret_cast<float *>(smem_raw + pl.off_dinv);      // own l
+    float *ut = reinterpret_cast<float *>(smem_raw + pl.off_u);         // index 1 + m + l for own l
+    float *ex = reinterpret_cast<float *>(smem_raw + pl.off_ex);        // [par][row][var][m]
+    const int UB = 1 + m;                 // c0 / utile index of own local index 0
+    const int Uhi = 1 + m + nown;         // utile index of the upper halo row
     const float *ex_lo = has_lo ? cl.map_shared_rank(ex, rank - 1) : nullptr;
     const float *ex_hi = has_hi ? cl.map_shared_rank(ex, rank + 1) : nullptr;
     auto exi = [m](int par, int row, int var) { return ((par * 2 + row) * 3 + var) * m; };
@@ -800,23 +705,15 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1) slab_solve_reg_kerne
     double *wb0 = g.w + so;
     double *b = g.b + so;
 
-    // ---- one-time setup: stencil rows into shared memory, zero the u tile
-    float dinv[NPT];
-#pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-        const int l = tid + k * nt;
-        dinv[k] = 0.0f;
-        if (l < nown) {
-            const int node = own0 + l;
-            const int j = node / m, i = node - j * m;
-            c0[l] = make_float4(Ai[node], Ai[n + node], Ai[2 * n + node], Ai[3 * n + node]);
-            const float wv = i > 0 ? Ai[n + node - 1] : 0.0f;
-            const float sv = j > 0 ? Ai[2 * n + node - m] : 0.0f;
-            const float swv = (i > 0 && j > 0) ? Ai[3 * n + node - m - 1] : 0.0f;
-            dinv[k] = Ai[4 * n + node];
-            c1[l] = make_float4(wv, sv, swv, dinv[k]);
-        }
+    // ---- one-time setup: stencil rows (own rows and the row below) into
+    //      shared memory, D^-1, zeroed u tile
+    for (int t = tid; t < pl.csize; t += nt) {
+        const int node = own0 - m + (t - 1);   // t = 0 is the pad
+        float4 c = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (t > 0 && node >= 0 && node < own1) c = make_float4(Ai[node], Ai[n + node], Ai[2 * n + node], Ai[3 * n + node]);
+        c0[t] = c;
     }
+    for (int l = tid; l < nown; l += nt) dv[l] = Ai[4 * n + own0 + l];
     for (int t = tid; t < pl.usize; t += nt) ut[t] = 0.0f;
     for (int node = own0 + tid; node < own1; node += nt) {
         double v0, w0;
@@ -842,34 +739,28 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1) slab_solve_reg_kerne
     const int last0 = nown - m;   // local index of the first node of the last own row
 
     for (int step = 0; step < g.nsteps; ++step) {
-        // ---- block load
+        // ---- block load: b = M (v + dt R), w update, r0 = b - A v
         const double *wcur = wb0 + wpar * SN;
         double *wnext = wb0 + (wpar ^ 1) * SN;
-        for (int node = tile0 + tid; node < tile1; node += nt) {
-            const double vv = ldcg(v + node), ww = ldcg(wcur + node);
-            const double Rr = vv * (vv - g.a) * (1.0 - vv) - ww;
-            ytile[node - tile0] = vv + dt * Rr;
-        }
-        __syncthreads();
         {
+            // (the FP32 residual is staged in the u tile, which is free here;
+            //  the init below moves it into registers)
             double acc[2] = {0.0, 0.0};
-#pragma unroll
-            for (int k = 0; k < NPT; ++k) {
-                const int l = tid + k * nt;
-                if (l < nown) {
-                    const int node = own0 + l;
-                    const int j = node / m, i = node - j * m;
-                    const double bb = mass_apply(m, i, j, g.h2, ytile, node - tile0);
-                    b[node] = bb;
-                    const double vv = v[node], ww = wcur[node];
-                    wnext[node] = ww + dt * g.eps * (vv - g.gam * ww);
-                    const double rr = bb - stencil_apply_global(A64, n, m, node, i, j, v);
-                    r[k] = (float)rr;
-                    acc[0] += bb * bb;
-                    acc[1] += rr * rr;
-                    if (l < m) ex[exi(0, 0, 0) + l] = r[k];
-                    if (l >= last0) ex[exi(0, 1, 0) + l - last0] = r[k];
-                }
+#pragma unroll 1
+            for (int l = tid; l < nown; l += nt) {
+                const int node = own0 + l;
+                const int j = node / m, i = node - j * m;
+                const double bb = mass_apply_y(m, i, j, g.h2, v, wcur, node, dt, g.a);
+                b[node] = bb;
+                const double vv = v[node], ww = wcur[node];
+                wnext[node] = ww + dt * g.eps * (vv - g.gam * ww);
+                const double rr = bb - stencil_apply_global(A64, n, m, node, i, j, v);
+                const float rf = (float)rr;
+                ut[UB + l] = rf;
+                acc[0] += bb * bb;
+                acc[1] += rr * rr;
+                if (l < m) ex[exi(0, 0, 0) + l] = rf;
+                if (l >= last0) ex[exi(0, 1, 0) + l - last0] = rf;
             }
             cluster_reduce<2, CS>(acc, wsl, csl, par, [&](double(&t)[2]) {
                 ctl.s0 = t[0];
@@ -891,18 +782,16 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1) slab_solve_reg_kerne
             if (sweep > 0) {
                 // FP64 residual b - A v of the refined iterate, exported as r_0
                 double racc[1] = {0.0};
-#pragma unroll
-                for (int k = 0; k < NPT; ++k) {
-                    const int l = tid + k * nt;
-                    if (l < nown) {
-                        const int node = own0 + l;
-                        const int j = node / m, i = node - j * m;
-                        const double rr = b[node] - stencil_apply_global(A64, n, m, node, i, j, v);
-                        r[k] = (float)rr;
-                        racc[0] += rr * rr;
-                        if (l < m) ex[exi(0, 0, 0) + l] = r[k];
-                        if (l >= last0) ex[exi(0, 1, 0) + l - last0] = r[k];
-                    }
+#pragma unroll 1
+                for (int l = tid; l < nown; l += nt) {
+                    const int node = own0 + l;
+                    const int j = node / m, i = node - j * m;
+                    const double rr = b[node] - stencil_apply_global(A64, n, m, node, i, j, v);
+                    const float rf = (float)rr;
+                    ut[UB + l] = rf;
+                    racc[0] += rr * rr;
+                    if (l < m) ex[exi(0, 0, 0) + l] = rf;
+                    if (l >= last0) ex[exi(0, 1, 0) + l - last0] = rf;
                 }
                 cluster_reduce<1, CS>(racc, wsl, csl, par, [&](double(&t)[1]) { ctl.s1 = t[0]; });
                 par ^= 1;
@@ -922,12 +811,14 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1) slab_solve_reg_kerne
 #pragma unroll
             for (int k = 0; k < NPT; ++k) {
                 const int l = tid + k * nt;
-                r[k] *= rscale;
-                if (l < nown) ut[UB + l] = r[k] * dinv[k];
+                if (l < nown) {
+                    r[k] = ut[UB + l] * rscale;
+                    ut[UB + l] = r[k] * dv[l];
+                }
             }
             if (has_lo)
                 for (int i = tid; i < m; i += nt)
-                    ut[1 + i] = (ex_lo[exi(0, 1, 0) + i] * rscale) * Ai[4 * n + tile0 + i];
+                    ut[1 + i] = (ex_lo[exi(0, 1, 0) + i] * rscale) * Ai[4 * n + own0 - m + i];
             if (has_hi)
                 for (int i = tid; i < m; i += nt)
                     ut[Uhi + i] = (ex_hi[exi(0, 0, 0) + i] * rscale) * Ai[4 * n + own1 + i];
@@ -956,6 +847,19 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1) slab_solve_reg_kerne
                 ctl.beta = beta;
                 ctl.code = code;
             };
+            // w = A u for own local index l (u read from the tile)
+            auto apply = [&](int l) {
+                const int t = UB + l;
+                const float4 a = c0[t];
+                float wn = a.x * ut[t];
+                wn = fmaf(a.y, ut[t + 1], wn);
+                wn = fmaf(c0[t - 1].y, ut[t - 1], wn);
+                wn = fmaf(a.z, ut[t + m], wn);
+                wn = fmaf(c0[t - m].z, ut[t - m], wn);
+                wn = fmaf(a.w, ut[t + m + 1], wn);
+                wn = fmaf(c0[t - m - 1].w, ut[t - m - 1], wn);
+                return wn;
+            };
             {
                 float iacc[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
@@ -965,16 +869,8 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1) slab_solve_reg_kerne
                     p[k] = 0.0f;
                     sv[k] = 0.0f;
                     if (l < nown) {
-                        const int t = UB + l;
-                        const float4 a = c0[l], bq = c1[l];
-                        const float u0 = ut[t];
-                        float wn = a.x * u0;
-                        wn = fmaf(a.y, ut[t + 1], wn);
-                        wn = fmaf(bq.x, ut[t - 1], wn);
-                        wn = fmaf(a.z, ut[t + m], wn);
-                        wn = fmaf(bq.y, ut[t - m], wn);
-                        wn = fmaf(a.w, ut[t + m + 1], wn);
-                        wn = fmaf(bq.z, ut[t - m - 1], wn);
+                        const float u0 = ut[UB + l];
+                        const float wn = apply(l);
                         w[k] = wn;
                         iacc[0] = fmaf(r[k], u0, iacc[0]);
                         iacc[1] = fmaf(wn, u0, iacc[1]);
@@ -996,23 +892,21 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1) slab_solve_reg_kerne
                 const float ta = (float)ctl.alpha, tb = (float)ctl.beta;
                 const int cur = it & 1, nxt = cur ^ 1;
                 float pacc[3] = {0.0f, 0.0f, 0.0f};
-                float un[NPT];
                 // own nodes: s_i, r_{i+1}, u_{i+1}, p_i, x_{i+1}
 #pragma unroll
                 for (int k = 0; k < NPT; ++k) {
                     const int l = tid + k * nt;
-                    un[k] = 0.0f;
                     if (l < nown) {
+                        const float di = dv[l];
                         const float si = it == 0 ? w[k] : fmaf(tb, sv[k], w[k]);
                         const float rn = fmaf(-ta, si, r[k]);
-                        const float uk = rn * dinv[k];
+                        const float uk = rn * di;
                         ut[UB + l] = uk;
-                        const float ui = r[k] * dinv[k];
+                        const float ui = r[k] * di;
                         p[k] = it == 0 ? ui : fmaf(tb, p[k], ui);
                         x[k] = fmaf(ta, p[k], x[k]);
                         sv[k] = si;
                         r[k] = rn;
-                        un[k] = uk;
                         pacc[0] = fmaf(rn, uk, pacc[0]);
                         pacc[2] = fmaf(rn, rn, pacc[2]);
                         if (l < m) {
@@ -1033,7 +927,7 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1) slab_solve_reg_kerne
                         // at it = 0 the exported r_0 rows are still unscaled
                         const float ri = it == 0 ? er[i] * rscale : er[i];
                         const float si = it == 0 ? ew[i] : fmaf(tb, es[i], ew[i]);
-                        ut[1 + i] = fmaf(-ta, si, ri) * Ai[4 * n + tile0 + i];
+                        ut[1 + i] = fmaf(-ta, si, ri) * Ai[4 * n + own0 - m + i];
                     }
                 }
                 if (has_hi) {
@@ -1051,17 +945,9 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1) slab_solve_reg_kerne
                 for (int k = 0; k < NPT; ++k) {
                     const int l = tid + k * nt;
                     if (l < nown) {
-                        const int t = UB + l;
-                        const float4 a = c0[l], bq = c1[l];
-                        float wn = a.x * un[k];
-                        wn = fmaf(a.y, ut[t + 1], wn);
-                        wn = fmaf(bq.x, ut[t - 1], wn);
-                        wn = fmaf(a.z, ut[t + m], wn);
-                        wn = fmaf(bq.y, ut[t - m], wn);
-                        wn = fmaf(a.w, ut[t + m + 1], wn);
-                        wn = fmaf(bq.z, ut[t - m - 1], wn);
+                        const float wn = apply(l);
                         w[k] = wn;
-                        pacc[1] = fmaf(wn, un[k], pacc[1]);
+                        pacc[1] = fmaf(wn, ut[UB + l], pacc[1]);
                         if (l < m) ex[exi(nxt, 0, 1) + l] = wn;
                         if (l >= last0) ex[exi(nxt, 1, 1) + l - last0] = wn;
                     }
@@ -1098,59 +984,6 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1) slab_solve_reg_kerne
         g.status[sample] = status;
     }
     cl.sync();
-}
-
-// ---------------------------------------------------------------------------
-// K7: Y = Q_l - Q_{l-1} and per-level sums in FP64.  One block, two passes
-// (mean, then centred squares); the tree is fixed by blockDim, so the sums do
-// not depend on how samples were batched.
-// sums[0] = sum Y, sums[1] = sum (Y - mean Y)^2.
-// ---------------------------------------------------------------------------
-__global__ void level_sums_kernel(const double *__restrict__ qf, const double *__restrict__ qc, int64_t S,
-                                  double *__restrict__ y, double *__restrict__ sums)
-{
-    __shared__ double buf[1024];
-    __shared__ double mean_sh;
-    double s1 = 0.0;
-    for (int64_t k = threadIdx.x; k < S; k += blockDim.x) {
-        const double yy = qc ? qf[k] - qc[k] : qf[k];
-        if (y) y[k] = yy;
-        s1 += yy;
-    }
-    buf[threadIdx.x] = s1;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) buf[threadIdx.x] += buf[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        sums[0] = buf[0];
-        mean_sh = buf[0] / (double)S;
-    }
-    __syncthreads();
-    const double mu = mean_sh;
-    double s2 = 0.0;
-    for (int64_t k = threadIdx.x; k < S; k += blockDim.x) {
-        const double d = (qc ? qf[k] - qc[k] : qf[k]) - mu;
-        s2 += d * d;
-    }
-    __syncthreads();
-    buf[threadIdx.x] = s2;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) buf[threadIdx.x] += buf[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) sums[1] = buf[0];
-}
-
-// worst-of status merge of the fine and coarse members
-__global__ void merge_status_kernel(const int32_t *__restrict__ a, const int32_t *__restrict__ c, int64_t S,
-                                    int32_t *__restrict__ out)
-{
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= S) return;
-    out[k] = c ? (a[k] > c[k] ? a[k] : c[k]) : a[k];
 }
 
 }  // namespace mlq

@@ -1,0 +1,88 @@
+// mlq_launch.cuh -- launch entry points of the slab-solver kernels.
+//
+// The kernel templates are instantiated in separate translation units
+// (mlq_reg_inst.cu once per cluster size, mlq_slab_inst.cu once per inner
+// precision) so that the library builds in parallel; the host runtime calls
+// them through these functions.
+#pragma once
+
+#include <cstddef>
+#include <cuda_runtime.h>
+
+#include "mlq_kernels.cuh"
+
+namespace mlq {
+
+#define MLQ_DECLARE_REG(CS)                                                                                   \
+    cudaError_t launch_reg_cs##CS(int npt, const SolveArgs<float> &a, int nclusters, int threads, size_t smem, \
+                                  cudaStream_t st);                                                           \
+    int active_reg_cs##CS(int npt, int threads, size_t smem);
+MLQ_DECLARE_REG(1)
+MLQ_DECLARE_REG(2)
+MLQ_DECLARE_REG(4)
+MLQ_DECLARE_REG(8)
+MLQ_DECLARE_REG(16)
+#undef MLQ_DECLARE_REG
+
+cudaError_t launch_slab_f32(int cs, bool resident, const SolveArgs<float> &a, int nclusters, int threads,
+                            size_t smem, cudaStream_t st);
+cudaError_t launch_slab_f64(int cs, bool resident, const SolveArgs<double> &a, int nclusters, int threads,
+                            size_t smem, cudaStream_t st);
+
+// cluster launch of `kern` with CS CTAs per cluster
+template <int CS, typename K, typename A>
+cudaError_t cluster_launch(K kern, const A &args, int nclusters, int threads, size_t smem, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (CS > 8) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(nclusters * CS));
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args);
+}
+
+// clusters of `kern` that can be resident at once (0 if none / on error)
+template <int CS, typename K>
+int cluster_occupancy(K kern, int threads, size_t smem)
+{
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (CS > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)CS);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nc;
+}
+
+}  // namespace mlq

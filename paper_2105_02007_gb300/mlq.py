@@ -62,6 +62,8 @@ _lib.mlq_workspace_bytes.argtypes = [_vp, ctypes.c_int, _i64, ctypes.c_int, ctyp
 _lib.mlq_launch_count.argtypes = [_vp, ctypes.POINTER(_i64)]
 _lib.mlq_level_launch.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                   ctypes.POINTER(ctypes.c_int)]
+_lib.mlq_autotune.argtypes = [_vp, ctypes.c_int, _i64, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
 _lib.mlq_set_profiling.argtypes = [_vp, ctypes.c_int]
 _lib.mlq_member_profile.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(MemberStats)]
 _lib.mlq_strerror.restype = ctypes.c_char_p
@@ -73,7 +75,7 @@ EXPORTED = ["mlq_default_options", "mlq_default_model", "mlq_create", "mlq_destr
             "mlq_set_model", "mlq_add_level", "mlq_set_initial_state", "mlq_set_initial_disk", "mlq_set_kl",
             "mlq_build_kl", "mlq_centroid_table", "mlq_solve", "mlq_estimate", "mlq_workspace_bytes",
             "mlq_launch_count", "mlq_level_launch", "mlq_strerror", "mlq_last_cuda_error", "mlq_set_profiling",
-            "mlq_member_profile"]
+            "mlq_member_profile", "mlq_autotune"]
 
 
 class MLQError(RuntimeError):
@@ -241,6 +243,15 @@ class Context:
         _check(_lib.mlq_workspace_bytes(self._h, level, S, int(with_coarse), ctypes.byref(b)),
                "mlq_workspace_bytes", self._h)
         return b.value
+
+    def autotune(self, level: int, xi, probe_steps: int = 2):
+        """Time the launch shapes of a level on a short probe run and keep
+        the fastest.  Returns (cluster, threads, probe ms)."""
+        keep, px = _ptr(xi, np.float64)
+        c, t, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(_lib.mlq_autotune(self._h, level, int(xi.shape[0]), px, probe_steps, ctypes.byref(c),
+                                 ctypes.byref(t), ctypes.byref(ms)), "mlq_autotune", self._h)
+        return c.value, t.value, ms.value
 
     def set_profiling(self, enable: bool = True):
         _check(_lib.mlq_set_profiling(self._h, int(enable)), "mlq_set_profiling", self._h)

@@ -314,3 +314,21 @@ def test_mlmc_estimate_matches_oracle(mlq, prec):
     for l in range(3):
         assert np.max(np.abs(ys[l] - yref[l])) < tol * np.max(np.abs(yref[0]))
     assert abs(rmse - rmse_ref) < (1e-2 if prec else 1e-6) * rmse_ref
+
+
+@pytest.mark.parametrize("m", [17, 65])
+def test_autotune_keeps_parity(mlq, m):
+    mesh = O.mesh2d(m)
+    modes, _ = O.kl_build(mesh, 0.09, 0.04, 6)
+    phi = O.centroid_table(mesh, modes, mesh)
+    xi = inputs.gaussian_xi(5, 0, 0, 6, 6)
+    q_ref = O.solve_batch(mesh, phi, xi, 0.05, 6)[0]
+    with mlq.Context(0, 1) as ctx:
+        ctx.add_level(0, m, 0.05, 6)
+        ctx.set_kl(0, phi)
+        cs, th, ms = ctx.autotune(0, xi, probe_steps=2)
+        assert cs >= 1 and th >= 32 and ms > 0
+        assert ctx.level_launch(0) == (cs, th)
+        r = ctx.solve(0, xi)
+    assert np.all(r["status"] == 0)
+    assert rel(r["q_fine"], q_ref) < TOL[1]
