@@ -43,7 +43,8 @@ typedef enum {
     MLQ_ECUDA = -3,        /* a CUDA runtime call failed; see mlq_last_cuda_error */
     MLQ_ENOTREADY = -4,    /* serving: the request has not finished */
     MLQ_ETIMEOUT = -5,     /* a bounded wait ran out */
-    MLQ_EUNSUPPORTED = -6  /* valid request this build does not implement */
+    MLQ_EUNSUPPORTED = -6, /* valid request this build does not implement */
+    MLQ_ETOOBIG = -7       /* request larger than mlq_solve_noalloc's fixed scratch */
 } mlq_status;
 
 typedef enum { MLQ_FP64 = 0, MLQ_MIXED = 1 } mlq_precision;
@@ -197,6 +198,48 @@ int mlq_member_profile(mlq_ctx *ctx, int max_members, int *count, mlq_member_sta
  * CTA, and the probe time in milliseconds.  MLQ_EUNSUPPORTED in FP64 mode. */
 int mlq_autotune(mlq_ctx *ctx, int level, int64_t S, const double *xi, int probe_steps, int *cluster_out,
                  int *threads_out, double *ms_out);
+
+/* Solve without allocating anything.
+ *
+ * For callers that cannot call cudaMalloc at the time they need a solve:
+ * code running while a stream is being captured into a CUDA graph in the
+ * global capture mode (where the runtime rejects allocation calls), and
+ * processes whose device memory is owned by another allocator with a fixed
+ * budget (a serving engine that reserved HBM up front, a framework's caching
+ * allocator), where a library allocation would fail or break the budget.
+ * No context is needed: the call creates no stream, event or buffer, and
+ * calls no cudaMalloc/cudaFree or other allocating routine.
+ *
+ * It runs the same kernels as mlq_solve in the mixed path (KL synthesis,
+ * stencil set-up, register-resident slab solver) on one level without a
+ * coarse member, with all working memory in one fixed, statically allocated
+ * device array of MLQ_NOALLOC_SCRATCH_BYTES that every GPU which loads the
+ * library holds until the process exits.  Requests whose working set does
+ * not fit return MLQ_ETOOBIG; the working set is about
+ *   92 * S * m^2 + 32 * S * (m-1)^2 bytes  (m x m nodes, S samples),
+ * e.g. 33 x 33 nodes with up to ~250 samples, or 257 x 257 nodes with 4.
+ *
+ * Arguments: structured 2D level of m x m nodes, time step dt, nsteps time
+ * blocks; model and opt may be NULL (defaults; opt->precision must be
+ * MLQ_MIXED); K modes; phi (n_elem x K), theta_mean (n_elem or NULL), xi
+ * (S x K), v0 / w0 (m^2 or NULL: the disc start of radius 0.1) -- all DEVICE
+ * pointers owned by the caller; outputs q (S, FP64), status and iters (S,
+ * int32, may be NULL), DEVICE pointers.  Host pointers return MLQ_EINVAL.
+ * The work is queued on cuda_stream (NULL = legacy default stream) and the
+ * call returns without waiting; synchronize the stream before reading q.
+ *
+ * The first call on a device looks up the device address of the scratch
+ * array (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture begins.  Every call uses the same array and
+ * leaves its contents behind; the kernels initialise everything they read,
+ * so results do not depend on earlier calls.  Calls whose work overlaps on
+ * the GPU (other streams, other host threads) race on the array: order them
+ * on one stream.  (The paper has no counterpart: this is an integration
+ * variant of mlq_solve.) */
+#define MLQ_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int mlq_solve_noalloc(int m, double dt, int32_t nsteps, const mlq_model *model, const mlq_options *opt, int K,
+                      const double *phi, const double *theta_mean, const double *xi, int64_t S, const double *v0,
+                      const double *w0, double *q, int32_t *status, int32_t *iters, void *cuda_stream);
 
 /* Count of kernel launches the context has issued since creation. */
 int mlq_launch_count(mlq_ctx *ctx, int64_t *count);

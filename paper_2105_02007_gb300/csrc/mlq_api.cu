@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <vector>
 
 namespace {
@@ -912,6 +913,153 @@ int mlq_autotune(mlq_ctx *ctx, int level, int64_t S, const double *xi, int probe
     return MLQ_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Solve without allocating: scratch in a fixed device array (see mlq.h).
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[MLQ_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device (host code may
+// not use the symbol itself as a pointer).  Looked up once per device.
+int noalloc_scratch(int dev, void **out)
+{
+    if (dev < 0 || dev >= kMaxDevices) return MLQ_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return MLQ_ECUDA;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return MLQ_OK;
+}
+
+bool on_device(const void *p)
+{
+    if (!p) return true;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mlq_solve_noalloc(int m, double dt, int32_t nsteps, const mlq_model *model, const mlq_options *opt, int K,
+                      const double *phi, const double *theta_mean, const double *xi, int64_t S, const double *v0,
+                      const double *w0, double *q, int32_t *status, int32_t *iters, void *cuda_stream)
+{
+    if (m < 2 || m > 8193 || !(dt > 0.0) || nsteps < 0 || K < 1 || K > kMaxK || S < 0 || S > 65535) return MLQ_EINVAL;
+    if (!phi || !xi || !q) return MLQ_EINVAL;
+    if (!on_device(phi) || !on_device(theta_mean) || !on_device(xi) || !on_device(v0) || !on_device(w0) ||
+        !on_device(q) || !on_device(status) || !on_device(iters))
+        return MLQ_EINVAL;
+    mlq_model md;
+    if (model) md = *model;
+    else mlq_default_model(&md);
+    mlq_options o;
+    if (opt) o = *opt;
+    else mlq_default_options(&o, MLQ_MIXED);
+    if (o.precision != MLQ_MIXED || validate_options(&o) != MLQ_OK) return MLQ_EINVAL;
+    if (S == 0) return MLQ_OK;
+    const int64_t n = (int64_t)m * m, ne = 2 * (int64_t)(m - 1) * (m - 1);
+    // scratch layout: cs2 | A64 | A32 | v | w (2) | b | q | iters | status
+    const size_t sn = (size_t)S * n;
+    size_t off = 0;
+    auto put = [&](size_t bytes) {
+        const size_t at = off;
+        off += align_up(bytes, 256);
+        return at;
+    };
+    const size_t o_cs2 = put((size_t)S * ne * 16), o_a64 = put(sn * mlq::kSlots2D * 8),
+                 o_a32 = put(sn * mlq::kSlots2D * 4), o_v = put(sn * 8), o_w = put(2 * sn * 8), o_b = put(sn * 8),
+                 o_it = put((size_t)S * 4), o_st = put((size_t)S * 4);
+    if (off > MLQ_NOALLOC_SCRATCH_BYTES) return MLQ_ETOOBIG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return MLQ_ECUDA;
+    void *base = nullptr;
+    int st = noalloc_scratch(dev, &base);
+    if (st != MLQ_OK) return st;
+    char *sc = (char *)base;
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+
+    // launch shape: the smallest cluster whose register-kernel layout fits
+    int smem_optin = 0;
+    if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return MLQ_ECUDA;
+    int cs = 0, npt = 0, threads = 0;
+    for (int c = 1; c <= 8 && c <= m && cs == 0; c *= 2) {
+        const mlq::RegPlan rp = mlq::reg_plan(m, c);
+        if (rp.total > smem_optin - 2048) continue;
+        for (int k : kNpt) {
+            int th = ((rp.nmax + k - 1) / k + 31) / 32 * 32;
+            if (th < 32) th = 32;
+            if (th > npt_max_threads(k)) continue;
+            cs = c;
+            npt = k;
+            threads = th;
+            break;
+        }
+    }
+    if (cs == 0) return MLQ_ETOOBIG;
+    const mlq::RegPlan rp = mlq::reg_plan(m, cs);
+
+    double *cs2 = (double *)(sc + o_cs2);
+    double *A64 = (double *)(sc + o_a64);
+    float *A32 = (float *)(sc + o_a32);
+    mlq::kl_synthesis_kernel<<<dim3((unsigned)((ne + 255) / 256), (unsigned)S), 256, 0, stream>>>(
+        phi, theta_mean, xi, K, (int)ne, (int)S, cs2);
+    if (cudaGetLastError() != cudaSuccess) return MLQ_ECUDA;
+    const double h = 1.0 / (double)(m - 1);
+    mlq::stencil_setup_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)S), 256, 0, stream>>>(
+        cs2, m, h, dt, md.s_l, md.s_t, (int)S, A64, A32);
+    if (cudaGetLastError() != cudaSuccess) return MLQ_ECUDA;
+    mlq::SolveArgs<float> a{};
+    a.m = m;
+    a.n = (int)n;
+    a.h2 = h * h;
+    a.dt = dt;
+    a.nsteps = nsteps;
+    a.a = md.a;
+    a.eps = md.eps;
+    a.gam = md.gamma;
+    a.rtol_out = o.rtol;
+    a.rtol_in = o.rtol_inner;
+    a.max_iter = o.max_iter;
+    a.max_sweeps = o.max_sweeps;
+    a.A64 = A64;
+    a.Ai = A32;
+    a.v = (double *)(sc + o_v);
+    a.w = (double *)(sc + o_w);
+    a.b = (double *)(sc + o_b);
+    a.v0 = v0;
+    a.w0 = v0 ? w0 : nullptr;
+    a.radius2 = 0.01;
+    a.S = (int)S;
+    a.q = q;
+    a.iters = iters ? iters : (int32_t *)(sc + o_it);
+    a.status = status ? status : (int32_t *)(sc + o_st);
+    if (launch_reg_any(cs, npt, a, (int)S, threads, (size_t)rp.total, stream) != cudaSuccess) {
+        cudaGetLastError();
+        return MLQ_ECUDA;
+    }
+    return MLQ_OK;
+}
+
 int mlq_launch_count(mlq_ctx *ctx, int64_t *count)
 {
     if (!ctx || !count) return MLQ_EINVAL;
@@ -940,6 +1088,7 @@ const char *mlq_strerror(int s)
     case MLQ_ENOTREADY: return "not ready";
     case MLQ_ETIMEOUT: return "timed out";
     case MLQ_EUNSUPPORTED: return "not supported by this build";
+    case MLQ_ETOOBIG: return "request exceeds the fixed scratch of mlq_solve_noalloc (MLQ_NOALLOC_SCRATCH_BYTES)";
     default: return "unknown status";
     }
 }

@@ -64,6 +64,8 @@ _lib.mlq_level_launch.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int
                                   ctypes.POINTER(ctypes.c_int)]
 _lib.mlq_autotune.argtypes = [_vp, ctypes.c_int, _i64, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+_lib.mlq_solve_noalloc.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int32, _vp, _vp, ctypes.c_int, _vp, _vp,
+                                   _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.mlq_set_profiling.argtypes = [_vp, ctypes.c_int]
 _lib.mlq_member_profile.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(MemberStats)]
 _lib.mlq_strerror.restype = ctypes.c_char_p
@@ -75,7 +77,7 @@ EXPORTED = ["mlq_default_options", "mlq_default_model", "mlq_create", "mlq_destr
             "mlq_set_model", "mlq_add_level", "mlq_set_initial_state", "mlq_set_initial_disk", "mlq_set_kl",
             "mlq_build_kl", "mlq_centroid_table", "mlq_solve", "mlq_estimate", "mlq_workspace_bytes",
             "mlq_launch_count", "mlq_level_launch", "mlq_strerror", "mlq_last_cuda_error", "mlq_set_profiling",
-            "mlq_member_profile", "mlq_autotune"]
+            "mlq_member_profile", "mlq_autotune", "mlq_solve_noalloc"]
 
 
 class MLQError(RuntimeError):
@@ -145,6 +147,26 @@ def centroid_table(m_fine: int, modes_f: np.ndarray, m_coarse: int) -> np.ndarra
     _check(_lib.mlq_centroid_table(2, fd.ctypes.data_as(_vp), pm, K, cd.ctypes.data_as(_vp),
                                    phi.ctypes.data_as(_vp)), "mlq_centroid_table")
     return phi
+
+
+MLQ_ETOOBIG = -7
+
+
+def solve_noalloc(m: int, dt: float, nsteps: int, phi, xi, q, status=None, iters=None, theta_mean=None,
+                  v0=None, w0=None, stream=None, model: Model | None = None, options: Options | None = None):
+    """The library's allocation-free solve (mlq_solve_noalloc): every array
+    argument is a CUDA tensor owned by the caller; the work is queued on
+    `stream` (a cudaStream_t handle, None = legacy default stream) and the
+    call returns without waiting."""
+    def dp(t):
+        return None if t is None else _vp(t.data_ptr())
+
+    K = int(xi.shape[1])
+    code = _lib.mlq_solve_noalloc(m, dt, nsteps, ctypes.byref(model) if model is not None else None,
+                                  ctypes.byref(options) if options is not None else None, K, dp(phi),
+                                  dp(theta_mean), dp(xi), int(xi.shape[0]), dp(v0), dp(w0), dp(q), dp(status),
+                                  dp(iters), _vp(stream) if stream else None)
+    _check(code, "mlq_solve_noalloc")
 
 
 class Context:
