@@ -182,7 +182,8 @@ int mlq_workspace_bytes(mlq_ctx *ctx, int level, int64_t S, int with_coarse, siz
 typedef struct {
     double kernel_ms;       /* slab-solver kernel duration (CUDA events) */
     int level, coarse;      /* level of the mesh; 1 = coarse member of a pair */
-    int cluster, resident;  /* launch shape used */
+    int cluster, resident;  /* launch shape used (resident as in mlq_level_launch) */
+    int threads, npt;       /* threads per CTA; nodes per thread (register kernel, else 0) */
     int64_t samples, nodes, steps;
     int64_t cg_iterations;  /* CG iterations summed over samples, blocks, sweeps */
 } mlq_member_stats;

@@ -72,6 +72,7 @@ struct mlq_ctx {
     cudaEvent_t ev_t0[kStreams] = {}, ev_t1[kStreams] = {};
     int nmembers = 0;
     int prof_level[kStreams] = {}, prof_coarse[kStreams] = {}, prof_cs[kStreams] = {}, prof_resident[kStreams] = {};
+    int prof_threads[kStreams] = {}, prof_npt[kStreams] = {};
     int64_t prof_samples[kStreams] = {}, prof_nodes[kStreams] = {}, prof_steps[kStreams] = {};
     const int32_t *prof_iters_dev[kStreams] = {};
 };
@@ -407,6 +408,8 @@ int launch_member(mlq_ctx *ctx, const Member &mb, cudaStream_t st, int slot, int
         ctx->prof_coarse[slot] = coarse;
         ctx->prof_cs[slot] = sh.cs;
         ctx->prof_resident[slot] = sh.npt > 0 ? 2 : (sh.resident ? 1 : 0);
+        ctx->prof_threads[slot] = sh.threads;
+        ctx->prof_npt[slot] = sh.npt;
         ctx->prof_samples[slot] = mb.S;
         ctx->prof_nodes[slot] = L.n;
         ctx->prof_steps[slot] = L.nsteps;
@@ -828,6 +831,8 @@ int mlq_member_profile(mlq_ctx *ctx, int max_members, int *count, mlq_member_sta
         o.coarse = ctx->prof_coarse[k];
         o.cluster = ctx->prof_cs[k];
         o.resident = ctx->prof_resident[k];
+        o.threads = ctx->prof_threads[k];
+        o.npt = ctx->prof_npt[k];
         o.samples = ctx->prof_samples[k];
         o.nodes = ctx->prof_nodes[k];
         o.steps = ctx->prof_steps[k];

@@ -38,7 +38,8 @@ class Model(ctypes.Structure):
 
 class MemberStats(ctypes.Structure):
     _fields_ = [("kernel_ms", ctypes.c_double), ("level", ctypes.c_int), ("coarse", ctypes.c_int),
-                ("cluster", ctypes.c_int), ("resident", ctypes.c_int), ("samples", ctypes.c_int64),
+                ("cluster", ctypes.c_int), ("resident", ctypes.c_int), ("threads", ctypes.c_int),
+                ("npt", ctypes.c_int), ("samples", ctypes.c_int64),
                 ("nodes", ctypes.c_int64), ("steps", ctypes.c_int64), ("cg_iterations", ctypes.c_int64)]
 
 
