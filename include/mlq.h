@@ -168,6 +168,14 @@ int mlq_solve(mlq_ctx *ctx, int level, int64_t S, const double *xi, int with_coa
 int mlq_estimate(mlq_ctx *ctx, int L, const int64_t *N, const double *const *xi, double *mean_out,
                  double *var_out, double *rmse_out, double *const *y_out);
 
+/* The KL synthesis step alone (eq. KLlowrank), for verification: for S
+ * samples xi (host or device, S x K) write cs2_out[(s*n_elem + e)*2 + {0,1}]
+ * = (cos 2 theta, sin 2 theta) of element e (host or device, FP64).  The mixed
+ * path computes theta on the tensor cores (tcgen05, TF32 operands split into
+ * high and low parts, ~21-bit products, FP32 accumulation); the FP64 path on
+ * the CUDA cores in FP64.  MLQ_ETIMEOUT if a bounded device wait ran out. */
+int mlq_synthesize(mlq_ctx *ctx, int level, int64_t S, const double *xi, double *cs2_out);
+
 /* Bytes of device workspace a solve of S samples on `level` (and level-1
  * when with_coarse) uses; the context allocates and caches it. */
 int mlq_workspace_bytes(mlq_ctx *ctx, int level, int64_t S, int with_coarse, size_t *bytes);

@@ -169,6 +169,16 @@ def kl_build(mesh: Mesh, sigma2: float, ell: float, K: int, return_factor: bool 
     return modes, lam
 
 
+def kl_synthesis(phi: np.ndarray, xi: np.ndarray, theta_mean=None) -> np.ndarray:
+    """eq. KLlowrank per element: theta[s, e] = theta_mean[e] + sum_k phi[e, k]
+    xi[s, k], returned as (cos 2 theta, sin 2 theta) with shape (S, n_elem, 2),
+    the form the fibre tensor D = s_t I + (s_l - s_t) f f^T depends on."""
+    theta = np.asarray(xi, dtype=np.float64) @ np.asarray(phi, dtype=np.float64).T
+    if theta_mean is not None:
+        theta = theta + np.asarray(theta_mean)[None, :]
+    return np.stack([np.cos(2.0 * theta), np.sin(2.0 * theta)], axis=-1)
+
+
 def centroid_table(fine: Mesh, modes_f: np.ndarray, coarse: Mesh) -> np.ndarray:
     """Phi[e, k] = fine P1 interpolant of mode k at the centroid of coarse
     element e: the midpoint-rule transfer of Sec. 4."""

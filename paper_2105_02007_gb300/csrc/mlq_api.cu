@@ -7,6 +7,7 @@
 // concurrently.  All compute happens in the kernels of mlq_kernels.cuh.
 #include "mlq.h"
 #include "mlq_aux.cuh"
+#include "mlq_kl_tc.cuh"
 #include "mlq_launch.cuh"
 
 #include <algorithm>
@@ -32,6 +33,9 @@ struct Level {
     int nsteps = 0;
     int K = 0;
     double *d_phi = nullptr;         // ne x K
+    float *d_phi_hi = nullptr;       // ne x Kp, TF32 high part (tensor-core synthesis)
+    float *d_phi_lo = nullptr;       // ne x Kp, remainder
+    int Kp = 0;                      // K rounded up to 8
     double *d_theta_mean = nullptr;  // ne or null
     double *d_v0 = nullptr, *d_w0 = nullptr;
     double radius = 0.1;
@@ -63,6 +67,7 @@ struct mlq_ctx {
     cudaEvent_t ev_fork = nullptr;
     cudaEvent_t ev_join[kStreams] = {};
     int64_t launches = 0;
+    int *d_err = nullptr;   // set by kernels whose bounded waits time out
     std::string cuda_error;
     int max_cluster = 8;
     int smem_optin = 48 * 1024;
@@ -330,17 +335,42 @@ int ensure_workspace(mlq_ctx *ctx, size_t bytes)
     return MLQ_OK;
 }
 
+// K1.  Mixed path: tensor cores (TF32 split, FP32-accurate); FP64 path: FP64
+// on the CUDA cores (the 1e-10 parity of that path needs the FP64 angle).
+int launch_synthesis(mlq_ctx *ctx, const Level &L, const double *d_xi, int S, double *cs2, cudaStream_t st)
+{
+    if (ctx->opt.precision == MLQ_MIXED && L.d_phi_hi) {
+        const size_t limit = 200 * 1024;
+        int NT = ((S + 15) / 16) * 16;
+        if (NT > 256) NT = 256;
+        while (NT > 16 && (size_t)2 * (mlq::kTcM + NT) * L.Kp * 4 + 64 > limit) NT -= 16;
+        const size_t smem = (size_t)2 * (mlq::kTcM + NT) * L.Kp * 4 + 64;
+        if (smem <= limit) {
+            MLQ_CUDA(ctx, cudaFuncSetAttribute(mlq::kl_synthesis_tc_kernel,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            dim3 grd((unsigned)((L.ne + mlq::kTcM - 1) / mlq::kTcM), (unsigned)((S + NT - 1) / NT));
+            mlq::kl_synthesis_tc_kernel<<<grd, 128, smem, st>>>(L.d_phi_hi, L.d_phi_lo, L.d_theta_mean, d_xi, L.K,
+                                                                 L.Kp, L.ne, S, NT, cs2, ctx->d_err);
+            MLQ_CUDA(ctx, cudaGetLastError());
+            ctx->launches++;
+            return MLQ_OK;
+        }
+    }
+    dim3 blk(256), grd((unsigned)((L.ne + 255) / 256), (unsigned)S);
+    mlq::kl_synthesis_kernel<<<grd, blk, 0, st>>>(L.d_phi, L.d_theta_mean, d_xi, L.K, L.ne, S, cs2);
+    MLQ_CUDA(ctx, cudaGetLastError());
+    ctx->launches++;
+    return MLQ_OK;
+}
+
 template <typename TI>
 int launch_member_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream_t st, int slot)
 {
     const bool mixed = sizeof(TI) == 4;
     // K1: KL synthesis (theta -> cos 2t, sin 2t)
     {
-        dim3 blk(256), grd((unsigned)((L.ne + 255) / 256), (unsigned)mb.S);
-        mlq::kl_synthesis_kernel<<<grd, blk, 0, st>>>(L.d_phi, L.d_theta_mean, mb.d_xi, L.K, L.ne, (int)mb.S,
-                                                        mb.cs2);
-        MLQ_CUDA(ctx, cudaGetLastError());
-        ctx->launches++;
+        int st1 = launch_synthesis(ctx, L, mb.d_xi, (int)mb.S, mb.cs2, st);
+        if (st1 != MLQ_OK) return st1;
     }
     // K2: stencil of A = M + dt K(theta)
     {
@@ -418,6 +448,19 @@ int launch_member(mlq_ctx *ctx, const Member &mb, cudaStream_t st, int slot, int
     }
     if (ctx->opt.precision == MLQ_MIXED) return launch_member_t<float>(ctx, L, mb, st, slot);
     return launch_member_t<double>(ctx, L, mb, st, slot);
+}
+
+// device error flag (a bounded wait ran out): report once and clear
+int check_err(mlq_ctx *ctx)
+{
+    int h = 0;
+    MLQ_CUDA(ctx, cudaMemcpy(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        MLQ_CUDA(ctx, cudaMemset(ctx->d_err, 0, sizeof(int)));
+        ctx->cuda_error = "a bounded device wait timed out";
+        return MLQ_ETIMEOUT;
+    }
+    return MLQ_OK;
 }
 
 int check_level(const mlq_ctx *ctx, int level)
@@ -515,6 +558,8 @@ int mlq_create(mlq_ctx **out, int device, void *cuda_stream, const mlq_options *
     cudaGetLastError();
     (void)nonportable;
     if (o.cluster > ctx->max_cluster) return fail(MLQ_EUNSUPPORTED);
+    if (cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess || cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess)
+        return fail(MLQ_ENOMEM);
     *out = ctx;
     return MLQ_OK;
 }
@@ -534,7 +579,10 @@ int mlq_destroy(mlq_ctx *ctx)
         if (ctx->ev_t1[k]) cudaEventDestroy(ctx->ev_t1[k]);
     }
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    cudaFree(ctx->d_err);
     for (auto &L : ctx->levels) {
+        cudaFree(L.d_phi_hi);
+        cudaFree(L.d_phi_lo);
         cudaFree(L.d_phi);
         cudaFree(L.d_theta_mean);
         cudaFree(L.d_v0);
@@ -572,6 +620,8 @@ int mlq_add_level(mlq_ctx *ctx, int level, int dim, const int32_t *dims, const d
     if (m < 2 || m > 8193 || !(dt > 0.0) || nsteps < 0) return MLQ_EINVAL;
     Level &L = ctx->levels[level];
     cudaFree(L.d_phi);
+    cudaFree(L.d_phi_hi);
+    cudaFree(L.d_phi_lo);
     cudaFree(L.d_theta_mean);
     cudaFree(L.d_v0);
     cudaFree(L.d_w0);
@@ -628,12 +678,60 @@ int mlq_set_kl(mlq_ctx *ctx, int level, int K, const double *phi, const double *
     L.d_phi = L.d_theta_mean = nullptr;
     MLQ_CUDA(ctx, cudaMalloc(&L.d_phi, sizeof(double) * (size_t)L.ne * K));
     MLQ_CUDA(ctx, cudaMemcpy(L.d_phi, phi, sizeof(double) * (size_t)L.ne * K, cudaMemcpyDefault));
+    // TF32 split of the table for the tensor-core synthesis: hi = the value
+    // rounded to FP32 with the low 13 mantissa bits cleared, lo = remainder
+    {
+        cudaFree(L.d_phi_hi);
+        cudaFree(L.d_phi_lo);
+        L.d_phi_hi = L.d_phi_lo = nullptr;
+        L.Kp = (K + 7) / 8 * 8;
+        std::vector<double> hp((size_t)L.ne * K);
+        MLQ_CUDA(ctx, cudaMemcpy(hp.data(), L.d_phi, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost));
+        std::vector<float> hi((size_t)L.ne * L.Kp, 0.0f), lo((size_t)L.ne * L.Kp, 0.0f);
+        for (int64_t e = 0; e < L.ne; ++e)
+            for (int k = 0; k < K; ++k) {
+                const float x = (float)hp[(size_t)e * K + k];
+                uint32_t b;
+                std::memcpy(&b, &x, 4);
+                b &= 0xFFFFE000u;
+                float h;
+                std::memcpy(&h, &b, 4);
+                hi[(size_t)e * L.Kp + k] = h;
+                lo[(size_t)e * L.Kp + k] = x - h;
+            }
+        MLQ_CUDA(ctx, cudaMalloc(&L.d_phi_hi, sizeof(float) * hi.size()));
+        MLQ_CUDA(ctx, cudaMalloc(&L.d_phi_lo, sizeof(float) * lo.size()));
+        MLQ_CUDA(ctx, cudaMemcpy(L.d_phi_hi, hi.data(), sizeof(float) * hi.size(), cudaMemcpyHostToDevice));
+        MLQ_CUDA(ctx, cudaMemcpy(L.d_phi_lo, lo.data(), sizeof(float) * lo.size(), cudaMemcpyHostToDevice));
+    }
     if (theta_mean) {
         MLQ_CUDA(ctx, cudaMalloc(&L.d_theta_mean, sizeof(double) * (size_t)L.ne));
         MLQ_CUDA(ctx, cudaMemcpy(L.d_theta_mean, theta_mean, sizeof(double) * (size_t)L.ne, cudaMemcpyDefault));
     }
     L.K = K;
     return MLQ_OK;
+}
+
+int mlq_synthesize(mlq_ctx *ctx, int level, int64_t S, const double *xi, double *cs2_out)
+{
+    if (!ctx || !xi || !cs2_out || S < 1 || S > 65535) return MLQ_EINVAL;
+    if (check_level(ctx, level) != MLQ_OK) return MLQ_EINVAL;
+    MLQ_CUDA(ctx, cudaSetDevice(ctx->device));
+    const Level &L = ctx->levels[level];
+    const size_t out_b = align_up((size_t)S * L.ne * 16, 256), xi_b = align_up((size_t)S * L.K * 8, 256);
+    int st = ensure_workspace(ctx, out_b + xi_b);
+    if (st != MLQ_OK) return st;
+    double *cs2 = (double *)ctx->ws;
+    const double *d_xi = xi;
+    if (!is_device_ptr(xi)) {
+        double *dx = (double *)((char *)ctx->ws + out_b);
+        MLQ_CUDA(ctx, cudaMemcpyAsync(dx, xi, sizeof(double) * S * L.K, cudaMemcpyHostToDevice, ctx->stream));
+        d_xi = dx;
+    }
+    if ((st = launch_synthesis(ctx, L, d_xi, (int)S, cs2, ctx->stream)) != MLQ_OK) return st;
+    MLQ_CUDA(ctx, cudaMemcpyAsync(cs2_out, cs2, (size_t)S * L.ne * 16, cudaMemcpyDefault, ctx->stream));
+    MLQ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return check_err(ctx);
 }
 
 int mlq_workspace_bytes(mlq_ctx *ctx, int level, int64_t S, int with_coarse, size_t *bytes)
@@ -717,7 +815,7 @@ int mlq_solve(mlq_ctx *ctx, int level, int64_t S, const double *xi, int with_coa
     if ((st = copy_out(ctx, status, stbuf, S * 4, ctx->stream)) != MLQ_OK) return st;
     if ((st = copy_out(ctx, iters, mf.iters, S * 4, ctx->stream)) != MLQ_OK) return st;
     MLQ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    return MLQ_OK;
+    return check_err(ctx);
 }
 
 int mlq_estimate(mlq_ctx *ctx, int L, const int64_t *N, const double *const *xi, double *mean_out,
@@ -793,6 +891,7 @@ int mlq_estimate(mlq_ctx *ctx, int L, const int64_t *N, const double *const *xi,
     MLQ_CUDA(ctx, cudaMemcpyAsync(hs.data(), sums, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost,
                                   ctx->stream));
     MLQ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if ((st = check_err(ctx)) != MLQ_OK) return st;
     double mean = 0.0, mse = 0.0;
     for (int l = 0; l <= L; ++l) {
         const double nl = (double)N[l];

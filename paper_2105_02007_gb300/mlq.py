@@ -67,6 +67,7 @@ _lib.mlq_autotune.argtypes = [_vp, ctypes.c_int, _i64, _vp, ctypes.c_int, ctypes
                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
 _lib.mlq_solve_noalloc.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int32, _vp, _vp, ctypes.c_int, _vp, _vp,
                                    _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.mlq_synthesize.argtypes = [_vp, ctypes.c_int, _i64, _vp, _vp]
 _lib.mlq_set_profiling.argtypes = [_vp, ctypes.c_int]
 _lib.mlq_member_profile.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(MemberStats)]
 _lib.mlq_strerror.restype = ctypes.c_char_p
@@ -78,7 +79,7 @@ EXPORTED = ["mlq_default_options", "mlq_default_model", "mlq_create", "mlq_destr
             "mlq_set_model", "mlq_add_level", "mlq_set_initial_state", "mlq_set_initial_disk", "mlq_set_kl",
             "mlq_build_kl", "mlq_centroid_table", "mlq_solve", "mlq_estimate", "mlq_workspace_bytes",
             "mlq_launch_count", "mlq_level_launch", "mlq_strerror", "mlq_last_cuda_error", "mlq_set_profiling",
-            "mlq_member_profile", "mlq_autotune", "mlq_solve_noalloc"]
+            "mlq_member_profile", "mlq_autotune", "mlq_solve_noalloc", "mlq_synthesize"]
 
 
 class MLQError(RuntimeError):
@@ -260,6 +261,14 @@ class Context:
         if return_y:
             return mean.value, var, rmse.value, ys
         return mean.value, var, rmse.value
+
+    def synthesize(self, level: int, xi):
+        """KL synthesis alone: (cos 2 theta, sin 2 theta), shape (S, n_elem, 2)."""
+        keep, px = _ptr(xi, np.float64)
+        S = int(xi.shape[0])
+        out = np.zeros((S, self.levels[level]["ne"], 2))
+        _check(_lib.mlq_synthesize(self._h, level, S, px, out.ctypes.data_as(_vp)), "mlq_synthesize", self._h)
+        return out
 
     def workspace_bytes(self, level: int, S: int, with_coarse: bool = False) -> int:
         b = ctypes.c_size_t()

@@ -332,3 +332,31 @@ def test_autotune_keeps_parity(mlq, m):
         r = ctx.solve(0, xi)
     assert np.all(r["status"] == 0)
     assert rel(r["q_fine"], q_ref) < TOL[1]
+
+
+# --------------------------------------------------------------------------
+# KL synthesis step alone (row a2): FP64 CUDA-core path and the tcgen05
+# tensor-core path of the mixed precision (TF32 split, FP32 accumulation),
+# over ragged element and sample tiles and K padded to a multiple of 8.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("m,K,S", [(17, 16, 5), (17, 6, 300), (65, 16, 33), (33, 64, 17), (9, 1, 1)])
+def test_kl_synthesis_parity(mlq, m, K, S):
+    rng = np.random.default_rng(m * 1000 + K * 10 + S)
+    ne = 2 * (m - 1) ** 2
+    phi = rng.normal(scale=0.3 / np.sqrt(K), size=(ne, K))
+    tm = rng.normal(scale=0.2, size=ne)
+    xi = inputs.gaussian_xi(2, 1, 0, S, K)
+    ref = O.kl_synthesis(phi, xi, tm)
+    # Tensor-core bound: each TF32 part keeps 11 significant bits, so the
+    # three-product split loses at most ~3 * 2^-20 |phi xi| per term (the
+    # dropped lo*lo product and the truncation of both lo parts); FP32
+    # accumulation of K terms adds K * 2^-24 sum |phi xi|; the argument of
+    # cos/sin is 2 theta; sincosf and the FP32 rounding of theta add ~1e-6.
+    l1 = np.max(np.abs(xi) @ np.abs(phi).T)
+    tol_tc = 2 * (3 * 2.0 ** -20 + K * 2.0 ** -24) * l1 + 1e-6
+    for prec, tol in ((0, 1e-13), (1, tol_tc)):
+        with mlq.Context(0, prec) as ctx:
+            ctx.add_level(0, m, 0.1, 1)
+            ctx.set_kl(0, phi, tm)
+            got = ctx.synthesize(0, xi)
+        assert np.max(np.abs(got - ref)) < tol, (prec, np.max(np.abs(got - ref)))
