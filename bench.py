@@ -242,6 +242,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-graphs", action="store_true", help="run estimates eagerly instead of as CUDA graphs")
     ap.add_argument("--case", default=None, help="profile one member solve, e.g. level=4,samples=1,steps=4")
     args = ap.parse_args()
     if args.case:
@@ -272,7 +273,7 @@ def main():
     phis = [mlq.centroid_table(LEVEL_M[-1], modes, m) for m in LEVEL_M]
 
     def make_ctx(p):
-        ctx = mlq.Context(local, p, stream=stream.cuda_stream)
+        ctx = mlq.Context(local, p, stream=stream.cuda_stream, graphs=0 if args.no_graphs else 1)
         for l, m in enumerate(LEVEL_M):
             ctx.add_level(l, m, level_dt(l), level_steps(l))
             ctx.set_kl(l, phis[l])
@@ -417,6 +418,7 @@ def main():
                        "dof_steps_per_step": dof, "precision": pkey, "l2": "256 MiB buffer zeroed before each "
                        "timed estimate (inside the timed region, on the same stream)",
                        "parallelism": f"replicas x{world}, seed = rank",
+                       "cuda_graph": not args.no_graphs,
                        "launch_shapes": {str(l): list(v) for l, v in tuned.items()}},
             "time_to_rmse_s": ms_all / 1000.0, "estimate": mean, "rmse": rmse, "var_l": list(var),
             "e2e": {"value": world * dof / e2e_s if e2e_s else None, "unit": UNIT, "h2d_bytes_per_step": h2d,

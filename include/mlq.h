@@ -82,7 +82,12 @@ typedef struct {
  *   storage    where a sample's PCG vectors live: 0 = on chip (registers and
  *              shared memory of its cluster) when they fit, else global
  *              memory; 1 = on chip (a solve whose level does not fit returns
- *              MLQ_EUNSUPPORTED); 2 = global memory. */
+ *              MLQ_EUNSUPPORTED); 2 = global memory.
+ *   graphs     1 = mlq_estimate captures its whole multi-stream launch
+ *              sequence into a CUDA graph and replays it while the
+ *              configuration, sizes and pointers are unchanged (needs a
+ *              non-NULL stream in mlq_create and device xi / y arrays;
+ *              otherwise it runs eagerly).  0 = always eager. */
 typedef struct {
     int precision;
     double rtol;
@@ -92,6 +97,7 @@ typedef struct {
     int cluster;
     int threads;
     int storage;
+    int graphs;
 } mlq_options;
 
 /* Fill *opt / *model with the defaults listed above (rtol 1e-13 for FP64,

@@ -68,6 +68,14 @@ struct mlq_ctx {
     cudaEvent_t ev_join[kStreams] = {};
     int64_t launches = 0;
     int *d_err = nullptr;   // set by kernels whose bounded waits time out
+    double *h_sums = nullptr;  // pinned host copy of the per-level sums
+    // CUDA graph of the last estimate (options.graphs): replayed while the
+    // key (configuration generation, sizes, pointers) is unchanged
+    uint64_t generation = 1;
+    std::vector<uint64_t> graph_key;
+    cudaGraphExec_t graph_exec = nullptr;
+    int64_t graph_launches = 0;
+    bool capturing = false;
     std::string cuda_error;
     int max_cluster = 8;
     int smem_optin = 48 * 1024;
@@ -415,7 +423,8 @@ int launch_member_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream_t
     const Shape sh = choose_launch(ctx, L, mb.S);
     if (ctx->opt.storage == 1 && !sh.resident) return MLQ_EUNSUPPORTED;
     const bool timed = ctx->profile && slot >= 0 && slot < kStreams;
-    if (timed) MLQ_CUDA(ctx, cudaEventRecord(ctx->ev_t0[slot], st));
+    const unsigned evf = ctx->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if (timed) MLQ_CUDA(ctx, cudaEventRecordWithFlags(ctx->ev_t0[slot], st, evf));
     if constexpr (sizeof(TI) == 4) {
         if (sh.npt > 0)
             MLQ_CUDA(ctx, launch_reg_any(sh.cs, sh.npt, a, (int)mb.S, sh.threads, sh.smem, st));
@@ -424,7 +433,7 @@ int launch_member_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream_t
     } else {
         MLQ_CUDA(ctx, launch_slab_cs<TI>(sh.cs, a, (int)mb.S, sh.threads, sh.smem, sh.resident, st));
     }
-    if (timed) MLQ_CUDA(ctx, cudaEventRecord(ctx->ev_t1[slot], st));
+    if (timed) MLQ_CUDA(ctx, cudaEventRecordWithFlags(ctx->ev_t1[slot], st, evf));
     ctx->launches++;
     return MLQ_OK;
 }
@@ -479,6 +488,43 @@ int copy_out(mlq_ctx *ctx, void *dst, const void *src, size_t bytes, cudaStream_
 
 }  // namespace
 
+// Profiling bookkeeping of a member whose kernels run from a replayed graph.
+void launch_member_profile_only(mlq_ctx *ctx, const Member &mb, int slot, int coarse)
+{
+    const Level &L = ctx->levels[mb.level];
+    const Shape sh = choose_launch(ctx, L, mb.S);
+    ctx->prof_level[slot] = mb.level;
+    ctx->prof_coarse[slot] = coarse;
+    ctx->prof_cs[slot] = sh.cs;
+    ctx->prof_resident[slot] = sh.npt > 0 ? 2 : (sh.resident ? 1 : 0);
+    ctx->prof_threads[slot] = sh.threads;
+    ctx->prof_npt[slot] = sh.npt;
+    ctx->prof_samples[slot] = mb.S;
+    ctx->prof_nodes[slot] = L.n;
+    ctx->prof_steps[slot] = L.nsteps;
+    ctx->prof_iters_dev[slot] = mb.iters;
+    ctx->nmembers = std::max(ctx->nmembers, slot + 1);
+}
+
+// Wait for an estimate and combine the per-level FP64 sums on the host.
+int finish_estimate(mlq_ctx *ctx, int L, const int64_t *N, double *mean_out, double *var_out, double *rmse_out)
+{
+    MLQ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    int st = check_err(ctx);
+    if (st != MLQ_OK) return st;
+    double mean = 0.0, mse = 0.0;
+    for (int l = 0; l <= L; ++l) {
+        const double nl = (double)N[l];
+        const double v = ctx->h_sums[2 * l + 1] / (nl - 1.0);
+        mean += ctx->h_sums[2 * l] / nl;
+        mse += v / nl;
+        if (var_out) var_out[l] = v;
+    }
+    *mean_out = mean;
+    if (rmse_out) *rmse_out = std::sqrt(mse);
+    return MLQ_OK;
+}
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
@@ -495,6 +541,7 @@ int mlq_default_options(mlq_options *opt, int precision)
     opt->cluster = 0;
     opt->threads = 0;
     opt->storage = 0;
+    opt->graphs = 0;
     return MLQ_OK;
 }
 
@@ -560,6 +607,7 @@ int mlq_create(mlq_ctx **out, int device, void *cuda_stream, const mlq_options *
     if (o.cluster > ctx->max_cluster) return fail(MLQ_EUNSUPPORTED);
     if (cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess || cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess)
         return fail(MLQ_ENOMEM);
+    if (cudaMallocHost(&ctx->h_sums, sizeof(double) * 2 * kMaxLevels) != cudaSuccess) return fail(MLQ_ENOMEM);
     *out = ctx;
     return MLQ_OK;
 }
@@ -580,6 +628,8 @@ int mlq_destroy(mlq_ctx *ctx)
     }
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     cudaFree(ctx->d_err);
+    if (ctx->h_sums) cudaFreeHost(ctx->h_sums);
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
     for (auto &L : ctx->levels) {
         cudaFree(L.d_phi_hi);
         cudaFree(L.d_phi_lo);
@@ -596,6 +646,7 @@ int mlq_destroy(mlq_ctx *ctx)
 int mlq_set_options(mlq_ctx *ctx, const mlq_options *opt)
 {
     if (!ctx || !opt || validate_options(opt) != MLQ_OK) return MLQ_EINVAL;
+    ctx->generation++;
     if (opt->cluster > ctx->max_cluster) return MLQ_EUNSUPPORTED;
     ctx->opt = *opt;
     return MLQ_OK;
@@ -604,6 +655,7 @@ int mlq_set_options(mlq_ctx *ctx, const mlq_options *opt)
 int mlq_set_model(mlq_ctx *ctx, const mlq_model *m)
 {
     if (!ctx || !m) return MLQ_EINVAL;
+    ctx->generation++;
     if (!(m->s_l > 0.0) || !(m->s_t > 0.0) || !(m->T > 0.0)) return MLQ_EINVAL;
     ctx->model = *m;
     return MLQ_OK;
@@ -618,6 +670,7 @@ int mlq_add_level(mlq_ctx *ctx, int level, int dim, const int32_t *dims, const d
     if (dim != 2) return MLQ_EINVAL;
     const int m = dims[0];
     if (m < 2 || m > 8193 || !(dt > 0.0) || nsteps < 0) return MLQ_EINVAL;
+    ctx->generation++;
     Level &L = ctx->levels[level];
     cudaFree(L.d_phi);
     cudaFree(L.d_phi_hi);
@@ -641,6 +694,7 @@ int mlq_add_level(mlq_ctx *ctx, int level, int dim, const int32_t *dims, const d
 int mlq_set_initial_state(mlq_ctx *ctx, int level, const double *v0, const double *w0)
 {
     if (!ctx || !v0 || level < 0 || level >= kMaxLevels || !ctx->levels[level].defined) return MLQ_EINVAL;
+    ctx->generation++;
     Level &L = ctx->levels[level];
     MLQ_CUDA(ctx, cudaSetDevice(ctx->device));
     if (!L.d_v0) MLQ_CUDA(ctx, cudaMalloc(&L.d_v0, sizeof(double) * L.n));
@@ -659,6 +713,7 @@ int mlq_set_initial_disk(mlq_ctx *ctx, int level, double radius)
 {
     if (!ctx || level < 0 || level >= kMaxLevels || !ctx->levels[level].defined || !(radius >= 0.0))
         return MLQ_EINVAL;
+    ctx->generation++;
     Level &L = ctx->levels[level];
     cudaFree(L.d_v0);
     cudaFree(L.d_w0);
@@ -671,6 +726,7 @@ int mlq_set_kl(mlq_ctx *ctx, int level, int K, const double *phi, const double *
 {
     if (!ctx || !phi || K < 1 || K > kMaxK || level < 0 || level >= kMaxLevels || !ctx->levels[level].defined)
         return MLQ_EINVAL;
+    ctx->generation++;
     Level &L = ctx->levels[level];
     MLQ_CUDA(ctx, cudaSetDevice(ctx->device));
     cudaFree(L.d_phi);
@@ -864,45 +920,94 @@ int mlq_estimate(mlq_ctx *ctx, int L, const int64_t *N, const double *const *xi,
         }
         fine[l].d_xi = coarse[l].d_xi = d_xi;
     }
-    MLQ_CUDA(ctx, cudaEventRecord(ctx->ev_fork, ctx->stream));
+    // CUDA graph: capture the whole estimate once, replay while unchanged
+    bool use_graph = ctx->opt.graphs != 0 && ctx->stream != nullptr;
+    for (int l = 0; l <= L && use_graph; ++l) {
+        if (!is_device_ptr(xi[l])) use_graph = false;
+        if (y_out && y_out[l] && !is_device_ptr(y_out[l])) use_graph = false;
+    }
+    std::vector<uint64_t> key;
+    if (use_graph) {
+        key.push_back(ctx->generation);
+        key.push_back((uint64_t)L);
+        key.push_back((uint64_t)(uintptr_t)ctx->ws);
+        key.push_back((uint64_t)ctx->profile);
+        for (int l = 0; l <= L; ++l) {
+            key.push_back((uint64_t)N[l]);
+            key.push_back((uint64_t)(uintptr_t)xi[l]);
+            key.push_back((uint64_t)(uintptr_t)(y_out ? y_out[l] : nullptr));
+        }
+        if (ctx->graph_exec && key == ctx->graph_key) {
+            ctx->nmembers = 0;
+            for (int l = L, sid = 0; l >= 0; --l)
+                for (int k = 0; k < (l > 0 ? 2 : 1); ++k, ++sid)
+                    if (ctx->profile) launch_member_profile_only(ctx, k == 0 ? fine[l] : coarse[l], sid, k);
+            MLQ_CUDA(ctx, cudaGraphLaunch(ctx->graph_exec, ctx->stream));
+            ctx->launches += ctx->graph_launches;
+            return finish_estimate(ctx, L, N, mean_out, var_out, rmse_out);
+        }
+        if (ctx->graph_exec) {
+            cudaGraphExecDestroy(ctx->graph_exec);
+            ctx->graph_exec = nullptr;
+        }
+        MLQ_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        ctx->capturing = true;
+    }
+    const int64_t launches_before = ctx->launches;
+    auto abort_capture = [&](int code) {
+        if (ctx->capturing) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(ctx->stream, &g);
+            if (g) cudaGraphDestroy(g);
+            ctx->capturing = false;
+            cudaGetLastError();
+        }
+        return code;
+    };
+    if (cudaEventRecord(ctx->ev_fork, ctx->stream) != cudaSuccess) return abort_capture(MLQ_ECUDA);
     // largest levels first so that they start first
     int sid = 0;
     for (int l = L; l >= 0; --l) {
         for (int k = 0; k < (l > 0 ? 2 : 1); ++k) {
             cudaStream_t s = ctx->pool[sid];
-            MLQ_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_fork, 0));
+            if (cudaStreamWaitEvent(s, ctx->ev_fork, 0) != cudaSuccess) return abort_capture(MLQ_ECUDA);
             st = launch_member(ctx, k == 0 ? fine[l] : coarse[l], s, sid, k);
-            if (st != MLQ_OK) return st;
-            MLQ_CUDA(ctx, cudaEventRecord(ctx->ev_join[sid], s));
-            MLQ_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_join[sid], 0));
+            if (st != MLQ_OK) return abort_capture(st);
+            if (cudaEventRecord(ctx->ev_join[sid], s) != cudaSuccess ||
+                cudaStreamWaitEvent(ctx->stream, ctx->ev_join[sid], 0) != cudaSuccess)
+                return abort_capture(MLQ_ECUDA);
             ++sid;
         }
     }
     for (int l = 0; l <= L; ++l) {
         mlq::level_sums_kernel<<<1, 1024, 0, ctx->stream>>>(fine[l].q, l > 0 ? coarse[l].q : nullptr, N[l],
                                                               ybuf[l], sums + 2 * l);
-        MLQ_CUDA(ctx, cudaGetLastError());
+        if (cudaGetLastError() != cudaSuccess) return abort_capture(MLQ_ECUDA);
         ctx->launches++;
         if (y_out && y_out[l]) {
-            if ((st = copy_out(ctx, y_out[l], ybuf[l], (size_t)N[l] * 8, ctx->stream)) != MLQ_OK) return st;
+            if ((st = copy_out(ctx, y_out[l], ybuf[l], (size_t)N[l] * 8, ctx->stream)) != MLQ_OK)
+                return abort_capture(st);
         }
     }
-    std::vector<double> hs(2 * (L + 1));
-    MLQ_CUDA(ctx, cudaMemcpyAsync(hs.data(), sums, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost,
-                                  ctx->stream));
-    MLQ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    if ((st = check_err(ctx)) != MLQ_OK) return st;
-    double mean = 0.0, mse = 0.0;
-    for (int l = 0; l <= L; ++l) {
-        const double nl = (double)N[l];
-        const double v = hs[2 * l + 1] / (nl - 1.0);
-        mean += hs[2 * l] / nl;
-        mse += v / nl;
-        if (var_out) var_out[l] = v;
+    if (cudaMemcpyAsync(ctx->h_sums, sums, sizeof(double) * 2 * (L + 1), cudaMemcpyDeviceToHost, ctx->stream) !=
+        cudaSuccess)
+        return abort_capture(MLQ_ECUDA);
+    if (ctx->capturing) {
+        cudaGraph_t g = nullptr;
+        ctx->capturing = false;
+        MLQ_CUDA(ctx, cudaStreamEndCapture(ctx->stream, &g));
+        cudaError_t e = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            ctx->graph_exec = nullptr;
+            ctx->cuda_error = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e);
+            return MLQ_ECUDA;
+        }
+        ctx->graph_key = key;
+        ctx->graph_launches = ctx->launches - launches_before;
+        MLQ_CUDA(ctx, cudaGraphLaunch(ctx->graph_exec, ctx->stream));
     }
-    *mean_out = mean;
-    if (rmse_out) *rmse_out = std::sqrt(mse);
-    return MLQ_OK;
+    return finish_estimate(ctx, L, N, mean_out, var_out, rmse_out);
 }
 
 int mlq_set_profiling(mlq_ctx *ctx, int enable)
@@ -1011,6 +1116,7 @@ int mlq_autotune(mlq_ctx *ctx, int level, int64_t S, const double *xi, int probe
     L.tuned_cs = pick.cs;
     L.tuned_npt = pick.npt;
     L.tuned_threads = pick.threads;
+    ctx->generation++;
     if (cluster_out) *cluster_out = pick.cs;
     if (threads_out) *threads_out = pick.threads;
     if (ms_out) *ms_out = best;

@@ -360,3 +360,35 @@ def test_kl_synthesis_parity(mlq, m, K, S):
             ctx.set_kl(0, phi, tm)
             got = ctx.synthesize(0, xi)
         assert np.max(np.abs(got - ref)) < tol, (prec, np.max(np.abs(got - ref)))
+
+
+def test_estimate_graph_capture_and_replay(mlq):
+    import torch
+
+    ms, dts, N = [9, 17], [0.2, 0.1], [24, 8]
+    fine = O.mesh2d(17)
+    modes, _ = O.kl_build(fine, 0.09, 0.04, 4)
+    phis = [O.centroid_table(fine, modes, O.mesh2d(m)) for m in ms]
+    xis = [inputs.gaussian_xi(0, l, 0, N[l], 4) for l in range(2)]
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    d_xi = [torch.from_numpy(x).to(dev) for x in xis]
+    res = {}
+    for graphs in (0, 1):
+        with mlq.Context(0, mlq.MLQ_MIXED, stream=stream.cuda_stream, graphs=graphs) as ctx:
+            for l, (m, dt) in enumerate(zip(ms, dts)):
+                ctx.add_level(l, m, dt, int(round(2.0 / dt)))
+                ctx.set_kl(l, phis[l])
+            torch.cuda.synchronize(dev)
+            first = ctx.estimate(d_xi)
+            n1 = ctx.launch_count()
+            second = ctx.estimate(d_xi)                # replay when graphs = 1
+            assert ctx.launch_count() == 2 * n1
+            assert first[0] == second[0] and np.array_equal(first[1], second[1])
+            # new values behind the same pointers are picked up by the replay
+            d_xi[1].copy_(torch.from_numpy(inputs.gaussian_xi(1, 1, 0, N[1], 4)).to(dev))
+            third = ctx.estimate(d_xi)
+            d_xi[1].copy_(torch.from_numpy(xis[1]).to(dev))
+            res[graphs] = (first, third)
+    assert res[0][0][0] == res[1][0][0]
+    assert res[0][1][0] == res[1][1][0] and res[0][1][0] != res[0][0][0]
