@@ -9,8 +9,9 @@ coarse members):
   (s_l 1, s_t 0.2, a 0.1, eps 0.01, gamma 0.5); initial quarter disc of
   radius 0.1; fibre angle = Gaussian KL field, 16 modes of
   0.09 exp(-|x-y|^2/0.04) on the finest mesh; xi ~ N(0,1) from Philox,
-  seed = rank; QoI = integral of v at T.  Mixed precision (FP32 inner PCG in
-  FP64 refinement to 1e-12), all levels running concurrently.
+  seed = rank; QoI = integral of v at T.  Mixed precision (FP32 inner PCG
+  preconditioned by a multigrid V-cycle, inside FP64 refinement to 1e-12), all
+  levels running concurrently from one CUDA graph.
 
 Metric: DOF-steps/s (node x time block x sample, fine and coarse members
 both counted); time-to-RMSE = wall time of one estimate.
@@ -42,12 +43,17 @@ T_END = 10.0
 WORKLOAD = "MLMC 2D monodomain, 5 nested levels 17^2..257^2, N=4096/1024/256/64/16, K=16"
 METRIC = "MLMC DOF-steps/s (time-to-RMSE of one estimate alongside)"
 UNIT = "DOF-steps/s"
-# algorithmic bytes the method moves per DOF (2D, mixed FP32 inner PCG):
-# per CG iteration 4 stencil coefficients (16 B) + SpMV operand/result (8 B)
-# + vector updates (32 B); per time block the reaction/load/residual pass
-# with FP64 state (~64 B).  FP64 doubles both.
-BYTES_PER_DOF_ITER = {"mixed": 56.0, "fp64": 112.0}
-BYTES_PER_DOF_STEP = {"mixed": 64.0, "fp64": 64.0}
+# Algorithmic bytes a memory-streaming implementation of the same solver
+# moves per DOF (2D), each array read or written once per pass:
+#  Jacobi-PCG iteration (FP32): 4 stencil coefficients 16 B + SpMV operand and
+#    result 8 B + vector updates 32 B = 56 B; FP64: 112 B.
+#  multigrid-PCG iteration (FP32): CG updates 44 B, pre-smoothing 12 B,
+#    residual 28 B, restriction 5 B, interpolation 9 B, post-smoothing 28 B,
+#    w = A u 24 B on the fine level (150 B) plus a third of the V-cycle part
+#    for the coarse levels (27 B) = 176 B.
+#  per time block: the reaction / load / FP64 residual pass, ~64 B.
+BYTES_PER_DOF_ITER = {"jacobi": 56.0, "mg": 176.0, "fp64": 112.0}
+BYTES_PER_DOF_STEP = {"jacobi": 64.0, "mg": 64.0, "fp64": 64.0}
 
 
 def level_dt(l):
@@ -353,22 +359,27 @@ def main():
     members = profiles[-1]
     pkey = args.precision
 
+    def solver(d):
+        return "fp64" if pkey == "fp64" else ("mg" if d["resident"] == 3 else "jacobi")
+
     def alg_bytes(d):
-        return (d["cg_iterations"] * d["nodes"] * BYTES_PER_DOF_ITER[pkey]
-                + d["samples"] * d["steps"] * d["nodes"] * BYTES_PER_DOF_STEP[pkey])
+        k = solver(d)
+        return (d["cg_iterations"] * d["nodes"] * BYTES_PER_DOF_ITER[k]
+                + d["samples"] * d["steps"] * d["nodes"] * BYTES_PER_DOF_STEP[k])
 
     k_dom = max(range(len(members)), key=lambda k: alg_bytes(members[k]))
     dom = members[k_dom]
     dom_ms = statistics.mean(p[k_dom]["kernel_ms"] for p in profiles)
     achieved = alg_bytes(dom) / (dom_ms / 1000.0) / 1e9
     hbm = peaks.get("hbm_gbs", 6800.0)
-    if dom["resident"] == 2:
+    if dom["resident"] == 3:
+        kname = f"slab_solve_mg_kernel<{dom['cluster']},{dom.get('npt', 0)}>"
+    elif dom["resident"] == 2:
         kname = f"slab_solve_reg_kernel<{dom['cluster']},{dom.get('npt', 0)}>"
     else:
         kname = (f"slab_solve_kernel<{'float' if pkey == 'mixed' else 'double'},{dom['cluster']},"
                  f"{'true' if dom['resident'] else 'false'}>")
-    traffic = load_traffic(f"slab_solve_reg_kernel<{dom['cluster']}>" if dom["resident"] == 2 else kname,
-                           dom["samples"], dom["steps"])
+    traffic = load_traffic(kname, dom["samples"], dom["steps"])
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "traffic": traffic, "kernel": kname,
             "launch": f"level {dom['level']} {'coarse' if dom['coarse'] else 'fine'} member, "
@@ -376,10 +387,11 @@ def main():
                       f"{dom['cg_iterations']} CG iterations, cluster {dom['cluster']}",
             "kernel_ms": dom_ms, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks
             else "fallback 6800 GB/s",
-            "note": ("algorithmic bytes of a memory-streaming PCG (56 B per DOF and CG iteration + 64 B per "
-                     "DOF and block) over the kernel's event time; the kernel keeps its vectors in "
-                     "registers and shared memory, so its DRAM traffic is far below these bytes"
-                     if dom["resident"] else "algorithmic bytes over event time")}
+            "note": (f"algorithmic bytes of a memory-streaming {solver(dom)} PCG "
+                     f"({BYTES_PER_DOF_ITER[solver(dom)]:.0f} B per DOF and CG iteration + "
+                     f"{BYTES_PER_DOF_STEP[solver(dom)]:.0f} B per DOF and block) over the kernel's event time; "
+                     "the kernel keeps its vectors in registers and shared memory, so its DRAM traffic is far "
+                     "below these bytes" if dom["resident"] else "algorithmic bytes over event time")}
     mean, var, rmse = results[-1]
 
     # ---- plain FP64 on the same inputs, for the same estimate

@@ -87,7 +87,13 @@ typedef struct {
  *              sequence into a CUDA graph and replays it while the
  *              configuration, sizes and pointers are unchanged (needs a
  *              non-NULL stream in mlq_create and device xi / y arrays;
- *              otherwise it runs eagerly).  0 = always eager. */
+ *              otherwise it runs eagerly).  0 = always eager.
+ *   precond    preconditioner of the inner PCG in the mixed path: 0 = Jacobi,
+ *              1 = geometric multigrid V(1,1) on the nested hierarchy of the
+ *              level's mesh (Galerkin coarse operators, damped Jacobi
+ *              smoothing), distributed over the sample's cluster; used when
+ *              its shared-memory layout fits, else Jacobi.  The FP64 path
+ *              always uses Jacobi (the oracle's preconditioner). */
 typedef struct {
     int precision;
     double rtol;
@@ -98,10 +104,13 @@ typedef struct {
     int threads;
     int storage;
     int graphs;
+    int precond;
 } mlq_options;
 
 /* Fill *opt / *model with the defaults listed above (rtol 1e-13 for FP64,
- * rtol 1e-12 and rtol_inner 1e-5 for MIXED, max_iter 100000, max_sweeps 20). */
+ * rtol 1e-12 and rtol_inner 1e-5 for MIXED, max_iter 100000, max_sweeps 20,
+ * precond 1 (multigrid) for MIXED and 0 for FP64; mlq_solve_noalloc always
+ * uses the Jacobi inner preconditioner). */
 int mlq_default_options(mlq_options *opt, int precision);
 int mlq_default_model(mlq_model *model);
 
@@ -260,9 +269,10 @@ int mlq_solve_noalloc(int m, double dt, int32_t nsteps, const mlq_model *model, 
 int mlq_launch_count(mlq_ctx *ctx, int64_t *count);
 
 /* Launch shape chosen for a level under the context's options: cluster size
- * (CTAs per sample), threads per CTA, and *resident: 2 = the sample's PCG
- * vectors live in registers with the stencil rows in shared memory (mixed
- * path), 1 = vectors in the cluster's shared memory, 0 = in global memory.
+ * (CTAs per sample), threads per CTA, and *resident: 3 = register kernel
+ * with the multigrid preconditioner, 2 = the sample's PCG vectors live in
+ * registers with the stencil rows in shared memory (mixed path), 1 = vectors
+ * in the cluster's shared memory, 0 = in global memory.
  * resident may be NULL. */
 int mlq_level_launch(mlq_ctx *ctx, int level, int *cluster, int *threads, int *resident);
 

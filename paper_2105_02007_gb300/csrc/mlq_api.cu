@@ -41,6 +41,7 @@ struct Level {
     double radius = 0.1;
     mlq::FastDiv divm{};
     int tuned_cs = 0, tuned_npt = 0, tuned_threads = 0;  // set by mlq_autotune (mixed path)
+    bool tuned_mg = false;
 };
 
 struct Member {
@@ -51,7 +52,20 @@ struct Member {
     double *cs2 = nullptr, *A64 = nullptr, *v = nullptr, *w = nullptr, *b = nullptr, *q = nullptr;
     void *Ai = nullptr, *r = nullptr, *s = nullptr, *wc = nullptr, *p = nullptr, *x = nullptr;
     int32_t *iters = nullptr, *status = nullptr;
+    float *mgA[mlq::kMgMaxLevels] = {};    // coarse-level stencils (multigrid)
+    mlq::D3 *mgD[mlq::kMgMaxLevels] = {};  // coarse-level mean conductivities
 };
+
+// multigrid levels below the fine one: m_c = (m_{c-1} + 1) / 2 while m_c >= 3
+int mg_coarse_levels(int m)
+{
+    int c = 0;
+    while (c + 1 < mlq::kMgMaxLevels && m >= 5 && (m - 1) % 2 == 0) {
+        m = (m + 1) / 2;
+        ++c;
+    }
+    return c;
+}
 
 }  // namespace
 
@@ -133,6 +147,7 @@ struct Shape {
     bool resident;
     size_t smem;
     int npt;  // > 0: register-resident mixed kernel with this many nodes per thread
+    bool mg = false;  // register kernel with the multigrid preconditioner
 };
 
 // nodes-per-thread variants compiled for the register-resident kernel
@@ -162,14 +177,50 @@ std::vector<Shape> reg_candidates(const mlq_ctx *ctx, const Level &L)
     return out;
 }
 
+// Multigrid candidates: every cluster size whose multigrid layout fits.
+std::vector<Shape> mg_candidates(const mlq_ctx *ctx, const Level &L)
+{
+    std::vector<Shape> out;
+    const int limit = ctx->smem_optin - 2048;
+    for (int c = 1; c <= ctx->max_cluster; c *= 2) {
+        if (c > L.m) break;
+        const mlq::MgPlan mp = mlq::mg_plan(L.m, c);
+        if (mp.total > limit) continue;
+        const int nmax = mp.lv[0].rows_max * L.m;
+        for (int npt : {4, 8, 12}) {
+            int th = ((nmax + npt - 1) / npt + 31) / 32 * 32;
+            if (th < 32) th = 32;
+            if (th > npt_max_threads(npt)) continue;
+            Shape sh{c, th, true, (size_t)mp.total, npt};
+            sh.mg = true;
+            out.push_back(sh);
+            break;
+        }
+    }
+    return out;
+}
+
 Shape choose_launch(mlq_ctx *ctx, const Level &L, int64_t S = 0)
 {
+    if (ctx->opt.precision == MLQ_MIXED && ctx->opt.precond == 1 && ctx->opt.storage != 2) {
+        if (L.tuned_cs > 0 && L.tuned_mg && ctx->opt.cluster <= 0 && ctx->opt.threads <= 0) {
+            Shape sh{L.tuned_cs, L.tuned_threads, true, (size_t)mlq::mg_plan(L.m, L.tuned_cs).total, L.tuned_npt};
+            sh.mg = true;
+            return sh;
+        }
+        std::vector<Shape> cand = mg_candidates(ctx, L);
+        for (const Shape &c : cand)
+            if (ctx->opt.cluster <= 0 || c.cs == ctx->opt.cluster) return c;
+    }
+    if (L.tuned_mg && ctx->opt.precond != 1) {
+        // a multigrid tuning does not apply to the Jacobi kernel
+    }
     const int ti = ctx->opt.precision == MLQ_MIXED ? 4 : 8;
     const int limit = ctx->smem_optin - 2048;  // room for the static reduction buffers
     const bool allow = ctx->opt.storage != 2;
     // mixed path: the register-resident kernel when a shape fits
     if (ti == 4 && allow) {
-        if (L.tuned_cs > 0 && ctx->opt.cluster <= 0 && ctx->opt.threads <= 0) {
+        if (L.tuned_cs > 0 && !L.tuned_mg && ctx->opt.cluster <= 0 && ctx->opt.threads <= 0) {
             const mlq::RegPlan rp = mlq::reg_plan(L.m, L.tuned_cs);
             return Shape{L.tuned_cs, L.tuned_threads, true, (size_t)rp.total, L.tuned_npt};
         }
@@ -257,6 +308,19 @@ cudaError_t launch_reg_any(int cs, int npt, const mlq::SolveArgs<float> &a, int 
     }
 }
 
+cudaError_t launch_mg_any(int cs, int npt, const mlq::SolveArgs<float> &a, const mlq::MgPtrs &ptrs,
+                          const mlq::MgPlan &plan, int ncl, int threads, cudaStream_t st)
+{
+    switch (cs) {
+    case 1: return mlq::launch_mg_cs1(npt, a, ptrs, plan, ncl, threads, st);
+    case 2: return mlq::launch_mg_cs2(npt, a, ptrs, plan, ncl, threads, st);
+    case 4: return mlq::launch_mg_cs4(npt, a, ptrs, plan, ncl, threads, st);
+    case 8: return mlq::launch_mg_cs8(npt, a, ptrs, plan, ncl, threads, st);
+    case 16: return mlq::launch_mg_cs16(npt, a, ptrs, plan, ncl, threads, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 int max_active_clusters_reg(mlq_ctx *ctx, int cs, int npt, int threads, size_t smem)
 {
     (void)ctx;
@@ -300,6 +364,14 @@ size_t member_bytes(const mlq_ctx *ctx, const Level &L, int64_t S)
     add((size_t)S * 8);                     // q
     add((size_t)S * 4);                     // iters
     add((size_t)S * 4);                     // status
+    if (mixed && ctx->opt.precond == 1) {
+        int mc = L.m;
+        for (int c = 1; c <= mg_coarse_levels(L.m); ++c) {
+            mc = (mc + 1) / 2;
+            add((size_t)S * mlq::kSlots2D * mc * mc * 4);
+            add((size_t)S * 2 * (mc - 1) * (mc - 1) * sizeof(mlq::D3));
+        }
+    }
     return t;
 }
 
@@ -327,6 +399,14 @@ void member_carve(const mlq_ctx *ctx, const Level &L, Member &mb, char *&cur)
     mb.q = (double *)take((size_t)mb.S * 8);
     mb.iters = (int32_t *)take((size_t)mb.S * 4);
     mb.status = (int32_t *)take((size_t)mb.S * 4);
+    if (mixed && ctx->opt.precond == 1) {
+        int mc = L.m;
+        for (int c = 1; c <= mg_coarse_levels(L.m); ++c) {
+            mc = (mc + 1) / 2;
+            mb.mgA[c] = (float *)take((size_t)mb.S * mlq::kSlots2D * mc * mc * 4);
+            mb.mgD[c] = (mlq::D3 *)take((size_t)mb.S * 2 * (mc - 1) * (mc - 1) * sizeof(mlq::D3));
+        }
+    }
 }
 
 int ensure_workspace(mlq_ctx *ctx, size_t bytes)
@@ -426,7 +506,26 @@ int launch_member_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream_t
     const unsigned evf = ctx->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (timed) MLQ_CUDA(ctx, cudaEventRecordWithFlags(ctx->ev_t0[slot], st, evf));
     if constexpr (sizeof(TI) == 4) {
-        if (sh.npt > 0)
+        if (sh.mg) {
+            const mlq::MgPlan mp = mlq::mg_plan(L.m, sh.cs);
+            mlq::MgPtrs ptrs{};
+            int mc = L.m;
+            for (int c = 1; c < mp.nl; ++c) {
+                const int mf = mc;
+                mc = (mc + 1) / 2;
+                const int nec = 2 * (mc - 1) * (mc - 1);
+                mlq::mg_coarsen_kernel<<<dim3((unsigned)((nec + 255) / 256), (unsigned)mb.S), 256, 0, st>>>(
+                    c == 1 ? mb.cs2 : nullptr, c == 1 ? nullptr : mb.mgD[c - 1], mf, (int)mb.S, ctx->model.s_l,
+                    ctx->model.s_t, mb.mgD[c]);
+                mlq::mg_stencil_kernel<<<dim3((unsigned)((mc * mc + 255) / 256), (unsigned)mb.S), 256, 0, st>>>(
+                    mb.mgD[c], mc, L.dt, (int)mb.S, mb.mgA[c]);
+                MLQ_CUDA(ctx, cudaGetLastError());
+                ctx->launches += 2;
+                ptrs.A[c] = mb.mgA[c];
+            }
+            if (timed) MLQ_CUDA(ctx, cudaEventRecordWithFlags(ctx->ev_t0[slot], st, evf));
+            MLQ_CUDA(ctx, launch_mg_any(sh.cs, sh.npt, a, ptrs, mp, (int)mb.S, sh.threads, st));
+        } else if (sh.npt > 0)
             MLQ_CUDA(ctx, launch_reg_any(sh.cs, sh.npt, a, (int)mb.S, sh.threads, sh.smem, st));
         else
             MLQ_CUDA(ctx, launch_slab_cs<TI>(sh.cs, a, (int)mb.S, sh.threads, sh.smem, sh.resident, st));
@@ -446,7 +545,7 @@ int launch_member(mlq_ctx *ctx, const Member &mb, cudaStream_t st, int slot, int
         ctx->prof_level[slot] = mb.level;
         ctx->prof_coarse[slot] = coarse;
         ctx->prof_cs[slot] = sh.cs;
-        ctx->prof_resident[slot] = sh.npt > 0 ? 2 : (sh.resident ? 1 : 0);
+        ctx->prof_resident[slot] = sh.mg ? 3 : (sh.npt > 0 ? 2 : (sh.resident ? 1 : 0));
         ctx->prof_threads[slot] = sh.threads;
         ctx->prof_npt[slot] = sh.npt;
         ctx->prof_samples[slot] = mb.S;
@@ -496,7 +595,7 @@ void launch_member_profile_only(mlq_ctx *ctx, const Member &mb, int slot, int co
     ctx->prof_level[slot] = mb.level;
     ctx->prof_coarse[slot] = coarse;
     ctx->prof_cs[slot] = sh.cs;
-    ctx->prof_resident[slot] = sh.npt > 0 ? 2 : (sh.resident ? 1 : 0);
+    ctx->prof_resident[slot] = sh.mg ? 3 : (sh.npt > 0 ? 2 : (sh.resident ? 1 : 0));
     ctx->prof_threads[slot] = sh.threads;
     ctx->prof_npt[slot] = sh.npt;
     ctx->prof_samples[slot] = mb.S;
@@ -542,6 +641,7 @@ int mlq_default_options(mlq_options *opt, int precision)
     opt->threads = 0;
     opt->storage = 0;
     opt->graphs = 0;
+    opt->precond = precision == MLQ_MIXED ? 1 : 0;
     return MLQ_OK;
 }
 
@@ -566,6 +666,7 @@ static int validate_options(const mlq_options *o)
         return MLQ_EINVAL;
     if (o->threads != 0 && (o->threads < 64 || o->threads > 512 || o->threads % 32)) return MLQ_EINVAL;
     if (o->storage < 0 || o->storage > 2) return MLQ_EINVAL;
+    if (o->precond < 0 || o->precond > 1) return MLQ_EINVAL;
     return MLQ_OK;
 }
 
@@ -1057,7 +1158,7 @@ int mlq_autotune(mlq_ctx *ctx, int level, int64_t S, const double *xi, int probe
     if (check_level(ctx, level) != MLQ_OK) return MLQ_EINVAL;
     if (ctx->opt.precision != MLQ_MIXED || ctx->opt.storage == 2) return MLQ_EUNSUPPORTED;
     Level &L = ctx->levels[level];
-    std::vector<Shape> cand = reg_candidates(ctx, L);
+    std::vector<Shape> cand = ctx->opt.precond == 1 ? mg_candidates(ctx, L) : reg_candidates(ctx, L);
     if (cand.empty()) return MLQ_EUNSUPPORTED;
     // also try the next nodes-per-thread variant of each cluster size
     const size_t nbase = cand.size();
@@ -1069,12 +1170,16 @@ int mlq_autotune(mlq_ctx *ctx, int level, int64_t S, const double *xi, int probe
             int th = ((rp.nmax + npt - 1) / npt + 31) / 32 * 32;
             if (th < 32) th = 32;
             if (th > npt_max_threads(npt)) continue;
-            cand.push_back(Shape{c.cs, th, true, c.smem, npt});
+            if (c.mg && npt > 12) break;
+            Shape sh{c.cs, th, true, c.smem, npt};
+            sh.mg = c.mg;
+            cand.push_back(sh);
             break;
         }
     }
     const int saved_steps = L.nsteps;
     const int saved_cs = L.tuned_cs, saved_npt = L.tuned_npt, saved_th = L.tuned_threads;
+    const bool saved_mg = L.tuned_mg;
     const mlq_options saved_opt = ctx->opt;
     ctx->opt.cluster = 0;
     ctx->opt.threads = 0;
@@ -1090,6 +1195,7 @@ int mlq_autotune(mlq_ctx *ctx, int level, int64_t S, const double *xi, int probe
             L.tuned_cs = c.cs;
             L.tuned_npt = c.npt;
             L.tuned_threads = c.threads;
+            L.tuned_mg = c.mg;
             if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) { st = MLQ_ECUDA; break; }
             st = mlq_solve(ctx, level, S, xi, 0, nullptr, nullptr, nullptr, nullptr, nullptr);
             if (st != MLQ_OK) break;
@@ -1111,11 +1217,13 @@ int mlq_autotune(mlq_ctx *ctx, int level, int64_t S, const double *xi, int probe
         L.tuned_cs = saved_cs;
         L.tuned_npt = saved_npt;
         L.tuned_threads = saved_th;
+        L.tuned_mg = saved_mg;
         return st;
     }
     L.tuned_cs = pick.cs;
     L.tuned_npt = pick.npt;
     L.tuned_threads = pick.threads;
+    L.tuned_mg = pick.mg;
     ctx->generation++;
     if (cluster_out) *cluster_out = pick.cs;
     if (threads_out) *threads_out = pick.threads;
@@ -1284,7 +1392,7 @@ int mlq_level_launch(mlq_ctx *ctx, int level, int *cluster, int *threads, int *r
     const Shape sh = choose_launch(ctx, ctx->levels[level]);
     *cluster = sh.cs;
     *threads = sh.threads;
-    if (resident) *resident = sh.npt > 0 ? 2 : (sh.resident ? 1 : 0);
+    if (resident) *resident = sh.mg ? 3 : (sh.npt > 0 ? 2 : (sh.resident ? 1 : 0));
     return MLQ_OK;
 }
 

@@ -9,6 +9,7 @@
 #pragma once
 
 #include "mlq_kernels.cuh"
+#include "mlq_mg.cuh"
 
 namespace mlq {
 
@@ -177,6 +178,106 @@ __global__ void merge_status_kernel(const int32_t *__restrict__ a, const int32_t
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= S) return;
     out[k] = c ? (a[k] > c[k] ? a[k] : c[k]) : a[k];
+}
+
+// ---------------------------------------------------------------------------
+// Multigrid set-up (see mlq_mg.cuh): coarse conductivities and stencils.
+// ---------------------------------------------------------------------------
+// Dbar of level c >= 1 from level c-1 (level 0 given as cos/sin(2 theta)).
+// The four children of coarse square (I, J) in the finer mesh:
+//   lower(I,J): lower(2I,2J), lower(2I+1,2J), lower(2I+1,2J+1), upper(2I+1,2J)
+//   upper(I,J): upper(2I,2J), upper(2I,2J+1), upper(2I+1,2J+1), lower(2I,2J+1)
+__global__ void mg_coarsen_kernel(const double *__restrict__ cs2, const D3 *__restrict__ dfine, int mf, int S,
+                                  double s_l, double s_t, D3 *__restrict__ dcoarse)
+{
+    const int mc = (mf + 1) / 2;
+    const int nec = 2 * (mc - 1) * (mc - 1), nef = 2 * (mf - 1) * (mf - 1);
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.y;
+    if (e >= nec || s >= S) return;
+    const int cell = e >> 1, up = e & 1;
+    const int I = cell % (mc - 1), J = cell / (mc - 1);
+    const int cf = mf - 1;
+    auto el = [&](int ci, int cj, int u) { return 2 * (ci + cf * cj) + u; };
+    int ch[4];
+    if (!up) {
+        ch[0] = el(2 * I, 2 * J, 0);
+        ch[1] = el(2 * I + 1, 2 * J, 0);
+        ch[2] = el(2 * I + 1, 2 * J + 1, 0);
+        ch[3] = el(2 * I + 1, 2 * J, 1);
+    } else {
+        ch[0] = el(2 * I, 2 * J, 1);
+        ch[1] = el(2 * I, 2 * J + 1, 1);
+        ch[2] = el(2 * I + 1, 2 * J + 1, 1);
+        ch[3] = el(2 * I, 2 * J + 1, 0);
+    }
+    double a = 0.0, b = 0.0, c = 0.0;
+    if (cs2) {
+        const double sbar = 0.5 * (s_l + s_t), hds = 0.5 * (s_l - s_t);
+        for (int k = 0; k < 4; ++k) {
+            const double *q = cs2 + ((size_t)s * nef + ch[k]) * 2;
+            a += sbar + hds * q[0];
+            b += hds * q[1];
+            c += sbar - hds * q[0];
+        }
+    } else {
+        for (int k = 0; k < 4; ++k) {
+            const D3 d = dfine[(size_t)s * nef + ch[k]];
+            a += d.a;
+            b += d.b;
+            c += d.c;
+        }
+    }
+    dcoarse[(size_t)s * nec + e] = D3{(float)(0.25 * a), (float)(0.25 * b), (float)(0.25 * c)};
+}
+
+// FP32 stencil (diag, E, N, NE, 1/diag) of A_c = M_c + dt K_c(Dbar_c) on the
+// m x m level (same element formulas as stencil_setup_kernel).
+__global__ void mg_stencil_kernel(const D3 *__restrict__ dbar, int m, double dt, int S, float *__restrict__ A)
+{
+    const int n = m * m;
+    const int node = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.y;
+    if (node >= n || s >= S) return;
+    const int i = node % m, j = node / m;
+    const int mc = m - 1, ne = 2 * mc * mc;
+    const double h = 1.0 / (double)(m - 1);
+    const double mdiag = h * h / 12.0, moff = h * h / 24.0;
+    const D3 *d = dbar + (size_t)s * ne;
+    auto el = [&](int ci, int cj, int u) { return d[2 * (ci + mc * cj) + u]; };
+    double diag = 0.0, east = 0.0, north = 0.0, nea = 0.0;
+    if (i < mc && j < mc) {
+        D3 D = el(i, j, 0);
+        diag += 0.5 * D.a * dt + mdiag;
+        east += -0.5 * (D.a - D.b) * dt + moff;
+        nea += -0.5 * D.b * dt + moff;
+        D = el(i, j, 1);
+        diag += 0.5 * D.c * dt + mdiag;
+        nea += -0.5 * D.b * dt + moff;
+        north += 0.5 * (D.b - D.c) * dt + moff;
+    }
+    if (i >= 1 && j < mc) {
+        const D3 D = el(i - 1, j, 0);
+        diag += 0.5 * (D.a - 2.0 * D.b + D.c) * dt + mdiag;
+        north += 0.5 * (D.b - D.c) * dt + moff;
+    }
+    if (i >= 1 && j >= 1) {
+        D3 D = el(i - 1, j - 1, 0);
+        diag += 0.5 * D.c * dt + mdiag;
+        D = el(i - 1, j - 1, 1);
+        diag += 0.5 * D.a * dt + mdiag;
+    }
+    if (i < mc && j >= 1) {
+        const D3 D = el(i, j - 1, 1);
+        diag += 0.5 * (D.a - 2.0 * D.b + D.c) * dt + mdiag;
+        east += -0.5 * (D.a - D.b) * dt + moff;
+    }
+    float *a = A + (size_t)s * kSlots2D * n;
+    a[node] = (float)diag;
+    a[n + node] = (float)east;
+    a[2 * n + node] = (float)north;
+    a[3 * n + node] = (float)nea;
+    a[4 * n + node] = (float)(1.0 / diag);
 }
 
 }  // namespace mlq

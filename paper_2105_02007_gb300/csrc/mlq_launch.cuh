@@ -10,13 +10,16 @@
 #include <cuda_runtime.h>
 
 #include "mlq_kernels.cuh"
+#include "mlq_mg.cuh"
 
 namespace mlq {
 
 #define MLQ_DECLARE_REG(CS)                                                                                   \
     cudaError_t launch_reg_cs##CS(int npt, const SolveArgs<float> &a, int nclusters, int threads, size_t smem, \
                                   cudaStream_t st);                                                           \
-    int active_reg_cs##CS(int npt, int threads, size_t smem);
+    int active_reg_cs##CS(int npt, int threads, size_t smem);                                                  \
+    cudaError_t launch_mg_cs##CS(int npt, const SolveArgs<float> &a, const MgPtrs &ptrs, const MgPlan &plan,  \
+                                 int nclusters, int threads, cudaStream_t st);
 MLQ_DECLARE_REG(1)
 MLQ_DECLARE_REG(2)
 MLQ_DECLARE_REG(4)
@@ -30,8 +33,8 @@ cudaError_t launch_slab_f64(int cs, bool resident, const SolveArgs<double> &a, i
                             size_t smem, cudaStream_t st);
 
 // cluster launch of `kern` with CS CTAs per cluster
-template <int CS, typename K, typename A>
-cudaError_t cluster_launch(K kern, const A &args, int nclusters, int threads, size_t smem, cudaStream_t st)
+template <int CS, typename K, typename... A>
+cudaError_t cluster_launch(K kern, int nclusters, int threads, size_t smem, cudaStream_t st, const A &...args)
 {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -51,7 +54,7 @@ cudaError_t cluster_launch(K kern, const A &args, int nclusters, int threads, si
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, args);
+    return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
 // clusters of `kern` that can be resident at once (0 if none / on error)

@@ -15,10 +15,23 @@ cudaError_t MLQ_CAT(launch_reg_cs, MLQ_CS)(int npt, const SolveArgs<float> &a, i
                                            size_t smem, cudaStream_t st)
 {
     switch (npt) {
-    case 4: return cluster_launch<MLQ_CS>(slab_solve_reg_kernel<MLQ_CS, 4>, a, nclusters, threads, smem, st);
-    case 8: return cluster_launch<MLQ_CS>(slab_solve_reg_kernel<MLQ_CS, 8>, a, nclusters, threads, smem, st);
-    case 12: return cluster_launch<MLQ_CS>(slab_solve_reg_kernel<MLQ_CS, 12>, a, nclusters, threads, smem, st);
-    case 17: return cluster_launch<MLQ_CS>(slab_solve_reg_kernel<MLQ_CS, 17>, a, nclusters, threads, smem, st);
+    case 4: return cluster_launch<MLQ_CS>(slab_solve_reg_kernel<MLQ_CS, 4>, nclusters, threads, smem, st, a);
+    case 8: return cluster_launch<MLQ_CS>(slab_solve_reg_kernel<MLQ_CS, 8>, nclusters, threads, smem, st, a);
+    case 12: return cluster_launch<MLQ_CS>(slab_solve_reg_kernel<MLQ_CS, 12>, nclusters, threads, smem, st, a);
+    case 17: return cluster_launch<MLQ_CS>(slab_solve_reg_kernel<MLQ_CS, 17>, nclusters, threads, smem, st, a);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t MLQ_CAT(launch_mg_cs, MLQ_CS)(int npt, const SolveArgs<float> &a, const MgPtrs &ptrs,
+                                          const MgPlan &plan, int nclusters, int threads, cudaStream_t st)
+{
+    const size_t smem = (size_t)plan.total;
+    switch (npt) {
+    case 4: return cluster_launch<MLQ_CS>(slab_solve_mg_kernel<MLQ_CS, 4>, nclusters, threads, smem, st, a, ptrs, plan);
+    case 8: return cluster_launch<MLQ_CS>(slab_solve_mg_kernel<MLQ_CS, 8>, nclusters, threads, smem, st, a, ptrs, plan);
+    case 12:
+        return cluster_launch<MLQ_CS>(slab_solve_mg_kernel<MLQ_CS, 12>, nclusters, threads, smem, st, a, ptrs, plan);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -21,8 +21,8 @@ template <int CS>
 static cudaError_t launch_cs(bool resident, const SolveArgs<TI> &a, int nclusters, int threads, size_t smem,
                              cudaStream_t st)
 {
-    if (resident) return cluster_launch<CS>(slab_solve_kernel<TI, CS, true>, a, nclusters, threads, smem, st);
-    return cluster_launch<CS>(slab_solve_kernel<TI, CS, false>, a, nclusters, threads, smem, st);
+    if (resident) return cluster_launch<CS>(slab_solve_kernel<TI, CS, true>, nclusters, threads, smem, st, a);
+    return cluster_launch<CS>(slab_solve_kernel<TI, CS, false>, nclusters, threads, smem, st, a);
 }
 
 cudaError_t MLQ_LAUNCH_SLAB(int cs, bool resident, const SolveArgs<TI> &a, int nclusters, int threads, size_t smem,

@@ -28,7 +28,8 @@ S_CONVERGED, S_MAXITER, S_NONFINITE, S_CANCELLED = 0, 1, 2, 3
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("rtol", ctypes.c_double), ("rtol_inner", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("max_sweeps", ctypes.c_int), ("cluster", ctypes.c_int),
-                ("threads", ctypes.c_int), ("storage", ctypes.c_int), ("graphs", ctypes.c_int)]
+                ("threads", ctypes.c_int), ("storage", ctypes.c_int), ("graphs", ctypes.c_int),
+                ("precond", ctypes.c_int)]
 
 
 class Model(ctypes.Structure):

@@ -51,10 +51,13 @@ def c1():
     return dict(mesh=mesh, phi=phi, xi=xi, q=q)
 
 
+@pytest.mark.parametrize("precond", [0, 1])
 @pytest.mark.parametrize("storage", [1, 2])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_c1_full_config_parity(mlq, c1, prec, storage):
-    with mlq.Context(0, prec, storage=storage) as ctx:
+def test_c1_full_config_parity(mlq, c1, prec, storage, precond):
+    if prec == 0 and precond == 1:
+        pytest.skip("the FP64 path uses Jacobi only")
+    with mlq.Context(0, prec, storage=storage, precond=precond) as ctx:
         ctx.add_level(0, 33, 0.05, 200)
         ctx.set_kl(0, c1["phi"])
         r = ctx.solve(0, c1["xi"])
@@ -84,7 +87,7 @@ def test_launch_shapes_random_state(mlq, prec, m, cluster, threads, storage):
     q_ref, _, st = O.solve_batch(mesh, phi, xi, 0.1, 15, v0=v0, w0=w0, theta_mean=tm)
     assert np.all(st == 0)
     try:
-        ctx = mlq.Context(0, prec, cluster=cluster, threads=threads, storage=storage)
+        ctx = mlq.Context(0, prec, cluster=cluster, threads=threads, storage=storage, precond=0)
     except mlq.MLQError as e:
         if e.code == -6:
             pytest.skip("cluster size not available on this device")
@@ -316,14 +319,15 @@ def test_mlmc_estimate_matches_oracle(mlq, prec):
     assert abs(rmse - rmse_ref) < (1e-2 if prec else 1e-6) * rmse_ref
 
 
+@pytest.mark.parametrize("precond", [0, 1])
 @pytest.mark.parametrize("m", [17, 65])
-def test_autotune_keeps_parity(mlq, m):
+def test_autotune_keeps_parity(mlq, m, precond):
     mesh = O.mesh2d(m)
     modes, _ = O.kl_build(mesh, 0.09, 0.04, 6)
     phi = O.centroid_table(mesh, modes, mesh)
     xi = inputs.gaussian_xi(5, 0, 0, 6, 6)
     q_ref = O.solve_batch(mesh, phi, xi, 0.05, 6)[0]
-    with mlq.Context(0, 1) as ctx:
+    with mlq.Context(0, 1, precond=precond) as ctx:
         ctx.add_level(0, m, 0.05, 6)
         ctx.set_kl(0, phi)
         cs, th, ms = ctx.autotune(0, xi, probe_steps=2)
@@ -392,3 +396,37 @@ def test_estimate_graph_capture_and_replay(mlq):
             res[graphs] = (first, third)
     assert res[0][0][0] == res[1][0][0]
     assert res[0][1][0] == res[1][1][0] and res[0][1][0] != res[0][0][0]
+
+
+# --------------------------------------------------------------------------
+# Multigrid-preconditioned inner PCG (mixed path): same QoI as the oracle,
+# on every cluster size that fits, over the nested hierarchy of each mesh.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("m,cluster,steps", [(9, 1, 6), (17, 1, 10), (33, 2, 8), (65, 1, 6), (65, 4, 6),
+                                             (129, 4, 4), (257, 16, 3)])
+def test_multigrid_parity(mlq, m, cluster, steps):
+    mesh = O.mesh2d(m)
+    rng = np.random.default_rng(m + cluster)
+    K = 6
+    modes, _ = O.kl_build(mesh, 0.09, 0.04, K)
+    phi = O.centroid_table(mesh, modes, mesh)
+    v0 = rng.uniform(0, 1, size=mesh.n)
+    w0 = rng.uniform(0, 0.2, size=mesh.n)
+    dt = 0.1 * 16.0 / (m - 1)
+    xi = inputs.gaussian_xi(4, 0, 0, 3, K)
+    q_ref, _, st = O.solve_batch(mesh, phi, xi, dt, steps, v0=v0, w0=w0, nthreads=2)
+    assert np.all(st == 0)
+    try:
+        ctx = mlq.Context(0, mlq.MLQ_MIXED, precond=1, cluster=cluster)
+    except mlq.MLQError as e:
+        if e.code == -6:
+            pytest.skip("cluster size not available")
+        raise
+    with ctx:
+        ctx.add_level(0, m, dt, steps)
+        ctx.set_kl(0, phi)
+        ctx.set_initial_state(0, v0, w0)
+        assert ctx.level_launch(0, True)[2] == 3
+        r = ctx.solve(0, xi)
+    assert np.all(r["status"] == 0), r["status"]
+    assert rel(r["q_fine"], q_ref) < TOL[1]
