@@ -181,11 +181,11 @@ std::vector<Shape> reg_candidates(const mlq_ctx *ctx, const Level &L)
 std::vector<Shape> mg_candidates(const mlq_ctx *ctx, const Level &L)
 {
     std::vector<Shape> out;
-    const int limit = ctx->smem_optin - 2048;
+    const int limit = ctx->smem_optin - 3072;  // room for the static reduction buffers
     for (int c = 1; c <= ctx->max_cluster; c *= 2) {
         if (c > L.m) break;
         const mlq::MgPlan mp = mlq::mg_plan(L.m, c);
-        if (mp.total > limit) continue;
+        if (mp.nl == 0 || mp.total > limit) continue;
         const int nmax = mp.lv[0].rows_max * L.m;
         for (int npt : {4, 8, 12}) {
             int th = ((nmax + npt - 1) / npt + 31) / 32 * 32;
@@ -353,7 +353,7 @@ size_t member_bytes(const mlq_ctx *ctx, const Level &L, int64_t S)
     add((size_t)S * L.ne * 2 * 8);          // cs2
     add(sn * mlq::kSlots2D * 8);            // A64
     if (mixed) add(sn * mlq::kSlots2D * 4); // A32
-    add(sn * 8);                            // v
+    add((mixed && ctx->opt.precond == 1 ? 2 : 1) * sn * 8);  // v (multigrid: solution and guess)
     add(2 * sn * 8);                        // w
     add(sn * 8);                            // b
     add(2 * sn * ti);                       // r
@@ -388,7 +388,7 @@ void member_carve(const mlq_ctx *ctx, const Level &L, Member &mb, char *&cur)
     mb.cs2 = (double *)take((size_t)mb.S * L.ne * 2 * 8);
     mb.A64 = (double *)take(sn * mlq::kSlots2D * 8);
     mb.Ai = mixed ? take(sn * mlq::kSlots2D * 4) : (void *)mb.A64;
-    mb.v = (double *)take(sn * 8);
+    mb.v = (double *)take((mixed && ctx->opt.precond == 1 ? 2 : 1) * sn * 8);
     mb.w = (double *)take(2 * sn * 8);
     mb.b = (double *)take(sn * 8);
     mb.r = take(2 * sn * ti);
@@ -1166,8 +1166,8 @@ int mlq_autotune(mlq_ctx *ctx, int level, int64_t S, const double *xi, int probe
         const Shape c = cand[k];
         for (int npt : kNpt) {
             if (npt <= c.npt) continue;
-            const mlq::RegPlan rp = mlq::reg_plan(L.m, c.cs);
-            int th = ((rp.nmax + npt - 1) / npt + 31) / 32 * 32;
+            const int nmax = c.mg ? mlq::mg_plan(L.m, c.cs).lv[0].rows_max * L.m : mlq::reg_plan(L.m, c.cs).nmax;
+            int th = ((nmax + npt - 1) / npt + 31) / 32 * 32;
             if (th < 32) th = 32;
             if (th > npt_max_threads(npt)) continue;
             if (c.mg && npt > 12) break;

@@ -53,7 +53,7 @@ struct SolveArgs {
     int max_iter, max_sweeps;
     const double *A64;            // [S][4][n]
     const TI *Ai;                 // [S][4][n] stencil in the inner precision
-    double *v;                    // [S][n]
+    double *v;                    // [S][n]; [2][S][n] for the multigrid kernel
     double *w;                    // [2][S][n]
     double *b;                    // [S][n]
     TI *r, *s, *wc;               // [2][S][n] each

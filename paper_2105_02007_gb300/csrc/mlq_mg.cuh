@@ -13,10 +13,13 @@
 //     restriction P^T and interpolation P, a few damped Jacobi sweeps on the
 //     coarsest level: a fixed symmetric positive definite operator, so it can
 //     precondition CG.
-// Every level is distributed over the cluster exactly like the fine grid: a
-// CTA owns the rows J with 2J in its band of the finer level; halo rows come
-// from the neighbouring CTAs' shared memory over DSMEM after a cluster
-// barrier.
+// The fine levels are distributed over the cluster like the fine grid: a CTA
+// owns the rows J with 2J in its band of the finer level.  A CTA writes the
+// boundary rows it computes straight into its neighbours' halo rows (DSMEM
+// stores), so an exchange is one cluster barrier.  Once a level is small
+// (kMgGatherM nodes per side or fewer) its right-hand side is broadcast to
+// every CTA and the rest of the hierarchy runs redundantly in each CTA with
+// block barriers only.
 #pragma once
 
 #include "mlq_kernels.cuh"
@@ -24,7 +27,9 @@
 namespace mlq {
 
 constexpr int kMgMaxLevels = 8;
-constexpr float kMgOmega = 0.6f;
+constexpr float kMgOmega = 0.7f;   // lambda_max(D^-1 A) <= 2.5 on every level: omega lambda < 2
+constexpr int kMgGatherM = 17;        // gather levels of at most this many nodes per side
+constexpr int kMgCoarsestSweeps = 6;  // damped Jacobi sweeps on the coarsest level
 
 // Conductivity of an element as (d11, d12, d22).
 struct D3 {
@@ -37,21 +42,24 @@ struct D3 {
 //   band(c,r)    rows [R0, R1) of level c owned by cluster rank r: level 0
 //                splits the m rows evenly, level c takes the rows J with 2J in
 //                the band of level c-1
-// The hierarchy stops before a level where a band would be empty or m < 3.
+//   local        the level is held whole by every CTA (rows [0, m_c)); the
+//                first local level of a cluster is filled by a broadcast
 // Shared layout per level (bytes, the same in every CTA): four stencil
 // arrays D, E, N, NE (structure of arrays: conflict-free neighbour reads),
-// each 1 + (rows_max + 1) * m floats (pad, row R0-1, own rows); tiles XA, XB,
-// RR of 1 + (rows_max + 2) * m + 1 floats (pad, halo row R0-1, own rows,
-// halo row R1, pad); BB, rows_max * m floats (own rows only).
+// each 1 + (rows + 1) * m floats (pad, row R0-1, stored rows); tiles XA, XB,
+// RR of 1 + (rows + 2) * m + 1 floats (pad, halo row R0-1, stored rows, halo
+// row R1, pad); BB, rows * m floats (stored rows only).  rows is the largest
+// band over the ranks for a distributed level and m_c for a local one.
 // ---------------------------------------------------------------------------
 struct MgLevelPlan {
-    int m, rows_max;
+    int m, rows_max, local;
     int off_d, off_e, off_n, off_ne, off_xa, off_xb, off_r, off_b;
     int csize, tile;
 };
 
 struct MgPlan {
-    int nl;      // levels
+    int nl;      // levels (0: no valid layout)
+    int gather;  // first local level
     int total;   // bytes
     MgLevelPlan lv[kMgMaxLevels];
 };
@@ -77,8 +85,11 @@ __host__ __device__ inline MgPlan mg_plan(int m0, int cs)
 {
     MgPlan pl;
     pl.nl = 0;
+    pl.gather = 0;
+    pl.total = 0;
     int off = 0;
     int m = m0;
+    bool local = cs == 1;
     for (int c = 0; c < kMgMaxLevels; ++c) {
         int rmax = 0, rmin = 1 << 30;
         for (int r = 0; r < cs; ++r) {
@@ -87,12 +98,20 @@ __host__ __device__ inline MgPlan mg_plan(int m0, int cs)
             rmax = b - a > rmax ? b - a : rmax;
             rmin = b - a < rmin ? b - a : rmin;
         }
-        if (c > 0 && (rmin < 1 || m < 3)) break;
+        if (!local) {
+            if (c == 0 && rmin < 1) return pl;  // a rank without fine rows
+            if (c > 0 && (m <= kMgGatherM || rmin < 1)) {
+                local = true;
+                pl.gather = c;
+            }
+        }
+        const int rows = local ? m : rmax;
         MgLevelPlan &L = pl.lv[c];
         L.m = m;
-        L.rows_max = rmax;
-        L.csize = 1 + (rmax + 1) * m;
-        L.tile = 1 + (rmax + 2) * m + 1;
+        L.rows_max = rows;
+        L.local = local ? 1 : 0;
+        L.csize = 1 + (rows + 1) * m;
+        L.tile = 1 + (rows + 2) * m + 1;
         const int cb = align16(L.csize * 4), tb = align16(L.tile * 4);
         L.off_d = off;
         L.off_e = off + cb;
@@ -104,13 +123,75 @@ __host__ __device__ inline MgPlan mg_plan(int m0, int cs)
         L.off_r = off + 2 * tb;
         off += 3 * tb;
         L.off_b = off;
-        off += align16(rmax * m * 4);
+        off += align16(rows * m * 4);
         pl.nl = c + 1;
         if (m < 5 || (m - 1) % 2) break;
         m = (m + 1) / 2;
     }
+    // a cluster needs a local coarsest level (the coarsest sweeps are local)
+    if (cs > 1 && (pl.nl < 2 || !pl.lv[pl.nl - 1].local)) {
+        pl.nl = 0;
+        return pl;
+    }
     pl.total = off;
     return pl;
+}
+
+// Cluster sum for the multigrid kernel: every CTA writes its partial sums
+// into slot [rank] of every CTA's cs buffer, one cluster barrier, then each
+// CTA adds the CS slots in rank order (bitwise the same result in every CTA).
+template <int NV, int CS, typename TA, typename F>
+__device__ __forceinline__ void cluster_reduce_push(TA (&v)[NV], double (*wsl)[4], double (*cs)[16][4], int par,
+                                                    F &&fin)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) wsl[warp][k] = (double)v[k];
+    }
+    __syncthreads();
+    double acc[NV];
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] = lane < nwarp ? wsl[lane][k] : 0.0;
+        for (int o = 1; o < nwarp; o <<= 1) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+        }
+        // the butterfly leaves the total in lane 0 (and its group): give it
+        // to every lane, which pushes it to one rank
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] = __shfl_sync(0xffffffffu, acc[k], 0);
+    }
+    if constexpr (CS == 1) {
+        if (threadIdx.x == 0) fin(acc);
+    } else {
+        cg::cluster_group cl = cg::this_cluster();
+        const int rank = (int)cl.block_rank();
+        if (warp == 0 && lane < CS) {
+            double *dst = cl.map_shared_rank(&cs[par][rank][0], lane);
+#pragma unroll
+            for (int k = 0; k < NV; ++k) dst[k] = acc[k];
+        }
+        cl.sync();
+        if (warp == 0) {
+            double t[NV];
+#pragma unroll
+            for (int k = 0; k < NV; ++k) t[k] = lane < CS ? cs[par][lane][k] : 0.0;
+#pragma unroll
+            for (int o = 1; o < CS; o <<= 1) {
+#pragma unroll
+                for (int k = 0; k < NV; ++k) t[k] += __shfl_xor_sync(0xffffffffu, t[k], o);
+            }
+            if (lane == 0) fin(t);
+        }
+    }
+    __syncthreads();
 }
 
 template <int CS, int NPT>
@@ -119,9 +200,9 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double wsl[32][4];
-    __shared__ double csl[2][4];
+    __shared__ double csp[2][16][4];
     __shared__ Ctl ctl;
-    // per-level band of this CTA and of its neighbours
+    // per-level stored band of this CTA and the first row of rank - 1's band
     __shared__ int sR0[kMgMaxLevels], sR1[kMgMaxLevels], sLo[kMgMaxLevels];
 
     cg::cluster_group cl = cg::this_cluster();
@@ -132,14 +213,18 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1)
     const int NL = plan.nl;
     if (tid < NL) {
         int a, b;
-        mg_band(g.m, CS, rank, tid, &a, &b);
+        if (plan.lv[tid].local) {
+            a = 0;
+            b = plan.lv[tid].m;
+        } else {
+            mg_band(g.m, CS, rank, tid, &a, &b);
+        }
         sR0[tid] = a;
         sR1[tid] = b;
-        if (has_lo) {
+        sLo[tid] = 0;
+        if (has_lo && !plan.lv[tid].local) {
             mg_band(g.m, CS, rank - 1, tid, &a, &b);
             sLo[tid] = a;
-        } else {
-            sLo[tid] = 0;
         }
     }
     __syncthreads();
@@ -151,7 +236,7 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1)
     const size_t so = (size_t)sample * n;
     const size_t SN = (size_t)g.S * n;
     const double *A64 = g.A64 + (size_t)sample * kSlots2D * n;
-    double *v = g.v + so;
+    double *vb0 = g.v + so;   // [2][S][n]: solution of the last block, guess of the next
     double *wb0 = g.w + so;
     double *b = g.b + so;
 
@@ -189,34 +274,38 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1)
             v0 = (xx * xx + yy * yy <= g.radius2) ? 1.0 : 0.0;
             w0 = 0.0;
         }
-        v[node] = v0;
+        vb0[node] = v0;
         wb0[node] = w0;
     }
     cl.sync();
 
     // ---- helpers ----------------------------------------------------------
-    // import the halo rows of the tile at byte offset `off` on level c
-    auto exchange = [&](int c, int off) {
-        if constexpr (CS == 1) {
-            __syncthreads();
-        } else {
-            const int mc = plan.lv[c].m, R0 = sR0[c], R1 = sR1[c];
-            cl.sync();
-            float *T = F_(off);
-            if (has_lo) {
-                const float *nb = cl.map_shared_rank(T, rank - 1);
-                const int src = 1 + mc + (R0 - 1 - sLo[c]) * mc;   // rank-1's last own row
-                for (int i = tid; i < mc; i += nt) T[1 + i] = nb[src + i];
+    // barrier after the rows of a level were written (and pushed)
+    auto level_sync = [&](bool dist) {
+        if constexpr (CS > 1) {
+            if (dist) {
+                cl.sync();
+                return;
             }
-            if (has_hi) {
-                const float *nb = cl.map_shared_rank(T, rank + 1);
-                const int dst = 1 + mc + (R1 - R0) * mc;
-                for (int i = tid; i < mc; i += nt) T[dst + i] = nb[1 + mc + i];
+        }
+        __syncthreads();
+    };
+    // value of own row-local index l (stored rows of level c) of the tile at
+    // byte offset off, also written into the neighbours' halo rows
+    auto push = [&](int c, int off, int mc, int rows, int l, float val) {
+        if constexpr (CS > 1) {
+            if (has_lo && l < mc) {
+                float *nb = cl.map_shared_rank(F_(off), rank - 1);
+                nb[1 + mc + (sR0[c] - sLo[c]) * mc + l] = val;   // rank-1's halo row R1
             }
-            __syncthreads();
+            const int last = (rows - 1) * mc;
+            if (has_hi && l >= last) {
+                float *nb = cl.map_shared_rank(F_(off), rank + 1);
+                nb[1 + (l - last)] = val;                          // rank+1's halo row R0-1
+            }
         }
     };
-    // (A x)_t on level c, t = tile index of an own node (= stencil index + 0)
+    // (A x)_t on level c, t = tile index of a stored node
     auto spmv = [&](const float *Dd, const float *Ee, const float *Nn, const float *NE, int mc, const float *x,
                     int t) {
         float w = Dd[t] * x[t];
@@ -229,48 +318,50 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1)
         return w;
     };
 
-    // V-cycle on BB of level 0 (own rows), result in XA of level 0
+    // V-cycle on BB of level 0 (own rows); the result is left in the RR tile
+    // of level 0 (own rows and halo rows).
+    //   descend, level c:  XA = omega D^-1 BB (pushed), RR = BB - A XA
+    //                      (pushed), BB_{c+1} = P^T RR
+    //   coarsest:          damped Jacobi sweeps from XA
+    //   ascend, level c:   XB = XA + P X_{c+1} on the stored rows and the halo
+    //                      rows, RR = XB + omega D^-1 (BB - A XB) (pushed)
     auto vcycle = [&]() {
-        for (int c = 0; c < NL; ++c) {
+        for (int c = 0; c < NL - 1; ++c) {
             const MgLevelPlan &P = plan.lv[c];
-            const int mc = P.m, nown_c = (sR1[c] - sR0[c]) * mc, base = 1 + mc;
+            const bool dist = !P.local;
+            const int mc = P.m, R0 = sR0[c], rows = sR1[c] - R0, nown_c = rows * mc, base = 1 + mc;
             const float *Dd = F_(P.off_d), *Ee = F_(P.off_e), *Nn = F_(P.off_n), *NE = F_(P.off_ne);
-            float *xa = F_(P.off_xa), *xb = F_(P.off_xb), *rr = F_(P.off_r), *bb = F_(P.off_b);
+            float *xa = F_(P.off_xa), *rr = F_(P.off_r), *bb = F_(P.off_b);
             // pre-smoothing from zero: XA = omega D^-1 B
-            for (int l = tid; l < nown_c; l += nt) xa[base + l] = kMgOmega * bb[l] / Dd[base + l];
-            if (c == NL - 1) {
-                // coarsest: further damped Jacobi sweeps, ping-pong XA / XB
-                const int sweeps = CS == 1 ? 6 : 10;
-                float *X = xa, *Y = xb;
-                int ox = P.off_xa, oy = P.off_xb;
-                for (int k = 1; k < sweeps; ++k) {
-                    exchange(c, ox);
-                    for (int l = tid; l < nown_c; l += nt) {
-                        const int t = base + l;
-                        Y[t] = X[t] + kMgOmega * (bb[l] - spmv(Dd, Ee, Nn, NE, mc, X, t)) / Dd[t];
-                    }
-                    float *tp = X;
-                    X = Y;
-                    Y = tp;
-                    const int to = ox;
-                    ox = oy;
-                    oy = to;
-                }
-                if (X != xa)
-                    for (int l = tid; l < nown_c; l += nt) xa[base + l] = X[base + l];
-                break;
+            for (int l = tid; l < nown_c; l += nt) {
+                const float x = __fdividef(kMgOmega * bb[l], Dd[base + l]);
+                xa[base + l] = x;
+                if (dist) push(c, P.off_xa, mc, rows, l, x);
             }
+            level_sync(dist);
             // residual RR = B - A XA
-            exchange(c, P.off_xa);
-            for (int l = tid; l < nown_c; l += nt) rr[base + l] = bb[l] - spmv(Dd, Ee, Nn, NE, mc, xa, base + l);
-            exchange(c, P.off_r);
+            for (int l = tid; l < nown_c; l += nt) {
+                const float r = bb[l] - spmv(Dd, Ee, Nn, NE, mc, xa, base + l);
+                rr[base + l] = r;
+                if (dist) push(c, P.off_r, mc, rows, l, r);
+            }
+            level_sync(dist);
             // restriction: B_{c+1}(I, J) = R(2I, 2J) + 1/2 sum of the six neighbours
             const MgLevelPlan &Q = plan.lv[c + 1];
-            const int mq = Q.m, R0q = sR0[c + 1], nown_q = (sR1[c + 1] - R0q) * mq;
+            const int mq = Q.m;
+            const bool bcast = dist && Q.local;   // first local level: broadcast
+            int B0 = sR0[c + 1], B1 = sR1[c + 1];
+            if (bcast) mg_band(g.m, CS, rank, c + 1, &B0, &B1);
             float *bq = F_(Q.off_b);
-            const int R0 = sR0[c];
-            for (int l = tid; l < nown_q; l += nt) {
-                const int J = R0q + l / mq, I = l - (l / mq) * mq;
+            const int nq = (B1 - B0) * mq;
+            const int qdj = nt / mq, qdi = nt - qdj * mq;
+            int jl = tid / mq, I = tid - jl * mq;
+            for (int l = tid; l < nq; l += nt, jl += qdj, I += qdi) {
+                if (I >= mq) {
+                    I -= mq;
+                    ++jl;
+                }
+                const int J = B0 + jl;
                 const int i = 2 * I, j = 2 * J;
                 const int t = 1 + (j - (R0 - 1)) * mc + i;
                 float h = 0.0f;
@@ -280,69 +371,140 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1)
                 if (j > 0) h += rr[t - mc];
                 if (i + 1 < mc && j + 1 < mc) h += rr[t + mc + 1];
                 if (i > 0 && j > 0) h += rr[t - mc - 1];
-                bq[l] = rr[t] + 0.5f * h;
+                const float val = rr[t] + 0.5f * h;
+                if constexpr (CS > 1) {
+                    if (bcast) {
+                        const int q = J * mq + I;
+#pragma unroll 1
+                        for (int r = 0; r < CS; ++r) cl.map_shared_rank(bq, r)[q] = val;
+                        continue;
+                    }
+                }
+                bq[l] = val;
+            }
+            if constexpr (CS > 1) {
+                if (bcast) cl.sync();
+            }
+        }
+        // coarsest level (held whole): damped Jacobi sweeps, ping-pong XA / XB
+        int xq_off;
+        {
+            const MgLevelPlan &P = plan.lv[NL - 1];
+            const int mc = P.m, nown_c = (sR1[NL - 1] - sR0[NL - 1]) * mc, base = 1 + mc;
+            const float *Dd = F_(P.off_d), *Ee = F_(P.off_e), *Nn = F_(P.off_n), *NE = F_(P.off_ne);
+            const float *bb = F_(P.off_b);
+            float *X = F_(P.off_xa), *Y = F_(P.off_xb);
+            xq_off = P.off_xa;
+            int yo = P.off_xb;
+            for (int l = tid; l < nown_c; l += nt) X[base + l] = __fdividef(kMgOmega * bb[l], Dd[base + l]);
+            for (int k = 1; k < kMgCoarsestSweeps; ++k) {
+                __syncthreads();
+                for (int l = tid; l < nown_c; l += nt) {
+                    const int t = base + l;
+                    Y[t] = X[t] + __fdividef(kMgOmega * (bb[l] - spmv(Dd, Ee, Nn, NE, mc, X, t)), Dd[t]);
+                }
+                float *tp = X;
+                X = Y;
+                Y = tp;
+                const int to = xq_off;
+                xq_off = yo;
+                yo = to;
+            }
+            __syncthreads();
+            if (NL == 1) {
+                // one-level hierarchy: the result goes where the caller reads it
+                float *R = F_(P.off_r);
+                for (int l = tid; l < nown_c; l += nt) R[base + l] = X[base + l];
+                __syncthreads();
             }
         }
         // ascend: interpolate and post-smooth
         for (int c = NL - 2; c >= 0; --c) {
             const MgLevelPlan &P = plan.lv[c], &Q = plan.lv[c + 1];
-            const int mc = P.m, R0 = sR0[c], nown_c = (sR1[c] - R0) * mc, base = 1 + mc;
+            const bool dist = !P.local;
+            const int mc = P.m, R0 = sR0[c], R1 = sR1[c], rows = R1 - R0, nown_c = rows * mc, base = 1 + mc;
             const int mq = Q.m, R0q = sR0[c + 1];
             const float *Dd = F_(P.off_d), *Ee = F_(P.off_e), *Nn = F_(P.off_n), *NE = F_(P.off_ne);
-            float *xa = F_(P.off_xa), *xb = F_(P.off_xb), *bb = F_(P.off_b);
-            const float *xq = F_(Q.off_xa);
-            exchange(c + 1, Q.off_xa);
-            // XB = XA + P X_{c+1}
-            for (int l = tid; l < nown_c; l += nt) {
-                const int jl = l / mc, i = l - jl * mc, j = R0 + jl;
+            const float *xa = F_(P.off_xa), *bb = F_(P.off_b);
+            float *xb = F_(P.off_xb), *rr = F_(P.off_r);
+            const float *xq = F_(xq_off);
+            // XB = XA + P X_{c+1}: stored rows, and the halo rows of a
+            // distributed level (their XA came with the pre-smoothing push)
+            const int jlo = (dist && has_lo) ? R0 - 1 : R0, jhi = (dist && has_hi) ? R1 + 1 : R1;
+            const int nx = (jhi - jlo) * mc;
+            const int xdj = nt / mc, xdi = nt - xdj * mc;
+            int jl = tid / mc, i = tid - jl * mc;
+            for (int l = tid; l < nx; l += nt, jl += xdj, i += xdi) {
+                if (i >= mc) {
+                    i -= mc;
+                    ++jl;
+                }
+                const int j = jlo + jl;
+                const int t = 1 + (j - (R0 - 1)) * mc + i;
                 const int tq = 1 + ((j >> 1) - (R0q - 1)) * mq + (i >> 1);
                 float pv;
                 if (!(i & 1) && !(j & 1)) pv = xq[tq];
                 else if ((i & 1) && !(j & 1)) pv = 0.5f * (xq[tq] + xq[tq + 1]);
                 else if (!(i & 1) && (j & 1)) pv = 0.5f * (xq[tq] + xq[tq + mq]);
                 else pv = 0.5f * (xq[tq] + xq[tq + mq + 1]);
-                xb[base + l] = xa[base + l] + pv;
+                xb[t] = xa[t] + pv;
             }
-            exchange(c, P.off_xb);
-            // XA = XB + omega D^-1 (B - A XB)
+            __syncthreads();
+            // X_c = XB + omega D^-1 (B - A XB), into RR
             for (int l = tid; l < nown_c; l += nt) {
                 const int t = base + l;
-                xa[t] = xb[t] + kMgOmega * (bb[l] - spmv(Dd, Ee, Nn, NE, mc, xb, t)) / Dd[t];
+                const float x = xb[t] + __fdividef(kMgOmega * (bb[l] - spmv(Dd, Ee, Nn, NE, mc, xb, t)), Dd[t]);
+                rr[t] = x;
+                if (dist) push(c, P.off_r, mc, rows, l, x);
             }
+            level_sync(dist);
+            xq_off = P.off_r;
         }
     };
 
     const MgLevelPlan &P0 = plan.lv[0];
     const float *D0 = F_(P0.off_d), *E0 = F_(P0.off_e), *N0 = F_(P0.off_n), *NE0 = F_(P0.off_ne);
-    float *XA0 = F_(P0.off_xa), *RR0 = F_(P0.off_r), *BB0 = F_(P0.off_b);
+    float *RR0 = F_(P0.off_r), *BB0 = F_(P0.off_b);
     const int FB = 1 + m;   // tile index of own local 0 on the fine level
 
     float r[NPT], u[NPT], w[NPT], sv[NPT], p[NPT], x[NPT];
-    int wpar = 0, par = 0;
+    int wpar = 0, vpar = 0, par = 0;
     int64_t total_iters = 0;
     int32_t status = S_CONVERGED;
     const double dt = g.dt;
 
     for (int step = 0; step < g.nsteps; ++step) {
-        // ---- block load: b = M (v + dt R), w update, r0 = b - A v (into RR)
+        // ---- block load: b = M (v + dt R), w update, extrapolated initial
+        // guess 2 v_n - v_{n-1} (v_n on the first block) in the other v
+        // buffer, then r0 = b - A guess (into RR)
         const double *wcur = wb0 + wpar * SN;
         double *wnext = wb0 + (wpar ^ 1) * SN;
+        const double *vcur = vb0 + vpar * SN;
+        double *v = vb0 + (vpar ^ 1) * SN;
+        vpar ^= 1;
+#pragma unroll 1
+        for (int l = tid; l < nown; l += nt) {
+            const int node = own0 + l;
+            const int j = node / m, i = node - j * m;
+            b[node] = mass_apply_y(m, i, j, g.h2, vcur, wcur, node, dt, g.a);
+            const double vv = vcur[node], ww = wcur[node];
+            wnext[node] = ww + dt * g.eps * (vv - g.gam * ww);
+            v[node] = step > 0 ? 2.0 * vv - v[node] : vv;
+        }
+        cl.sync();
         {
             double acc[2] = {0.0, 0.0};
 #pragma unroll 1
             for (int l = tid; l < nown; l += nt) {
                 const int node = own0 + l;
                 const int j = node / m, i = node - j * m;
-                const double bb = mass_apply_y(m, i, j, g.h2, v, wcur, node, dt, g.a);
-                b[node] = bb;
-                const double vv = v[node], ww = wcur[node];
-                wnext[node] = ww + dt * g.eps * (vv - g.gam * ww);
+                const double bb = b[node];
                 const double rr = bb - stencil_apply_global(A64, n, m, node, i, j, v);
                 RR0[FB + l] = (float)rr;
                 acc[0] += bb * bb;
                 acc[1] += rr * rr;
             }
-            cluster_reduce<2, CS>(acc, wsl, csl, par, [&](double(&t)[2]) {
+            cluster_reduce_push<2, CS>(acc, wsl, csp, par, [&](double(&t)[2]) {
                 ctl.s0 = t[0];
                 ctl.s1 = t[1];
             });
@@ -369,7 +531,7 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1)
                     RR0[FB + l] = (float)rr;
                     racc[0] += rr * rr;
                 }
-                cluster_reduce<1, CS>(racc, wsl, csl, par, [&](double(&t)[1]) { ctl.s1 = t[0]; });
+                cluster_reduce_push<1, CS>(racc, wsl, csp, par, [&](double(&t)[1]) { ctl.s1 = t[0]; });
                 par ^= 1;
                 rnorm2 = ctl.s1;
                 if (!isfinite(rnorm2)) { nonfinite = true; break; }
@@ -377,7 +539,9 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1)
             if (rnorm2 <= tol_out2) { solved = true; break; }
             const double rnorm = sqrt(rnorm2);
             const float rscale = (float)(1.0 / rnorm);
-            const double tol_in2 = g.rtol_in * g.rtol_in;
+            // inner target: rtol_in, or a quarter of what the outer test still
+            // needs when that is looser (the last sweep of a block)
+            const double tol_in2 = fmax(g.rtol_in * g.rtol_in, 0.0625 * tol_out2 / rnorm2);
 
             // ---- init: r0 (normalised), u0 = MG(r0), w0 = A u0
 #pragma unroll
@@ -393,14 +557,13 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1)
             }
             __syncthreads();
             vcycle();
-            exchange(0, P0.off_xa);
             float iacc[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
             for (int k = 0; k < NPT; ++k) {
                 const int l = tid + k * nt;
                 if (l < nown) {
-                    u[k] = XA0[FB + l];
-                    w[k] = spmv(D0, E0, N0, NE0, m, XA0, FB + l);
+                    u[k] = RR0[FB + l];
+                    w[k] = spmv(D0, E0, N0, NE0, m, RR0, FB + l);
                     iacc[0] = fmaf(r[k], u[k], iacc[0]);
                     iacc[1] = fmaf(w[k], u[k], iacc[1]);
                     iacc[2] = fmaf(r[k], r[k], iacc[2]);
@@ -429,7 +592,7 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1)
                 ctl.beta = beta;
                 ctl.code = code;
             };
-            cluster_reduce<3, CS>(iacc, wsl, csl, par, [&](double(&t)[3]) { decide(t[0], t[1], t[2]); });
+            cluster_reduce_push<3, CS>(iacc, wsl, csp, par, [&](double(&t)[3]) { decide(t[0], t[1], t[2]); });
             par ^= 1;
             while (true) {
                 const int code = ctl.code;
@@ -453,21 +616,20 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1)
                 }
                 __syncthreads();
                 vcycle();
-                exchange(0, P0.off_xa);
                 float pacc[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
                 for (int k = 0; k < NPT; ++k) {
                     const int l = tid + k * nt;
                     if (l < nown) {
-                        u[k] = XA0[FB + l];
-                        w[k] = spmv(D0, E0, N0, NE0, m, XA0, FB + l);
+                        u[k] = RR0[FB + l];
+                        w[k] = spmv(D0, E0, N0, NE0, m, RR0, FB + l);
                         pacc[0] = fmaf(r[k], u[k], pacc[0]);
                         pacc[1] = fmaf(w[k], u[k], pacc[1]);
                         pacc[2] = fmaf(r[k], r[k], pacc[2]);
                     }
                 }
                 ++it;
-                cluster_reduce<3, CS>(pacc, wsl, csl, par, [&](double(&t)[3]) { decide(t[0], t[1], t[2]); });
+                cluster_reduce_push<3, CS>(pacc, wsl, csp, par, [&](double(&t)[3]) { decide(t[0], t[1], t[2]); });
                 par ^= 1;
             }
             total_iters += it;
@@ -486,12 +648,13 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1)
         if (!solved && status == S_CONVERGED) status = S_MAXITER;
     }
 
+    const double *vfin = vb0 + vpar * SN;   // solution of the last block
     double qacc[1] = {0.0};
     for (int node = own0 + tid; node < own1; node += nt) {
         const int j = node / m, i = node - j * m;
-        qacc[0] += lumped_mass(m, i, j, g.h2) * v[node];
+        qacc[0] += lumped_mass(m, i, j, g.h2) * vfin[node];
     }
-    cluster_reduce<1, CS>(qacc, wsl, csl, par, [&](double(&t)[1]) { ctl.s0 = t[0]; });
+    cluster_reduce_push<1, CS>(qacc, wsl, csp, par, [&](double(&t)[1]) { ctl.s0 = t[0]; });
     if (rank == 0 && tid == 0) {
         g.q[sample] = status == S_NONFINITE ? __longlong_as_double(0x7ff8000000000000LL) : ctl.s0;
         g.iters[sample] = (int32_t)(total_iters > 0x7fffffff ? 0x7fffffff : total_iters);

@@ -402,8 +402,9 @@ def test_estimate_graph_capture_and_replay(mlq):
 # Multigrid-preconditioned inner PCG (mixed path): same QoI as the oracle,
 # on every cluster size that fits, over the nested hierarchy of each mesh.
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("m,cluster,steps", [(9, 1, 6), (17, 1, 10), (33, 2, 8), (65, 1, 6), (65, 4, 6),
-                                             (129, 4, 4), (257, 16, 3)])
+@pytest.mark.parametrize("m,cluster,steps", [(3, 1, 5), (9, 1, 6), (9, 8, 5), (17, 1, 10), (17, 4, 6),
+                                             (17, 16, 6), (33, 2, 8), (33, 16, 5), (65, 1, 6), (65, 4, 6),
+                                             (129, 4, 4), (129, 16, 3), (257, 16, 3)])
 def test_multigrid_parity(mlq, m, cluster, steps):
     mesh = O.mesh2d(m)
     rng = np.random.default_rng(m + cluster)
