@@ -166,16 +166,21 @@ def kernel_source_hash() -> str:
     import hashlib
 
     h = hashlib.sha256()
-    for f in ("mlq_kernels.cuh", "mlq_aux.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2105_02007_gb300", "csrc", f), "rb").read())
+    csrc = os.path.join(ROOT, "paper_2105_02007_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cuh", ".cu")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def load_traffic(kernel_key: str, samples: int, steps: int):
     """DRAM bytes (read + write) per launch of `kernel_key`, from the committed
-    ncu summary profiles/traffic.json, scaled from the captured case to this
-    launch by samples x time blocks; None if there is no capture for this
-    kernel or the kernel sources changed since it was taken."""
+    ncu summary profiles/traffic.json, scaled from the captured cases to this
+    launch; None if there is no capture for this kernel or the kernel sources
+    changed since it was taken.  Two captures of one sample at different
+    block counts give a per-sample set-up part and a per-block part
+    (bytes = samples x (base + steps x per_block)); one capture scales by
+    samples x blocks."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(path))
@@ -184,7 +189,14 @@ def load_traffic(kernel_key: str, samples: int, steps: int):
     e = d.get(kernel_key)
     if not e or e.get("source_hash") != kernel_source_hash():
         return None
-    return e["dram_bytes"] * (samples * steps) / (e["samples"] * e["steps"])
+    caps = sorted(e["captures"], key=lambda c: c["steps"])
+    if len(caps) >= 2:
+        a, b = caps[0], caps[-1]
+        per_block = (b["dram_bytes"] / b["samples"] - a["dram_bytes"] / a["samples"]) / (b["steps"] - a["steps"])
+        base = a["dram_bytes"] / a["samples"] - a["steps"] * per_block
+        return samples * (base + steps * max(per_block, 0.0))
+    c = caps[0]
+    return c["dram_bytes"] * (samples * steps) / (c["samples"] * c["steps"])
 
 
 def run_reference(args):
@@ -438,7 +450,8 @@ def main():
             "gpu_launches": launches, "clocks": clk, "roofline": roof,
             "cpu_baseline": cpu, "fp64": fp64,
             "members": [{k: d[k] for k in ("level", "coarse", "cluster", "threads", "npt", "resident", "samples",
-                                            "kernel_ms", "cg_iterations")} for d in members],
+                                            "kernel_ms", "start_ms", "end_ms", "cg_iterations")}
+                        for d in members],
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -209,6 +209,7 @@ typedef struct {
     int threads, npt;       /* threads per CTA; nodes per thread (register kernel, else 0) */
     int64_t samples, nodes, steps;
     int64_t cg_iterations;  /* CG iterations summed over samples, blocks, sweeps */
+    double start_ms, end_ms; /* kernel start / end after the start of the call (events) */
 } mlq_member_stats;
 int mlq_set_profiling(mlq_ctx *ctx, int enable);
 int mlq_member_profile(mlq_ctx *ctx, int max_members, int *count, mlq_member_stats *out);

@@ -23,6 +23,9 @@ namespace {
 constexpr int kMaxLevels = 16;
 constexpr int kMaxK = 256;
 constexpr int kStreams = 12;
+// concurrent member streams of an estimate: the device's default number of
+// hardware work queues (CUDA_DEVICE_MAX_CONNECTIONS); more streams share one
+constexpr int kLanes = 8;
 
 struct Level {
     bool defined = false;
@@ -49,7 +52,7 @@ struct Member {
     int64_t S = 0;
     const double *d_xi = nullptr;
     // workspace pieces
-    double *cs2 = nullptr, *A64 = nullptr, *v = nullptr, *w = nullptr, *b = nullptr, *q = nullptr;
+    double *cs2 = nullptr, *A64 = nullptr, *v = nullptr, *w = nullptr, *b = nullptr, *y = nullptr, *q = nullptr;
     void *Ai = nullptr, *r = nullptr, *s = nullptr, *wc = nullptr, *p = nullptr, *x = nullptr;
     int32_t *iters = nullptr, *status = nullptr;
     float *mgA[mlq::kMgMaxLevels] = {};    // coarse-level stencils (multigrid)
@@ -79,6 +82,7 @@ struct mlq_ctx {
     size_t ws_bytes = 0;
     cudaStream_t pool[kStreams] = {};
     cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_start = nullptr;  // start of the last solve / estimate (profiling)
     cudaEvent_t ev_join[kStreams] = {};
     int64_t launches = 0;
     int *d_err = nullptr;   // set by kernels whose bounded waits time out
@@ -356,6 +360,7 @@ size_t member_bytes(const mlq_ctx *ctx, const Level &L, int64_t S)
     add((mixed && ctx->opt.precond == 1 ? 2 : 1) * sn * 8);  // v (multigrid: solution and guess)
     add(2 * sn * 8);                        // w
     add(sn * 8);                            // b
+    if (mixed && ctx->opt.precond == 1) add(sn * 8);  // y (multigrid kernel)
     add(2 * sn * ti);                       // r
     add(2 * sn * ti);                       // s
     add(2 * sn * ti);                       // wc
@@ -391,6 +396,7 @@ void member_carve(const mlq_ctx *ctx, const Level &L, Member &mb, char *&cur)
     mb.v = (double *)take((mixed && ctx->opt.precond == 1 ? 2 : 1) * sn * 8);
     mb.w = (double *)take(2 * sn * 8);
     mb.b = (double *)take(sn * 8);
+    mb.y = (mixed && ctx->opt.precond == 1) ? (double *)take(sn * 8) : nullptr;
     mb.r = take(2 * sn * ti);
     mb.s = take(2 * sn * ti);
     mb.wc = take(2 * sn * ti);
@@ -451,17 +457,22 @@ int launch_synthesis(mlq_ctx *ctx, const Level &L, const double *d_xi, int S, do
     return MLQ_OK;
 }
 
+// Member launch phases: set-up (KL synthesis, stencils, multigrid levels)
+// and the slab solve; an estimate runs every member's set-up before the first
+// solve so that the long solver kernels do not hold SMs the set-ups wait for.
+enum { kSetup = 1, kSolve = 2, kBoth = 3 };
+
 template <typename TI>
-int launch_member_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream_t st, int slot)
+int launch_member_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream_t st, int slot, int phase)
 {
     const bool mixed = sizeof(TI) == 4;
     // K1: KL synthesis (theta -> cos 2t, sin 2t)
-    {
+    if (phase & kSetup) {
         int st1 = launch_synthesis(ctx, L, mb.d_xi, (int)mb.S, mb.cs2, st);
         if (st1 != MLQ_OK) return st1;
     }
     // K2: stencil of A = M + dt K(theta)
-    {
+    if (phase & kSetup) {
         dim3 blk(256), grd((unsigned)((L.n + 255) / 256), (unsigned)mb.S);
         mlq::stencil_setup_kernel<<<grd, blk, 0, st>>>(mb.cs2, L.m, L.h, L.dt, ctx->model.s_l, ctx->model.s_t,
                                                          (int)mb.S, mb.A64, mixed ? (float *)mb.Ai : nullptr);
@@ -488,6 +499,7 @@ int launch_member_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream_t
     a.v = mb.v;
     a.w = mb.w;
     a.b = mb.b;
+    a.y = mb.y;
     a.r = (TI *)mb.r;
     a.s = (TI *)mb.s;
     a.wc = (TI *)mb.wc;
@@ -504,7 +516,6 @@ int launch_member_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream_t
     if (ctx->opt.storage == 1 && !sh.resident) return MLQ_EUNSUPPORTED;
     const bool timed = ctx->profile && slot >= 0 && slot < kStreams;
     const unsigned evf = ctx->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
-    if (timed) MLQ_CUDA(ctx, cudaEventRecordWithFlags(ctx->ev_t0[slot], st, evf));
     if constexpr (sizeof(TI) == 4) {
         if (sh.mg) {
             const mlq::MgPlan mp = mlq::mg_plan(L.m, sh.cs);
@@ -514,22 +525,31 @@ int launch_member_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream_t
                 const int mf = mc;
                 mc = (mc + 1) / 2;
                 const int nec = 2 * (mc - 1) * (mc - 1);
-                mlq::mg_coarsen_kernel<<<dim3((unsigned)((nec + 255) / 256), (unsigned)mb.S), 256, 0, st>>>(
-                    c == 1 ? mb.cs2 : nullptr, c == 1 ? nullptr : mb.mgD[c - 1], mf, (int)mb.S, ctx->model.s_l,
-                    ctx->model.s_t, mb.mgD[c]);
-                mlq::mg_stencil_kernel<<<dim3((unsigned)((mc * mc + 255) / 256), (unsigned)mb.S), 256, 0, st>>>(
-                    mb.mgD[c], mc, L.dt, (int)mb.S, mb.mgA[c]);
-                MLQ_CUDA(ctx, cudaGetLastError());
-                ctx->launches += 2;
+                if (phase & kSetup) {
+                    mlq::mg_coarsen_kernel<<<dim3((unsigned)((nec + 255) / 256), (unsigned)mb.S), 256, 0, st>>>(
+                        c == 1 ? mb.cs2 : nullptr, c == 1 ? nullptr : mb.mgD[c - 1], mf, (int)mb.S,
+                        ctx->model.s_l, ctx->model.s_t, mb.mgD[c]);
+                    mlq::mg_stencil_kernel<<<dim3((unsigned)((mc * mc + 255) / 256), (unsigned)mb.S), 256, 0,
+                                             st>>>(mb.mgD[c], mc, L.dt, (int)mb.S, mb.mgA[c]);
+                    MLQ_CUDA(ctx, cudaGetLastError());
+                    ctx->launches += 2;
+                }
                 ptrs.A[c] = mb.mgA[c];
             }
+            if (!(phase & kSolve)) return MLQ_OK;
             if (timed) MLQ_CUDA(ctx, cudaEventRecordWithFlags(ctx->ev_t0[slot], st, evf));
             MLQ_CUDA(ctx, launch_mg_any(sh.cs, sh.npt, a, ptrs, mp, (int)mb.S, sh.threads, st));
-        } else if (sh.npt > 0)
-            MLQ_CUDA(ctx, launch_reg_any(sh.cs, sh.npt, a, (int)mb.S, sh.threads, sh.smem, st));
-        else
-            MLQ_CUDA(ctx, launch_slab_cs<TI>(sh.cs, a, (int)mb.S, sh.threads, sh.smem, sh.resident, st));
+        } else {
+            if (!(phase & kSolve)) return MLQ_OK;
+            if (timed) MLQ_CUDA(ctx, cudaEventRecordWithFlags(ctx->ev_t0[slot], st, evf));
+            if (sh.npt > 0)
+                MLQ_CUDA(ctx, launch_reg_any(sh.cs, sh.npt, a, (int)mb.S, sh.threads, sh.smem, st));
+            else
+                MLQ_CUDA(ctx, launch_slab_cs<TI>(sh.cs, a, (int)mb.S, sh.threads, sh.smem, sh.resident, st));
+        }
     } else {
+        if (!(phase & kSolve)) return MLQ_OK;
+        if (timed) MLQ_CUDA(ctx, cudaEventRecordWithFlags(ctx->ev_t0[slot], st, evf));
         MLQ_CUDA(ctx, launch_slab_cs<TI>(sh.cs, a, (int)mb.S, sh.threads, sh.smem, sh.resident, st));
     }
     if (timed) MLQ_CUDA(ctx, cudaEventRecordWithFlags(ctx->ev_t1[slot], st, evf));
@@ -537,7 +557,7 @@ int launch_member_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream_t
     return MLQ_OK;
 }
 
-int launch_member(mlq_ctx *ctx, const Member &mb, cudaStream_t st, int slot, int coarse)
+int launch_member(mlq_ctx *ctx, const Member &mb, cudaStream_t st, int slot, int coarse, int phase = kBoth)
 {
     const Level &L = ctx->levels[mb.level];
     if (ctx->profile && slot >= 0 && slot < kStreams) {
@@ -554,8 +574,8 @@ int launch_member(mlq_ctx *ctx, const Member &mb, cudaStream_t st, int slot, int
         ctx->prof_iters_dev[slot] = mb.iters;
         ctx->nmembers = std::max(ctx->nmembers, slot + 1);
     }
-    if (ctx->opt.precision == MLQ_MIXED) return launch_member_t<float>(ctx, L, mb, st, slot);
-    return launch_member_t<double>(ctx, L, mb, st, slot);
+    if (ctx->opt.precision == MLQ_MIXED) return launch_member_t<float>(ctx, L, mb, st, slot, phase);
+    return launch_member_t<double>(ctx, L, mb, st, slot, phase);
 }
 
 // device error flag (a bounded wait ran out): report once and clear
@@ -689,12 +709,18 @@ int mlq_create(mlq_ctx **out, int device, void *cuda_stream, const mlq_options *
         return code;
     };
     if (cudaSetDevice(device) != cudaSuccess) return fail(MLQ_ECUDA);
+    int prio_least = 0, prio_greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess) return fail(MLQ_ECUDA);
     for (int k = 0; k < kStreams; ++k) {
-        if (cudaStreamCreateWithFlags(&ctx->pool[k], cudaStreamNonBlocking) != cudaSuccess) return fail(MLQ_ECUDA);
+        // priority by pair: members (2k, 2k+1) of the k-th largest level
+        if (cudaStreamCreateWithPriority(&ctx->pool[k], cudaStreamNonBlocking,
+                                         std::min(prio_least, prio_greatest + k / 2)) != cudaSuccess)
+            return fail(MLQ_ECUDA);
         if (cudaEventCreateWithFlags(&ctx->ev_join[k], cudaEventDisableTiming) != cudaSuccess)
             return fail(MLQ_ECUDA);
     }
     if (cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess) return fail(MLQ_ECUDA);
+    if (cudaEventCreate(&ctx->ev_start) != cudaSuccess) return fail(MLQ_ECUDA);
     for (int k = 0; k < kStreams; ++k)
         if (cudaEventCreate(&ctx->ev_t0[k]) != cudaSuccess || cudaEventCreate(&ctx->ev_t1[k]) != cudaSuccess)
             return fail(MLQ_ECUDA);
@@ -728,6 +754,7 @@ int mlq_destroy(mlq_ctx *ctx)
         if (ctx->ev_t1[k]) cudaEventDestroy(ctx->ev_t1[k]);
     }
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
     cudaFree(ctx->d_err);
     if (ctx->h_sums) cudaFreeHost(ctx->h_sums);
     if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
@@ -949,6 +976,7 @@ int mlq_solve(mlq_ctx *ctx, int level, int64_t S, const double *xi, int with_coa
     mf.d_xi = d_xi;
     mc.d_xi = d_xi;
     // fork: fine on pool[0], coarse on pool[1]
+    if (ctx->profile) MLQ_CUDA(ctx, cudaEventRecord(ctx->ev_start, ctx->stream));
     MLQ_CUDA(ctx, cudaEventRecord(ctx->ev_fork, ctx->stream));
     const int nm = with_coarse ? 2 : 1;
     for (int k = 0; k < nm; ++k) {
@@ -1065,19 +1093,32 @@ int mlq_estimate(mlq_ctx *ctx, int L, const int64_t *N, const double *const *xi,
         }
         return code;
     };
+    if (ctx->profile && cudaEventRecordWithFlags(ctx->ev_start, ctx->stream,
+                                                 ctx->capturing ? cudaEventRecordExternal : cudaEventRecordDefault) !=
+                            cudaSuccess)
+        return abort_capture(MLQ_ECUDA);
     if (cudaEventRecord(ctx->ev_fork, ctx->stream) != cudaSuccess) return abort_capture(MLQ_ECUDA);
-    // largest levels first so that they start first
-    int sid = 0;
-    for (int l = L; l >= 0; --l) {
-        for (int k = 0; k < (l > 0 ? 2 : 1); ++k) {
-            cudaStream_t s = ctx->pool[sid];
-            if (cudaStreamWaitEvent(s, ctx->ev_fork, 0) != cudaSuccess) return abort_capture(MLQ_ECUDA);
-            st = launch_member(ctx, k == 0 ? fine[l] : coarse[l], s, sid, k);
-            if (st != MLQ_OK) return abort_capture(st);
-            if (cudaEventRecord(ctx->ev_join[sid], s) != cudaSuccess ||
-                cudaStreamWaitEvent(ctx->stream, ctx->ev_join[sid], 0) != cudaSuccess)
-                return abort_capture(MLQ_ECUDA);
-            ++sid;
+    // every member's set-up first (short kernels), joined, then the solves,
+    // largest levels first on the higher-priority streams: the finest level
+    // is the critical path and takes freed SMs first
+    for (int phase : {kSetup, kSolve}) {
+        if (phase == kSolve && cudaEventRecord(ctx->ev_fork, ctx->stream) != cudaSuccess)
+            return abort_capture(MLQ_ECUDA);
+        int sid = 0;
+        for (int l = L; l >= 0; --l) {
+            for (int k = 0; k < (l > 0 ? 2 : 1); ++k) {
+                // the device has kLanes hardware queues by default: members
+                // past the last lane (the smallest) run in turn on it instead
+                // of sharing a queue with a large member
+                cudaStream_t s = ctx->pool[std::min(sid, kLanes - 1)];
+                if (cudaStreamWaitEvent(s, ctx->ev_fork, 0) != cudaSuccess) return abort_capture(MLQ_ECUDA);
+                st = launch_member(ctx, k == 0 ? fine[l] : coarse[l], s, sid, k, phase);
+                if (st != MLQ_OK) return abort_capture(st);
+                if (cudaEventRecord(ctx->ev_join[sid], s) != cudaSuccess ||
+                    cudaStreamWaitEvent(ctx->stream, ctx->ev_join[sid], 0) != cudaSuccess)
+                    return abort_capture(MLQ_ECUDA);
+                ++sid;
+            }
         }
     }
     for (int l = 0; l <= L; ++l) {
@@ -1097,7 +1138,8 @@ int mlq_estimate(mlq_ctx *ctx, int L, const int64_t *N, const double *const *xi,
         cudaGraph_t g = nullptr;
         ctx->capturing = false;
         MLQ_CUDA(ctx, cudaStreamEndCapture(ctx->stream, &g));
-        cudaError_t e = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+        // kernel nodes keep the priority of the stream they were captured from
+        cudaError_t e = cudaGraphInstantiate(&ctx->graph_exec, g, cudaGraphInstantiateFlagUseNodePriority);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) {
             ctx->graph_exec = nullptr;
@@ -1132,6 +1174,10 @@ int mlq_member_profile(mlq_ctx *ctx, int max_members, int *count, mlq_member_sta
         MLQ_CUDA(ctx, cudaEventSynchronize(ctx->ev_t1[k]));
         MLQ_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_t0[k], ctx->ev_t1[k]));
         o.kernel_ms = ms;
+        MLQ_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_start, ctx->ev_t0[k]));
+        o.start_ms = ms;
+        MLQ_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_start, ctx->ev_t1[k]));
+        o.end_ms = ms;
         o.level = ctx->prof_level[k];
         o.coarse = ctx->prof_coarse[k];
         o.cluster = ctx->prof_cs[k];

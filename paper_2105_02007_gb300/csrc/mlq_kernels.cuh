@@ -56,6 +56,7 @@ struct SolveArgs {
     double *v;                    // [S][n]; [2][S][n] for the multigrid kernel
     double *w;                    // [2][S][n]
     double *b;                    // [S][n]
+    double *y;                    // [S][n] v + dt R(v, w) per node (multigrid kernel), else null
     TI *r, *s, *wc;               // [2][S][n] each
     TI *p, *x;                    // [S][n]
     const double *v0, *w0;        // [n] or null

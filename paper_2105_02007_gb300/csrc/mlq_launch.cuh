@@ -47,13 +47,20 @@ cudaError_t cluster_launch(K kern, int nclusters, int threads, size_t smem, cuda
     cfg.blockDim = dim3((unsigned)threads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    // the stream's priority as a launch attribute: a captured graph node
+    // keeps it
+    int prio = 0;
+    e = cudaStreamGetPriority(st, &prio);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = CS;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributePriority;
+    attr[1].val.priority = prio;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 

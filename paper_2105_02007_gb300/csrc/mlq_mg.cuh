@@ -30,6 +30,7 @@ constexpr int kMgMaxLevels = 8;
 constexpr float kMgOmega = 0.7f;   // lambda_max(D^-1 A) <= 2.5 on every level: omega lambda < 2
 constexpr int kMgGatherM = 17;        // gather levels of at most this many nodes per side
 constexpr int kMgCoarsestSweeps = 6;  // damped Jacobi sweeps on the coarsest level
+constexpr int kMgWarpM = 9;           // levels of at most this many nodes per side run on one warp
 
 // Conductivity of an element as (d11, d12, d22).
 struct D3 {
@@ -58,8 +59,9 @@ struct MgLevelPlan {
 };
 
 struct MgPlan {
-    int nl;      // levels (0: no valid layout)
-    int gather;  // first local level
+    int nl;          // levels (0: no valid layout)
+    int gather;      // first local level
+    int warp_level;  // first level run by one warp (nl: none)
     int total;   // bytes
     MgLevelPlan lv[kMgMaxLevels];
 };
@@ -86,6 +88,7 @@ __host__ __device__ inline MgPlan mg_plan(int m0, int cs)
     MgPlan pl;
     pl.nl = 0;
     pl.gather = 0;
+    pl.warp_level = 0;
     pl.total = 0;
     int off = 0;
     int m = m0;
@@ -133,8 +136,32 @@ __host__ __device__ inline MgPlan mg_plan(int m0, int cs)
         pl.nl = 0;
         return pl;
     }
+    // the warp levels: local, below level 0, at most kMgWarpM nodes per side
+    pl.warp_level = pl.nl;
+    for (int c = pl.nl - 1; c >= 1 && pl.lv[c].local && pl.lv[c].m <= kMgWarpM; --c) pl.warp_level = c;
     pl.total = off;
     return pl;
+}
+
+// b_P = (M y)_P for a per-sample global vector y written by other CTAs of
+// the cluster in this launch (read through L2): the consistent P1 mass
+// stencil, h^2/12 per incident triangle on the diagonal and h^2/24 per
+// triangle sharing the edge (Sec. 3.1).
+__device__ __forceinline__ double mass_apply_cg(int m, int i, int j, double h2, const double *y, int node)
+{
+    const int mc = m - 1;
+    const bool cij = (i < mc && j < mc), cim = (i >= 1 && j < mc), cmm = (i >= 1 && j >= 1),
+               cjm = (i < mc && j >= 1);
+    const int ninc = 2 * cij + cim + 2 * cmm + cjm;
+    double acc = (double)ninc * (h2 / 12.0) * __ldcg(y + node);
+    const double e = h2 / 24.0;
+    if (i + 1 < m) acc += e * (double)(cij + cjm) * __ldcg(y + node + 1);
+    if (i > 0) acc += e * (double)(cim + cmm) * __ldcg(y + node - 1);
+    if (j + 1 < m) acc += e * (double)(cij + cim) * __ldcg(y + node + m);
+    if (j > 0) acc += e * (double)(cjm + cmm) * __ldcg(y + node - m);
+    if (i + 1 < m && j + 1 < m) acc += e * (double)(2 * cij) * __ldcg(y + node + m + 1);
+    if (i > 0 && j > 0) acc += e * (double)(2 * cmm) * __ldcg(y + node - m - 1);
+    return acc;
 }
 
 // Cluster sum for the multigrid kernel: every CTA writes its partial sums
@@ -239,6 +266,7 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1)
     double *vb0 = g.v + so;   // [2][S][n]: solution of the last block, guess of the next
     double *wb0 = g.w + so;
     double *b = g.b + so;
+    double *yb = g.y + so;
 
     // ---- one-time set-up: stencil rows of every level, zeroed tiles
     for (int c = 0; c < NL; ++c) {
@@ -325,141 +353,158 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1)
     //   coarsest:          damped Jacobi sweeps from XA
     //   ascend, level c:   XB = XA + P X_{c+1} on the stored rows and the halo
     //                      rows, RR = XB + omega D^-1 (BB - A XB) (pushed)
-    auto vcycle = [&]() {
-        for (int c = 0; c < NL - 1; ++c) {
-            const MgLevelPlan &P = plan.lv[c];
-            const bool dist = !P.local;
-            const int mc = P.m, R0 = sR0[c], rows = sR1[c] - R0, nown_c = rows * mc, base = 1 + mc;
-            const float *Dd = F_(P.off_d), *Ee = F_(P.off_e), *Nn = F_(P.off_n), *NE = F_(P.off_ne);
-            float *xa = F_(P.off_xa), *rr = F_(P.off_r), *bb = F_(P.off_b);
-            // pre-smoothing from zero: XA = omega D^-1 B
-            for (int l = tid; l < nown_c; l += nt) {
-                const float x = __fdividef(kMgOmega * bb[l], Dd[base + l]);
-                xa[base + l] = x;
-                if (dist) push(c, P.off_xa, mc, rows, l, x);
+    // Levels from plan.warp_level on (a few dozen nodes) run on warp 0 alone
+    // with warp barriers; lt / lnt are the thread's index and the stride.
+    const int WL = plan.warp_level;
+    auto bar = [&](bool wm, bool dist) {
+        if (wm) __syncwarp();
+        else level_sync(dist);
+    };
+    auto descend = [&](int c, bool wm) {
+        const int lt = wm ? (tid & 31) : tid, lnt = wm ? 32 : nt;
+        const MgLevelPlan &P = plan.lv[c];
+        const bool dist = !P.local;
+        const int mc = P.m, R0 = sR0[c], rows = sR1[c] - R0, nown_c = rows * mc, base = 1 + mc;
+        const float *Dd = F_(P.off_d), *Ee = F_(P.off_e), *Nn = F_(P.off_n), *NE = F_(P.off_ne);
+        float *xa = F_(P.off_xa), *rr = F_(P.off_r), *bb = F_(P.off_b);
+        // pre-smoothing from zero: XA = omega D^-1 B
+        for (int l = lt; l < nown_c; l += lnt) {
+            const float x = __fdividef(kMgOmega * bb[l], Dd[base + l]);
+            xa[base + l] = x;
+            if (dist) push(c, P.off_xa, mc, rows, l, x);
+        }
+        bar(wm, dist);
+        // residual RR = B - A XA
+        for (int l = lt; l < nown_c; l += lnt) {
+            const float r = bb[l] - spmv(Dd, Ee, Nn, NE, mc, xa, base + l);
+            rr[base + l] = r;
+            if (dist) push(c, P.off_r, mc, rows, l, r);
+        }
+        bar(wm, dist);
+        // restriction: B_{c+1}(I, J) = R(2I, 2J) + 1/2 sum of the six neighbours
+        const MgLevelPlan &Q = plan.lv[c + 1];
+        const int mq = Q.m;
+        const bool bcast = dist && Q.local;   // first local level: broadcast
+        int B0 = sR0[c + 1], B1 = sR1[c + 1];
+        if (bcast) mg_band(g.m, CS, rank, c + 1, &B0, &B1);
+        float *bq = F_(Q.off_b);
+        const int nq = (B1 - B0) * mq;
+        const int qdj = lnt / mq, qdi = lnt - qdj * mq;
+        int jl = lt / mq, I = lt - jl * mq;
+        for (int l = lt; l < nq; l += lnt, jl += qdj, I += qdi) {
+            if (I >= mq) {
+                I -= mq;
+                ++jl;
             }
-            level_sync(dist);
-            // residual RR = B - A XA
-            for (int l = tid; l < nown_c; l += nt) {
-                const float r = bb[l] - spmv(Dd, Ee, Nn, NE, mc, xa, base + l);
-                rr[base + l] = r;
-                if (dist) push(c, P.off_r, mc, rows, l, r);
-            }
-            level_sync(dist);
-            // restriction: B_{c+1}(I, J) = R(2I, 2J) + 1/2 sum of the six neighbours
-            const MgLevelPlan &Q = plan.lv[c + 1];
-            const int mq = Q.m;
-            const bool bcast = dist && Q.local;   // first local level: broadcast
-            int B0 = sR0[c + 1], B1 = sR1[c + 1];
-            if (bcast) mg_band(g.m, CS, rank, c + 1, &B0, &B1);
-            float *bq = F_(Q.off_b);
-            const int nq = (B1 - B0) * mq;
-            const int qdj = nt / mq, qdi = nt - qdj * mq;
-            int jl = tid / mq, I = tid - jl * mq;
-            for (int l = tid; l < nq; l += nt, jl += qdj, I += qdi) {
-                if (I >= mq) {
-                    I -= mq;
-                    ++jl;
-                }
-                const int J = B0 + jl;
-                const int i = 2 * I, j = 2 * J;
-                const int t = 1 + (j - (R0 - 1)) * mc + i;
-                float h = 0.0f;
-                if (i + 1 < mc) h += rr[t + 1];
-                if (i > 0) h += rr[t - 1];
-                if (j + 1 < mc) h += rr[t + mc];
-                if (j > 0) h += rr[t - mc];
-                if (i + 1 < mc && j + 1 < mc) h += rr[t + mc + 1];
-                if (i > 0 && j > 0) h += rr[t - mc - 1];
-                const float val = rr[t] + 0.5f * h;
-                if constexpr (CS > 1) {
-                    if (bcast) {
-                        const int q = J * mq + I;
-#pragma unroll 1
-                        for (int r = 0; r < CS; ++r) cl.map_shared_rank(bq, r)[q] = val;
-                        continue;
-                    }
-                }
-                bq[l] = val;
-            }
+            const int J = B0 + jl;
+            const int i = 2 * I, j = 2 * J;
+            const int t = 1 + (j - (R0 - 1)) * mc + i;
+            float h = 0.0f;
+            if (i + 1 < mc) h += rr[t + 1];
+            if (i > 0) h += rr[t - 1];
+            if (j + 1 < mc) h += rr[t + mc];
+            if (j > 0) h += rr[t - mc];
+            if (i + 1 < mc && j + 1 < mc) h += rr[t + mc + 1];
+            if (i > 0 && j > 0) h += rr[t - mc - 1];
+            const float val = rr[t] + 0.5f * h;
             if constexpr (CS > 1) {
-                if (bcast) cl.sync();
-            }
-        }
-        // coarsest level (held whole): damped Jacobi sweeps, ping-pong XA / XB
-        int xq_off;
-        {
-            const MgLevelPlan &P = plan.lv[NL - 1];
-            const int mc = P.m, nown_c = (sR1[NL - 1] - sR0[NL - 1]) * mc, base = 1 + mc;
-            const float *Dd = F_(P.off_d), *Ee = F_(P.off_e), *Nn = F_(P.off_n), *NE = F_(P.off_ne);
-            const float *bb = F_(P.off_b);
-            float *X = F_(P.off_xa), *Y = F_(P.off_xb);
-            xq_off = P.off_xa;
-            int yo = P.off_xb;
-            for (int l = tid; l < nown_c; l += nt) X[base + l] = __fdividef(kMgOmega * bb[l], Dd[base + l]);
-            for (int k = 1; k < kMgCoarsestSweeps; ++k) {
-                __syncthreads();
-                for (int l = tid; l < nown_c; l += nt) {
-                    const int t = base + l;
-                    Y[t] = X[t] + __fdividef(kMgOmega * (bb[l] - spmv(Dd, Ee, Nn, NE, mc, X, t)), Dd[t]);
+                if (bcast) {
+                    const int q = J * mq + I;
+#pragma unroll 1
+                    for (int r = 0; r < CS; ++r) cl.map_shared_rank(bq, r)[q] = val;
+                    continue;
                 }
-                float *tp = X;
-                X = Y;
-                Y = tp;
-                const int to = xq_off;
-                xq_off = yo;
-                yo = to;
             }
-            __syncthreads();
-            if (NL == 1) {
-                // one-level hierarchy: the result goes where the caller reads it
-                float *R = F_(P.off_r);
-                for (int l = tid; l < nown_c; l += nt) R[base + l] = X[base + l];
-                __syncthreads();
-            }
+            bq[l] = val;
         }
-        // ascend: interpolate and post-smooth
-        for (int c = NL - 2; c >= 0; --c) {
-            const MgLevelPlan &P = plan.lv[c], &Q = plan.lv[c + 1];
-            const bool dist = !P.local;
-            const int mc = P.m, R0 = sR0[c], R1 = sR1[c], rows = R1 - R0, nown_c = rows * mc, base = 1 + mc;
-            const int mq = Q.m, R0q = sR0[c + 1];
-            const float *Dd = F_(P.off_d), *Ee = F_(P.off_e), *Nn = F_(P.off_n), *NE = F_(P.off_ne);
-            const float *xa = F_(P.off_xa), *bb = F_(P.off_b);
-            float *xb = F_(P.off_xb), *rr = F_(P.off_r);
-            const float *xq = F_(xq_off);
-            // XB = XA + P X_{c+1}: stored rows, and the halo rows of a
-            // distributed level (their XA came with the pre-smoothing push)
-            const int jlo = (dist && has_lo) ? R0 - 1 : R0, jhi = (dist && has_hi) ? R1 + 1 : R1;
-            const int nx = (jhi - jlo) * mc;
-            const int xdj = nt / mc, xdi = nt - xdj * mc;
-            int jl = tid / mc, i = tid - jl * mc;
-            for (int l = tid; l < nx; l += nt, jl += xdj, i += xdi) {
-                if (i >= mc) {
-                    i -= mc;
-                    ++jl;
-                }
-                const int j = jlo + jl;
-                const int t = 1 + (j - (R0 - 1)) * mc + i;
-                const int tq = 1 + ((j >> 1) - (R0q - 1)) * mq + (i >> 1);
-                float pv;
-                if (!(i & 1) && !(j & 1)) pv = xq[tq];
-                else if ((i & 1) && !(j & 1)) pv = 0.5f * (xq[tq] + xq[tq + 1]);
-                else if (!(i & 1) && (j & 1)) pv = 0.5f * (xq[tq] + xq[tq + mq]);
-                else pv = 0.5f * (xq[tq] + xq[tq + mq + 1]);
-                xb[t] = xa[t] + pv;
-            }
-            __syncthreads();
-            // X_c = XB + omega D^-1 (B - A XB), into RR
-            for (int l = tid; l < nown_c; l += nt) {
+        if constexpr (CS > 1) {
+            if (bcast) cl.sync();
+        }
+    };
+    // coarsest level (held whole): damped Jacobi sweeps, ping-pong XA / XB;
+    // the result is in XB after an odd number of swaps, else in XA
+    const int coarse_res = (kMgCoarsestSweeps - 1) % 2 ? plan.lv[NL - 1].off_xb : plan.lv[NL - 1].off_xa;
+    auto coarsest = [&](bool wm) {
+        const int lt = wm ? (tid & 31) : tid, lnt = wm ? 32 : nt;
+        const MgLevelPlan &P = plan.lv[NL - 1];
+        const int mc = P.m, nown_c = (sR1[NL - 1] - sR0[NL - 1]) * mc, base = 1 + mc;
+        const float *Dd = F_(P.off_d), *Ee = F_(P.off_e), *Nn = F_(P.off_n), *NE = F_(P.off_ne);
+        const float *bb = F_(P.off_b);
+        float *X = F_(P.off_xa), *Y = F_(P.off_xb);
+        for (int l = lt; l < nown_c; l += lnt) X[base + l] = __fdividef(kMgOmega * bb[l], Dd[base + l]);
+        for (int k = 1; k < kMgCoarsestSweeps; ++k) {
+            bar(wm, false);
+            for (int l = lt; l < nown_c; l += lnt) {
                 const int t = base + l;
-                const float x = xb[t] + __fdividef(kMgOmega * (bb[l] - spmv(Dd, Ee, Nn, NE, mc, xb, t)), Dd[t]);
-                rr[t] = x;
-                if (dist) push(c, P.off_r, mc, rows, l, x);
+                Y[t] = X[t] + __fdividef(kMgOmega * (bb[l] - spmv(Dd, Ee, Nn, NE, mc, X, t)), Dd[t]);
             }
-            level_sync(dist);
-            xq_off = P.off_r;
+            float *tp = X;
+            X = Y;
+            Y = tp;
         }
+        bar(wm, false);
+        if (NL == 1) {
+            // one-level hierarchy: the result goes where the caller reads it
+            float *R = F_(P.off_r);
+            for (int l = lt; l < nown_c; l += lnt) R[base + l] = X[base + l];
+            bar(wm, false);
+        }
+    };
+    // interpolate from the tile at xq_off and post-smooth level c
+    auto ascend = [&](int c, bool wm, int xq_off) {
+        const int lt = wm ? (tid & 31) : tid, lnt = wm ? 32 : nt;
+        const MgLevelPlan &P = plan.lv[c], &Q = plan.lv[c + 1];
+        const bool dist = !P.local;
+        const int mc = P.m, R0 = sR0[c], R1 = sR1[c], rows = R1 - R0, nown_c = rows * mc, base = 1 + mc;
+        const int mq = Q.m, R0q = sR0[c + 1];
+        const float *Dd = F_(P.off_d), *Ee = F_(P.off_e), *Nn = F_(P.off_n), *NE = F_(P.off_ne);
+        const float *xa = F_(P.off_xa), *bb = F_(P.off_b);
+        float *xb = F_(P.off_xb), *rr = F_(P.off_r);
+        const float *xq = F_(xq_off);
+        // XB = XA + P X_{c+1}: stored rows, and the halo rows of a
+        // distributed level (their XA came with the pre-smoothing push).
+        // P: the coarse value at even-even nodes, else the mean of the two
+        // coarse ends of the fine edge (E, N or NE of the coarse node)
+        const int jlo = (dist && has_lo) ? R0 - 1 : R0, jhi = (dist && has_hi) ? R1 + 1 : R1;
+        const int nx = (jhi - jlo) * mc;
+        const int xdj = lnt / mc, xdi = lnt - xdj * mc;
+        int jl = lt / mc, i = lt - jl * mc;
+        for (int l = lt; l < nx; l += lnt, jl += xdj, i += xdi) {
+            if (i >= mc) {
+                i -= mc;
+                ++jl;
+            }
+            const int j = jlo + jl;
+            const int t = 1 + (j - (R0 - 1)) * mc + i;
+            const int tq = 1 + ((j >> 1) - (R0q - 1)) * mq + (i >> 1);
+            const float pv = 0.5f * (xq[tq] + xq[tq + (i & 1) + (j & 1) * mq]);
+            xb[t] = xa[t] + pv;
+        }
+        bar(wm, false);
+        // X_c = XB + omega D^-1 (B - A XB), into RR
+        for (int l = lt; l < nown_c; l += lnt) {
+            const int t = base + l;
+            const float x = xb[t] + __fdividef(kMgOmega * (bb[l] - spmv(Dd, Ee, Nn, NE, mc, xb, t)), Dd[t]);
+            rr[t] = x;
+            if (dist) push(c, P.off_r, mc, rows, l, x);
+        }
+        bar(wm, dist);
+    };
+    auto vcycle = [&]() {
+        const int top = WL < NL - 1 ? WL : NL - 1;   // levels [0, top) descend with all threads
+        for (int c = 0; c < top; ++c) descend(c, false);
+        if (WL < NL) {
+            __syncthreads();   // BB of the first warp level was written by every thread
+            if ((tid >> 5) == 0) {
+                for (int c = WL; c < NL - 1; ++c) descend(c, true);
+                coarsest(true);
+                for (int c = NL - 2; c >= WL; --c) ascend(c, true, c + 1 == NL - 1 ? coarse_res : plan.lv[c + 1].off_r);
+            }
+            __syncthreads();
+        } else {
+            coarsest(false);
+        }
+        for (int c = top - 1; c >= 0; --c) ascend(c, false, c + 1 == NL - 1 ? coarse_res : plan.lv[c + 1].off_r);
     };
 
     const MgLevelPlan &P0 = plan.lv[0];
@@ -482,12 +527,13 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1)
         const double *vcur = vb0 + vpar * SN;
         double *v = vb0 + (vpar ^ 1) * SN;
         vpar ^= 1;
+        // y = v + dt R(v, w) once per node (the mass product reads it at the
+        // seven stencil points)
 #pragma unroll 1
         for (int l = tid; l < nown; l += nt) {
             const int node = own0 + l;
-            const int j = node / m, i = node - j * m;
-            b[node] = mass_apply_y(m, i, j, g.h2, vcur, wcur, node, dt, g.a);
             const double vv = vcur[node], ww = wcur[node];
+            yb[node] = vv + dt * (vv * (vv - g.a) * (1.0 - vv) - ww);
             wnext[node] = ww + dt * g.eps * (vv - g.gam * ww);
             v[node] = step > 0 ? 2.0 * vv - v[node] : vv;
         }
@@ -498,7 +544,8 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1)
             for (int l = tid; l < nown; l += nt) {
                 const int node = own0 + l;
                 const int j = node / m, i = node - j * m;
-                const double bb = b[node];
+                const double bb = mass_apply_cg(m, i, j, g.h2, yb, node);
+                b[node] = bb;
                 const double rr = bb - stencil_apply_global(A64, n, m, node, i, j, v);
                 RR0[FB + l] = (float)rr;
                 acc[0] += bb * bb;

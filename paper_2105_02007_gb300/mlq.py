@@ -41,7 +41,8 @@ class MemberStats(ctypes.Structure):
     _fields_ = [("kernel_ms", ctypes.c_double), ("level", ctypes.c_int), ("coarse", ctypes.c_int),
                 ("cluster", ctypes.c_int), ("resident", ctypes.c_int), ("threads", ctypes.c_int),
                 ("npt", ctypes.c_int), ("samples", ctypes.c_int64),
-                ("nodes", ctypes.c_int64), ("steps", ctypes.c_int64), ("cg_iterations", ctypes.c_int64)]
+                ("nodes", ctypes.c_int64), ("steps", ctypes.c_int64), ("cg_iterations", ctypes.c_int64),
+                ("start_ms", ctypes.c_double), ("end_ms", ctypes.c_double)]
 
 
 _vp = ctypes.c_void_p
