@@ -1,0 +1,383 @@
+// mlq_3d.cuh -- P1 on Kuhn tetrahedra of a structured box (the 3D slab of
+// the configurations), Sec. 3.1: set-up of the 15-point stencils and the
+// batched time-block solver.
+//
+// Mesh convention (the same as the library's documented mesh, include/mlq.h):
+//   nodes   (i, j, k), node = i + mx (j + my k), x = Lx i / (mx - 1), ...
+//   cells   c = i + (mx - 1)(j + (my - 1) k), six tetrahedra e = 6 c + s;
+//           tetrahedron s walks from corner (i, j, k) to (i+1, j+1, k+1) along
+//           the unit steps perm[s][0], perm[s][1], perm[s][2] (Kuhn / Freudenthal
+//           splitting, nested under regular refinement)
+//   barycentric coordinates on tetrahedron s, xi = local coordinates in [0,1]^3
+//   along the steps: lambda_0 = 1 - xi_a, lambda_1 = xi_a - xi_b,
+//   lambda_2 = xi_b - xi_c, lambda_3 = xi_c (a, b, c = the step axes in order).
+// Every edge of a tetrahedron joins its vertices q < q' along a direction with
+// components in {0, 1}: the stencil of a node P is its diagonal plus the
+// couplings to P + d for the seven such directions d (slot = dx + 2 dy + 4 dz);
+// the coupling to P - d is slot d of node P - d (the matrices are symmetric).
+//
+// Solver (one sample per cluster of CS CTAs, everything in global memory and
+// L2; the 3D levels outgrow the shared memory of a cluster):
+//   per time block  y = v + dt R(v, w); b = M y; w <- w + dt eps (v - gam w);
+//                   r = b - A v in FP64
+//   inner solve     Jacobi-preconditioned CG (Chronopoulos-Gear: one cluster
+//                   reduction per iteration) on A d = r / ||r|| from d = 0 in
+//                   the inner precision TI, v += ||r|| d; the mixed path
+//                   repeats while ||b - A v|| > rtol ||b|| (iterative
+//                   refinement in FP64), the FP64 path runs one sweep to that
+//                   tolerance
+//   QoI             Q = sum_P m_P v_P with the lumped mass m = M 1.
+// CTA `rank` owns a contiguous range of grid lines (j, k); another CTA's
+// values are read through L2 (ld.cg) after a cluster barrier.
+#pragma once
+
+#include "mlq_3d_types.cuh"
+#include "mlq_kernels.cuh"
+
+namespace mlq {
+
+// ---------------------------------------------------------------------------
+// Level set-up (sample independent): FP64 mass stencil [8][n] and lumped mass
+// m_P = (incident tetrahedra) |e| / 4.  Gathers over the (up to) 24
+// tetrahedra at the node in a fixed order.
+// ---------------------------------------------------------------------------
+__global__ void level3d_setup_kernel(Grid3 g, double *__restrict__ M3, double *__restrict__ lump)
+{
+    const int64_t P = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= g.n) return;
+    const int i = (int)(P % g.mx), j = (int)((P / g.mx) % g.my), k = (int)(P / ((int64_t)g.mx * g.my));
+    const double vol = g.hx * g.hy * g.hz / 6.0;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int cnt = 0;
+    for (int d = 0; d < 8; ++d) {   // cell with P at corner d
+        const int ci = i - (d & 1), cj = j - ((d >> 1) & 1), ck = k - ((d >> 2) & 1);
+        if (ci < 0 || cj < 0 || ck < 0 || ci >= g.mx - 1 || cj >= g.my - 1 || ck >= g.mz - 1) continue;
+        for (int s = 0; s < 6; ++s) {
+            int q = -1;
+            for (int t = 0; t < 4; ++t)
+                if (kuhn_vertex(s, t) == d) q = t;
+            if (q < 0) continue;
+            ++cnt;
+            acc[0] += vol / 10.0;
+            for (int t = q + 1; t < 4; ++t) acc[kuhn_vertex(s, t) ^ d] += vol / 20.0;
+        }
+    }
+    for (int sl = 0; sl < 8; ++sl) M3[(int64_t)sl * g.n + P] = acc[sl];
+    lump[P] = cnt * vol / 4.0;
+}
+
+// ---------------------------------------------------------------------------
+// K2 (3D): per sample the stencil of A = M + dt K(theta): A64 [S][9][n] FP64
+// (slot 8 = 1 / diagonal) and, when Ai is not null, the same in FP32.
+// ---------------------------------------------------------------------------
+__global__ void stencil3d_setup_kernel(const double *__restrict__ cs2, Grid3 g, double dt, double s_l, double s_t,
+                                       int S, double *__restrict__ A64, float *__restrict__ A32)
+{
+    const int64_t P = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int smp = blockIdx.y;
+    if (P >= g.n || smp >= S) return;
+    const int i = (int)(P % g.mx), j = (int)((P / g.mx) % g.my), k = (int)(P / ((int64_t)g.mx * g.my));
+    const double vol = g.hx * g.hy * g.hz / 6.0;
+    const int64_t ne = 6LL * (g.mx - 1) * (g.my - 1) * (g.mz - 1);
+    const double *c2 = cs2 + (size_t)smp * ne * 2;
+    const double hds = 0.5 * (s_l - s_t);
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int d = 0; d < 8; ++d) {
+        const int ci = i - (d & 1), cj = j - ((d >> 1) & 1), ck = k - ((d >> 2) & 1);
+        if (ci < 0 || cj < 0 || ck < 0 || ci >= g.mx - 1 || cj >= g.my - 1 || ck >= g.mz - 1) continue;
+        const int64_t cell = ci + (int64_t)(g.mx - 1) * (cj + (int64_t)(g.my - 1) * ck);
+        for (int s = 0; s < 6; ++s) {
+            int q = -1;
+            for (int t = 0; t < 4; ++t)
+                if (kuhn_vertex(s, t) == d) q = t;
+            if (q < 0) continue;
+            const double c = c2[(6 * cell + s) * 2], sn = c2[(6 * cell + s) * 2 + 1];
+            // D = s_t I + (s_l - s_t) f f^T with f f^T = (1/2)[[1 + c, sn, 0], [sn, 1 - c, 0], [0, 0, 0]]
+            const double d11 = s_t + hds * (1.0 + c), d22 = s_t + hds * (1.0 - c), d12 = hds * sn, d33 = s_t;
+            double G[4][3];
+            kuhn_grads(g, s, G);
+            const double Dq[3] = {d11 * G[q][0] + d12 * G[q][1], d12 * G[q][0] + d22 * G[q][1], d33 * G[q][2]};
+            for (int t = q; t < 4; ++t) {
+                const double kq = vol * (Dq[0] * G[t][0] + Dq[1] * G[t][1] + Dq[2] * G[t][2]);
+                const double mq = vol / 20.0 * (t == q ? 2.0 : 1.0);
+                acc[kuhn_vertex(s, t) ^ d] += mq + dt * kq;
+            }
+        }
+    }
+    double *a = A64 + (size_t)smp * kSlots3D * g.n;
+    for (int sl = 0; sl < 8; ++sl) a[(int64_t)sl * g.n + P] = acc[sl];
+    a[8LL * g.n + P] = 1.0 / acc[0];
+    if (A32) {
+        float *f = A32 + (size_t)smp * kSlots3D * g.n;
+        for (int sl = 0; sl < 8; ++sl) f[(int64_t)sl * g.n + P] = (float)acc[sl];
+        f[8LL * g.n + P] = (float)(1.0 / acc[0]);
+    }
+}
+
+// (C x)_P for a symmetric 15-point stencil C [8][n]: slot d at P couples to
+// P + d, slot d at P - d couples to P - d.  x read through L2.
+template <typename T, typename TX>
+__device__ __forceinline__ T apply15(const T *__restrict__ C, const Grid3 &g, const TX *x, int64_t P, int i, int j,
+                                     int k)
+{
+    const int64_t n = g.n;
+    T acc = C[P] * (T)__ldcg(x + P);
+#pragma unroll
+    for (int sl = 1; sl < 8; ++sl) {
+        const int dx = sl & 1, dy = (sl >> 1) & 1, dz = (sl >> 2) & 1;
+        const int64_t off = dir_offset(g, sl);
+        if (i + dx < g.mx && j + dy < g.my && k + dz < g.mz) acc += C[sl * n + P] * (T)__ldcg(x + P + off);
+        if (i >= dx && j >= dy && k >= dz) acc += C[sl * n + P - off] * (T)__ldcg(x + P - off);
+    }
+    return acc;
+}
+
+// node walk over the CTA's nodes P = P0 + l (l = tid, tid + nt, ...) keeping
+// (i, j, k) without a division per node
+struct Walk3 {
+    int i, j, k, di, dj, dk;
+    __device__ void init(int64_t P, int nt, const Grid3 &g)
+    {
+        i = (int)(P % g.mx);
+        const int64_t line = P / g.mx;
+        j = (int)(line % g.my);
+        k = (int)(line / g.my);
+        di = nt % g.mx;
+        const int lines = nt / g.mx;
+        dj = lines % g.my;
+        dk = lines / g.my;
+    }
+    __device__ void next(const Grid3 &g)
+    {
+        i += di;
+        j += dj;
+        k += dk;
+        if (i >= g.mx) {
+            i -= g.mx;
+            ++j;
+        }
+        if (j >= g.my) {
+            j -= g.my;
+            ++k;
+        }
+    }
+};
+
+
+template <typename TI, int CS>
+__global__ void __launch_bounds__(512, 1) slab_solve_3d_kernel(Solve3Args<TI> g)
+{
+    __shared__ double wsl[32][4];
+    __shared__ double csl[2][4];
+    __shared__ Ctl ctl;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int sample = blockIdx.x / CS;
+    const Grid3 G = g.g;
+    const int64_t n = G.n;
+    const int64_t lines = (int64_t)G.my * G.mz;
+    const int64_t own0 = (lines * rank / CS) * G.mx, own1 = (lines * (rank + 1) / CS) * G.mx;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    constexpr bool mixed = sizeof(TI) == 4;
+
+    const size_t so = (size_t)sample * n;
+    const size_t SN = (size_t)g.S * n;
+    const double *A64 = g.A64 + (size_t)sample * kSlots3D * n;
+    const TI *Ai = g.Ai + (size_t)sample * kSlots3D * n;
+    const TI *Dinv = Ai + 8 * n;
+    double *v = g.v + so, *wb0 = g.w + so, *b = g.b + so, *yb = g.y + so;
+    TI *R = g.r + so, *U = g.u + so, *W = g.wv + so, *Sv = g.s + so, *Pv = g.p + so, *X = g.x + so;
+
+    for (int64_t P = own0 + tid; P < own1; P += nt) {
+        double v0, w0;
+        if (g.v0) {
+            v0 = g.v0[P];
+            w0 = g.w0 ? g.w0[P] : 0.0;
+        } else {
+            const int i = (int)(P % G.mx), j = (int)((P / G.mx) % G.my), k = (int)(P / ((int64_t)G.mx * G.my));
+            const double xx = g.Lx * i / (G.mx - 1), yy = g.Ly * j / (G.my - 1), zz = g.Lz * k / (G.mz - 1);
+            v0 = (xx * xx + yy * yy + zz * zz <= g.radius2) ? 1.0 : 0.0;
+            w0 = 0.0;
+        }
+        v[P] = v0;
+        wb0[P] = w0;
+    }
+    cl.sync();
+
+    int wpar = 0, par = 0;
+    int64_t total_iters = 0;
+    int32_t status = S_CONVERGED;
+    const double dt = g.dt;
+
+    for (int step = 0; step < g.nsteps; ++step) {
+        const double *wcur = wb0 + wpar * SN;
+        double *wnext = wb0 + (wpar ^ 1) * SN;
+        for (int64_t P = own0 + tid; P < own1; P += nt) {
+            const double vv = v[P], ww = wcur[P];
+            yb[P] = vv + dt * (vv * (vv - g.a) * (1.0 - vv) - ww);
+            wnext[P] = ww + dt * g.eps * (vv - g.gam * ww);
+        }
+        wpar ^= 1;
+        cl.sync();
+        {
+            double acc[2] = {0.0, 0.0};
+            Walk3 wk;
+            wk.init(own0 + tid, nt, G);
+            for (int64_t P = own0 + tid; P < own1; P += nt, wk.next(G)) {
+                const double bb = apply15<double, double>(g.M3, G, yb, P, wk.i, wk.j, wk.k);
+                b[P] = bb;
+                const double rr = bb - apply15<double, double>(A64, G, v, P, wk.i, wk.j, wk.k);
+                R[P] = (TI)rr;
+                acc[0] += bb * bb;
+                acc[1] += rr * rr;
+            }
+            cluster_reduce<2, CS>(acc, wsl, csl, par, [&](double(&t)[2]) {
+                ctl.s0 = t[0];
+                ctl.s1 = t[1];
+            });
+            par ^= 1;
+        }
+        const double bnorm2 = ctl.s0;
+        double rnorm2 = ctl.s1;
+        if (!(isfinite(bnorm2) && isfinite(rnorm2))) {
+            status = S_NONFINITE;
+            break;
+        }
+        const double tol_out2 = g.rtol_out * g.rtol_out * bnorm2;
+        bool nonfinite = false, solved = false;
+        const int sweeps = mixed ? g.max_sweeps : 1;
+        for (int sweep = 0; sweep < sweeps; ++sweep) {
+            if (sweep > 0) {
+                double racc[1] = {0.0};
+                Walk3 wk;
+                wk.init(own0 + tid, nt, G);
+                for (int64_t P = own0 + tid; P < own1; P += nt, wk.next(G)) {
+                    const double rr = b[P] - apply15<double, double>(A64, G, v, P, wk.i, wk.j, wk.k);
+                    R[P] = (TI)rr;
+                    racc[0] += rr * rr;
+                }
+                cluster_reduce<1, CS>(racc, wsl, csl, par, [&](double(&t)[1]) { ctl.s1 = t[0]; });
+                par ^= 1;
+                rnorm2 = ctl.s1;
+                if (!isfinite(rnorm2)) {
+                    nonfinite = true;
+                    break;
+                }
+            }
+            if (rnorm2 <= tol_out2) {
+                solved = true;
+                break;
+            }
+            const double rnorm = sqrt(rnorm2);
+            const TI rscale = (TI)(1.0 / rnorm);
+            // inner target relative to the normalised start: rtol_in, or what
+            // the outer test still needs when that is looser; the FP64 path
+            // solves to the outer target in this one sweep
+            const double need = tol_out2 / rnorm2;
+            const double tol_in2 = mixed ? fmax(g.rtol_in * g.rtol_in, 0.0625 * need) : need;
+
+            // init: r0 normalised, u0 = D^-1 r0, x = p = s = 0
+            for (int64_t P = own0 + tid; P < own1; P += nt) {
+                const TI rr = R[P] * rscale;
+                R[P] = rr;
+                U[P] = Dinv[P] * rr;
+                X[P] = (TI)0;
+                Pv[P] = (TI)0;
+                Sv[P] = (TI)0;
+            }
+            cl.sync();
+            double gamma_prev = 1.0, eta_prev = 1.0;
+            int it = 0;
+            auto decide = [&](double gamma, double delta, double rr) {
+                double alpha = 0.0, beta = 0.0;
+                int code;
+                if (!isfinite(rr) || !isfinite(gamma) || !isfinite(delta)) code = 3;
+                else if (rr <= tol_in2) code = 1;
+                else if (it >= g.max_iter) code = 2;
+                else {
+                    code = 0;
+                    double eta = delta;
+                    if (it > 0) {
+                        beta = gamma / gamma_prev;
+                        eta = delta - beta * beta * eta_prev;
+                    }
+                    alpha = gamma / eta;
+                    gamma_prev = gamma;
+                    eta_prev = eta;
+                }
+                ctl.alpha = alpha;
+                ctl.beta = beta;
+                ctl.code = code;
+            };
+            double gacc = 0.0, racc = 0.0;   // (r, u) and (r, r) of the current iterate
+            for (int64_t P = own0 + tid; P < own1; P += nt) {
+                const TI rr = R[P], uu = U[P];
+                gacc += (double)(rr * uu);
+                racc += (double)(rr * rr);
+            }
+            while (true) {
+                // w = A u, (w, u); one reduction of (r, u), (w, u), (r, r)
+                double pacc[3] = {gacc, 0.0, racc};
+                {
+                    Walk3 wk;
+                    wk.init(own0 + tid, nt, G);
+                    for (int64_t P = own0 + tid; P < own1; P += nt, wk.next(G)) {
+                        const TI ww = apply15<TI, TI>(Ai, G, U, P, wk.i, wk.j, wk.k);
+                        W[P] = ww;
+                        pacc[1] += (double)(ww * U[P]);
+                    }
+                }
+                cluster_reduce<3, CS>(pacc, wsl, csl, par, [&](double(&t)[3]) { decide(t[0], t[1], t[2]); });
+                par ^= 1;
+                const int code = ctl.code;
+                if (code != 0) {
+                    if (code == 3) nonfinite = true;
+                    else if (code == 2) status = status == S_CONVERGED ? S_MAXITER : status;
+                    break;
+                }
+                const TI ta = (TI)ctl.alpha, tb = (TI)ctl.beta;
+                // s = w + b s; p = u + b p; x += a p; r -= a s; u = D^-1 r
+                gacc = 0.0;
+                racc = 0.0;
+                for (int64_t P = own0 + tid; P < own1; P += nt) {
+                    const TI ww = W[P], uu = U[P];
+                    const TI ss = it == 0 ? ww : ww + tb * Sv[P];
+                    const TI pp = it == 0 ? uu : uu + tb * Pv[P];
+                    Sv[P] = ss;
+                    Pv[P] = pp;
+                    X[P] += ta * pp;
+                    const TI rr = R[P] - ta * ss;
+                    R[P] = rr;
+                    const TI un = Dinv[P] * rr;
+                    U[P] = un;
+                    gacc += (double)(rr * un);
+                    racc += (double)(rr * rr);
+                }
+                ++it;
+                cl.sync();
+            }
+            total_iters += it;
+            if (nonfinite) break;
+            for (int64_t P = own0 + tid; P < own1; P += nt) v[P] = fma((double)X[P], rnorm, v[P]);
+            cl.sync();
+            if (!mixed) solved = true;
+        }
+        if (nonfinite) {
+            status = S_NONFINITE;
+            break;
+        }
+        if (!solved && status == S_CONVERGED) status = S_MAXITER;
+    }
+
+    double qacc[1] = {0.0};
+    for (int64_t P = own0 + tid; P < own1; P += nt) qacc[0] += g.lump[P] * v[P];
+    cluster_reduce<1, CS>(qacc, wsl, csl, par, [&](double(&t)[1]) { ctl.s0 = t[0]; });
+    if (rank == 0 && tid == 0) {
+        g.q[sample] = status == S_NONFINITE ? __longlong_as_double(0x7ff8000000000000LL) : ctl.s0;
+        g.iters[sample] = (int32_t)(total_iters > 0x7fffffff ? 0x7fffffff : total_iters);
+        g.status[sample] = status;
+    }
+    cl.sync();
+}
+
+}  // namespace mlq

@@ -45,6 +45,11 @@ struct Level {
     mlq::FastDiv divm{};
     int tuned_cs = 0, tuned_npt = 0, tuned_threads = 0;  // set by mlq_autotune (mixed path)
     bool tuned_mg = false;
+    // dim 3: mx x my x mz nodes on [0, Lx] x [0, Ly] x [0, Lz], six Kuhn
+    // tetrahedra per cube; the level's FP64 mass stencil and lumped mass
+    mlq::Grid3 g3{};
+    double Lx = 1.0, Ly = 1.0, Lz = 0.25;
+    double *d_M3 = nullptr, *d_lump = nullptr;
 };
 
 struct Member {
@@ -53,7 +58,7 @@ struct Member {
     const double *d_xi = nullptr;
     // workspace pieces
     double *cs2 = nullptr, *A64 = nullptr, *v = nullptr, *w = nullptr, *b = nullptr, *y = nullptr, *q = nullptr;
-    void *Ai = nullptr, *r = nullptr, *s = nullptr, *wc = nullptr, *p = nullptr, *x = nullptr;
+    void *Ai = nullptr, *r = nullptr, *s = nullptr, *wc = nullptr, *p = nullptr, *x = nullptr, *u = nullptr;
     int32_t *iters = nullptr, *status = nullptr;
     float *mgA[mlq::kMgMaxLevels] = {};    // coarse-level stencils (multigrid)
     mlq::D3 *mgD[mlq::kMgMaxLevels] = {};  // coarse-level mean conductivities
@@ -204,8 +209,22 @@ std::vector<Shape> mg_candidates(const mlq_ctx *ctx, const Level &L)
     return out;
 }
 
+// 3D: one sample per cluster, vectors in global memory; the cluster grows
+// with the sample so that each CTA streams a few thousand nodes or more
+Shape choose_launch_3d(const mlq_ctx *ctx, const Level &L)
+{
+    const int64_t lines = (int64_t)L.g3.my * L.g3.mz;
+    int cs = L.n >= 200000 ? 16 : (L.n >= 50000 ? 8 : (L.n >= 12000 ? 4 : 1));
+    if (ctx->opt.cluster > 0) cs = ctx->opt.cluster;
+    while (cs > 1 && (cs > ctx->max_cluster || cs > lines)) cs /= 2;
+    int threads = ctx->opt.threads > 0 ? ctx->opt.threads / 32 * 32 : 512;
+    threads = std::min(512, std::max(32, threads));
+    return Shape{cs, threads, false, 0, 0};
+}
+
 Shape choose_launch(mlq_ctx *ctx, const Level &L, int64_t S = 0)
 {
+    if (L.dim == 3) return choose_launch_3d(ctx, L);
     if (ctx->opt.precision == MLQ_MIXED && ctx->opt.precond == 1 && ctx->opt.storage != 2) {
         if (L.tuned_cs > 0 && L.tuned_mg && ctx->opt.cluster <= 0 && ctx->opt.threads <= 0) {
             Shape sh{L.tuned_cs, L.tuned_threads, true, (size_t)mlq::mg_plan(L.m, L.tuned_cs).total, L.tuned_npt};
@@ -354,6 +373,20 @@ size_t member_bytes(const mlq_ctx *ctx, const Level &L, int64_t S)
     const size_t sn = (size_t)S * L.n;
     size_t t = 0;
     auto add = [&](size_t bytes) { t += align_up(bytes, 256); };
+    if (L.dim == 3) {
+        add((size_t)S * L.ne * 2 * 8);                 // cs2
+        add(sn * mlq::kSlots3D * 8);                    // A64
+        if (mixed) add(sn * mlq::kSlots3D * 4);         // A32
+        add(sn * 8);                                    // v
+        add(2 * sn * 8);                                // w
+        add(sn * 8);                                    // b
+        add(sn * 8);                                    // y
+        for (int k = 0; k < 6; ++k) add(sn * ti);       // r u w s p x
+        add((size_t)S * 8);
+        add((size_t)S * 4);
+        add((size_t)S * 4);
+        return t;
+    }
     add((size_t)S * L.ne * 2 * 8);          // cs2
     add(sn * mlq::kSlots2D * 8);            // A64
     if (mixed) add(sn * mlq::kSlots2D * 4); // A32
@@ -390,6 +423,25 @@ void member_carve(const mlq_ctx *ctx, const Level &L, Member &mb, char *&cur)
         cur += align_up(bytes, 256);
         return (void *)p;
     };
+    if (L.dim == 3) {
+        mb.cs2 = (double *)take((size_t)mb.S * L.ne * 2 * 8);
+        mb.A64 = (double *)take(sn * mlq::kSlots3D * 8);
+        mb.Ai = mixed ? take(sn * mlq::kSlots3D * 4) : (void *)mb.A64;
+        mb.v = (double *)take(sn * 8);
+        mb.w = (double *)take(2 * sn * 8);
+        mb.b = (double *)take(sn * 8);
+        mb.y = (double *)take(sn * 8);
+        mb.r = take(sn * ti);
+        mb.u = take(sn * ti);
+        mb.wc = take(sn * ti);
+        mb.s = take(sn * ti);
+        mb.p = take(sn * ti);
+        mb.x = take(sn * ti);
+        mb.q = (double *)take((size_t)mb.S * 8);
+        mb.iters = (int32_t *)take((size_t)mb.S * 4);
+        mb.status = (int32_t *)take((size_t)mb.S * 4);
+        return;
+    }
     mb.cs2 = (double *)take((size_t)mb.S * L.ne * 2 * 8);
     mb.A64 = (double *)take(sn * mlq::kSlots2D * 8);
     mb.Ai = mixed ? take(sn * mlq::kSlots2D * 4) : (void *)mb.A64;
@@ -462,9 +514,70 @@ int launch_synthesis(mlq_ctx *ctx, const Level &L, const double *d_xi, int S, do
 // solve so that the long solver kernels do not hold SMs the set-ups wait for.
 enum { kSetup = 1, kSolve = 2, kBoth = 3 };
 
+// 3D member: K1 as in 2D, the 15-point stencil set-up, the global-memory
+// cluster solver
+template <typename TI>
+int launch_member3d_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream_t st, int slot, int phase)
+{
+    const bool mixed = sizeof(TI) == 4;
+    if (phase & kSetup) {
+        int st1 = launch_synthesis(ctx, L, mb.d_xi, (int)mb.S, mb.cs2, st);
+        if (st1 != MLQ_OK) return st1;
+        MLQ_CUDA(ctx, mlq::launch_stencil3d_setup(mb.cs2, L.g3, L.dt, ctx->model.s_l, ctx->model.s_t, (int)mb.S,
+                                                  mb.A64, mixed ? (float *)mb.Ai : nullptr, st));
+        ctx->launches++;
+    }
+    if (!(phase & kSolve)) return MLQ_OK;
+    mlq::Solve3Args<TI> a{};
+    a.g = L.g3;
+    a.Lx = L.Lx;
+    a.Ly = L.Ly;
+    a.Lz = L.Lz;
+    a.dt = L.dt;
+    a.nsteps = L.nsteps;
+    a.a = ctx->model.a;
+    a.eps = ctx->model.eps;
+    a.gam = ctx->model.gamma;
+    a.rtol_out = ctx->opt.rtol;
+    a.rtol_in = ctx->opt.rtol_inner;
+    a.max_iter = ctx->opt.max_iter;
+    a.max_sweeps = mixed ? ctx->opt.max_sweeps : 1;
+    a.M3 = L.d_M3;
+    a.lump = L.d_lump;
+    a.A64 = mb.A64;
+    a.Ai = (const TI *)mb.Ai;
+    a.v = mb.v;
+    a.w = mb.w;
+    a.b = mb.b;
+    a.y = mb.y;
+    a.r = (TI *)mb.r;
+    a.u = (TI *)mb.u;
+    a.wv = (TI *)mb.wc;
+    a.s = (TI *)mb.s;
+    a.p = (TI *)mb.p;
+    a.x = (TI *)mb.x;
+    a.v0 = L.d_v0;
+    a.w0 = L.d_w0;
+    a.radius2 = L.radius * L.radius;
+    a.S = (int)mb.S;
+    a.q = mb.q;
+    a.iters = mb.iters;
+    a.status = mb.status;
+    const Shape sh = choose_launch_3d(ctx, L);
+    const bool timed = ctx->profile && slot >= 0 && slot < kStreams;
+    const unsigned evf = ctx->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if (timed) MLQ_CUDA(ctx, cudaEventRecordWithFlags(ctx->ev_t0[slot], st, evf));
+    if constexpr (sizeof(TI) == 4) MLQ_CUDA(ctx, mlq::launch_3d_f32(sh.cs, a, (int)mb.S, sh.threads, st));
+    else MLQ_CUDA(ctx, mlq::launch_3d_f64(sh.cs, a, (int)mb.S, sh.threads, st));
+    if (timed) MLQ_CUDA(ctx, cudaEventRecordWithFlags(ctx->ev_t1[slot], st, evf));
+    ctx->launches++;
+    return MLQ_OK;
+}
+
 template <typename TI>
 int launch_member_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream_t st, int slot, int phase)
 {
+    if (L.dim == 3) return launch_member3d_t<TI>(ctx, L, mb, st, slot, phase);
     const bool mixed = sizeof(TI) == 4;
     // K1: KL synthesis (theta -> cos 2t, sin 2t)
     if (phase & kSetup) {
@@ -765,6 +878,8 @@ int mlq_destroy(mlq_ctx *ctx)
         cudaFree(L.d_theta_mean);
         cudaFree(L.d_v0);
         cudaFree(L.d_w0);
+        cudaFree(L.d_M3);
+        cudaFree(L.d_lump);
     }
     cudaFree(ctx->ws);
     delete ctx;
@@ -792,12 +907,17 @@ int mlq_set_model(mlq_ctx *ctx, const mlq_model *m)
 int mlq_add_level(mlq_ctx *ctx, int level, int dim, const int32_t *dims, const double *lengths, double dt,
                   int32_t nsteps)
 {
-    (void)lengths;
     if (!ctx || !dims || level < 0 || level >= kMaxLevels) return MLQ_EINVAL;
-    if (dim == 3) return MLQ_EUNSUPPORTED;
-    if (dim != 2) return MLQ_EINVAL;
-    const int m = dims[0];
-    if (m < 2 || m > 8193 || !(dt > 0.0) || nsteps < 0) return MLQ_EINVAL;
+    if (dim != 2 && dim != 3) return MLQ_EINVAL;
+    if (!(dt > 0.0) || nsteps < 0) return MLQ_EINVAL;
+    if (dim == 3) {
+        const int64_t nn = (int64_t)dims[0] * dims[1] * dims[2];
+        if (dims[0] < 2 || dims[1] < 2 || dims[2] < 2 || nn > (int64_t)1 << 28) return MLQ_EINVAL;
+        if (lengths && !(lengths[0] > 0.0 && lengths[1] > 0.0 && lengths[2] > 0.0)) return MLQ_EINVAL;
+    } else if (dims[0] < 2 || dims[0] > 8193) {
+        return MLQ_EINVAL;
+    }
+    MLQ_CUDA(ctx, cudaSetDevice(ctx->device));
     ctx->generation++;
     Level &L = ctx->levels[level];
     cudaFree(L.d_phi);
@@ -806,7 +926,37 @@ int mlq_add_level(mlq_ctx *ctx, int level, int dim, const int32_t *dims, const d
     cudaFree(L.d_theta_mean);
     cudaFree(L.d_v0);
     cudaFree(L.d_w0);
+    cudaFree(L.d_M3);
+    cudaFree(L.d_lump);
     L = Level();
+    if (dim == 3) {
+        L.dim = 3;
+        if (lengths) {
+            L.Lx = lengths[0];
+            L.Ly = lengths[1];
+            L.Lz = lengths[2];
+        }
+        mlq::Grid3 &g = L.g3;
+        g.mx = dims[0];
+        g.my = dims[1];
+        g.mz = dims[2];
+        g.n = dims[0] * dims[1] * dims[2];
+        g.hx = L.Lx / (g.mx - 1);
+        g.hy = L.Ly / (g.my - 1);
+        g.hz = L.Lz / (g.mz - 1);
+        L.n = g.n;
+        L.ne = 6 * (g.mx - 1) * (g.my - 1) * (g.mz - 1);
+        L.dt = dt;
+        L.nsteps = nsteps;
+        MLQ_CUDA(ctx, cudaMalloc(&L.d_M3, sizeof(double) * 8 * (size_t)L.n));
+        MLQ_CUDA(ctx, cudaMalloc(&L.d_lump, sizeof(double) * (size_t)L.n));
+        MLQ_CUDA(ctx, mlq::launch_level3d_setup(g, L.d_M3, L.d_lump, ctx->stream));
+        MLQ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        ctx->launches++;
+        L.defined = true;
+        return MLQ_OK;
+    }
+    const int m = dims[0];
     L.dim = 2;
     L.m = m;
     L.n = m * m;
@@ -1204,6 +1354,7 @@ int mlq_autotune(mlq_ctx *ctx, int level, int64_t S, const double *xi, int probe
     if (check_level(ctx, level) != MLQ_OK) return MLQ_EINVAL;
     if (ctx->opt.precision != MLQ_MIXED || ctx->opt.storage == 2) return MLQ_EUNSUPPORTED;
     Level &L = ctx->levels[level];
+    if (L.dim == 3) return MLQ_EUNSUPPORTED;
     std::vector<Shape> cand = ctx->opt.precond == 1 ? mg_candidates(ctx, L) : reg_candidates(ctx, L);
     if (cand.empty()) return MLQ_EUNSUPPORTED;
     // also try the next nodes-per-thread variant of each cluster size

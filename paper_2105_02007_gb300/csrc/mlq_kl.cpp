@@ -109,6 +109,129 @@ void p1_at(const Grid2 &g, const double *f, int K, double px, double py, double 
     for (int k = 0; k < K; ++k) out[k] = wa * f[a * K + k] + wb * f[nb * K + k] + wc * f[nc * K + k];
 }
 
+// 3D structured box of Kuhn tetrahedra (see the mesh convention in mlq.h):
+// nodes i + mx (j + my k), six tetrahedra per cube stepping along the axes
+// of one permutation.
+struct Grid3h {
+    int mx, my, mz;
+    double hx, hy, hz;
+    int64_t n() const { return (int64_t)mx * my * mz; }
+};
+
+const int kPerm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+// y = M x for the P1 mass matrix (|e|/20 (1 + delta_ab) per tetrahedron)
+void mass_apply3(const Grid3h &g, const double *x, double *y, int ncol)
+{
+    const int64_t n = g.n();
+    std::fill(y, y + n * ncol, 0.0);
+    const double c = g.hx * g.hy * g.hz / 6.0 / 20.0;
+    for (int k = 0; k + 1 < g.mz; ++k)
+        for (int j = 0; j + 1 < g.my; ++j)
+            for (int i = 0; i + 1 < g.mx; ++i)
+                for (int s = 0; s < 6; ++s) {
+                    int64_t v[4];
+                    int idx[3] = {i, j, k};
+                    v[0] = idx[0] + (int64_t)g.mx * (idx[1] + (int64_t)g.my * idx[2]);
+                    for (int q = 0; q < 3; ++q) {
+                        idx[kPerm[s][q]] += 1;
+                        v[q + 1] = idx[0] + (int64_t)g.mx * (idx[1] + (int64_t)g.my * idx[2]);
+                    }
+                    for (int col = 0; col < ncol; ++col) {
+                        double sum = 0.0;
+                        for (int a = 0; a < 4; ++a) sum += x[v[a] * ncol + col];
+                        for (int a = 0; a < 4; ++a) y[v[a] * ncol + col] += c * (sum + x[v[a] * ncol + col]);
+                    }
+                }
+}
+
+// Value at (px, py, pz) of the P1 interpolant of K nodal fields on the Kuhn
+// mesh: the tetrahedron of the cube is the one whose steps follow the local
+// coordinates in decreasing order; the weights are the differences of the
+// sorted coordinates (continuous across faces, so ties do not matter).
+void p1_at3(const Grid3h &g, const double *f, int K, double px, double py, double pz, double *out)
+{
+    const double s[3] = {px / g.hx, py / g.hy, pz / g.hz};
+    const int mm[3] = {g.mx, g.my, g.mz};
+    int c[3];
+    double u[3];
+    for (int a = 0; a < 3; ++a) {
+        c[a] = std::min(std::max((int)std::floor(s[a]), 0), mm[a] - 2);
+        u[a] = s[a] - c[a];
+    }
+    int ord[3] = {0, 1, 2};
+    std::stable_sort(ord, ord + 3, [&](int a, int b) { return u[a] > u[b]; });
+    int idx[3] = {c[0], c[1], c[2]};
+    const double wts[4] = {1.0 - u[ord[0]], u[ord[0]] - u[ord[1]], u[ord[1]] - u[ord[2]], u[ord[2]]};
+    for (int k = 0; k < K; ++k) out[k] = 0.0;
+    for (int q = 0; q < 4; ++q) {
+        if (q > 0) idx[ord[q - 1]] += 1;
+        const int64_t v = idx[0] + (int64_t)g.mx * (idx[1] + (int64_t)g.my * idx[2]);
+        for (int k = 0; k < K; ++k) out[k] += wts[q] * f[v * K + k];
+    }
+}
+
+// K steps of pivoted Cholesky of the covariance over the node coordinates
+// (first maximum of the residual diagonal as pivot), B = L^T M L, its
+// eigenpairs by cyclic Jacobi, modes v_k = L q_k sorted by decreasing
+// eigenvalue, largest-magnitude entry positive (eqs. approxEig, redEig).
+template <typename Coord, typename Mass>
+int build_kl_nodes(int64_t n, Coord coord, Mass mass, double sigma2, double ell, int K, double *modes_out,
+                   double *lambda_out)
+{
+    std::vector<double> X(n * 3);
+    for (int64_t t = 0; t < n; ++t) coord(t, &X[t * 3]);
+    auto cov = [&](int64_t a, int64_t b) {
+        const double dx = X[a * 3] - X[b * 3], dy = X[a * 3 + 1] - X[b * 3 + 1], dz = X[a * 3 + 2] - X[b * 3 + 2];
+        return sigma2 * std::exp(-(dx * dx + dy * dy + dz * dz) / ell);
+    };
+    std::vector<double> L((size_t)n * K, 0.0), r(n, sigma2);
+    for (int k = 0; k < K; ++k) {
+        int64_t piv = std::max_element(r.begin(), r.end()) - r.begin();
+        const double lp = std::sqrt(r[piv]);
+        if (!(lp > 0.0)) return MLQ_EINVAL;
+        for (int64_t t = 0; t < n; ++t) {
+            double c = cov(t, piv);
+            for (int q = 0; q < k; ++q) c -= L[(size_t)t * K + q] * L[(size_t)piv * K + q];
+            L[(size_t)t * K + k] = c / lp;
+        }
+        for (int64_t t = 0; t < n; ++t) r[t] -= L[(size_t)t * K + k] * L[(size_t)t * K + k];
+    }
+    std::vector<double> ML((size_t)n * K);
+    mass(L.data(), ML.data(), K);
+    std::vector<double> B((size_t)K * K, 0.0);
+    for (int a = 0; a < K; ++a)
+        for (int c = a; c < K; ++c) {
+            double sum = 0.0;
+            for (int64_t t = 0; t < n; ++t) sum += L[(size_t)t * K + a] * ML[(size_t)t * K + c];
+            B[(size_t)a * K + c] = sum;
+            B[(size_t)c * K + a] = sum;
+        }
+    std::vector<double> lam, Q;
+    sym_eigen(K, B, lam, Q);
+    std::vector<int> ord(K);
+    for (int k = 0; k < K; ++k) ord[k] = k;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) { return lam[a] > lam[c]; });
+    for (int k = 0; k < K; ++k) {
+        const int src = ord[k];
+        lambda_out[k] = lam[src];
+        double big = 0.0;
+        int64_t arg = 0;
+        for (int64_t t = 0; t < n; ++t) {
+            double sum = 0.0;
+            for (int q = 0; q < K; ++q) sum += L[(size_t)t * K + q] * Q[(size_t)q * K + src];
+            modes_out[(size_t)t * K + k] = sum;
+            if (std::fabs(sum) > big) {
+                big = std::fabs(sum);
+                arg = t;
+            }
+        }
+        if (modes_out[(size_t)arg * K + k] < 0.0)
+            for (int64_t t = 0; t < n; ++t) modes_out[(size_t)t * K + k] = -modes_out[(size_t)t * K + k];
+    }
+    return MLQ_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -116,9 +239,23 @@ extern "C" {
 int mlq_build_kl(int dim, const int32_t *dims, const double *lengths, double sigma2, double ell, int K,
                  double *modes_out, double *lambda_out)
 {
-    (void)lengths;
-    if (dim == 3) return MLQ_EUNSUPPORTED;
-    if (dim != 2 || !dims || !modes_out || !lambda_out || !(sigma2 > 0.0) || !(ell > 0.0)) return MLQ_EINVAL;
+    if ((dim != 2 && dim != 3) || !dims || !modes_out || !lambda_out || !(sigma2 > 0.0) || !(ell > 0.0))
+        return MLQ_EINVAL;
+    if (dim == 3) {
+        const double Lx = lengths ? lengths[0] : 1.0, Ly = lengths ? lengths[1] : 1.0,
+                     Lz = lengths ? lengths[2] : 0.25;
+        if (dims[0] < 2 || dims[1] < 2 || dims[2] < 2 || !(Lx > 0.0 && Ly > 0.0 && Lz > 0.0)) return MLQ_EINVAL;
+        Grid3h g{dims[0], dims[1], dims[2], Lx / (dims[0] - 1), Ly / (dims[1] - 1), Lz / (dims[2] - 1)};
+        const int64_t n = g.n();
+        if (K < 1 || K > n || K > 4096) return MLQ_EINVAL;
+        auto coord = [&](int64_t t, double *x) {
+            x[0] = g.hx * (double)(t % g.mx);
+            x[1] = g.hy * (double)((t / g.mx) % g.my);
+            x[2] = g.hz * (double)(t / ((int64_t)g.mx * g.my));
+        };
+        auto mass = [&](const double *x, double *y, int ncol) { mass_apply3(g, x, y, ncol); };
+        return build_kl_nodes(n, coord, mass, sigma2, ell, K, modes_out, lambda_out);
+    }
     const int m = dims[0];
     if (m < 2) return MLQ_EINVAL;
     const int64_t n = (int64_t)m * m;
@@ -186,8 +323,27 @@ int mlq_build_kl(int dim, const int32_t *dims, const double *lengths, double sig
 int mlq_centroid_table(int dim, const int32_t *fine_dims, const double *modes_f, int K, const int32_t *coarse_dims,
                        double *phi_out)
 {
-    if (dim == 3) return MLQ_EUNSUPPORTED;
-    if (dim != 2 || !fine_dims || !coarse_dims || !modes_f || !phi_out || K < 1) return MLQ_EINVAL;
+    if ((dim != 2 && dim != 3) || !fine_dims || !coarse_dims || !modes_f || !phi_out || K < 1) return MLQ_EINVAL;
+    if (dim == 3) {
+        // the box is the same on both meshes; lengths drop out of the
+        // node-index arithmetic, so unit spacing per axis is used
+        for (int a = 0; a < 3; ++a)
+            if (fine_dims[a] < 2 || coarse_dims[a] < 2) return MLQ_EINVAL;
+        Grid3h gf{fine_dims[0], fine_dims[1], fine_dims[2], 1.0 / (fine_dims[0] - 1), 1.0 / (fine_dims[1] - 1),
+                  1.0 / (fine_dims[2] - 1)};
+        const double H[3] = {1.0 / (coarse_dims[0] - 1), 1.0 / (coarse_dims[1] - 1), 1.0 / (coarse_dims[2] - 1)};
+        int64_t e = 0;
+        for (int k = 0; k + 1 < coarse_dims[2]; ++k)
+            for (int j = 0; j + 1 < coarse_dims[1]; ++j)
+                for (int i = 0; i + 1 < coarse_dims[0]; ++i)
+                    for (int s = 0; s < 6; ++s, ++e) {
+                        // centroid: 3/4, 2/4, 1/4 of a cell along the first, second, third step
+                        double p[3] = {(double)i, (double)j, (double)k};
+                        for (int q = 0; q < 3; ++q) p[kPerm[s][q]] += (3.0 - q) / 4.0;
+                        p1_at3(gf, modes_f, K, p[0] * H[0], p[1] * H[1], p[2] * H[2], phi_out + e * K);
+                    }
+        return MLQ_OK;
+    }
     const int mf = fine_dims[0], mc = coarse_dims[0];
     if (mf < 2 || mc < 2) return MLQ_EINVAL;
     Grid2 gf{mf, 1.0 / (mf - 1)};

@@ -9,6 +9,7 @@
 #include <cstddef>
 #include <cuda_runtime.h>
 
+#include "mlq_3d_types.cuh"
 #include "mlq_kernels.cuh"
 #include "mlq_mg.cuh"
 
@@ -26,6 +27,13 @@ MLQ_DECLARE_REG(4)
 MLQ_DECLARE_REG(8)
 MLQ_DECLARE_REG(16)
 #undef MLQ_DECLARE_REG
+
+// 3D (Kuhn tetrahedra), mlq_3d_inst.cu
+cudaError_t launch_3d_f32(int cs, const Solve3Args<float> &a, int nclusters, int threads, cudaStream_t st);
+cudaError_t launch_3d_f64(int cs, const Solve3Args<double> &a, int nclusters, int threads, cudaStream_t st);
+cudaError_t launch_level3d_setup(const Grid3 &g, double *M3, double *lump, cudaStream_t st);
+cudaError_t launch_stencil3d_setup(const double *cs2, const Grid3 &g, double dt, double s_l, double s_t, int S,
+                                   double *A64, float *A32, cudaStream_t st);
 
 cudaError_t launch_slab_f32(int cs, bool resident, const SolveArgs<float> &a, int nclusters, int threads,
                             size_t smem, cudaStream_t st);

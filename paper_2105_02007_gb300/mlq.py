@@ -131,24 +131,43 @@ def default_model(**kw) -> Model:
     return m
 
 
-def build_kl(m: int, sigma2: float, ell: float, K: int):
-    """KL modes (n x K) and eigenvalues (K) on the m x m structured mesh."""
-    dims = np.array([m, 0, 0], dtype=np.int32)
-    modes = np.zeros((m * m, K))
+def _dims(m):
+    """(dim, int32[3]) from m (2D, m x m nodes) or (mx, my, mz) (3D)."""
+    if np.ndim(m) == 0:
+        return 2, np.array([int(m), 0, 0], dtype=np.int32)
+    return 3, np.array([int(v) for v in m], dtype=np.int32)
+
+
+def _counts(dim, d):
+    """(nodes, elements) of a structured mesh."""
+    if dim == 2:
+        return int(d[0]) ** 2, 2 * (int(d[0]) - 1) ** 2
+    return int(d[0] * d[1] * d[2]), 6 * int((d[0] - 1) * (d[1] - 1) * (d[2] - 1))
+
+
+def build_kl(m, sigma2: float, ell: float, K: int, lengths=None):
+    """KL modes (n x K) and eigenvalues (K) on the structured mesh: m x m
+    nodes on the unit square, or m = (mx, my, mz) nodes on the box with the
+    given lengths (default 1 x 1 x 0.25) in Kuhn tetrahedra."""
+    dim, dims = _dims(m)
+    n, _ = _counts(dim, dims)
+    lg = None if lengths is None else np.ascontiguousarray(lengths, dtype=np.float64)
+    modes = np.zeros((n, K))
     lam = np.zeros(K)
-    _check(_lib.mlq_build_kl(2, dims.ctypes.data_as(_vp), None, sigma2, ell, K, modes.ctypes.data_as(_vp),
-                             lam.ctypes.data_as(_vp)), "mlq_build_kl")
+    _check(_lib.mlq_build_kl(dim, dims.ctypes.data_as(_vp), None if lg is None else lg.ctypes.data_as(_vp),
+                             sigma2, ell, K, modes.ctypes.data_as(_vp), lam.ctypes.data_as(_vp)), "mlq_build_kl")
     return modes, lam
 
 
-def centroid_table(m_fine: int, modes_f: np.ndarray, m_coarse: int) -> np.ndarray:
-    """Midpoint-rule transfer of fine nodal modes to the coarse elements."""
+def centroid_table(m_fine, modes_f: np.ndarray, m_coarse) -> np.ndarray:
+    """Midpoint-rule transfer of fine nodal modes to the coarse elements (2D:
+    m x m meshes; 3D: (mx, my, mz) meshes of the same box)."""
     K = modes_f.shape[1]
-    fd = np.array([m_fine, 0, 0], dtype=np.int32)
-    cd = np.array([m_coarse, 0, 0], dtype=np.int32)
+    dim, fd = _dims(m_fine)
+    _, cd = _dims(m_coarse)
     mf, pm = _host(modes_f, np.float64)
-    phi = np.zeros((2 * (m_coarse - 1) ** 2, K))
-    _check(_lib.mlq_centroid_table(2, fd.ctypes.data_as(_vp), pm, K, cd.ctypes.data_as(_vp),
+    phi = np.zeros((_counts(dim, cd)[1], K))
+    _check(_lib.mlq_centroid_table(dim, fd.ctypes.data_as(_vp), pm, K, cd.ctypes.data_as(_vp),
                                    phi.ctypes.data_as(_vp)), "mlq_centroid_table")
     return phi
 
@@ -208,11 +227,16 @@ class Context:
     def set_model(self, **kw):
         _check(_lib.mlq_set_model(self._h, ctypes.byref(default_model(**kw))), "mlq_set_model", self._h)
 
-    def add_level(self, level: int, m: int, dt: float, nsteps: int, dim: int = 2):
-        dims = np.array([m, 0, 0], dtype=np.int32)
-        _check(_lib.mlq_add_level(self._h, level, dim, dims.ctypes.data_as(_vp), None, dt, nsteps),
+    def add_level(self, level: int, m, dt: float, nsteps: int, lengths=None):
+        """Level on m x m nodes (2D) or m = (mx, my, mz) nodes of the box with
+        `lengths` (3D, default 1 x 1 x 0.25)."""
+        dim, dims = _dims(m)
+        lg = None if lengths is None else np.ascontiguousarray(lengths, dtype=np.float64)
+        _check(_lib.mlq_add_level(self._h, level, dim, dims.ctypes.data_as(_vp),
+                                  None if lg is None else lg.ctypes.data_as(_vp), dt, nsteps),
                "mlq_add_level", self._h)
-        self.levels[level] = dict(m=m, dt=dt, nsteps=nsteps, n=m * m, ne=2 * (m - 1) ** 2)
+        n, ne = _counts(dim, dims)
+        self.levels[level] = dict(m=m, dt=dt, nsteps=nsteps, n=n, ne=ne)
 
     def set_initial_state(self, level: int, v0, w0=None):
         v, pv = _host(v0, np.float64)

@@ -65,3 +65,27 @@ def test_product_centroid_table_matches_oracle(mlq):
         ref = O.centroid_table(fine, modes, coarse)
         got = mlq.centroid_table(33, modes, mc)
         assert np.allclose(got, ref, rtol=0, atol=1e-15)
+
+
+def test_product_kl_3d_matches_oracle_invariants(mlq):
+    # Kuhn-tetrahedra box 0.5 x 0.75 x 0.25: the same eigenvalues, M-orthogonal
+    # modes and the same represented covariance as the oracle's builder
+    dims, lengths, K = (6, 7, 4), (0.5, 0.75, 0.25), 8
+    pm, pl = mlq.build_kl(dims, 0.09, 0.04, K, lengths=lengths)
+    mesh = O.mesh3d(*dims, *lengths)
+    om, ol = O.kl_build(mesh, 0.09, 0.04, K)
+    assert np.allclose(pl, ol, rtol=1e-11, atol=1e-15)
+    rp, ci, mv, _ = O.assemble(mesh)
+    M = O.csr_to_dense(rp, ci, mv, mesh.n)
+    assert np.allclose(pm.T @ M @ pm, np.diag(pl), atol=1e-13)
+    assert np.allclose(pm @ pm.T, om @ om.T, atol=1e-12)
+
+
+def test_product_centroid_table_3d_matches_oracle(mlq):
+    fine = O.mesh3d(9, 9, 5)
+    modes, _ = O.kl_build(fine, 0.09, 0.04, 4)
+    for cd in ((9, 9, 5), (5, 5, 3), (3, 3, 2)):
+        coarse = O.mesh3d(*cd)
+        ref = O.centroid_table(fine, modes, coarse)
+        got = mlq.centroid_table((9, 9, 5), modes, cd)
+        assert np.allclose(got, ref, rtol=0, atol=1e-14)
