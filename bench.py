@@ -249,6 +249,72 @@ def run_case(spec: str):
     return 0
 
 
+# 3D levels (Kuhn tetrahedra on [0,1]^2 x [0,0.25]): h_0 = 1/32 with 9 node
+# planes, refined by halving; dt_0 = 0.05 halved per level, T = 10.
+LEVEL3_DIMS = [(33, 33, 9), (65, 65, 17), (129, 129, 33), (257, 257, 65)]
+ELL3 = 0.15 ** 2
+# Algorithmic bytes per DOF of the 3D Jacobi-PCG (Chronopoulos-Gear) as a
+# memory-streaming solver moves them, each array once per pass: update pass
+# reads w s p x r u and 1/diag, writes s p x r u (48 B FP32); matvec pass
+# reads 8 stencil slots and u, writes w (40 B FP32) -> 88 B per iteration;
+# FP64 inner: 176 B.  Per block: reaction / w update (32 B), b = M y and
+# r = b - A v (two FP64 15-point passes, stencil slots 64 B + vectors 28 B),
+# one refinement residual (~90 B), v update (20 B) -> ~300 B.
+BYTES3D_PER_DOF_ITER = {"mixed": 88.0, "fp64": 176.0}
+BYTES3D_PER_DOF_STEP = 300.0
+
+
+def level3_dt(l):
+    return 0.05 * 0.5 ** l
+
+
+def run_case3d(spec: str):
+    """One 3D member solve: --case3d level=L,samples=S,steps=N[,precision=mixed|fp64][,K=16].
+    KL modes of c = 0.09 exp(-|x-y|^2 / 0.15^2) on the level's own mesh.
+    Prints time, DOF-steps/s, iterations and the algorithmic bandwidth
+    against the measured HBM copy peak."""
+    kv = dict(item.split("=") for item in spec.split(","))
+    level = int(kv.get("level", 2))
+    S = int(kv.get("samples", 4))
+    steps = int(kv.get("steps", 2))
+    K = int(kv.get("K", 16))
+    prec_name = kv.get("precision", "mixed")
+    from paper_2105_02007_gb300 import build, inputs
+
+    build.build()
+    from paper_2105_02007_gb300 import mlq
+
+    prec = mlq.MLQ_MIXED if prec_name == "mixed" else mlq.MLQ_FP64
+    dims = LEVEL3_DIMS[level]
+    modes, _ = mlq.build_kl(dims, SIGMA2, ELL3, K)
+    phi = mlq.centroid_table(dims, modes, dims)
+    with mlq.Context(0, prec) as ctx:
+        ctx.add_level(level, dims, level3_dt(level), steps)
+        ctx.set_kl(level, phi)
+        ctx.set_profiling(True)
+        xi = inputs.gaussian_xi(0, level, 0, S, K)
+        ctx.solve(level, xi)    # warm-up
+        res = ctx.solve(level, xi)
+        prof = ctx.member_profile()[0]
+    n = dims[0] * dims[1] * dims[2]
+    it = prof["cg_iterations"]
+    sec = prof["kernel_ms"] / 1e3
+    algo = n * (it * BYTES3D_PER_DOF_ITER[prec_name] + S * steps * BYTES3D_PER_DOF_STEP)
+    peaks = None
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = (peaks or {}).get("hbm_gbs", 6800.0)
+    print(json.dumps({"case3d": spec, "dims": dims, "kernel_ms": prof["kernel_ms"], "cg_iterations": it,
+                      "iterations_per_block": it / (S * steps), "cluster": prof["cluster"],
+                      "threads": prof["threads"], "dof_steps_per_s": n * S * steps / sec,
+                      "algorithmic_gbs": algo / sec / 1e9, "hbm_peak_gbs": hbm,
+                      "frac": algo / sec / 1e9 / hbm, "q0": float(res["q_fine"][0]),
+                      "status": [int(x) for x in res["status"][:4]]}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -262,9 +328,12 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-graphs", action="store_true", help="run estimates eagerly instead of as CUDA graphs")
     ap.add_argument("--case", default=None, help="profile one member solve, e.g. level=4,samples=1,steps=4")
+    ap.add_argument("--case3d", default=None, help="one 3D member solve, e.g. level=2,samples=8,steps=2")
     args = ap.parse_args()
     if args.case:
         return run_case(args.case)
+    if args.case3d:
+        return run_case3d(args.case3d)
     if args.impl == "reference":
         return run_reference(args)
 

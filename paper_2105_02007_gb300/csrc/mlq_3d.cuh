@@ -165,7 +165,7 @@ struct Walk3 {
 
 
 template <typename TI, int CS>
-__global__ void __launch_bounds__(512, 1) slab_solve_3d_kernel(Solve3Args<TI> g)
+__global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
 {
     __shared__ double wsl[32][4];
     __shared__ double csl[2][4];
@@ -184,9 +184,14 @@ __global__ void __launch_bounds__(512, 1) slab_solve_3d_kernel(Solve3Args<TI> g)
     const size_t SN = (size_t)g.S * n;
     const double *A64 = g.A64 + (size_t)sample * kSlots3D * n;
     const TI *Ai = g.Ai + (size_t)sample * kSlots3D * n;
-    const TI *Dinv = Ai + 8 * n;
+    const TI *__restrict__ Dinv = Ai + 8 * n;
     double *v = g.v + so, *wb0 = g.w + so, *b = g.b + so, *yb = g.y + so;
-    TI *R = g.r + so, *U = g.u + so, *W = g.wv + so, *Sv = g.s + so, *Pv = g.p + so, *X = g.x + so;
+    TI *__restrict__ R = g.r + so;
+    TI *__restrict__ U = g.u + so;
+    TI *__restrict__ W = g.wv + so;
+    TI *__restrict__ Sv = g.s + so;
+    TI *__restrict__ Pv = g.p + so;
+    TI *__restrict__ X = g.x + so;
 
     for (int64_t P = own0 + tid; P < own1; P += nt) {
         double v0, w0;
@@ -321,6 +326,7 @@ __global__ void __launch_bounds__(512, 1) slab_solve_3d_kernel(Solve3Args<TI> g)
                 {
                     Walk3 wk;
                     wk.init(own0 + tid, nt, G);
+#pragma unroll 2
                     for (int64_t P = own0 + tid; P < own1; P += nt, wk.next(G)) {
                         const TI ww = apply15<TI, TI>(Ai, G, U, P, wk.i, wk.j, wk.k);
                         W[P] = ww;
@@ -339,6 +345,7 @@ __global__ void __launch_bounds__(512, 1) slab_solve_3d_kernel(Solve3Args<TI> g)
                 // s = w + b s; p = u + b p; x += a p; r -= a s; u = D^-1 r
                 gacc = 0.0;
                 racc = 0.0;
+#pragma unroll 4
                 for (int64_t P = own0 + tid; P < own1; P += nt) {
                     const TI ww = W[P], uu = U[P];
                     const TI ss = it == 0 ? ww : ww + tb * Sv[P];

@@ -102,6 +102,7 @@ struct mlq_ctx {
     std::string cuda_error;
     int max_cluster = 8;
     int smem_optin = 48 * 1024;
+    int num_sms = 1;
     // optional per-member timing of the slab kernel (CUDA events on the
     // member's stream) and iteration totals of the last solve/estimate
     bool profile = false;
@@ -209,12 +210,15 @@ std::vector<Shape> mg_candidates(const mlq_ctx *ctx, const Level &L)
     return out;
 }
 
-// 3D: one sample per cluster, vectors in global memory; the cluster grows
-// with the sample so that each CTA streams a few thousand nodes or more
-Shape choose_launch_3d(const mlq_ctx *ctx, const Level &L)
+// 3D: one sample per cluster, vectors in global memory (bandwidth-bound):
+// the cluster grows while the batch still covers the SMs twice (two CTAs
+// resident per SM) and every CTA keeps a few thousand nodes
+Shape choose_launch_3d(const mlq_ctx *ctx, const Level &L, int64_t S = 0)
 {
     const int64_t lines = (int64_t)L.g3.my * L.g3.mz;
-    int cs = L.n >= 200000 ? 16 : (L.n >= 50000 ? 8 : (L.n >= 12000 ? 4 : 1));
+    int cs = 1;
+    const int64_t slots = 2LL * std::max(ctx->num_sms, 1);
+    while (cs < 16 && (int64_t)(2 * cs) * std::max<int64_t>(S, 1) <= slots && L.n / (2 * cs) >= 4096) cs *= 2;
     if (ctx->opt.cluster > 0) cs = ctx->opt.cluster;
     while (cs > 1 && (cs > ctx->max_cluster || cs > lines)) cs /= 2;
     int threads = ctx->opt.threads > 0 ? ctx->opt.threads / 32 * 32 : 512;
@@ -224,7 +228,7 @@ Shape choose_launch_3d(const mlq_ctx *ctx, const Level &L)
 
 Shape choose_launch(mlq_ctx *ctx, const Level &L, int64_t S = 0)
 {
-    if (L.dim == 3) return choose_launch_3d(ctx, L);
+    if (L.dim == 3) return choose_launch_3d(ctx, L, S);
     if (ctx->opt.precision == MLQ_MIXED && ctx->opt.precond == 1 && ctx->opt.storage != 2) {
         if (L.tuned_cs > 0 && L.tuned_mg && ctx->opt.cluster <= 0 && ctx->opt.threads <= 0) {
             Shape sh{L.tuned_cs, L.tuned_threads, true, (size_t)mlq::mg_plan(L.m, L.tuned_cs).total, L.tuned_npt};
@@ -563,7 +567,7 @@ int launch_member3d_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream
     a.q = mb.q;
     a.iters = mb.iters;
     a.status = mb.status;
-    const Shape sh = choose_launch_3d(ctx, L);
+    const Shape sh = choose_launch_3d(ctx, L, mb.S);
     const bool timed = ctx->profile && slot >= 0 && slot < kStreams;
     const unsigned evf = ctx->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (timed) MLQ_CUDA(ctx, cudaEventRecordWithFlags(ctx->ev_t0[slot], st, evf));
@@ -841,6 +845,7 @@ int mlq_create(mlq_ctx **out, int device, void *cuda_stream, const mlq_options *
     int nonportable = 0;
     cudaDeviceGetAttribute(&nonportable, cudaDevAttrClusterLaunch, device);
     cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
     ctx->max_cluster = mlq::active_reg_cs16(8, 512, 48 * 1024) > 0 ? 16 : 8;
     cudaGetLastError();
     (void)nonportable;
