@@ -315,6 +315,70 @@ def run_case3d(spec: str):
     return 0
 
 
+def run_serve(spec: str):
+    """Serving workload: --serve rate=R,requests=N[,levels=0-2][,chunk=16][,seed=0].
+    A Poisson stream (exponential inter-arrival, seed) of requests; each picks
+    a level uniformly in the range, 1..256 samples, a target RMSE log-uniform
+    in [1e-4, 1e-2] x |Qbar| (Qbar = 1.125e-3, the 2D estimate) and xi drawn
+    with seed = request id.  Requests go through mlq_submit / mlq_poll on one
+    context; prints latency percentiles and served DOF-steps/s."""
+    import time
+
+    kv = dict(item.split("=") for item in spec.split(","))
+    rate = float(kv.get("rate", 50))
+    nreq = int(kv.get("requests", 200))
+    lo, hi = (int(x) for x in kv.get("levels", "0-2").split("-"))
+    chunk = int(kv.get("chunk", 16))
+    seed = int(kv.get("seed", 0))
+    from paper_2105_02007_gb300 import build, inputs
+
+    build.build()
+    from paper_2105_02007_gb300 import mlq
+
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, nreq))
+    levels = rng.integers(lo, hi + 1, nreq)
+    samples = rng.integers(1, 257, nreq)
+    targets = 1.125e-3 * 10.0 ** rng.uniform(-4, -2, nreq)
+    modes, _ = mlq.build_kl(LEVEL_M[-1], SIGMA2, ELL, K_MODES)
+    ctx = mlq.Context(0, mlq.MLQ_MIXED)
+    for l in range(lo, hi + 1):
+        ctx.add_level(l, LEVEL_M[l], level_dt(l), level_steps(l))
+        ctx.set_kl(l, mlq.centroid_table(LEVEL_M[-1], modes, LEVEL_M[l]))
+    xis = [inputs.gaussian_xi(i, int(levels[i]), 0, int(samples[i]), K_MODES) for i in range(nreq)]
+    # warm-up: one small request per level (kernel load, workspace)
+    for l in range(lo, hi + 1):
+        ctx.wait(ctx.submit(l, inputs.gaussian_xi(0, l, 0, 2, K_MODES), 0.0, 2))
+    pending, done = {}, {}
+    t0 = time.monotonic()
+    i = 0
+    while i < nreq or pending:
+        now = time.monotonic() - t0
+        while i < nreq and arrivals[i] <= now:
+            pending[ctx.submit(int(levels[i]), xis[i], float(targets[i]), chunk)] = i
+            i += 1
+        for t in list(pending):
+            r = ctx.poll(t)
+            if r is not None:
+                done[pending.pop(t)] = r
+        time.sleep(0.001)
+    wall = time.monotonic() - t0
+    ctx.close()
+    lat = np.array([done[k]["latency_ms"] for k in range(nreq)])
+    used = np.array([done[k]["samples_used"] for k in range(nreq)])
+    dof = sum(int(used[k]) * LEVEL_M[levels[k]] ** 2 * level_steps(int(levels[k])) for k in range(nreq))
+    offered = rate * float(np.mean([LEVEL_M[l] ** 2 * level_steps(l) for l in range(lo, hi + 1)])) * 128.5
+    print(json.dumps({"serve": spec, "requests": nreq, "completed": len(done),
+                      "status_ok": int(sum(done[k]["status"] == 0 for k in range(nreq))),
+                      "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
+                                     "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
+                      "wall_s": wall, "samples_used_mean": float(used.mean()),
+                      "early_stop_fraction": float(np.mean(used < samples)),
+                      "served_dof_steps_per_s": dof / wall, "offered_dof_steps_per_s_at_full_samples": offered,
+                      "batches_mean": float(np.mean([done[k]["batches"] for k in range(nreq)]))}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -329,11 +393,14 @@ def main():
     ap.add_argument("--no-graphs", action="store_true", help="run estimates eagerly instead of as CUDA graphs")
     ap.add_argument("--case", default=None, help="profile one member solve, e.g. level=4,samples=1,steps=4")
     ap.add_argument("--case3d", default=None, help="one 3D member solve, e.g. level=2,samples=8,steps=2")
+    ap.add_argument("--serve", default=None, help="serving stream, e.g. rate=50,requests=200,levels=0-2")
     args = ap.parse_args()
     if args.case:
         return run_case(args.case)
     if args.case3d:
         return run_case3d(args.case3d)
+    if args.serve:
+        return run_serve(args.serve)
     if args.impl == "reference":
         return run_reference(args)
 

@@ -277,6 +277,46 @@ int mlq_launch_count(mlq_ctx *ctx, int64_t *count);
  * resident may be NULL. */
 int mlq_level_launch(mlq_ctx *ctx, int level, int *cluster, int *threads, int *resident);
 
+/* Serving: requests for the QoI mean at one level, answered asynchronously.
+ *
+ * Each request asks for the plain Monte Carlo mean of Q_l (eq. SL) over at
+ * most `samples` draws xi (rows of a samples x K matrix), stopping early once
+ * the statistical error is small enough: the samples are solved in chunks of
+ * `chunk` (a power of two), and the request finishes at the first chunk
+ * boundary n where sqrt(V_n / n) <= target_rmse (V_n the unbiased sample
+ * variance of the first n values, n >= 2), or after all samples.  A worker
+ * thread of the context packs the next chunk of every waiting request at the
+ * level of the oldest one into a single batched solve (continuous batching,
+ * at most 2^24 DOFs and 65535 samples per batch).  Each sample's Q depends
+ * only on its own xi, and the stopping rule only on the values in index
+ * order, so a request's result does not depend on what it was batched with
+ * (bit for bit on the 2D levels; the 3D launch shape follows the batch size,
+ * so there to rounding).  xi is copied at submission (host pointer).
+ * mlq_submit / mlq_poll may be called from any thread; the other calls on
+ * the context wait for the worker's current batch.  mlq_destroy stops the
+ * worker after its current batch; unfinished requests are dropped. */
+typedef struct {
+    int level;           /* a defined level of the context */
+    int64_t samples;     /* maximum number of samples, 1 .. 2^20 */
+    const double *xi;    /* host, samples x K, row-major (K of the level's KL table) */
+    double target_rmse;  /* <= 0: solve all samples */
+    int32_t chunk;       /* samples per chunk, a power of two; 0 = 16 */
+} mlq_request;
+
+typedef struct {
+    int status;            /* MLQ_OK, or the error of a batch of this request */
+    int32_t worst;         /* worst per-sample status (mlq_sample_status) */
+    int64_t samples_used;  /* n at which the request stopped */
+    double mean, rmse;     /* mean of Q_l over the n samples and sqrt(V_n / n) */
+    double latency_ms;     /* submission to completion (host clock) */
+    int64_t batches;       /* batched solves the request took part in */
+} mlq_result;
+
+int mlq_submit(mlq_ctx *ctx, const mlq_request *req, uint64_t *ticket);
+/* MLQ_ENOTREADY while the request runs; MLQ_OK fills *out and releases the
+ * ticket (a second poll of it returns MLQ_EINVAL). */
+int mlq_poll(mlq_ctx *ctx, uint64_t ticket, mlq_result *out);
+
 const char *mlq_strerror(int status);
 const char *mlq_last_cuda_error(mlq_ctx *ctx);
 

@@ -14,8 +14,14 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
 #include <string>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 namespace {
@@ -77,7 +83,18 @@ int mg_coarse_levels(int m)
 
 }  // namespace
 
+struct Server;  // request queue and worker of mlq_submit / mlq_poll
+
+// takes the context's lock for the rest of the calling scope (ctx may be null)
+#define MLQ_GUARD(c)                                      \
+    std::unique_lock<std::recursive_mutex> mlq_guard_;    \
+    if (c) mlq_guard_ = std::unique_lock<std::recursive_mutex>((c)->mu)
+
 struct mlq_ctx {
+    // held by every call that uses the device or the level table, and by the
+    // serving worker around each batch
+    std::recursive_mutex mu;
+    Server *server = nullptr;
     int device = 0;
     cudaStream_t stream = nullptr;
     mlq_options opt{};
@@ -761,6 +778,10 @@ int finish_estimate(mlq_ctx *ctx, int L, const int64_t *N, double *mean_out, dou
     return MLQ_OK;
 }
 
+namespace {
+void serve_stop(mlq_ctx *ctx);  // stops and frees the serving worker (below)
+}
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
@@ -860,6 +881,7 @@ int mlq_create(mlq_ctx **out, int device, void *cuda_stream, const mlq_options *
 int mlq_destroy(mlq_ctx *ctx)
 {
     if (!ctx) return MLQ_EINVAL;
+    serve_stop(ctx);
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     for (int k = 0; k < kStreams; ++k) {
@@ -893,6 +915,7 @@ int mlq_destroy(mlq_ctx *ctx)
 
 int mlq_set_options(mlq_ctx *ctx, const mlq_options *opt)
 {
+    MLQ_GUARD(ctx);
     if (!ctx || !opt || validate_options(opt) != MLQ_OK) return MLQ_EINVAL;
     ctx->generation++;
     if (opt->cluster > ctx->max_cluster) return MLQ_EUNSUPPORTED;
@@ -902,6 +925,7 @@ int mlq_set_options(mlq_ctx *ctx, const mlq_options *opt)
 
 int mlq_set_model(mlq_ctx *ctx, const mlq_model *m)
 {
+    MLQ_GUARD(ctx);
     if (!ctx || !m) return MLQ_EINVAL;
     ctx->generation++;
     if (!(m->s_l > 0.0) || !(m->s_t > 0.0) || !(m->T > 0.0)) return MLQ_EINVAL;
@@ -912,6 +936,7 @@ int mlq_set_model(mlq_ctx *ctx, const mlq_model *m)
 int mlq_add_level(mlq_ctx *ctx, int level, int dim, const int32_t *dims, const double *lengths, double dt,
                   int32_t nsteps)
 {
+    MLQ_GUARD(ctx);
     if (!ctx || !dims || level < 0 || level >= kMaxLevels) return MLQ_EINVAL;
     if (dim != 2 && dim != 3) return MLQ_EINVAL;
     if (!(dt > 0.0) || nsteps < 0) return MLQ_EINVAL;
@@ -976,6 +1001,7 @@ int mlq_add_level(mlq_ctx *ctx, int level, int dim, const int32_t *dims, const d
 
 int mlq_set_initial_state(mlq_ctx *ctx, int level, const double *v0, const double *w0)
 {
+    MLQ_GUARD(ctx);
     if (!ctx || !v0 || level < 0 || level >= kMaxLevels || !ctx->levels[level].defined) return MLQ_EINVAL;
     ctx->generation++;
     Level &L = ctx->levels[level];
@@ -994,6 +1020,7 @@ int mlq_set_initial_state(mlq_ctx *ctx, int level, const double *v0, const doubl
 
 int mlq_set_initial_disk(mlq_ctx *ctx, int level, double radius)
 {
+    MLQ_GUARD(ctx);
     if (!ctx || level < 0 || level >= kMaxLevels || !ctx->levels[level].defined || !(radius >= 0.0))
         return MLQ_EINVAL;
     ctx->generation++;
@@ -1007,6 +1034,7 @@ int mlq_set_initial_disk(mlq_ctx *ctx, int level, double radius)
 
 int mlq_set_kl(mlq_ctx *ctx, int level, int K, const double *phi, const double *theta_mean)
 {
+    MLQ_GUARD(ctx);
     if (!ctx || !phi || K < 1 || K > kMaxK || level < 0 || level >= kMaxLevels || !ctx->levels[level].defined)
         return MLQ_EINVAL;
     ctx->generation++;
@@ -1053,6 +1081,7 @@ int mlq_set_kl(mlq_ctx *ctx, int level, int K, const double *phi, const double *
 
 int mlq_synthesize(mlq_ctx *ctx, int level, int64_t S, const double *xi, double *cs2_out)
 {
+    MLQ_GUARD(ctx);
     if (!ctx || !xi || !cs2_out || S < 1 || S > 65535) return MLQ_EINVAL;
     if (check_level(ctx, level) != MLQ_OK) return MLQ_EINVAL;
     MLQ_CUDA(ctx, cudaSetDevice(ctx->device));
@@ -1075,6 +1104,7 @@ int mlq_synthesize(mlq_ctx *ctx, int level, int64_t S, const double *xi, double 
 
 int mlq_workspace_bytes(mlq_ctx *ctx, int level, int64_t S, int with_coarse, size_t *bytes)
 {
+    MLQ_GUARD(ctx);
     if (!ctx || !bytes || S < 0) return MLQ_EINVAL;
     if (check_level(ctx, level) != MLQ_OK) return MLQ_EINVAL;
     size_t t = member_bytes(ctx, ctx->levels[level], S);
@@ -1091,6 +1121,7 @@ int mlq_workspace_bytes(mlq_ctx *ctx, int level, int64_t S, int with_coarse, siz
 int mlq_solve(mlq_ctx *ctx, int level, int64_t S, const double *xi, int with_coarse, double *q_fine,
               double *q_coarse, double *y, int32_t *status, int32_t *iters)
 {
+    MLQ_GUARD(ctx);
     if (!ctx || !xi || S < 0 || S > 65535) return MLQ_EINVAL;
     if (check_level(ctx, level) != MLQ_OK) return MLQ_EINVAL;
     if (with_coarse) {
@@ -1161,6 +1192,7 @@ int mlq_solve(mlq_ctx *ctx, int level, int64_t S, const double *xi, int with_coa
 int mlq_estimate(mlq_ctx *ctx, int L, const int64_t *N, const double *const *xi, double *mean_out,
                  double *var_out, double *rmse_out, double *const *y_out)
 {
+    MLQ_GUARD(ctx);
     if (!ctx || !N || !xi || !mean_out || L < 0 || L >= kMaxLevels) return MLQ_EINVAL;
     if (2 * (L + 1) > kStreams) return MLQ_EUNSUPPORTED;
     for (int l = 0; l <= L; ++l) {
@@ -1310,6 +1342,7 @@ int mlq_estimate(mlq_ctx *ctx, int L, const int64_t *N, const double *const *xi,
 
 int mlq_set_profiling(mlq_ctx *ctx, int enable)
 {
+    MLQ_GUARD(ctx);
     if (!ctx) return MLQ_EINVAL;
     ctx->profile = enable != 0;
     return MLQ_OK;
@@ -1317,6 +1350,7 @@ int mlq_set_profiling(mlq_ctx *ctx, int enable)
 
 int mlq_member_profile(mlq_ctx *ctx, int max_members, int *count, mlq_member_stats *out)
 {
+    MLQ_GUARD(ctx);
     if (!ctx || !count || (max_members > 0 && !out)) return MLQ_EINVAL;
     if (!ctx->profile) return MLQ_EINVAL;
     MLQ_CUDA(ctx, cudaSetDevice(ctx->device));
@@ -1355,6 +1389,7 @@ int mlq_member_profile(mlq_ctx *ctx, int max_members, int *count, mlq_member_sta
 int mlq_autotune(mlq_ctx *ctx, int level, int64_t S, const double *xi, int probe_steps, int *cluster_out,
                  int *threads_out, double *ms_out)
 {
+    MLQ_GUARD(ctx);
     if (!ctx || !xi || S < 1 || probe_steps < 1) return MLQ_EINVAL;
     if (check_level(ctx, level) != MLQ_OK) return MLQ_EINVAL;
     if (ctx->opt.precision != MLQ_MIXED || ctx->opt.storage == 2) return MLQ_EUNSUPPORTED;
@@ -1589,6 +1624,7 @@ int mlq_launch_count(mlq_ctx *ctx, int64_t *count)
 
 int mlq_level_launch(mlq_ctx *ctx, int level, int *cluster, int *threads, int *resident)
 {
+    MLQ_GUARD(ctx);
     if (!ctx || !cluster || !threads || level < 0 || level >= kMaxLevels || !ctx->levels[level].defined)
         return MLQ_EINVAL;
     const Shape sh = choose_launch(ctx, ctx->levels[level]);
@@ -1616,6 +1652,215 @@ const char *mlq_strerror(int s)
 const char *mlq_last_cuda_error(mlq_ctx *ctx)
 {
     return ctx ? ctx->cuda_error.c_str() : "";
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Serving (mlq_submit / mlq_poll): continuous batching of per-level Monte
+// Carlo requests on a worker thread of the context.
+// ===========================================================================
+struct ServeReq {
+    uint64_t id = 0;
+    int level = 0;
+    int64_t samples = 0;
+    double target = 0.0;
+    int64_t chunk = 16;
+    int K = 0;
+    std::vector<double> xi;  // samples x K
+    int64_t next = 0;        // first sample not yet solved
+    std::vector<double> q;
+    std::vector<int32_t> st;
+    int64_t checked = 0;     // chunk boundaries below this were tested
+    bool finished = false;
+    mlq_result res{};
+    std::chrono::steady_clock::time_point t0;
+};
+
+struct Server {
+    std::mutex mu;
+    std::condition_variable cv;
+    std::map<uint64_t, std::unique_ptr<ServeReq>> reqs;
+    std::deque<uint64_t> order;  // arrival order of unfinished requests
+    uint64_t next_id = 1;
+    bool stop = false;
+    std::thread worker;
+};
+
+namespace {
+
+constexpr int64_t kServeMaxDofs = int64_t(1) << 24;  // DOFs per batched solve
+constexpr int64_t kServeMaxSamples = int64_t(1) << 20;
+
+// mean and sqrt(V_n / n) of the first n values, in index order
+void serve_stats(const ServeReq &r, int64_t n, double *mean, double *rmse)
+{
+    double m = 0.0;
+    for (int64_t i = 0; i < n; ++i) m += r.q[i];
+    m /= (double)n;
+    double v = 0.0;
+    for (int64_t i = 0; i < n; ++i) v += (r.q[i] - m) * (r.q[i] - m);
+    v = n > 1 ? v / (double)(n - 1) : 0.0;
+    *mean = m;
+    *rmse = n > 1 ? std::sqrt(v / (double)n) : INFINITY;
+}
+
+void serve_finish(ServeReq &r, int64_t n, int status)
+{
+    r.finished = true;
+    r.res.status = status;
+    r.res.samples_used = n;
+    int32_t worst = 0;
+    for (int64_t i = 0; i < n; ++i) worst = std::max(worst, r.st[i]);
+    r.res.worst = worst;
+    if (n > 0) serve_stats(r, n, &r.res.mean, &r.res.rmse);
+    r.res.latency_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - r.t0).count();
+}
+
+// after new results: test the chunk boundaries in order
+void serve_check(ServeReq &r)
+{
+    while (!r.finished) {
+        const int64_t b = std::min(r.checked + r.chunk, r.samples);
+        if (b > r.next) return;
+        r.checked = b;
+        double mean, rmse;
+        serve_stats(r, b, &mean, &rmse);
+        if ((r.target > 0.0 && b >= 2 && rmse <= r.target) || b == r.samples) serve_finish(r, b, MLQ_OK);
+    }
+}
+
+void serve_loop(mlq_ctx *ctx)
+{
+    Server &sv = *ctx->server;
+    std::vector<double> xi, q;
+    std::vector<int32_t> st, it;
+    for (;;) {
+        struct Part { ServeReq *r; int64_t first, count; };
+        std::vector<Part> parts;
+        int level = -1, K = 0;
+        {
+            std::unique_lock<std::mutex> lk(sv.mu);
+            sv.cv.wait(lk, [&] { return sv.stop || !sv.order.empty(); });
+            if (sv.stop) return;
+            // the oldest request sets the level; every waiting request at that
+            // level adds its next chunk (adaptive) or all its samples
+            ServeReq &head = *sv.reqs.at(sv.order.front());
+            level = head.level;
+            K = head.K;
+            const int64_t n = ctx->levels[level].n;
+            const int64_t cap = std::max<int64_t>(1, std::min<int64_t>(65535, kServeMaxDofs / std::max<int64_t>(n, 1)));
+            int64_t total = 0;
+            for (uint64_t id : sv.order) {
+                ServeReq &r = *sv.reqs.at(id);
+                if (r.level != level || r.K != K) continue;
+                int64_t take = r.target > 0.0 ? std::min(r.chunk, r.samples - r.next) : r.samples - r.next;
+                take = std::min(take, cap - total);
+                if (take <= 0) break;
+                parts.push_back({&r, r.next, take});
+                total += take;
+            }
+            xi.resize((size_t)total * K);
+            int64_t off = 0;
+            for (const Part &p : parts) {
+                std::memcpy(xi.data() + off * K, p.r->xi.data() + p.first * K, sizeof(double) * p.count * K);
+                off += p.count;
+            }
+        }
+        const int64_t S = (int64_t)xi.size() / std::max(K, 1);
+        q.assign(S, 0.0);
+        st.assign(S, 0);
+        it.assign(S, 0);
+        int code;
+        {
+            std::lock_guard<std::recursive_mutex> g(ctx->mu);
+            code = mlq_solve(ctx, level, S, xi.data(), 0, q.data(), nullptr, nullptr, st.data(), it.data());
+        }
+        std::lock_guard<std::mutex> lk(sv.mu);
+        int64_t off = 0;
+        for (const Part &p : parts) {
+            ServeReq &r = *p.r;
+            r.res.batches++;
+            if (code != MLQ_OK) {
+                serve_finish(r, 0, code);
+            } else {
+                std::copy(q.begin() + off, q.begin() + off + p.count, r.q.begin() + p.first);
+                std::copy(st.begin() + off, st.begin() + off + p.count, r.st.begin() + p.first);
+                r.next = p.first + p.count;
+                serve_check(r);
+            }
+            off += p.count;
+        }
+        for (auto i = sv.order.begin(); i != sv.order.end();)
+            i = sv.reqs.at(*i)->finished ? sv.order.erase(i) : i + 1;
+        sv.cv.notify_all();
+    }
+}
+
+void serve_stop(mlq_ctx *ctx)
+{
+    if (!ctx->server) return;
+    {
+        std::lock_guard<std::mutex> lk(ctx->server->mu);
+        ctx->server->stop = true;
+    }
+    ctx->server->cv.notify_all();
+    if (ctx->server->worker.joinable()) ctx->server->worker.join();
+    delete ctx->server;
+    ctx->server = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mlq_submit(mlq_ctx *ctx, const mlq_request *req, uint64_t *ticket)
+{
+    if (!ctx || !req || !ticket || !req->xi) return MLQ_EINVAL;
+    const int64_t chunk = req->chunk > 0 ? req->chunk : 16;
+    if ((chunk & (chunk - 1)) != 0 || req->samples < 1 || req->samples > kServeMaxSamples) return MLQ_EINVAL;
+    auto r = std::make_unique<ServeReq>();
+    {
+        MLQ_GUARD(ctx);
+        if (check_level(ctx, req->level) != MLQ_OK || ctx->levels[req->level].K < 1) return MLQ_EINVAL;
+        r->K = ctx->levels[req->level].K;
+        if (!ctx->server) {
+            ctx->server = new Server();
+            ctx->server->worker = std::thread(serve_loop, ctx);
+        }
+    }
+    r->level = req->level;
+    r->samples = req->samples;
+    r->target = req->target_rmse;
+    r->chunk = chunk;
+    r->xi.assign(req->xi, req->xi + (size_t)req->samples * r->K);
+    r->q.assign(req->samples, 0.0);
+    r->st.assign(req->samples, 0);
+    r->t0 = std::chrono::steady_clock::now();
+    Server &sv = *ctx->server;
+    {
+        std::lock_guard<std::mutex> lk(sv.mu);
+        r->id = sv.next_id++;
+        *ticket = r->id;
+        sv.order.push_back(r->id);
+        sv.reqs[r->id] = std::move(r);
+    }
+    sv.cv.notify_all();
+    return MLQ_OK;
+}
+
+int mlq_poll(mlq_ctx *ctx, uint64_t ticket, mlq_result *out)
+{
+    if (!ctx || !out || !ctx->server) return MLQ_EINVAL;
+    Server &sv = *ctx->server;
+    std::lock_guard<std::mutex> lk(sv.mu);
+    auto i = sv.reqs.find(ticket);
+    if (i == sv.reqs.end()) return MLQ_EINVAL;
+    if (!i->second->finished) return MLQ_ENOTREADY;
+    *out = i->second->res;
+    sv.reqs.erase(i);
+    return MLQ_OK;
 }
 
 }  // extern "C"

@@ -37,6 +37,17 @@ class Model(ctypes.Structure):
                 ("eps", ctypes.c_double), ("gamma", ctypes.c_double), ("T", ctypes.c_double)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int), ("samples", ctypes.c_int64), ("xi", ctypes.c_void_p),
+                ("target_rmse", ctypes.c_double), ("chunk", ctypes.c_int32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("worst", ctypes.c_int32), ("samples_used", ctypes.c_int64),
+                ("mean", ctypes.c_double), ("rmse", ctypes.c_double), ("latency_ms", ctypes.c_double),
+                ("batches", ctypes.c_int64)]
+
+
 class MemberStats(ctypes.Structure):
     _fields_ = [("kernel_ms", ctypes.c_double), ("level", ctypes.c_int), ("coarse", ctypes.c_int),
                 ("cluster", ctypes.c_int), ("resident", ctypes.c_int), ("threads", ctypes.c_int),
@@ -61,6 +72,8 @@ _lib.mlq_build_kl.argtypes = [ctypes.c_int, _vp, _vp, ctypes.c_double, ctypes.c_
 _lib.mlq_centroid_table.argtypes = [ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp]
 _lib.mlq_solve.argtypes = [_vp, ctypes.c_int, _i64, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
 _lib.mlq_estimate.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.mlq_submit.argtypes = [_vp, _vp, _vp]
+_lib.mlq_poll.argtypes = [_vp, ctypes.c_uint64, _vp]
 _lib.mlq_workspace_bytes.argtypes = [_vp, ctypes.c_int, _i64, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
 _lib.mlq_launch_count.argtypes = [_vp, ctypes.POINTER(_i64)]
 _lib.mlq_level_launch.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -81,7 +94,7 @@ EXPORTED = ["mlq_default_options", "mlq_default_model", "mlq_create", "mlq_destr
             "mlq_set_model", "mlq_add_level", "mlq_set_initial_state", "mlq_set_initial_disk", "mlq_set_kl",
             "mlq_build_kl", "mlq_centroid_table", "mlq_solve", "mlq_estimate", "mlq_workspace_bytes",
             "mlq_launch_count", "mlq_level_launch", "mlq_strerror", "mlq_last_cuda_error", "mlq_set_profiling",
-            "mlq_member_profile", "mlq_autotune", "mlq_solve_noalloc", "mlq_synthesize"]
+            "mlq_member_profile", "mlq_autotune", "mlq_solve_noalloc", "mlq_synthesize", "mlq_submit", "mlq_poll"]
 
 
 class MLQError(RuntimeError):
@@ -321,6 +334,39 @@ class Context:
         cnt = ctypes.c_int()
         _check(_lib.mlq_member_profile(self._h, 16, ctypes.byref(cnt), buf), "mlq_member_profile", self._h)
         return [{f: getattr(buf[k], f) for f, _ in MemberStats._fields_} for k in range(min(cnt.value, 16))]
+
+    def submit(self, level: int, xi, target_rmse: float = 0.0, chunk: int = 16) -> int:
+        """Queue a request for the mean of Q_level over the rows of xi (host,
+        samples x K), stopping at the first chunk boundary where the
+        statistical error sqrt(V_n / n) <= target_rmse.  Returns a ticket."""
+        x, px = _host(xi, np.float64)
+        req = Request(level, int(x.shape[0]), px, float(target_rmse), int(chunk))
+        t = ctypes.c_uint64()
+        _check(_lib.mlq_submit(self._h, ctypes.byref(req), ctypes.byref(t)), "mlq_submit", self._h)
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while the request runs, else a dict of its result (the ticket
+        is released)."""
+        res = Result()
+        code = _lib.mlq_poll(self._h, ctypes.c_uint64(ticket), ctypes.byref(res))
+        if code == -4:
+            return None
+        _check(code, "mlq_poll", self._h)
+        return {f: getattr(res, f) for f, _ in Result._fields_}
+
+    def wait(self, ticket: int, timeout: float = 600.0, interval: float = 0.002):
+        """Poll until the request is done (or raise TimeoutError)."""
+        import time
+
+        end = time.monotonic() + timeout
+        while True:
+            r = self.poll(ticket)
+            if r is not None:
+                return r
+            if time.monotonic() > end:
+                raise TimeoutError(f"request {ticket} not done after {timeout} s")
+            time.sleep(interval)
 
     def launch_count(self) -> int:
         c = _i64()
