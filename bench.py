@@ -162,14 +162,22 @@ def load_peaks():
         return {}
 
 
-def kernel_source_hash() -> str:
+# device sources each slab kernel is compiled from (its translation unit and
+# the headers holding its code)
+KERNEL_SOURCES = {"slab_solve_mg_kernel": ("mlq_mg.cuh", "mlq_kernels.cuh", "mlq_reg_inst.cu"),
+                  "slab_solve_reg_kernel": ("mlq_kernels.cuh", "mlq_reg_inst.cu"),
+                  "slab_solve_kernel": ("mlq_kernels.cuh", "mlq_slab_inst.cu")}
+
+
+def kernel_source_hash(kernel_key: str) -> str:
     import hashlib
 
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2105_02007_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cuh", ".cu")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    base = kernel_key.split("<")[0]
+    files = KERNEL_SOURCES.get(base) or sorted(f for f in os.listdir(csrc) if f.endswith((".cuh", ".cu")))
+    for f in files:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -187,7 +195,7 @@ def load_traffic(kernel_key: str, samples: int, steps: int):
     except Exception:
         return None
     e = d.get(kernel_key)
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != kernel_source_hash(kernel_key):
         return None
     caps = sorted(e["captures"], key=lambda c: c["steps"])
     if len(caps) >= 2:
