@@ -499,14 +499,24 @@ def main():
     e2e_vals = []
     h2d = sum(x.numel() * 8 for x in xi_pin)
     d2h = sum(LEVEL_N) * 8 + 16 * len(LEVEL_N)
+    e2e_y = None
     for _ in range(args.e2e_steps):
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx.estimate(xi_pin, return_y=True)
+        e2e_y = ctx.estimate(xi_pin, return_y=True)[3]
         torch.cuda.synchronize()
         e2e_vals.append(time.perf_counter() - t0)
     e2e_s = max(e2e_vals) if e2e_vals else None
+    combined = None
+    if dist is not None:
+        from paper_2105_02007_gb300 import distributed as D
+
+        if e2e_s is not None:
+            e2e_s = D.max_over_ranks(e2e_s)
+        # the one exchange: every rank's Y_l to rank 0, merged in rank order
+        ys = e2e_y if e2e_y is not None else ctx.estimate(xi_pin, return_y=True)[3]
+        combined = D.combine_estimates(ys)
 
     # ---- roofline of the dominant kernel: the member launch that moves the
     #      most algorithmic bytes (members run concurrently, so each launch's
@@ -593,6 +603,8 @@ def main():
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clk, "roofline": roof,
             "cpu_baseline": cpu, "fp64": fp64,
+            "estimate_all_ranks": None if combined is None else {"estimate": combined[0], "rmse": combined[2],
+                                                                  "ranks": world},
             "members": [{k: d[k] for k in ("level", "coarse", "cluster", "threads", "npt", "resident", "samples",
                                             "kernel_ms", "start_ms", "end_ms", "cg_iterations")}
                         for d in members],
