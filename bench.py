@@ -268,7 +268,12 @@ ELL3 = 0.15 ** 2
 # FP64 inner: 176 B.  Per block: reaction / w update (32 B), b = M y and
 # r = b - A v (two FP64 15-point passes, stencil slots 64 B + vectors 28 B),
 # one refinement residual (~90 B), v update (20 B) -> ~300 B.
-BYTES3D_PER_DOF_ITER = {"mixed": 88.0, "fp64": 176.0}
+# Multigrid (FP32) adds per fine DOF: pre-smoothing (bb, 1/diag in, xa out)
+# 12 B, residual (8 slots, xa, bb in, rr out) 44 B, restriction 4 B,
+# interpolation (xa, coarse in, xb out) 12 B, post-smoothing (8 slots, xb, bb,
+# 1/diag in, result out) 48 B, plus an eighth of that per coarser level;
+# the CG part (update pass without 1/diag, matvec) stays: ~84 + 120 x 8/7 = 221 B.
+BYTES3D_PER_DOF_ITER = {"mixed": 88.0, "fp64": 176.0, "mg": 221.0}
 BYTES3D_PER_DOF_STEP = 300.0
 
 
@@ -293,10 +298,11 @@ def run_case3d(spec: str):
     from paper_2105_02007_gb300 import mlq
 
     prec = mlq.MLQ_MIXED if prec_name == "mixed" else mlq.MLQ_FP64
+    precond = int(kv.get("precond", 1 if prec_name == "mixed" else 0))
     dims = LEVEL3_DIMS[level]
     modes, _ = mlq.build_kl(dims, SIGMA2, ELL3, K)
     phi = mlq.centroid_table(dims, modes, dims)
-    with mlq.Context(0, prec) as ctx:
+    with mlq.Context(0, prec, precond=precond) as ctx:
         ctx.add_level(level, dims, level3_dt(level), steps)
         ctx.set_kl(level, phi)
         ctx.set_profiling(True)
@@ -307,7 +313,8 @@ def run_case3d(spec: str):
     n = dims[0] * dims[1] * dims[2]
     it = prof["cg_iterations"]
     sec = prof["kernel_ms"] / 1e3
-    algo = n * (it * BYTES3D_PER_DOF_ITER[prec_name] + S * steps * BYTES3D_PER_DOF_STEP)
+    per_it = BYTES3D_PER_DOF_ITER["mg" if (prec_name == "mixed" and precond == 1) else prec_name]
+    algo = n * (it * per_it + S * steps * BYTES3D_PER_DOF_STEP)
     peaks = None
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))

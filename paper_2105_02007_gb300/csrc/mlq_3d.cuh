@@ -36,6 +36,8 @@
 
 namespace mlq {
 
+constexpr int kMgCoarsestSweeps3D = 6;  // damped Jacobi sweeps on the coarsest 3D level
+
 // ---------------------------------------------------------------------------
 // Level set-up (sample independent): FP64 mass stencil [8][n] and lumped mass
 // m_P = (incident tetrahedra) |e| / 4.  Gathers over the (up to) 24
@@ -66,22 +68,16 @@ __global__ void level3d_setup_kernel(Grid3 g, double *__restrict__ M3, double *_
     lump[P] = cnt * vol / 4.0;
 }
 
-// ---------------------------------------------------------------------------
-// K2 (3D): per sample the stencil of A = M + dt K(theta): A64 [S][9][n] FP64
-// (slot 8 = 1 / diagonal) and, when Ai is not null, the same in FP32.
-// ---------------------------------------------------------------------------
-__global__ void stencil3d_setup_kernel(const double *__restrict__ cs2, Grid3 g, double dt, double s_l, double s_t,
-                                       int S, double *__restrict__ A64, float *__restrict__ A32)
+// Gather of the stencil of M + dt K(D) at node P over the (up to) 24
+// tetrahedra at P, in a fixed order; getD(e, d11, d12, d22) gives the
+// in-plane block of D on tetrahedron e (d33 = s_t).
+template <typename GetD>
+__device__ __forceinline__ void stencil3d_gather(const Grid3 &g, int64_t P, double dt, double s_t, GetD getD,
+                                                 double (&acc)[8])
 {
-    const int64_t P = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int smp = blockIdx.y;
-    if (P >= g.n || smp >= S) return;
     const int i = (int)(P % g.mx), j = (int)((P / g.mx) % g.my), k = (int)(P / ((int64_t)g.mx * g.my));
     const double vol = g.hx * g.hy * g.hz / 6.0;
-    const int64_t ne = 6LL * (g.mx - 1) * (g.my - 1) * (g.mz - 1);
-    const double *c2 = cs2 + (size_t)smp * ne * 2;
-    const double hds = 0.5 * (s_l - s_t);
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int sl = 0; sl < 8; ++sl) acc[sl] = 0.0;
     for (int d = 0; d < 8; ++d) {
         const int ci = i - (d & 1), cj = j - ((d >> 1) & 1), ck = k - ((d >> 2) & 1);
         if (ci < 0 || cj < 0 || ck < 0 || ci >= g.mx - 1 || cj >= g.my - 1 || ck >= g.mz - 1) continue;
@@ -91,9 +87,9 @@ __global__ void stencil3d_setup_kernel(const double *__restrict__ cs2, Grid3 g, 
             for (int t = 0; t < 4; ++t)
                 if (kuhn_vertex(s, t) == d) q = t;
             if (q < 0) continue;
-            const double c = c2[(6 * cell + s) * 2], sn = c2[(6 * cell + s) * 2 + 1];
-            // D = s_t I + (s_l - s_t) f f^T with f f^T = (1/2)[[1 + c, sn, 0], [sn, 1 - c, 0], [0, 0, 0]]
-            const double d11 = s_t + hds * (1.0 + c), d22 = s_t + hds * (1.0 - c), d12 = hds * sn, d33 = s_t;
+            double d11, d12, d22;
+            getD(6 * cell + s, d11, d12, d22);
+            const double d33 = s_t;
             double G[4][3];
             kuhn_grads(g, s, G);
             const double Dq[3] = {d11 * G[q][0] + d12 * G[q][1], d12 * G[q][0] + d22 * G[q][1], d33 * G[q][2]};
@@ -104,6 +100,30 @@ __global__ void stencil3d_setup_kernel(const double *__restrict__ cs2, Grid3 g, 
             }
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// K2 (3D): per sample the stencil of A = M + dt K(theta): A64 [S][9][n] FP64
+// (slot 8 = 1 / diagonal) and, when Ai is not null, the same in FP32.
+// D = s_t I + (s_l - s_t) f f^T with f f^T = (1/2)[[1 + c, sn, 0], [sn, 1 - c, 0], [0, 0, 0]]
+// from (c, sn) = (cos 2t, sin 2t) per tetrahedron.
+// ---------------------------------------------------------------------------
+__global__ void stencil3d_setup_kernel(const double *__restrict__ cs2, Grid3 g, double dt, double s_l, double s_t,
+                                       int S, double *__restrict__ A64, float *__restrict__ A32)
+{
+    const int64_t P = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int smp = blockIdx.y;
+    if (P >= g.n || smp >= S) return;
+    const int64_t ne = 6LL * (g.mx - 1) * (g.my - 1) * (g.mz - 1);
+    const double *c2 = cs2 + (size_t)smp * ne * 2;
+    const double hds = 0.5 * (s_l - s_t);
+    double acc[8];
+    stencil3d_gather(g, P, dt, s_t, [&](int64_t e, double &d11, double &d12, double &d22) {
+        const double c = c2[e * 2], sn = c2[e * 2 + 1];
+        d11 = s_t + hds * (1.0 + c);
+        d22 = s_t + hds * (1.0 - c);
+        d12 = hds * sn;
+    }, acc);
     double *a = A64 + (size_t)smp * kSlots3D * g.n;
     for (int sl = 0; sl < 8; ++sl) a[(int64_t)sl * g.n + P] = acc[sl];
     a[8LL * g.n + P] = 1.0 / acc[0];
@@ -112,6 +132,75 @@ __global__ void stencil3d_setup_kernel(const double *__restrict__ cs2, Grid3 g, 
         for (int sl = 0; sl < 8; ++sl) f[(int64_t)sl * g.n + P] = (float)acc[sl];
         f[8LL * g.n + P] = (float)(1.0 / acc[0]);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Multigrid set-up, per sample and coarse level c: the mean in-plane D over
+// the eight children of every coarse tetrahedron (the fine tetrahedra of its
+// 2 x 2 x 2 fine cells whose centroid lies in it: the centroid's coarse-local
+// coordinates follow the coarse tetrahedron's step order), read from
+// (cos 2t, sin 2t) on the fine mesh (c = 1) or from the previous level's means.
+// ---------------------------------------------------------------------------
+__global__ void coarsen3d_kernel(const double *__restrict__ cs2, const float *__restrict__ dfine, Grid3 gf,
+                                 Grid3 gc, int S, double s_l, double s_t, float *__restrict__ dc)
+{
+    const int64_t E = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int smp = blockIdx.y;
+    const int64_t nec = 6LL * (gc.mx - 1) * (gc.my - 1) * (gc.mz - 1);
+    const int64_t nef = 6LL * (gf.mx - 1) * (gf.my - 1) * (gf.mz - 1);
+    if (E >= nec || smp >= S) return;
+    const int64_t C = E / 6;
+    const int Sx = (int)(E % 6);
+    const int I = (int)(C % (gc.mx - 1)), J = (int)((C / (gc.mx - 1)) % (gc.my - 1)),
+              K = (int)(C / ((int64_t)(gc.mx - 1) * (gc.my - 1)));
+    const int a0 = kuhn_axis(Sx, 0), a1 = kuhn_axis(Sx, 1), a2 = kuhn_axis(Sx, 2);
+    const double hds = 0.5 * (s_l - s_t);
+    double d11 = 0.0, d12 = 0.0, d22 = 0.0;
+    for (int o = 0; o < 8; ++o) {
+        const int ox = o & 1, oy = (o >> 1) & 1, oz = (o >> 2) & 1;
+        const int64_t cf = (2 * I + ox) + (int64_t)(gf.mx - 1) * ((2 * J + oy) + (int64_t)(gf.my - 1) * (2 * K + oz));
+        for (int s = 0; s < 6; ++s) {
+            double cen[3] = {(double)ox, (double)oy, (double)oz};
+            for (int q = 0; q < 3; ++q) cen[kuhn_axis(s, q)] += (3.0 - q) / 4.0;
+            if (!(cen[a0] > cen[a1] && cen[a1] > cen[a2])) continue;
+            const int64_t e = 6 * cf + s;
+            if (cs2) {
+                const double c = cs2[((size_t)smp * nef + e) * 2], sn = cs2[((size_t)smp * nef + e) * 2 + 1];
+                d11 += s_t + hds * (1.0 + c);
+                d22 += s_t + hds * (1.0 - c);
+                d12 += hds * sn;
+            } else {
+                const float *q = dfine + ((size_t)smp * nef + e) * 3;
+                d11 += q[0];
+                d12 += q[1];
+                d22 += q[2];
+            }
+        }
+    }
+    float *out = dc + ((size_t)smp * nec + E) * 3;
+    out[0] = (float)(d11 / 8.0);
+    out[1] = (float)(d12 / 8.0);
+    out[2] = (float)(d22 / 8.0);
+}
+
+// coarse-level stencil (FP32, 9 slots with 1 / diagonal) from the mean D
+__global__ void stencil3d_from_d_kernel(const float *__restrict__ dbar, Grid3 g, double dt, double s_t, int S,
+                                        float *__restrict__ A32)
+{
+    const int64_t P = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int smp = blockIdx.y;
+    if (P >= g.n || smp >= S) return;
+    const int64_t ne = 6LL * (g.mx - 1) * (g.my - 1) * (g.mz - 1);
+    const float *d = dbar + (size_t)smp * ne * 3;
+    double acc[8];
+    stencil3d_gather(g, P, dt, s_t, [&](int64_t e, double &d11, double &d12, double &d22) {
+        d11 = d[e * 3];
+        d12 = d[e * 3 + 1];
+        d22 = d[e * 3 + 2];
+    }, acc);
+    float *f = A32 + (size_t)smp * kSlots3D * g.n;
+    for (int sl = 0; sl < 8; ++sl) f[(int64_t)sl * g.n + P] = (float)acc[sl];
+    f[8LL * g.n + P] = (float)(1.0 / acc[0]);
 }
 
 // (C x)_P for a symmetric 15-point stencil C [8][n]: slot d at P couples to
@@ -214,6 +303,122 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
     int32_t status = S_CONVERGED;
     const double dt = g.dt;
 
+    // ---- multigrid preconditioner u = MG(r) (FP32 inner path, nl > 1):
+    // V(1,1) with damped Jacobi, P^T restriction (the fine node 2I plus half
+    // of the fourteen edge midpoints 2I +- d), P1 interpolation (a fine node
+    // takes the mean of the coarse ends of the coarse edge it halves),
+    // Jacobi sweeps on the coarsest level.  Every level is split over the
+    // cluster by grid lines; values of other CTAs are read through L2 after a
+    // cluster barrier.  Input: R (level 0 right-hand side), result in U.
+    constexpr bool kMg = sizeof(TI) == 4;
+    const bool mgp = kMg && g.mg.nl > 1;
+    auto vcycle = [&]() {
+        if constexpr (kMg) {
+            const Mg3Args &M = g.mg;
+            const int NL = M.nl;
+            const float om = M.omega;
+            auto span = [&](int c, int64_t &o0, int64_t &o1) {
+                const int64_t ln = (int64_t)M.g[c].my * M.g[c].mz;
+                o0 = (ln * rank / CS) * M.g[c].mx;
+                o1 = (ln * (rank + 1) / CS) * M.g[c].mx;
+            };
+            auto Aof = [&](int c) -> const float * {
+                return c == 0 ? (const float *)Ai : M.A[c] + (size_t)sample * kSlots3D * M.g[c].n;
+            };
+            auto vec = [&](float *const *base, int c) { return base[c] + (size_t)sample * M.g[c].n; };
+            auto BB = [&](int c) -> float * { return c == 0 ? (float *)R : vec(M.bb, c); };
+            auto RR = [&](int c) -> float * { return c == 0 ? (float *)U : vec(M.rr, c); };
+            for (int c = 0; c < NL - 1; ++c) {
+                const Grid3 &Gc = M.g[c];
+                const float *A = Aof(c), *Dv = A + 8 * (size_t)Gc.n;
+                float *xa = vec(M.xa, c), *rr = RR(c), *bb = BB(c);
+                int64_t o0, o1;
+                span(c, o0, o1);
+                for (int64_t P = o0 + tid; P < o1; P += nt) xa[P] = om * Dv[P] * __ldcg(bb + P);
+                cl.sync();
+                {
+                    Walk3 wk;
+                    wk.init(o0 + tid, nt, Gc);
+                    for (int64_t P = o0 + tid; P < o1; P += nt, wk.next(Gc))
+                        rr[P] = __ldcg(bb + P) - apply15<float, float>(A, Gc, xa, P, wk.i, wk.j, wk.k);
+                }
+                cl.sync();
+                // restriction into level c+1
+                const Grid3 &Gq = M.g[c + 1];
+                float *bq = BB(c + 1);
+                int64_t q0, q1;
+                span(c + 1, q0, q1);
+                Walk3 wq;
+                wq.init(q0 + tid, nt, Gq);
+                for (int64_t Q = q0 + tid; Q < q1; Q += nt, wq.next(Gq)) {
+                    const int fi = 2 * wq.i, fj = 2 * wq.j, fk = 2 * wq.k;
+                    const int64_t f = fi + (int64_t)Gc.mx * (fj + (int64_t)Gc.my * fk);
+                    float h = 0.0f;
+#pragma unroll
+                    for (int sl = 1; sl < 8; ++sl) {
+                        const int dx = sl & 1, dy = (sl >> 1) & 1, dz = (sl >> 2) & 1;
+                        const int64_t off = dir_offset(Gc, sl);
+                        if (fi + dx < Gc.mx && fj + dy < Gc.my && fk + dz < Gc.mz) h += __ldcg(rr + f + off);
+                        if (fi >= dx && fj >= dy && fk >= dz) h += __ldcg(rr + f - off);
+                    }
+                    bq[Q] = __ldcg(rr + f) + 0.5f * h;
+                }
+                cl.sync();
+            }
+            // coarsest: damped Jacobi sweeps, ping-pong XA / XB
+            {
+                const int c = NL - 1;
+                const Grid3 &Gc = M.g[c];
+                const float *A = Aof(c), *Dv = A + 8 * (size_t)Gc.n;
+                float *X = vec(M.xa, c), *Y = vec(M.xb, c), *bb = BB(c);
+                int64_t o0, o1;
+                span(c, o0, o1);
+                for (int64_t P = o0 + tid; P < o1; P += nt) X[P] = om * Dv[P] * __ldcg(bb + P);
+                for (int k = 1; k < kMgCoarsestSweeps3D; ++k) {
+                    cl.sync();
+                    Walk3 wk;
+                    wk.init(o0 + tid, nt, Gc);
+                    for (int64_t P = o0 + tid; P < o1; P += nt, wk.next(Gc))
+                        Y[P] = __ldcg(X + P) +
+                               om * Dv[P] * (__ldcg(bb + P) - apply15<float, float>(A, Gc, X, P, wk.i, wk.j, wk.k));
+                    float *t = X;
+                    X = Y;
+                    Y = t;
+                }
+                cl.sync();
+            }
+            // ascend
+            for (int c = NL - 2; c >= 0; --c) {
+                const Grid3 &Gc = M.g[c], &Gq = M.g[c + 1];
+                const float *A = Aof(c), *Dv = A + 8 * (size_t)Gc.n;
+                const float *xq = (c + 1 == NL - 1) ? ((kMgCoarsestSweeps3D - 1) % 2 ? vec(M.xb, c + 1) : vec(M.xa, c + 1))
+                                                    : RR(c + 1);
+                float *xa = vec(M.xa, c), *xb = vec(M.xb, c), *rr = RR(c), *bb = BB(c);
+                int64_t o0, o1;
+                span(c, o0, o1);
+                {
+                    Walk3 wk;
+                    wk.init(o0 + tid, nt, Gc);
+                    for (int64_t P = o0 + tid; P < o1; P += nt, wk.next(Gc)) {
+                        const int ci = wk.i >> 1, cj = wk.j >> 1, ck = wk.k >> 1;
+                        const int64_t qa = ci + (int64_t)Gq.mx * (cj + (int64_t)Gq.my * ck);
+                        const int64_t qb = qa + (wk.i & 1) + (int64_t)Gq.mx * ((wk.j & 1) + (int64_t)Gq.my * (wk.k & 1));
+                        xb[P] = __ldcg(xa + P) + 0.5f * (__ldcg(xq + qa) + __ldcg(xq + qb));
+                    }
+                }
+                cl.sync();
+                {
+                    Walk3 wk;
+                    wk.init(o0 + tid, nt, Gc);
+                    for (int64_t P = o0 + tid; P < o1; P += nt, wk.next(Gc))
+                        rr[P] = __ldcg(xb + P) +
+                                om * Dv[P] * (__ldcg(bb + P) - apply15<float, float>(A, Gc, xb, P, wk.i, wk.j, wk.k));
+                }
+                cl.sync();
+            }
+        }
+    };
+
     for (int step = 0; step < g.nsteps; ++step) {
         const double *wcur = wb0 + wpar * SN;
         double *wnext = wb0 + (wpar ^ 1) * SN;
@@ -285,12 +490,13 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
             for (int64_t P = own0 + tid; P < own1; P += nt) {
                 const TI rr = R[P] * rscale;
                 R[P] = rr;
-                U[P] = Dinv[P] * rr;
+                if (!mgp) U[P] = Dinv[P] * rr;
                 X[P] = (TI)0;
                 Pv[P] = (TI)0;
                 Sv[P] = (TI)0;
             }
             cl.sync();
+            if (mgp) vcycle();
             double gamma_prev = 1.0, eta_prev = 1.0;
             int it = 0;
             auto decide = [&](double gamma, double delta, double rr) {
@@ -316,7 +522,7 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
             };
             double gacc = 0.0, racc = 0.0;   // (r, u) and (r, r) of the current iterate
             for (int64_t P = own0 + tid; P < own1; P += nt) {
-                const TI rr = R[P], uu = U[P];
+                const TI rr = R[P], uu = __ldcg(U + P);
                 gacc += (double)(rr * uu);
                 racc += (double)(rr * rr);
             }
@@ -330,7 +536,7 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                     for (int64_t P = own0 + tid; P < own1; P += nt, wk.next(G)) {
                         const TI ww = apply15<TI, TI>(Ai, G, U, P, wk.i, wk.j, wk.k);
                         W[P] = ww;
-                        pacc[1] += (double)(ww * U[P]);
+                        pacc[1] += (double)(ww * __ldcg(U + P));
                     }
                 }
                 cluster_reduce<3, CS>(pacc, wsl, csl, par, [&](double(&t)[3]) { decide(t[0], t[1], t[2]); });
@@ -347,7 +553,7 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                 racc = 0.0;
 #pragma unroll 4
                 for (int64_t P = own0 + tid; P < own1; P += nt) {
-                    const TI ww = W[P], uu = U[P];
+                    const TI ww = W[P], uu = __ldcg(U + P);
                     const TI ss = it == 0 ? ww : ww + tb * Sv[P];
                     const TI pp = it == 0 ? uu : uu + tb * Pv[P];
                     Sv[P] = ss;
@@ -355,13 +561,19 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                     X[P] += ta * pp;
                     const TI rr = R[P] - ta * ss;
                     R[P] = rr;
-                    const TI un = Dinv[P] * rr;
-                    U[P] = un;
-                    gacc += (double)(rr * un);
                     racc += (double)(rr * rr);
+                    if (!mgp) {
+                        const TI un = Dinv[P] * rr;
+                        U[P] = un;
+                        gacc += (double)(rr * un);
+                    }
                 }
                 ++it;
                 cl.sync();
+                if (mgp) {
+                    vcycle();
+                    for (int64_t P = own0 + tid; P < own1; P += nt) gacc += (double)(R[P] * __ldcg(U + P));
+                }
             }
             total_iters += it;
             if (nonfinite) break;

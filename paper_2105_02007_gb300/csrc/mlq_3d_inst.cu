@@ -43,4 +43,17 @@ cudaError_t launch_stencil3d_setup(const double *cs2, const Grid3 &g, double dt,
     return cudaGetLastError();
 }
 
+cudaError_t launch_mg3_setup(const double *cs2, const float *dfine, const Grid3 &gf, const Grid3 &gc, int S,
+                             double dt, double s_l, double s_t, float *dc, float *Ac, cudaStream_t st)
+{
+    const int64_t nec = 6LL * (gc.mx - 1) * (gc.my - 1) * (gc.mz - 1);
+    coarsen3d_kernel<<<dim3((unsigned)((nec + 255) / 256), (unsigned)S), 256, 0, st>>>(cs2, dfine, gf, gc, S, s_l,
+                                                                                      s_t, dc);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    stencil3d_from_d_kernel<<<dim3((unsigned)((gc.n + 255) / 256), (unsigned)S), 256, 0, st>>>(dc, gc, dt, s_t, S,
+                                                                                               Ac);
+    return cudaGetLastError();
+}
+
 }  // namespace mlq

@@ -58,6 +58,43 @@ __host__ __device__ inline void kuhn_grads(const Grid3 &g, int s, double (&G)[4]
     }
 }
 
+// Geometric multigrid on the nested Kuhn hierarchy (regular refinement of
+// the box: m_{c+1} = (m_c + 1) / 2 nodes per axis while every axis has an odd
+// count >= 3).  Level 0 is the fine mesh; per sample and coarse level the
+// stencil of A_c = M_c + dt K_c(Dbar_c) (Dbar_c the mean of D over the eight
+// children of a coarse tetrahedron, which makes A_c = P^T A_{c-1} P for P1)
+// and four work vectors.
+constexpr int kMg3MaxLevels = 8;
+
+struct Mg3Args {
+    int nl;                           // levels including the fine one (1: Jacobi)
+    float omega;                      // damped-Jacobi weight
+    Grid3 g[kMg3MaxLevels];
+    const float *A[kMg3MaxLevels];    // [S][9][n_c] (index 0 unused: the fine Ai)
+    float *xa[kMg3MaxLevels], *xb[kMg3MaxLevels], *rr[kMg3MaxLevels], *bb[kMg3MaxLevels];  // [S][n_c]
+};
+
+// the hierarchy below a fine grid; returns the number of levels
+__host__ __device__ inline int mg3_hierarchy(const Grid3 &g0, Grid3 *out, int max_levels)
+{
+    out[0] = g0;
+    int nl = 1;
+    while (nl < max_levels) {
+        const Grid3 &f = out[nl - 1];
+        if (f.mx < 3 || f.my < 3 || f.mz < 3 || (f.mx - 1) % 2 || (f.my - 1) % 2 || (f.mz - 1) % 2) break;
+        Grid3 c;
+        c.mx = (f.mx + 1) / 2;
+        c.my = (f.my + 1) / 2;
+        c.mz = (f.mz + 1) / 2;
+        c.n = c.mx * c.my * c.mz;
+        c.hx = 2.0 * f.hx;
+        c.hy = 2.0 * f.hy;
+        c.hz = 2.0 * f.hz;
+        out[nl++] = c;
+    }
+    return nl;
+}
+
 template <typename TI>
 struct Solve3Args {
     Grid3 g;
@@ -77,6 +114,7 @@ struct Solve3Args {
     int S;
     double *q;
     int32_t *iters, *status;
+    Mg3Args mg;                   // nl > 1: multigrid preconditioner (FP32 inner only)
 };
 
 }  // namespace mlq

@@ -68,7 +68,11 @@ struct Member {
     int32_t *iters = nullptr, *status = nullptr;
     float *mgA[mlq::kMgMaxLevels] = {};    // coarse-level stencils (multigrid)
     mlq::D3 *mgD[mlq::kMgMaxLevels] = {};  // coarse-level mean conductivities
+    float *mg3v[mlq::kMg3MaxLevels][4] = {};  // 3D multigrid work vectors xa, xb, rr, bb
 };
+
+// 3D multigrid in use for a level (FP32 inner path)
+bool uses_mg3(const mlq_ctx *ctx, const Level &L);
 
 // multigrid levels below the fine one: m_c = (m_{c-1} + 1) / 2 while m_c >= 3
 int mg_coarse_levels(int m)
@@ -243,6 +247,13 @@ Shape choose_launch_3d(const mlq_ctx *ctx, const Level &L, int64_t S = 0)
     return Shape{cs, threads, false, 0, 0};
 }
 
+bool uses_mg3(const mlq_ctx *ctx, const Level &L)
+{
+    if (L.dim != 3 || ctx->opt.precision != MLQ_MIXED || ctx->opt.precond != 1) return false;
+    mlq::Grid3 gl[mlq::kMg3MaxLevels];
+    return mlq::mg3_hierarchy(L.g3, gl, mlq::kMg3MaxLevels) > 1;
+}
+
 Shape choose_launch(mlq_ctx *ctx, const Level &L, int64_t S = 0)
 {
     if (L.dim == 3) return choose_launch_3d(ctx, L, S);
@@ -406,6 +417,19 @@ size_t member_bytes(const mlq_ctx *ctx, const Level &L, int64_t S)
         add((size_t)S * 8);
         add((size_t)S * 4);
         add((size_t)S * 4);
+        if (uses_mg3(ctx, L)) {
+            mlq::Grid3 gl[mlq::kMg3MaxLevels];
+            const int nl = mlq::mg3_hierarchy(L.g3, gl, mlq::kMg3MaxLevels);
+            add(sn * 4);                                // level-0 xa
+            add(sn * 4);                                // level-0 xb
+            for (int c = 1; c < nl; ++c) {
+                const size_t nc = (size_t)S * gl[c].n;
+                const size_t nec = (size_t)S * 6 * (gl[c].mx - 1) * (gl[c].my - 1) * (gl[c].mz - 1);
+                add(nec * 3 * 4);                       // mean D
+                add(nc * mlq::kSlots3D * 4);            // stencil
+                for (int k = 0; k < 4; ++k) add(nc * 4);
+            }
+        }
         return t;
     }
     add((size_t)S * L.ne * 2 * 8);          // cs2
@@ -461,6 +485,19 @@ void member_carve(const mlq_ctx *ctx, const Level &L, Member &mb, char *&cur)
         mb.q = (double *)take((size_t)mb.S * 8);
         mb.iters = (int32_t *)take((size_t)mb.S * 4);
         mb.status = (int32_t *)take((size_t)mb.S * 4);
+        if (uses_mg3(ctx, L)) {
+            mlq::Grid3 gl[mlq::kMg3MaxLevels];
+            const int nl = mlq::mg3_hierarchy(L.g3, gl, mlq::kMg3MaxLevels);
+            mb.mg3v[0][0] = (float *)take(sn * 4);
+            mb.mg3v[0][1] = (float *)take(sn * 4);
+            for (int c = 1; c < nl; ++c) {
+                const size_t nc = (size_t)mb.S * gl[c].n;
+                const size_t nec = (size_t)mb.S * 6 * (gl[c].mx - 1) * (gl[c].my - 1) * (gl[c].mz - 1);
+                mb.mgD[c] = (mlq::D3 *)take(nec * 3 * 4);
+                mb.mgA[c] = (float *)take(nc * mlq::kSlots3D * 4);
+                for (int k = 0; k < 4; ++k) mb.mg3v[c][k] = (float *)take(nc * 4);
+            }
+        }
         return;
     }
     mb.cs2 = (double *)take((size_t)mb.S * L.ne * 2 * 8);
@@ -499,6 +536,17 @@ int ensure_workspace(mlq_ctx *ctx, size_t bytes)
     }
     MLQ_CUDA(ctx, cudaMalloc(&ctx->ws, bytes));
     ctx->ws_bytes = bytes;
+    return MLQ_OK;
+}
+
+// the carve of a call stays inside the workspace it sized (a piece past the
+// end would be taken for host memory by the copy engine)
+int carve_check(mlq_ctx *ctx, const char *cur, size_t more)
+{
+    if ((size_t)(cur - (const char *)ctx->ws) + more > ctx->ws_bytes) {
+        ctx->cuda_error = "internal: workspace carve exceeds the sized workspace";
+        return MLQ_ENOMEM;
+    }
     return MLQ_OK;
 }
 
@@ -547,6 +595,16 @@ int launch_member3d_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream
         MLQ_CUDA(ctx, mlq::launch_stencil3d_setup(mb.cs2, L.g3, L.dt, ctx->model.s_l, ctx->model.s_t, (int)mb.S,
                                                   mb.A64, mixed ? (float *)mb.Ai : nullptr, st));
         ctx->launches++;
+        if (uses_mg3(ctx, L)) {
+            mlq::Grid3 gl[mlq::kMg3MaxLevels];
+            const int nl = mlq::mg3_hierarchy(L.g3, gl, mlq::kMg3MaxLevels);
+            for (int c = 1; c < nl; ++c) {
+                MLQ_CUDA(ctx, mlq::launch_mg3_setup(c == 1 ? mb.cs2 : nullptr, c == 1 ? nullptr : (const float *)mb.mgD[c - 1],
+                                                    gl[c - 1], gl[c], (int)mb.S, L.dt, ctx->model.s_l,
+                                                    ctx->model.s_t, (float *)mb.mgD[c], mb.mgA[c], st));
+                ctx->launches += 2;
+            }
+        }
     }
     if (!(phase & kSolve)) return MLQ_OK;
     mlq::Solve3Args<TI> a{};
@@ -584,6 +642,20 @@ int launch_member3d_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream
     a.q = mb.q;
     a.iters = mb.iters;
     a.status = mb.status;
+    a.mg.nl = 1;
+    if (uses_mg3(ctx, L)) {
+        a.mg.nl = mlq::mg3_hierarchy(L.g3, a.mg.g, mlq::kMg3MaxLevels);
+        a.mg.omega = 0.7f;  // lambda_max(D^-1 A) <= 2.4 for P1 on Kuhn tetrahedra
+        a.mg.xa[0] = mb.mg3v[0][0];
+        a.mg.xb[0] = mb.mg3v[0][1];
+        for (int c = 1; c < a.mg.nl; ++c) {
+            a.mg.A[c] = mb.mgA[c];
+            a.mg.xa[c] = mb.mg3v[c][0];
+            a.mg.xb[c] = mb.mg3v[c][1];
+            a.mg.rr[c] = mb.mg3v[c][2];
+            a.mg.bb[c] = mb.mg3v[c][3];
+        }
+    }
     const Shape sh = choose_launch_3d(ctx, L, mb.S);
     const bool timed = ctx->profile && slot >= 0 && slot < kStreams;
     const unsigned evf = ctx->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
@@ -1154,6 +1226,7 @@ int mlq_solve(mlq_ctx *ctx, int level, int64_t S, const double *xi, int with_coa
     cur += align_up((size_t)S * 4, 256);
     // xi on the device
     const double *d_xi = xi;
+    if ((st = carve_check(ctx, cur, is_device_ptr(xi) ? 0 : (size_t)S * K * 8)) != MLQ_OK) return st;
     if (!is_device_ptr(xi)) {
         double *dx = (double *)cur;
         MLQ_CUDA(ctx, cudaMemcpyAsync(dx, xi, sizeof(double) * S * K, cudaMemcpyHostToDevice, ctx->stream));
@@ -1227,6 +1300,7 @@ int mlq_estimate(mlq_ctx *ctx, int L, const int64_t *N, const double *const *xi,
         ybuf[l] = (double *)cur;
         cur += align_up((size_t)N[l] * 8, 256);
         const double *d_xi = xi[l];
+        if ((st = carve_check(ctx, cur, is_device_ptr(xi[l]) ? 0 : (size_t)N[l] * K * 8)) != MLQ_OK) return st;
         if (!is_device_ptr(xi[l])) {
             double *dx = (double *)cur;
             cur += align_up((size_t)N[l] * K * 8, 256);

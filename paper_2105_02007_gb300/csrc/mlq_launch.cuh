@@ -34,6 +34,8 @@ cudaError_t launch_3d_f64(int cs, const Solve3Args<double> &a, int nclusters, in
 cudaError_t launch_level3d_setup(const Grid3 &g, double *M3, double *lump, cudaStream_t st);
 cudaError_t launch_stencil3d_setup(const double *cs2, const Grid3 &g, double dt, double s_l, double s_t, int S,
                                    double *A64, float *A32, cudaStream_t st);
+cudaError_t launch_mg3_setup(const double *cs2, const float *dfine, const Grid3 &gf, const Grid3 &gc, int S,
+                             double dt, double s_l, double s_t, float *dc, float *Ac, cudaStream_t st);
 
 cudaError_t launch_slab_f32(int cs, bool resident, const SolveArgs<float> &a, int nclusters, int threads,
                             size_t smem, cudaStream_t st);

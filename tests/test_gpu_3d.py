@@ -43,17 +43,19 @@ def setup3d(dims, K, seed, S, radius=0.29):
     return mesh, phi, xi, v0, w0
 
 
-# every cluster size the line count allows, ragged line bands, both precisions
+# every cluster size the line count allows, ragged line bands, FP64 and the
+# mixed path with the Jacobi and the multigrid inner preconditioner (meshes
+# with 1..4 multigrid levels; 13 x 11 x 6 cannot be coarsened)
 @pytest.mark.parametrize("dims,cluster", [((5, 5, 3), 1), ((9, 9, 5), 1), ((9, 9, 5), 4), ((9, 7, 5), 8),
-                                          ((17, 17, 5), 16), ((13, 11, 6), 2)])
-@pytest.mark.parametrize("prec", [0, 1])
-def test_3d_parity(mlq, dims, cluster, prec):
+                                          ((17, 17, 5), 16), ((13, 11, 6), 2), ((33, 33, 9), 4)])
+@pytest.mark.parametrize("prec,precond", [(0, 0), (1, 0), (1, 1)])
+def test_3d_parity(mlq, dims, cluster, prec, precond):
     mesh, phi, xi, v0, w0 = setup3d(dims, 6, 11, 5)
     nsteps, dt = 8, 0.05
     q_ref, _, st = O.solve_batch(mesh, phi, xi, dt, nsteps, v0=v0, w0=w0, nthreads=2)
     assert np.all(st == 0)
     try:
-        ctx = mlq.Context(0, prec, cluster=cluster)
+        ctx = mlq.Context(0, prec, cluster=cluster, precond=precond)
     except mlq.MLQError as e:
         if e.code == -6:
             pytest.skip("cluster size not available")
