@@ -19,7 +19,8 @@
 // Solver (one sample per cluster of CS CTAs, everything in global memory and
 // L2; the 3D levels outgrow the shared memory of a cluster):
 //   per time block  y = v + dt R(v, w); b = M y; w <- w + dt eps (v - gam w);
-//                   r = b - A v in FP64
+//                   r = b - A v in FP64 from the extrapolated guess
+//                   v = 2 v_n - v_{n-1}
 //   inner solve     Jacobi-preconditioned CG (Chronopoulos-Gear: one cluster
 //                   reduction per iteration) on A d = r / ||r|| from d = 0 in
 //                   the inner precision TI, v += ||r|| d; the mixed path
@@ -274,7 +275,8 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
     const double *A64 = g.A64 + (size_t)sample * kSlots3D * n;
     const TI *Ai = g.Ai + (size_t)sample * kSlots3D * n;
     const TI *__restrict__ Dinv = Ai + 8 * n;
-    double *v = g.v + so, *wb0 = g.w + so, *b = g.b + so, *yb = g.y + so;
+    // v: [2][S][n], the solution of the last block and the guess of the next
+    double *vb0 = g.v + so, *wb0 = g.w + so, *b = g.b + so, *yb = g.y + so;
     TI *__restrict__ R = g.r + so;
     TI *__restrict__ U = g.u + so;
     TI *__restrict__ W = g.wv + so;
@@ -293,7 +295,7 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
             v0 = (xx * xx + yy * yy + zz * zz <= g.radius2) ? 1.0 : 0.0;
             w0 = 0.0;
         }
-        v[P] = v0;
+        vb0[P] = v0;
         wb0[P] = w0;
     }
     cl.sync();
@@ -419,13 +421,20 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
         }
     };
 
+    int vpar = 0;
     for (int step = 0; step < g.nsteps; ++step) {
+        // the block starts from 2 v_n - v_{n-1} (v_n on the first block),
+        // kept in the other buffer
+        const double *vcur = vb0 + vpar * SN;
+        double *v = vb0 + (vpar ^ 1) * SN;
+        vpar ^= 1;
         const double *wcur = wb0 + wpar * SN;
         double *wnext = wb0 + (wpar ^ 1) * SN;
         for (int64_t P = own0 + tid; P < own1; P += nt) {
-            const double vv = v[P], ww = wcur[P];
+            const double vv = vcur[P], ww = wcur[P];
             yb[P] = vv + dt * (vv * (vv - g.a) * (1.0 - vv) - ww);
             wnext[P] = ww + dt * g.eps * (vv - g.gam * ww);
+            v[P] = step > 0 ? 2.0 * vv - v[P] : vv;
         }
         wpar ^= 1;
         cl.sync();
@@ -589,7 +598,8 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
     }
 
     double qacc[1] = {0.0};
-    for (int64_t P = own0 + tid; P < own1; P += nt) qacc[0] += g.lump[P] * v[P];
+    const double *vfin = vb0 + vpar * SN;   // solution of the last block
+    for (int64_t P = own0 + tid; P < own1; P += nt) qacc[0] += g.lump[P] * vfin[P];
     cluster_reduce<1, CS>(qacc, wsl, csl, par, [&](double(&t)[1]) { ctl.s0 = t[0]; });
     if (rank == 0 && tid == 0) {
         g.q[sample] = status == S_NONFINITE ? __longlong_as_double(0x7ff8000000000000LL) : ctl.s0;

@@ -107,7 +107,7 @@ struct Solve3Args {
     const double *M3, *lump;      // [8][n], [n] (level)
     const double *A64;            // [S][9][n]
     const TI *Ai;                 // [S][9][n] (the FP64 path: A64)
-    double *v, *w, *b, *y;        // [S][n], [2][S][n], [S][n], [S][n]
+    double *v, *w, *b, *y;        // [2][S][n], [2][S][n], [S][n], [S][n]
     TI *r, *u, *wv, *s, *p, *x;   // [S][n] each
     const double *v0, *w0;        // [n] or null
     double radius2;
