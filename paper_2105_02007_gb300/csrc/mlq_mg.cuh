@@ -47,9 +47,10 @@ struct D3 {
 //                first local level of a cluster is filled by a broadcast
 // Shared layout per level (bytes, the same in every CTA): four stencil
 // arrays D, E, N, NE (structure of arrays: conflict-free neighbour reads),
-// each 1 + (rows + 1) * m floats (pad, row R0-1, stored rows); tiles XA, XB,
-// RR of 1 + (rows + 2) * m + 1 floats (pad, halo row R0-1, stored rows, halo
-// row R1, pad); BB, rows * m floats (stored rows only).  rows is the largest
+// each 1 + (rows + 1) * m floats (pad, row R0-1, stored rows); tiles XA, RR
+// (and XB on the coarsest level) of 1 + (rows + 2) * m + 1 floats (pad, halo
+// row R0-1, stored rows, halo row R1, pad); BB, rows * m floats (stored rows
+// only).  rows is the largest
 // band over the ranks for a distributed level and m_c for a local one.
 // ---------------------------------------------------------------------------
 struct MgLevelPlan {
@@ -115,18 +116,6 @@ __host__ __device__ inline MgPlan mg_plan(int m0, int cs)
         L.local = local ? 1 : 0;
         L.csize = 1 + (rows + 1) * m;
         L.tile = 1 + (rows + 2) * m + 1;
-        const int cb = align16(L.csize * 4), tb = align16(L.tile * 4);
-        L.off_d = off;
-        L.off_e = off + cb;
-        L.off_n = off + 2 * cb;
-        L.off_ne = off + 3 * cb;
-        off += 4 * cb;
-        L.off_xa = off;
-        L.off_xb = off + tb;
-        L.off_r = off + 2 * tb;
-        off += 3 * tb;
-        L.off_b = off;
-        off += align16(rows * m * 4);
         pl.nl = c + 1;
         if (m < 5 || (m - 1) % 2) break;
         m = (m + 1) / 2;
@@ -135,6 +124,28 @@ __host__ __device__ inline MgPlan mg_plan(int m0, int cs)
     if (cs > 1 && (pl.nl < 2 || !pl.lv[pl.nl - 1].local)) {
         pl.nl = 0;
         return pl;
+    }
+    // offsets; only the coarsest level needs the second tile XB (its sweeps
+    // ping-pong), elsewhere XB = XA + P X_{c+1} is formed in place in XA
+    for (int c = 0; c < pl.nl; ++c) {
+        MgLevelPlan &L = pl.lv[c];
+        const int cb = align16(L.csize * 4), tb = align16(L.tile * 4);
+        L.off_d = off;
+        L.off_e = off + cb;
+        L.off_n = off + 2 * cb;
+        L.off_ne = off + 3 * cb;
+        off += 4 * cb;
+        L.off_xa = off;
+        L.off_r = off + tb;
+        off += 2 * tb;
+        if (c == pl.nl - 1) {
+            L.off_xb = off;
+            off += tb;
+        } else {
+            L.off_xb = L.off_xa;
+        }
+        L.off_b = off;
+        off += align16(L.rows_max * L.m * 4);
     }
     // the warp levels: local, below level 0, at most kMgWarpM nodes per side
     pl.warp_level = pl.nl;
