@@ -211,6 +211,25 @@ __device__ __forceinline__ T apply15(const T *__restrict__ C, const Grid3 &g, co
                                      int k)
 {
     const int64_t n = g.n;
+    if (i > 0 && j > 0 && k > 0 && i + 1 < g.mx && j + 1 < g.my && k + 1 < g.mz) {
+        // interior node: all fourteen neighbours exist; every load is issued
+        // before the first product so that they are in flight together
+        T c[15], xv[15];
+        c[0] = C[P];
+        xv[0] = (T)__ldcg(x + P);
+#pragma unroll
+        for (int sl = 1; sl < 8; ++sl) {
+            const int64_t off = dir_offset(g, sl);
+            c[2 * sl - 1] = C[sl * n + P];
+            c[2 * sl] = C[sl * n + P - off];
+            xv[2 * sl - 1] = (T)__ldcg(x + P + off);
+            xv[2 * sl] = (T)__ldcg(x + P - off);
+        }
+        T acc = c[0] * xv[0];
+#pragma unroll
+        for (int q = 1; q < 15; ++q) acc += c[q] * xv[q];
+        return acc;
+    }
     T acc = C[P] * (T)__ldcg(x + P);
 #pragma unroll
     for (int sl = 1; sl < 8; ++sl) {
