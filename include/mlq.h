@@ -13,7 +13,9 @@
  *   - Arrays documented as "host or device" may be either; the library asks
  *     the CUDA driver which one a pointer is.  Device pointers must be on the
  *     context's device; the caller keeps ownership.
- *   - A context is used from one host thread at a time.
+ *   - A context may be shared by host threads: the calls that use the device
+ *     or the level table take the context's lock (one at a time);
+ *     mlq_submit / mlq_poll only touch the serving queue.
  *   - Per-sample failures (iteration cap, NaN/Inf) come back in status[] and
  *     never abort the other samples of a batch.
  *
@@ -23,6 +25,13 @@
  *                                      and element 2c+1 = (i,j)(i+1,j+1)(i,j+1).
  *   Red refinement maps the m-node mesh to the (2m-1)-node mesh: the levels
  *   are nested (Sec. 3.1 of the paper: nested meshes with h_l ~ 2^-l).
+ *   3D, box [0,Lx] x [0,Ly] x [0,Lz] (default 1 x 1 x 0.25), mx x my x mz
+ *   nodes: node (i,j,k) = i + mx*(j + my*k) at (Lx i/(mx-1), ...); cube
+ *   c = i + (mx-1)*(j + (my-1)*k) holds the six Kuhn tetrahedra 6c + s,
+ *   s = 0..5, each the path from corner (i,j,k) to (i+1,j+1,k+1) stepping
+ *   along the axes in the order (x,y,z), (x,z,y), (y,x,z), (y,z,x), (z,x,y),
+ *   (z,y,x); the fibre direction is in-plane, f = (cos t, sin t, 0).  Regular
+ *   refinement (2m-1 nodes per axis) nests these meshes.
  */
 #ifndef MLQ_H
 #define MLQ_H
@@ -122,10 +131,16 @@ int mlq_destroy(mlq_ctx *ctx);
 int mlq_set_options(mlq_ctx *ctx, const mlq_options *opt);
 int mlq_set_model(mlq_ctx *ctx, const mlq_model *model);
 
-/* Declare level `level` (0..15) of the nested hierarchy {T_l} (Sec. 3.1):
- * a structured 2D mesh of m x m nodes on the unit square (dim = 2; dims[0] = m;
- * lengths ignored) with time step dt and nsteps time blocks (nsteps dt = T).
- * dim = 3 returns MLQ_EUNSUPPORTED in this build. */
+/* Declare level `level` (0..15) of the nested hierarchy {T_l} (Sec. 3.1)
+ * with time step dt and nsteps time blocks (nsteps dt = T):
+ *   dim = 2: the m x m node mesh of the unit square (dims[0] = m, lengths
+ *            ignored);
+ *   dim = 3: the mx x my x mz node Kuhn mesh of the box (dims = {mx, my, mz},
+ *            each >= 2, at most 2^28 nodes; lengths = {Lx, Ly, Lz} or NULL
+ *            for 1 x 1 x 0.25).  The mixed path solves 3D levels with the
+ *            vectors in device memory (one cluster per sample) and a
+ *            multigrid preconditioner when every axis has an odd node count
+ *            >= 3; mlq_autotune and mlq_solve_noalloc are 2D only. */
 int mlq_add_level(mlq_ctx *ctx, int level, int dim, const int32_t *dims, const double *lengths, double dt,
                   int32_t nsteps);
 
@@ -144,7 +159,8 @@ int mlq_set_initial_disk(mlq_ctx *ctx, int level, double radius);
 int mlq_set_kl(mlq_ctx *ctx, int level, int K, const double *phi, const double *theta_mean);
 
 /* Host helper: KL modes of the covariance c(x,y) = sigma2 exp(-|x-y|^2 / ell)
- * on the structured 2D mesh of m x m nodes (dims[0] = m), by K steps of
+ * on a structured mesh (dim 2: dims[0] = m, unit square; dim 3: dims =
+ * {mx, my, mz} with lengths as in mlq_add_level), by K steps of
  * pivoted Cholesky C ~ L L^T (eq. approxEig) and the reduced K x K
  * eigenproblem L^T M L v~ = lambda v~ with the P1 mass matrix M (eq. redEig).
  * modes_out: host, n x K row-major, v_k = L v~_k (so v_i^T M v_j =
@@ -154,9 +170,10 @@ int mlq_build_kl(int dim, const int32_t *dims, const double *lengths, double sig
                  double *modes_out, double *lambda_out);
 
 /* Host helper: midpoint-rule transfer (Sec. 4) of nodal modes on the fine
- * structured mesh (fine_dims[0] = mf) to a coarse nested mesh (coarse_dims[0]
- * = mc): phi_out[e*K + k] = fine P1 interpolant of mode k at the centroid of
- * coarse element e.  modes_f: host, mf^2 x K; phi_out: host, n_elem_c x K. */
+ * structured mesh (2D: fine_dims[0] = mf; 3D: fine_dims = {mx, my, mz}) to a
+ * coarse nested mesh of the same domain (coarse_dims likewise):
+ * phi_out[e*K + k] = fine P1 interpolant of mode k at the centroid of coarse
+ * element e.  modes_f: host, n_fine x K; phi_out: host, n_elem_c x K. */
 int mlq_centroid_table(int dim, const int32_t *fine_dims, const double *modes_f, int K,
                        const int32_t *coarse_dims, double *phi_out);
 

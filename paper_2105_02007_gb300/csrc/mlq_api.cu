@@ -1835,7 +1835,15 @@ void serve_loop(mlq_ctx *ctx)
                 parts.push_back({&r, r.next, take});
                 total += take;
             }
-            xi.resize((size_t)total * K);
+            try {
+                xi.resize((size_t)total * K);
+            } catch (const std::bad_alloc &) {
+                for (const Part &p : parts) serve_finish(*p.r, 0, MLQ_ENOMEM);
+                for (auto i = sv.order.begin(); i != sv.order.end();)
+                    i = sv.reqs.at(*i)->finished ? sv.order.erase(i) : i + 1;
+                sv.cv.notify_all();
+                continue;
+            }
             int64_t off = 0;
             for (const Part &p : parts) {
                 std::memcpy(xi.data() + off * K, p.r->xi.data() + p.first * K, sizeof(double) * p.count * K);
@@ -1843,11 +1851,15 @@ void serve_loop(mlq_ctx *ctx)
             }
         }
         const int64_t S = (int64_t)xi.size() / std::max(K, 1);
-        q.assign(S, 0.0);
-        st.assign(S, 0);
-        it.assign(S, 0);
-        int code;
-        {
+        int code = MLQ_OK;
+        try {
+            q.assign(S, 0.0);
+            st.assign(S, 0);
+            it.assign(S, 0);
+        } catch (const std::bad_alloc &) {
+            code = MLQ_ENOMEM;
+        }
+        if (code == MLQ_OK) {
             std::lock_guard<std::recursive_mutex> g(ctx->mu);
             code = mlq_solve(ctx, level, S, xi.data(), 0, q.data(), nullptr, nullptr, st.data(), it.data());
         }
@@ -1890,7 +1902,7 @@ void serve_stop(mlq_ctx *ctx)
 extern "C" {
 
 int mlq_submit(mlq_ctx *ctx, const mlq_request *req, uint64_t *ticket)
-{
+try {
     if (!ctx || !req || !ticket || !req->xi) return MLQ_EINVAL;
     const int64_t chunk = req->chunk > 0 ? req->chunk : 16;
     if ((chunk & (chunk - 1)) != 0 || req->samples < 1 || req->samples > kServeMaxSamples) return MLQ_EINVAL;
@@ -1922,6 +1934,10 @@ int mlq_submit(mlq_ctx *ctx, const mlq_request *req, uint64_t *ticket)
     }
     sv.cv.notify_all();
     return MLQ_OK;
+} catch (const std::bad_alloc &) {
+    return MLQ_ENOMEM;
+} catch (...) {  // thread creation
+    return MLQ_ECUDA;
 }
 
 int mlq_poll(mlq_ctx *ctx, uint64_t ticket, mlq_result *out)
