@@ -331,6 +331,59 @@ def run_case3d(spec: str):
     return 0
 
 
+def run_c3(spec: str):
+    """The 3D MLQMC estimator end to end: --c3 [T=0.5][,K=16][,L=3].
+    Kuhn levels LEVEL3_DIMS[0..L], dt_l = 0.05 * 2^-l over [0, T]; KL modes of
+    c = 0.09 exp(-|x-y|^2 / 0.15^2) on the finest mesh (K modes) transferred by
+    the midpoint rule; per level 4^(L-l) lattice points (CBC generating
+    vector, product weights lambda_k / lambda_1) x 16 random shifts, mapped to
+    Gaussians; mlq_estimate over all levels (mixed path, multigrid).  Prints
+    the DOF-steps/s of the timed estimate and the MLQMC estimate with its
+    shift-based RMSE."""
+    import time
+
+    kv = dict(item.split("=") for item in spec.split(",")) if spec else {}
+    T = float(kv.get("T", 0.5))
+    K = int(kv.get("K", 16))
+    L = int(kv.get("L", 3))
+    R = 16
+    from paper_2105_02007_gb300 import build, inputs
+
+    build.build()
+    from paper_2105_02007_gb300 import mlq
+
+    dims = LEVEL3_DIMS[: L + 1]
+    t0 = time.perf_counter()
+    modes, lam = mlq.build_kl(dims[-1], SIGMA2, ELL3, K)
+    phis = [mlq.centroid_table(dims[-1], modes, d) for d in dims]
+    setup_s = time.perf_counter() - t0
+    steps = [int(round(T / level3_dt(l))) for l in range(L + 1)]
+    npts = [4 ** (L - l) for l in range(L + 1)]
+    xis = [inputs.qmc_xi(0, l, npts[l], R, K, lam / lam[0]).reshape(-1, K) for l in range(L + 1)]
+    ctx = mlq.Context(0, mlq.MLQ_MIXED)
+    for l, d in enumerate(dims):
+        ctx.add_level(l, d, level3_dt(l), steps[l])
+        ctx.set_kl(l, phis[l])
+    import torch
+
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    mean, var, rmse_mc, ys = ctx.estimate(xis, return_y=True)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t1
+    ctx.close()
+    n = [d[0] * d[1] * d[2] for d in dims]
+    dof = sum(len(xis[l]) * (n[l] * steps[l] + (n[l - 1] * steps[l - 1] if l > 0 else 0)) for l in range(L + 1))
+    # MLQMC: per level the mean over the R shifts of the lattice means; the
+    # error estimate from the spread over the shifts
+    qmc_var = [float(np.var(np.asarray(y).reshape(R, -1).mean(axis=1), ddof=1) / R) for y in ys]
+    print(json.dumps({"c3": spec or "T=0.5", "levels": [list(d) for d in dims], "steps": steps,
+                      "solves": [len(x) for x in xis], "K": K, "seconds": sec, "dof_steps": dof,
+                      "dof_steps_per_s": dof / sec, "estimate": mean, "rmse_qmc": float(sum(qmc_var) ** 0.5),
+                      "host_kl_setup_s": setup_s}))
+    return 0
+
+
 def run_serve(spec: str):
     """Serving workload: --serve rate=R,requests=N[,levels=0-2][,chunk=16][,seed=0].
     A Poisson stream (exponential inter-arrival, seed) of requests; each picks
@@ -413,6 +466,8 @@ def main():
     ap.add_argument("--case", default=None, help="profile one member solve, e.g. level=4,samples=1,steps=4")
     ap.add_argument("--case3d", default=None, help="one 3D member solve, e.g. level=2,samples=8,steps=2")
     ap.add_argument("--serve", default=None, help="serving stream, e.g. rate=50,requests=200,levels=0-2")
+    ap.add_argument("--c3", default=None, nargs="?", const="",
+                    help="3D MLQMC estimate end to end, e.g. T=0.5,K=16,L=3")
     args = ap.parse_args()
     if args.case:
         return run_case(args.case)
@@ -420,6 +475,8 @@ def main():
         return run_case3d(args.case3d)
     if args.serve:
         return run_serve(args.serve)
+    if args.c3 is not None:
+        return run_c3(args.c3)
     if args.impl == "reference":
         return run_reference(args)
 
