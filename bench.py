@@ -332,9 +332,9 @@ def run_case3d(spec: str):
 
 
 def run_c3(spec: str):
-    """The 3D MLQMC estimator end to end: --c3 [T=0.5][,K=16][,L=3].
+    """The 3D MLQMC estimator end to end: --c3 [T=0.5][,K=64][,L=3].
     Kuhn levels LEVEL3_DIMS[0..L], dt_l = 0.05 * 2^-l over [0, T]; KL modes of
-    c = 0.09 exp(-|x-y|^2 / 0.15^2) on the finest mesh (K modes) transferred by
+    c = 0.09 exp(-|x-y|^2 / 0.15^2) on the finest mesh (K = 64 modes) transferred by
     the midpoint rule; per level 4^(L-l) lattice points (CBC generating
     vector, product weights lambda_k / lambda_1) x 16 random shifts, mapped to
     Gaussians; mlq_estimate over all levels (mixed path, multigrid).  Prints
@@ -344,7 +344,7 @@ def run_c3(spec: str):
 
     kv = dict(item.split("=") for item in spec.split(",")) if spec else {}
     T = float(kv.get("T", 0.5))
-    K = int(kv.get("K", 16))
+    K = int(kv.get("K", 64))
     L = int(kv.get("L", 3))
     R = 16
     from paper_2105_02007_gb300 import build, inputs

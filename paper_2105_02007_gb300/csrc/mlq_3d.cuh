@@ -28,8 +28,9 @@
 //                   refinement in FP64), the FP64 path runs one sweep to that
 //                   tolerance
 //   QoI             Q = sum_P m_P v_P with the lumped mass m = M 1.
-// CTA `rank` owns a contiguous range of grid lines (j, k); another CTA's
-// values are read through L2 (ld.cg) after a cluster barrier.
+// CTA `rank` owns the grid lines j0 <= j < j1 of every plane k (on every
+// level); another CTA's values are read through L2 (ld.cg) after a cluster
+// barrier.
 #pragma once
 
 #include "mlq_3d_types.cuh"
@@ -241,37 +242,94 @@ __device__ __forceinline__ T apply15(const T *__restrict__ C, const Grid3 &g, co
     return acc;
 }
 
-// node walk over the CTA's nodes P = P0 + l (l = tid, tid + nt, ...) keeping
-// (i, j, k) without a division per node
+// The nodes a CTA owns on one level: grid lines j0 <= j < j0 + nj of every
+// plane k.  They are visited line by line, j fastest inside the band and
+// then k, so that the nodes a 15-point product reads in the planes k +- 1
+// were visited one band of lines earlier (nj x mx nodes) rather than one
+// whole plane earlier: the reuse stays inside L2 when every SM streams.
+struct Band3 {
+    int mx, my, j0, nj;
+    int64_t cnt;
+};
+
+__device__ __forceinline__ Band3 band3(const Grid3 &g, int rank, int cs)
+{
+    Band3 b;
+    b.mx = g.mx;
+    b.my = g.my;
+    b.j0 = (int)((int64_t)g.my * rank / cs);
+    b.nj = (int)((int64_t)g.my * (rank + 1) / cs) - b.j0;
+    b.cnt = (int64_t)b.nj * g.mx * g.mz;
+    return b;
+}
+
+// a thread's position (i, j0 + jl, k) in its band, advanced by a fixed
+// stride of band-local indices without a division per node (nj > 0)
 struct Walk3 {
-    int i, j, k, di, dj, dk;
-    __device__ void init(int64_t P, int nt, const Grid3 &g)
+    int i, jl, k, di, dj, dk;
+    __device__ void init(const Band3 &b, int64_t f, int64_t stride)
     {
-        i = (int)(P % g.mx);
-        const int64_t line = P / g.mx;
-        j = (int)(line % g.my);
-        k = (int)(line / g.my);
-        di = nt % g.mx;
-        const int lines = nt / g.mx;
-        dj = lines % g.my;
-        dk = lines / g.my;
+        i = (int)(f % b.mx);
+        const int64_t line = f / b.mx;
+        jl = (int)(line % b.nj);
+        k = (int)(line / b.nj);
+        di = (int)(stride % b.mx);
+        const int64_t lines = stride / b.mx;
+        dj = (int)(lines % b.nj);
+        dk = (int)(lines / b.nj);
     }
-    __device__ void next(const Grid3 &g)
+    __device__ void next(const Band3 &b)
     {
         i += di;
-        j += dj;
+        jl += dj;
         k += dk;
-        if (i >= g.mx) {
-            i -= g.mx;
-            ++j;
+        if (i >= b.mx) {
+            i -= b.mx;
+            ++jl;
         }
-        if (j >= g.my) {
-            j -= g.my;
+        if (jl >= b.nj) {
+            jl -= b.nj;
             ++k;
         }
     }
+    __device__ int j(const Band3 &b) const { return b.j0 + jl; }
+    __device__ int64_t node(const Band3 &b) const { return i + (int64_t)b.mx * (b.j0 + jl + (int64_t)b.my * k); }
 };
 
+template <typename T, int N>
+struct Vals {
+    T v[N];
+};
+
+// For every node of the band: r = ld(P, i, j, k), then st(P, r).  U nodes
+// per thread and round, the loads of all U issued before the first store,
+// so that a pass with few loads per node still keeps U times the bytes in
+// flight (HBM latency, not bandwidth, bounds a pass with one node per round).
+template <int U, typename Ld, typename St>
+__device__ __forceinline__ void sweep3(const Band3 &b, int tid, int nt, Ld &&ld, St &&st)
+{
+    if (b.cnt <= 0) return;
+    using R = decltype(ld((int64_t)0, 0, 0, 0));
+    Walk3 wk;
+    wk.init(b, tid, nt);
+    for (int64_t f = tid; f < b.cnt; f += (int64_t)U * nt) {
+        R r[U];
+        int64_t P[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            P[u] = wk.node(b);
+            if (f + (int64_t)u * nt < b.cnt) r[u] = ld(P[u], wk.i, wk.j(b), wk.k);
+            wk.next(b);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (f + (int64_t)u * nt < b.cnt) st(P[u], r[u]);
+    }
+}
+
+// nodes per thread and round: streaming passes with a few loads per node,
+// and passes with a 15-point product (thirty loads of their own)
+constexpr int kU3 = 4, kU15 = 1;
 
 template <typename TI, int CS>
 __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
@@ -284,8 +342,7 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
     const int sample = blockIdx.x / CS;
     const Grid3 G = g.g;
     const int64_t n = G.n;
-    const int64_t lines = (int64_t)G.my * G.mz;
-    const int64_t own0 = (lines * rank / CS) * G.mx, own1 = (lines * (rank + 1) / CS) * G.mx;
+    const Band3 B0 = band3(G, rank, CS);
     const int tid = threadIdx.x, nt = blockDim.x;
     constexpr bool mixed = sizeof(TI) == 4;
 
@@ -303,20 +360,24 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
     TI *__restrict__ Pv = g.p + so;
     TI *__restrict__ X = g.x + so;
 
-    for (int64_t P = own0 + tid; P < own1; P += nt) {
-        double v0, w0;
-        if (g.v0) {
-            v0 = g.v0[P];
-            w0 = g.w0 ? g.w0[P] : 0.0;
-        } else {
-            const int i = (int)(P % G.mx), j = (int)((P / G.mx) % G.my), k = (int)(P / ((int64_t)G.mx * G.my));
-            const double xx = g.Lx * i / (G.mx - 1), yy = g.Ly * j / (G.my - 1), zz = g.Lz * k / (G.mz - 1);
-            v0 = (xx * xx + yy * yy + zz * zz <= g.radius2) ? 1.0 : 0.0;
-            w0 = 0.0;
-        }
-        vb0[P] = v0;
-        wb0[P] = w0;
-    }
+    sweep3<1>(
+        B0, tid, nt,
+        [&](int64_t P, int i, int j, int k) {
+            Vals<double, 2> s0;
+            if (g.v0) {
+                s0.v[0] = g.v0[P];
+                s0.v[1] = g.w0 ? g.w0[P] : 0.0;
+            } else {
+                const double xx = g.Lx * i / (G.mx - 1), yy = g.Ly * j / (G.my - 1), zz = g.Lz * k / (G.mz - 1);
+                s0.v[0] = (xx * xx + yy * yy + zz * zz <= g.radius2) ? 1.0 : 0.0;
+                s0.v[1] = 0.0;
+            }
+            return s0;
+        },
+        [&](int64_t P, const Vals<double, 2> &s0) {
+            vb0[P] = s0.v[0];
+            wb0[P] = s0.v[1];
+        });
     cl.sync();
 
     int wpar = 0, par = 0;
@@ -338,11 +399,6 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
             const Mg3Args &M = g.mg;
             const int NL = M.nl;
             const float om = M.omega;
-            auto span = [&](int c, int64_t &o0, int64_t &o1) {
-                const int64_t ln = (int64_t)M.g[c].my * M.g[c].mz;
-                o0 = (ln * rank / CS) * M.g[c].mx;
-                o1 = (ln * (rank + 1) / CS) * M.g[c].mx;
-            };
             auto Aof = [&](int c) -> const float * {
                 return c == 0 ? (const float *)Ai : M.A[c] + (size_t)sample * kSlots3D * M.g[c].n;
             };
@@ -351,90 +407,95 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
             auto RR = [&](int c) -> float * { return c == 0 ? (float *)U : vec(M.rr, c); };
             for (int c = 0; c < NL - 1; ++c) {
                 const Grid3 &Gc = M.g[c];
+                const Band3 Bc = band3(Gc, rank, CS);
                 const float *A = Aof(c), *Dv = A + 8 * (size_t)Gc.n;
                 float *xa = vec(M.xa, c), *rr = RR(c), *bb = BB(c);
-                int64_t o0, o1;
-                span(c, o0, o1);
-                for (int64_t P = o0 + tid; P < o1; P += nt) xa[P] = om * Dv[P] * __ldcg(bb + P);
+                // pre-smoothing from zero: XA = omega D^-1 B
+                sweep3<kU3>(
+                    Bc, tid, nt, [&](int64_t P, int, int, int) { return om * Dv[P] * __ldcg(bb + P); },
+                    [&](int64_t P, float x) { xa[P] = x; });
                 cl.sync();
-                {
-                    Walk3 wk;
-                    wk.init(o0 + tid, nt, Gc);
-                    for (int64_t P = o0 + tid; P < o1; P += nt, wk.next(Gc))
-                        rr[P] = __ldcg(bb + P) - apply15<float, float>(A, Gc, xa, P, wk.i, wk.j, wk.k);
-                }
+                // residual RR = B - A XA
+                sweep3<kU15>(
+                    Bc, tid, nt,
+                    [&](int64_t P, int i, int j, int k) {
+                        return __ldcg(bb + P) - apply15<float, float>(A, Gc, xa, P, i, j, k);
+                    },
+                    [&](int64_t P, float r) { rr[P] = r; });
                 cl.sync();
                 // restriction into level c+1
                 const Grid3 &Gq = M.g[c + 1];
                 float *bq = BB(c + 1);
-                int64_t q0, q1;
-                span(c + 1, q0, q1);
-                Walk3 wq;
-                wq.init(q0 + tid, nt, Gq);
-                for (int64_t Q = q0 + tid; Q < q1; Q += nt, wq.next(Gq)) {
-                    const int fi = 2 * wq.i, fj = 2 * wq.j, fk = 2 * wq.k;
-                    const int64_t f = fi + (int64_t)Gc.mx * (fj + (int64_t)Gc.my * fk);
-                    float h = 0.0f;
+                sweep3<kU15>(
+                    band3(Gq, rank, CS), tid, nt,
+                    [&](int64_t, int ci, int cj, int ck) {
+                        const int fi = 2 * ci, fj = 2 * cj, fk = 2 * ck;
+                        const int64_t f = fi + (int64_t)Gc.mx * (fj + (int64_t)Gc.my * fk);
+                        float h = 0.0f;
 #pragma unroll
-                    for (int sl = 1; sl < 8; ++sl) {
-                        const int dx = sl & 1, dy = (sl >> 1) & 1, dz = (sl >> 2) & 1;
-                        const int64_t off = dir_offset(Gc, sl);
-                        if (fi + dx < Gc.mx && fj + dy < Gc.my && fk + dz < Gc.mz) h += __ldcg(rr + f + off);
-                        if (fi >= dx && fj >= dy && fk >= dz) h += __ldcg(rr + f - off);
-                    }
-                    bq[Q] = __ldcg(rr + f) + 0.5f * h;
-                }
+                        for (int sl = 1; sl < 8; ++sl) {
+                            const int dx = sl & 1, dy = (sl >> 1) & 1, dz = (sl >> 2) & 1;
+                            const int64_t off = dir_offset(Gc, sl);
+                            if (fi + dx < Gc.mx && fj + dy < Gc.my && fk + dz < Gc.mz) h += __ldcg(rr + f + off);
+                            if (fi >= dx && fj >= dy && fk >= dz) h += __ldcg(rr + f - off);
+                        }
+                        return __ldcg(rr + f) + 0.5f * h;
+                    },
+                    [&](int64_t Q, float v) { bq[Q] = v; });
                 cl.sync();
             }
             // coarsest: damped Jacobi sweeps, ping-pong XA / XB
             {
                 const int c = NL - 1;
                 const Grid3 &Gc = M.g[c];
+                const Band3 Bc = band3(Gc, rank, CS);
                 const float *A = Aof(c), *Dv = A + 8 * (size_t)Gc.n;
-                float *X = vec(M.xa, c), *Y = vec(M.xb, c), *bb = BB(c);
-                int64_t o0, o1;
-                span(c, o0, o1);
-                for (int64_t P = o0 + tid; P < o1; P += nt) X[P] = om * Dv[P] * __ldcg(bb + P);
+                float *X0 = vec(M.xa, c), *Y0 = vec(M.xb, c), *bb = BB(c);
+                sweep3<kU3>(
+                    Bc, tid, nt, [&](int64_t P, int, int, int) { return om * Dv[P] * __ldcg(bb + P); },
+                    [&](int64_t P, float x) { X0[P] = x; });
                 for (int k = 1; k < kMgCoarsestSweeps3D; ++k) {
                     cl.sync();
-                    Walk3 wk;
-                    wk.init(o0 + tid, nt, Gc);
-                    for (int64_t P = o0 + tid; P < o1; P += nt, wk.next(Gc))
-                        Y[P] = __ldcg(X + P) +
-                               om * Dv[P] * (__ldcg(bb + P) - apply15<float, float>(A, Gc, X, P, wk.i, wk.j, wk.k));
-                    float *t = X;
-                    X = Y;
-                    Y = t;
+                    sweep3<kU15>(
+                        Bc, tid, nt,
+                        [&](int64_t P, int i, int j, int kk) {
+                            return __ldcg(X0 + P) +
+                                   om * Dv[P] * (__ldcg(bb + P) - apply15<float, float>(A, Gc, X0, P, i, j, kk));
+                        },
+                        [&](int64_t P, float x) { Y0[P] = x; });
+                    float *t = X0;
+                    X0 = Y0;
+                    Y0 = t;
                 }
                 cl.sync();
             }
             // ascend
             for (int c = NL - 2; c >= 0; --c) {
                 const Grid3 &Gc = M.g[c], &Gq = M.g[c + 1];
+                const Band3 Bc = band3(Gc, rank, CS);
                 const float *A = Aof(c), *Dv = A + 8 * (size_t)Gc.n;
                 const float *xq = (c + 1 == NL - 1) ? ((kMgCoarsestSweeps3D - 1) % 2 ? vec(M.xb, c + 1) : vec(M.xa, c + 1))
                                                     : RR(c + 1);
                 float *xa = vec(M.xa, c), *xb = vec(M.xb, c), *rr = RR(c), *bb = BB(c);
-                int64_t o0, o1;
-                span(c, o0, o1);
-                {
-                    Walk3 wk;
-                    wk.init(o0 + tid, nt, Gc);
-                    for (int64_t P = o0 + tid; P < o1; P += nt, wk.next(Gc)) {
-                        const int ci = wk.i >> 1, cj = wk.j >> 1, ck = wk.k >> 1;
+                // XB = XA + P X_{c+1}
+                sweep3<kU3>(
+                    Bc, tid, nt,
+                    [&](int64_t P, int i, int j, int k) {
+                        const int ci = i >> 1, cj = j >> 1, ck = k >> 1;
                         const int64_t qa = ci + (int64_t)Gq.mx * (cj + (int64_t)Gq.my * ck);
-                        const int64_t qb = qa + (wk.i & 1) + (int64_t)Gq.mx * ((wk.j & 1) + (int64_t)Gq.my * (wk.k & 1));
-                        xb[P] = __ldcg(xa + P) + 0.5f * (__ldcg(xq + qa) + __ldcg(xq + qb));
-                    }
-                }
+                        const int64_t qb = qa + (i & 1) + (int64_t)Gq.mx * ((j & 1) + (int64_t)Gq.my * (k & 1));
+                        return __ldcg(xa + P) + 0.5f * (__ldcg(xq + qa) + __ldcg(xq + qb));
+                    },
+                    [&](int64_t P, float x) { xb[P] = x; });
                 cl.sync();
-                {
-                    Walk3 wk;
-                    wk.init(o0 + tid, nt, Gc);
-                    for (int64_t P = o0 + tid; P < o1; P += nt, wk.next(Gc))
-                        rr[P] = __ldcg(xb + P) +
-                                om * Dv[P] * (__ldcg(bb + P) - apply15<float, float>(A, Gc, xb, P, wk.i, wk.j, wk.k));
-                }
+                // post-smoothing X_c = XB + omega D^-1 (B - A XB), into RR
+                sweep3<kU15>(
+                    Bc, tid, nt,
+                    [&](int64_t P, int i, int j, int k) {
+                        return __ldcg(xb + P) +
+                               om * Dv[P] * (__ldcg(bb + P) - apply15<float, float>(A, Gc, xb, P, i, j, k));
+                    },
+                    [&](int64_t P, float x) { rr[P] = x; });
                 cl.sync();
             }
         }
@@ -449,26 +510,39 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
         vpar ^= 1;
         const double *wcur = wb0 + wpar * SN;
         double *wnext = wb0 + (wpar ^ 1) * SN;
-        for (int64_t P = own0 + tid; P < own1; P += nt) {
-            const double vv = vcur[P], ww = wcur[P];
-            yb[P] = vv + dt * (vv * (vv - g.a) * (1.0 - vv) - ww);
-            wnext[P] = ww + dt * g.eps * (vv - g.gam * ww);
-            v[P] = step > 0 ? 2.0 * vv - v[P] : vv;
-        }
+        sweep3<2>(
+            B0, tid, nt,
+            [&](int64_t P, int, int, int) {
+                const double vv = vcur[P], ww = wcur[P];
+                Vals<double, 3> o;
+                o.v[0] = vv + dt * (vv * (vv - g.a) * (1.0 - vv) - ww);
+                o.v[1] = ww + dt * g.eps * (vv - g.gam * ww);
+                o.v[2] = step > 0 ? 2.0 * vv - v[P] : vv;
+                return o;
+            },
+            [&](int64_t P, const Vals<double, 3> &o) {
+                yb[P] = o.v[0];
+                wnext[P] = o.v[1];
+                v[P] = o.v[2];
+            });
         wpar ^= 1;
         cl.sync();
         {
             double acc[2] = {0.0, 0.0};
-            Walk3 wk;
-            wk.init(own0 + tid, nt, G);
-            for (int64_t P = own0 + tid; P < own1; P += nt, wk.next(G)) {
-                const double bb = apply15<double, double>(g.M3, G, yb, P, wk.i, wk.j, wk.k);
-                b[P] = bb;
-                const double rr = bb - apply15<double, double>(A64, G, v, P, wk.i, wk.j, wk.k);
-                R[P] = (TI)rr;
-                acc[0] += bb * bb;
-                acc[1] += rr * rr;
-            }
+            sweep3<1>(
+                B0, tid, nt,
+                [&](int64_t P, int i, int j, int k) {
+                    Vals<double, 2> o;
+                    o.v[0] = apply15<double, double>(g.M3, G, yb, P, i, j, k);
+                    o.v[1] = o.v[0] - apply15<double, double>(A64, G, v, P, i, j, k);
+                    return o;
+                },
+                [&](int64_t P, const Vals<double, 2> &o) {
+                    b[P] = o.v[0];
+                    R[P] = (TI)o.v[1];
+                    acc[0] += o.v[0] * o.v[0];
+                    acc[1] += o.v[1] * o.v[1];
+                });
             cluster_reduce<2, CS>(acc, wsl, csl, par, [&](double(&t)[2]) {
                 ctl.s0 = t[0];
                 ctl.s1 = t[1];
@@ -487,13 +561,15 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
         for (int sweep = 0; sweep < sweeps; ++sweep) {
             if (sweep > 0) {
                 double racc[1] = {0.0};
-                Walk3 wk;
-                wk.init(own0 + tid, nt, G);
-                for (int64_t P = own0 + tid; P < own1; P += nt, wk.next(G)) {
-                    const double rr = b[P] - apply15<double, double>(A64, G, v, P, wk.i, wk.j, wk.k);
-                    R[P] = (TI)rr;
-                    racc[0] += rr * rr;
-                }
+                sweep3<1>(
+                    B0, tid, nt,
+                    [&](int64_t P, int i, int j, int k) {
+                        return b[P] - apply15<double, double>(A64, G, v, P, i, j, k);
+                    },
+                    [&](int64_t P, double rr) {
+                        R[P] = (TI)rr;
+                        racc[0] += rr * rr;
+                    });
                 cluster_reduce<1, CS>(racc, wsl, csl, par, [&](double(&t)[1]) { ctl.s1 = t[0]; });
                 par ^= 1;
                 rnorm2 = ctl.s1;
@@ -514,15 +590,22 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
             const double need = tol_out2 / rnorm2;
             const double tol_in2 = mixed ? fmax(g.rtol_in * g.rtol_in, 0.0625 * need) : need;
 
-            // init: r0 normalised, u0 = D^-1 r0, x = p = s = 0
-            for (int64_t P = own0 + tid; P < own1; P += nt) {
-                const TI rr = R[P] * rscale;
-                R[P] = rr;
-                if (!mgp) U[P] = Dinv[P] * rr;
-                X[P] = (TI)0;
-                Pv[P] = (TI)0;
-                Sv[P] = (TI)0;
-            }
+            // init: r0 normalised, u0 = D^-1 r0 (Jacobi), x = p = s = 0
+            sweep3<kU3>(
+                B0, tid, nt,
+                [&](int64_t P, int, int, int) {
+                    Vals<TI, 2> o;
+                    o.v[0] = R[P] * rscale;
+                    o.v[1] = mgp ? (TI)0 : Dinv[P] * o.v[0];
+                    return o;
+                },
+                [&](int64_t P, const Vals<TI, 2> &o) {
+                    R[P] = o.v[0];
+                    if (!mgp) U[P] = o.v[1];
+                    X[P] = (TI)0;
+                    Pv[P] = (TI)0;
+                    Sv[P] = (TI)0;
+                });
             cl.sync();
             if (mgp) vcycle();
             double gamma_prev = 1.0, eta_prev = 1.0;
@@ -548,25 +631,35 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                 ctl.beta = beta;
                 ctl.code = code;
             };
-            double gacc = 0.0, racc = 0.0;   // (r, u) and (r, r) of the current iterate
-            for (int64_t P = own0 + tid; P < own1; P += nt) {
-                const TI rr = R[P], uu = __ldcg(U + P);
-                gacc += (double)(rr * uu);
-                racc += (double)(rr * rr);
-            }
+            // (r, u) and (r, r) of the current iterate
+            double gacc = 0.0, racc = 0.0;
+            sweep3<kU3>(
+                B0, tid, nt,
+                [&](int64_t P, int, int, int) {
+                    Vals<TI, 2> o;
+                    o.v[0] = R[P];
+                    o.v[1] = __ldcg(U + P);
+                    return o;
+                },
+                [&](int64_t, const Vals<TI, 2> &o) {
+                    gacc += (double)(o.v[0] * o.v[1]);
+                    racc += (double)(o.v[0] * o.v[0]);
+                });
             while (true) {
                 // w = A u, (w, u); one reduction of (r, u), (w, u), (r, r)
                 double pacc[3] = {gacc, 0.0, racc};
-                {
-                    Walk3 wk;
-                    wk.init(own0 + tid, nt, G);
-#pragma unroll 2
-                    for (int64_t P = own0 + tid; P < own1; P += nt, wk.next(G)) {
-                        const TI ww = apply15<TI, TI>(Ai, G, U, P, wk.i, wk.j, wk.k);
-                        W[P] = ww;
-                        pacc[1] += (double)(ww * __ldcg(U + P));
-                    }
-                }
+                sweep3<kU15>(
+                    B0, tid, nt,
+                    [&](int64_t P, int i, int j, int k) {
+                        Vals<TI, 2> o;
+                        o.v[0] = apply15<TI, TI>(Ai, G, U, P, i, j, k);
+                        o.v[1] = __ldcg(U + P);
+                        return o;
+                    },
+                    [&](int64_t P, const Vals<TI, 2> &o) {
+                        W[P] = o.v[0];
+                        pacc[1] += (double)(o.v[0] * o.v[1]);
+                    });
                 cluster_reduce<3, CS>(pacc, wsl, csl, par, [&](double(&t)[3]) { decide(t[0], t[1], t[2]); });
                 par ^= 1;
                 const int code = ctl.code;
@@ -579,33 +672,44 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                 // s = w + b s; p = u + b p; x += a p; r -= a s; u = D^-1 r
                 gacc = 0.0;
                 racc = 0.0;
-#pragma unroll 4
-                for (int64_t P = own0 + tid; P < own1; P += nt) {
-                    const TI ww = W[P], uu = __ldcg(U + P);
-                    const TI ss = it == 0 ? ww : ww + tb * Sv[P];
-                    const TI pp = it == 0 ? uu : uu + tb * Pv[P];
-                    Sv[P] = ss;
-                    Pv[P] = pp;
-                    X[P] += ta * pp;
-                    const TI rr = R[P] - ta * ss;
-                    R[P] = rr;
-                    racc += (double)(rr * rr);
-                    if (!mgp) {
-                        const TI un = Dinv[P] * rr;
-                        U[P] = un;
-                        gacc += (double)(rr * un);
-                    }
-                }
+                sweep3<2>(
+                    B0, tid, nt,
+                    [&](int64_t P, int, int, int) {
+                        const TI ww = W[P], uu = __ldcg(U + P);
+                        Vals<TI, 5> o;
+                        o.v[0] = it == 0 ? ww : ww + tb * Sv[P];
+                        o.v[1] = it == 0 ? uu : uu + tb * Pv[P];
+                        o.v[2] = X[P] + ta * o.v[1];
+                        o.v[3] = R[P] - ta * o.v[0];
+                        o.v[4] = mgp ? (TI)0 : Dinv[P] * o.v[3];
+                        return o;
+                    },
+                    [&](int64_t P, const Vals<TI, 5> &o) {
+                        Sv[P] = o.v[0];
+                        Pv[P] = o.v[1];
+                        X[P] = o.v[2];
+                        R[P] = o.v[3];
+                        racc += (double)(o.v[3] * o.v[3]);
+                        if (!mgp) {
+                            U[P] = o.v[4];
+                            gacc += (double)(o.v[3] * o.v[4]);
+                        }
+                    });
                 ++it;
                 cl.sync();
                 if (mgp) {
                     vcycle();
-                    for (int64_t P = own0 + tid; P < own1; P += nt) gacc += (double)(R[P] * __ldcg(U + P));
+                    sweep3<kU3>(
+                        B0, tid, nt,
+                        [&](int64_t P, int, int, int) { return (double)(R[P] * __ldcg(U + P)); },
+                        [&](int64_t, double t) { gacc += t; });
                 }
             }
             total_iters += it;
             if (nonfinite) break;
-            for (int64_t P = own0 + tid; P < own1; P += nt) v[P] = fma((double)X[P], rnorm, v[P]);
+            sweep3<2>(
+                B0, tid, nt, [&](int64_t P, int, int, int) { return fma((double)X[P], rnorm, v[P]); },
+                [&](int64_t P, double t) { v[P] = t; });
             cl.sync();
             if (!mixed) solved = true;
         }
@@ -618,7 +722,9 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
 
     double qacc[1] = {0.0};
     const double *vfin = vb0 + vpar * SN;   // solution of the last block
-    for (int64_t P = own0 + tid; P < own1; P += nt) qacc[0] += g.lump[P] * vfin[P];
+    sweep3<1>(
+        B0, tid, nt, [&](int64_t P, int, int, int) { return g.lump[P] * vfin[P]; },
+        [&](int64_t, double t) { qacc[0] += t; });
     cluster_reduce<1, CS>(qacc, wsl, csl, par, [&](double(&t)[1]) { ctl.s0 = t[0]; });
     if (rank == 0 && tid == 0) {
         g.q[sample] = status == S_NONFINITE ? __longlong_as_double(0x7ff8000000000000LL) : ctl.s0;
