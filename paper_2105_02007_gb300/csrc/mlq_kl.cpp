@@ -7,11 +7,42 @@
 #include "mlq.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
+#include <new>
+#include <thread>
 #include <vector>
 
 namespace {
+
+// Nodes per chunk of the host loops below.  Every reduction is formed per
+// chunk and the chunk results are combined in chunk order, so the results
+// depend on this constant but not on the number of threads.
+constexpr int64_t kChunk = 8192;
+
+// f(c) for c = 0 .. nchunks-1, spread over the host's cores
+template <typename F>
+void parallel_chunks(int64_t nchunks, F &&f)
+{
+    const int64_t hw = std::max(1u, std::thread::hardware_concurrency());
+    const int64_t nt = std::min<int64_t>(hw, nchunks);
+    if (nt <= 1) {
+        for (int64_t c = 0; c < nchunks; ++c) f(c);
+        return;
+    }
+    std::atomic<int64_t> next{0};
+    auto work = [&]() {
+        for (int64_t c; (c = next.fetch_add(1)) < nchunks;) f(c);
+    };
+    std::vector<std::thread> pool;
+    pool.reserve(nt - 1);
+    for (int64_t t = 1; t < nt; ++t) pool.emplace_back(work);
+    work();
+    for (auto &th : pool) th.join();
+}
+
+int64_t nchunks_of(int64_t n) { return (n + kChunk - 1) / kChunk; }
 
 struct Grid2 {
     int m;
@@ -27,7 +58,8 @@ void mass_apply(const Grid2 &g, const double *x, double *y, int ncol)
 {
     const int m = g.m, mc = m - 1;
     const double d = g.h * g.h / 12.0, e = g.h * g.h / 24.0;
-    for (int j = 0; j < m; ++j)
+    parallel_chunks(m, [&](int64_t jc) {
+        const int j = (int)jc;
         for (int i = 0; i < m; ++i) {
             const int64_t P = i + (int64_t)m * j;
             const int cij = (i < mc && j < mc), cim = (i >= 1 && j < mc), cmm = (i >= 1 && j >= 1),
@@ -44,6 +76,7 @@ void mass_apply(const Grid2 &g, const double *x, double *y, int ncol)
                 y[P * ncol + c] = acc;
             }
         }
+    });
 }
 
 // Symmetric eigen-decomposition by cyclic Jacobi rotations; the eigenvectors
@@ -126,10 +159,14 @@ void mass_apply3(const Grid3h &g, const double *x, double *y, int ncol)
     const int64_t n = g.n();
     std::fill(y, y + n * ncol, 0.0);
     const double c = g.hx * g.hy * g.hz / 6.0 / 20.0;
-    for (int k = 0; k + 1 < g.mz; ++k)
-        for (int j = 0; j + 1 < g.my; ++j)
-            for (int i = 0; i + 1 < g.mx; ++i)
-                for (int s = 0; s < 6; ++s) {
+    // a cell plane k adds into the node planes k and k + 1: the even cell
+    // planes first, then the odd ones, each set in parallel
+    for (int parity = 0; parity < 2; ++parity)
+        parallel_chunks((g.mz - 1 - parity + 1) / 2, [&](int64_t kc) {
+            const int k = 2 * (int)kc + parity;
+            for (int j = 0; j + 1 < g.my; ++j)
+                for (int i = 0; i + 1 < g.mx; ++i)
+                    for (int s = 0; s < 6; ++s) {
                     int64_t v[4];
                     int idx[3] = {i, j, k};
                     v[0] = idx[0] + (int64_t)g.mx * (idx[1] + (int64_t)g.my * idx[2]);
@@ -143,6 +180,7 @@ void mass_apply3(const Grid3h &g, const double *x, double *y, int ncol)
                         for (int a = 0; a < 4; ++a) y[v[a] * ncol + col] += c * (sum + x[v[a] * ncol + col]);
                     }
                 }
+        });
 }
 
 // Value at (px, py, pz) of the P1 interpolant of K nodal fields on the Kuhn
@@ -179,65 +217,119 @@ template <typename Coord, typename Mass>
 int build_kl_nodes(int64_t n, Coord coord, Mass mass, double sigma2, double ell, int K, double *modes_out,
                    double *lambda_out)
 {
+    const int64_t nc = nchunks_of(n);
+    auto chunk = [&](int64_t c, int64_t &t0, int64_t &t1) {
+        t0 = c * kChunk;
+        t1 = std::min(n, t0 + kChunk);
+    };
     std::vector<double> X(n * 3);
     for (int64_t t = 0; t < n; ++t) coord(t, &X[t * 3]);
     auto cov = [&](int64_t a, int64_t b) {
         const double dx = X[a * 3] - X[b * 3], dy = X[a * 3 + 1] - X[b * 3 + 1], dz = X[a * 3 + 2] - X[b * 3 + 2];
         return sigma2 * std::exp(-(dx * dx + dy * dy + dz * dz) / ell);
     };
+    // pivoted Cholesky: L (n x K, row-major), residual diagonal r; the pivot
+    // is the first maximum of r (per-chunk first maxima, combined in order)
     std::vector<double> L((size_t)n * K, 0.0), r(n, sigma2);
+    std::vector<double> cmax(nc);
+    std::vector<int64_t> carg(nc);
     for (int k = 0; k < K; ++k) {
-        int64_t piv = std::max_element(r.begin(), r.end()) - r.begin();
+        parallel_chunks(nc, [&](int64_t c) {
+            int64_t t0, t1;
+            chunk(c, t0, t1);
+            const int64_t a = std::max_element(r.begin() + t0, r.begin() + t1) - r.begin();
+            cmax[c] = r[a];
+            carg[c] = a;
+        });
+        int64_t piv = carg[0];
+        for (int64_t c = 1; c < nc; ++c)
+            if (cmax[c] > r[piv]) piv = carg[c];
         const double lp = std::sqrt(r[piv]);
         if (!(lp > 0.0)) return MLQ_EINVAL;
-        for (int64_t t = 0; t < n; ++t) {
-            double c = cov(t, piv);
-            for (int q = 0; q < k; ++q) c -= L[(size_t)t * K + q] * L[(size_t)piv * K + q];
-            L[(size_t)t * K + k] = c / lp;
-        }
-        for (int64_t t = 0; t < n; ++t) r[t] -= L[(size_t)t * K + k] * L[(size_t)t * K + k];
+        parallel_chunks(nc, [&](int64_t c) {
+            int64_t t0, t1;
+            chunk(c, t0, t1);
+            for (int64_t t = t0; t < t1; ++t) {
+                double v = cov(t, piv);
+                for (int q = 0; q < k; ++q) v -= L[(size_t)t * K + q] * L[(size_t)piv * K + q];
+                v /= lp;
+                L[(size_t)t * K + k] = v;
+                r[t] -= v * v;
+            }
+        });
     }
+    // B = L^T (M L): upper triangle summed per node range, the ranges added
+    // in order (as many ranges as chunks while their K x K partial sums stay
+    // within 2^24 values)
     std::vector<double> ML((size_t)n * K);
     mass(L.data(), ML.data(), K);
-    std::vector<double> B((size_t)K * K, 0.0);
-    for (int a = 0; a < K; ++a)
-        for (int c = a; c < K; ++c) {
-            double sum = 0.0;
-            for (int64_t t = 0; t < n; ++t) sum += L[(size_t)t * K + a] * ML[(size_t)t * K + c];
-            B[(size_t)a * K + c] = sum;
-            B[(size_t)c * K + a] = sum;
+    const int64_t nb = std::min<int64_t>(nc, std::max<int64_t>(1, ((int64_t)1 << 24) / ((int64_t)K * K)));
+    std::vector<double> Bc((size_t)nb * K * K, 0.0);
+    parallel_chunks(nb, [&](int64_t c) {
+        const int64_t t0 = n * c / nb, t1 = n * (c + 1) / nb;
+        double *b = &Bc[(size_t)c * K * K];
+        for (int64_t t = t0; t < t1; ++t) {
+            const double *lt = &L[(size_t)t * K], *mt = &ML[(size_t)t * K];
+            for (int a = 0; a < K; ++a) {
+                const double la = lt[a];
+                for (int q = a; q < K; ++q) b[(size_t)a * K + q] += la * mt[q];
+            }
         }
+    });
+    std::vector<double> B((size_t)K * K, 0.0);
+    for (int64_t c = 0; c < nb; ++c)
+        for (int a = 0; a < K; ++a)
+            for (int q = a; q < K; ++q) B[(size_t)a * K + q] += Bc[((size_t)c * K + a) * K + q];
+    for (int a = 0; a < K; ++a)
+        for (int q = 0; q < a; ++q) B[(size_t)a * K + q] = B[(size_t)q * K + a];
     std::vector<double> lam, Q;
     sym_eigen(K, B, lam, Q);
     std::vector<int> ord(K);
     for (int k = 0; k < K; ++k) ord[k] = k;
     std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) { return lam[a] > lam[c]; });
-    for (int k = 0; k < K; ++k) {
-        const int src = ord[k];
-        lambda_out[k] = lam[src];
-        double big = 0.0;
-        int64_t arg = 0;
-        for (int64_t t = 0; t < n; ++t) {
-            double sum = 0.0;
-            for (int q = 0; q < K; ++q) sum += L[(size_t)t * K + q] * Q[(size_t)q * K + src];
-            modes_out[(size_t)t * K + k] = sum;
-            if (std::fabs(sum) > big) {
-                big = std::fabs(sum);
-                arg = t;
+    for (int k = 0; k < K; ++k) lambda_out[k] = lam[ord[k]];
+    // modes v_k = L q_k; per mode the first entry of largest magnitude
+    std::vector<double> big((size_t)nc * K, 0.0);
+    std::vector<int64_t> arg((size_t)nc * K, 0);
+    parallel_chunks(nc, [&](int64_t c) {
+        int64_t t0, t1;
+        chunk(c, t0, t1);
+        for (int k = 0; k < K; ++k) arg[(size_t)c * K + k] = t0;
+        for (int64_t t = t0; t < t1; ++t)
+            for (int k = 0; k < K; ++k) {
+                const int src = ord[k];
+                double sum = 0.0;
+                for (int q = 0; q < K; ++q) sum += L[(size_t)t * K + q] * Q[(size_t)q * K + src];
+                modes_out[(size_t)t * K + k] = sum;
+                if (std::fabs(sum) > big[(size_t)c * K + k]) {
+                    big[(size_t)c * K + k] = std::fabs(sum);
+                    arg[(size_t)c * K + k] = t;
+                }
             }
-        }
-        if (modes_out[(size_t)arg * K + k] < 0.0)
-            for (int64_t t = 0; t < n; ++t) modes_out[(size_t)t * K + k] = -modes_out[(size_t)t * K + k];
+    });
+    std::vector<char> flip(K, 0);
+    for (int k = 0; k < K; ++k) {
+        double b = big[k];
+        int64_t a = arg[k];
+        for (int64_t c = 1; c < nc; ++c)
+            if (big[(size_t)c * K + k] > b) {
+                b = big[(size_t)c * K + k];
+                a = arg[(size_t)c * K + k];
+            }
+        flip[k] = modes_out[(size_t)a * K + k] < 0.0;
     }
+    parallel_chunks(nc, [&](int64_t c) {
+        int64_t t0, t1;
+        chunk(c, t0, t1);
+        for (int64_t t = t0; t < t1; ++t)
+            for (int k = 0; k < K; ++k)
+                if (flip[k]) modes_out[(size_t)t * K + k] = -modes_out[(size_t)t * K + k];
+    });
     return MLQ_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-int mlq_build_kl(int dim, const int32_t *dims, const double *lengths, double sigma2, double ell, int K,
-                 double *modes_out, double *lambda_out)
+int build_kl(int dim, const int32_t *dims, const double *lengths, double sigma2, double ell, int K,
+             double *modes_out, double *lambda_out)
 {
     if ((dim != 2 && dim != 3) || !dims || !modes_out || !lambda_out || !(sigma2 > 0.0) || !(ell > 0.0))
         return MLQ_EINVAL;
@@ -261,67 +353,17 @@ int mlq_build_kl(int dim, const int32_t *dims, const double *lengths, double sig
     const int64_t n = (int64_t)m * m;
     if (K < 1 || K > n || K > 4096) return MLQ_EINVAL;
     Grid2 g{m, 1.0 / (m - 1)};
-    std::vector<double> xs(n), ys(n);
-    for (int64_t t = 0; t < n; ++t) {
-        xs[t] = g.x(t);
-        ys[t] = g.y(t);
-    }
-    auto cov = [&](int64_t a, int64_t b) {
-        const double dx = xs[a] - xs[b], dy = ys[a] - ys[b];
-        return sigma2 * std::exp(-(dx * dx + dy * dy) / ell);
+    auto coord = [&](int64_t t, double *x) {
+        x[0] = g.x(t);
+        x[1] = g.y(t);
+        x[2] = 0.0;
     };
-    // pivoted Cholesky: L (n x K, row-major), residual diagonal r
-    std::vector<double> L((size_t)n * K, 0.0), r(n, sigma2);
-    for (int k = 0; k < K; ++k) {
-        int64_t piv = std::max_element(r.begin(), r.end()) - r.begin();  // first maximum
-        const double lp = std::sqrt(r[piv]);
-        if (!(lp > 0.0)) return MLQ_EINVAL;
-        for (int64_t t = 0; t < n; ++t) {
-            double c = cov(t, piv);
-            for (int q = 0; q < k; ++q) c -= L[(size_t)t * K + q] * L[(size_t)piv * K + q];
-            L[(size_t)t * K + k] = c / lp;
-        }
-        for (int64_t t = 0; t < n; ++t) r[t] -= L[(size_t)t * K + k] * L[(size_t)t * K + k];
-    }
-    // B = L^T (M L)
-    std::vector<double> ML((size_t)n * K);
-    mass_apply(g, L.data(), ML.data(), K);
-    std::vector<double> B((size_t)K * K, 0.0);
-    for (int a = 0; a < K; ++a)
-        for (int c = a; c < K; ++c) {
-            double s = 0.0;
-            for (int64_t t = 0; t < n; ++t) s += L[(size_t)t * K + a] * ML[(size_t)t * K + c];
-            B[(size_t)a * K + c] = s;
-        }
-    for (int a = 0; a < K; ++a)
-        for (int c = 0; c < a; ++c) B[(size_t)a * K + c] = B[(size_t)c * K + a];
-    std::vector<double> lam, Q;
-    sym_eigen(K, B, lam, Q);
-    std::vector<int> ord(K);
-    for (int k = 0; k < K; ++k) ord[k] = k;
-    std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) { return lam[a] > lam[c]; });
-    for (int k = 0; k < K; ++k) {
-        const int src = ord[k];
-        lambda_out[k] = lam[src];
-        double big = 0.0;
-        int64_t arg = 0;
-        for (int64_t t = 0; t < n; ++t) {
-            double s = 0.0;
-            for (int q = 0; q < K; ++q) s += L[(size_t)t * K + q] * Q[(size_t)q * K + src];
-            modes_out[(size_t)t * K + k] = s;
-            if (std::fabs(s) > big) {
-                big = std::fabs(s);
-                arg = t;
-            }
-        }
-        if (modes_out[(size_t)arg * K + k] < 0.0)
-            for (int64_t t = 0; t < n; ++t) modes_out[(size_t)t * K + k] = -modes_out[(size_t)t * K + k];
-    }
-    return MLQ_OK;
+    auto mass = [&](const double *x, double *y, int ncol) { mass_apply(g, x, y, ncol); };
+    return build_kl_nodes(n, coord, mass, sigma2, ell, K, modes_out, lambda_out);
 }
 
-int mlq_centroid_table(int dim, const int32_t *fine_dims, const double *modes_f, int K, const int32_t *coarse_dims,
-                       double *phi_out)
+int centroid_table(int dim, const int32_t *fine_dims, const double *modes_f, int K, const int32_t *coarse_dims,
+                   double *phi_out)
 {
     if ((dim != 2 && dim != 3) || !fine_dims || !coarse_dims || !modes_f || !phi_out || K < 1) return MLQ_EINVAL;
     if (dim == 3) {
@@ -332,8 +374,10 @@ int mlq_centroid_table(int dim, const int32_t *fine_dims, const double *modes_f,
         Grid3h gf{fine_dims[0], fine_dims[1], fine_dims[2], 1.0 / (fine_dims[0] - 1), 1.0 / (fine_dims[1] - 1),
                   1.0 / (fine_dims[2] - 1)};
         const double H[3] = {1.0 / (coarse_dims[0] - 1), 1.0 / (coarse_dims[1] - 1), 1.0 / (coarse_dims[2] - 1)};
-        int64_t e = 0;
-        for (int k = 0; k + 1 < coarse_dims[2]; ++k)
+        const int64_t cells_per_plane = (int64_t)(coarse_dims[0] - 1) * (coarse_dims[1] - 1);
+        parallel_chunks(coarse_dims[2] - 1, [&](int64_t kc) {
+            const int k = (int)kc;
+            int64_t e = 6 * cells_per_plane * k;
             for (int j = 0; j + 1 < coarse_dims[1]; ++j)
                 for (int i = 0; i + 1 < coarse_dims[0]; ++i)
                     for (int s = 0; s < 6; ++s, ++e) {
@@ -342,13 +386,15 @@ int mlq_centroid_table(int dim, const int32_t *fine_dims, const double *modes_f,
                         for (int q = 0; q < 3; ++q) p[kPerm[s][q]] += (3.0 - q) / 4.0;
                         p1_at3(gf, modes_f, K, p[0] * H[0], p[1] * H[1], p[2] * H[2], phi_out + e * K);
                     }
+        });
         return MLQ_OK;
     }
     const int mf = fine_dims[0], mc = coarse_dims[0];
     if (mf < 2 || mc < 2) return MLQ_EINVAL;
     Grid2 gf{mf, 1.0 / (mf - 1)};
     const double H = 1.0 / (mc - 1);
-    for (int j = 0; j + 1 < mc; ++j)
+    parallel_chunks(mc - 1, [&](int64_t jc) {
+        const int j = (int)jc;
         for (int i = 0; i + 1 < mc; ++i) {
             const int64_t c = i + (int64_t)(mc - 1) * j;
             // centroids of the lower and upper triangle of square (i, j)
@@ -357,7 +403,37 @@ int mlq_centroid_table(int dim, const int32_t *fine_dims, const double *modes_f,
             p1_at(gf, modes_f, K, xl, yl, phi_out + (2 * c) * K);
             p1_at(gf, modes_f, K, xu, yu, phi_out + (2 * c + 1) * K);
         }
+    });
     return MLQ_OK;
+}
+
+// host allocation or thread creation failures become status codes
+template <typename F>
+int guarded(F &&f)
+{
+    try {
+        return f();
+    } catch (const std::bad_alloc &) {
+        return MLQ_ENOMEM;
+    } catch (...) {
+        return MLQ_ENOMEM;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int mlq_build_kl(int dim, const int32_t *dims, const double *lengths, double sigma2, double ell, int K,
+                 double *modes_out, double *lambda_out)
+{
+    return guarded([&] { return build_kl(dim, dims, lengths, sigma2, ell, K, modes_out, lambda_out); });
+}
+
+int mlq_centroid_table(int dim, const int32_t *fine_dims, const double *modes_f, int K, const int32_t *coarse_dims,
+                       double *phi_out)
+{
+    return guarded([&] { return centroid_table(dim, fine_dims, modes_f, K, coarse_dims, phi_out); });
 }
 
 }  // extern "C"

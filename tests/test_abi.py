@@ -89,3 +89,15 @@ def test_product_centroid_table_3d_matches_oracle(mlq):
         ref = O.centroid_table(fine, modes, coarse)
         got = mlq.centroid_table((9, 9, 5), modes, cd)
         assert np.allclose(got, ref, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("dims,ell", [((25, 25, 17), 0.15 ** 2), (97, 0.04)])
+def test_product_kl_over_several_chunks_matches_oracle(mlq, dims, ell):
+    # meshes of more than one 8192-node chunk of the threaded host builder:
+    # pivots, B = L^T M L and the sign rule combine per-chunk results
+    mesh = O.mesh3d(*dims) if isinstance(dims, tuple) else O.mesh2d(dims)
+    assert mesh.n > 8192
+    om, ol = O.kl_build(mesh, 0.09, ell, 8)
+    pm, pl = mlq.build_kl(dims, 0.09, ell, 8)
+    assert np.allclose(pl, ol, rtol=1e-12, atol=0)
+    assert np.allclose(pm, om, rtol=0, atol=1e-12)
