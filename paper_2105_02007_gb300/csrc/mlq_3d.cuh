@@ -301,18 +301,41 @@ struct Vals {
     T v[N];
 };
 
+// L2 prefetch (one bulk request, TMA unit) of the 16-byte aligned part of
+// elements [lo, hi) of an array
+template <typename T>
+__device__ __forceinline__ void prefetch_l2(const T *a, int64_t lo, int64_t hi)
+{
+    const uintptr_t s = ((uintptr_t)(a + lo) + 15) & ~(uintptr_t)15;
+    const uintptr_t e = (uintptr_t)(a + hi) & ~(uintptr_t)15;
+    if (e > s) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(s), "r"((uint32_t)(e - s)) : "memory");
+}
+
+struct NoPrefetch {
+    __device__ void operator()(int64_t, int64_t) const {}
+};
+
 // For every node of the band: r = ld(P, i, j, k), then st(P, r).  U nodes
 // per thread and round, the loads of all U issued before the first store,
 // so that a pass with few loads per node still keeps U times the bytes in
 // flight (HBM latency, not bandwidth, bounds a pass with one node per round).
-template <int U, typename Ld, typename St>
-__device__ __forceinline__ void sweep3(const Band3 &b, int tid, int nt, Ld &&ld, St &&st)
+// pf(lo, hi) prefetches the node range [lo, hi) of the pass's streamed
+// arrays into L2: thread 0 hands it the band of the plane after the one it
+// is in (one contiguous range of nj x mx nodes per plane), so the CTA's
+// loads find their lines in L2.
+template <int U, typename Ld, typename St, typename Pf = NoPrefetch>
+__device__ __forceinline__ void sweep3(const Band3 &b, int tid, int nt, Ld &&ld, St &&st, Pf &&pf = Pf{})
 {
     if (b.cnt <= 0) return;
     using R = decltype(ld((int64_t)0, 0, 0, 0));
+    const int64_t plane = (int64_t)b.mx * b.my, band = (int64_t)b.mx * b.nj, base = (int64_t)b.mx * b.j0;
+    const int planes = (int)(b.cnt / band);
+    int ahead = 0;   // planes handed to pf so far (thread 0)
     Walk3 wk;
     wk.init(b, tid, nt);
     for (int64_t f = tid; f < b.cnt; f += (int64_t)U * nt) {
+        if (tid == 0)
+            for (; ahead < planes && ahead <= wk.k + 1; ++ahead) pf(base + plane * ahead, base + plane * ahead + band);
         R r[U];
         int64_t P[U];
 #pragma unroll
@@ -359,6 +382,12 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
     TI *__restrict__ Sv = g.s + so;
     TI *__restrict__ Pv = g.p + so;
     TI *__restrict__ X = g.x + so;
+    // L2 prefetch sets of the streaming passes: the eight stencil slots of a
+    // level, and single vectors
+    auto pf_slots = [](const auto *A, int64_t nn, int64_t lo, int64_t hi) {
+#pragma unroll 1
+        for (int sl = 0; sl < 8; ++sl) prefetch_l2(A + sl * nn, lo, hi);
+    };
 
     sweep3<1>(
         B0, tid, nt,
@@ -413,7 +442,11 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                 // pre-smoothing from zero: XA = omega D^-1 B
                 sweep3<kU3>(
                     Bc, tid, nt, [&](int64_t P, int, int, int) { return om * Dv[P] * __ldcg(bb + P); },
-                    [&](int64_t P, float x) { xa[P] = x; });
+                    [&](int64_t P, float x) { xa[P] = x; },
+                    [&](int64_t lo, int64_t hi) {
+                        prefetch_l2(Dv, lo, hi);
+                        prefetch_l2(bb, lo, hi);
+                    });
                 cl.sync();
                 // residual RR = B - A XA
                 sweep3<kU15>(
@@ -421,7 +454,12 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                     [&](int64_t P, int i, int j, int k) {
                         return __ldcg(bb + P) - apply15<float, float>(A, Gc, xa, P, i, j, k);
                     },
-                    [&](int64_t P, float r) { rr[P] = r; });
+                    [&](int64_t P, float r) { rr[P] = r; },
+                    [&](int64_t lo, int64_t hi) {
+                        pf_slots(A, Gc.n, lo, hi);
+                        prefetch_l2(xa, lo, hi);
+                        prefetch_l2(bb, lo, hi);
+                    });
                 cl.sync();
                 // restriction into level c+1
                 const Grid3 &Gq = M.g[c + 1];
@@ -486,7 +524,7 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                         const int64_t qb = qa + (i & 1) + (int64_t)Gq.mx * ((j & 1) + (int64_t)Gq.my * (k & 1));
                         return __ldcg(xa + P) + 0.5f * (__ldcg(xq + qa) + __ldcg(xq + qb));
                     },
-                    [&](int64_t P, float x) { xb[P] = x; });
+                    [&](int64_t P, float x) { xb[P] = x; }, [&](int64_t lo, int64_t hi) { prefetch_l2(xa, lo, hi); });
                 cl.sync();
                 // post-smoothing X_c = XB + omega D^-1 (B - A XB), into RR
                 sweep3<kU15>(
@@ -495,7 +533,13 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                         return __ldcg(xb + P) +
                                om * Dv[P] * (__ldcg(bb + P) - apply15<float, float>(A, Gc, xb, P, i, j, k));
                     },
-                    [&](int64_t P, float x) { rr[P] = x; });
+                    [&](int64_t P, float x) { rr[P] = x; },
+                    [&](int64_t lo, int64_t hi) {
+                        pf_slots(A, Gc.n, lo, hi);
+                        prefetch_l2(Dv, lo, hi);
+                        prefetch_l2(xb, lo, hi);
+                        prefetch_l2(bb, lo, hi);
+                    });
                 cl.sync();
             }
         }
@@ -644,6 +688,10 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                 [&](int64_t, const Vals<TI, 2> &o) {
                     gacc += (double)(o.v[0] * o.v[1]);
                     racc += (double)(o.v[0] * o.v[0]);
+                },
+                [&](int64_t lo, int64_t hi) {
+                    prefetch_l2(R, lo, hi);
+                    prefetch_l2(U, lo, hi);
                 });
             while (true) {
                 // w = A u, (w, u); one reduction of (r, u), (w, u), (r, r)
@@ -659,6 +707,10 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                     [&](int64_t P, const Vals<TI, 2> &o) {
                         W[P] = o.v[0];
                         pacc[1] += (double)(o.v[0] * o.v[1]);
+                    },
+                    [&](int64_t lo, int64_t hi) {
+                        pf_slots(Ai, n, lo, hi);
+                        prefetch_l2(U, lo, hi);
                     });
                 cluster_reduce<3, CS>(pacc, wsl, csl, par, [&](double(&t)[3]) { decide(t[0], t[1], t[2]); });
                 par ^= 1;
@@ -694,6 +746,15 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                             U[P] = o.v[4];
                             gacc += (double)(o.v[3] * o.v[4]);
                         }
+                    },
+                    [&](int64_t lo, int64_t hi) {
+                        prefetch_l2(W, lo, hi);
+                        prefetch_l2(U, lo, hi);
+                        prefetch_l2(Sv, lo, hi);
+                        prefetch_l2(Pv, lo, hi);
+                        prefetch_l2(X, lo, hi);
+                        prefetch_l2(R, lo, hi);
+                        if (!mgp) prefetch_l2(Dinv, lo, hi);
                     });
                 ++it;
                 cl.sync();
@@ -702,7 +763,11 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                     sweep3<kU3>(
                         B0, tid, nt,
                         [&](int64_t P, int, int, int) { return (double)(R[P] * __ldcg(U + P)); },
-                        [&](int64_t, double t) { gacc += t; });
+                        [&](int64_t, double t) { gacc += t; },
+                        [&](int64_t lo, int64_t hi) {
+                            prefetch_l2(R, lo, hi);
+                            prefetch_l2(U, lo, hi);
+                        });
                 }
             }
             total_iters += it;
