@@ -136,7 +136,7 @@ int mlq_set_model(mlq_ctx *ctx, const mlq_model *model);
  *   dim = 2: the m x m node mesh of the unit square (dims[0] = m, lengths
  *            ignored);
  *   dim = 3: the mx x my x mz node Kuhn mesh of the box (dims = {mx, my, mz},
- *            each >= 2, at most 2^28 nodes; lengths = {Lx, Ly, Lz} or NULL
+ *            each >= 2, at most 2^27 nodes; lengths = {Lx, Ly, Lz} or NULL
  *            for 1 x 1 x 0.25).  The mixed path solves 3D levels with the
  *            vectors in device memory (one cluster per sample) and a
  *            multigrid preconditioner when every axis has an odd node count

@@ -208,10 +208,10 @@ __global__ void stencil3d_from_d_kernel(const float *__restrict__ dbar, Grid3 g,
 // (C x)_P for a symmetric 15-point stencil C [8][n]: slot d at P couples to
 // P + d, slot d at P - d couples to P - d.  x read through L2.
 template <typename T, typename TX>
-__device__ __forceinline__ T apply15(const T *__restrict__ C, const Grid3 &g, const TX *x, int64_t P, int i, int j,
+__device__ __forceinline__ T apply15(const T *__restrict__ C, const Grid3 &g, const TX *x, int P, int i, int j,
                                      int k)
 {
-    const int64_t n = g.n;
+    const int n = g.n;
     if (i > 0 && j > 0 && k > 0 && i + 1 < g.mx && j + 1 < g.my && k + 1 < g.mz) {
         // interior node: all fourteen neighbours exist; every load is issued
         // before the first product so that they are in flight together
@@ -220,7 +220,7 @@ __device__ __forceinline__ T apply15(const T *__restrict__ C, const Grid3 &g, co
         xv[0] = (T)__ldcg(x + P);
 #pragma unroll
         for (int sl = 1; sl < 8; ++sl) {
-            const int64_t off = dir_offset(g, sl);
+            const int off = dir_offset32(g, sl);
             c[2 * sl - 1] = C[sl * n + P];
             c[2 * sl] = C[sl * n + P - off];
             xv[2 * sl - 1] = (T)__ldcg(x + P + off);
@@ -235,7 +235,7 @@ __device__ __forceinline__ T apply15(const T *__restrict__ C, const Grid3 &g, co
 #pragma unroll
     for (int sl = 1; sl < 8; ++sl) {
         const int dx = sl & 1, dy = (sl >> 1) & 1, dz = (sl >> 2) & 1;
-        const int64_t off = dir_offset(g, sl);
+        const int off = dir_offset32(g, sl);
         if (i + dx < g.mx && j + dy < g.my && k + dz < g.mz) acc += C[sl * n + P] * (T)__ldcg(x + P + off);
         if (i >= dx && j >= dy && k >= dz) acc += C[sl * n + P - off] * (T)__ldcg(x + P - off);
     }
@@ -249,7 +249,7 @@ __device__ __forceinline__ T apply15(const T *__restrict__ C, const Grid3 &g, co
 // whole plane earlier: the reuse stays inside L2 when every SM streams.
 struct Band3 {
     int mx, my, j0, nj;
-    int64_t cnt;
+    int cnt;
 };
 
 __device__ __forceinline__ Band3 band3(const Grid3 &g, int rank, int cs)
@@ -257,9 +257,9 @@ __device__ __forceinline__ Band3 band3(const Grid3 &g, int rank, int cs)
     Band3 b;
     b.mx = g.mx;
     b.my = g.my;
-    b.j0 = (int)((int64_t)g.my * rank / cs);
-    b.nj = (int)((int64_t)g.my * (rank + 1) / cs) - b.j0;
-    b.cnt = (int64_t)b.nj * g.mx * g.mz;
+    b.j0 = (int)(g.my * rank / cs);
+    b.nj = (int)(g.my * (rank + 1) / cs) - b.j0;
+    b.cnt = b.nj * g.mx * g.mz;
     return b;
 }
 
@@ -267,14 +267,14 @@ __device__ __forceinline__ Band3 band3(const Grid3 &g, int rank, int cs)
 // stride of band-local indices without a division per node (nj > 0)
 struct Walk3 {
     int i, jl, k, di, dj, dk;
-    __device__ void init(const Band3 &b, int64_t f, int64_t stride)
+    __device__ void init(const Band3 &b, int f, int stride)
     {
         i = (int)(f % b.mx);
-        const int64_t line = f / b.mx;
+        const int line = f / b.mx;
         jl = (int)(line % b.nj);
         k = (int)(line / b.nj);
         di = (int)(stride % b.mx);
-        const int64_t lines = stride / b.mx;
+        const int lines = stride / b.mx;
         dj = (int)(lines % b.nj);
         dk = (int)(lines / b.nj);
     }
@@ -293,7 +293,7 @@ struct Walk3 {
         }
     }
     __device__ int j(const Band3 &b) const { return b.j0 + jl; }
-    __device__ int64_t node(const Band3 &b) const { return i + (int64_t)b.mx * (b.j0 + jl + (int64_t)b.my * k); }
+    __device__ int node(const Band3 &b) const { return i + b.mx * (b.j0 + jl + b.my * k); }
 };
 
 template <typename T, int N>
@@ -304,7 +304,7 @@ struct Vals {
 // L2 prefetch (one bulk request, TMA unit) of the 16-byte aligned part of
 // elements [lo, hi) of an array
 template <typename T>
-__device__ __forceinline__ void prefetch_l2(const T *a, int64_t lo, int64_t hi)
+__device__ __forceinline__ void prefetch_l2(const T *a, int lo, int hi)
 {
     const uintptr_t s = ((uintptr_t)(a + lo) + 15) & ~(uintptr_t)15;
     const uintptr_t e = (uintptr_t)(a + hi) & ~(uintptr_t)15;
@@ -312,7 +312,7 @@ __device__ __forceinline__ void prefetch_l2(const T *a, int64_t lo, int64_t hi)
 }
 
 struct NoPrefetch {
-    __device__ void operator()(int64_t, int64_t) const {}
+    __device__ void operator()(int, int) const {}
 };
 
 // For every node of the band: r = ld(P, i, j, k), then st(P, r).  U nodes
@@ -327,26 +327,26 @@ template <int U, typename Ld, typename St, typename Pf = NoPrefetch>
 __device__ __forceinline__ void sweep3(const Band3 &b, int tid, int nt, Ld &&ld, St &&st, Pf &&pf = Pf{})
 {
     if (b.cnt <= 0) return;
-    using R = decltype(ld((int64_t)0, 0, 0, 0));
-    const int64_t plane = (int64_t)b.mx * b.my, band = (int64_t)b.mx * b.nj, base = (int64_t)b.mx * b.j0;
+    using R = decltype(ld(0, 0, 0, 0));
+    const int plane = b.mx * b.my, band = b.mx * b.nj, base = b.mx * b.j0;
     const int planes = (int)(b.cnt / band);
     int ahead = 0;   // planes handed to pf so far (thread 0)
     Walk3 wk;
     wk.init(b, tid, nt);
-    for (int64_t f = tid; f < b.cnt; f += (int64_t)U * nt) {
+    for (int f = tid; f < b.cnt; f += U * nt) {
         if (tid == 0)
             for (; ahead < planes && ahead <= wk.k + 1; ++ahead) pf(base + plane * ahead, base + plane * ahead + band);
         R r[U];
-        int64_t P[U];
+        int P[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             P[u] = wk.node(b);
-            if (f + (int64_t)u * nt < b.cnt) r[u] = ld(P[u], wk.i, wk.j(b), wk.k);
+            if (f + u * nt < b.cnt) r[u] = ld(P[u], wk.i, wk.j(b), wk.k);
             wk.next(b);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            if (f + (int64_t)u * nt < b.cnt) st(P[u], r[u]);
+            if (f + u * nt < b.cnt) st(P[u], r[u]);
     }
 }
 
@@ -360,11 +360,15 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
     __shared__ double wsl[32][4];
     __shared__ double csl[2][4];
     __shared__ Ctl ctl;
+    // the multigrid level table, indexed by the level at run time: a copy in
+    // shared memory keeps those reads out of local memory
+    __shared__ Mg3Args sM;
+    if (threadIdx.x == 0) sM = g.mg;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const int sample = blockIdx.x / CS;
     const Grid3 G = g.g;
-    const int64_t n = G.n;
+    const int n = G.n;
     const Band3 B0 = band3(G, rank, CS);
     const int tid = threadIdx.x, nt = blockDim.x;
     constexpr bool mixed = sizeof(TI) == 4;
@@ -384,14 +388,14 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
     TI *__restrict__ X = g.x + so;
     // L2 prefetch sets of the streaming passes: the eight stencil slots of a
     // level, and single vectors
-    auto pf_slots = [](const auto *A, int64_t nn, int64_t lo, int64_t hi) {
+    auto pf_slots = [](const auto *A, int nn, int lo, int hi) {
 #pragma unroll 1
         for (int sl = 0; sl < 8; ++sl) prefetch_l2(A + sl * nn, lo, hi);
     };
 
     sweep3<1>(
         B0, tid, nt,
-        [&](int64_t P, int i, int j, int k) {
+        [&](int P, int i, int j, int k) {
             Vals<double, 2> s0;
             if (g.v0) {
                 s0.v[0] = g.v0[P];
@@ -403,7 +407,7 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
             }
             return s0;
         },
-        [&](int64_t P, const Vals<double, 2> &s0) {
+        [&](int P, const Vals<double, 2> &s0) {
             vb0[P] = s0.v[0];
             wb0[P] = s0.v[1];
         });
@@ -425,7 +429,7 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
     const bool mgp = kMg && g.mg.nl > 1;
     auto vcycle = [&]() {
         if constexpr (kMg) {
-            const Mg3Args &M = g.mg;
+            const Mg3Args &M = sM;
             const int NL = M.nl;
             const float om = M.omega;
             auto Aof = [&](int c) -> const float * {
@@ -441,9 +445,9 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                 float *xa = vec(M.xa, c), *rr = RR(c), *bb = BB(c);
                 // pre-smoothing from zero: XA = omega D^-1 B
                 sweep3<kU3>(
-                    Bc, tid, nt, [&](int64_t P, int, int, int) { return om * Dv[P] * __ldcg(bb + P); },
-                    [&](int64_t P, float x) { xa[P] = x; },
-                    [&](int64_t lo, int64_t hi) {
+                    Bc, tid, nt, [&](int P, int, int, int) { return om * Dv[P] * __ldcg(bb + P); },
+                    [&](int P, float x) { xa[P] = x; },
+                    [&](int lo, int hi) {
                         prefetch_l2(Dv, lo, hi);
                         prefetch_l2(bb, lo, hi);
                     });
@@ -451,11 +455,11 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                 // residual RR = B - A XA
                 sweep3<kU15>(
                     Bc, tid, nt,
-                    [&](int64_t P, int i, int j, int k) {
+                    [&](int P, int i, int j, int k) {
                         return __ldcg(bb + P) - apply15<float, float>(A, Gc, xa, P, i, j, k);
                     },
-                    [&](int64_t P, float r) { rr[P] = r; },
-                    [&](int64_t lo, int64_t hi) {
+                    [&](int P, float r) { rr[P] = r; },
+                    [&](int lo, int hi) {
                         pf_slots(A, Gc.n, lo, hi);
                         prefetch_l2(xa, lo, hi);
                         prefetch_l2(bb, lo, hi);
@@ -466,20 +470,20 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                 float *bq = BB(c + 1);
                 sweep3<kU15>(
                     band3(Gq, rank, CS), tid, nt,
-                    [&](int64_t, int ci, int cj, int ck) {
+                    [&](int, int ci, int cj, int ck) {
                         const int fi = 2 * ci, fj = 2 * cj, fk = 2 * ck;
-                        const int64_t f = fi + (int64_t)Gc.mx * (fj + (int64_t)Gc.my * fk);
+                        const int f = fi + Gc.mx * (fj + Gc.my * fk);
                         float h = 0.0f;
 #pragma unroll
                         for (int sl = 1; sl < 8; ++sl) {
                             const int dx = sl & 1, dy = (sl >> 1) & 1, dz = (sl >> 2) & 1;
-                            const int64_t off = dir_offset(Gc, sl);
+                            const int off = dir_offset32(Gc, sl);
                             if (fi + dx < Gc.mx && fj + dy < Gc.my && fk + dz < Gc.mz) h += __ldcg(rr + f + off);
                             if (fi >= dx && fj >= dy && fk >= dz) h += __ldcg(rr + f - off);
                         }
                         return __ldcg(rr + f) + 0.5f * h;
                     },
-                    [&](int64_t Q, float v) { bq[Q] = v; });
+                    [&](int Q, float v) { bq[Q] = v; });
                 cl.sync();
             }
             // coarsest: damped Jacobi sweeps, ping-pong XA / XB
@@ -490,17 +494,17 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                 const float *A = Aof(c), *Dv = A + 8 * (size_t)Gc.n;
                 float *X0 = vec(M.xa, c), *Y0 = vec(M.xb, c), *bb = BB(c);
                 sweep3<kU3>(
-                    Bc, tid, nt, [&](int64_t P, int, int, int) { return om * Dv[P] * __ldcg(bb + P); },
-                    [&](int64_t P, float x) { X0[P] = x; });
+                    Bc, tid, nt, [&](int P, int, int, int) { return om * Dv[P] * __ldcg(bb + P); },
+                    [&](int P, float x) { X0[P] = x; });
                 for (int k = 1; k < kMgCoarsestSweeps3D; ++k) {
                     cl.sync();
                     sweep3<kU15>(
                         Bc, tid, nt,
-                        [&](int64_t P, int i, int j, int kk) {
+                        [&](int P, int i, int j, int kk) {
                             return __ldcg(X0 + P) +
                                    om * Dv[P] * (__ldcg(bb + P) - apply15<float, float>(A, Gc, X0, P, i, j, kk));
                         },
-                        [&](int64_t P, float x) { Y0[P] = x; });
+                        [&](int P, float x) { Y0[P] = x; });
                     float *t = X0;
                     X0 = Y0;
                     Y0 = t;
@@ -518,23 +522,23 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                 // XB = XA + P X_{c+1}
                 sweep3<kU3>(
                     Bc, tid, nt,
-                    [&](int64_t P, int i, int j, int k) {
+                    [&](int P, int i, int j, int k) {
                         const int ci = i >> 1, cj = j >> 1, ck = k >> 1;
-                        const int64_t qa = ci + (int64_t)Gq.mx * (cj + (int64_t)Gq.my * ck);
-                        const int64_t qb = qa + (i & 1) + (int64_t)Gq.mx * ((j & 1) + (int64_t)Gq.my * (k & 1));
+                        const int qa = ci + Gq.mx * (cj + Gq.my * ck);
+                        const int qb = qa + (i & 1) + Gq.mx * ((j & 1) + Gq.my * (k & 1));
                         return __ldcg(xa + P) + 0.5f * (__ldcg(xq + qa) + __ldcg(xq + qb));
                     },
-                    [&](int64_t P, float x) { xb[P] = x; }, [&](int64_t lo, int64_t hi) { prefetch_l2(xa, lo, hi); });
+                    [&](int P, float x) { xb[P] = x; }, [&](int lo, int hi) { prefetch_l2(xa, lo, hi); });
                 cl.sync();
                 // post-smoothing X_c = XB + omega D^-1 (B - A XB), into RR
                 sweep3<kU15>(
                     Bc, tid, nt,
-                    [&](int64_t P, int i, int j, int k) {
+                    [&](int P, int i, int j, int k) {
                         return __ldcg(xb + P) +
                                om * Dv[P] * (__ldcg(bb + P) - apply15<float, float>(A, Gc, xb, P, i, j, k));
                     },
-                    [&](int64_t P, float x) { rr[P] = x; },
-                    [&](int64_t lo, int64_t hi) {
+                    [&](int P, float x) { rr[P] = x; },
+                    [&](int lo, int hi) {
                         pf_slots(A, Gc.n, lo, hi);
                         prefetch_l2(Dv, lo, hi);
                         prefetch_l2(xb, lo, hi);
@@ -556,7 +560,7 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
         double *wnext = wb0 + (wpar ^ 1) * SN;
         sweep3<2>(
             B0, tid, nt,
-            [&](int64_t P, int, int, int) {
+            [&](int P, int, int, int) {
                 const double vv = vcur[P], ww = wcur[P];
                 Vals<double, 3> o;
                 o.v[0] = vv + dt * (vv * (vv - g.a) * (1.0 - vv) - ww);
@@ -564,7 +568,7 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                 o.v[2] = step > 0 ? 2.0 * vv - v[P] : vv;
                 return o;
             },
-            [&](int64_t P, const Vals<double, 3> &o) {
+            [&](int P, const Vals<double, 3> &o) {
                 yb[P] = o.v[0];
                 wnext[P] = o.v[1];
                 v[P] = o.v[2];
@@ -575,13 +579,13 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
             double acc[2] = {0.0, 0.0};
             sweep3<1>(
                 B0, tid, nt,
-                [&](int64_t P, int i, int j, int k) {
+                [&](int P, int i, int j, int k) {
                     Vals<double, 2> o;
                     o.v[0] = apply15<double, double>(g.M3, G, yb, P, i, j, k);
                     o.v[1] = o.v[0] - apply15<double, double>(A64, G, v, P, i, j, k);
                     return o;
                 },
-                [&](int64_t P, const Vals<double, 2> &o) {
+                [&](int P, const Vals<double, 2> &o) {
                     b[P] = o.v[0];
                     R[P] = (TI)o.v[1];
                     acc[0] += o.v[0] * o.v[0];
@@ -607,10 +611,10 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                 double racc[1] = {0.0};
                 sweep3<1>(
                     B0, tid, nt,
-                    [&](int64_t P, int i, int j, int k) {
+                    [&](int P, int i, int j, int k) {
                         return b[P] - apply15<double, double>(A64, G, v, P, i, j, k);
                     },
-                    [&](int64_t P, double rr) {
+                    [&](int P, double rr) {
                         R[P] = (TI)rr;
                         racc[0] += rr * rr;
                     });
@@ -637,13 +641,13 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
             // init: r0 normalised, u0 = D^-1 r0 (Jacobi), x = p = s = 0
             sweep3<kU3>(
                 B0, tid, nt,
-                [&](int64_t P, int, int, int) {
+                [&](int P, int, int, int) {
                     Vals<TI, 2> o;
                     o.v[0] = R[P] * rscale;
                     o.v[1] = mgp ? (TI)0 : Dinv[P] * o.v[0];
                     return o;
                 },
-                [&](int64_t P, const Vals<TI, 2> &o) {
+                [&](int P, const Vals<TI, 2> &o) {
                     R[P] = o.v[0];
                     if (!mgp) U[P] = o.v[1];
                     X[P] = (TI)0;
@@ -679,17 +683,17 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
             double gacc = 0.0, racc = 0.0;
             sweep3<kU3>(
                 B0, tid, nt,
-                [&](int64_t P, int, int, int) {
+                [&](int P, int, int, int) {
                     Vals<TI, 2> o;
                     o.v[0] = R[P];
                     o.v[1] = __ldcg(U + P);
                     return o;
                 },
-                [&](int64_t, const Vals<TI, 2> &o) {
+                [&](int, const Vals<TI, 2> &o) {
                     gacc += (double)(o.v[0] * o.v[1]);
                     racc += (double)(o.v[0] * o.v[0]);
                 },
-                [&](int64_t lo, int64_t hi) {
+                [&](int lo, int hi) {
                     prefetch_l2(R, lo, hi);
                     prefetch_l2(U, lo, hi);
                 });
@@ -698,17 +702,17 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                 double pacc[3] = {gacc, 0.0, racc};
                 sweep3<kU15>(
                     B0, tid, nt,
-                    [&](int64_t P, int i, int j, int k) {
+                    [&](int P, int i, int j, int k) {
                         Vals<TI, 2> o;
                         o.v[0] = apply15<TI, TI>(Ai, G, U, P, i, j, k);
                         o.v[1] = __ldcg(U + P);
                         return o;
                     },
-                    [&](int64_t P, const Vals<TI, 2> &o) {
+                    [&](int P, const Vals<TI, 2> &o) {
                         W[P] = o.v[0];
                         pacc[1] += (double)(o.v[0] * o.v[1]);
                     },
-                    [&](int64_t lo, int64_t hi) {
+                    [&](int lo, int hi) {
                         pf_slots(Ai, n, lo, hi);
                         prefetch_l2(U, lo, hi);
                     });
@@ -726,7 +730,7 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                 racc = 0.0;
                 sweep3<2>(
                     B0, tid, nt,
-                    [&](int64_t P, int, int, int) {
+                    [&](int P, int, int, int) {
                         const TI ww = W[P], uu = __ldcg(U + P);
                         Vals<TI, 5> o;
                         o.v[0] = it == 0 ? ww : ww + tb * Sv[P];
@@ -736,7 +740,7 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                         o.v[4] = mgp ? (TI)0 : Dinv[P] * o.v[3];
                         return o;
                     },
-                    [&](int64_t P, const Vals<TI, 5> &o) {
+                    [&](int P, const Vals<TI, 5> &o) {
                         Sv[P] = o.v[0];
                         Pv[P] = o.v[1];
                         X[P] = o.v[2];
@@ -747,7 +751,7 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                             gacc += (double)(o.v[3] * o.v[4]);
                         }
                     },
-                    [&](int64_t lo, int64_t hi) {
+                    [&](int lo, int hi) {
                         prefetch_l2(W, lo, hi);
                         prefetch_l2(U, lo, hi);
                         prefetch_l2(Sv, lo, hi);
@@ -762,9 +766,9 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                     vcycle();
                     sweep3<kU3>(
                         B0, tid, nt,
-                        [&](int64_t P, int, int, int) { return (double)(R[P] * __ldcg(U + P)); },
-                        [&](int64_t, double t) { gacc += t; },
-                        [&](int64_t lo, int64_t hi) {
+                        [&](int P, int, int, int) { return (double)(R[P] * __ldcg(U + P)); },
+                        [&](int, double t) { gacc += t; },
+                        [&](int lo, int hi) {
                             prefetch_l2(R, lo, hi);
                             prefetch_l2(U, lo, hi);
                         });
@@ -773,8 +777,8 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
             total_iters += it;
             if (nonfinite) break;
             sweep3<2>(
-                B0, tid, nt, [&](int64_t P, int, int, int) { return fma((double)X[P], rnorm, v[P]); },
-                [&](int64_t P, double t) { v[P] = t; });
+                B0, tid, nt, [&](int P, int, int, int) { return fma((double)X[P], rnorm, v[P]); },
+                [&](int P, double t) { v[P] = t; });
             cl.sync();
             if (!mixed) solved = true;
         }
@@ -788,8 +792,8 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
     double qacc[1] = {0.0};
     const double *vfin = vb0 + vpar * SN;   // solution of the last block
     sweep3<1>(
-        B0, tid, nt, [&](int64_t P, int, int, int) { return g.lump[P] * vfin[P]; },
-        [&](int64_t, double t) { qacc[0] += t; });
+        B0, tid, nt, [&](int P, int, int, int) { return g.lump[P] * vfin[P]; },
+        [&](int, double t) { qacc[0] += t; });
     cluster_reduce<1, CS>(qacc, wsl, csl, par, [&](double(&t)[1]) { ctl.s0 = t[0]; });
     if (rank == 0 && tid == 0) {
         g.q[sample] = status == S_NONFINITE ? __longlong_as_double(0x7ff8000000000000LL) : ctl.s0;

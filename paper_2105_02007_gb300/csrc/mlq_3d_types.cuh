@@ -41,6 +41,13 @@ __host__ __device__ inline int64_t dir_offset(const Grid3 &g, int slot)
     return (int64_t)(slot & 1) + (int64_t)g.mx * (((slot >> 1) & 1) + (int64_t)g.my * ((slot >> 2) & 1));
 }
 
+// the same in 32 bits: the solver indexes a sample's arrays (at most nine
+// slots of n nodes, n <= 2^27) with int
+__host__ __device__ inline int dir_offset32(const Grid3 &g, int slot)
+{
+    return (slot & 1) + g.mx * (((slot >> 1) & 1) + g.my * ((slot >> 2) & 1));
+}
+
 // Element matrices of tetrahedron s (|e| = hx hy hz / 6):
 //   M_e[a][b] = |e| / 20 (1 + delta_ab),  K_e[a][b] = |e| g_a^T D g_b,
 // D = s_t I + (s_l - s_t) f f^T, f = (cos t, sin t, 0), given (cos 2t, sin 2t).

@@ -1014,7 +1014,8 @@ int mlq_add_level(mlq_ctx *ctx, int level, int dim, const int32_t *dims, const d
     if (!(dt > 0.0) || nsteps < 0) return MLQ_EINVAL;
     if (dim == 3) {
         const int64_t nn = (int64_t)dims[0] * dims[1] * dims[2];
-        if (dims[0] < 2 || dims[1] < 2 || dims[2] < 2 || nn > (int64_t)1 << 28) return MLQ_EINVAL;
+        // nine stencil slots of a sample must stay within 32-bit indices
+        if (dims[0] < 2 || dims[1] < 2 || dims[2] < 2 || nn > (int64_t)1 << 27) return MLQ_EINVAL;
         if (lengths && !(lengths[0] > 0.0 && lengths[1] > 0.0 && lengths[2] > 0.0)) return MLQ_EINVAL;
     } else if (dims[0] < 2 || dims[0] > 8193) {
         return MLQ_EINVAL;
