@@ -424,10 +424,18 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
     // takes the mean of the coarse ends of the coarse edge it halves),
     // Jacobi sweeps on the coarsest level.  Every level is split over the
     // cluster by grid lines; values of other CTAs are read through L2 after a
-    // cluster barrier.  Input: R (level 0 right-hand side), result in U.
+    // cluster barrier.  Input: R (level 0 right-hand side) and its
+    // pre-smoothed XA_0 = omega D^-1 R, written by the pass that formed R;
+    // result in U.  Returns (r, u) and (r, r) (the thread's partial sums),
+    // formed in the level-0 post-smoothing.
     constexpr bool kMg = sizeof(TI) == 4;
     const bool mgp = kMg && g.mg.nl > 1;
+    float *const xa0 = mgp ? g.mg.xa[0] + so : nullptr;
+    const TI om0 = (TI)g.mg.omega;
     auto vcycle = [&]() {
+        Vals<double, 2> sums;
+        sums.v[0] = 0.0;
+        sums.v[1] = 0.0;
         if constexpr (kMg) {
             const Mg3Args &M = sM;
             const int NL = M.nl;
@@ -443,15 +451,17 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                 const Band3 Bc = band3(Gc, rank, CS);
                 const float *A = Aof(c), *Dv = A + 8 * (size_t)Gc.n;
                 float *xa = vec(M.xa, c), *rr = RR(c), *bb = BB(c);
-                // pre-smoothing from zero: XA = omega D^-1 B
-                sweep3<kU3>(
-                    Bc, tid, nt, [&](int P, int, int, int) { return om * Dv[P] * __ldcg(bb + P); },
-                    [&](int P, float x) { xa[P] = x; },
-                    [&](int lo, int hi) {
-                        prefetch_l2(Dv, lo, hi);
-                        prefetch_l2(bb, lo, hi);
-                    });
-                cl.sync();
+                // pre-smoothing from zero: XA = omega D^-1 B (level 0: done)
+                if (c > 0) {
+                    sweep3<kU3>(
+                        Bc, tid, nt, [&](int P, int, int, int) { return om * Dv[P] * __ldcg(bb + P); },
+                        [&](int P, float x) { xa[P] = x; },
+                        [&](int lo, int hi) {
+                            prefetch_l2(Dv, lo, hi);
+                            prefetch_l2(bb, lo, hi);
+                        });
+                    cl.sync();
+                }
                 // residual RR = B - A XA
                 sweep3<kU15>(
                     Bc, tid, nt,
@@ -531,22 +541,40 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                     [&](int P, float x) { xb[P] = x; }, [&](int lo, int hi) { prefetch_l2(xa, lo, hi); });
                 cl.sync();
                 // post-smoothing X_c = XB + omega D^-1 (B - A XB), into RR
-                sweep3<kU15>(
-                    Bc, tid, nt,
-                    [&](int P, int i, int j, int k) {
-                        return __ldcg(xb + P) +
-                               om * Dv[P] * (__ldcg(bb + P) - apply15<float, float>(A, Gc, xb, P, i, j, k));
-                    },
-                    [&](int P, float x) { rr[P] = x; },
-                    [&](int lo, int hi) {
-                        pf_slots(A, Gc.n, lo, hi);
-                        prefetch_l2(Dv, lo, hi);
-                        prefetch_l2(xb, lo, hi);
-                        prefetch_l2(bb, lo, hi);
-                    });
+                auto pf_post = [&](int lo, int hi) {
+                    pf_slots(A, Gc.n, lo, hi);
+                    prefetch_l2(Dv, lo, hi);
+                    prefetch_l2(xb, lo, hi);
+                    prefetch_l2(bb, lo, hi);
+                };
+                if (c > 0) {
+                    sweep3<kU15>(
+                        Bc, tid, nt,
+                        [&](int P, int i, int j, int k) {
+                            return __ldcg(xb + P) +
+                                   om * Dv[P] * (__ldcg(bb + P) - apply15<float, float>(A, Gc, xb, P, i, j, k));
+                        },
+                        [&](int P, float x) { rr[P] = x; }, pf_post);
+                } else {
+                    sweep3<kU15>(
+                        Bc, tid, nt,
+                        [&](int P, int i, int j, int k) {
+                            Vals<float, 2> o;
+                            o.v[1] = __ldcg(bb + P);
+                            o.v[0] = __ldcg(xb + P) + om * Dv[P] * (o.v[1] - apply15<float, float>(A, Gc, xb, P, i, j, k));
+                            return o;
+                        },
+                        [&](int P, const Vals<float, 2> &o) {
+                            rr[P] = o.v[0];
+                            sums.v[0] += (double)(o.v[1] * o.v[0]);
+                            sums.v[1] += (double)(o.v[1] * o.v[1]);
+                        },
+                        pf_post);
+                }
                 cl.sync();
             }
         }
+        return sums;
     };
 
     int vpar = 0;
@@ -638,24 +666,32 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
             const double need = tol_out2 / rnorm2;
             const double tol_in2 = mixed ? fmax(g.rtol_in * g.rtol_in, 0.0625 * need) : need;
 
-            // init: r0 normalised, u0 = D^-1 r0 (Jacobi), x = p = s = 0
+            // init: r0 normalised, x = p = s = 0; u0 = D^-1 r0 (Jacobi) or the
+            // multigrid's pre-smoothed XA_0 = omega D^-1 r0
             sweep3<kU3>(
                 B0, tid, nt,
                 [&](int P, int, int, int) {
                     Vals<TI, 2> o;
                     o.v[0] = R[P] * rscale;
-                    o.v[1] = mgp ? (TI)0 : Dinv[P] * o.v[0];
+                    o.v[1] = mgp ? om0 * Dinv[P] * o.v[0] : Dinv[P] * o.v[0];
                     return o;
                 },
                 [&](int P, const Vals<TI, 2> &o) {
                     R[P] = o.v[0];
-                    if (!mgp) U[P] = o.v[1];
+                    if (mgp) xa0[P] = (float)o.v[1];
+                    else U[P] = o.v[1];
                     X[P] = (TI)0;
                     Pv[P] = (TI)0;
                     Sv[P] = (TI)0;
                 });
             cl.sync();
-            if (mgp) vcycle();
+            // (r, u) and (r, r) of the current iterate
+            double gacc = 0.0, racc = 0.0;
+            if (mgp) {
+                const Vals<double, 2> t = vcycle();
+                gacc = t.v[0];
+                racc = t.v[1];
+            }
             double gamma_prev = 1.0, eta_prev = 1.0;
             int it = 0;
             auto decide = [&](double gamma, double delta, double rr) {
@@ -679,24 +715,24 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                 ctl.beta = beta;
                 ctl.code = code;
             };
-            // (r, u) and (r, r) of the current iterate
-            double gacc = 0.0, racc = 0.0;
-            sweep3<kU3>(
-                B0, tid, nt,
-                [&](int P, int, int, int) {
-                    Vals<TI, 2> o;
-                    o.v[0] = R[P];
-                    o.v[1] = __ldcg(U + P);
-                    return o;
-                },
-                [&](int, const Vals<TI, 2> &o) {
-                    gacc += (double)(o.v[0] * o.v[1]);
-                    racc += (double)(o.v[0] * o.v[0]);
-                },
-                [&](int lo, int hi) {
-                    prefetch_l2(R, lo, hi);
-                    prefetch_l2(U, lo, hi);
-                });
+            if (!mgp) {
+                sweep3<kU3>(
+                    B0, tid, nt,
+                    [&](int P, int, int, int) {
+                        Vals<TI, 2> o;
+                        o.v[0] = R[P];
+                        o.v[1] = __ldcg(U + P);
+                        return o;
+                    },
+                    [&](int, const Vals<TI, 2> &o) {
+                        gacc += (double)(o.v[0] * o.v[1]);
+                        racc += (double)(o.v[0] * o.v[0]);
+                    },
+                    [&](int lo, int hi) {
+                        prefetch_l2(R, lo, hi);
+                        prefetch_l2(U, lo, hi);
+                    });
+            }
             while (true) {
                 // w = A u, (w, u); one reduction of (r, u), (w, u), (r, r)
                 double pacc[3] = {gacc, 0.0, racc};
@@ -737,7 +773,7 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                         o.v[1] = it == 0 ? uu : uu + tb * Pv[P];
                         o.v[2] = X[P] + ta * o.v[1];
                         o.v[3] = R[P] - ta * o.v[0];
-                        o.v[4] = mgp ? (TI)0 : Dinv[P] * o.v[3];
+                        o.v[4] = mgp ? om0 * Dinv[P] * o.v[3] : Dinv[P] * o.v[3];
                         return o;
                     },
                     [&](int P, const Vals<TI, 5> &o) {
@@ -746,7 +782,9 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                         X[P] = o.v[2];
                         R[P] = o.v[3];
                         racc += (double)(o.v[3] * o.v[3]);
-                        if (!mgp) {
+                        if (mgp) {
+                            xa0[P] = (float)o.v[4];
+                        } else {
                             U[P] = o.v[4];
                             gacc += (double)(o.v[3] * o.v[4]);
                         }
@@ -758,21 +796,11 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                         prefetch_l2(Pv, lo, hi);
                         prefetch_l2(X, lo, hi);
                         prefetch_l2(R, lo, hi);
-                        if (!mgp) prefetch_l2(Dinv, lo, hi);
+                        prefetch_l2(Dinv, lo, hi);
                     });
                 ++it;
                 cl.sync();
-                if (mgp) {
-                    vcycle();
-                    sweep3<kU3>(
-                        B0, tid, nt,
-                        [&](int P, int, int, int) { return (double)(R[P] * __ldcg(U + P)); },
-                        [&](int, double t) { gacc += t; },
-                        [&](int lo, int hi) {
-                            prefetch_l2(R, lo, hi);
-                            prefetch_l2(U, lo, hi);
-                        });
-                }
+                if (mgp) gacc = vcycle().v[0];
             }
             total_iters += it;
             if (nonfinite) break;
