@@ -269,12 +269,14 @@ ELL3 = 0.15 ** 2
 # FP64 inner: 176 B.  Per block: reaction / w update (32 B), b = M y and
 # r = b - A v (two FP64 15-point passes, stencil slots 64 B + vectors 28 B),
 # one refinement residual (~90 B), v update (20 B) -> ~300 B.
-# Multigrid (FP32) adds per fine DOF: pre-smoothing (bb, 1/diag in, xa out)
-# 12 B, residual (8 slots, xa, bb in, rr out) 44 B, restriction 4 B,
-# interpolation (xa, coarse in, xb out) 12 B, post-smoothing (8 slots, xb, bb,
-# 1/diag in, result out) 48 B, plus an eighth of that per coarser level;
-# the CG part (update pass without 1/diag, matvec) stays: ~84 + 120 x 8/7 = 221 B.
-BYTES3D_PER_DOF_ITER = {"mixed": 88.0, "fp64": 176.0, "mg": 221.0}
+# Multigrid (FP32): the CG update pass also forms the level-0 pre-smoothing
+# (reads 1/diag, writes xa: 48 B with the updates) and the level-0
+# post-smoothing (8 slots, xb, bb, 1/diag in, result out: 48 B) also forms
+# (r, u); residual (8 slots, xa, bb in, rr out) 44 B, restriction 4 B,
+# interpolation (xa, coarse in, xb out) 12 B; matvec 40 B; each coarser level
+# an eighth of the V-cycle's 120 B (pre-smoothing 12 B there):
+# 48 + 40 + 108 + 120 / 7 = 213 B.
+BYTES3D_PER_DOF_ITER = {"mixed": 88.0, "fp64": 176.0, "mg": 213.0}
 BYTES3D_PER_DOF_STEP = 300.0
 
 
