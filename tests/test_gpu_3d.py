@@ -173,3 +173,73 @@ def test_3d_mlqmc_estimate_matches_oracle(mlq):
     for l in range(2):
         assert np.max(np.abs(ys[l] - yref[l])) < 1e-6 * np.max(np.abs(yref[0]))
     assert abs(mean - est_ref) < 1e-6 * abs(est_ref)
+
+
+# --------------------------------------------------------------------------
+# Full-size 3D levels in the launch shapes of the estimate (257 x 257 x 65
+# with 16 samples: clusters of 16; 129 x 129 x 33 with 64 samples: clusters
+# of 4), checked by properties that hold at any size and, at 129 x 129 x 33,
+# on sampled xi against the oracle over two time blocks.
+# --------------------------------------------------------------------------
+def lumped_mass(mesh):
+    # row sums of the P1 mass matrix: |e| / 4 per vertex of every tetrahedron
+    hx, hy, hz = (L / (m - 1) for L, m in zip(mesh.lengths, mesh.dims))
+    return np.bincount(mesh.conn.ravel(), minlength=mesh.n) * (hx * hy * hz / 6.0 / 4.0)
+
+
+def test_3d_full_size_block_conserves_mass_weighted_state(mlq):
+    # K 1 = 0, so one block gives m^T v+ = 1^T (M + dt K) v+ = 1^T M y with
+    # y = v + dt R(v, w): the QoI after one block is m^T y, for any fibres
+    dims, dt, S = (257, 257, 65), 0.00625, 16
+    mesh = O.mesh3d(*dims)
+    rng = np.random.default_rng(7)
+    phi = rng.normal(scale=0.5, size=(mesh.ne, 2))
+    v0 = rng.uniform(0, 1, size=mesh.n)
+    w0 = rng.uniform(0, 0.2, size=mesh.n)
+    y = v0 + dt * (v0 * (v0 - 0.1) * (1 - v0) - w0)
+    expect = lumped_mass(mesh) @ y
+    with mlq.Context(0, 1) as ctx:
+        ctx.add_level(0, dims, dt, 1)
+        ctx.set_kl(0, phi)
+        ctx.set_initial_state(0, v0, w0)
+        ctx.set_profiling(True)
+        r = ctx.solve(0, inputs.gaussian_xi(3, 3, 0, S, 2))
+        assert ctx.member_profile()[0]["cluster"] == 16
+    assert np.all(r["status"] == 0)
+    assert np.max(np.abs(r["q_fine"] - expect)) < 1e-9 * abs(expect)
+
+
+def test_3d_full_size_uniform_state(mlq):
+    dims, dt, S, nb = (257, 257, 65), 0.00625, 16, 12
+    mesh = O.mesh3d(*dims)
+    phi = np.random.default_rng(8).normal(size=(mesh.ne, 1))
+    v, w = 0.45, 0.03
+    with mlq.Context(0, 1) as ctx:
+        ctx.add_level(0, dims, dt, nb)
+        ctx.set_kl(0, phi)
+        ctx.set_initial_state(0, np.full(mesh.n, v), np.full(mesh.n, w))
+        r = ctx.solve(0, inputs.gaussian_xi(4, 3, 0, S, 1))
+    for _ in range(nb):
+        v, w = v + dt * (v * (v - 0.1) * (1 - v) - w), w + dt * 0.01 * (v - 0.5 * w)
+    assert np.all(r["status"] == 0)
+    assert np.allclose(r["q_fine"], 0.25 * v, rtol=1e-9, atol=0)
+
+
+def test_3d_level2_sampled_against_oracle(mlq):
+    dims, dt, S, nb, K = (129, 129, 33), 0.0125, 64, 2, 4
+    mesh = O.mesh3d(*dims)
+    modes, _ = O.kl_build(mesh, 0.09, 0.15 ** 2, K)
+    phi = O.centroid_table(mesh, modes, mesh)
+    xi = inputs.gaussian_xi(0, 2, 0, S, K)
+    with mlq.Context(0, 1) as ctx:
+        ctx.add_level(0, dims, dt, nb)
+        ctx.set_kl(0, phi)
+        ctx.set_profiling(True)
+        r = ctx.solve(0, xi)
+        assert ctx.member_profile()[0]["cluster"] == 4
+    assert np.all(r["status"] == 0)
+    pick = [0, 37, 63]
+    v0, _ = O.initial_state(mesh, 0.1)
+    q_ref, _, st = O.solve_batch(mesh, phi, xi[pick], dt, nb, v0=v0, nthreads=3)
+    assert np.all(st == 0)
+    assert rel(r["q_fine"][pick], q_ref) < TOL[1]
