@@ -212,9 +212,14 @@ __device__ __forceinline__ T apply15(const T *__restrict__ C, const Grid3 &g, co
                                      int k)
 {
     const int n = g.n;
-    if (i > 0 && j > 0 && k > 0 && i + 1 < g.mx && j + 1 < g.my && k + 1 < g.mz) {
-        // interior node: all fourteen neighbours exist; every load is issued
-        // before the first product so that they are in flight together
+    const int off7 = 1 + g.mx + g.mx * g.my;   // the largest offset, direction (1, 1, 1)
+    if (P >= off7 && P + off7 < n) {
+        // every P +- d is a node of the mesh (all but the first and last
+        // planes): a coupling that does not exist (i or j on the boundary,
+        // P +- d wrapping to another line) has a zero slot, set up so by the
+        // gather over the incident tetrahedra, and adds exactly nothing; so
+        // the product takes no branch per neighbour, and every load is
+        // issued before the first product so that they are in flight together
         T c[15], xv[15];
         c[0] = C[P];
         xv[0] = (T)__ldcg(x + P);
