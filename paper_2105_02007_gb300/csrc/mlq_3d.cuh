@@ -207,43 +207,33 @@ __global__ void stencil3d_from_d_kernel(const float *__restrict__ dbar, Grid3 g,
 
 // (C x)_P for a symmetric 15-point stencil C [8][n]: slot d at P couples to
 // P + d, slot d at P - d couples to P - d.  x read through L2.
+// One path for every node, so boundary nodes do not split their warp: a
+// coupling that does not exist (P on the boundary, P +- d wrapping to
+// another line or plane) has a zero slot, set up so by the gather over the
+// incident tetrahedra, and adds exactly nothing; a neighbour index outside
+// the array (first and last planes) is replaced by P and its slot by 0.
+// Every load is issued before the first product so that they are in
+// flight together.
 template <typename T, typename TX>
-__device__ __forceinline__ T apply15(const T *__restrict__ C, const Grid3 &g, const TX *x, int P, int i, int j,
-                                     int k)
+__device__ __forceinline__ T apply15(const T *__restrict__ C, const Grid3 &g, const TX *x, int P, int, int, int)
 {
     const int n = g.n;
-    const int off7 = 1 + g.mx + g.mx * g.my;   // the largest offset, direction (1, 1, 1)
-    if (P >= off7 && P + off7 < n) {
-        // every P +- d is a node of the mesh (all but the first and last
-        // planes): a coupling that does not exist (i or j on the boundary,
-        // P +- d wrapping to another line) has a zero slot, set up so by the
-        // gather over the incident tetrahedra, and adds exactly nothing; so
-        // the product takes no branch per neighbour, and every load is
-        // issued before the first product so that they are in flight together
-        T c[15], xv[15];
-        c[0] = C[P];
-        xv[0] = (T)__ldcg(x + P);
-#pragma unroll
-        for (int sl = 1; sl < 8; ++sl) {
-            const int off = dir_offset32(g, sl);
-            c[2 * sl - 1] = C[sl * n + P];
-            c[2 * sl] = C[sl * n + P - off];
-            xv[2 * sl - 1] = (T)__ldcg(x + P + off);
-            xv[2 * sl] = (T)__ldcg(x + P - off);
-        }
-        T acc = c[0] * xv[0];
-#pragma unroll
-        for (int q = 1; q < 15; ++q) acc += c[q] * xv[q];
-        return acc;
-    }
-    T acc = C[P] * (T)__ldcg(x + P);
+    T c[15], xv[15];
+    c[0] = C[P];
+    xv[0] = (T)__ldcg(x + P);
 #pragma unroll
     for (int sl = 1; sl < 8; ++sl) {
-        const int dx = sl & 1, dy = (sl >> 1) & 1, dz = (sl >> 2) & 1;
         const int off = dir_offset32(g, sl);
-        if (i + dx < g.mx && j + dy < g.my && k + dz < g.mz) acc += C[sl * n + P] * (T)__ldcg(x + P + off);
-        if (i >= dx && j >= dy && k >= dz) acc += C[sl * n + P - off] * (T)__ldcg(x + P - off);
+        const bool up = P + off < n, dn = P >= off;
+        const T cu = C[sl * n + P], cd = C[sl * n + (dn ? P - off : P)];
+        c[2 * sl - 1] = up ? cu : (T)0;
+        c[2 * sl] = dn ? cd : (T)0;
+        xv[2 * sl - 1] = (T)__ldcg(x + (up ? P + off : P));
+        xv[2 * sl] = (T)__ldcg(x + (dn ? P - off : P));
     }
+    T acc = c[0] * xv[0];
+#pragma unroll
+    for (int q = 1; q < 15; ++q) acc += c[q] * xv[q];
     return acc;
 }
 
@@ -488,15 +478,26 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                     [&](int, int ci, int cj, int ck) {
                         const int fi = 2 * ci, fj = 2 * cj, fk = 2 * ck;
                         const int f = fi + Gc.mx * (fj + Gc.my * fk);
-                        float h = 0.0f;
+                        // branch-free: a missing neighbour loads the centre
+                        // and enters with weight 0 (h + 0 v = h exactly), so
+                        // boundary nodes do not split their warp
+                        float v[15], wgt[15];
+                        v[0] = __ldcg(rr + f);
 #pragma unroll
                         for (int sl = 1; sl < 8; ++sl) {
                             const int dx = sl & 1, dy = (sl >> 1) & 1, dz = (sl >> 2) & 1;
                             const int off = dir_offset32(Gc, sl);
-                            if (fi + dx < Gc.mx && fj + dy < Gc.my && fk + dz < Gc.mz) h += __ldcg(rr + f + off);
-                            if (fi >= dx && fj >= dy && fk >= dz) h += __ldcg(rr + f - off);
+                            const bool up = fi + dx < Gc.mx && fj + dy < Gc.my && fk + dz < Gc.mz;
+                            const bool dn = fi >= dx && fj >= dy && fk >= dz;
+                            v[2 * sl - 1] = __ldcg(rr + (up ? f + off : f));
+                            v[2 * sl] = __ldcg(rr + (dn ? f - off : f));
+                            wgt[2 * sl - 1] = up ? 1.0f : 0.0f;
+                            wgt[2 * sl] = dn ? 1.0f : 0.0f;
                         }
-                        return __ldcg(rr + f) + 0.5f * h;
+                        float h = 0.0f;
+#pragma unroll
+                        for (int q = 1; q < 15; ++q) h += wgt[q] * v[q];
+                        return v[0] + 0.5f * h;
                     },
                     [&](int Q, float v) { bq[Q] = v; });
                 cl.sync();
