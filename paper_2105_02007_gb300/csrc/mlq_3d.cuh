@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
     const double *A64 = g.A64 + (size_t)sample * kSlots3D * n;
     const TI *Ai = g.Ai + (size_t)sample * kSlots3D * n;
     const TI *__restrict__ Dinv = Ai + 8 * n;
-    // v: [2][S][n], the solution of the last block and the guess of the next
+    // v: [kVRing][S][n], the solutions of the last blocks and the guess of the next
     double *vb0 = g.v + so, *wb0 = g.w + so, *b = g.b + so, *yb = g.y + so;
     TI *__restrict__ R = g.r + so;
     TI *__restrict__ U = g.u + so;
@@ -583,13 +583,15 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
         return sums;
     };
 
-    int vpar = 0;
+    auto vring = [&](int j) { return vb0 + (size_t)(((j % kVRing) + kVRing) % kVRing) * SN; };
     for (int step = 0; step < g.nsteps; ++step) {
-        // the block starts from 2 v_n - v_{n-1} (v_n on the first block),
-        // kept in the other buffer
-        const double *vcur = vb0 + vpar * SN;
-        double *v = vb0 + (vpar ^ 1) * SN;
-        vpar ^= 1;
+        // the block starts from the extrapolation of order guess_order(step)
+        // over v_n, v_{n-1}, ..., kept in the buffer of v_{n+1} (which held
+        // v_{n-3})
+        const double *vcur = vring(step);
+        const double *vm1 = vring(step - 1), *vm2 = vring(step - 2);
+        double *v = vring(step + 1);
+        const int gp = guess_order(step);
         const double *wcur = wb0 + wpar * SN;
         double *wnext = wb0 + (wpar ^ 1) * SN;
         sweep3<2>(
@@ -599,7 +601,7 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                 Vals<double, 3> o;
                 o.v[0] = vv + dt * (vv * (vv - g.a) * (1.0 - vv) - ww);
                 o.v[1] = ww + dt * g.eps * (vv - g.gam * ww);
-                o.v[2] = step > 0 ? 2.0 * vv - v[P] : vv;
+                o.v[2] = extrapolate(gp, vv, gp >= 1 ? vm1[P] : 0.0, gp >= 2 ? vm2[P] : 0.0, gp >= 3 ? v[P] : 0.0);
                 return o;
             },
             [&](int P, const Vals<double, 3> &o) {
@@ -824,7 +826,7 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
     }
 
     double qacc[1] = {0.0};
-    const double *vfin = vb0 + vpar * SN;   // solution of the last block
+    const double *vfin = vring(g.nsteps);   // solution of the last block
     sweep3<1>(
         B0, tid, nt, [&](int P, int, int, int) { return g.lump[P] * vfin[P]; },
         [&](int, double t) { qacc[0] += t; });

@@ -409,7 +409,7 @@ size_t member_bytes(const mlq_ctx *ctx, const Level &L, int64_t S)
         add((size_t)S * L.ne * 2 * 8);                 // cs2
         add(sn * mlq::kSlots3D * 8);                    // A64
         if (mixed) add(sn * mlq::kSlots3D * 4);         // A32
-        add(2 * sn * 8);                                // v (solution and guess)
+        add(mlq::kVRing * sn * 8);                      // v (last solutions and guess)
         add(2 * sn * 8);                                // w
         add(sn * 8);                                    // b
         add(sn * 8);                                    // y
@@ -435,7 +435,7 @@ size_t member_bytes(const mlq_ctx *ctx, const Level &L, int64_t S)
     add((size_t)S * L.ne * 2 * 8);          // cs2
     add(sn * mlq::kSlots2D * 8);            // A64
     if (mixed) add(sn * mlq::kSlots2D * 4); // A32
-    add((mixed && ctx->opt.precond == 1 ? 2 : 1) * sn * 8);  // v (multigrid: solution and guess)
+    add((mixed && ctx->opt.precond == 1 ? mlq::kVRing : 1) * sn * 8);  // v (multigrid: last solutions and guess)
     add(2 * sn * 8);                        // w
     add(sn * 8);                            // b
     if (mixed && ctx->opt.precond == 1) add(sn * 8);  // y (multigrid kernel)
@@ -472,7 +472,7 @@ void member_carve(const mlq_ctx *ctx, const Level &L, Member &mb, char *&cur)
         mb.cs2 = (double *)take((size_t)mb.S * L.ne * 2 * 8);
         mb.A64 = (double *)take(sn * mlq::kSlots3D * 8);
         mb.Ai = mixed ? take(sn * mlq::kSlots3D * 4) : (void *)mb.A64;
-        mb.v = (double *)take(2 * sn * 8);
+        mb.v = (double *)take(mlq::kVRing * sn * 8);
         mb.w = (double *)take(2 * sn * 8);
         mb.b = (double *)take(sn * 8);
         mb.y = (double *)take(sn * 8);
@@ -503,7 +503,7 @@ void member_carve(const mlq_ctx *ctx, const Level &L, Member &mb, char *&cur)
     mb.cs2 = (double *)take((size_t)mb.S * L.ne * 2 * 8);
     mb.A64 = (double *)take(sn * mlq::kSlots2D * 8);
     mb.Ai = mixed ? take(sn * mlq::kSlots2D * 4) : (void *)mb.A64;
-    mb.v = (double *)take((mixed && ctx->opt.precond == 1 ? 2 : 1) * sn * 8);
+    mb.v = (double *)take((mixed && ctx->opt.precond == 1 ? mlq::kVRing : 1) * sn * 8);
     mb.w = (double *)take(2 * sn * 8);
     mb.b = (double *)take(sn * 8);
     mb.y = (mixed && ctx->opt.precond == 1) ? (double *)take(sn * 8) : nullptr;

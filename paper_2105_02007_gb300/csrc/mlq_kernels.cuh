@@ -41,6 +41,29 @@ struct FastDiv {
 // ---------------------------------------------------------------------------
 // Slab solver.
 // ---------------------------------------------------------------------------
+
+// Solutions of the last blocks kept for the initial guess of the next one
+// (multigrid kernels): v_j lives in buffer j mod kVRing of [kVRing][S][n].
+// The guess of block `step` (from v_step, v_step-1, ...) is the polynomial
+// extrapolation of order guess_order(step): the value at t + dt of the
+// polynomial through the last p + 1 solutions.  The order starts at 0 and
+// rises by one every two blocks: the first blocks follow a discontinuous
+// initial state, and a stencil reaching back to it or to the first rough
+// solutions makes a worse guess than v_step itself.
+constexpr int kVRing = 4;
+
+__host__ __device__ inline int guess_order(int step) { return step < 3 ? 0 : ((step - 1) / 2 < 3 ? (step - 1) / 2 : 3); }
+
+__host__ __device__ inline double extrapolate(int p, double v0, double v1, double v2, double v3)
+{
+    switch (p) {
+    case 0: return v0;
+    case 1: return 2.0 * v0 - v1;
+    case 2: return 3.0 * v0 - 3.0 * v1 + v2;
+    default: return 4.0 * v0 - 6.0 * v1 + 4.0 * v2 - v3;
+    }
+}
+
 template <typename TI>
 struct SolveArgs {
     int m, n;
@@ -53,7 +76,7 @@ struct SolveArgs {
     int max_iter, max_sweeps;
     const double *A64;            // [S][4][n]
     const TI *Ai;                 // [S][4][n] stencil in the inner precision
-    double *v;                    // [S][n]; [2][S][n] for the multigrid kernel
+    double *v;                    // [S][n]; [kVRing][S][n] for the multigrid kernel
     double *w;                    // [2][S][n]
     double *b;                    // [S][n]
     double *y;                    // [S][n] v + dt R(v, w) per node (multigrid kernel), else null

@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1)
     const size_t so = (size_t)sample * n;
     const size_t SN = (size_t)g.S * n;
     const double *A64 = g.A64 + (size_t)sample * kSlots2D * n;
-    double *vb0 = g.v + so;   // [2][S][n]: solution of the last block, guess of the next
+    double *vb0 = g.v + so;   // [kVRing][S][n]: solutions of the last blocks, guess of the next
     double *wb0 = g.w + so;
     double *b = g.b + so;
     double *yb = g.y + so;
@@ -524,20 +524,22 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1)
     const int FB = 1 + m;   // tile index of own local 0 on the fine level
 
     float r[NPT], u[NPT], w[NPT], sv[NPT], p[NPT], x[NPT];
-    int wpar = 0, vpar = 0, par = 0;
+    int wpar = 0, par = 0;
+    auto vring = [&](int j) { return vb0 + (size_t)(((j % kVRing) + kVRing) % kVRing) * SN; };
     int64_t total_iters = 0;
     int32_t status = S_CONVERGED;
     const double dt = g.dt;
 
     for (int step = 0; step < g.nsteps; ++step) {
         // ---- block load: b = M (v + dt R), w update, extrapolated initial
-        // guess 2 v_n - v_{n-1} (v_n on the first block) in the other v
-        // buffer, then r0 = b - A guess (into RR)
+        // guess (order guess_order(step) over v_n, v_{n-1}, ...) in the
+        // buffer of v_{n+1}, then r0 = b - A guess (into RR)
         const double *wcur = wb0 + wpar * SN;
         double *wnext = wb0 + (wpar ^ 1) * SN;
-        const double *vcur = vb0 + vpar * SN;
-        double *v = vb0 + (vpar ^ 1) * SN;
-        vpar ^= 1;
+        const double *vcur = vring(step);
+        const double *vm1 = vring(step - 1), *vm2 = vring(step - 2);
+        double *v = vring(step + 1);   // holds v_{n-3} until the guess replaces it
+        const int gp = guess_order(step);
         // y = v + dt R(v, w) once per node (the mass product reads it at the
         // seven stencil points)
 #pragma unroll 1
@@ -546,7 +548,8 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1)
             const double vv = vcur[node], ww = wcur[node];
             yb[node] = vv + dt * (vv * (vv - g.a) * (1.0 - vv) - ww);
             wnext[node] = ww + dt * g.eps * (vv - g.gam * ww);
-            v[node] = step > 0 ? 2.0 * vv - v[node] : vv;
+            v[node] = extrapolate(gp, vv, gp >= 1 ? vm1[node] : 0.0, gp >= 2 ? vm2[node] : 0.0,
+                                  gp >= 3 ? v[node] : 0.0);
         }
         cl.sync();
         {
@@ -706,7 +709,7 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1)
         if (!solved && status == S_CONVERGED) status = S_MAXITER;
     }
 
-    const double *vfin = vb0 + vpar * SN;   // solution of the last block
+    const double *vfin = vring(g.nsteps);   // solution of the last block
     double qacc[1] = {0.0};
     for (int node = own0 + tid; node < own1; node += nt) {
         const int j = node / m, i = node - j * m;
