@@ -161,6 +161,13 @@ __host__ __device__ inline MgPlan mg_plan(int m0, int cs)
 __device__ __forceinline__ double mass_apply_cg(int m, int i, int j, double h2, const double *y, int node)
 {
     const int mc = m - 1;
+    if (i > 0 && j > 0 && i < mc && j < mc) {
+        // interior: six incident triangles (h^2/2 on the diagonal), every
+        // edge shared by two (h^2/12 each)
+        const double ye = __ldcg(y + node + 1), yw = __ldcg(y + node - 1), yn = __ldcg(y + node + m),
+                     ys = __ldcg(y + node - m), yne = __ldcg(y + node + m + 1), ysw = __ldcg(y + node - m - 1);
+        return (h2 / 2.0) * __ldcg(y + node) + (h2 / 12.0) * (((ye + yw) + (yn + ys)) + (yne + ysw));
+    }
     const bool cij = (i < mc && j < mc), cim = (i >= 1 && j < mc), cmm = (i >= 1 && j >= 1),
                cjm = (i < mc && j >= 1);
     const int ninc = 2 * cij + cim + 2 * cmm + cjm;
