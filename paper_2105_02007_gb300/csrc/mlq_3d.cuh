@@ -587,9 +587,9 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
     for (int step = 0; step < g.nsteps; ++step) {
         // the block starts from the extrapolation of order guess_order(step)
         // over v_n, v_{n-1}, ..., kept in the buffer of v_{n+1} (which held
-        // v_{n-3})
+        // v_{n-4})
         const double *vcur = vring(step);
-        const double *vm1 = vring(step - 1), *vm2 = vring(step - 2);
+        const double *vm1 = vring(step - 1), *vm2 = vring(step - 2), *vm3 = vring(step - 3);
         double *v = vring(step + 1);
         const int gp = guess_order(step);
         const double *wcur = wb0 + wpar * SN;
@@ -601,7 +601,8 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                 Vals<double, 3> o;
                 o.v[0] = vv + dt * (vv * (vv - g.a) * (1.0 - vv) - ww);
                 o.v[1] = ww + dt * g.eps * (vv - g.gam * ww);
-                o.v[2] = extrapolate(gp, vv, gp >= 1 ? vm1[P] : 0.0, gp >= 2 ? vm2[P] : 0.0, gp >= 3 ? v[P] : 0.0);
+                o.v[2] = extrapolate(gp, vv, gp >= 1 ? vm1[P] : 0.0, gp >= 2 ? vm2[P] : 0.0, gp >= 3 ? vm3[P] : 0.0,
+                                     gp >= 4 ? v[P] : 0.0);
                 return o;
             },
             [&](int P, const Vals<double, 3> &o) {

@@ -50,17 +50,24 @@ struct FastDiv {
 // rises by one every two blocks: the first blocks follow a discontinuous
 // initial state, and a stencil reaching back to it or to the first rough
 // solutions makes a worse guess than v_step itself.
-constexpr int kVRing = 4;
+constexpr int kVRing = 5;
+constexpr int kGuessOrderMax = kVRing - 1;
 
-__host__ __device__ inline int guess_order(int step) { return step < 3 ? 0 : ((step - 1) / 2 < 3 ? (step - 1) / 2 : 3); }
+__host__ __device__ inline int guess_order(int step)
+{
+    return step < 3 ? 0 : ((step - 1) / 2 < kGuessOrderMax ? (step - 1) / 2 : kGuessOrderMax);
+}
 
-__host__ __device__ inline double extrapolate(int p, double v0, double v1, double v2, double v3)
+// value at t_{n+1} of the polynomial of order p through v0 = v_n, v1 =
+// v_{n-1}, ... (binomial weights: the p+1-th difference vanishes)
+__host__ __device__ inline double extrapolate(int p, double v0, double v1, double v2, double v3, double v4)
 {
     switch (p) {
     case 0: return v0;
     case 1: return 2.0 * v0 - v1;
     case 2: return 3.0 * v0 - 3.0 * v1 + v2;
-    default: return 4.0 * v0 - 6.0 * v1 + 4.0 * v2 - v3;
+    case 3: return 4.0 * v0 - 6.0 * v1 + 4.0 * v2 - v3;
+    default: return 5.0 * v0 - 10.0 * v1 + 10.0 * v2 - 5.0 * v3 + v4;
     }
 }
 

@@ -544,8 +544,8 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1)
         const double *wcur = wb0 + wpar * SN;
         double *wnext = wb0 + (wpar ^ 1) * SN;
         const double *vcur = vring(step);
-        const double *vm1 = vring(step - 1), *vm2 = vring(step - 2);
-        double *v = vring(step + 1);   // holds v_{n-3} until the guess replaces it
+        const double *vm1 = vring(step - 1), *vm2 = vring(step - 2), *vm3 = vring(step - 3);
+        double *v = vring(step + 1);   // holds v_{n-4} until the guess replaces it
         const int gp = guess_order(step);
         // y = v + dt R(v, w) once per node (the mass product reads it at the
         // seven stencil points)
@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1)
             yb[node] = vv + dt * (vv * (vv - g.a) * (1.0 - vv) - ww);
             wnext[node] = ww + dt * g.eps * (vv - g.gam * ww);
             v[node] = extrapolate(gp, vv, gp >= 1 ? vm1[node] : 0.0, gp >= 2 ? vm2[node] : 0.0,
-                                  gp >= 3 ? v[node] : 0.0);
+                                  gp >= 3 ? vm3[node] : 0.0, gp >= 4 ? v[node] : 0.0);
         }
         cl.sync();
         {
