@@ -19,8 +19,8 @@
 // Solver (one sample per cluster of CS CTAs, everything in global memory and
 // L2; the 3D levels outgrow the shared memory of a cluster):
 //   per time block  y = v + dt R(v, w); b = M y; w <- w + dt eps (v - gam w);
-//                   r = b - A v in FP64 from the extrapolated guess
-//                   v = 2 v_n - v_{n-1}
+//                   r = b - A v in FP64 from the guess v extrapolated
+//                   from the last block solutions (guess_order)
 //   inner solve     Jacobi-preconditioned CG (Chronopoulos-Gear: one cluster
 //                   reduction per iteration) on A d = r / ||r|| from d = 0 in
 //                   the inner precision TI, v += ||r|| d; the mixed path
