@@ -669,11 +669,12 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
             }
             const double rnorm = sqrt(rnorm2);
             const TI rscale = (TI)(1.0 / rnorm);
-            // inner target relative to the normalised start: rtol_in, or what
-            // the outer test still needs when that is looser; the FP64 path
-            // solves to the outer target in this one sweep
+            // inner target relative to the normalised start: rtol_in, or half
+            // of what the outer test still needs when that is looser (the
+            // FP64 check after the sweep decides); the FP64 path solves to the
+            // outer target in this one sweep
             const double need = tol_out2 / rnorm2;
-            const double tol_in2 = mixed ? fmax(g.rtol_in * g.rtol_in, 0.0625 * need) : need;
+            const double tol_in2 = mixed ? fmax(g.rtol_in * g.rtol_in, 0.25 * need) : need;
 
             // init: r0 normalised, x = p = s = 0; u0 = D^-1 r0 (Jacobi) or the
             // multigrid's pre-smoothed XA_0 = omega D^-1 r0

@@ -607,9 +607,10 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1)
             if (rnorm2 <= tol_out2) { solved = true; break; }
             const double rnorm = sqrt(rnorm2);
             const float rscale = (float)(1.0 / rnorm);
-            // inner target: rtol_in, or a quarter of what the outer test still
-            // needs when that is looser (the last sweep of a block)
-            const double tol_in2 = fmax(g.rtol_in * g.rtol_in, 0.0625 * tol_out2 / rnorm2);
+            // inner target: rtol_in, or half of what the outer test still
+            // needs when that is looser (the last sweep of a block; the
+            // FP64 check after the sweep decides whether the block is done)
+            const double tol_in2 = fmax(g.rtol_in * g.rtol_in, 0.25 * tol_out2 / rnorm2);
 
             // ---- init: r0 (normalised), u0 = MG(r0), w0 = A u0
 #pragma unroll
