@@ -334,7 +334,7 @@ def run_case3d(spec: str):
 
 
 def run_c3(spec: str):
-    """The 3D MLQMC estimator end to end: --c3 [T=0.5][,K=64][,L=3].
+    """The 3D MLQMC estimator end to end: --c3 [T=10][,K=64][,L=3].
     Kuhn levels LEVEL3_DIMS[0..L], dt_l = 0.05 * 2^-l over [0, T]; KL modes of
     c = 0.09 exp(-|x-y|^2 / 0.15^2) on the finest mesh (K = 64 modes) transferred by
     the midpoint rule; per level 4^(L-l) lattice points (CBC generating
@@ -345,7 +345,7 @@ def run_c3(spec: str):
     import time
 
     kv = dict(item.split("=") for item in spec.split(",")) if spec else {}
-    T = float(kv.get("T", 0.5))
+    T = float(kv.get("T", 10.0))
     K = int(kv.get("K", 64))
     L = int(kv.get("L", 3))
     R = 16
@@ -379,7 +379,7 @@ def run_c3(spec: str):
     # MLQMC: per level the mean over the R shifts of the lattice means; the
     # error estimate from the spread over the shifts
     qmc_var = [float(np.var(np.asarray(y).reshape(R, -1).mean(axis=1), ddof=1) / R) for y in ys]
-    print(json.dumps({"c3": spec or "T=0.5", "levels": [list(d) for d in dims], "steps": steps,
+    print(json.dumps({"c3": spec or "T=10", "levels": [list(d) for d in dims], "steps": steps,
                       "solves": [len(x) for x in xis], "K": K, "seconds": sec, "dof_steps": dof,
                       "dof_steps_per_s": dof / sec, "estimate": mean, "rmse_qmc": float(sum(qmc_var) ** 0.5),
                       "host_kl_setup_s": setup_s}))
