@@ -13,10 +13,14 @@ ctypes loader, numpy wrappers and the estimators of Sec. 4:
   single level  QoI^SL_L = Q_L(F_L)                                   (eq. SL)
   multilevel    QoI^ML_L = sum_l Q_{L-l}(F_l - F_{l-1}), F_{-1} = 0   (eq. StandardML)
 
+  non-nested   QoI^ML_L = sum_l (Q_l - Q_{l-1})(F_{L-l}), Q_{-1} = 0     (eq. PimpedML)
+
 Parity status per function (each is pinned by ``tests/test_oracle_pins.py``
-unless noted):
+or, for the fibre frames, point location and eq. PimpedML,
+``tests/test_oracle_lv.py``):
   mesh2d, mesh3d, assemble, kl_build, centroid_table, solve, solve_batch,
-  mc_estimate, mlmc_estimate, qmc_estimate: pinned.
+  p1_at_points, centroid_table_unrelated, mc_estimate, mlmc_estimate,
+  qmc_estimate, pimped_ml_estimate: pinned.
 """
 from __future__ import annotations
 
@@ -73,6 +77,13 @@ def _load():
     lib.mlqo_solve_batch.argtypes = [c.c_int, c.c_int64, _f64p, c.c_int64, _i32p, c.c_int, _f64p, c.c_void_p,
                                      c.c_int64, _f64p, _f64p, c.c_double, c.c_int, c.c_double, c.c_int64,
                                      _f64p, c.c_void_p, c.c_int, _f64p, _i64p, _i32p]
+    lib.mlqo_assemble_f.argtypes = [c.c_int, c.c_int64, _f64p, c.c_int64, _i32p, c.c_void_p, c.c_void_p,
+                                    c.c_double, c.c_double, _i64p, _i32p, _f64p, _f64p]
+    lib.mlqo_solve_batch_f.argtypes = [c.c_int, c.c_int64, _f64p, c.c_int64, _i32p, c.c_void_p, c.c_int, _f64p,
+                                       c.c_void_p, c.c_int64, _f64p, _f64p, c.c_double, c.c_int, c.c_double,
+                                       c.c_int64, _f64p, c.c_void_p, c.c_int, _f64p, _i64p, _i32p]
+    lib.mlqo_p1_at_points.argtypes = [c.c_int, c.c_int64, _f64p, c.c_int64, _i32p, c.c_int, _f64p, c.c_int64,
+                                      _f64p, _f64p, c.c_void_p, c.c_void_p]
     lib.mlqo_max_threads.restype = c.c_int
     _lib = lib
     return lib
@@ -86,7 +97,8 @@ def max_threads() -> int:
 # meshes (Sec. 3.1)
 # --------------------------------------------------------------------------
 class Mesh:
-    """A structured simplicial mesh: dims, box lengths, nodes, elements."""
+    """A simplicial mesh: nodes and elements (dims and box lengths for the
+    structured meshes, zeros for an unstructured one)."""
 
     def __init__(self, dim, dims, lengths, xyz, conn):
         self.dim = dim
@@ -112,6 +124,15 @@ def mesh2d(m: int) -> Mesh:
     return Mesh(2, (m,), (1.0, 1.0), xy, conn)
 
 
+def unstructured_mesh(xyz: np.ndarray, conn: np.ndarray) -> Mesh:
+    """A mesh given by its nodes (n x dim) and simplices (n_e x (dim + 1))."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    d = xyz.shape[1]
+    assert conn.shape[1] == d + 1
+    return Mesh(d, (0,) * d, (0.0,) * d, xyz, conn)
+
+
 def mesh3d(mx: int, my: int, mz: int, lx: float = 1.0, ly: float = 1.0, lz: float = 0.25) -> Mesh:
     """Box [0,lx]x[0,ly]x[0,lz], mx*my*mz nodes, six Kuhn tetrahedra per cube."""
     xyz = np.zeros((mx * my * mz, 3))
@@ -123,9 +144,19 @@ def mesh3d(mx: int, my: int, mz: int, lx: float = 1.0, ly: float = 1.0, lz: floa
 # --------------------------------------------------------------------------
 # matrices (Sec. 3.1, eq. AdmV)
 # --------------------------------------------------------------------------
-def assemble(mesh: Mesh, theta=None, s_l: float = 1.0, s_t: float = 0.2):
+def _opt(a, shape=None):
+    if a is None:
+        return None, None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        assert a.shape == shape, (a.shape, shape)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def assemble(mesh: Mesh, theta=None, s_l: float = 1.0, s_t: float = 0.2, frames=None):
     """CSR (rp, ci, M values, K values) of the consistent mass matrix and the
-    stiffness matrix of D = s_t I + (s_l - s_t) f f^T, f = (cos t, sin t[, 0])."""
+    stiffness matrix of D = s_t I + (s_l - s_t) f f^T, f = cos t e1 + sin t e2
+    with (e1, e2) the element's frame (frames: n_e x 6) or the x-y axes."""
     lib = _load()
     nnz = lib.mlqo_pattern_nnz(mesh.dim, mesh.n, mesh.ne, mesh.conn)
     rp = np.zeros(mesh.n + 1, dtype=np.int64)
@@ -137,7 +168,9 @@ def assemble(mesh: Mesh, theta=None, s_l: float = 1.0, s_t: float = 0.2):
         th = np.ascontiguousarray(theta, dtype=np.float64)
         assert th.shape == (mesh.ne,)
     ptr = th.ctypes.data_as(ctypes.c_void_p) if th is not None else None
-    assert lib.mlqo_assemble(mesh.dim, mesh.n, mesh.xyz, mesh.ne, mesh.conn, ptr, s_l, s_t, rp, ci, mv, kv) == 0
+    fr, fptr = _opt(frames, (mesh.ne, 6))
+    assert lib.mlqo_assemble_f(mesh.dim, mesh.n, mesh.xyz, mesh.ne, mesh.conn, ptr, fptr, s_l, s_t, rp, ci, mv,
+                               kv) == 0
     return rp, ci, mv, kv
 
 
@@ -233,9 +266,10 @@ def solve(mesh: Mesh, theta, dt: float, nsteps: int, v0=None, w0=None, model=Non
 
 def solve_batch(mesh: Mesh, phi: np.ndarray, xi: np.ndarray, dt: float, nsteps: int, v0=None, w0=None,
                 theta_mean=None, model=None, rtol: float = 1e-13, maxit: int | None = None,
-                nthreads: int = 0):
-    """S samples: theta_e = theta_mean_e + sum_k phi[e,k] xi[s,k] (eq. KLlowrank).
-    Returns (Q[S], iters[S], status[S])."""
+                nthreads: int = 0, frames=None):
+    """S samples: theta_e = theta_mean_e + sum_k phi[e,k] xi[s,k] (eq. KLlowrank),
+    the fibre turned by theta_e in the plane of the element's frame (frames:
+    n_e x 6) or of the x-y axes.  Returns (Q[S], iters[S], status[S])."""
     lib = _load()
     xi = np.ascontiguousarray(xi, dtype=np.float64)
     S, K = xi.shape
@@ -249,12 +283,40 @@ def solve_batch(mesh: Mesh, phi: np.ndarray, xi: np.ndarray, dt: float, nsteps: 
     it = np.zeros(S, dtype=np.int64)
     st = np.zeros(S, dtype=np.int32)
     maxit = 10 * mesh.n if maxit is None else maxit
-    assert lib.mlqo_solve_batch(mesh.dim, mesh.n, mesh.xyz, mesh.ne, mesh.conn, K, np.ascontiguousarray(phi),
-                                tm.ctypes.data_as(ctypes.c_void_p) if tm is not None else None, S, xi,
-                                _model_vec(model), dt, nsteps, rtol, maxit, v0,
-                                w0a.ctypes.data_as(ctypes.c_void_p) if w0a is not None else None, nthreads,
-                                q, it, st) == 0
+    fr, fptr = _opt(frames, (mesh.ne, 6))
+    assert lib.mlqo_solve_batch_f(mesh.dim, mesh.n, mesh.xyz, mesh.ne, mesh.conn, fptr, K,
+                                  np.ascontiguousarray(phi, dtype=np.float64),
+                                  tm.ctypes.data_as(ctypes.c_void_p) if tm is not None else None, S, xi,
+                                  _model_vec(model), dt, nsteps, rtol, maxit, v0,
+                                  w0a.ctypes.data_as(ctypes.c_void_p) if w0a is not None else None, nthreads,
+                                  q, it, st) == 0
     return q, it, st
+
+
+def p1_at_points(mesh: Mesh, f: np.ndarray, pts: np.ndarray, return_location: bool = False):
+    """Values at points (np x dim) of the P1 interpolants on `mesh` of the
+    nodal fields f (n x K): the simplex containing a point, else (a point
+    outside the discretised domain) the nearby simplex whose smallest
+    barycentric coordinate is largest, extended linearly."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    if f.ndim == 1:
+        f = f[:, None]
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    K = f.shape[1]
+    out = np.zeros((pts.shape[0], K))
+    el = np.zeros(pts.shape[0], dtype=np.int32)
+    lm = np.zeros(pts.shape[0])
+    assert _load().mlqo_p1_at_points(mesh.dim, mesh.n, mesh.xyz, mesh.ne, mesh.conn, K, f, pts.shape[0], pts, out,
+                                     el.ctypes.data_as(ctypes.c_void_p), lm.ctypes.data_as(ctypes.c_void_p)) == 0
+    return (out, el, lm) if return_location else out
+
+
+def centroid_table_unrelated(fine: Mesh, modes_f: np.ndarray, coarse: Mesh) -> np.ndarray:
+    """Phi[e, k] = fine P1 interpolant of mode k at the centroid of element e
+    of an unrelated (non-nested) mesh: the intergrid transfer of Sec. 4 by
+    point location."""
+    cen = coarse.xyz[coarse.conn].mean(axis=1)
+    return p1_at_points(fine, modes_f, cen)
 
 
 # --------------------------------------------------------------------------
@@ -282,6 +344,21 @@ def mlmc_estimate(y_levels):
         var.append(v)
         mse += v / np.asarray(y).size
     return est, var, mse ** 0.5
+
+
+def pimped_ml_estimate(F_terms, N):
+    """eq. PimpedML with nested sample rules: sum_{l=0}^L (Q_l - Q_{l-1})(F_{L-l}),
+    Q_l the mean over the first N_l points (N_0 <= ... <= N_L), Q_{-1} = 0.
+    F_terms[l] holds F_{L-l} (the QoI on mesh L-l) at the first N_l points.
+    Each term needs one mesh only, so the meshes need not be nested."""
+    est = 0.0
+    for l, f in enumerate(F_terms):
+        f = np.asarray(f, dtype=np.float64)
+        assert f.size >= N[l]
+        est += float(np.sum(f[:N[l]]) / N[l])
+        if l > 0:
+            est -= float(np.sum(f[:N[l - 1]]) / N[l - 1])
+    return est
 
 
 def qmc_estimate(q_by_shift: np.ndarray):

@@ -21,6 +21,10 @@
  *     explicitly, so each block is an SPD solve
  *   - KL expansion by pivoted Cholesky + reduced eigenproblem   (Sec. 2.3, eqs. approxEig, redEig)
  *   - fine-to-coarse transfer of the field by the midpoint rule (Sec. 4, intergrid transfer)
+ *   - the same transfer between unrelated meshes: P1 values   (Sec. 4; non-nested meshes,
+ *     at the other mesh's centroids by point location           Sec. 5.4)
+ *   - fibres turning in the plane of a per-element frame       (eq. AdmV with a general
+ *     (e.g. the wall-tangent pair of a ventricle shell)          fibre direction)
  *
  * Storage is CSR with an explicit pattern; the linear solver is textbook
  * Jacobi-preconditioned CG.  Nothing is blocked, fused or reordered.
@@ -156,11 +160,17 @@ static double simplex_gradients(int d, const double *X, double *g)
     return d == 2 ? vol / 2.0 : vol / 6.0;
 }
 
-/* D = s_t I + (s_l - s_t) f f^T with f = (cos th, sin th[, 0]): eq. AdmV with
- * g = s_t and |V| = s_l (fibre rotated in the x-y plane). */
-static void conductivity(int d, double th, double s_l, double s_t, double *D)
+/* D = s_t I + (s_l - s_t) f f^T: eq. AdmV with g = s_t and |V| = s_l.  The
+ * unit fibre f = cos(th) e1 + sin(th) e2 turns by th in the plane of an
+ * orthonormal pair (e1, e2) given per element (frame = e1 then e2, 6 values;
+ * NULL: the x-y plane, f = (cos th, sin th[, 0])). */
+static void conductivity(int d, double th, const double *frame, double s_l, double s_t, double *D)
 {
     double f[3] = {cos(th), sin(th), 0.0};
+    if (frame) {
+        const double c = cos(th), s = sin(th);
+        for (int r = 0; r < 3; ++r) f[r] = c * frame[r] + s * frame[3 + r];
+    }
     for (int r = 0; r < d; ++r)
         for (int c = 0; c < d; ++c) D[r * d + c] = (r == c ? s_t : 0.0) + (s_l - s_t) * f[r] * f[c];
 }
@@ -265,7 +275,7 @@ static int64_t find_col(const pattern_t *P, int64_t i, int32_t j)
 /* Assemble M and K(theta) (theta per element; NULL means theta = 0) into the
  * pattern's value arrays. */
 static void assemble(int d, const double *xyz, int64_t ne, const int32_t *conn, const double *theta,
-                     double s_l, double s_t, const pattern_t *P, double *mval, double *kval)
+                     const double *frames, double s_l, double s_t, const pattern_t *P, double *mval, double *kval)
 {
     int nv = d + 1;
     if (mval) memset(mval, 0, sizeof(double) * (size_t)P->nnz);
@@ -274,7 +284,7 @@ static void assemble(int d, const double *xyz, int64_t ne, const int32_t *conn, 
         double X[12], D[9], Ke[16], Me[16];
         for (int a = 0; a < nv; ++a)
             for (int c = 0; c < d; ++c) X[a * d + c] = xyz[(int64_t)conn[e * nv + a] * d + c];
-        conductivity(d, theta ? theta[e] : 0.0, s_l, s_t, D);
+        conductivity(d, theta ? theta[e] : 0.0, frames ? frames + e * 6 : NULL, s_l, s_t, D);
         element_matrices(d, X, D, Ke, Me);
         for (int a = 0; a < nv; ++a)
             for (int b = 0; b < nv; ++b) {
@@ -295,17 +305,195 @@ int64_t mlqo_pattern_nnz(int d, int64_t n, int64_t ne, const int32_t *conn)
     return nnz;
 }
 
-/* Public: CSR of M and K(theta).  rp has n+1 entries, ci/mval/kval nnz. */
-int mlqo_assemble(int d, int64_t n, const double *xyz, int64_t ne, const int32_t *conn, const double *theta,
-                  double s_l, double s_t, int64_t *rp, int32_t *ci, double *mval, double *kval)
+/* Public: CSR of M and K(theta) with fibre frames (NULL: the x-y plane).
+ * rp has n+1 entries, ci/mval/kval nnz. */
+int mlqo_assemble_f(int d, int64_t n, const double *xyz, int64_t ne, const int32_t *conn, const double *theta,
+                    const double *frames, double s_l, double s_t, int64_t *rp, int32_t *ci, double *mval,
+                    double *kval)
 {
     pattern_t P;
     int st = build_pattern(d, n, ne, conn, &P);
     if (st != MLQO_OK) return st;
-    assemble(d, xyz, ne, conn, theta, s_l, s_t, &P, mval, kval);
+    assemble(d, xyz, ne, conn, theta, frames, s_l, s_t, &P, mval, kval);
     memcpy(rp, P.rp, sizeof(int64_t) * (size_t)(n + 1));
     memcpy(ci, P.ci, sizeof(int32_t) * (size_t)P.nnz);
     free_pattern(&P);
+    return MLQO_OK;
+}
+
+/* Public: CSR of M and K(theta), fibres in the x-y plane. */
+int mlqo_assemble(int d, int64_t n, const double *xyz, int64_t ne, const int32_t *conn, const double *theta,
+                  double s_l, double s_t, int64_t *rp, int32_t *ci, double *mval, double *kval)
+{
+    return mlqo_assemble_f(d, n, xyz, ne, conn, theta, NULL, s_l, s_t, rp, ci, mval, kval);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Transfer between unrelated meshes (Sec. 4, intergrid transfer; non-nested */
+/* levels of Sec. 5.4): the P1 interpolant of nodal fields at points.        */
+/* ------------------------------------------------------------------------ */
+
+/* Barycentric coordinates of point x in simplex e (d+1 values). */
+static void barycentric(int d, const double *xyz, const int32_t *conn, int64_t e, const double *x, double *lam)
+{
+    int nv = d + 1;
+    double X0[3], A[9];
+    for (int c = 0; c < d; ++c) X0[c] = xyz[(int64_t)conn[e * nv] * d + c];
+    /* columns of A: X_a - X_0, a = 1..d */
+    for (int a = 1; a <= d; ++a)
+        for (int c = 0; c < d; ++c) A[c * d + (a - 1)] = xyz[(int64_t)conn[e * nv + a] * d + c] - X0[c];
+    double r[3];
+    for (int c = 0; c < d; ++c) r[c] = x[c] - X0[c];
+    /* solve A l = r by Cramer's rule */
+    double det, l[3];
+    if (d == 2) {
+        det = A[0] * A[3] - A[1] * A[2];
+        l[0] = (r[0] * A[3] - A[1] * r[1]) / det;
+        l[1] = (A[0] * r[1] - r[0] * A[2]) / det;
+    } else {
+        det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) + A[2] * (A[3] * A[7] - A[4] * A[6]);
+        for (int col = 0; col < 3; ++col) {
+            double B[9];
+            memcpy(B, A, sizeof(B));
+            for (int c = 0; c < 3; ++c) B[c * 3 + col] = r[c];
+            l[col] = (B[0] * (B[4] * B[8] - B[5] * B[7]) - B[1] * (B[3] * B[8] - B[5] * B[6]) +
+                      B[2] * (B[3] * B[7] - B[4] * B[6])) / det;
+        }
+    }
+    double s = 0.0;
+    for (int a = 0; a < d; ++a) { lam[a + 1] = l[a]; s += l[a]; }
+    lam[0] = 1.0 - s;
+}
+
+/* Public: out[p, k] = sum_a lambda_a f[node_a, k] for the simplex that
+ * contains point p (the first in element order when p lies on a shared
+ * face).  A point outside the mesh (a centroid of another mesh of a curved
+ * domain) takes the simplex among those near it whose smallest barycentric
+ * coordinate is largest, and the linear extension of its P1 function.
+ * Search: a uniform grid of buckets over the node bounding box, each bucket
+ * listing (in element order) the simplices whose bounding box meets it;
+ * rings of buckets around the point's bucket are scanned until a simplex
+ * contains the point, or one ring past the first ring with candidates.
+ * elem_out / lam_min_out (may be NULL): the simplex used and its smallest
+ * barycentric coordinate. */
+int mlqo_p1_at_points(int d, int64_t n, const double *xyz, int64_t ne, const int32_t *conn, int K, const double *f,
+                      int64_t np, const double *pts, double *out, int32_t *elem_out, double *lam_min_out)
+{
+    if ((d != 2 && d != 3) || n < 1 || ne < 1 || K < 0) return MLQO_EINVAL;
+    int nv = d + 1;
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int c = 0; c < d; ++c) lo[c] = hi[c] = xyz[c];
+    for (int64_t i = 0; i < n; ++i)
+        for (int c = 0; c < d; ++c) {
+            double v = xyz[i * d + c];
+            if (v < lo[c]) lo[c] = v;
+            if (v > hi[c]) hi[c] = v;
+        }
+    int nb = (int)ceil(pow((double)ne / 4.0, 1.0 / d));
+    if (nb < 1) nb = 1;
+    if (nb > 1024) nb = 1024;
+    double w[3];
+    for (int c = 0; c < d; ++c) w[c] = (hi[c] - lo[c]) / nb > 0 ? (hi[c] - lo[c]) / nb : 1.0;
+    int64_t nbuck = 1;
+    for (int c = 0; c < d; ++c) nbuck *= nb;
+    int64_t *cnt = calloc((size_t)nbuck + 1, sizeof(int64_t));
+    if (!cnt) return MLQO_ENOMEM;
+    int ib[3][2];
+    /* two passes: count, then fill (element order within each bucket) */
+    int32_t *list = NULL;
+    int64_t *fillp = NULL;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int64_t e = 0; e < ne; ++e) {
+            for (int c = 0; c < d; ++c) {
+                double a = xyz[(int64_t)conn[e * nv] * d + c], b = a;
+                for (int q = 1; q < nv; ++q) {
+                    double v = xyz[(int64_t)conn[e * nv + q] * d + c];
+                    if (v < a) a = v;
+                    if (v > b) b = v;
+                }
+                int i0 = (int)floor((a - lo[c]) / w[c]), i1 = (int)floor((b - lo[c]) / w[c]);
+                ib[c][0] = i0 < 0 ? 0 : (i0 >= nb ? nb - 1 : i0);
+                ib[c][1] = i1 < 0 ? 0 : (i1 >= nb ? nb - 1 : i1);
+            }
+            int kz0 = d == 3 ? ib[2][0] : 0, kz1 = d == 3 ? ib[2][1] : 0;
+            for (int kz = kz0; kz <= kz1; ++kz)
+                for (int ky = ib[1][0]; ky <= ib[1][1]; ++ky)
+                    for (int kx = ib[0][0]; kx <= ib[0][1]; ++kx) {
+                        int64_t bkt = kx + (int64_t)nb * (ky + (int64_t)nb * kz);
+                        if (pass == 0) cnt[bkt + 1]++;
+                        else list[fillp[bkt]++] = (int32_t)e;
+                    }
+        }
+        if (pass == 0) {
+            for (int64_t b = 0; b < nbuck; ++b) cnt[b + 1] += cnt[b];
+            list = malloc(sizeof(int32_t) * (size_t)(cnt[nbuck] > 0 ? cnt[nbuck] : 1));
+            fillp = malloc(sizeof(int64_t) * (size_t)nbuck);
+            if (!list || !fillp) { free(cnt); free(list); free(fillp); return MLQO_ENOMEM; }
+            for (int64_t b = 0; b < nbuck; ++b) fillp[b] = cnt[b];
+        }
+    }
+    free(fillp);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 256)
+#endif
+    for (int64_t p = 0; p < np; ++p) {
+        const double *x = pts + p * d;
+        int home[3] = {0, 0, 0};
+        for (int c = 0; c < d; ++c) {
+            int i = (int)floor((x[c] - lo[c]) / w[c]);
+            home[c] = i < 0 ? 0 : (i >= nb ? nb - 1 : i);
+        }
+        int64_t best = -1;
+        double best_min = -INFINITY, best_lam[4] = {0, 0, 0, 0};
+        int found = 0, seen_at = -1;
+        for (int rad = 0; rad <= nb && !found; ++rad) {
+            if (seen_at >= 0 && rad > seen_at + 1) break;
+            int z0 = d == 3 ? home[2] - rad : 0, z1 = d == 3 ? home[2] + rad : 0;
+            for (int kz = z0; kz <= z1 && !found; ++kz)
+                for (int ky = home[1] - rad; ky <= home[1] + rad && !found; ++ky)
+                    for (int kx = home[0] - rad; kx <= home[0] + rad && !found; ++kx) {
+                        if (kx < 0 || ky < 0 || kz < 0 || kx >= nb || ky >= nb || kz >= nb) continue;
+                        int ring = abs(kx - home[0]);
+                        if (abs(ky - home[1]) > ring) ring = abs(ky - home[1]);
+                        if (d == 3 && abs(kz - home[2]) > ring) ring = abs(kz - home[2]);
+                        if (ring != rad) continue;   /* only the shell of this radius */
+                        int64_t bkt = kx + (int64_t)nb * (ky + (int64_t)nb * kz);
+                        for (int64_t t = cnt[bkt]; t < cnt[bkt + 1]; ++t) {
+                            int64_t e = list[t];
+                            double lam[4];
+                            barycentric(d, xyz, conn, e, x, lam);
+                            double mn = lam[0];
+                            for (int a = 1; a < nv; ++a) if (lam[a] < mn) mn = lam[a];
+                            if (seen_at < 0) seen_at = rad;
+                            if (mn > best_min || (mn == best_min && e < best)) {
+                                best_min = mn;
+                                best = e;
+                                memcpy(best_lam, lam, sizeof(lam));
+                            }
+                            if (mn >= -1e-12) {
+                                /* contained; every simplex containing the point is listed in
+                                 * its own bucket (rad 0) in element order, so this is the
+                                 * first of them */
+                                best = e;
+                                best_min = mn;
+                                memcpy(best_lam, lam, sizeof(lam));
+                                found = 1;
+                                break;
+                            }
+                        }
+                    }
+        }
+        if (elem_out) elem_out[p] = (int32_t)best;
+        if (lam_min_out) lam_min_out[p] = best_min;
+        for (int k = 0; k < K; ++k) {
+            double v = 0.0;
+            if (best >= 0)
+                for (int a = 0; a < nv; ++a) v += best_lam[a] * f[(int64_t)conn[best * nv + a] * K + k];
+            out[p * K + k] = v;
+        }
+    }
+    free(cnt);
+    free(list);
     return MLQO_OK;
 }
 
@@ -415,7 +603,7 @@ int mlqo_kl_build(int d, int64_t n, const double *xyz, int64_t ne, const int32_t
         free(L); free(mval); free(ML); free(B); free(lam); free(V); free_pattern(&P);
         return MLQO_ENOMEM;
     }
-    assemble(d, xyz, ne, conn, NULL, 1.0, 1.0, &P, mval, NULL);
+    assemble(d, xyz, ne, conn, NULL, NULL, 1.0, 1.0, &P, mval, NULL);
     for (int64_t i = 0; i < n; ++i)
         for (int64_t t = P.rp[i]; t < P.rp[i + 1]; ++t)
             for (int k = 0; k < K; ++k) ML[i * K + k] += mval[t] * L[(int64_t)P.ci[t] * K + k];
@@ -628,7 +816,7 @@ static int problem_setup(int d, int64_t n, const double *xyz, int64_t ne, const 
     pr->mval = malloc(sizeof(double) * nnz);
     pr->mlump = malloc(sizeof(double) * (size_t)n);
     if (!pr->mval || !pr->mlump) return MLQO_ENOMEM;
-    assemble(d, xyz, ne, conn, NULL, 1.0, 1.0, &pr->P, pr->mval, NULL);
+    assemble(d, xyz, ne, conn, NULL, NULL, 1.0, 1.0, &pr->P, pr->mval, NULL);
     for (int64_t i = 0; i < n; ++i) {
         double s = 0.0;
         for (int64_t t = pr->P.rp[i]; t < pr->P.rp[i + 1]; ++t) s += pr->mval[t];
@@ -646,7 +834,8 @@ static void problem_free(problem_t *pr)
 }
 
 static double solve_one(int d, const double *xyz, const int32_t *conn, const problem_t *pr,
-                        const double *theta, const double *model, double dt, int nsteps, double rtol,
+                        const double *theta, const double *frames, const double *model, double dt, int nsteps,
+                        double rtol,
                         int64_t maxit, double *v, double *w, int64_t *iters_out, int *status_out)
 {
     const pattern_t *P = &pr->P;
@@ -659,7 +848,7 @@ static double solve_one(int d, const double *xyz, const int32_t *conn, const pro
     double *x = malloc(sizeof(double) * (size_t)n), *r = malloc(sizeof(double) * (size_t)n);
     double *z = malloc(sizeof(double) * (size_t)n), *p = malloc(sizeof(double) * (size_t)n);
     double *q = malloc(sizeof(double) * (size_t)n);
-    assemble(d, xyz, pr->ne, conn, theta, s_l, s_t, P, NULL, kval);
+    assemble(d, xyz, pr->ne, conn, theta, frames, s_l, s_t, P, NULL, kval);
     for (int64_t t = 0; t < nnz; ++t) aval[t] = pr->mval[t] + dt * kval[t];
     for (int64_t i = 0; i < n; ++i) dinv[i] = 1.0 / aval[find_col(P, i, (int32_t)i)];
     int64_t iters = 0;
@@ -698,7 +887,7 @@ int mlqo_solve(int d, int64_t n, const double *xyz, int64_t ne, const int32_t *c
     int st = problem_setup(d, n, xyz, ne, conn, &pr);
     if (st != MLQO_OK) { problem_free(&pr); return st; }
     int s;
-    *q_out = solve_one(d, xyz, conn, &pr, theta, model, dt, nsteps, rtol, maxit, v, w, iters_out, &s);
+    *q_out = solve_one(d, xyz, conn, &pr, theta, NULL, model, dt, nsteps, rtol, maxit, v, w, iters_out, &s);
     if (status_out) *status_out = s;
     problem_free(&pr);
     return MLQO_OK;
@@ -706,13 +895,14 @@ int mlqo_solve(int d, int64_t n, const double *xyz, int64_t ne, const int32_t *c
 
 /* Public: a batch of S samples.  Sample s uses the angle field
  *   theta_e = theta_mean_e + sum_k phi[e*K+k] * xi[s*K+k]     (eq. KLlowrank)
- * and the initial state v0, w0 (w0 may be NULL = 0).  Samples run in
- * parallel over nthreads OpenMP threads (<= 0: the runtime default).
- * q_out[s], iters[s] (may be NULL), status[s] (may be NULL). */
-int mlqo_solve_batch(int d, int64_t n, const double *xyz, int64_t ne, const int32_t *conn, int K,
-                     const double *phi, const double *theta_mean, int64_t S, const double *xi,
-                     const double *model, double dt, int nsteps, double rtol, int64_t maxit, const double *v0,
-                     const double *w0, int nthreads, double *q_out, int64_t *iters, int32_t *status)
+ * turning the fibre in the plane of the element's frame (frames: n_e x 6, or
+ * NULL for the x-y plane), and the initial state v0, w0 (w0 may be NULL = 0).
+ * Samples run in parallel over nthreads OpenMP threads (<= 0: the runtime
+ * default).  q_out[s], iters[s] (may be NULL), status[s] (may be NULL). */
+int mlqo_solve_batch_f(int d, int64_t n, const double *xyz, int64_t ne, const int32_t *conn, const double *frames,
+                       int K, const double *phi, const double *theta_mean, int64_t S, const double *xi,
+                       const double *model, double dt, int nsteps, double rtol, int64_t maxit, const double *v0,
+                       const double *w0, int nthreads, double *q_out, int64_t *iters, int32_t *status)
 {
     problem_t pr;
     int st = problem_setup(d, n, xyz, ne, conn, &pr);
@@ -732,13 +922,23 @@ int mlqo_solve_batch(int d, int64_t n, const double *xyz, int64_t ne, const int3
         for (int64_t i = 0; i < n; ++i) { v[i] = v0[i]; w[i] = w0 ? w0[i] : 0.0; }
         int64_t it = 0;
         int sst = 0;
-        q_out[s] = solve_one(d, xyz, conn, &pr, theta, model, dt, nsteps, rtol, maxit, v, w, &it, &sst);
+        q_out[s] = solve_one(d, xyz, conn, &pr, theta, frames, model, dt, nsteps, rtol, maxit, v, w, &it, &sst);
         if (iters) iters[s] = it;
         if (status) status[s] = sst;
         free(theta); free(v); free(w);
     }
     problem_free(&pr);
     return MLQO_OK;
+}
+
+/* Public: the batch with fibres in the x-y plane. */
+int mlqo_solve_batch(int d, int64_t n, const double *xyz, int64_t ne, const int32_t *conn, int K,
+                     const double *phi, const double *theta_mean, int64_t S, const double *xi,
+                     const double *model, double dt, int nsteps, double rtol, int64_t maxit, const double *v0,
+                     const double *w0, int nthreads, double *q_out, int64_t *iters, int32_t *status)
+{
+    return mlqo_solve_batch_f(d, n, xyz, ne, conn, NULL, K, phi, theta_mean, S, xi, model, dt, nsteps, rtol, maxit,
+                              v0, w0, nthreads, q_out, iters, status);
 }
 
 /* Public: number of OpenMP threads a parallel region would use. */
