@@ -177,6 +177,29 @@ int mlq_build_kl(int dim, const int32_t *dims, const double *lengths, double sig
 int mlq_centroid_table(int dim, const int32_t *fine_dims, const double *modes_f, int K,
                        const int32_t *coarse_dims, double *phi_out);
 
+/* Host helper: KL modes (as mlq_build_kl, eqs. approxEig and redEig) on a
+ * general simplicial mesh: xyz host, n x dim node coordinates; conn host,
+ * ne x (dim + 1) node indices (0-based, each < n) of triangles (dim 2) or
+ * tetrahedra (dim 3).  The P1 mass matrix is assembled from the simplices
+ * (|e| (1 + delta_ab) / ((dim + 1)(dim + 2)) per simplex).  modes_out: host,
+ * n x K; lambda_out: host, K, descending.  MLQ_EINVAL for a bad mesh or K
+ * outside 1 .. min(n, 4096). */
+int mlq_build_kl_mesh(int dim, int64_t n, const double *xyz, int64_t ne, const int32_t *conn, double sigma2,
+                      double ell, int K, double *modes_out, double *lambda_out);
+
+/* Host helper: values at np points (pts host, np x dim) of the P1
+ * interpolants of K nodal fields (f host, n x K) on a general simplicial
+ * mesh (xyz, conn as in mlq_build_kl_mesh): the intergrid transfer of Sec. 4
+ * between meshes that are not nested (Sec. 5.4), e.g. phi_out of a level =
+ * the finest-mesh modes at that level's element centroids.  A point takes
+ * the first simplex (in element order) that contains it; a point in no
+ * simplex (a centroid near a curved boundary discretised differently) takes
+ * the first simplex whose smallest barycentric coordinate is within 1e-12 of
+ * the largest over all simplices, and the linear extension of its P1
+ * function.  out: host, np x K. */
+int mlq_p1_at_points(int dim, int64_t n, const double *xyz, int64_t ne, const int32_t *conn, int K, const double *f,
+                     int64_t np, const double *pts, double *out);
+
 /* Solve S samples (0 <= S <= 65535) on `level`.  xi: host or device, S x K row-major FP64
  * (sample s uses xi[s*K .. s*K+K-1]).  For each sample: synthesise theta
  * (eq. KLlowrank), set up A = M + dt K(theta), run the nsteps time blocks,

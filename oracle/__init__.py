@@ -295,9 +295,10 @@ def solve_batch(mesh: Mesh, phi: np.ndarray, xi: np.ndarray, dt: float, nsteps: 
 
 def p1_at_points(mesh: Mesh, f: np.ndarray, pts: np.ndarray, return_location: bool = False):
     """Values at points (np x dim) of the P1 interpolants on `mesh` of the
-    nodal fields f (n x K): the simplex containing a point, else (a point
-    outside the discretised domain) the nearby simplex whose smallest
-    barycentric coordinate is largest, extended linearly."""
+    nodal fields f (n x K): the first simplex containing a point, else (a
+    point outside the discretised domain) the first simplex whose smallest
+    barycentric coordinate is within 1e-12 of the largest, extended
+    linearly."""
     f = np.ascontiguousarray(f, dtype=np.float64)
     if f.ndim == 1:
         f = f[:, None]

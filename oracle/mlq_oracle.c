@@ -367,15 +367,15 @@ static void barycentric(int d, const double *xyz, const int32_t *conn, int64_t e
 
 /* Public: out[p, k] = sum_a lambda_a f[node_a, k] for the simplex that
  * contains point p (the first in element order when p lies on a shared
- * face).  A point outside the mesh (a centroid of another mesh of a curved
- * domain) takes the simplex among those near it whose smallest barycentric
- * coordinate is largest, and the linear extension of its P1 function.
- * Search: a uniform grid of buckets over the node bounding box, each bucket
- * listing (in element order) the simplices whose bounding box meets it;
- * rings of buckets around the point's bucket are scanned until a simplex
- * contains the point, or one ring past the first ring with candidates.
- * elem_out / lam_min_out (may be NULL): the simplex used and its smallest
- * barycentric coordinate. */
+ * face).  A point in no simplex (a centroid of another mesh of a curved
+ * domain that falls outside this discretisation) takes, over all simplices,
+ * the first (in element order) whose smallest barycentric coordinate is
+ * within 1e-12 of the largest, and the linear extension of its P1 function.
+ * Containing simplices are found through a uniform grid of buckets over the
+ * node bounding box, each bucket listing (in element order) the simplices
+ * whose bounding box meets it: a simplex that contains p is listed in p's
+ * bucket.  elem_out / lam_min_out (may be NULL): the simplex used and its
+ * smallest barycentric coordinate. */
 int mlqo_p1_at_points(int d, int64_t n, const double *xyz, int64_t ne, const int32_t *conn, int K, const double *f,
                       int64_t np, const double *pts, double *out, int32_t *elem_out, double *lam_min_out)
 {
@@ -392,18 +392,18 @@ int mlqo_p1_at_points(int d, int64_t n, const double *xyz, int64_t ne, const int
     int nb = (int)ceil(pow((double)ne / 4.0, 1.0 / d));
     if (nb < 1) nb = 1;
     if (nb > 1024) nb = 1024;
-    double w[3];
+    double w[3] = {1.0, 1.0, 1.0};
     for (int c = 0; c < d; ++c) w[c] = (hi[c] - lo[c]) / nb > 0 ? (hi[c] - lo[c]) / nb : 1.0;
     int64_t nbuck = 1;
     for (int c = 0; c < d; ++c) nbuck *= nb;
     int64_t *cnt = calloc((size_t)nbuck + 1, sizeof(int64_t));
     if (!cnt) return MLQO_ENOMEM;
-    int ib[3][2];
-    /* two passes: count, then fill (element order within each bucket) */
     int32_t *list = NULL;
     int64_t *fillp = NULL;
+    /* two passes: count, then fill (element order within each bucket) */
     for (int pass = 0; pass < 2; ++pass) {
         for (int64_t e = 0; e < ne; ++e) {
+            int ib[3][2] = {{0, 0}, {0, 0}, {0, 0}};
             for (int c = 0; c < d; ++c) {
                 double a = xyz[(int64_t)conn[e * nv] * d + c], b = a;
                 for (int q = 1; q < nv; ++q) {
@@ -415,8 +415,7 @@ int mlqo_p1_at_points(int d, int64_t n, const double *xyz, int64_t ne, const int
                 ib[c][0] = i0 < 0 ? 0 : (i0 >= nb ? nb - 1 : i0);
                 ib[c][1] = i1 < 0 ? 0 : (i1 >= nb ? nb - 1 : i1);
             }
-            int kz0 = d == 3 ? ib[2][0] : 0, kz1 = d == 3 ? ib[2][1] : 0;
-            for (int kz = kz0; kz <= kz1; ++kz)
+            for (int kz = ib[2][0]; kz <= ib[2][1]; ++kz)
                 for (int ky = ib[1][0]; ky <= ib[1][1]; ++ky)
                     for (int kx = ib[0][0]; kx <= ib[0][1]; ++kx) {
                         int64_t bkt = kx + (int64_t)nb * (ky + (int64_t)nb * kz);
@@ -438,57 +437,55 @@ int mlqo_p1_at_points(int d, int64_t n, const double *xyz, int64_t ne, const int
 #endif
     for (int64_t p = 0; p < np; ++p) {
         const double *x = pts + p * d;
-        int home[3] = {0, 0, 0};
+        int64_t home = 0, stride = 1;
         for (int c = 0; c < d; ++c) {
             int i = (int)floor((x[c] - lo[c]) / w[c]);
-            home[c] = i < 0 ? 0 : (i >= nb ? nb - 1 : i);
+            i = i < 0 ? 0 : (i >= nb ? nb - 1 : i);
+            home += i * stride;
+            stride *= nb;
         }
         int64_t best = -1;
-        double best_min = -INFINITY, best_lam[4] = {0, 0, 0, 0};
-        int found = 0, seen_at = -1;
-        for (int rad = 0; rad <= nb && !found; ++rad) {
-            if (seen_at >= 0 && rad > seen_at + 1) break;
-            int z0 = d == 3 ? home[2] - rad : 0, z1 = d == 3 ? home[2] + rad : 0;
-            for (int kz = z0; kz <= z1 && !found; ++kz)
-                for (int ky = home[1] - rad; ky <= home[1] + rad && !found; ++ky)
-                    for (int kx = home[0] - rad; kx <= home[0] + rad && !found; ++kx) {
-                        if (kx < 0 || ky < 0 || kz < 0 || kx >= nb || ky >= nb || kz >= nb) continue;
-                        int ring = abs(kx - home[0]);
-                        if (abs(ky - home[1]) > ring) ring = abs(ky - home[1]);
-                        if (d == 3 && abs(kz - home[2]) > ring) ring = abs(kz - home[2]);
-                        if (ring != rad) continue;   /* only the shell of this radius */
-                        int64_t bkt = kx + (int64_t)nb * (ky + (int64_t)nb * kz);
-                        for (int64_t t = cnt[bkt]; t < cnt[bkt + 1]; ++t) {
-                            int64_t e = list[t];
-                            double lam[4];
-                            barycentric(d, xyz, conn, e, x, lam);
-                            double mn = lam[0];
-                            for (int a = 1; a < nv; ++a) if (lam[a] < mn) mn = lam[a];
-                            if (seen_at < 0) seen_at = rad;
-                            if (mn > best_min || (mn == best_min && e < best)) {
-                                best_min = mn;
-                                best = e;
-                                memcpy(best_lam, lam, sizeof(lam));
-                            }
-                            if (mn >= -1e-12) {
-                                /* contained; every simplex containing the point is listed in
-                                 * its own bucket (rad 0) in element order, so this is the
-                                 * first of them */
-                                best = e;
-                                best_min = mn;
-                                memcpy(best_lam, lam, sizeof(lam));
-                                found = 1;
-                                break;
-                            }
-                        }
-                    }
+        double best_min = -INFINITY, best_lam[4] = {0, 0, 0, 0}, lam[4];
+        for (int64_t t = cnt[home]; t < cnt[home + 1]; ++t) {
+            int64_t e = list[t];
+            barycentric(d, xyz, conn, e, x, lam);
+            double mn = lam[0];
+            for (int a = 1; a < nv; ++a) if (lam[a] < mn) mn = lam[a];
+            if (mn >= -1e-12) {
+                best = e;
+                best_min = mn;
+                memcpy(best_lam, lam, sizeof(lam));
+                break;
+            }
+        }
+        if (best < 0) {
+            /* in no simplex: over all of them the largest smallest coordinate,
+             * then the first simplex within 1e-12 of it (near-ties, e.g. beyond
+             * a boundary vertex shared by several simplices, go to the lowest
+             * index whatever the rounding) */
+            for (int64_t e = 0; e < ne; ++e) {
+                barycentric(d, xyz, conn, e, x, lam);
+                double mn = lam[0];
+                for (int a = 1; a < nv; ++a) if (lam[a] < mn) mn = lam[a];
+                if (mn > best_min) best_min = mn;
+            }
+            for (int64_t e = 0; e < ne; ++e) {
+                barycentric(d, xyz, conn, e, x, lam);
+                double mn = lam[0];
+                for (int a = 1; a < nv; ++a) if (lam[a] < mn) mn = lam[a];
+                if (mn >= best_min - 1e-12) {
+                    best = e;
+                    best_min = mn;
+                    memcpy(best_lam, lam, sizeof(lam));
+                    break;
+                }
+            }
         }
         if (elem_out) elem_out[p] = (int32_t)best;
         if (lam_min_out) lam_min_out[p] = best_min;
         for (int k = 0; k < K; ++k) {
             double v = 0.0;
-            if (best >= 0)
-                for (int a = 0; a < nv; ++a) v += best_lam[a] * f[(int64_t)conn[best * nv + a] * K + k];
+            for (int a = 0; a < nv; ++a) v += best_lam[a] * f[(int64_t)conn[best * nv + a] * K + k];
             out[p * K + k] = v;
         }
     }

@@ -7,8 +7,10 @@
 #include "mlq.h"
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
+#include <cstring>
 #include <cstdint>
 #include <new>
 #include <thread>
@@ -328,6 +330,215 @@ int build_kl_nodes(int64_t n, Coord coord, Mass mass, double sigma2, double ell,
     return MLQ_OK;
 }
 
+// General simplicial mesh (triangles or tetrahedra given by node lists).
+struct SimplexMesh {
+    int d;
+    int64_t n, ne;
+    const double *xyz;     // n x d
+    const int32_t *conn;   // ne x (d + 1)
+};
+
+// |e|: the simplex measure (area or volume) from the edge vectors
+double simplex_measure(const SimplexMesh &m, int64_t e)
+{
+    const int nv = m.d + 1;
+    const double *p0 = m.xyz + (int64_t)m.conn[e * nv] * m.d;
+    double E[3][3] = {};
+    for (int a = 1; a < nv; ++a)
+        for (int c = 0; c < m.d; ++c) E[a - 1][c] = m.xyz[(int64_t)m.conn[e * nv + a] * m.d + c] - p0[c];
+    if (m.d == 2) return 0.5 * std::fabs(E[0][0] * E[1][1] - E[0][1] * E[1][0]);
+    const double cx = E[1][1] * E[2][2] - E[1][2] * E[2][1], cy = E[1][2] * E[2][0] - E[1][0] * E[2][2],
+                 cz = E[1][0] * E[2][1] - E[1][1] * E[2][0];
+    return std::fabs(E[0][0] * cx + E[0][1] * cy + E[0][2] * cz) / 6.0;
+}
+
+// Simplices at each node, in element order (CSR: start[n + 1], list)
+void node_incidence(const SimplexMesh &m, std::vector<int64_t> &start, std::vector<int32_t> &list)
+{
+    const int nv = m.d + 1;
+    start.assign((size_t)m.n + 1, 0);
+    for (int64_t e = 0; e < m.ne; ++e)
+        for (int a = 0; a < nv; ++a) ++start[(size_t)m.conn[e * nv + a] + 1];
+    for (int64_t i = 0; i < m.n; ++i) start[(size_t)i + 1] += start[(size_t)i];
+    list.resize((size_t)start[(size_t)m.n]);
+    std::vector<int64_t> fill(start.begin(), start.end() - 1);
+    for (int64_t e = 0; e < m.ne; ++e)
+        for (int a = 0; a < nv; ++a) list[(size_t)fill[(size_t)m.conn[e * nv + a]]++] = (int32_t)e;
+}
+
+// y = M x for the P1 mass matrix, M_e = |e| (1 + delta_ab) / ((d + 1)(d + 2)),
+// gathered per node: (M x)_i = sum over e at i of |e| / ((d+1)(d+2)) (x_i +
+// sum_{a in e} x_a)
+void mass_apply_mesh(const SimplexMesh &m, const std::vector<double> &meas, const std::vector<int64_t> &start,
+                     const std::vector<int32_t> &list, const double *x, double *y, int ncol)
+{
+    const int nv = m.d + 1;
+    const double w = 1.0 / (double)((m.d + 1) * (m.d + 2));
+    parallel_chunks(nchunks_of(m.n), [&](int64_t c) {
+        const int64_t i0 = c * kChunk, i1 = std::min(m.n, i0 + kChunk);
+        std::vector<double> acc((size_t)ncol);
+        for (int64_t i = i0; i < i1; ++i) {
+            std::fill(acc.begin(), acc.end(), 0.0);
+            for (int64_t t = start[(size_t)i]; t < start[(size_t)i + 1]; ++t) {
+                const int64_t e = list[(size_t)t];
+                const double c_e = meas[(size_t)e] * w;
+                for (int col = 0; col < ncol; ++col) {
+                    double sum = x[i * ncol + col];
+                    for (int a = 0; a < nv; ++a) sum += x[(int64_t)m.conn[e * nv + a] * ncol + col];
+                    acc[(size_t)col] += c_e * sum;
+                }
+            }
+            for (int col = 0; col < ncol; ++col) y[i * ncol + col] = acc[(size_t)col];
+        }
+    });
+}
+
+bool mesh_ok(int dim, int64_t n, const double *xyz, int64_t ne, const int32_t *conn)
+{
+    if ((dim != 2 && dim != 3) || n < 1 || ne < 1 || !xyz || !conn) return false;
+    for (int64_t t = 0; t < ne * (dim + 1); ++t)
+        if (conn[t] < 0 || conn[t] >= n) return false;
+    return true;
+}
+
+int build_kl_mesh(int dim, int64_t n, const double *xyz, int64_t ne, const int32_t *conn, double sigma2, double ell,
+                  int K, double *modes_out, double *lambda_out)
+{
+    if (!mesh_ok(dim, n, xyz, ne, conn) || !modes_out || !lambda_out || !(sigma2 > 0.0) || !(ell > 0.0))
+        return MLQ_EINVAL;
+    if (K < 1 || K > n || K > 4096) return MLQ_EINVAL;
+    const SimplexMesh m{dim, n, ne, xyz, conn};
+    std::vector<double> meas((size_t)ne);
+    for (int64_t e = 0; e < ne; ++e) meas[(size_t)e] = simplex_measure(m, e);
+    std::vector<int64_t> start;
+    std::vector<int32_t> list;
+    node_incidence(m, start, list);
+    auto coord = [&](int64_t t, double *x) {
+        for (int c = 0; c < 3; ++c) x[c] = c < dim ? xyz[t * dim + c] : 0.0;
+    };
+    auto mass = [&](const double *x, double *y, int ncol) { mass_apply_mesh(m, meas, start, list, x, y, ncol); };
+    return build_kl_nodes(n, coord, mass, sigma2, ell, K, modes_out, lambda_out);
+}
+
+// Barycentric coordinates of x in simplex e as ratios of signed measures
+// (x replacing one vertex at a time); returns the smallest
+double barycentric_of(const SimplexMesh &m, int64_t e, const double *x, double *lam)
+{
+    const int nv = m.d + 1;
+    double P[4][3] = {};
+    for (int a = 0; a < nv; ++a)
+        for (int c = 0; c < m.d; ++c) P[a][c] = m.xyz[(int64_t)m.conn[e * nv + a] * m.d + c];
+    auto signed_measure = [&](const double (*Q)[3]) {
+        if (m.d == 2) return (Q[1][0] - Q[0][0]) * (Q[2][1] - Q[0][1]) - (Q[1][1] - Q[0][1]) * (Q[2][0] - Q[0][0]);
+        const double a[3] = {Q[1][0] - Q[0][0], Q[1][1] - Q[0][1], Q[1][2] - Q[0][2]};
+        const double b[3] = {Q[2][0] - Q[0][0], Q[2][1] - Q[0][1], Q[2][2] - Q[0][2]};
+        const double c[3] = {Q[3][0] - Q[0][0], Q[3][1] - Q[0][1], Q[3][2] - Q[0][2]};
+        return a[0] * (b[1] * c[2] - b[2] * c[1]) + a[1] * (b[2] * c[0] - b[0] * c[2]) + a[2] * (b[0] * c[1] - b[1] * c[0]);
+    };
+    const double whole = signed_measure(P);
+    double mn = 1e300;
+    for (int a = 0; a < nv; ++a) {
+        double Q[4][3];
+        std::memcpy(Q, P, sizeof(Q));
+        for (int c = 0; c < m.d; ++c) Q[a][c] = x[c];
+        lam[a] = signed_measure(Q) / whole;
+        mn = std::min(mn, lam[a]);
+    }
+    return mn;
+}
+
+int p1_at_points(int dim, int64_t n, const double *xyz, int64_t ne, const int32_t *conn, int K, const double *f,
+                 int64_t np, const double *pts, double *out)
+{
+    if (!mesh_ok(dim, n, xyz, ne, conn) || K < 1 || np < 0 || (np > 0 && (!f || !pts || !out))) return MLQ_EINVAL;
+    const SimplexMesh m{dim, n, ne, xyz, conn};
+    const int nv = dim + 1;
+    // buckets: a uniform grid over the node bounding box; each lists, in
+    // element order, the simplices whose bounding box meets it
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int c = 0; c < dim; ++c) lo[c] = hi[c] = xyz[c];
+    for (int64_t i = 0; i < n; ++i)
+        for (int c = 0; c < dim; ++c) {
+            lo[c] = std::min(lo[c], xyz[i * dim + c]);
+            hi[c] = std::max(hi[c], xyz[i * dim + c]);
+        }
+    const int g = std::max(1, std::min(512, (int)std::lround(std::pow((double)ne / 6.0, 1.0 / dim))));
+    double inv[3] = {1, 1, 1};
+    for (int c = 0; c < dim; ++c) inv[c] = hi[c] > lo[c] ? g / (hi[c] - lo[c]) : 1.0;
+    auto cell = [&](int c, double v) { return std::max(0, std::min(g - 1, (int)std::floor((v - lo[c]) * inv[c]))); };
+    int64_t nb = 1;
+    for (int c = 0; c < dim; ++c) nb *= g;
+    std::vector<std::array<int, 6>> box((size_t)ne);
+    std::vector<int64_t> bstart((size_t)nb + 1, 0);
+    for (int64_t e = 0; e < ne; ++e) {
+        std::array<int, 6> r{0, 0, 0, 0, 0, 0};
+        for (int c = 0; c < dim; ++c) {
+            double a = 1e300, b = -1e300;
+            for (int q = 0; q < nv; ++q) {
+                const double v = xyz[(int64_t)conn[e * nv + q] * dim + c];
+                a = std::min(a, v);
+                b = std::max(b, v);
+            }
+            r[2 * c] = cell(c, a);
+            r[2 * c + 1] = cell(c, b);
+        }
+        box[(size_t)e] = r;
+        for (int z = r[4]; z <= r[5]; ++z)
+            for (int y = r[2]; y <= r[3]; ++y)
+                for (int x = r[0]; x <= r[1]; ++x) ++bstart[(size_t)(x + (int64_t)g * (y + (int64_t)g * z)) + 1];
+    }
+    for (int64_t b = 0; b < nb; ++b) bstart[(size_t)b + 1] += bstart[(size_t)b];
+    std::vector<int32_t> blist((size_t)bstart[(size_t)nb]);
+    {
+        std::vector<int64_t> fill(bstart.begin(), bstart.end() - 1);
+        for (int64_t e = 0; e < ne; ++e) {
+            const std::array<int, 6> &r = box[(size_t)e];
+            for (int z = r[4]; z <= r[5]; ++z)
+                for (int y = r[2]; y <= r[3]; ++y)
+                    for (int x = r[0]; x <= r[1]; ++x)
+                        blist[(size_t)fill[(size_t)(x + (int64_t)g * (y + (int64_t)g * z))]++] = (int32_t)e;
+        }
+    }
+    parallel_chunks((np + 1023) / 1024, [&](int64_t c) {
+        const int64_t p0 = c * 1024, p1 = std::min(np, p0 + 1024);
+        for (int64_t p = p0; p < p1; ++p) {
+            const double *x = pts + p * dim;
+            int64_t b = 0, stride = 1;
+            for (int cc = 0; cc < dim; ++cc) {
+                b += cell(cc, x[cc]) * stride;
+                stride *= g;
+            }
+            double lam[4], best_lam[4] = {0, 0, 0, 0};
+            int64_t best = -1;
+            // a simplex containing x meets x's bucket: the first of them
+            for (int64_t t = bstart[(size_t)b]; t < bstart[(size_t)b + 1] && best < 0; ++t) {
+                const int64_t e = blist[(size_t)t];
+                if (barycentric_of(m, e, x, lam) >= -1e-12) {
+                    best = e;
+                    std::memcpy(best_lam, lam, sizeof(lam));
+                }
+            }
+            if (best < 0) {
+                // in no simplex: the first simplex whose smallest coordinate is
+                // within 1e-12 of the largest over all simplices
+                double best_min = -1e300;
+                for (int64_t e = 0; e < ne; ++e) best_min = std::max(best_min, barycentric_of(m, e, x, lam));
+                for (int64_t e = 0; e < ne && best < 0; ++e)
+                    if (barycentric_of(m, e, x, lam) >= best_min - 1e-12) {
+                        best = e;
+                        std::memcpy(best_lam, lam, sizeof(lam));
+                    }
+            }
+            for (int k = 0; k < K; ++k) {
+                double v = 0.0;
+                for (int a = 0; a < nv; ++a) v += best_lam[a] * f[(int64_t)conn[best * nv + a] * K + k];
+                out[p * K + k] = v;
+            }
+        }
+    });
+    return MLQ_OK;
+}
+
 int build_kl(int dim, const int32_t *dims, const double *lengths, double sigma2, double ell, int K,
              double *modes_out, double *lambda_out)
 {
@@ -434,6 +645,18 @@ int mlq_centroid_table(int dim, const int32_t *fine_dims, const double *modes_f,
                        double *phi_out)
 {
     return guarded([&] { return centroid_table(dim, fine_dims, modes_f, K, coarse_dims, phi_out); });
+}
+
+int mlq_build_kl_mesh(int dim, int64_t n, const double *xyz, int64_t ne, const int32_t *conn, double sigma2,
+                      double ell, int K, double *modes_out, double *lambda_out)
+{
+    return guarded([&] { return build_kl_mesh(dim, n, xyz, ne, conn, sigma2, ell, K, modes_out, lambda_out); });
+}
+
+int mlq_p1_at_points(int dim, int64_t n, const double *xyz, int64_t ne, const int32_t *conn, int K, const double *f,
+                     int64_t np, const double *pts, double *out)
+{
+    return guarded([&] { return p1_at_points(dim, n, xyz, ne, conn, K, f, np, pts, out); });
 }
 
 }  // extern "C"

@@ -70,6 +70,9 @@ _lib.mlq_set_initial_disk.argtypes = [_vp, ctypes.c_int, ctypes.c_double]
 _lib.mlq_set_kl.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp]
 _lib.mlq_build_kl.argtypes = [ctypes.c_int, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, _vp, _vp]
 _lib.mlq_centroid_table.argtypes = [ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp]
+_lib.mlq_build_kl_mesh.argtypes = [ctypes.c_int, _i64, _vp, _i64, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                   _vp, _vp]
+_lib.mlq_p1_at_points.argtypes = [ctypes.c_int, _i64, _vp, _i64, _vp, ctypes.c_int, _vp, _i64, _vp, _vp]
 _lib.mlq_solve.argtypes = [_vp, ctypes.c_int, _i64, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
 _lib.mlq_estimate.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.mlq_submit.argtypes = [_vp, _vp, _vp]
@@ -92,7 +95,7 @@ _lib.mlq_last_cuda_error.argtypes = [_vp]
 
 EXPORTED = ["mlq_default_options", "mlq_default_model", "mlq_create", "mlq_destroy", "mlq_set_options",
             "mlq_set_model", "mlq_add_level", "mlq_set_initial_state", "mlq_set_initial_disk", "mlq_set_kl",
-            "mlq_build_kl", "mlq_centroid_table", "mlq_solve", "mlq_estimate", "mlq_workspace_bytes",
+            "mlq_build_kl", "mlq_centroid_table", "mlq_build_kl_mesh", "mlq_p1_at_points", "mlq_solve", "mlq_estimate", "mlq_workspace_bytes",
             "mlq_launch_count", "mlq_level_launch", "mlq_strerror", "mlq_last_cuda_error", "mlq_set_profiling",
             "mlq_member_profile", "mlq_autotune", "mlq_solve_noalloc", "mlq_synthesize", "mlq_submit", "mlq_poll"]
 
@@ -183,6 +186,40 @@ def centroid_table(m_fine, modes_f: np.ndarray, m_coarse) -> np.ndarray:
     _check(_lib.mlq_centroid_table(dim, fd.ctypes.data_as(_vp), pm, K, cd.ctypes.data_as(_vp),
                                    phi.ctypes.data_as(_vp)), "mlq_centroid_table")
     return phi
+
+
+def _mesh_args(xyz, conn):
+    xyz, px = _host(xyz, np.float64)
+    conn, pc = _host(conn, np.int32)
+    return xyz, px, conn, pc
+
+
+def build_kl_mesh(xyz: np.ndarray, conn: np.ndarray, sigma2: float, ell: float, K: int):
+    """KL modes (n x K) and eigenvalues (K) on a general simplicial mesh
+    (nodes n x dim, simplices n_e x (dim + 1))."""
+    xyz, px, conn, pc = _mesh_args(xyz, conn)
+    n, dim = xyz.shape
+    modes = np.zeros((n, K))
+    lam = np.zeros(K)
+    _check(_lib.mlq_build_kl_mesh(dim, n, px, conn.shape[0], pc, sigma2, ell, K, modes.ctypes.data_as(_vp),
+                                  lam.ctypes.data_as(_vp)), "mlq_build_kl_mesh")
+    return modes, lam
+
+
+def p1_at_points(xyz: np.ndarray, conn: np.ndarray, f: np.ndarray, pts: np.ndarray) -> np.ndarray:
+    """Values at points (np x dim) of the P1 interpolants of nodal fields
+    f (n x K) on a general simplicial mesh (the transfer between unrelated
+    meshes)."""
+    xyz, px, conn, pc = _mesh_args(xyz, conn)
+    n, dim = xyz.shape
+    f2 = np.asarray(f, dtype=np.float64)
+    f2 = f2[:, None] if f2.ndim == 1 else f2
+    f2, pf = _host(f2, np.float64)
+    pts, pp = _host(pts, np.float64)
+    out = np.zeros((pts.shape[0], f2.shape[1]))
+    _check(_lib.mlq_p1_at_points(dim, n, px, conn.shape[0], pc, f2.shape[1], pf, pts.shape[0], pp,
+                                 out.ctypes.data_as(_vp)), "mlq_p1_at_points")
+    return out
 
 
 MLQ_ETOOBIG = -7

@@ -101,3 +101,55 @@ def test_product_kl_over_several_chunks_matches_oracle(mlq, dims, ell):
     pm, pl = mlq.build_kl(dims, 0.09, ell, 8)
     assert np.allclose(pl, ol, rtol=1e-12, atol=0)
     assert np.allclose(pm, om, rtol=0, atol=1e-12)
+
+
+def test_product_kl_on_a_general_mesh_matches_oracle(mlq):
+    # the left-ventricle shell (unstructured tetrahedra, more than one
+    # 8192-node chunk): same eigenvalues and modes as the oracle's builder
+    from paper_2105_02007_gb300 import lv_inputs as LV
+
+    xyz, conn = LV.lv_mesh(3, 40, 70)
+    mesh = O.unstructured_mesh(xyz, conn)
+    assert mesh.n > 8192
+    om, ol = O.kl_build(mesh, 0.09, 0.15 ** 2, 6)
+    pm, pl = mlq.build_kl_mesh(xyz, conn, 0.09, 0.15 ** 2, 6)
+    assert np.allclose(pl, ol, rtol=1e-12, atol=0)
+    # the shell's rotational symmetry makes eigenvalues nearly equal, so the
+    # modes within such a cluster are not unique: compare the represented
+    # covariance V V^T (= L L^T of the pivoted Cholesky factor) on vectors
+    r = np.random.default_rng(7).normal(size=(mesh.n, 3))
+    cov_o, cov_p = om @ (om.T @ r), pm @ (pm.T @ r)
+    assert np.max(np.abs(cov_p - cov_o)) < 1e-12 * np.max(np.abs(cov_o))
+    # a 2D triangulation given as a general mesh: the same as the structured call
+    m2 = O.mesh2d(17)
+    pm2, pl2 = mlq.build_kl_mesh(m2.xyz, m2.conn, 0.09, 0.04, 5)
+    sm2, sl2 = mlq.build_kl(17, 0.09, 0.04, 5)
+    assert np.allclose(pl2, sl2, rtol=1e-12, atol=0) and np.allclose(pm2, sm2, rtol=0, atol=1e-12)
+    with pytest.raises(mlq.MLQError):
+        mlq.build_kl_mesh(xyz, np.where(conn == 0, xyz.shape[0], conn), 0.09, 0.04, 4)   # index out of range
+
+
+def test_product_point_transfer_matches_oracle(mlq):
+    from paper_2105_02007_gb300 import lv_inputs as LV
+
+    fine_xyz, fine_conn = LV.lv_mesh(3, 17, 29)
+    fine = O.unstructured_mesh(fine_xyz, fine_conn)
+    coarse = O.unstructured_mesh(*LV.lv_mesh(2, 7, 11))
+    cen = coarse.xyz[coarse.conn].mean(axis=1)
+    # and points just outside: beyond the epicardium, inside the cavity,
+    # above the base
+    mu, _, _ = LV.prolate_coordinates(fine_xyz)
+    epi = fine_xyz[np.abs(mu - LV.MU_EPI) < 1e-9][::7]
+    endo = fine_xyz[np.abs(mu - LV.MU_ENDO) < 1e-9][::7]
+    base = fine_xyz[np.abs(fine_xyz[:, 2]) < 1e-12][::5] + np.array([0.0, 0.0, 2e-3])
+    pts = np.concatenate([cen, epi * 1.002, endo * 0.998, base])
+    f = np.random.default_rng(6).normal(size=(fine.n, 3))
+    ref, el, lam_min = O.p1_at_points(fine, f, pts, return_location=True)
+    got = mlq.p1_at_points(fine_xyz, fine_conn, f, pts)
+    inside = lam_min >= -1e-12
+    assert (~inside).sum() > 20             # the case of points outside is exercised
+    # points inside: the P1 function is continuous, any containing simplex agrees
+    assert np.max(np.abs(got[inside] - ref[inside])) < 1e-12
+    # points outside: the same simplex by the same rule (up to rounding of the
+    # barycentric coordinates)
+    assert np.max(np.abs(got[~inside] - ref[~inside])) < 1e-9
