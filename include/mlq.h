@@ -200,6 +200,36 @@ int mlq_build_kl_mesh(int dim, int64_t n, const double *xyz, int64_t ne, const i
 int mlq_p1_at_points(int dim, int64_t n, const double *xyz, int64_t ne, const int32_t *conn, int K, const double *f,
                      int64_t np, const double *pts, double *out);
 
+/* Levels on general tetrahedral meshes (non-nested hierarchies; Sec. 4 and
+ * the ventricle of Sec. 5.4): a self-contained FP64 member.  One object per
+ * mesh; it owns its device arrays and uses the default stream.
+ *
+ * mlq_mesh_create: n nodes (xyz host, n x 3), ne tetrahedra (conn host,
+ * ne x 4, 0-based, non-degenerate, ne <= 2^27), optional fibre frames
+ * (frames host, ne x 6: two orthonormal vectors e1, e2 per tetrahedron; NULL
+ * = the x and y axes).  Sets up the CSR pattern of the P1 matrices, the
+ * element geometry and the consistent mass M (|e| (1 + delta_ab) / 20).
+ * MLQ_EINVAL for bad sizes, indices or a degenerate tetrahedron.
+ * mlq_mesh_set_kl: the per-element KL table phi (host, ne x K) and mean angle
+ * theta_mean (host, ne, may be NULL = 0); the fibre of sample s on element e
+ * is f = cos(theta) e1 + sin(theta) e2 with theta = theta_mean_e + sum_k
+ * phi[e K + k] xi[s K + k] (eq. KLlowrank), D = s_t I + (s_l - s_t) f f^T
+ * (eq. AdmV).
+ * mlq_mesh_solve: S samples (xi host, S x K), nsteps time blocks of dt from
+ * the initial state v0, w0 (host, n; w0 may be NULL = 0): b = M (v + dt R),
+ * (M + dt K) v+ = b by Jacobi-preconditioned CG from v until ||r|| <= rtol
+ * ||b|| (at most 10 n iterations per block), w += dt eps (v - gam w);
+ * q_out (host, S) = m^T v(T) with m = M 1; status (mlq_sample_status, worst
+ * block) and iters (CG iterations summed over blocks) may be NULL.  Blocks
+ * until done. */
+typedef struct mlq_mesh mlq_mesh;
+int mlq_mesh_create(mlq_mesh **out, int device, int64_t n, const double *xyz, int64_t ne, const int32_t *conn,
+                    const double *frames);
+int mlq_mesh_destroy(mlq_mesh *mesh);
+int mlq_mesh_set_kl(mlq_mesh *mesh, int K, const double *phi, const double *theta_mean);
+int mlq_mesh_solve(mlq_mesh *mesh, const mlq_model *model, double dt, int32_t nsteps, double rtol, const double *v0,
+                   const double *w0, int64_t S, const double *xi, double *q_out, int32_t *status, int32_t *iters);
+
 /* Solve S samples (0 <= S <= 65535) on `level`.  xi: host or device, S x K row-major FP64
  * (sample s uses xi[s*K .. s*K+K-1]).  For each sample: synthesise theta
  * (eq. KLlowrank), set up A = M + dt K(theta), run the nsteps time blocks,

@@ -73,6 +73,11 @@ _lib.mlq_centroid_table.argtypes = [ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _
 _lib.mlq_build_kl_mesh.argtypes = [ctypes.c_int, _i64, _vp, _i64, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                    _vp, _vp]
 _lib.mlq_p1_at_points.argtypes = [ctypes.c_int, _i64, _vp, _i64, _vp, ctypes.c_int, _vp, _i64, _vp, _vp]
+_lib.mlq_mesh_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, _i64, _vp, _i64, _vp, _vp]
+_lib.mlq_mesh_destroy.argtypes = [_vp]
+_lib.mlq_mesh_set_kl.argtypes = [_vp, ctypes.c_int, _vp, _vp]
+_lib.mlq_mesh_solve.argtypes = [_vp, _vp, ctypes.c_double, ctypes.c_int32, ctypes.c_double, _vp, _vp, _i64, _vp, _vp,
+                                _vp, _vp]
 _lib.mlq_solve.argtypes = [_vp, ctypes.c_int, _i64, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
 _lib.mlq_estimate.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.mlq_submit.argtypes = [_vp, _vp, _vp]
@@ -95,7 +100,8 @@ _lib.mlq_last_cuda_error.argtypes = [_vp]
 
 EXPORTED = ["mlq_default_options", "mlq_default_model", "mlq_create", "mlq_destroy", "mlq_set_options",
             "mlq_set_model", "mlq_add_level", "mlq_set_initial_state", "mlq_set_initial_disk", "mlq_set_kl",
-            "mlq_build_kl", "mlq_centroid_table", "mlq_build_kl_mesh", "mlq_p1_at_points", "mlq_solve", "mlq_estimate", "mlq_workspace_bytes",
+            "mlq_build_kl", "mlq_centroid_table", "mlq_build_kl_mesh", "mlq_p1_at_points", "mlq_mesh_create",
+            "mlq_mesh_destroy", "mlq_mesh_set_kl", "mlq_mesh_solve", "mlq_solve", "mlq_estimate", "mlq_workspace_bytes",
             "mlq_launch_count", "mlq_level_launch", "mlq_strerror", "mlq_last_cuda_error", "mlq_set_profiling",
             "mlq_member_profile", "mlq_autotune", "mlq_solve_noalloc", "mlq_synthesize", "mlq_submit", "mlq_poll"]
 
@@ -220,6 +226,58 @@ def p1_at_points(xyz: np.ndarray, conn: np.ndarray, f: np.ndarray, pts: np.ndarr
     _check(_lib.mlq_p1_at_points(dim, n, px, conn.shape[0], pc, f2.shape[1], pf, pts.shape[0], pp,
                                  out.ctypes.data_as(_vp)), "mlq_p1_at_points")
     return out
+
+
+class MeshLevel:
+    """A level on a general tetrahedral mesh (mlq_mesh_*): FP64 Jacobi-PCG
+    member for non-nested hierarchies."""
+
+    def __init__(self, xyz: np.ndarray, conn: np.ndarray, frames=None, device: int = 0):
+        self._xyz, px, self._conn, pc = _mesh_args(xyz, conn)
+        self.n, self.ne = self._xyz.shape[0], self._conn.shape[0]
+        fr, pf = (None, None) if frames is None else _host(frames, np.float64)
+        h = _vp()
+        _check(_lib.mlq_mesh_create(ctypes.byref(h), device, self.n, px, self.ne, pc, pf), "mlq_mesh_create")
+        self._h = h
+        self.K = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.mlq_mesh_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        self.close()
+
+    def set_kl(self, phi: np.ndarray, theta_mean=None):
+        phi, pp = _host(phi, np.float64)
+        tm, pt = (None, None) if theta_mean is None else _host(theta_mean, np.float64)
+        _check(_lib.mlq_mesh_set_kl(self._h, phi.shape[1], pp, pt), "mlq_mesh_set_kl")
+        self.K = phi.shape[1]
+
+    def solve(self, xi: np.ndarray, dt: float, nsteps: int, v0: np.ndarray, w0=None, rtol: float = 1e-13,
+              model=None):
+        xi, px = _host(xi, np.float64)
+        S = xi.shape[0]
+        v0, pv = _host(v0, np.float64)
+        w0a, pw = (None, None) if w0 is None else _host(w0, np.float64)
+        md = Model()
+        _lib.mlq_default_model(ctypes.byref(md))
+        for k, v in (model or {}).items():
+            setattr(md, k, v)
+        q = np.zeros(S)
+        st = np.zeros(S, dtype=np.int32)
+        it = np.zeros(S, dtype=np.int32)
+        _check(_lib.mlq_mesh_solve(self._h, ctypes.byref(md), dt, nsteps, rtol, pv, pw, S, px,
+                                   q.ctypes.data_as(_vp), st.ctypes.data_as(_vp), it.ctypes.data_as(_vp)),
+               "mlq_mesh_solve")
+        return q, st, it
 
 
 MLQ_ETOOBIG = -7

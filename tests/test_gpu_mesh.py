@@ -1,0 +1,79 @@
+"""Levels on general tetrahedral meshes (mlq_mesh_*): the synthetic
+left-ventricle shell with wall-tangent fibre frames and helix angles, against
+the FP64 oracle on the same seeded inputs (FP64 path: 1e-10 relative per
+sample), plus the properties that hold at any size."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2105_02007_gb300 import inputs
+from paper_2105_02007_gb300 import lv_inputs as LV
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mlq():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_02007_gb300 import build
+
+    build.build()
+    from paper_2105_02007_gb300 import mlq as m
+
+    return m
+
+
+def test_mesh_level_matches_oracle_on_the_shell(mlq):
+    xyz, conn = LV.lv_mesh(2, 8, 14)
+    frames, alpha = LV.lv_fibres(xyz, conn)
+    mesh = O.unstructured_mesh(xyz, conn)
+    fine_xyz, fine_conn = LV.lv_mesh(3, 11, 19)           # KL on an unrelated finer shell
+    modes, _ = O.kl_build(O.unstructured_mesh(fine_xyz, fine_conn), 0.09, 0.15 ** 2, 4)
+    phi = O.centroid_table_unrelated(O.unstructured_mesh(fine_xyz, fine_conn), modes, mesh)
+    xi = inputs.gaussian_xi(0, 0, 0, 5, 4)
+    v0, w0 = LV.stimulus(xyz, radius=0.4)
+    dt, nb = 0.05, 12
+    q_ref, _, st = O.solve_batch(mesh, phi, xi, dt, nb, v0=v0, w0=w0, theta_mean=alpha, frames=frames, nthreads=2)
+    assert np.all(st == 0)
+    with mlq.MeshLevel(xyz, conn, frames) as lvl:
+        lvl.set_kl(phi, alpha)
+        q, status, iters = lvl.solve(xi, dt, nb, v0, w0)
+    assert np.all(status == 0) and np.all(iters > 0)
+    assert np.max(np.abs(q - q_ref) / np.abs(q_ref)) < 1e-10
+
+
+def test_mesh_level_conservation_and_uniform_state(mlq):
+    xyz, conn = LV.lv_mesh(3, 12, 20)
+    frames, alpha = LV.lv_fibres(xyz, conn)
+    mesh = O.unstructured_mesh(xyz, conn)
+    rp, ci, mv, _ = O.assemble(mesh)
+    m = np.zeros(mesh.n)
+    np.add.at(m, ci, mv)
+    rng = np.random.default_rng(2)
+    v0, w0, dt = rng.uniform(0, 1, mesh.n), rng.uniform(0, 0.2, mesh.n), 0.02
+    phi = rng.normal(scale=0.3, size=(mesh.ne, 2))
+    xi = inputs.gaussian_xi(1, 0, 0, 3, 2)
+    with mlq.MeshLevel(xyz, conn, frames) as lvl:
+        lvl.set_kl(phi, alpha)
+        q, st, _ = lvl.solve(xi, dt, 1, v0, w0)
+        assert np.all(st == 0)
+        assert np.allclose(q, m @ (v0 + dt * (v0 * (v0 - 0.1) * (1 - v0) - w0)), rtol=1e-11, atol=0)
+        v, w = 0.4, 0.02
+        q, st, _ = lvl.solve(xi, dt, 10, np.full(mesh.n, v), np.full(mesh.n, w))
+    for _ in range(10):
+        v, w = v + dt * (v * (v - 0.1) * (1 - v) - w), w + dt * 0.01 * (v - 0.5 * w)
+    assert np.all(st == 0)
+    assert np.allclose(q, m.sum() * v, rtol=1e-11, atol=0)
+
+
+def test_mesh_level_rejects_bad_input(mlq):
+    xyz, conn = LV.lv_mesh(1, 3, 5)
+    with pytest.raises(mlq.MLQError):
+        mlq.MeshLevel(xyz, np.where(conn == 1, xyz.shape[0] + 3, conn))
+    flat = conn.copy()
+    flat[0, 3] = flat[0, 2]                                  # degenerate tetrahedron
+    with pytest.raises(mlq.MLQError):
+        mlq.MeshLevel(xyz, flat)
