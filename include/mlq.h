@@ -196,7 +196,9 @@ int mlq_build_kl_mesh(int dim, int64_t n, const double *xyz, int64_t ne, const i
  * simplex (a centroid near a curved boundary discretised differently) takes
  * the first simplex whose smallest barycentric coordinate is within 1e-12 of
  * the largest over all simplices, and the linear extension of its P1
- * function.  out: host, np x K. */
+ * function (each such point costs a scan over all simplices; points inside
+ * are found through a bucket grid).  Runs on the host's cores.
+ * out: host, np x K. */
 int mlq_p1_at_points(int dim, int64_t n, const double *xyz, int64_t ne, const int32_t *conn, int K, const double *f,
                      int64_t np, const double *pts, double *out);
 
