@@ -13,6 +13,10 @@ index) into the random variables xi that parametrise the fibre field
   y_i = frac(i z / N + Delta), xi = Phi^{-1}(y), with the generating vector z
   chosen component by component (Sloan & Reztsov 2002; Nuyens & Cools 2006)
   for product weights gamma_k, and shifts Delta from Philox.
+* Halton points (Halton 1960): coordinate k of point i is the radical
+  inverse of i in the k-th prime base.  With the paper's uniform random
+  variables Y_k on [-1, 1] (Sec. 2.3: sigma_k = sqrt(3 lambda_k)) a point maps
+  to xi_k = sqrt(3) (2 y_k - 1), the unit-variance scaling of the modes.
 """
 from __future__ import annotations
 
@@ -143,3 +147,39 @@ def qmc_xi(seed: int, level: int, N: int, R: int, K: int, gamma: np.ndarray) -> 
     z = cbc_lattice(N, K, gamma)
     shifts = uniform_shifts(seed, level, R, K)
     return np.stack([gaussian_from_uniform(lattice_points(z, N, shifts[r])) for r in range(R)])
+
+
+def first_primes(K: int) -> np.ndarray:
+    """The first K primes."""
+    out = []
+    c = 2
+    while len(out) < K:
+        if all(c % p for p in out if p * p <= c):
+            out.append(c)
+        c += 1
+    return np.array(out, dtype=np.int64)
+
+
+def radical_inverse(i: np.ndarray, base: int) -> np.ndarray:
+    """sum_j d_j base^-(j+1) for i = sum_j d_j base^j (exact in base 2, to
+    rounding in the other bases)."""
+    i = np.asarray(i, dtype=np.int64).copy()
+    out = np.zeros(i.shape, dtype=np.float64)
+    f = 1.0 / base
+    while np.any(i > 0):
+        out += (i % base) * f
+        i //= base
+        f /= base
+    return out
+
+
+def halton(N: int, K: int, first: int = 0) -> np.ndarray:
+    """Points first .. first + N - 1 of the K-dimensional Halton sequence
+    (point 0 is the origin).  Shape (N, K), entries in [0, 1)."""
+    idx = np.arange(first, first + N, dtype=np.int64)
+    return np.stack([radical_inverse(idx, int(b)) for b in first_primes(K)], axis=1)
+
+
+def uniform_xi(y: np.ndarray) -> np.ndarray:
+    """xi = sqrt(3) (2 y - 1): Y uniform on [-1, 1] with unit variance."""
+    return math.sqrt(3.0) * (2.0 * np.asarray(y, dtype=np.float64) - 1.0)

@@ -63,3 +63,49 @@ def test_qmc_xi_shapes_and_shift_range():
     assert x.shape == (4, 16, 3) and np.all(np.isfinite(x))
     s = inputs.uniform_shifts(0, 1, 100, 3)
     assert s.min() >= 0 and s.max() < 1
+
+
+def test_halton_known_points_and_stratification():
+    from paper_2105_02007_gb300 import inputs
+
+    assert list(inputs.first_primes(6)) == [2, 3, 5, 7, 11, 13]
+    h = inputs.halton(9, 3)
+    assert list(h[:5, 0]) == [0.0, 0.5, 0.25, 0.75, 0.125]
+    assert np.allclose(h[:4, 1], [0.0, 1 / 3, 2 / 3, 1 / 9], rtol=0, atol=1e-15)
+    assert np.allclose(h[1:6, 2], [0.2, 0.4, 0.6, 0.8, 0.04], rtol=0, atol=1e-15)
+    # the first b^m points of coordinate k are the grid {j / b^m} (exactly in
+    # base 2, to rounding in the others)
+    for k, b in enumerate([2, 3, 5]):
+        m = {2: 10, 3: 6, 5: 4}[b]
+        col = np.sort(inputs.halton(b ** m, 3)[:, k])
+        if b == 2:
+            assert np.array_equal(col, np.arange(b ** m) / b ** m)
+        else:
+            assert np.max(np.abs(col - np.arange(b ** m) / b ** m)) < 1e-15
+    # consecutive blocks continue the sequence
+    assert np.array_equal(inputs.halton(5, 4, first=7), inputs.halton(12, 4)[7:])
+
+
+def test_halton_integrates_better_than_random_points():
+    from paper_2105_02007_gb300 import inputs
+
+    K = 3
+    f = lambda y: np.prod(1.0 + 0.5 * (y - 0.5), axis=1)     # exact integral 1
+    err = [abs(f(inputs.halton(N, K)).mean() - 1.0) for N in (1024, 16384)]
+    # close to the 1/N rate of a low-discrepancy sequence (random points: 1/sqrt N)
+    assert err[1] < err[0] / 8
+    rng = np.random.default_rng(0)
+    err_mc = np.sqrt(np.mean([(f(rng.random((16384, K))).mean() - 1.0) ** 2 for _ in range(20)]))
+    assert err[1] < err_mc / 5
+
+
+def test_uniform_map_has_unit_variance():
+    from paper_2105_02007_gb300 import inputs
+
+    # on the grid {j / N} the map gives exactly mean -sqrt(3)/N and the
+    # variance of the discrete uniform law on N points of [-sqrt 3, sqrt 3)
+    N = 2 ** 12
+    xi = inputs.uniform_xi(np.arange(N) / N)
+    assert abs(xi.mean() + np.sqrt(3.0) / N) < 1e-14
+    assert abs(xi.var() - (1.0 - 1.0 / N ** 2)) < 1e-12
+    assert xi.min() == -np.sqrt(3.0) and xi.max() < np.sqrt(3.0)
