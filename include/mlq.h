@@ -202,6 +202,15 @@ int mlq_build_kl_mesh(int dim, int64_t n, const double *xyz, int64_t ne, const i
 int mlq_p1_at_points(int dim, int64_t n, const double *xyz, int64_t ne, const int32_t *conn, int K, const double *f,
                      int64_t np, const double *pts, double *out);
 
+/* Host helper: numbers of samples per level for eq. StandardML with Monte
+ * Carlo rules that minimise the cost sum_l N_l cost[l] subject to the
+ * statistical error sqrt(sum_l var[l] / N_l) <= eps:
+ * N_l = max(nmin, ceil(eps^-2 sqrt(var[l] / cost[l]) sum_k sqrt(var[k] cost[k]))).
+ * var (V_l of the level differences, >= 0), cost (> 0, e.g. DOF-steps per
+ * sample) and N_out are host arrays of L + 1 entries.  MLQ_EINVAL for bad
+ * arguments or counts beyond 4e18. */
+int mlq_mlmc_allocation(int L, const double *var, const double *cost, double eps, int64_t nmin, int64_t *N_out);
+
 /* Levels on general tetrahedral meshes (non-nested hierarchies; Sec. 4 and
  * the ventricle of Sec. 5.4): a self-contained FP64 member.  One object per
  * mesh; it owns its device arrays and uses the default stream.

@@ -73,6 +73,7 @@ _lib.mlq_centroid_table.argtypes = [ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _
 _lib.mlq_build_kl_mesh.argtypes = [ctypes.c_int, _i64, _vp, _i64, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                    _vp, _vp]
 _lib.mlq_p1_at_points.argtypes = [ctypes.c_int, _i64, _vp, _i64, _vp, ctypes.c_int, _vp, _i64, _vp, _vp]
+_lib.mlq_mlmc_allocation.argtypes = [ctypes.c_int, _vp, _vp, ctypes.c_double, _i64, _vp]
 _lib.mlq_mesh_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, _i64, _vp, _i64, _vp, _vp]
 _lib.mlq_mesh_destroy.argtypes = [_vp]
 _lib.mlq_mesh_set_kl.argtypes = [_vp, ctypes.c_int, _vp, _vp]
@@ -101,7 +102,7 @@ _lib.mlq_last_cuda_error.argtypes = [_vp]
 EXPORTED = ["mlq_default_options", "mlq_default_model", "mlq_create", "mlq_destroy", "mlq_set_options",
             "mlq_set_model", "mlq_add_level", "mlq_set_initial_state", "mlq_set_initial_disk", "mlq_set_kl",
             "mlq_build_kl", "mlq_centroid_table", "mlq_build_kl_mesh", "mlq_p1_at_points", "mlq_mesh_create",
-            "mlq_mesh_destroy", "mlq_mesh_set_kl", "mlq_mesh_solve", "mlq_solve", "mlq_estimate", "mlq_workspace_bytes",
+            "mlq_mesh_destroy", "mlq_mesh_set_kl", "mlq_mesh_solve", "mlq_mlmc_allocation", "mlq_solve", "mlq_estimate", "mlq_workspace_bytes",
             "mlq_launch_count", "mlq_level_launch", "mlq_strerror", "mlq_last_cuda_error", "mlq_set_profiling",
             "mlq_member_profile", "mlq_autotune", "mlq_solve_noalloc", "mlq_synthesize", "mlq_submit", "mlq_poll"]
 
@@ -226,6 +227,16 @@ def p1_at_points(xyz: np.ndarray, conn: np.ndarray, f: np.ndarray, pts: np.ndarr
     _check(_lib.mlq_p1_at_points(dim, n, px, conn.shape[0], pc, f2.shape[1], pf, pts.shape[0], pp,
                                  out.ctypes.data_as(_vp)), "mlq_p1_at_points")
     return out
+
+
+def mlmc_allocation(var, cost, eps: float, nmin: int = 2) -> np.ndarray:
+    """Samples per level minimising the cost for RMSE_stat <= eps
+    (mlq_mlmc_allocation)."""
+    var, pv = _host(var, np.float64)
+    cost, pc = _host(cost, np.float64)
+    N = np.zeros(var.size, dtype=np.int64)
+    _check(_lib.mlq_mlmc_allocation(var.size - 1, pv, pc, eps, nmin, N.ctypes.data_as(_vp)), "mlq_mlmc_allocation")
+    return N
 
 
 class MeshLevel:

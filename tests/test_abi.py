@@ -153,3 +153,33 @@ def test_product_point_transfer_matches_oracle(mlq):
     # points outside: the same simplex by the same rule (up to rounding of the
     # barycentric coordinates)
     assert np.max(np.abs(got[~inside] - ref[~inside])) < 1e-9
+
+
+def test_mlmc_allocation_is_the_constrained_optimum(mlq):
+    # closed form: V_l = 4^-l, C_l = 4^l gives N_l = (L + 1) 4^-l / eps^2
+    L, eps = 4, 1e-3
+    V = 4.0 ** -np.arange(L + 1)
+    C = 4.0 ** np.arange(L + 1)
+    N = mlq.mlmc_allocation(V, C, eps, nmin=1)
+    assert np.array_equal(N, np.ceil((L + 1) * 4.0 ** -np.arange(L + 1) / eps ** 2).astype(np.int64))
+    # generic: the error target holds, and no other allocation meeting it is
+    # cheaper (first-order optimality: perturbations along the constraint)
+    rng = np.random.default_rng(8)
+    V, C, eps = rng.uniform(1e-6, 1e-3, 5), rng.uniform(1, 1e4, 5), 2e-4
+    N = mlq.mlmc_allocation(V, C, eps, nmin=1)
+    assert np.sum(V / N) <= eps ** 2 * (1 + 1e-12)
+    n_star = np.sqrt(V / C) * np.sum(np.sqrt(V * C)) / eps ** 2
+    assert np.allclose(np.sum(V / n_star), eps ** 2, rtol=1e-12)
+    cost = np.sum(n_star * C)
+    for _ in range(50):
+        d = rng.normal(size=5) * 0.05 * n_star
+        d -= (np.sum(V / n_star ** 2 * d) / np.sum((V / n_star ** 2) ** 2)) * V / n_star ** 2   # stay on the constraint to first order
+        m = n_star + d
+        scale = np.sum(V / m) / eps ** 2                     # restore the constraint exactly
+        assert np.sum(m * scale * C) >= cost * (1 - 1e-12)
+    # nmin and a level without variance
+    N = mlq.mlmc_allocation([0.0, 1e-4], [1.0, 10.0], 1e-3, nmin=3)
+    assert N[0] == 3 and N[1] == np.ceil(np.sqrt(1e-5) * np.sqrt(1e-3) / 1e-6)
+    for bad in (dict(var=[-1.0], cost=[1.0]), dict(var=[1.0], cost=[0.0])):
+        with pytest.raises(mlq.MLQError):
+            mlq.mlmc_allocation(bad["var"], bad["cost"], 1e-3)
