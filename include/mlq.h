@@ -119,7 +119,7 @@ typedef struct {
 /* Fill *opt / *model with the defaults listed above (rtol 1e-13 for FP64,
  * rtol 1e-12 and rtol_inner 1e-5 for MIXED, max_iter 100000, max_sweeps 20,
  * precond 1 (multigrid) for MIXED and 0 for FP64; mlq_solve_noalloc always
- * uses the Jacobi inner preconditioner). */
+ * uses the Jacobi inner preconditioner and ignores the launch options). */
 int mlq_default_options(mlq_options *opt, int precision);
 int mlq_default_model(mlq_model *model);
 
@@ -307,21 +307,27 @@ int mlq_autotune(mlq_ctx *ctx, int level, int64_t S, const double *xi, int probe
 
 /* Solve without allocating anything.
  *
- * For callers that cannot call cudaMalloc at the time they need a solve:
- * code running while a stream is being captured into a CUDA graph in the
- * global capture mode (where the runtime rejects allocation calls), and
- * processes whose device memory is owned by another allocator with a fixed
- * budget (a serving engine that reserved HBM up front, a framework's caching
- * allocator), where a library allocation would fail or break the budget.
- * No context is needed: the call creates no stream, event or buffer, and
- * calls no cudaMalloc/cudaFree or other allocating routine.
+ * For callers that cannot call cudaMalloc when they need a solve: processes
+ * whose device memory belongs to another allocator with a fixed budget (a
+ * serving engine that reserved its HBM up front, a framework's caching
+ * allocator), where a library allocation would fail or break the budget, and
+ * latency-critical loops that must not take the device-wide synchronisation
+ * a cudaMalloc/cudaFree may imply.  No context is needed: the call creates no
+ * stream, event or buffer, and calls no cudaMalloc/cudaFree or other
+ * allocating routine.
  *
- * It runs the same kernels as mlq_solve in the mixed path (KL synthesis,
- * stencil set-up, register-resident slab solver) on one level without a
- * coarse member, with all working memory in one fixed, statically allocated
- * device array of MLQ_NOALLOC_SCRATCH_BYTES that every GPU which loads the
- * library holds until the process exits.  Requests whose working set does
- * not fit return MLQ_ETOOBIG; the working set is about
+ * What runs: the FP64 KL synthesis kernel (eq. KLlowrank on the CUDA cores,
+ * not the tensor-core variant mlq_solve uses in the mixed path), the stencil
+ * set-up, and the register-resident slab solver with the Jacobi inner
+ * preconditioner, FP32 inner PCG inside FP64 refinement; one level, no coarse
+ * member.  Its QoI agrees with mlq_solve (mixed path, either preconditioner)
+ * within the mixed-path tolerance (1e-6 relative), not bit for bit.  The
+ * launch shape is chosen by the call: opt->cluster, opt->threads,
+ * opt->storage, opt->graphs and opt->precond are ignored.  All working memory
+ * is one fixed, statically allocated device array of
+ * MLQ_NOALLOC_SCRATCH_BYTES that every GPU which loads the library holds
+ * until the process exits.  Requests whose working set does not fit return
+ * MLQ_ETOOBIG; the working set is about
  *   92 * S * m^2 + 32 * S * (m-1)^2 bytes  (m x m nodes, S samples),
  * e.g. 33 x 33 nodes with up to ~250 samples, or 257 x 257 nodes with 4.
  *
@@ -329,10 +335,11 @@ int mlq_autotune(mlq_ctx *ctx, int level, int64_t S, const double *xi, int probe
  * blocks; model and opt may be NULL (defaults; opt->precision must be
  * MLQ_MIXED); K modes; phi (n_elem x K), theta_mean (n_elem or NULL), xi
  * (S x K), v0 / w0 (m^2 or NULL: the disc start of radius 0.1) -- all DEVICE
- * pointers owned by the caller; outputs q (S, FP64), status and iters (S,
- * int32, may be NULL), DEVICE pointers.  Host pointers return MLQ_EINVAL.
- * The work is queued on cuda_stream (NULL = legacy default stream) and the
- * call returns without waiting; synchronize the stream before reading q.
+ * pointers of the current device (or managed memory), owned by the caller;
+ * outputs q (S, FP64), status and iters (S, int32, may be NULL), likewise.
+ * Host pointers and memory of another GPU return MLQ_EINVAL.  The work is
+ * queued on cuda_stream (NULL = legacy default stream) and the call returns
+ * without waiting; synchronize the stream before reading q.
  *
  * The first call on a device looks up the device address of the scratch
  * array (cudaGetSymbolAddress) with that device current; make that first

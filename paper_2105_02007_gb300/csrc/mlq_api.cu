@@ -1574,7 +1574,10 @@ int noalloc_scratch(int dev, void **out)
     return MLQ_OK;
 }
 
-bool on_device(const void *p)
+// A pointer the kernels on device `dev` may use: device memory of that
+// device, or managed memory.  Memory of another GPU is refused: the kernels
+// would reach it only through peer access, which the call does not set up.
+bool on_device(const void *p, int dev)
 {
     if (!p) return true;
     cudaPointerAttributes a{};
@@ -1582,7 +1585,8 @@ bool on_device(const void *p)
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -1595,8 +1599,10 @@ int mlq_solve_noalloc(int m, double dt, int32_t nsteps, const mlq_model *model, 
 {
     if (m < 2 || m > 8193 || !(dt > 0.0) || nsteps < 0 || K < 1 || K > kMaxK || S < 0 || S > 65535) return MLQ_EINVAL;
     if (!phi || !xi || !q) return MLQ_EINVAL;
-    if (!on_device(phi) || !on_device(theta_mean) || !on_device(xi) || !on_device(v0) || !on_device(w0) ||
-        !on_device(q) || !on_device(status) || !on_device(iters))
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return MLQ_ECUDA;
+    if (!on_device(phi, dev) || !on_device(theta_mean, dev) || !on_device(xi, dev) || !on_device(v0, dev) ||
+        !on_device(w0, dev) || !on_device(q, dev) || !on_device(status, dev) || !on_device(iters, dev))
         return MLQ_EINVAL;
     mlq_model md;
     if (model) md = *model;
@@ -1619,8 +1625,6 @@ int mlq_solve_noalloc(int m, double dt, int32_t nsteps, const mlq_model *model, 
                  o_a32 = put(sn * mlq::kSlots2D * 4), o_v = put(sn * 8), o_w = put(2 * sn * 8), o_b = put(sn * 8),
                  o_it = put((size_t)S * 4), o_st = put((size_t)S * 4);
     if (off > MLQ_NOALLOC_SCRATCH_BYTES) return MLQ_ETOOBIG;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return MLQ_ECUDA;
     void *base = nullptr;
     int st = noalloc_scratch(dev, &base);
     if (st != MLQ_OK) return st;

@@ -9,7 +9,7 @@
 //     triangle is the average of D over its four children (the coarse basis
 //     gradients are constant on it), so A_c = M_c + dt K_c(Dbar_c), set up per
 //     sample by mg_coarsen_kernel and mg_stencil_kernel;
-//   * V(1,1) cycle, damped Jacobi (omega = 0.6) as pre- and post-smoother,
+//   * V(1,1) cycle, damped Jacobi (omega = kMgOmega) as pre- and post-smoother,
 //     restriction P^T and interpolation P, a few damped Jacobi sweeps on the
 //     coarsest level: a fixed symmetric positive definite operator, so it can
 //     precondition CG.

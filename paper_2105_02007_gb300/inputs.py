@@ -174,8 +174,12 @@ def radical_inverse(i: np.ndarray, base: int) -> np.ndarray:
 
 
 def halton(N: int, K: int, first: int = 0) -> np.ndarray:
-    """Points first .. first + N - 1 of the K-dimensional Halton sequence
-    (point 0 is the origin).  Shape (N, K), entries in [0, 1)."""
+    """Points first .. first + N - 1 of the K-dimensional Halton sequence.
+    Shape (N, K), entries in [0, 1).  Point 0 is the origin, which
+    uniform_xi maps to the corner xi = -sqrt(3) in every coordinate: an
+    unrandomised quadrature rule should start at first = 1 so that it does
+    not carry that corner sample (first = 0 keeps the exact stratification
+    of the first b^m points in base b)."""
     idx = np.arange(first, first + N, dtype=np.int64)
     return np.stack([radical_inverse(idx, int(b)) for b in first_primes(K)], axis=1)
 

@@ -141,6 +141,56 @@ def test_lemma_2_1_eigenvalues_of_conductivity(th):
         assert abs((K @ u)[i] + lam * h * h) < 1e-13
 
 
+def _lemma_2_1_check_3d(mesh, h, th, frames, dirs):
+    # For constant D the P1 stiffness of a translation-invariant mesh applied
+    # to u = (a.x)^2/2 at an interior node equals -(a^T D a) times the node's
+    # lumped mass (h^3 on the Kuhn cube mesh): div(D grad u) = a^T D a, and the
+    # stencil annihilates constants and linear fields.  With f the fibre, a = f
+    # gives s_l (Lemma 2.1: G f = |V| f) and every a orthogonal to f gives s_t.
+    rp, ci, _, kv = O.assemble(mesh, np.full(mesh.ne, th), SL, ST, frames=frames)
+    K = O.csr_to_dense(rp, ci, kv, mesh.n)
+    m = mesh.dims[0]
+    interior = [i + m * (j + m * k) for i in (2, 3, 4) for j in (2, 4) for k in (3, 4)]
+    for a, lam in dirs:
+        u = 0.5 * (mesh.xyz @ a) ** 2
+        Ku = K @ u
+        for i in interior:
+            assert abs(Ku[i] + lam * h ** 3) < 1e-13, (a, i, Ku[i], -lam * h ** 3)
+
+
+@pytest.mark.parametrize("th", [0.0, 0.7, -2.0, 1.3])
+def test_lemma_2_1_eigenvalues_of_conductivity_3d(th):
+    # Kuhn tetrahedra of the unit cube, 7 x 7 x 7 nodes, in-plane fibre
+    # f = (cos t, sin t, 0): f gives s_l; the in-plane normal of f and e_z give s_t.
+    m = 7
+    h = 1.0 / (m - 1)
+    mesh = O.mesh3d(m, m, m, 1.0, 1.0, 1.0)
+    f = np.array([np.cos(th), np.sin(th), 0.0])
+    fp = np.array([-np.sin(th), np.cos(th), 0.0])
+    ez = np.array([0.0, 0.0, 1.0])
+    b = (f + ez) / np.sqrt(2.0)          # mixes both eigenvalues: s_t + (s_l - s_t)/2
+    _lemma_2_1_check_3d(mesh, h, th, None, [(f, SL), (fp, ST), (ez, ST), (b, 0.5 * (SL + ST))])
+
+
+@pytest.mark.parametrize("th", [0.0, 0.9, -2.4])
+def test_lemma_2_1_with_frame_out_of_plane(th):
+    # The fibre turns in the plane of a frame (e1, e2) tilted out of the x-y
+    # plane (the ventricle's wall-tangent frames): f = cos t e1 + sin t e2
+    # gives s_l, the in-frame normal -sin t e1 + cos t e2 and e1 x e2 give s_t.
+    m = 7
+    h = 1.0 / (m - 1)
+    mesh = O.mesh3d(m, m, m, 1.0, 1.0, 1.0)
+    rng = np.random.default_rng(11)
+    Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    e1, e2 = Q[:, 0], Q[:, 1]
+    assert abs(e1[2]) > 0.1 and abs(e2[2]) > 0.1        # genuinely out of the x-y plane
+    frames = np.tile(np.concatenate([e1, e2]), (mesh.ne, 1))
+    f = np.cos(th) * e1 + np.sin(th) * e2
+    fp = -np.sin(th) * e1 + np.cos(th) * e2
+    nrm = np.cross(e1, e2)
+    _lemma_2_1_check_3d(mesh, h, th, frames, [(f, SL), (fp, ST), (nrm, ST)])
+
+
 # --------------------------------------------------------------------------
 # KL expansion
 # --------------------------------------------------------------------------
@@ -399,3 +449,27 @@ def test_mc_and_qmc_estimators_plain_definitions():
     assert mean == 3.5 and abs(var - 7.0) < 1e-15 and abs(rmse - np.sqrt(7.0 / 4)) < 1e-15
     est, r = O.qmc_estimate(np.array([[1.0, 3.0], [2.0, 4.0], [3.0, 5.0]]))
     assert est == 3.0 and abs(r - 1.0 / np.sqrt(3)) < 1e-15
+
+
+def test_cube_level_table_counts():
+    # Table cube-levels of Sec. 5.2.1 (tests/golden/cube_levels.txt): h and
+    # dt halve per level and the printed space-time DOF are 2^(4(l+1)).  With
+    # the horizon T = 0.32 (not printed; the reading that makes the table
+    # consistent) they equal the oracle's cube count of the Kuhn mesh of
+    # [-0.5, 0.5]^3 at h_l times the number of time blocks T / dt_l.
+    import os
+
+    rows = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "cube_levels.txt"))
+    T = 0.32
+    for l, dof, h, dt in rows:
+        l = int(l)
+        assert h == 0.5 * 2.0 ** -l and abs(dt - 0.16 * 2.0 ** -l) < 1e-15
+        m = int(round(1.0 / h)) + 1
+        mesh = O.mesh3d(m, m, m, 1.0, 1.0, 1.0) if m <= 9 else None
+        cubes = (m - 1) ** 3
+        if mesh is not None:
+            assert mesh.ne == 6 * cubes
+            vol = np.abs(simplex_volumes(mesh))
+            assert np.allclose(vol, h ** 3 / 6.0, rtol=1e-12)
+        assert cubes * int(round(T / dt)) == int(dof)
+        assert int(dof) == 2 ** (4 * (l + 1))

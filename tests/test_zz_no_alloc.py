@@ -1,8 +1,9 @@
 """The allocation-free entry point (mlq_solve_noalloc), called through the C
 ABI on CUDA tensors the test owns, against the regular mlq_solve on the same
-inputs.  Callers that cannot allocate device memory (stream capture in the
-global mode, a fixed-budget allocator owning the GPU) use this call; it runs
-the same kernels with its working memory in a fixed static device array.
+inputs.  Callers that cannot allocate device memory when they need a solve (a
+fixed-budget allocator owning the GPU's memory, a loop that must not take the
+synchronisation an allocation may imply) use this call; its working memory is
+a fixed static device array.
 
 The file name makes pytest collect it last."""
 import numpy as np
@@ -73,4 +74,19 @@ def test_noalloc_rejects_oversize_and_host_pointers(mlq):
     assert e.value.code == mlq.MLQ_ETOOBIG
     with pytest.raises(mlq.MLQError) as e:
         mlq.solve_noalloc(m, 0.01, 2, phi.cpu(), xi[:1], q[:1])
+    assert e.value.code == -1
+
+
+def test_noalloc_rejects_memory_of_another_gpu(mlq):
+    import torch
+
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs a second GPU")
+    m, K, S = 17, 4, 2
+    phi = torch.zeros((2 * (m - 1) ** 2, K), dtype=torch.float64, device="cuda:1")
+    xi = torch.zeros((S, K), dtype=torch.float64, device="cuda:0")
+    q = torch.zeros(S, dtype=torch.float64, device="cuda:0")
+    with torch.cuda.device(0):
+        with pytest.raises(mlq.MLQError) as e:
+            mlq.solve_noalloc(m, 0.01, 2, phi, xi, q)
     assert e.value.code == -1
