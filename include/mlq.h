@@ -254,6 +254,21 @@ int mlq_mesh_solve(mlq_mesh *mesh, const mlq_model *model, double dt, int32_t ns
 int mlq_solve(mlq_ctx *ctx, int level, int64_t S, const double *xi, int with_coarse, double *q_fine,
               double *q_coarse, double *y, int32_t *status, int32_t *iters);
 
+/* The field-valued result of a solve: the state at the final time of S
+ * samples (0 <= S <= 65535) on `level`, as mlq_solve computes it (same
+ * kernels, same launch shape, no coarse member).  Sec. 2.4 of the paper lets
+ * the QoI be a functional of the solution; this call returns the solution
+ * itself, the P1 nodal values of v_h(T) and of the recovery variable w(T).
+ * xi: host or device, S x K.  Outputs (host or device; any may be NULL):
+ *   v_out, w_out  S x n FP64, sample-major (v_out[s*n + i], node order of
+ *                 the mesh convention above);
+ *   q_out         S FP64, Q = m^T v(T) (as mlq_solve's q_fine);
+ *   status        S int32 (mlq_sample_status).
+ * A sample that met NaN/Inf stops early and its state is undefined.  Blocks
+ * until the results are written. */
+int mlq_solve_state(mlq_ctx *ctx, int level, int64_t S, const double *xi, double *v_out, double *w_out,
+                    double *q_out, int32_t *status);
+
 /* Multilevel Monte Carlo estimate (eq. StandardML with MC rules) over levels
  * 0..L (L <= 5): level l draws N[l] samples (2 <= N[l] <= 65535) xi[l] (host or device, N[l] x K_l) and
  * contributes the sample mean of Y_l = Q_l - Q_{l-1} (Q_{-1} = 0).  All

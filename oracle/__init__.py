@@ -18,7 +18,7 @@ ctypes loader, numpy wrappers and the estimators of Sec. 4:
 Parity status per function (each is pinned by ``tests/test_oracle_pins.py``
 or, for the fibre frames, point location and eq. PimpedML,
 ``tests/test_oracle_lv.py``):
-  mesh2d, mesh3d, assemble, kl_build, centroid_table, solve, solve_batch,
+  mesh2d, mesh3d, assemble, kl_build, centroid_table, solve, solve_batch, solve_states,
   p1_at_points, centroid_table_unrelated, mc_estimate, mlmc_estimate,
   qmc_estimate, pimped_ml_estimate: pinned.
 """
@@ -291,6 +291,25 @@ def solve_batch(mesh: Mesh, phi: np.ndarray, xi: np.ndarray, dt: float, nsteps: 
                                   w0a.ctypes.data_as(ctypes.c_void_p) if w0a is not None else None, nthreads,
                                   q, it, st) == 0
     return q, it, st
+
+
+def solve_states(mesh: Mesh, phi: np.ndarray, xi: np.ndarray, dt: float, nsteps: int, v0=None, w0=None,
+                 theta_mean=None, model=None, rtol: float = 1e-13):
+    """Final states of S samples, one at a time: theta_e = theta_mean_e +
+    sum_k phi[e, k] xi[s, k] (eq. KLlowrank) and the same block loop as
+    solve().  Returns (Q[S], v[S, n], w[S, n], status[S])."""
+    xi = np.atleast_2d(np.asarray(xi, dtype=np.float64))
+    S = xi.shape[0]
+    q = np.zeros(S)
+    V = np.zeros((S, mesh.n))
+    W = np.zeros((S, mesh.n))
+    st = np.zeros(S, dtype=np.int32)
+    for s in range(S):
+        theta = np.asarray(phi, dtype=np.float64) @ xi[s]
+        if theta_mean is not None:
+            theta = theta + np.asarray(theta_mean, dtype=np.float64)
+        q[s], V[s], W[s], _, st[s] = solve(mesh, theta, dt, nsteps, v0=v0, w0=w0, model=model, rtol=rtol)
+    return q, V, W, st
 
 
 def p1_at_points(mesh: Mesh, f: np.ndarray, pts: np.ndarray, return_location: bool = False):

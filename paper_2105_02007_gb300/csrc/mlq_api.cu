@@ -1263,6 +1263,55 @@ int mlq_solve(mlq_ctx *ctx, int level, int64_t S, const double *xi, int with_coa
     return check_err(ctx);
 }
 
+int mlq_solve_state(mlq_ctx *ctx, int level, int64_t S, const double *xi, double *v_out, double *w_out,
+                    double *q_out, int32_t *status)
+{
+    MLQ_GUARD(ctx);
+    if (!ctx || !xi || S < 0 || S > 65535) return MLQ_EINVAL;
+    if (check_level(ctx, level) != MLQ_OK) return MLQ_EINVAL;
+    if (S == 0) return MLQ_OK;
+    MLQ_CUDA(ctx, cudaSetDevice(ctx->device));
+    ctx->nmembers = 0;
+    const Level &L = ctx->levels[level];
+    const int K = L.K;
+    size_t need = 0;
+    mlq_workspace_bytes(ctx, level, S, 0, &need);
+    int st = ensure_workspace(ctx, need);
+    if (st != MLQ_OK) return st;
+    char *cur = (char *)ctx->ws;
+    Member mf;
+    mf.level = level;
+    mf.S = S;
+    member_carve(ctx, L, mf, cur);
+    cur += align_up((size_t)S * 8, 256) + 256 + align_up((size_t)S * 4, 256);  // as mlq_solve's carve
+    const double *d_xi = xi;
+    if ((st = carve_check(ctx, cur, is_device_ptr(xi) ? 0 : (size_t)S * K * 8)) != MLQ_OK) return st;
+    if (!is_device_ptr(xi)) {
+        double *dx = (double *)cur;
+        MLQ_CUDA(ctx, cudaMemcpyAsync(dx, xi, sizeof(double) * S * K, cudaMemcpyHostToDevice, ctx->stream));
+        d_xi = dx;
+    }
+    mf.d_xi = d_xi;
+    MLQ_CUDA(ctx, cudaEventRecord(ctx->ev_fork, ctx->stream));
+    MLQ_CUDA(ctx, cudaStreamWaitEvent(ctx->pool[0], ctx->ev_fork, 0));
+    if ((st = launch_member(ctx, mf, ctx->pool[0], 0, 0)) != MLQ_OK) return st;
+    MLQ_CUDA(ctx, cudaEventRecord(ctx->ev_join[0], ctx->pool[0]));
+    MLQ_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_join[0], 0));
+    // where the kernels leave the state after the last block: the ring kernels
+    // (multigrid and 3D) keep v_j in buffer j mod kVRing, the others update v
+    // in place; w alternates between two buffers, one per block
+    const size_t SN = (size_t)S * L.n;
+    const bool ring = L.dim == 3 || choose_launch(ctx, L, S).mg;
+    const double *vfin = mf.v + (ring ? (size_t)(L.nsteps % mlq::kVRing) * SN : 0);
+    const double *wfin = mf.w + (size_t)(L.nsteps & 1) * SN;
+    if ((st = copy_out(ctx, v_out, vfin, SN * 8, ctx->stream)) != MLQ_OK) return st;
+    if ((st = copy_out(ctx, w_out, wfin, SN * 8, ctx->stream)) != MLQ_OK) return st;
+    if ((st = copy_out(ctx, q_out, mf.q, S * 8, ctx->stream)) != MLQ_OK) return st;
+    if ((st = copy_out(ctx, status, mf.status, S * 4, ctx->stream)) != MLQ_OK) return st;
+    MLQ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return check_err(ctx);
+}
+
 int mlq_estimate(mlq_ctx *ctx, int L, const int64_t *N, const double *const *xi, double *mean_out,
                  double *var_out, double *rmse_out, double *const *y_out)
 {

@@ -80,6 +80,7 @@ _lib.mlq_mesh_set_kl.argtypes = [_vp, ctypes.c_int, _vp, _vp]
 _lib.mlq_mesh_solve.argtypes = [_vp, _vp, ctypes.c_double, ctypes.c_int32, ctypes.c_double, _vp, _vp, _i64, _vp, _vp,
                                 _vp, _vp]
 _lib.mlq_solve.argtypes = [_vp, ctypes.c_int, _i64, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
+_lib.mlq_solve_state.argtypes = [_vp, ctypes.c_int, _i64, _vp, _vp, _vp, _vp, _vp]
 _lib.mlq_estimate.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.mlq_submit.argtypes = [_vp, _vp, _vp]
 _lib.mlq_poll.argtypes = [_vp, ctypes.c_uint64, _vp]
@@ -102,7 +103,7 @@ _lib.mlq_last_cuda_error.argtypes = [_vp]
 EXPORTED = ["mlq_default_options", "mlq_default_model", "mlq_create", "mlq_destroy", "mlq_set_options",
             "mlq_set_model", "mlq_add_level", "mlq_set_initial_state", "mlq_set_initial_disk", "mlq_set_kl",
             "mlq_build_kl", "mlq_centroid_table", "mlq_build_kl_mesh", "mlq_p1_at_points", "mlq_mesh_create",
-            "mlq_mesh_destroy", "mlq_mesh_set_kl", "mlq_mesh_solve", "mlq_mlmc_allocation", "mlq_solve", "mlq_estimate", "mlq_workspace_bytes",
+            "mlq_mesh_destroy", "mlq_mesh_set_kl", "mlq_mesh_solve", "mlq_mlmc_allocation", "mlq_solve", "mlq_solve_state", "mlq_estimate", "mlq_workspace_bytes",
             "mlq_launch_count", "mlq_level_launch", "mlq_strerror", "mlq_last_cuda_error", "mlq_set_profiling",
             "mlq_member_profile", "mlq_autotune", "mlq_solve_noalloc", "mlq_synthesize", "mlq_submit", "mlq_poll"]
 
@@ -387,6 +388,18 @@ class Context:
         _check(_lib.mlq_solve(self._h, level, S, px, int(bool(with_coarse)), ptrs.get("q_fine"),
                               ptrs.get("q_coarse"), ptrs.get("y"), ptrs.get("status"), ptrs.get("iters")),
                "mlq_solve", self._h)
+        return res
+
+    def solve_state(self, level: int, xi):
+        """Final state of the samples xi (S x K) on `level` (mlq_solve_state):
+        dict of numpy arrays v, w (S x n), q (S) and status (S)."""
+        xk, px = _ptr(xi, np.float64)
+        S = int(xi.shape[0])
+        n = self.levels[level]["n"]
+        res = dict(v=np.zeros((S, n)), w=np.zeros((S, n)), q=np.zeros(S), status=np.zeros(S, dtype=np.int32))
+        _check(_lib.mlq_solve_state(self._h, level, S, px, res["v"].ctypes.data_as(_vp),
+                                    res["w"].ctypes.data_as(_vp), res["q"].ctypes.data_as(_vp),
+                                    res["status"].ctypes.data_as(_vp)), "mlq_solve_state", self._h)
         return res
 
     def estimate(self, xis, return_y: bool = False):

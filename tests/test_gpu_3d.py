@@ -70,6 +70,25 @@ def test_3d_parity(mlq, dims, cluster, prec, precond):
     assert rel(r["q_fine"], q_ref) < TOL[prec]
 
 
+@pytest.mark.parametrize("dims,cluster", [((9, 9, 5), 1), ((17, 17, 5), 4), ((33, 33, 9), 4)])
+@pytest.mark.parametrize("prec,precond", [(0, 0), (1, 0), (1, 1)])
+def test_3d_final_state_parity(mlq, dims, cluster, prec, precond):
+    # the field v_h(T), w(T) node by node against the oracle (relative to max |v|)
+    mesh, phi, xi, v0, w0 = setup3d(dims, 6, 13, 3)
+    nsteps, dt = 10, 0.05
+    q_ref, V, W, st = O.solve_states(mesh, phi, xi, dt, nsteps, v0=v0, w0=w0)
+    assert np.all(st == 0)
+    with mlq.Context(0, prec, cluster=cluster, precond=precond) as ctx:
+        ctx.add_level(0, dims, dt, nsteps)
+        ctx.set_kl(0, phi)
+        ctx.set_initial_disk(0, 0.29)
+        r = ctx.solve_state(0, xi)
+    assert np.all(r["status"] == 0), r["status"]
+    assert rel(r["q"], q_ref) < TOL[prec]
+    assert np.max(np.abs(r["v"] - V)) / np.max(np.abs(V)) < TOL[prec]
+    assert np.max(np.abs(r["w"] - W)) / np.max(np.abs(W)) < TOL[prec]
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_3d_random_state_and_lengths(mlq, prec):
     # a non-default box and a random initial state (every stencil entry and

@@ -66,6 +66,33 @@ def test_c1_full_config_parity(mlq, c1, prec, storage, precond):
     assert np.all(r["iters"] > 0)
 
 
+def field_err(a, b):
+    """max over nodes and samples of |a - b|, relative to max |b|."""
+    return np.max(np.abs(np.asarray(a) - np.asarray(b))) / np.max(np.abs(np.asarray(b)))
+
+
+@pytest.fixture(scope="module")
+def c1_states(c1):
+    q, V, W, st = O.solve_states(c1["mesh"], c1["phi"], c1["xi"], 0.05, 200)
+    assert np.all(st == 0)
+    return dict(q=q, v=V, w=W)
+
+
+@pytest.mark.parametrize("prec,precond,storage", [(0, 0, 0), (0, 0, 2), (1, 0, 0), (1, 1, 0), (1, 0, 2)])
+def test_c1_final_state_parity(mlq, c1, c1_states, prec, precond, storage):
+    # the whole field v_h(T) (and w(T)) node by node, not only Q = m^T v: a
+    # wrong stencil entry, load or reaction term that leaves the integral
+    # nearly unchanged still moves the field
+    with mlq.Context(0, prec, storage=storage, precond=precond) as ctx:
+        ctx.add_level(0, 33, 0.05, 200)
+        ctx.set_kl(0, c1["phi"])
+        r = ctx.solve_state(0, c1["xi"])
+    assert np.all(r["status"] == 0)
+    assert field_err(r["v"], c1_states["v"]) < TOL[prec]
+    assert field_err(r["w"], c1_states["w"]) < TOL[prec]
+    assert rel(r["q"], c1_states["q"]) < TOL[prec]
+
+
 # --------------------------------------------------------------------------
 # Launch shapes: cluster sizes 1..16 with ragged row bands, block sizes,
 # random initial states (every node active), a mean angle field.
@@ -238,19 +265,25 @@ def modes257():
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("m,dt", [(129, 0.0125), (257, 0.00625)])
 def test_full_size_meshes_sampled(mlq, modes257, prec, m, dt, storage):
-    steps = 8 if m == 257 else 16
+    # 12 blocks at 257 x 257: the multigrid path's extrapolated initial guess
+    # reaches its full order (4) from block 9 on, so the window covers it
+    steps = 12 if m == 257 else 16
     fine, modes = modes257
     mesh = fine if m == 257 else O.mesh2d(m)
     phi = O.centroid_table(fine, modes, mesh)
     xi = inputs.gaussian_xi(0, 4, 0, 2, 16)
-    q_ref, _, st = O.solve_batch(mesh, phi, xi, dt, steps, nthreads=2)
+    q_ref, V_ref, W_ref, st = O.solve_states(mesh, phi, xi, dt, steps)
     assert np.all(st == 0)
     with mlq.Context(0, prec, storage=storage) as ctx:
         ctx.add_level(0, m, dt, steps)
         ctx.set_kl(0, phi)
         r = ctx.solve(0, xi)
+        f = ctx.solve_state(0, xi)
     assert np.all(r["status"] == 0)
     assert rel(r["q_fine"], q_ref) < TOL[prec]
+    assert np.array_equal(f["q"], r["q_fine"])
+    assert field_err(f["v"], V_ref) < TOL[prec]
+    assert field_err(f["w"], W_ref) < TOL[prec]
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -431,3 +464,25 @@ def test_multigrid_parity(mlq, m, cluster, steps):
         r = ctx.solve(0, xi)
     assert np.all(r["status"] == 0), r["status"]
     assert rel(r["q_fine"], q_ref) < TOL[1]
+
+
+# --------------------------------------------------------------------------
+# The paper's QMC variant: Halton points (from point 1, skipping the origin)
+# mapped to the uniform KL variables xi = sqrt(3)(2y - 1), through the solver.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [0, 1])
+def test_halton_uniform_points_parity(mlq, prec):
+    m, K, S, dt, nsteps = 33, 8, 16, 0.05, 40
+    mesh = O.mesh2d(m)
+    modes, _ = O.kl_build(mesh, 0.09, 0.04, K)
+    phi = O.centroid_table(mesh, modes, mesh)
+    xi = inputs.uniform_xi(inputs.halton(S, K, first=1))
+    assert np.max(np.abs(xi)) < np.sqrt(3.0)
+    q_ref, _, st = O.solve_batch(mesh, phi, xi, dt, nsteps, nthreads=2)
+    assert np.all(st == 0)
+    with mlq.Context(0, prec) as ctx:
+        ctx.add_level(0, m, dt, nsteps)
+        ctx.set_kl(0, phi)
+        r = ctx.solve(0, xi)
+    assert np.all(r["status"] == 0)
+    assert rel(r["q_fine"], q_ref) < TOL[prec]

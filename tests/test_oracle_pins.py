@@ -418,6 +418,25 @@ def test_batch_equals_single_and_kl_synthesis():
     assert np.all(st == 0) and np.all(it > 0)
 
 
+def test_solve_states_match_batch_and_qoi():
+    # the per-sample field path: the same Q as the batched solver, and Q is
+    # m^T v(T) with m = M 1 from the assembled consistent mass
+    mesh = O.mesh2d(9)
+    modes, _ = O.kl_build(mesh, 0.09, 0.04, 4)
+    phi = O.centroid_table(mesh, modes, mesh)
+    xi = inputs.gaussian_xi(0, 0, 0, 3, 4)
+    tm = np.linspace(-0.2, 0.3, mesh.ne)
+    q, it, st = O.solve_batch(mesh, phi, xi, 0.1, 10, theta_mean=tm, nthreads=2)
+    qs, V, W, st2 = O.solve_states(mesh, phi, xi, 0.1, 10, theta_mean=tm)
+    assert np.all(st2 == 0) and np.all(st == 0)
+    # theta is summed in another order than in the batched C path: rounding only
+    assert np.max(np.abs(qs - q) / np.abs(q)) <= 1e-13
+    rp, ci, mv, _ = O.assemble(mesh)
+    mvec = O.csr_to_dense(rp, ci, mv, mesh.n).sum(axis=1)
+    assert np.allclose(V @ mvec, q, rtol=1e-14, atol=0)
+    assert V.shape == (3, mesh.n) and np.all(np.isfinite(W)) and np.any(W != 0)
+
+
 def test_maxiter_status():
     mesh = O.mesh2d(9)
     q, v, w, it, st = O.solve(mesh, np.zeros(mesh.ne), 0.1, 3, maxit=1)
