@@ -44,17 +44,20 @@ T_END = 10.0
 WORKLOAD = "MLMC 2D monodomain, 5 nested levels 17^2..257^2, N=4096/1024/256/64/16, K=16"
 METRIC = "MLMC DOF-steps/s (time-to-RMSE of one estimate alongside)"
 UNIT = "DOF-steps/s"
-# Algorithmic bytes a memory-streaming implementation of the same solver
-# moves per DOF (2D), each array read or written once per pass:
-#  Jacobi-PCG iteration (FP32): 4 stencil coefficients 16 B + SpMV operand and
-#    result 8 B + vector updates 32 B = 56 B; FP64: 112 B.
-#  multigrid-PCG iteration (FP32): CG updates 44 B, pre-smoothing 12 B,
-#    residual 28 B, restriction 5 B, interpolation 9 B, post-smoothing 28 B,
-#    w = A u 24 B on the fine level (150 B) plus a third of the V-cycle part
-#    for the coarse levels (27 B) = 176 B.
-#  per time block: the reaction / load / FP64 residual pass, ~64 B.
-BYTES_PER_DOF_ITER = {"jacobi": 56.0, "mg": 176.0, "fp64": 112.0}
-BYTES_PER_DOF_STEP = {"jacobi": 64.0, "mg": 64.0, "fp64": 64.0}
+# Algorithmic bytes per DOF (2D) of the scope table's figure for this path: a
+# matrix-free Jacobi-PCG as a memory-streaming solver moves them, each array
+# read or written once per pass: 4 stencil coefficients 16 B + SpMV operand
+# and result 8 B + vector updates 32 B = 56 B per CG iteration in FP32 (112 B
+# in FP64), plus ~64 B per time block (reaction and load, FP64 refinement
+# residual).  These bytes are the roofline's numerator whichever
+# preconditioner runs; the multigrid kernel's own streaming count (one
+# multigrid-PCG iteration: CG updates 44 B, pre-smoothing 12 B, residual 28 B,
+# restriction 5 B, interpolation 9 B, post-smoothing 28 B, w = A u 24 B on the
+# fine level, 150 B, plus a third of that V-cycle part for the coarse levels,
+# 27 B: 176 B) is reported beside it.
+BYTES_PER_DOF_ITER = {"mixed": 56.0, "fp64": 112.0}
+BYTES_PER_DOF_STEP = 64.0
+BYTES_PER_DOF_ITER_MG = 176.0
 
 
 def level_dt(l):
@@ -124,35 +127,104 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # the oracle on the host cores (bounded sample of the same workload)
 # ---------------------------------------------------------------------------
-def oracle_sample(slab_fraction: float, max_samples: int, seed: int = 0):
-    """Run the FP64 CPU oracle on a bounded sample of the workload: per level,
-    the first min(N_l, max_samples) samples of both members over the first
-    ceil(slab_fraction * steps) time blocks.  Returns (DOF-steps/s, seconds,
-    threads used, description)."""
+def _oracle_setup():
     import oracle as O
-    from paper_2105_02007_gb300 import inputs
 
     fine = O.mesh2d(LEVEL_M[-1])
     modes, _ = O.kl_build(fine, SIGMA2, ELL, K_MODES)
     meshes = [O.mesh2d(m) for m in LEVEL_M[:-1]] + [fine]
     phis = [O.centroid_table(fine, modes, mm) for mm in meshes]
+    return O, meshes, phis
+
+
+def oracle_sample(block_fraction: float, seed: int = 0, full_levels=(0, 1), setup=None):
+    """The FP64 CPU oracle on a bounded sample of the workload.  Every level
+    pair l (fine member on mesh l, coarse member on mesh l-1, the same xi)
+    takes its first S = min(N_l, max(16, host threads)) samples, so that every
+    host core has a sample; pairs in `full_levels` run the whole horizon, the
+    others the first ceil(block_fraction * steps) blocks of each member.
+    Per member the oracle's rate is measured, and the whole workload's time
+    is extrapolated member by member (its DOF-steps over the member's rate).
+    Returns a dict: value (DOF-steps/s of the whole workload, extrapolated),
+    sample_value (DOF-steps/s over the sample), seconds, threads, members
+    (level, coarse, mesh level, samples, blocks, q) and a description."""
+    from paper_2105_02007_gb300 import inputs
+
+    O, meshes, phis = setup or _oracle_setup()
     threads = O.max_threads()
-    work = []
+    members = []
+    t_all = 0.0
+    dof_all = 0
+    est_time = 0.0
     for l in range(len(LEVEL_M)):
-        s = min(LEVEL_N[l], max_samples)
-        xi = inputs.gaussian_xi(seed, l, 0, s, K_MODES)
-        for lm in ([l, l - 1] if l > 0 else [l]):
-            steps = max(1, int(np.ceil(slab_fraction * level_steps(lm))))
-            work.append((lm, xi, steps))
-    t0 = time.perf_counter()
-    dof = 0
-    for lm, xi, steps in work:
-        O.solve_batch(meshes[lm], phis[lm], xi, level_dt(lm), steps, nthreads=threads)
-        dof += xi.shape[0] * LEVEL_M[lm] ** 2 * steps
-    el = time.perf_counter() - t0
-    desc = (f"every level's fine and coarse member, first min(N_l,{max_samples}) samples, first "
-            f"{slab_fraction:.3g} of the time blocks (>=1), FP64 CSR Jacobi-PCG, OpenMP over samples")
-    return dof / el, el, threads, desc
+        S = min(LEVEL_N[l], max(16, threads))
+        xi = inputs.gaussian_xi(seed, l, 0, S, K_MODES)
+        for coarse, lm in enumerate([l, l - 1] if l > 0 else [l]):
+            full = level_steps(lm)
+            steps = full if l in full_levels else max(1, int(np.ceil(block_fraction * full)))
+            t0 = time.perf_counter()
+            q, _, _ = O.solve_batch(meshes[lm], phis[lm], xi, level_dt(lm), steps, nthreads=threads)
+            el = time.perf_counter() - t0
+            dof = S * LEVEL_M[lm] ** 2 * steps
+            t_all += el
+            dof_all += dof
+            rate = dof / el
+            est_time += LEVEL_N[l] * LEVEL_M[lm] ** 2 * full / rate
+            members.append(dict(level=l, coarse=coarse, mesh=lm, samples=S, blocks=steps, seconds=el,
+                                rate=rate, q=q, xi=xi))
+    desc = (f"every level pair l, first min(N_l, max(16, threads)) samples of both members; pairs "
+            f"{','.join(str(l) for l in full_levels)} over the whole horizon, the others over the first "
+            f"{block_fraction:.3g} of the time blocks; FP64 CSR Jacobi-PCG, OpenMP over samples; whole-workload "
+            "time extrapolated member by member from the measured rates")
+    return dict(value=dof_steps_per_estimate() / est_time, sample_value=dof_all / t_all, seconds=t_all,
+                threads=threads, members=members, desc=desc, setup=(O, meshes, phis))
+
+
+def oracle_transient_ratio(setup, seed: int = 0):
+    """How far the first blocks of a run misstate the oracle's rate: level 1
+    (33 x 33 nodes, 200 blocks) with one sample per host thread over its
+    first 4 blocks against the whole horizon (rate ratio)."""
+    from paper_2105_02007_gb300 import inputs
+
+    O, meshes, phis = setup
+    threads = O.max_threads()
+    xi = inputs.gaussian_xi(seed, 1, 0, max(16, threads), K_MODES)
+    rates = []
+    for steps in (4, level_steps(1)):
+        t0 = time.perf_counter()
+        O.solve_batch(meshes[1], phis[1], xi, level_dt(1), steps, nthreads=threads)
+        rates.append(xi.shape[0] * LEVEL_M[1] ** 2 * steps / (time.perf_counter() - t0))
+    return rates[0] / rates[1]
+
+
+def oracle_single_thread(setup, block_fraction: float = 0.01, seed: int = 0):
+    """The oracle on one host thread per level (the paper's work measure is
+    single-thread time): one sample over the first ceil(block_fraction *
+    steps) blocks of each level.  DOF-steps/s per level."""
+    from paper_2105_02007_gb300 import inputs
+
+    O, meshes, phis = setup
+    out = []
+    for l in range(len(LEVEL_M)):
+        steps = max(1, int(np.ceil(block_fraction * level_steps(l))))
+        xi = inputs.gaussian_xi(seed, l, 0, 1, K_MODES)
+        t0 = time.perf_counter()
+        O.solve_batch(meshes[l], phis[l], xi, level_dt(l), steps, nthreads=1)
+        out.append(LEVEL_M[l] ** 2 * steps / (time.perf_counter() - t0))
+    return out
+
+
+def gpu_vs_oracle(mlq, prec, sample, phis):
+    """The library on the oracle sample's members (same xi, same blocks):
+    the largest relative difference of the per-sample QoI per member."""
+    out = []
+    with mlq.Context(0, prec) as ctx:
+        for mb in sample["members"]:
+            ctx.add_level(mb["mesh"], LEVEL_M[mb["mesh"]], level_dt(mb["mesh"]), mb["blocks"])
+            ctx.set_kl(mb["mesh"], phis[mb["mesh"]])
+            q = ctx.solve(mb["mesh"], mb["xi"])["q_fine"]
+            out.append(float(np.max(np.abs(q - mb["q"]) / np.abs(mb["q"]))))
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -167,7 +239,8 @@ def load_peaks():
 # the headers holding its code)
 KERNEL_SOURCES = {"slab_solve_mg_kernel": ("mlq_mg.cuh", "mlq_kernels.cuh", "mlq_reg_inst.cu"),
                   "slab_solve_reg_kernel": ("mlq_kernels.cuh", "mlq_reg_inst.cu"),
-                  "slab_solve_kernel": ("mlq_kernels.cuh", "mlq_slab_inst.cu")}
+                  "slab_solve_kernel": ("mlq_kernels.cuh", "mlq_slab_inst.cu"),
+                  "slab_solve_3d_kernel": ("mlq_3d.cuh", "mlq_3d_types.cuh", "mlq_kernels.cuh", "mlq_3d_inst.cu")}
 
 
 def kernel_source_hash(kernel_key: str) -> str:
@@ -208,22 +281,90 @@ def load_traffic(kernel_key: str, samples: int, steps: int):
     return c["dram_bytes"] * (samples * steps) / (c["samples"] * c["steps"])
 
 
+def load_issue(kernel_key: str, member: dict):
+    """Issue-rate ceiling of an on-chip kernel: warp instructions per DOF and
+    CG iteration from an ncu capture (profiles/traffic.json, field "issue",
+    same source hash), scaled to this launch and set against the SM array's
+    issue rate (152 SMs x 4 schedulers x one warp instruction per cycle at
+    the clock of the capture's kernel timing, taken as the maximum SM
+    clock).  None without a current capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        e = json.load(open(path)).get(kernel_key)
+    except Exception:
+        return None
+    if not e or e.get("source_hash") != kernel_source_hash(kernel_key) or "issue" not in e:
+        return None
+    iss = e["issue"]
+    inst = iss["inst_per_dof_iter"] * member["cg_iterations"] * member["nodes"]
+    sec = member["kernel_ms"] / 1000.0
+    peak = iss["sms"] * 4 * iss["sm_mhz"] * 1e6
+    return {"inst": inst, "achieved_inst_per_s": inst / sec, "peak_inst_per_s": peak, "frac": inst / sec / peak,
+            "source": iss.get("source", "ncu smsp__inst_executed.sum")}
+
+
+def roofline_3d(mlq, inputs, peaks):
+    """The 3D member of the configuration's finest level (257 x 257 x 65 Kuhn
+    nodes, 16 samples, one time block of dt = 0.05 / 8, mixed path with the
+    multigrid preconditioner; K = 16 modes on the same mesh, the cost does not
+    depend on K): its kernel's CUDA-event time after one warm-up solve, the
+    algorithmic bytes of the streaming 3D solver (BYTES3D_* per DOF) over that
+    time, and the DRAM traffic of an ncu capture when one is current."""
+    level, S, steps, K = 3, 16, 1, 16
+    dims = LEVEL3_DIMS[level]
+    modes, _ = mlq.build_kl(dims, SIGMA2, ELL3, K)
+    phi = mlq.centroid_table(dims, modes, dims)
+    with mlq.Context(0, mlq.MLQ_MIXED) as ctx:
+        ctx.add_level(level, dims, level3_dt(level), steps)
+        ctx.set_kl(level, phi)
+        ctx.set_profiling(True)
+        xi = inputs.gaussian_xi(0, level, 0, S, K)
+        ctx.solve(level, xi)
+        ctx.solve(level, xi)
+        prof = ctx.member_profile()[0]
+    n = dims[0] * dims[1] * dims[2]
+    it = prof["cg_iterations"]
+    sec = prof["kernel_ms"] / 1e3
+    algo = n * (it * BYTES3D_PER_DOF_ITER["mg"] + S * steps * BYTES3D_PER_DOF_STEP)
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    kname = f"slab_solve_3d_kernel<float,{prof['cluster']}>"
+    traffic = load_traffic(kname, S, steps)
+    out = {"bound": "hbm", "achieved": algo / sec / 1e9, "peak": hbm, "unit": "GB/s", "frac": algo / sec / 1e9 / hbm,
+           "traffic": traffic, "kernel": kname, "kernel_ms": prof["kernel_ms"],
+           "launch": f"{dims[0]}x{dims[1]}x{dims[2]} nodes, {S} samples, {steps} block, {it} CG iterations, "
+                     f"cluster {prof['cluster']}",
+           "bytes": f"{BYTES3D_PER_DOF_ITER['mg']:.0f} B per DOF and CG iteration + {BYTES3D_PER_DOF_STEP:.0f} B "
+                    "per DOF and block (the streaming 3D multigrid PCG, every array once per pass)",
+           "dof_steps_per_s": n * S * steps / sec}
+    if traffic:
+        out["dram_gbs"] = traffic / sec / 1e9
+        out["dram_frac"] = traffic / sec / 1e9 / hbm
+    return out
+
+
 def run_reference(args):
+    """The reference arm: the oracle as it stands on the host cores, every
+    step a bounded sample of the workload (one sample per host thread on every
+    level pair, levels 0-1 over the whole horizon, the first blocks of the
+    others), sized so that warm-up plus timed steps take a few minutes."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    setup = _oracle_setup()
+    frac = 0.01 * min(1.0, 8.0 / max(1, args.warmup + args.steps))
     vals = []
     for k in range(args.warmup + args.steps):
-        rate, el, threads, desc = oracle_sample(1.0 / 400.0, 4, seed=0)
+        smp = oracle_sample(frac, seed=0, setup=setup)
         if k >= args.warmup:
-            vals.append((rate, el))
+            vals.append((smp["value"], smp["seconds"]))
     rate = sum(v[0] for v in vals) / len(vals)
     ms = 1000.0 * sum(v[1] for v in vals) / len(vals)
+    desc = smp["desc"]
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": desc},
-            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": smp["threads"], "kind": "oracle", "sample": desc},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -457,8 +598,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mlq", choices=["mlq", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--fp64-steps", type=int, default=0, help="timed FP64 comparison estimates (0: skip)")
-    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=1,
+                    help="timed plain-FP64 estimates on the same xi (0: skip)")
+    ap.add_argument("--jacobi-steps", type=int, default=1,
+                    help="timed mixed-precision estimates with the Jacobi inner preconditioner, the FP64 path's "
+                         "solver (0: skip)")
+    ap.add_argument("--no-3d", action="store_true", help="skip the 257x257x65 3D member of the line")
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--graphs", action="store_true",
@@ -577,7 +723,7 @@ def main():
         e2e_y = ctx.estimate(xi_pin, return_y=True)[3]
         torch.cuda.synchronize()
         e2e_vals.append(time.perf_counter() - t0)
-    e2e_s = max(e2e_vals) if e2e_vals else None
+    e2e_s = statistics.mean(e2e_vals) if e2e_vals else None
     combined = None
     if dist is not None:
         from paper_2105_02007_gb300 import distributed as D
@@ -595,13 +741,9 @@ def main():
     members = profiles[-1]
     pkey = args.precision
 
-    def solver(d):
-        return "fp64" if pkey == "fp64" else ("mg" if d["resident"] == 3 else "jacobi")
-
-    def alg_bytes(d):
-        k = solver(d)
-        return (d["cg_iterations"] * d["nodes"] * BYTES_PER_DOF_ITER[k]
-                + d["samples"] * d["steps"] * d["nodes"] * BYTES_PER_DOF_STEP[k])
+    def alg_bytes(d, per_iter=None):
+        it = BYTES_PER_DOF_ITER[pkey] if per_iter is None else per_iter
+        return d["nodes"] * (d["cg_iterations"] * it + d["samples"] * d["steps"] * BYTES_PER_DOF_STEP)
 
     k_dom = max(range(len(members)), key=lambda k: alg_bytes(members[k]))
     dom = members[k_dom]
@@ -623,39 +765,83 @@ def main():
                       f"{dom['cg_iterations']} CG iterations, cluster {dom['cluster']}",
             "kernel_ms": dom_ms, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks
             else "fallback 6800 GB/s",
-            "note": (f"algorithmic bytes of a memory-streaming {solver(dom)} PCG "
-                     f"({BYTES_PER_DOF_ITER[solver(dom)]:.0f} B per DOF and CG iteration + "
-                     f"{BYTES_PER_DOF_STEP[solver(dom)]:.0f} B per DOF and block) over the kernel's event time; "
-                     "the kernel keeps its vectors in registers and shared memory, so its DRAM traffic is far "
-                     "below these bytes" if dom["resident"] else "algorithmic bytes over event time")}
+            "bytes": f"{BYTES_PER_DOF_ITER[pkey]:.0f} B per DOF and CG iteration + {BYTES_PER_DOF_STEP:.0f} B per DOF "
+                     "and block (matrix-free Jacobi-PCG streaming figure)",
+            "note": "the kernel keeps its vectors in registers and shared memory (DRAM traffic far below the "
+                    "algorithmic bytes); it is bound by on-chip latency and issue, not by HBM"
+            if dom["resident"] else "algorithmic bytes over event time"}
+    if dom["resident"] == 3:
+        a_mg = alg_bytes(dom, BYTES_PER_DOF_ITER_MG) / (dom_ms / 1000.0) / 1e9
+        roof["streaming_mg"] = {"bytes_per_dof_iter": BYTES_PER_DOF_ITER_MG, "achieved": a_mg, "frac": a_mg / hbm}
+    issue = load_issue(kname, dom)
+    if issue:
+        roof["issue"] = issue
     mean, var, rmse = results[-1]
+    y_mixed = e2e_y if e2e_y is not None else ctx.estimate(xi_dev, return_y=True)[3]
 
-    # ---- plain FP64 on the same inputs, for the same estimate
-    fp64 = None
-    if args.fp64_steps > 0 and prec == mlq.MLQ_MIXED:
-        c64 = make_ctx(mlq.MLQ_FP64)
-        c64.estimate(xi_dev)
-        t64 = []
-        for _ in range(args.fp64_steps):
+    # ---- comparators on the same inputs: the plain FP64 path (FP64 Jacobi-PCG)
+    #      and the mixed path with the same Jacobi preconditioner (precision
+    #      alone); errors of every QoI against the FP64 path
+    def timed_estimates(c, k):
+        c.estimate(xi_dev)
+        t = []
+        for _ in range(k):
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             with torch.cuda.stream(stream):
+                flush.zero_()
                 e0.record(stream)
-                r64 = c64.estimate(xi_dev)
+                r = c.estimate(xi_dev, return_y=True)
                 e1.record(stream)
             e1.synchronize()
-            t64.append(e0.elapsed_time(e1))
-        ms64 = statistics.mean(t64)
-        fp64 = {"value": dof / (ms64 / 1000.0), "unit": UNIT, "ms_per_step": ms64, "estimate": r64[0],
-                "rmse": r64[2], "rel_diff_estimate_vs_mixed": abs(r64[0] - mean) / abs(r64[0]),
-                "mixed_speedup": ms64 / ms}
+            t.append(e0.elapsed_time(e1))
+        return statistics.mean(t), r
+
+    def qoi_errors(ref_mean, ref_y):
+        return {"estimate_rel": abs(mean - ref_mean) / abs(ref_mean),
+                "level_mean_rel": [float(abs(np.mean(a) - np.mean(b)) / abs(np.mean(b))) for a, b in zip(y_mixed, ref_y)],
+                "per_sample_y_max_rel": [float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+                                         for a, b in zip(y_mixed, ref_y)]}
+
+    fp64 = None
+    if args.fp64_steps > 0 and prec == mlq.MLQ_MIXED:
+        c64 = make_ctx(mlq.MLQ_FP64)
+        ms64, r64 = timed_estimates(c64, args.fp64_steps)
         c64.close()
+        fp64 = {"value": dof / (ms64 / 1000.0), "unit": UNIT, "ms_per_step": ms64, "time_to_rmse_s": ms64 / 1000.0,
+                "estimate": r64[0], "rmse": r64[2], "mixed_speedup": ms64 / ms,
+                "solver": "FP64 Jacobi-PCG from v^n, ||r|| <= 1e-13 ||b|| (the oracle's algorithm)",
+                "mixed_error_vs_fp64": qoi_errors(r64[0], r64[3])}
+    jac = None
+    if args.jacobi_steps > 0 and prec == mlq.MLQ_MIXED:
+        cj = make_ctx(mlq.MLQ_MIXED)
+        cj.set_options(precond=0)
+        msj, rj = timed_estimates(cj, args.jacobi_steps)
+        cj.close()
+        jac = {"value": dof / (msj / 1000.0), "unit": UNIT, "ms_per_step": msj, "estimate": rj[0],
+               "solver": "mixed FP32/FP64 Jacobi-PCG (the FP64 path's preconditioner, FP32 inner)",
+               "speedup_over_fp64": (fp64["ms_per_step"] / msj) if fp64 else None}
+
+    # ---- one 3D member (257 x 257 x 65 Kuhn nodes, 16 samples, one block,
+    #      mixed path, multigrid): algorithmic bytes over the kernel's time
+    roof3d = None
+    if not args.no_3d and prec == mlq.MLQ_MIXED:
+        roof3d = roofline_3d(mlq, inputs, peaks)
 
     cpu = None
+    oracle_err = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, el, threads, desc = oracle_sample(1.0 / 50.0, 16)
-        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc, "seconds": el}
+        smp = oracle_sample(0.01)
+        ratio = oracle_transient_ratio(smp["setup"])
+        single = oracle_single_thread(smp["setup"], 0.005)
+        cpu = {"value": smp["value"], "unit": UNIT, "cores": smp["threads"], "kind": "oracle", "sample": smp["desc"],
+               "seconds": smp["seconds"], "sample_value": smp["sample_value"],
+               "first_blocks_over_whole_horizon_rate": ratio,
+               "single_thread_dof_steps_per_s_by_level": single}
+        oracle_err = {"members": [f"pair {m['level']} {'coarse' if m['coarse'] else 'fine'} ({m['blocks']} blocks)"
+                                  for m in smp["members"]],
+                      "per_sample_q_max_rel": gpu_vs_oracle(mlq, prec, smp, phis)}
 
     if rank == 0:
         line = {
@@ -670,9 +856,9 @@ def main():
                        "launch_shapes": {str(l): list(v) for l, v in tuned.items()}},
             "time_to_rmse_s": ms_all / 1000.0, "estimate": mean, "rmse": rmse, "var_l": list(var),
             "e2e": {"value": world * dof / e2e_s if e2e_s else None, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches, "clocks": clk, "roofline": roof,
-            "cpu_baseline": cpu, "fp64": fp64,
+                    "d2h_bytes_per_step": d2h, "steps": len(e2e_vals)},
+            "gpu_launches": launches, "clocks": clk, "roofline": roof, "roofline_3d": roof3d,
+            "cpu_baseline": cpu, "fp64": fp64, "mixed_jacobi": jac, "error_vs_oracle": oracle_err,
             "estimate_all_ranks": None if combined is None else {"estimate": combined[0], "rmse": combined[2],
                                                                   "ranks": world},
             "members": [{k: d[k] for k in ("level", "coarse", "cluster", "threads", "npt", "resident", "samples",
