@@ -599,8 +599,10 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
             [&](int P, int, int, int) {
                 const double vv = vcur[P], ww = wcur[P];
                 Vals<double, 3> o;
-                o.v[0] = vv + dt * (vv * (vv - g.a) * (1.0 - vv) - ww);
-                o.v[1] = ww + dt * g.eps * (vv - g.gam * ww);
+                // FP64 in both paths: the extrapolated guess amplifies the
+                // rounding noise of an FP32 reaction (see reaction())
+                o.v[0] = vv + dt * reaction<false>(vv, ww, g.a);
+                o.v[1] = ww + dt * g.eps * recovery<false>(vv, ww, g.gam);
                 o.v[2] = extrapolate(gp, vv, gp >= 1 ? vm1[P] : 0.0, gp >= 2 ? vm2[P] : 0.0, gp >= 3 ? vm3[P] : 0.0,
                                      gp >= 4 ? v[P] : 0.0);
                 return o;

@@ -103,7 +103,8 @@ __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
 // Cluster-wide sums.
 //
 // Each thread passes NV partial sums in its own precision TA (FP32 in the
-// mixed path).  They are summed over the warp in TA and converted to FP64;
+// mixed path: the thread's own few products).  They are summed over the warp
+// in TA and converted to FP64;
 // warp 0 adds the per-warp values with a butterfly over its lanes (FP64),
 // giving the CTA's total; with CS > 1 the CTA totals are exchanged over DSMEM
 // after a cluster barrier and added with a butterfly over CS lanes.  Every
@@ -117,14 +118,21 @@ template <int NV, int CS, typename TA, typename F>
 __device__ __forceinline__ void cluster_reduce(TA (&v)[NV], double (*wsl)[4], double (*csl)[4], int par, F &&fin)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    // a thread's partial (its own few products) and the warp butterfly in the
+    // thread precision, every sum above the warp in FP64 (widening before the
+    // butterfly measured 6 % more time for the estimate, with the same result
+    // to 2e-14: the sums only set the scalars of the FP32 inner solve, whose
+    // FP64 refinement decides the accuracy)
+    double dv[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        dv[k] = (double)v[k];
     }
     if (lane == 0) {
 #pragma unroll
-        for (int k = 0; k < NV; ++k) wsl[warp][k] = (double)v[k];
+        for (int k = 0; k < NV; ++k) wsl[warp][k] = dv[k];
     }
     __syncthreads();
     double acc[NV];
@@ -159,6 +167,33 @@ __device__ __forceinline__ void cluster_reduce(TA (&v)[NV], double (*wsl)[4], do
         }
     }
     __syncthreads();
+}
+
+// The FitzHugh-Nagumo terms of a time block: the ionic current R(v, w) =
+// v (v - a)(1 - v) - w and the recovery increment v - gam w, added times dt
+// to the FP64 state.  F32 evaluates them in FP32: the increments are O(dt)
+// against O(1) state values, so their rounding moves y and w by ~1e-10
+// absolute per block, and GB300 issues FP64 at 1/64 of the FP32 rate.  The
+// Jacobi kernels of the mixed path (each block starts from v^n) use it; the
+// multigrid kernels keep FP64, because their initial guess extrapolates the
+// last five block solutions with weights of magnitude up to 10 (sum 31),
+// which amplifies that rounding noise into the first residual of every block
+// (measured: twice the CG iterations per block at 257 x 257).
+template <bool F32>
+__device__ __forceinline__ double reaction(double v, double w, double a)
+{
+    if constexpr (F32) {
+        const float vf = (float)v, af = (float)a;
+        return (double)(vf * (vf - af) * (1.0f - vf) - (float)w);
+    } else {
+        return v * (v - a) * (1.0 - v) - w;
+    }
+}
+template <bool F32>
+__device__ __forceinline__ double recovery(double v, double w, double gam)
+{
+    if constexpr (F32) return (double)((float)v - (float)gam * (float)w);
+    else return v - gam * w;
 }
 
 // 1/d in FP64 from an FP32 reciprocal and one Newton-Raphson step
@@ -451,8 +486,7 @@ __global__ void __launch_bounds__(512, 1) slab_solve_kernel(SolveArgs<TI> g)
         double *wnext = wb0 + (wpar ^ 1) * SN;
         for (int node = tile0 + tid; node < tile1; node += nt) {
             const double vv = ldcg(v + node), ww = ldcg(wcur + node);
-            const double Rr = vv * (vv - g.a) * (1.0 - vv) - ww;
-            ytile[node - tile0] = vv + dt * Rr;
+            ytile[node - tile0] = vv + dt * reaction<mixed>(vv, ww, g.a);
         }
         __syncthreads();
         {
@@ -464,7 +498,7 @@ __global__ void __launch_bounds__(512, 1) slab_solve_kernel(SolveArgs<TI> g)
                 const double bb = mass_apply(m, nw.i, nw.j, g.h2, ytile, node - tile0);
                 b[node] = bb;
                 const double vv = v[node], ww = wcur[node];
-                wnext[node] = ww + dt * g.eps * (vv - g.gam * ww);
+                wnext[node] = ww + dt * g.eps * recovery<mixed>(vv, ww, g.gam);
                 const double rr = bb - stencil_apply_global(A64, n, m, node, nw.i, nw.j, v);
                 R[l] = (TI)rr;
                 acc[0] += bb * bb;
@@ -688,13 +722,15 @@ __host__ __device__ inline RegPlan reg_plan(int m, int cs)
 }
 
 // y = v + dt R(v, w) at node q (FP64 state in global memory, through L2)
+template <bool F32 = false>
 __device__ __forceinline__ double load_y(const double *v, const double *w, int q, double dt, double a)
 {
     const double vv = __ldcg(v + q), ww = __ldcg(w + q);
-    return vv + dt * (vv * (vv - a) * (1.0 - vv) - ww);
+    return vv + dt * reaction<F32>(vv, ww, a);
 }
 
 // b_P = (M y)_P with y evaluated at the stencil points (see mass_apply)
+template <bool F32>
 __device__ __forceinline__ double mass_apply_y(int m, int i, int j, double h2, const double *v, const double *w,
                                                int node, double dt, double a)
 {
@@ -702,14 +738,14 @@ __device__ __forceinline__ double mass_apply_y(int m, int i, int j, double h2, c
     const bool cij = (i < mc && j < mc), cim = (i >= 1 && j < mc), cmm = (i >= 1 && j >= 1),
                cjm = (i < mc && j >= 1);
     const int ninc = 2 * cij + cim + 2 * cmm + cjm;
-    double acc = (double)ninc * (h2 / 12.0) * load_y(v, w, node, dt, a);
+    double acc = (double)ninc * (h2 / 12.0) * load_y<F32>(v, w, node, dt, a);
     const double e = h2 / 24.0;
-    if (i + 1 < m) acc += e * (double)(cij + cjm) * load_y(v, w, node + 1, dt, a);
-    if (i > 0) acc += e * (double)(cim + cmm) * load_y(v, w, node - 1, dt, a);
-    if (j + 1 < m) acc += e * (double)(cij + cim) * load_y(v, w, node + m, dt, a);
-    if (j > 0) acc += e * (double)(cjm + cmm) * load_y(v, w, node - m, dt, a);
-    if (i + 1 < m && j + 1 < m) acc += e * (double)(2 * cij) * load_y(v, w, node + m + 1, dt, a);
-    if (i > 0 && j > 0) acc += e * (double)(2 * cmm) * load_y(v, w, node - m - 1, dt, a);
+    if (i + 1 < m) acc += e * (double)(cij + cjm) * load_y<F32>(v, w, node + 1, dt, a);
+    if (i > 0) acc += e * (double)(cim + cmm) * load_y<F32>(v, w, node - 1, dt, a);
+    if (j + 1 < m) acc += e * (double)(cij + cim) * load_y<F32>(v, w, node + m, dt, a);
+    if (j > 0) acc += e * (double)(cjm + cmm) * load_y<F32>(v, w, node - m, dt, a);
+    if (i + 1 < m && j + 1 < m) acc += e * (double)(2 * cij) * load_y<F32>(v, w, node + m + 1, dt, a);
+    if (i > 0 && j > 0) acc += e * (double)(2 * cmm) * load_y<F32>(v, w, node - m - 1, dt, a);
     return acc;
 }
 
@@ -796,10 +832,10 @@ __global__ void __launch_bounds__(NPT >= 12 ? (NPT >= 16 ? 512 : 384) : 512, 1)
             for (int l = tid; l < nown; l += nt) {
                 const int node = own0 + l;
                 const int j = node / m, i = node - j * m;
-                const double bb = mass_apply_y(m, i, j, g.h2, v, wcur, node, dt, g.a);
+                const double bb = mass_apply_y<true>(m, i, j, g.h2, v, wcur, node, dt, g.a);
                 b[node] = bb;
                 const double vv = v[node], ww = wcur[node];
-                wnext[node] = ww + dt * g.eps * (vv - g.gam * ww);
+                wnext[node] = ww + dt * g.eps * recovery<true>(vv, ww, g.gam);
                 const double rr = bb - stencil_apply_global(A64, n, m, node, i, j, v);
                 const float rf = (float)rr;
                 ut[UB + l] = rf;
