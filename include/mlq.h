@@ -269,6 +269,43 @@ int mlq_solve(mlq_ctx *ctx, int level, int64_t S, const double *xi, int with_coa
 int mlq_solve_state(mlq_ctx *ctx, int level, int64_t S, const double *xi, double *v_out, double *w_out,
                     double *q_out, int32_t *status);
 
+/* Point quantities of interest (Sec. 2.4): the action potential u(x_p, t)
+ * and the activation time a(x_p) = min{t in [0, T] : u(x_p, t) >= u_th} at a
+ * few points x_p of a level, formed inside the solver's block loop.
+ *
+ * mlq_set_points: np points (0 <= np <= 32; 0 clears) of `level`, pts host,
+ * np x dim coordinates inside the level's domain (1e-12 slack), and the
+ * threshold u_th.  Each point is located once: the simplex of the mesh
+ * convention holding it (the first of its cell; the cell whose lower corner
+ * is floor(x / h)) and its barycentric weights, so u(x_p, t) is the P1 value
+ * of v_h(t) there.  MLQ_EINVAL for a point outside the domain.
+ *
+ * mlq_solve_points: S samples xi (host or device, S x K) on `level`, the
+ * same kernels and launch shape as mlq_solve.  Outputs (host or device; any
+ * may be NULL):
+ *   trace   S x np x (nsteps + 1) FP64: u(x_p, t_n) at t_n = n dt, n = 0 the
+ *           initial state (NaN after a sample stopped on NaN/Inf);
+ *   act     S x np FP64: a(x_p), with u(x_p, .) linear in time between block
+ *           ends: 0 if u(x_p, 0) >= u_th, else t_{n-1} + dt (u_th - u_{n-1}) /
+ *           (u_n - u_{n-1}) at the first n with u_n >= u_th; -1 if u never
+ *           reaches u_th on [0, T] (the paper's "not activated");
+ *   q_out   S FP64 (Q = m^T v(T), as mlq_solve); status S int32.
+ * MLQ_EINVAL if the level has no points.  Blocks until done. */
+int mlq_set_points(mlq_ctx *ctx, int level, int np, const double *pts, double u_th);
+int mlq_solve_points(mlq_ctx *ctx, int level, int64_t S, const double *xi, double *trace, double *act,
+                     double *q_out, int32_t *status);
+
+/* Host helpers for time quantities of interest (traces u_n at t_n = n dt,
+ * read as the function linear in time between them):
+ * mlq_trace_prolong: the coarse trace (nt_coarse + 1 values, step 2 dt) on the
+ *   fine time grid (2 nt_coarse + 1 values): the intergrid transfer in time
+ *   of Sec. 5 that the level differences of eq. StandardML need.
+ * mlq_time_norms: the L2(0, T) and H1(0, T) norms (eq. point-error, q = 0,
+ *   1) of the linear interpolant of e (nt + 1 values on [0, T]); either
+ *   output may be NULL. */
+int mlq_trace_prolong(int nt_coarse, const double *u_c, double *u_f);
+int mlq_time_norms(int nt, double T, const double *e, double *l2, double *h1);
+
 /* Multilevel Monte Carlo estimate (eq. StandardML with MC rules) over levels
  * 0..L (L <= 5): level l draws N[l] samples (2 <= N[l] <= 65535) xi[l] (host or device, N[l] x K_l) and
  * contributes the sample mean of Y_l = Q_l - Q_{l-1} (Q_{-1} = 0).  All

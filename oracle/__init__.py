@@ -19,6 +19,7 @@ Parity status per function (each is pinned by ``tests/test_oracle_pins.py``
 or, for the fibre frames, point location and eq. PimpedML,
 ``tests/test_oracle_lv.py``):
   mesh2d, mesh3d, assemble, kl_build, centroid_table, solve, solve_batch, solve_states,
+  solve_points, activation_time, time_norms,
   p1_at_points, centroid_table_unrelated, mc_estimate, mlmc_estimate,
   qmc_estimate, pimped_ml_estimate: pinned.
 """
@@ -310,6 +311,67 @@ def solve_states(mesh: Mesh, phi: np.ndarray, xi: np.ndarray, dt: float, nsteps:
             theta = theta + np.asarray(theta_mean, dtype=np.float64)
         q[s], V[s], W[s], _, st[s] = solve(mesh, theta, dt, nsteps, v0=v0, w0=w0, model=model, rtol=rtol)
     return q, V, W, st
+
+
+def activation_time(trace: np.ndarray, dt: float, u_th: float) -> float:
+    """a(x0) = min{t in [0, T] : u(x0, t) >= u_th} (Sec. 2.4, activation
+    map) for the trace u(x0, t_n), t_n = n dt, read as linear in time between
+    the block ends; -1 if the threshold is never reached."""
+    for n, u in enumerate(trace):
+        if u >= u_th:
+            if n == 0:
+                return 0.0
+            up = trace[n - 1]
+            return dt * ((n - 1) + (u_th - up) / (u - up))
+    return -1.0
+
+
+def solve_points(mesh: Mesh, phi: np.ndarray, xi: np.ndarray, dt: float, nsteps: int, pts: np.ndarray,
+                 u_th: float, v0=None, w0=None, theta_mean=None, model=None, rtol: float = 1e-13):
+    """Point QoIs of Sec. 2.4 for S samples: the action potential u(x_p, t_n)
+    (the P1 interpolant of v_h(t_n) at x_p) after every time block, n = 0..nsteps,
+    and the activation time of each trace.  The blocks run one solve() call
+    each from the state the last one left, so the arithmetic is that of
+    solve().  Returns (trace[S, np, nsteps+1], act[S, np], Q[S], status[S])."""
+    xi = np.atleast_2d(np.asarray(xi, dtype=np.float64))
+    pts = np.atleast_2d(np.asarray(pts, dtype=np.float64))
+    S, npts = xi.shape[0], pts.shape[0]
+    trace = np.zeros((S, npts, nsteps + 1))
+    act = np.zeros((S, npts))
+    q = np.zeros(S)
+    st = np.zeros(S, dtype=np.int32)
+    if v0 is None:
+        v0, w0 = initial_state(mesh)
+    for s in range(S):
+        theta = np.asarray(phi, dtype=np.float64) @ xi[s]
+        if theta_mean is not None:
+            theta = theta + np.asarray(theta_mean, dtype=np.float64)
+        v = np.array(v0, dtype=np.float64)
+        w = np.zeros(mesh.n) if w0 is None else np.array(w0, dtype=np.float64)
+        trace[s, :, 0] = p1_at_points(mesh, v[:, None], pts)[:, 0]
+        for n in range(1, nsteps + 1):
+            q[s], v, w, _, sst = solve(mesh, theta, dt, 1, v0=v, w0=w, model=model, rtol=rtol)
+            st[s] = max(st[s], sst)
+            trace[s, :, n] = p1_at_points(mesh, v[:, None], pts)[:, 0]
+        if nsteps == 0:
+            q[s] = solve(mesh, theta, dt, 0, v0=v, w0=w, model=model, rtol=rtol)[0]
+        for p in range(npts):
+            act[s, p] = activation_time(trace[s, p], dt, u_th)
+    return trace, act, q, st
+
+
+def time_norms(e: np.ndarray, T: float):
+    """L2(0, T) and H1(0, T) norms (eq. point-error, q = 0 and 1) of the
+    function linear between the values e_n at t_n = n T / nt.  Each step's
+    integral of e^2 by Simpson's rule (exact for the quadratic e^2 there), of
+    e'^2 as the constant slope squared times the step."""
+    e = np.asarray(e, dtype=np.float64)
+    nt = e.size - 1
+    dt = T / nt
+    mid = 0.5 * (e[:-1] + e[1:])
+    l2sq = float(np.sum(dt / 6.0 * (e[:-1] ** 2 + 4.0 * mid ** 2 + e[1:] ** 2)))
+    h1sq = float(np.sum(((e[1:] - e[:-1]) / dt) ** 2 * dt))
+    return np.sqrt(l2sq), np.sqrt(l2sq + h1sq)
 
 
 def p1_at_points(mesh: Mesh, f: np.ndarray, pts: np.ndarray, return_location: bool = False):

@@ -407,6 +407,9 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
             wb0[P] = s0.v[1];
         });
     cl.sync();
+    PointState pst;
+    const bool pth = rank == 0 && tid < g.pq.npts;   // point QoI threads
+    if (pth) point_record(g.pq, sample, g.nsteps, g.dt, vb0, pst);
 
     int wpar = 0, par = 0;
     int64_t total_iters = 0;
@@ -827,7 +830,9 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
             break;
         }
         if (!solved && status == S_CONVERGED) status = S_MAXITER;
+        if (pth) point_record(g.pq, sample, g.nsteps, dt, v, pst);
     }
+    if (pth) point_finish(g.pq, sample, g.nsteps, pst);
 
     double qacc[1] = {0.0};
     const double *vfin = vring(g.nsteps);   // solution of the last block

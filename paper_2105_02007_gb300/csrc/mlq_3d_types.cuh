@@ -5,6 +5,8 @@
 
 #include <cstdint>
 
+#include "mlq_points.cuh"
+
 namespace mlq {
 
 constexpr int kSlots3D = 9;  // diagonal, seven couplings, 1 / diagonal
@@ -122,6 +124,7 @@ struct Solve3Args {
     double *q;
     int32_t *iters, *status;
     Mg3Args mg;                   // nl > 1: multigrid preconditioner (FP32 inner only)
+    PointArgs pq;                 // point QoIs (npts = 0: none)
 };
 
 }  // namespace mlq

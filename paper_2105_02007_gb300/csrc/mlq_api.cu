@@ -56,6 +56,11 @@ struct Level {
     mlq::Grid3 g3{};
     double Lx = 1.0, Ly = 1.0, Lz = 0.25;
     double *d_M3 = nullptr, *d_lump = nullptr;
+    // point QoIs (mlq_set_points): simplex nodes and barycentric weights
+    int npts = 0;
+    double u_th = 0.0;
+    int *d_pt_node = nullptr;      // [npts][4]
+    double *d_pt_w = nullptr;      // [npts][4]
 };
 
 struct Member {
@@ -69,6 +74,7 @@ struct Member {
     float *mgA[mlq::kMgMaxLevels] = {};    // coarse-level stencils (multigrid)
     mlq::D3 *mgD[mlq::kMgMaxLevels] = {};  // coarse-level mean conductivities
     float *mg3v[mlq::kMg3MaxLevels][4] = {};  // 3D multigrid work vectors xa, xb, rr, bb
+    mlq::PointArgs pq{};   // point QoIs of this member (npts = 0: none)
 };
 
 // 3D multigrid in use for a level (FP32 inner path)
@@ -642,6 +648,7 @@ int launch_member3d_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream
     a.q = mb.q;
     a.iters = mb.iters;
     a.status = mb.status;
+    a.pq = mb.pq;
     a.mg.nl = 1;
     if (uses_mg3(ctx, L)) {
         a.mg.nl = mlq::mg3_hierarchy(L.g3, a.mg.g, mlq::kMg3MaxLevels);
@@ -718,6 +725,7 @@ int launch_member_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream_t
     a.q = mb.q;
     a.iters = mb.iters;
     a.status = mb.status;
+    a.pq = mb.pq;
     const Shape sh = choose_launch(ctx, L, mb.S);
     if (ctx->opt.storage == 1 && !sh.resident) return MLQ_EUNSUPPORTED;
     const bool timed = ctx->profile && slot >= 0 && slot < kStreams;
@@ -979,6 +987,8 @@ int mlq_destroy(mlq_ctx *ctx)
         cudaFree(L.d_w0);
         cudaFree(L.d_M3);
         cudaFree(L.d_lump);
+        cudaFree(L.d_pt_node);
+        cudaFree(L.d_pt_w);
     }
     cudaFree(ctx->ws);
     delete ctx;
@@ -1031,6 +1041,8 @@ int mlq_add_level(mlq_ctx *ctx, int level, int dim, const int32_t *dims, const d
     cudaFree(L.d_w0);
     cudaFree(L.d_M3);
     cudaFree(L.d_lump);
+    cudaFree(L.d_pt_node);
+    cudaFree(L.d_pt_w);
     L = Level();
     if (dim == 3) {
         L.dim = 3;
@@ -1306,6 +1318,154 @@ int mlq_solve_state(mlq_ctx *ctx, int level, int64_t S, const double *xi, double
     const double *wfin = mf.w + (size_t)(L.nsteps & 1) * SN;
     if ((st = copy_out(ctx, v_out, vfin, SN * 8, ctx->stream)) != MLQ_OK) return st;
     if ((st = copy_out(ctx, w_out, wfin, SN * 8, ctx->stream)) != MLQ_OK) return st;
+    if ((st = copy_out(ctx, q_out, mf.q, S * 8, ctx->stream)) != MLQ_OK) return st;
+    if ((st = copy_out(ctx, status, mf.status, S * 4, ctx->stream)) != MLQ_OK) return st;
+    MLQ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return check_err(ctx);
+}
+
+}  // extern "C"
+
+namespace {
+
+// The simplex of a structured level holding point x and the point's
+// barycentric weights there (nodes [4], weights [4]; 2D: the 4th entry
+// repeats node 0 with weight 0).  The cell is the one whose lower corner is
+// floor(x / h) (clamped to the mesh), the simplex the first of the cell, in
+// the mesh convention's order, that contains the point.  false if x lies
+// outside the domain by more than 1e-12 of its extent.
+bool locate_point(const Level &L, const double *x, int *node, double *w)
+{
+    if (L.dim == 2) {
+        const int m = L.m;
+        const double f[2] = {x[0] / L.h, x[1] / L.h};
+        int c[2];
+        double t[2];
+        for (int a = 0; a < 2; ++a) {
+            if (!(x[a] >= -1e-12 && x[a] <= 1.0 + 1e-12)) return false;
+            c[a] = std::min(std::max((int)std::floor(f[a]), 0), m - 2);
+            t[a] = std::min(std::max(f[a] - c[a], 0.0), 1.0);
+        }
+        const int n00 = c[0] + m * c[1];
+        if (t[1] <= t[0]) {   // element 2c: (i,j) (i+1,j) (i+1,j+1)
+            node[0] = n00; node[1] = n00 + 1; node[2] = n00 + m + 1;
+            w[0] = 1.0 - t[0]; w[1] = t[0] - t[1]; w[2] = t[1];
+        } else {              // element 2c+1: (i,j) (i+1,j+1) (i,j+1)
+            node[0] = n00; node[1] = n00 + m + 1; node[2] = n00 + m;
+            w[0] = 1.0 - t[1]; w[1] = t[0]; w[2] = t[1] - t[0];
+        }
+        node[3] = n00;
+        w[3] = 0.0;
+        return true;
+    }
+    const mlq::Grid3 &g = L.g3;
+    const int mm[3] = {g.mx, g.my, g.mz};
+    const double len[3] = {L.Lx, L.Ly, L.Lz}, hh[3] = {g.hx, g.hy, g.hz};
+    int c[3];
+    double t[3];
+    for (int a = 0; a < 3; ++a) {
+        if (!(x[a] >= -1e-12 * len[a] && x[a] <= len[a] * (1.0 + 1e-12))) return false;
+        const double f = x[a] / hh[a];
+        c[a] = std::min(std::max((int)std::floor(f), 0), mm[a] - 2);
+        t[a] = std::min(std::max(f - c[a], 0.0), 1.0);
+    }
+    // tetrahedron s of the cell holds the points whose local coordinates fall
+    // along its step axes: t[a0] >= t[a1] >= t[a2]
+    int s = 0;
+    for (; s < 6; ++s) {
+        const int a0 = mlq::kuhn_axis(s, 0), a1 = mlq::kuhn_axis(s, 1), a2 = mlq::kuhn_axis(s, 2);
+        if (t[a0] >= t[a1] && t[a1] >= t[a2]) break;
+    }
+    const int a0 = mlq::kuhn_axis(s, 0), a1 = mlq::kuhn_axis(s, 1), a2 = mlq::kuhn_axis(s, 2);
+    const double lam[4] = {1.0 - t[a0], t[a0] - t[a1], t[a1] - t[a2], t[a2]};
+    for (int q = 0; q < 4; ++q) {
+        const int msk = mlq::kuhn_vertex(s, q);
+        node[q] = (c[0] + (msk & 1)) + g.mx * ((c[1] + ((msk >> 1) & 1)) + g.my * (c[2] + ((msk >> 2) & 1)));
+        w[q] = lam[q];
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mlq_set_points(mlq_ctx *ctx, int level, int np, const double *pts, double u_th)
+{
+    MLQ_GUARD(ctx);
+    if (!ctx || level < 0 || level >= kMaxLevels || !ctx->levels[level].defined) return MLQ_EINVAL;
+    if (np < 0 || np > mlq::kMaxPoints || (np > 0 && !pts) || !std::isfinite(u_th)) return MLQ_EINVAL;
+    Level &L = ctx->levels[level];
+    std::vector<int> nd(4 * (size_t)std::max(np, 1));
+    std::vector<double> wt(4 * (size_t)std::max(np, 1));
+    for (int p = 0; p < np; ++p)
+        if (!locate_point(L, pts + (size_t)p * L.dim, &nd[4 * p], &wt[4 * p])) return MLQ_EINVAL;
+    MLQ_CUDA(ctx, cudaSetDevice(ctx->device));
+    MLQ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaFree(L.d_pt_node);
+    cudaFree(L.d_pt_w);
+    L.d_pt_node = nullptr;
+    L.d_pt_w = nullptr;
+    L.npts = 0;
+    if (np == 0) return MLQ_OK;
+    MLQ_CUDA(ctx, cudaMalloc(&L.d_pt_node, sizeof(int) * 4 * (size_t)np));
+    MLQ_CUDA(ctx, cudaMalloc(&L.d_pt_w, sizeof(double) * 4 * (size_t)np));
+    MLQ_CUDA(ctx, cudaMemcpy(L.d_pt_node, nd.data(), sizeof(int) * 4 * (size_t)np, cudaMemcpyHostToDevice));
+    MLQ_CUDA(ctx, cudaMemcpy(L.d_pt_w, wt.data(), sizeof(double) * 4 * (size_t)np, cudaMemcpyHostToDevice));
+    L.npts = np;
+    L.u_th = u_th;
+    return MLQ_OK;
+}
+
+int mlq_solve_points(mlq_ctx *ctx, int level, int64_t S, const double *xi, double *trace, double *act,
+                     double *q_out, int32_t *status)
+{
+    MLQ_GUARD(ctx);
+    if (!ctx || !xi || S < 0 || S > 65535) return MLQ_EINVAL;
+    if (check_level(ctx, level) != MLQ_OK || ctx->levels[level].npts < 1) return MLQ_EINVAL;
+    if (S == 0) return MLQ_OK;
+    MLQ_CUDA(ctx, cudaSetDevice(ctx->device));
+    ctx->nmembers = 0;
+    const Level &L = ctx->levels[level];
+    const int K = L.K, np = L.npts;
+    const size_t tr_bytes = align_up((size_t)S * np * (L.nsteps + 1) * 8, 256);
+    const size_t ac_bytes = align_up((size_t)S * np * 8, 256);
+    size_t need = 0;
+    mlq_workspace_bytes(ctx, level, S, 0, &need);
+    int st = ensure_workspace(ctx, need + tr_bytes + ac_bytes);
+    if (st != MLQ_OK) return st;
+    char *cur = (char *)ctx->ws;
+    Member mf;
+    mf.level = level;
+    mf.S = S;
+    member_carve(ctx, L, mf, cur);
+    cur += align_up((size_t)S * 8, 256) + 256 + align_up((size_t)S * 4, 256);  // as mlq_solve's carve
+    const double *d_xi = xi;
+    const size_t xi_bytes = is_device_ptr(xi) ? 0 : align_up((size_t)S * K * 8, 256);
+    if ((st = carve_check(ctx, cur, xi_bytes + tr_bytes + ac_bytes)) != MLQ_OK) return st;
+    if (xi_bytes) {
+        double *dx = (double *)cur;
+        cur += xi_bytes;
+        MLQ_CUDA(ctx, cudaMemcpyAsync(dx, xi, sizeof(double) * S * K, cudaMemcpyHostToDevice, ctx->stream));
+        d_xi = dx;
+    }
+    double *d_tr = (double *)cur;
+    cur += tr_bytes;
+    double *d_act = (double *)cur;
+    mf.d_xi = d_xi;
+    mf.pq.npts = np;
+    mf.pq.node = L.d_pt_node;
+    mf.pq.w = L.d_pt_w;
+    mf.pq.u_th = L.u_th;
+    mf.pq.trace = d_tr;
+    mf.pq.act = d_act;
+    MLQ_CUDA(ctx, cudaEventRecord(ctx->ev_fork, ctx->stream));
+    MLQ_CUDA(ctx, cudaStreamWaitEvent(ctx->pool[0], ctx->ev_fork, 0));
+    if ((st = launch_member(ctx, mf, ctx->pool[0], 0, 0)) != MLQ_OK) return st;
+    MLQ_CUDA(ctx, cudaEventRecord(ctx->ev_join[0], ctx->pool[0]));
+    MLQ_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_join[0], 0));
+    if ((st = copy_out(ctx, trace, d_tr, (size_t)S * np * (L.nsteps + 1) * 8, ctx->stream)) != MLQ_OK) return st;
+    if ((st = copy_out(ctx, act, d_act, (size_t)S * np * 8, ctx->stream)) != MLQ_OK) return st;
     if ((st = copy_out(ctx, q_out, mf.q, S * 8, ctx->stream)) != MLQ_OK) return st;
     if ((st = copy_out(ctx, status, mf.status, S * 4, ctx->stream)) != MLQ_OK) return st;
     MLQ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));

@@ -28,3 +28,40 @@ extern "C" int mlq_mlmc_allocation(int L, const double *var, const double *cost,
     }
     return MLQ_OK;
 }
+
+// Time quantities of interest (the action potential u(x_0, t) of Sec. 2.4):
+// a trace on level l holds u at the block ends t_n = n dt_l, n = 0..nt, and
+// is read as the function linear in time between them.  The level difference
+// of eq. StandardML for such a QoI needs the coarse trace on the fine time
+// grid (dt_l = dt_{l-1} / 2): the tensor-product intergrid transfer of
+// Sec. 5, here in time alone, is linear interpolation, which keeps the coarse
+// values at the even fine times and puts the mean of the two neighbours at
+// the odd ones.
+extern "C" int mlq_trace_prolong(int nt_coarse, const double *u_c, double *u_f)
+{
+    if (nt_coarse < 0 || !u_c || !u_f) return MLQ_EINVAL;
+    for (int n = 0; n <= nt_coarse; ++n) {
+        u_f[2 * n] = u_c[n];
+        if (n < nt_coarse) u_f[2 * n + 1] = 0.5 * (u_c[n] + u_c[n + 1]);
+    }
+    return MLQ_OK;
+}
+
+// Norms on (0, T) of the function e linear between e_n at t_n = n T / nt
+// (eq. point-error with q = 0 and q = 1): ||e||_{L2}^2 = sum over the steps
+// of dt (e_n^2 + e_n e_{n+1} + e_{n+1}^2) / 3, the H1 seminorm squared
+// sum (e_{n+1} - e_n)^2 / dt, and ||e||_{H1}^2 their sum.
+extern "C" int mlq_time_norms(int nt, double T, const double *e, double *l2, double *h1)
+{
+    if (nt < 1 || !(T > 0.0) || !e) return MLQ_EINVAL;
+    const double dt = T / nt;
+    double a = 0.0, b = 0.0;
+    for (int n = 0; n < nt; ++n) {
+        a += dt * (e[n] * e[n] + e[n] * e[n + 1] + e[n + 1] * e[n + 1]) / 3.0;
+        const double d = e[n + 1] - e[n];
+        b += d * d / dt;
+    }
+    if (l2) *l2 = std::sqrt(a);
+    if (h1) *h1 = std::sqrt(a + b);
+    return MLQ_OK;
+}

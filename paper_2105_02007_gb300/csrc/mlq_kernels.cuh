@@ -11,6 +11,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "mlq_points.cuh"
+
 namespace cg = cooperative_groups;
 
 namespace mlq {
@@ -94,6 +96,7 @@ struct SolveArgs {
     int S;
     double *q;                    // [S]
     int32_t *iters, *status;      // [S]
+    PointArgs pq;                 // point QoIs (npts = 0: none)
 };
 
 template <typename T>
@@ -473,6 +476,9 @@ __global__ void __launch_bounds__(512, 1) slab_solve_kernel(SolveArgs<TI> g)
         wb0[node] = w0;
     }
     cl.sync();
+    PointState pst;
+    const bool pth = rank == 0 && tid < g.pq.npts;   // point QoI threads
+    if (pth) point_record(g.pq, sample, g.nsteps, g.dt, v, pst);
 
     int wpar = 0;
     int64_t total_iters = 0;     // thread 0's count
@@ -660,7 +666,9 @@ __global__ void __launch_bounds__(512, 1) slab_solve_kernel(SolveArgs<TI> g)
             break;
         }
         if (!solved && status == S_CONVERGED) status = S_MAXITER;
+        if (pth) point_record(g.pq, sample, g.nsteps, dt, v, pst);
     }
+    if (pth) point_finish(g.pq, sample, g.nsteps, pst);
 
     double qacc[1] = {0.0};
     {
@@ -812,6 +820,9 @@ __global__ void __launch_bounds__(NPT >= 12 ? (NPT >= 16 ? 512 : 384) : 512, 1)
         wb0[node] = w0;
     }
     cl.sync();
+    PointState pst;
+    const bool pth = rank == 0 && tid < g.pq.npts;   // point QoI threads
+    if (pth) point_record(g.pq, sample, g.nsteps, g.dt, v, pst);
 
     float r[NPT], w[NPT], sv[NPT], p[NPT], x[NPT];
     int wpar = 0, par = 0;
@@ -1052,7 +1063,9 @@ __global__ void __launch_bounds__(NPT >= 12 ? (NPT >= 16 ? 512 : 384) : 512, 1)
             break;
         }
         if (!solved && status == S_CONVERGED) status = S_MAXITER;
+        if (pth) point_record(g.pq, sample, g.nsteps, dt, v, pst);
     }
+    if (pth) point_finish(g.pq, sample, g.nsteps, pst);
 
     double qacc[1] = {0.0};
     for (int node = own0 + tid; node < own1; node += nt) {

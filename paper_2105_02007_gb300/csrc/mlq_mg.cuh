@@ -331,6 +331,9 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1)
         wb0[node] = w0;
     }
     cl.sync();
+    PointState pst;
+    const bool pth = rank == 0 && tid < g.pq.npts;   // point QoI threads
+    if (pth) point_record(g.pq, sample, g.nsteps, g.dt, vb0, pst);
 
     // ---- helpers ----------------------------------------------------------
     // barrier after the rows of a level were written (and pushed)
@@ -725,7 +728,9 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1)
             break;
         }
         if (!solved && status == S_CONVERGED) status = S_MAXITER;
+        if (pth) point_record(g.pq, sample, g.nsteps, dt, v, pst);
     }
+    if (pth) point_finish(g.pq, sample, g.nsteps, pst);
 
     const double *vfin = vring(g.nsteps);   // solution of the last block
     double qacc[1] = {0.0};

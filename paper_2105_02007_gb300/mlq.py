@@ -81,6 +81,10 @@ _lib.mlq_mesh_solve.argtypes = [_vp, _vp, ctypes.c_double, ctypes.c_int32, ctype
                                 _vp, _vp]
 _lib.mlq_solve.argtypes = [_vp, ctypes.c_int, _i64, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
 _lib.mlq_solve_state.argtypes = [_vp, ctypes.c_int, _i64, _vp, _vp, _vp, _vp, _vp]
+_lib.mlq_set_points.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_double]
+_lib.mlq_solve_points.argtypes = [_vp, ctypes.c_int, _i64, _vp, _vp, _vp, _vp, _vp]
+_lib.mlq_trace_prolong.argtypes = [ctypes.c_int, _vp, _vp]
+_lib.mlq_time_norms.argtypes = [ctypes.c_int, ctypes.c_double, _vp, _vp, _vp]
 _lib.mlq_estimate.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.mlq_submit.argtypes = [_vp, _vp, _vp]
 _lib.mlq_poll.argtypes = [_vp, ctypes.c_uint64, _vp]
@@ -103,7 +107,8 @@ _lib.mlq_last_cuda_error.argtypes = [_vp]
 EXPORTED = ["mlq_default_options", "mlq_default_model", "mlq_create", "mlq_destroy", "mlq_set_options",
             "mlq_set_model", "mlq_add_level", "mlq_set_initial_state", "mlq_set_initial_disk", "mlq_set_kl",
             "mlq_build_kl", "mlq_centroid_table", "mlq_build_kl_mesh", "mlq_p1_at_points", "mlq_mesh_create",
-            "mlq_mesh_destroy", "mlq_mesh_set_kl", "mlq_mesh_solve", "mlq_mlmc_allocation", "mlq_solve", "mlq_solve_state", "mlq_estimate", "mlq_workspace_bytes",
+            "mlq_mesh_destroy", "mlq_mesh_set_kl", "mlq_mesh_solve", "mlq_mlmc_allocation", "mlq_solve", "mlq_solve_state", "mlq_set_points", "mlq_solve_points", "mlq_trace_prolong",
+            "mlq_time_norms", "mlq_estimate", "mlq_workspace_bytes",
             "mlq_launch_count", "mlq_level_launch", "mlq_strerror", "mlq_last_cuda_error", "mlq_set_profiling",
             "mlq_member_profile", "mlq_autotune", "mlq_solve_noalloc", "mlq_synthesize", "mlq_submit", "mlq_poll"]
 
@@ -402,6 +407,29 @@ class Context:
                                     res["status"].ctypes.data_as(_vp)), "mlq_solve_state", self._h)
         return res
 
+    def set_points(self, level: int, pts, u_th: float):
+        """Point QoIs of `level` at pts (np x dim) with threshold u_th (mlq_set_points)."""
+        p = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3 if isinstance(self.levels[level]["m"],
+                                                                                    (tuple, list)) else 2)
+        _check(_lib.mlq_set_points(self._h, level, p.shape[0], p.ctypes.data_as(_vp) if p.size else None,
+                                   float(u_th)), "mlq_set_points", self._h)
+        self.levels[level]["npts"] = p.shape[0]
+
+    def solve_points(self, level: int, xi):
+        """Traces and activation times of the samples xi (S x K) on `level`
+        (mlq_solve_points): dict of numpy arrays trace (S, np, nsteps + 1),
+        act (S, np), q (S), status (S)."""
+        xk, px = _ptr(xi, np.float64)
+        S = int(xi.shape[0])
+        L = self.levels[level]
+        npts, nt = L["npts"], L["nsteps"]
+        res = dict(trace=np.zeros((S, npts, nt + 1)), act=np.zeros((S, npts)), q=np.zeros(S),
+                   status=np.zeros(S, dtype=np.int32))
+        _check(_lib.mlq_solve_points(self._h, level, S, px, res["trace"].ctypes.data_as(_vp),
+                                     res["act"].ctypes.data_as(_vp), res["q"].ctypes.data_as(_vp),
+                                     res["status"].ctypes.data_as(_vp)), "mlq_solve_points", self._h)
+        return res
+
     def estimate(self, xis, return_y: bool = False):
         """MLMC over levels 0..L with xis[l] (N_l x K).  Returns (mean,
         var_l, rmse[, y_l])."""
@@ -499,3 +527,21 @@ class Context:
         _check(_lib.mlq_level_launch(self._h, level, ctypes.byref(c), ctypes.byref(t), ctypes.byref(r)),
                "mlq_level_launch")
         return (c.value, t.value, r.value) if with_resident else (c.value, t.value)
+
+
+def trace_prolong(u_c):
+    """Coarse trace on the fine time grid (mlq_trace_prolong)."""
+    u = np.ascontiguousarray(u_c, dtype=np.float64)
+    out = np.zeros(2 * (u.size - 1) + 1)
+    _check(_lib.mlq_trace_prolong(u.size - 1, u.ctypes.data_as(_vp), out.ctypes.data_as(_vp)), "mlq_trace_prolong")
+    return out
+
+
+def time_norms(e, T: float):
+    """(L2(0,T), H1(0,T)) norms of the linear interpolant of e (mlq_time_norms)."""
+    a = np.ascontiguousarray(e, dtype=np.float64)
+    l2 = ctypes.c_double()
+    h1 = ctypes.c_double()
+    _check(_lib.mlq_time_norms(a.size - 1, float(T), a.ctypes.data_as(_vp), ctypes.byref(l2), ctypes.byref(h1)),
+           "mlq_time_norms")
+    return l2.value, h1.value

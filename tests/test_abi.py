@@ -183,3 +183,23 @@ def test_mlmc_allocation_is_the_constrained_optimum(mlq):
     for bad in (dict(var=[-1.0], cost=[1.0]), dict(var=[1.0], cost=[0.0])):
         with pytest.raises(mlq.MLQError):
             mlq.mlmc_allocation(bad["var"], bad["cost"], 1e-3)
+
+
+def test_trace_helpers_match_oracle(mlq):
+    # time QoIs: the library's L2/H1(0,T) norms against the oracle's
+    # quadrature, and the time prolongation keeps the coarse values and is
+    # exact on linear functions
+    rng = np.random.default_rng(9)
+    e = rng.normal(size=41)
+    for T in (1.0, 10.0):
+        a = mlq.time_norms(e, T)
+        b = O.time_norms(e, T)
+        assert abs(a[0] - b[0]) <= 1e-13 * b[0] and abs(a[1] - b[1]) <= 1e-13 * b[1]
+    uc = rng.normal(size=11)
+    uf = mlq.trace_prolong(uc)
+    assert uf.size == 21 and np.array_equal(uf[::2], uc)
+    lin = 0.25 + 0.5 * np.arange(11.0)
+    assert np.allclose(mlq.trace_prolong(lin), 0.25 + 0.25 * np.arange(21.0), rtol=0, atol=1e-15)
+    # the prolonged coarse trace minus itself is zero in H1 (the level
+    # difference of a constant-in-level trace)
+    assert mlq.time_norms(mlq.trace_prolong(uc) - np.interp(np.arange(21) / 2.0, np.arange(11.0), uc), 1.0)[1] < 1e-14

@@ -492,3 +492,91 @@ def test_cube_level_table_counts():
             assert np.allclose(vol, h ** 3 / 6.0, rtol=1e-12)
         assert cubes * int(round(T / dt)) == int(dof)
         assert int(dof) == 2 ** (4 * (l + 1))
+
+
+# --------------------------------------------------------------------------
+# point QoIs of Sec. 2.4: action potential traces and activation times
+# --------------------------------------------------------------------------
+def test_activation_time_definition_on_hand_traces():
+    dt, th = 0.1, 0.5
+    assert O.activation_time(np.array([0.0, 0.2, 0.6, 0.9]), dt, th) == pytest.approx(0.1 + 0.1 * 0.3 / 0.4, abs=1e-15)
+    assert O.activation_time(np.array([0.7, 0.2]), dt, th) == 0.0
+    assert O.activation_time(np.array([0.0, 0.5]), dt, th) == pytest.approx(0.1, abs=1e-15)   # reached exactly
+    assert O.activation_time(np.array([0.1, 0.4, 0.49]), dt, th) == -1.0
+
+
+def test_point_traces_uniform_state_follow_scalar_recurrence():
+    # a spatially constant state stays constant (K 1 = 0, M c1 = c M1): at
+    # every point the trace is the scalar IMEX recurrence, and v0 = 0.3 > a
+    # excites, so the trace crosses u_th and a(x0) lies on its linear piece
+    mesh = O.mesh2d(9)
+    K = 3
+    modes, _ = O.kl_build(mesh, 0.09, 0.04, K)
+    phi = O.centroid_table(mesh, modes, mesh)
+    xi = inputs.gaussian_xi(2, 0, 0, 2, K)
+    dt, nsteps, th = 0.2, 40, 0.5
+    pts = np.array([[0.0, 0.0], [0.37, 0.81], [1.0, 0.5], [0.5, 0.5]])
+    v0, w0 = np.full(mesh.n, 0.3), np.full(mesh.n, 0.01)
+    tr, act, q, st = O.solve_points(mesh, phi, xi, dt, nsteps, pts, th, v0=v0, w0=w0)
+    assert np.all(st == 0)
+    a, eps, gam = 0.1, 0.01, 0.5
+    v, w = 0.3, 0.01
+    ref = [v]
+    for _ in range(nsteps):
+        v, w = v + dt * (v * (v - a) * (1 - v) - w), w + dt * eps * (v - gam * w)
+        ref.append(v)
+    ref = np.array(ref)
+    assert np.max(np.abs(tr - ref[None, None, :])) < 1e-12
+    n = int(np.argmax(ref >= th))
+    assert n > 0 and ref[n - 1] < th <= ref[n]
+    for s in range(2):
+        for p in range(len(pts)):
+            a_ = act[s, p]
+            assert (n - 1) * dt < a_ <= n * dt + 1e-15
+            u_at = tr[s, p, n - 1] + (a_ - (n - 1) * dt) / dt * (tr[s, p, n] - tr[s, p, n - 1])
+            assert abs(u_at - th) < 1e-12
+
+
+def test_point_traces_are_p1_values_of_the_state():
+    # at a node the trace is the node's value; inside a triangle it is the
+    # barycentric combination (weights from the geometry) of its vertices'
+    # traces; the final entry matches solve_states' field
+    m = 9
+    h = 1.0 / (m - 1)
+    mesh = O.mesh2d(m)
+    K = 4
+    modes, _ = O.kl_build(mesh, 0.09, 0.04, K)
+    phi = O.centroid_table(mesh, modes, mesh)
+    xi = inputs.gaussian_xi(5, 0, 0, 2, K)
+    v0, w0 = O.initial_state(mesh, 0.35)
+    i, j, s_, t_ = 3, 2, 0.7, 0.25                       # lower triangle of cell (3, 2): t <= s
+    x = np.array([(i + s_) * h, (j + t_) * h])
+    nodes = [(i, j), (i + 1, j), (i + 1, j + 1)]
+    wts = [1 - s_, s_ - t_, t_]
+    pts = np.vstack([x] + [np.array([a * h, b * h]) for a, b in nodes])
+    dt, nsteps = 0.1, 12
+    tr, act, q, st = O.solve_points(mesh, phi, xi, dt, nsteps, pts, 0.5, v0=v0, w0=w0)
+    comb = sum(wt * tr[:, 1 + k, :] for k, wt in enumerate(wts))
+    assert np.max(np.abs(tr[:, 0, :] - comb)) < 1e-14
+    qs, V, W, _ = O.solve_states(mesh, phi, xi, dt, nsteps, v0=v0, w0=w0)
+    for k, (a, b) in enumerate(nodes):
+        assert np.array_equal(tr[:, 1 + k, -1], V[:, a + m * b])
+    assert np.array_equal(q, qs)
+
+
+def test_time_norms_match_quadrature_of_the_interpolant():
+    import scipy.integrate
+
+    rng = np.random.default_rng(4)
+    T, nt = 2.5, 13
+    e = rng.normal(size=nt + 1)
+    t = np.linspace(0.0, T, nt + 1)
+    l2, h1 = O.time_norms(e, T)
+    f2 = sum(scipy.integrate.quad(lambda x: np.interp(x, t, e) ** 2, t[k], t[k + 1], epsabs=1e-14)[0]
+             for k in range(nt))
+    d2 = sum(((e[k + 1] - e[k]) / (t[k + 1] - t[k])) ** 2 * (t[k + 1] - t[k]) for k in range(nt))
+    assert abs(l2 - np.sqrt(f2)) < 1e-12
+    assert abs(h1 - np.sqrt(f2 + d2)) < 1e-12
+    # a linear function: |e|_{H1}^2 = slope^2 T, ||e||^2 = T (e0^2 + e0 e1 + e1^2) / 3
+    l2, h1 = O.time_norms(np.linspace(1.0, 3.0, 9), 2.0)
+    assert abs(l2 ** 2 - 2.0 * (1 + 3 + 9) / 3) < 1e-12 and abs(h1 ** 2 - l2 ** 2 - 2.0) < 1e-12
