@@ -527,26 +527,12 @@ def run_c3(spec: str):
     return 0
 
 
-def run_serve(spec: str):
-    """Serving workload: --serve rate=R,requests=N[,levels=0-2][,chunk=16][,seed=0].
-    A Poisson stream (exponential inter-arrival, seed) of requests; each picks
-    a level uniformly in the range, 1..256 samples, a target RMSE log-uniform
-    in [1e-4, 1e-2] x |Qbar| (Qbar = 1.125e-3, the 2D estimate) and xi drawn
-    with seed = request id.  Requests go through mlq_submit / mlq_poll on one
-    context; prints latency percentiles and served DOF-steps/s."""
-    import time
-
-    kv = dict(item.split("=") for item in spec.split(","))
-    rate = float(kv.get("rate", 50))
-    nreq = int(kv.get("requests", 200))
-    lo, hi = (int(x) for x in kv.get("levels", "0-2").split("-"))
-    chunk = int(kv.get("chunk", 16))
-    seed = int(kv.get("seed", 0))
-    from paper_2105_02007_gb300 import build, inputs
-
-    build.build()
-    from paper_2105_02007_gb300 import mlq
-
+def serve_stream(mlq, inputs, rate: float, nreq: int, lo: int, hi: int, chunk: int = 16, seed: int = 0):
+    """A Poisson stream (exponential inter-arrival times, seed) of serving
+    requests through mlq_submit / mlq_poll on one context: each picks a level
+    uniformly in lo..hi, 1..256 samples, a target RMSE log-uniform in
+    [1e-4, 1e-2] x |Qbar| (Qbar = 1.125e-3, the 2D estimate) and xi drawn with
+    seed = request id.  Returns latency percentiles and served DOF-steps/s."""
     rng = np.random.default_rng(seed)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, nreq))
     levels = rng.integers(lo, hi + 1, nreq)
@@ -580,14 +566,30 @@ def run_serve(spec: str):
     used = np.array([done[k]["samples_used"] for k in range(nreq)])
     dof = sum(int(used[k]) * LEVEL_M[levels[k]] ** 2 * level_steps(int(levels[k])) for k in range(nreq))
     offered = rate * float(np.mean([LEVEL_M[l] ** 2 * level_steps(l) for l in range(lo, hi + 1)])) * 128.5
-    print(json.dumps({"serve": spec, "requests": nreq, "completed": len(done),
-                      "status_ok": int(sum(done[k]["status"] == 0 for k in range(nreq))),
-                      "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
-                                     "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
-                      "wall_s": wall, "samples_used_mean": float(used.mean()),
-                      "early_stop_fraction": float(np.mean(used < samples)),
-                      "served_dof_steps_per_s": dof / wall, "offered_dof_steps_per_s_at_full_samples": offered,
-                      "batches_mean": float(np.mean([done[k]["batches"] for k in range(nreq)]))}))
+    by_level = {str(l): float(np.percentile(lat[levels == l], 50)) for l in range(lo, hi + 1) if np.any(levels == l)}
+    return {"requests": nreq, "rate_per_s": rate, "levels": f"{lo}-{hi}", "completed": len(done),
+            "status_ok": int(sum(done[k]["status"] == 0 for k in range(nreq))),
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
+                           "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
+            "p50_ms_by_level": by_level, "wall_s": wall, "samples_used_mean": float(used.mean()),
+            "early_stop_fraction": float(np.mean(used < samples)),
+            "served_dof_steps_per_s": dof / wall, "offered_dof_steps_per_s_at_full_samples": offered,
+            "batches_mean": float(np.mean([done[k]["batches"] for k in range(nreq)]))}
+
+
+def run_serve(spec: str):
+    """Serving workload: --serve rate=R,requests=N[,levels=0-2][,chunk=16][,seed=0]
+    (see serve_stream); prints its JSON record."""
+    kv = dict(item.split("=") for item in spec.split(","))
+    lo, hi = (int(x) for x in kv.get("levels", "0-2").split("-"))
+    from paper_2105_02007_gb300 import build, inputs
+
+    build.build()
+    from paper_2105_02007_gb300 import mlq
+
+    out = serve_stream(mlq, inputs, float(kv.get("rate", 50)), int(kv.get("requests", 200)), lo, hi,
+                       int(kv.get("chunk", 16)), int(kv.get("seed", 0)))
+    print(json.dumps({"serve": spec, **out}))
     return 0
 
 
@@ -604,6 +606,7 @@ def main():
                     help="timed mixed-precision estimates with the Jacobi inner preconditioner, the FP64 path's "
                          "solver (0: skip)")
     ap.add_argument("--no-3d", action="store_true", help="skip the 257x257x65 3D member of the line")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving stream of the line")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
@@ -829,6 +832,12 @@ def main():
     if not args.no_3d and prec == mlq.MLQ_MIXED:
         roof3d = roofline_3d(mlq, inputs, peaks)
 
+    # ---- serving: a Poisson stream at the configuration's rate (50/s) over
+    #      levels 0-4, through mlq_submit / mlq_poll (continuous batching)
+    serving = None
+    if not args.no_serve and prec == mlq.MLQ_MIXED and rank == 0:
+        serving = serve_stream(mlq, inputs, 50.0, 100, 0, 4)
+
     cpu = None
     oracle_err = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -859,6 +868,7 @@ def main():
                     "d2h_bytes_per_step": d2h, "steps": len(e2e_vals)},
             "gpu_launches": launches, "clocks": clk, "roofline": roof, "roofline_3d": roof3d,
             "cpu_baseline": cpu, "fp64": fp64, "mixed_jacobi": jac, "error_vs_oracle": oracle_err,
+            "serving": serving,
             "estimate_all_ranks": None if combined is None else {"estimate": combined[0], "rmse": combined[2],
                                                                   "ranks": world},
             "members": [{k: d[k] for k in ("level", "coarse", "cluster", "threads", "npt", "resident", "samples",

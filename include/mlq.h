@@ -424,17 +424,38 @@ int mlq_level_launch(mlq_ctx *ctx, int level, int *cluster, int *threads, int *r
  * the statistical error is small enough: the samples are solved in chunks of
  * `chunk` (a power of two), and the request finishes at the first chunk
  * boundary n where sqrt(V_n / n) <= target_rmse (V_n the unbiased sample
- * variance of the first n values, n >= 2), or after all samples.  A worker
- * thread of the context packs the next chunk of every waiting request at the
- * level of the oldest one into a single batched solve (continuous batching,
- * at most 2^24 DOFs and 65535 samples per batch).  Each sample's Q depends
- * only on its own xi, and the stopping rule only on the values in index
- * order, so a request's result does not depend on what it was batched with
- * (bit for bit on the 2D levels; the 3D launch shape follows the batch size,
- * so there to rounding).  xi is copied at submission (host pointer).
- * mlq_submit / mlq_poll may be called from any thread; the other calls on
- * the context wait for the worker's current batch.  mlq_destroy stops the
- * worker after its current batch; unfinished requests are dropped. */
+ * variance of the first n values, n >= 2), or after all samples.
+ *
+ * Continuous batching: a worker thread of the context runs up to six lanes,
+ * each a stream with its own device workspace.  Whenever a lane is idle it
+ * takes the level of the oldest waiting request whose level no lane is
+ * running (one batch per level at a time, so the long batches of fine
+ * levels cannot hold every lane) and packs the next chunk of every waiting
+ * request at that level into one
+ * batched solve (at most 2^24 DOFs and 65535 samples), so batches of
+ * different levels run on the device together and a request that arrives
+ * while others run starts as soon as a lane frees up.  Batches of less than
+ * 1e9 DOF-steps run on high-priority streams: their CTAs take the SMs that
+ * free up before those of long batches.  Lane workspaces come from the
+ * device's stream-ordered memory pool, so growing one does not wait for the
+ * batches of the other lanes.  A batch is admitted
+ * by device memory: its lane's workspace grows only while the free HBM
+ * (minus 256 MiB) and the budget of mlq_serve_limits allow it; otherwise
+ * it waits for running batches, and a batch that cannot fit with every other
+ * lane idle and released finishes its requests with MLQ_ENOMEM.  State stays
+ * on the device for the life of a batch; between chunks a request's samples
+ * wait on the host.
+ *
+ * Each sample's Q depends only on its own xi, and the stopping rule only on
+ * the values in index order, so a request's result does not depend on what
+ * it was batched with (bit for bit on the 2D levels; the 3D launch shape
+ * follows the batch size, so there to rounding).  xi is copied at submission
+ * (host pointer).  A request whose level is redefined or gets a KL table of
+ * another K before it is served finishes with MLQ_EINVAL.  mlq_submit /
+ * mlq_poll may be called from any thread; the worker takes the context's
+ * lock only to queue a batch, so other calls run beside serving.
+ * mlq_destroy stops the worker after the running batches; unfinished
+ * requests are dropped. */
 typedef struct {
     int level;           /* a defined level of the context */
     int64_t samples;     /* maximum number of samples, 1 .. 2^20 */
@@ -450,9 +471,19 @@ typedef struct {
     double mean, rmse;     /* mean of Q_l over the n samples and sqrt(V_n / n) */
     double latency_ms;     /* submission to completion (host clock) */
     int64_t batches;       /* batched solves the request took part in */
+    double first_ms, last_ms;  /* start of its first batch and end of its last,
+                                  ms after the serving worker started (host clock) */
 } mlq_result;
 
 int mlq_submit(mlq_ctx *ctx, const mlq_request *req, uint64_t *ticket);
+/* Serving resources: lanes (1..6, default 6) = batches on the device at the
+ * same time, each on its own stream with its own workspace; max_bytes = cap
+ * on the lanes' workspaces together (0, the default: the free device memory
+ * alone decides).  A batch whose workspace does not fit waits for running
+ * batches; one that does not fit with every other lane idle and released
+ * finishes its requests with MLQ_ENOMEM.  MLQ_ENOTREADY if lanes to be
+ * dropped still run a batch (call again later). */
+int mlq_serve_limits(mlq_ctx *ctx, int lanes, size_t max_bytes);
 /* MLQ_ENOTREADY while the request runs; MLQ_OK fills *out and releases the
  * ticket (a second poll of it returns MLQ_EINVAL). */
 int mlq_poll(mlq_ctx *ctx, uint64_t ticket, mlq_result *out);

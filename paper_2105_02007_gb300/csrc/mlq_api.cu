@@ -11,6 +11,7 @@
 #include "mlq_launch.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -104,7 +105,11 @@ struct mlq_ctx {
     // held by every call that uses the device or the level table, and by the
     // serving worker around each batch
     std::recursive_mutex mu;
-    Server *server = nullptr;
+    // serving worker, created by the first mlq_submit (under mu) and read by
+    // mlq_poll without it
+    std::atomic<Server *> server{nullptr};
+    int serve_lanes = 6;       // mlq_serve_limits
+    size_t serve_budget = 0;
     int device = 0;
     cudaStream_t stream = nullptr;
     mlq_options opt{};
@@ -1946,8 +1951,21 @@ const char *mlq_last_cuda_error(mlq_ctx *ctx)
 
 // ===========================================================================
 // Serving (mlq_submit / mlq_poll): continuous batching of per-level Monte
-// Carlo requests on a worker thread of the context.
+// Carlo requests.  A worker thread of the context owns up to kServeLanes
+// lanes (a stream, a device workspace, pinned host buffers); every idle lane
+// takes the next chunk of the waiting requests of one level (the level of
+// the oldest waiting request no lane is serving) as one batched solve, so
+// batches of different levels run on the device at the same time, and a
+// request that arrives while others run starts as soon as a lane frees up.
+// A batch is admitted by device memory: its lane's workspace grows only if
+// the free HBM (and the optional budget of mlq_serve_limits) covers it;
+// otherwise it waits for running batches, and a batch that cannot fit even
+// with every other lane idle and released is refused (MLQ_ENOMEM).
 // ===========================================================================
+constexpr int kServeLanes = 6;
+constexpr size_t kServeReserve = (size_t)256 << 20;   // HBM left free for the rest of the process
+constexpr double kServeShortWork = 1.0e9;              // DOF-steps below which a batch is short
+
 struct ServeReq {
     uint64_t id = 0;
     int level = 0;
@@ -1961,8 +1979,31 @@ struct ServeReq {
     std::vector<int32_t> st;
     int64_t checked = 0;     // chunk boundaries below this were tested
     bool finished = false;
+    bool in_flight = false;  // a lane holds its next chunk
     mlq_result res{};
     std::chrono::steady_clock::time_point t0;
+};
+
+struct ServePart {
+    ServeReq *r;
+    int64_t first, count;
+};
+
+struct ServeLane {
+    cudaStream_t stream = nullptr;      // the stream of the running batch (one of the two below)
+    cudaStream_t s_hi = nullptr, s_lo = nullptr;   // highest / lowest stream priority
+    cudaEvent_t done = nullptr;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    double *h_xi = nullptr, *h_q = nullptr;   // pinned: batch inputs and outputs
+    int32_t *h_st = nullptr, *h_err = nullptr;
+    int64_t h_cap = 0;                        // samples the pinned buffers hold (x K for xi)
+    int h_K = 0;
+    bool busy = false;
+    int level = -1;
+    int64_t S = 0;
+    double t_start = 0.0;
+    std::vector<ServePart> parts;
 };
 
 struct Server {
@@ -1972,6 +2013,10 @@ struct Server {
     std::deque<uint64_t> order;  // arrival order of unfinished requests
     uint64_t next_id = 1;
     bool stop = false;
+    int lanes = kServeLanes;     // lanes in use (mlq_serve_limits)
+    size_t budget = 0;           // bytes of lane workspaces (0: free HBM only)
+    ServeLane lane[kServeLanes];
+    std::chrono::steady_clock::time_point epoch = std::chrono::steady_clock::now();
     std::thread worker;
 };
 
@@ -1979,6 +2024,11 @@ namespace {
 
 constexpr int64_t kServeMaxDofs = int64_t(1) << 24;  // DOFs per batched solve
 constexpr int64_t kServeMaxSamples = int64_t(1) << 20;
+
+double serve_ms(const Server &sv)
+{
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - sv.epoch).count();
+}
 
 // mean and sqrt(V_n / n) of the first n values, in index order
 void serve_stats(const ServeReq &r, int64_t n, double *mean, double *rmse)
@@ -2019,96 +2069,327 @@ void serve_check(ServeReq &r)
     }
 }
 
-void serve_loop(mlq_ctx *ctx)
+void serve_prune(Server &sv)
 {
-    Server &sv = *ctx->server;
-    std::vector<double> xi, q;
-    std::vector<int32_t> st, it;
+    for (auto i = sv.order.begin(); i != sv.order.end();)
+        i = sv.reqs.at(*i)->finished ? sv.order.erase(i) : i + 1;
+}
+
+// the workspace a batch of S samples of `level` takes on a lane
+size_t serve_batch_bytes(const mlq_ctx *ctx, int level, int64_t S)
+{
+    const Level &L = ctx->levels[level];
+    return member_bytes(ctx, L, S) + align_up((size_t)S * L.K * 8, 256);
+}
+
+// Lane workspaces come from the device's stream-ordered pool
+// (cudaMallocAsync / cudaFreeAsync): a plain cudaFree would wait for every
+// running batch of every lane before it returns.
+void serve_release(ServeLane &ln)
+{
+    if (ln.ws) cudaFreeAsync(ln.ws, ln.stream);
+    ln.ws = nullptr;
+    ln.ws_bytes = 0;
+}
+
+// device memory a new workspace can take: free HBM plus what the pool holds
+// unused (freed lane workspaces not yet returned)
+size_t serve_free_bytes(int device)
+{
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaMemPool_t pool;
+    uint64_t rsv = 0, used = 0;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess &&
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &rsv) == cudaSuccess &&
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess && rsv > used)
+        fr += (size_t)(rsv - used);
+    cudaGetLastError();
+    return fr;
+}
+
+// Grow the lane's workspace to `bytes` if the device memory allows it:
+// 1 = ready, 0 = not now (too little free memory), -1 = CUDA error.
+int serve_reserve(const mlq_ctx *ctx, Server &sv, ServeLane &ln, size_t bytes, cudaStream_t st)
+{
+    size_t held = 0;
+    for (int k = 0; k < sv.lanes; ++k) held += sv.lane[k].ws_bytes;
+    if (ln.ws_bytes >= bytes && (sv.budget == 0 || held <= sv.budget)) return 1;
+    if (sv.budget > 0 && held - ln.ws_bytes + bytes > sv.budget) return 0;
+    const size_t fr = serve_free_bytes(ctx->device);
+    if (fr + ln.ws_bytes < bytes + kServeReserve) return 0;
+    serve_release(ln);
+    if (cudaMallocAsync(&ln.ws, bytes, st) != cudaSuccess) {
+        cudaGetLastError();
+        ln.ws = nullptr;
+        return 0;
+    }
+    ln.ws_bytes = bytes;
+    return 1;
+}
+
+int serve_host_buffers(ServeLane &ln, int64_t S, int K)
+{
+    if (S <= ln.h_cap && K <= ln.h_K) return MLQ_OK;
+    cudaFreeHost(ln.h_xi);
+    cudaFreeHost(ln.h_q);
+    cudaFreeHost(ln.h_st);
+    ln.h_xi = nullptr;
+    ln.h_q = nullptr;
+    ln.h_st = nullptr;
+    ln.h_cap = 0;
+    // grown geometrically from 4096 samples: freeing pinned memory waits
+    // for the device, so it should happen rarely
+    const int64_t cap = std::max<int64_t>(std::max<int64_t>(S, 4096), 2 * ln.h_cap);
+    const int kk = std::max(K, ln.h_K);
+    if (cudaMallocHost(&ln.h_xi, sizeof(double) * cap * kk) != cudaSuccess ||
+        cudaMallocHost(&ln.h_q, sizeof(double) * cap) != cudaSuccess ||
+        cudaMallocHost(&ln.h_st, sizeof(int32_t) * cap) != cudaSuccess) {
+        cudaGetLastError();
+        return MLQ_ENOMEM;
+    }
+    ln.h_cap = cap;
+    ln.h_K = (int)kk;
+    return MLQ_OK;
+}
+
+// queue one batch on a lane: xi in, the member's kernels, Q and status out,
+// the device error flag, then the lane's event
+int serve_launch(mlq_ctx *ctx, ServeLane &ln, int level, int64_t S)
+{
+    const Level &L = ctx->levels[level];
+    char *cur = (char *)ln.ws;
+    Member mb;
+    mb.level = level;
+    mb.S = S;
+    member_carve(ctx, L, mb, cur);
+    double *d_xi = (double *)cur;
+    MLQ_CUDA(ctx, cudaMemcpyAsync(d_xi, ln.h_xi, sizeof(double) * S * L.K, cudaMemcpyHostToDevice, ln.stream));
+    mb.d_xi = d_xi;
+    int st = launch_member(ctx, mb, ln.stream, -1, 0);
+    if (st != MLQ_OK) return st;
+    MLQ_CUDA(ctx, cudaMemcpyAsync(ln.h_q, mb.q, sizeof(double) * S, cudaMemcpyDeviceToHost, ln.stream));
+    MLQ_CUDA(ctx, cudaMemcpyAsync(ln.h_st, mb.status, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, ln.stream));
+    MLQ_CUDA(ctx, cudaMemcpyAsync(ln.h_err, ctx->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, ln.stream));
+    MLQ_CUDA(ctx, cudaEventRecord(ln.done, ln.stream));
+    return MLQ_OK;
+}
+
+// results of a finished lane into its requests
+void serve_harvest(Server &sv, ServeLane &ln, int code)
+{
+    if (code == MLQ_OK && *ln.h_err) code = MLQ_ETIMEOUT;
+    const double now = serve_ms(sv);
+    int64_t off = 0;
+    for (const ServePart &p : ln.parts) {
+        ServeReq &r = *p.r;
+        r.in_flight = false;
+        r.res.batches++;
+        if (r.res.batches == 1) r.res.first_ms = ln.t_start;
+        r.res.last_ms = now;
+        if (code != MLQ_OK) {
+            serve_finish(r, 0, code);
+        } else {
+            std::copy(ln.h_q + off, ln.h_q + off + p.count, r.q.begin() + p.first);
+            std::copy(ln.h_st + off, ln.h_st + off + p.count, r.st.begin() + p.first);
+            r.next = p.first + p.count;
+            serve_check(r);
+        }
+        off += p.count;
+    }
+    ln.parts.clear();
+    ln.busy = false;
+    ln.level = -1;
+}
+
+// The next batch for an idle lane: the oldest waiting request no lane is
+// serving sets the level; every waiting request at that level adds its next
+// chunk (or all its samples without a target), up to the batch caps.
+int64_t serve_form(mlq_ctx *ctx, Server &sv, std::vector<ServePart> &parts, int *level_out)
+{
+    parts.clear();
+    std::lock_guard<std::recursive_mutex> g(ctx->mu);   // the level table
+    // requests whose level changed its KL table (K) or was dropped since
+    // submission cannot be served with the xi they brought
+    for (uint64_t id : sv.order) {
+        ServeReq &r = *sv.reqs.at(id);
+        if (!r.finished && !r.in_flight &&
+            (!ctx->levels[r.level].defined || !ctx->levels[r.level].d_phi || ctx->levels[r.level].K != r.K))
+            serve_finish(r, 0, MLQ_EINVAL);
+    }
+    // one batch per level on the device at a time: a level that already runs
+    // in a lane waits, so a long batch of a fine level cannot take every lane
+    // from the short batches of the coarse ones
+    auto running = [&](int l) {
+        for (int k = 0; k < sv.lanes; ++k)
+            if (sv.lane[k].busy && sv.lane[k].level == l) return true;
+        return false;
+    };
+    int level = -1, K = 0;
+    for (uint64_t id : sv.order) {
+        const ServeReq &r = *sv.reqs.at(id);
+        if (!r.finished && !r.in_flight && !running(r.level)) {
+            level = r.level;
+            K = r.K;
+            break;
+        }
+    }
+    if (level < 0) return 0;
+    const int64_t n = ctx->levels[level].n;
+    const int64_t cap = std::max<int64_t>(1, std::min<int64_t>(65535, kServeMaxDofs / std::max<int64_t>(n, 1)));
+    int64_t total = 0;
+    for (uint64_t id : sv.order) {
+        ServeReq &r = *sv.reqs.at(id);
+        if (r.finished || r.in_flight || r.level != level || r.K != K) continue;
+        int64_t take = r.target > 0.0 ? std::min(r.chunk, r.samples - r.next) : r.samples - r.next;
+        take = std::min(take, cap - total);
+        if (take <= 0) break;
+        parts.push_back({&r, r.next, take});
+        total += take;
+    }
+    *level_out = level;
+    return total;
+}
+
+void serve_loop(mlq_ctx *ctx, Server *svp)
+{
+    Server &sv = *svp;
+    cudaSetDevice(ctx->device);
+    std::unique_lock<std::mutex> lk(sv.mu);
+    std::vector<ServePart> parts;
     for (;;) {
-        struct Part { ServeReq *r; int64_t first, count; };
-        std::vector<Part> parts;
-        int level = -1, K = 0;
-        {
-            std::unique_lock<std::mutex> lk(sv.mu);
-            sv.cv.wait(lk, [&] { return sv.stop || !sv.order.empty(); });
-            if (sv.stop) return;
-            // the oldest request sets the level; every waiting request at that
-            // level adds its next chunk (adaptive) or all its samples
-            ServeReq &head = *sv.reqs.at(sv.order.front());
-            level = head.level;
-            K = head.K;
-            const int64_t n = ctx->levels[level].n;
-            const int64_t cap = std::max<int64_t>(1, std::min<int64_t>(65535, kServeMaxDofs / std::max<int64_t>(n, 1)));
-            int64_t total = 0;
-            for (uint64_t id : sv.order) {
-                ServeReq &r = *sv.reqs.at(id);
-                if (r.level != level || r.K != K) continue;
-                int64_t take = r.target > 0.0 ? std::min(r.chunk, r.samples - r.next) : r.samples - r.next;
-                take = std::min(take, cap - total);
-                if (take <= 0) break;
-                parts.push_back({&r, r.next, take});
-                total += take;
+        bool busy = false;
+        for (int k = 0; k < sv.lanes; ++k) busy = busy || sv.lane[k].busy;
+        if (sv.stop && !busy) return;
+        if (busy) sv.cv.wait_for(lk, std::chrono::microseconds(100));
+        else if (!sv.stop) sv.cv.wait(lk, [&] { return sv.stop || !sv.order.empty(); });
+        // finished batches
+        for (int k = 0; k < sv.lanes; ++k) {
+            ServeLane &ln = sv.lane[k];
+            if (!ln.busy) continue;
+            const cudaError_t q = cudaEventQuery(ln.done);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess) cudaGetLastError();
+            serve_harvest(sv, ln, q == cudaSuccess ? MLQ_OK : MLQ_ECUDA);
+        }
+        if (sv.stop) continue;   // drain the running batches, start no new one
+        // new batches on idle lanes
+        for (int k = 0; k < sv.lanes; ++k) {
+            ServeLane &ln = sv.lane[k];
+            if (ln.busy) continue;
+            int level = -1;
+            const int64_t S = serve_form(ctx, sv, parts, &level);
+            if (S <= 0) break;
+            int K = 0;
+            size_t bytes = 0;
+            cudaStream_t bst;
+            {
+                std::lock_guard<std::recursive_mutex> g(ctx->mu);
+                const Level &Lv = ctx->levels[level];
+                K = Lv.K;
+                bytes = serve_batch_bytes(ctx, level, S);
+                // short batches on the high-priority stream: their CTAs take
+                // the SMs that free up before the CTAs of long batches (a fine
+                // level's CTA holds its SM for its sample's whole horizon)
+                bst = (double)S * Lv.n * Lv.nsteps < kServeShortWork ? ln.s_hi : ln.s_lo;
             }
-            try {
-                xi.resize((size_t)total * K);
-            } catch (const std::bad_alloc &) {
-                for (const Part &p : parts) serve_finish(*p.r, 0, MLQ_ENOMEM);
-                for (auto i = sv.order.begin(); i != sv.order.end();)
-                    i = sv.reqs.at(*i)->finished ? sv.order.erase(i) : i + 1;
+            int code = serve_host_buffers(ln, S, K);
+            int got = code == MLQ_OK ? serve_reserve(ctx, sv, ln, bytes, bst) : -1;
+            if (got == 0) {
+                bool others = false;
+                for (int j = 0; j < sv.lanes; ++j) others = others || sv.lane[j].busy;
+                if (others) break;   // wait for a running batch to free memory
+                for (int j = 0; j < sv.lanes; ++j) serve_release(sv.lane[j]);
+                got = serve_reserve(ctx, sv, ln, bytes, bst);
+                if (got == 0) code = MLQ_ENOMEM;   // cannot fit even alone: refuse
+            }
+            if (got != 1 || code != MLQ_OK) {
+                for (const ServePart &p : parts) serve_finish(*p.r, 0, code != MLQ_OK ? code : MLQ_ECUDA);
+                serve_prune(sv);
                 sv.cv.notify_all();
                 continue;
             }
             int64_t off = 0;
-            for (const Part &p : parts) {
-                std::memcpy(xi.data() + off * K, p.r->xi.data() + p.first * K, sizeof(double) * p.count * K);
+            for (const ServePart &p : parts) {
+                std::memcpy(ln.h_xi + off * K, p.r->xi.data() + p.first * K, sizeof(double) * p.count * K);
+                p.r->in_flight = true;
                 off += p.count;
             }
-        }
-        const int64_t S = (int64_t)xi.size() / std::max(K, 1);
-        int code = MLQ_OK;
-        try {
-            q.assign(S, 0.0);
-            st.assign(S, 0);
-            it.assign(S, 0);
-        } catch (const std::bad_alloc &) {
-            code = MLQ_ENOMEM;
-        }
-        if (code == MLQ_OK) {
-            std::lock_guard<std::recursive_mutex> g(ctx->mu);
-            code = mlq_solve(ctx, level, S, xi.data(), 0, q.data(), nullptr, nullptr, st.data(), it.data());
-        }
-        std::lock_guard<std::mutex> lk(sv.mu);
-        int64_t off = 0;
-        for (const Part &p : parts) {
-            ServeReq &r = *p.r;
-            r.res.batches++;
-            if (code != MLQ_OK) {
-                serve_finish(r, 0, code);
-            } else {
-                std::copy(q.begin() + off, q.begin() + off + p.count, r.q.begin() + p.first);
-                std::copy(st.begin() + off, st.begin() + off + p.count, r.st.begin() + p.first);
-                r.next = p.first + p.count;
-                serve_check(r);
+            ln.parts = parts;
+            ln.level = level;
+            ln.S = S;
+            ln.t_start = serve_ms(sv);
+            ln.stream = bst;
+            {
+                std::lock_guard<std::recursive_mutex> g(ctx->mu);
+                code = serve_launch(ctx, ln, level, S);
             }
-            off += p.count;
+            ln.busy = true;
+            if (code != MLQ_OK) {
+                cudaStreamSynchronize(ln.stream);
+                cudaGetLastError();
+                serve_harvest(sv, ln, code);
+            }
         }
-        for (auto i = sv.order.begin(); i != sv.order.end();)
-            i = sv.reqs.at(*i)->finished ? sv.order.erase(i) : i + 1;
+        serve_prune(sv);
         sv.cv.notify_all();
     }
 }
 
 void serve_stop(mlq_ctx *ctx)
 {
-    if (!ctx->server) return;
+    Server *sv = ctx->server.load();
+    if (!sv) return;
     {
-        std::lock_guard<std::mutex> lk(ctx->server->mu);
-        ctx->server->stop = true;
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
     }
-    ctx->server->cv.notify_all();
-    if (ctx->server->worker.joinable()) ctx->server->worker.join();
-    delete ctx->server;
-    ctx->server = nullptr;
+    sv->cv.notify_all();
+    if (sv->worker.joinable()) sv->worker.join();
+    for (ServeLane &ln : sv->lane) {
+        serve_release(ln);
+        if (ln.s_lo) cudaStreamSynchronize(ln.s_lo);
+        if (ln.s_hi) cudaStreamSynchronize(ln.s_hi);
+        cudaFreeHost(ln.h_xi);
+        cudaFreeHost(ln.h_q);
+        cudaFreeHost(ln.h_st);
+        cudaFreeHost(ln.h_err);
+        if (ln.done) cudaEventDestroy(ln.done);
+        if (ln.s_lo) cudaStreamDestroy(ln.s_lo);
+        if (ln.s_hi) cudaStreamDestroy(ln.s_hi);
+    }
+    ctx->server.store(nullptr);
+    delete sv;
+}
+
+// the server with its lanes' streams and events; null on failure
+Server *serve_create(mlq_ctx *ctx)
+{
+    std::unique_ptr<Server> sv(new Server());
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return nullptr;
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    for (ServeLane &ln : sv->lane) {
+        if (cudaStreamCreateWithPriority(&ln.s_lo, cudaStreamNonBlocking, lo) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&ln.s_hi, cudaStreamNonBlocking, hi) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ln.done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMallocHost(&ln.h_err, sizeof(int32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            for (ServeLane &l2 : sv->lane) {
+                if (l2.done) cudaEventDestroy(l2.done);
+                if (l2.s_lo) cudaStreamDestroy(l2.s_lo);
+                if (l2.s_hi) cudaStreamDestroy(l2.s_hi);
+                cudaFreeHost(l2.h_err);
+            }
+            return nullptr;
+        }
+        ln.stream = ln.s_lo;
+        *ln.h_err = 0;
+    }
+    return sv.release();
 }
 
 }  // namespace
@@ -2125,9 +2406,13 @@ try {
         MLQ_GUARD(ctx);
         if (check_level(ctx, req->level) != MLQ_OK || ctx->levels[req->level].K < 1) return MLQ_EINVAL;
         r->K = ctx->levels[req->level].K;
-        if (!ctx->server) {
-            ctx->server = new Server();
-            ctx->server->worker = std::thread(serve_loop, ctx);
+        if (!ctx->server.load()) {
+            Server *sv = serve_create(ctx);
+            if (!sv) return MLQ_ECUDA;
+            sv->lanes = ctx->serve_lanes;
+            sv->budget = ctx->serve_budget;
+            sv->worker = std::thread(serve_loop, ctx, sv);
+            ctx->server.store(sv);
         }
     }
     r->level = req->level;
@@ -2138,7 +2423,7 @@ try {
     r->q.assign(req->samples, 0.0);
     r->st.assign(req->samples, 0);
     r->t0 = std::chrono::steady_clock::now();
-    Server &sv = *ctx->server;
+    Server &sv = *ctx->server.load();
     {
         std::lock_guard<std::mutex> lk(sv.mu);
         r->id = sv.next_id++;
@@ -2154,10 +2439,37 @@ try {
     return MLQ_ECUDA;
 }
 
+int mlq_serve_limits(mlq_ctx *ctx, int lanes, size_t max_bytes)
+{
+    if (!ctx || lanes < 1 || lanes > kServeLanes) return MLQ_EINVAL;
+    {
+        MLQ_GUARD(ctx);
+        ctx->serve_lanes = lanes;
+        ctx->serve_budget = max_bytes;
+    }
+    // the worker takes the server's lock before the context's: never hold
+    // the context's lock here
+    if (Server *sv = ctx->server.load()) {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        for (int k = lanes; k < kServeLanes; ++k)
+            if (sv->lane[k].busy) return MLQ_ENOTREADY;   // shrink once those batches are done
+        for (int k = lanes; k < kServeLanes; ++k) serve_release(sv->lane[k]);
+        // idle lanes give their workspaces back: the next batch on each is
+        // admitted against the new budget
+        for (int k = 0; k < lanes; ++k)
+            if (!sv->lane[k].busy) serve_release(sv->lane[k]);
+        sv->lanes = lanes;
+        sv->budget = max_bytes;
+        sv->cv.notify_all();
+    }
+    return MLQ_OK;
+}
+
 int mlq_poll(mlq_ctx *ctx, uint64_t ticket, mlq_result *out)
 {
-    if (!ctx || !out || !ctx->server) return MLQ_EINVAL;
-    Server &sv = *ctx->server;
+    Server *svp = ctx ? ctx->server.load() : nullptr;
+    if (!out || !svp) return MLQ_EINVAL;
+    Server &sv = *svp;
     std::lock_guard<std::mutex> lk(sv.mu);
     auto i = sv.reqs.find(ticket);
     if (i == sv.reqs.end()) return MLQ_EINVAL;

@@ -22,6 +22,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 MLQ_FP64, MLQ_MIXED = 0, 1
+MLQ_EINVAL, MLQ_ENOMEM = -1, -2
 S_CONVERGED, S_MAXITER, S_NONFINITE, S_CANCELLED = 0, 1, 2, 3
 
 
@@ -45,7 +46,7 @@ class Request(ctypes.Structure):
 class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("worst", ctypes.c_int32), ("samples_used", ctypes.c_int64),
                 ("mean", ctypes.c_double), ("rmse", ctypes.c_double), ("latency_ms", ctypes.c_double),
-                ("batches", ctypes.c_int64)]
+                ("batches", ctypes.c_int64), ("first_ms", ctypes.c_double), ("last_ms", ctypes.c_double)]
 
 
 class MemberStats(ctypes.Structure):
@@ -88,6 +89,7 @@ _lib.mlq_time_norms.argtypes = [ctypes.c_int, ctypes.c_double, _vp, _vp, _vp]
 _lib.mlq_estimate.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.mlq_submit.argtypes = [_vp, _vp, _vp]
 _lib.mlq_poll.argtypes = [_vp, ctypes.c_uint64, _vp]
+_lib.mlq_serve_limits.argtypes = [_vp, ctypes.c_int, ctypes.c_size_t]
 _lib.mlq_workspace_bytes.argtypes = [_vp, ctypes.c_int, _i64, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
 _lib.mlq_launch_count.argtypes = [_vp, ctypes.POINTER(_i64)]
 _lib.mlq_level_launch.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -110,7 +112,7 @@ EXPORTED = ["mlq_default_options", "mlq_default_model", "mlq_create", "mlq_destr
             "mlq_mesh_destroy", "mlq_mesh_set_kl", "mlq_mesh_solve", "mlq_mlmc_allocation", "mlq_solve", "mlq_solve_state", "mlq_set_points", "mlq_solve_points", "mlq_trace_prolong",
             "mlq_time_norms", "mlq_estimate", "mlq_workspace_bytes",
             "mlq_launch_count", "mlq_level_launch", "mlq_strerror", "mlq_last_cuda_error", "mlq_set_profiling",
-            "mlq_member_profile", "mlq_autotune", "mlq_solve_noalloc", "mlq_synthesize", "mlq_submit", "mlq_poll"]
+            "mlq_member_profile", "mlq_autotune", "mlq_solve_noalloc", "mlq_synthesize", "mlq_submit", "mlq_poll", "mlq_serve_limits"]
 
 
 class MLQError(RuntimeError):
@@ -491,6 +493,10 @@ class Context:
         t = ctypes.c_uint64()
         _check(_lib.mlq_submit(self._h, ctypes.byref(req), ctypes.byref(t)), "mlq_submit", self._h)
         return t.value
+
+    def serve_limits(self, lanes: int = 6, max_bytes: int = 0):
+        """Serving lanes and workspace budget (mlq_serve_limits)."""
+        _check(_lib.mlq_serve_limits(self._h, int(lanes), int(max_bytes)), "mlq_serve_limits", self._h)
 
     def poll(self, ticket: int):
         """None while the request runs, else a dict of its result (the ticket

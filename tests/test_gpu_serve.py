@@ -124,3 +124,64 @@ def test_serve_rejects_bad_requests(mlq):
                 ctx.submit(**args)
         with pytest.raises(mlq.MLQError):
             ctx.poll(12345)
+
+
+# --------------------------------------------------------------------------
+# Continuous batching across levels and admission by device memory
+# --------------------------------------------------------------------------
+MIX = [(33, 0.05, 200), (65, 0.025, 400)]   # two levels whose batches run for a while
+
+
+def make_mix_ctx(mlq):
+    ctx = mlq.Context(0, mlq.MLQ_MIXED)
+    fine = O.mesh2d(65)
+    modes, _ = O.kl_build(fine, 0.09, 0.04, K)
+    for l, (m, dt, n) in enumerate(MIX):
+        ctx.add_level(l, m, dt, n)
+        ctx.set_kl(l, O.centroid_table(fine, modes, O.mesh2d(m)))
+    return ctx
+
+
+def overlap(a, b):
+    return min(a["last_ms"], b["last_ms"]) - max(a["first_ms"], b["first_ms"])
+
+
+def test_serve_levels_run_together_and_results_unchanged(mlq):
+    xa = inputs.gaussian_xi(41, 0, 0, 64, K)
+    xb = inputs.gaussian_xi(42, 1, 0, 32, K)
+    with make_mix_ctx(mlq) as ctx:
+        ta = ctx.submit(0, xa, 0.0, 64)
+        tb = ctx.submit(1, xb, 0.0, 32)
+        ra, rb = ctx.wait(ta), ctx.wait(tb)
+        qa = ctx.solve(0, xa)["q_fine"]
+        qb = ctx.solve(1, xb)["q_fine"]
+    assert ra["status"] == 0 and rb["status"] == 0
+    assert ra["batches"] == 1 and rb["batches"] == 1
+    assert overlap(ra, rb) > 0                 # the two levels were on the device together
+    n, mean, _ = expected(qa, 0.0, 64)
+    assert ra["mean"] == mean and ra["samples_used"] == 64
+    n, mean, _ = expected(qb, 0.0, 32)
+    assert rb["mean"] == mean and rb["samples_used"] == 32
+
+
+def test_serve_waits_for_memory_and_refuses_what_never_fits(mlq):
+    xa = inputs.gaussian_xi(43, 0, 0, 64, K)
+    xb = inputs.gaussian_xi(44, 1, 0, 32, K)
+    with make_mix_ctx(mlq) as ctx:
+        ba, bb = ctx.workspace_bytes(0, 64), ctx.workspace_bytes(1, 32)
+        # room for either batch, not for both: the second waits for the first
+        ctx.serve_limits(6, max(ba, bb) + 4096)
+        ta = ctx.submit(0, xa, 0.0, 64)
+        tb = ctx.submit(1, xb, 0.0, 32)
+        ra, rb = ctx.wait(ta), ctx.wait(tb)
+        assert ra["status"] == 0 and rb["status"] == 0
+        assert overlap(ra, rb) <= 0
+        alone_a = ctx.solve(0, xa)["q_fine"]
+        assert ra["mean"] == expected(alone_a, 0.0, 64)[1]
+        # a budget below one batch: the request is refused, the next one served
+        ctx.serve_limits(6, min(ba, bb) // 4)
+        r = ctx.wait(ctx.submit(1, xb, 0.0, 32))
+        assert r["status"] == mlq.MLQ_ENOMEM and r["samples_used"] == 0
+        ctx.serve_limits(6, 0)
+        r2 = ctx.wait(ctx.submit(1, xb, 0.0, 32))
+        assert r2["status"] == 0 and r2["mean"] == rb["mean"]
