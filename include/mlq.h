@@ -426,7 +426,8 @@ int mlq_level_launch(mlq_ctx *ctx, int level, int *cluster, int *threads, int *r
  * boundary n where sqrt(V_n / n) <= target_rmse (V_n the unbiased sample
  * variance of the first n values, n >= 2), or after all samples.
  *
- * Continuous batching: a worker thread of the context runs up to six lanes,
+ * Continuous batching: a worker thread of the context runs up to four lanes
+ * (mlq_serve_limits: 1..6),
  * each a stream with its own device workspace.  Whenever a lane is idle it
  * takes the level of the oldest waiting request whose level no lane is
  * running (one batch per level at a time, so the long batches of fine
@@ -476,7 +477,7 @@ typedef struct {
 } mlq_result;
 
 int mlq_submit(mlq_ctx *ctx, const mlq_request *req, uint64_t *ticket);
-/* Serving resources: lanes (1..6, default 6) = batches on the device at the
+/* Serving resources: lanes (1..6, default 4) = batches on the device at the
  * same time, each on its own stream with its own workspace; max_bytes = cap
  * on the lanes' workspaces together (0, the default: the free device memory
  * alone decides).  A batch whose workspace does not fit waits for running

@@ -108,7 +108,7 @@ struct mlq_ctx {
     // serving worker, created by the first mlq_submit (under mu) and read by
     // mlq_poll without it
     std::atomic<Server *> server{nullptr};
-    int serve_lanes = 6;       // mlq_serve_limits
+    int serve_lanes = 4;       // mlq_serve_limits (4 measured best of 1, 2, 4, 6 on the 50/s stream)
     size_t serve_budget = 0;
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -2013,7 +2013,7 @@ struct Server {
     std::deque<uint64_t> order;  // arrival order of unfinished requests
     uint64_t next_id = 1;
     bool stop = false;
-    int lanes = kServeLanes;     // lanes in use (mlq_serve_limits)
+    int lanes = 4;               // lanes in use (mlq_serve_limits)
     size_t budget = 0;           // bytes of lane workspaces (0: free HBM only)
     ServeLane lane[kServeLanes];
     std::chrono::steady_clock::time_point epoch = std::chrono::steady_clock::now();

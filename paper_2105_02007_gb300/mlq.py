@@ -494,7 +494,7 @@ class Context:
         _check(_lib.mlq_submit(self._h, ctypes.byref(req), ctypes.byref(t)), "mlq_submit", self._h)
         return t.value
 
-    def serve_limits(self, lanes: int = 6, max_bytes: int = 0):
+    def serve_limits(self, lanes: int = 4, max_bytes: int = 0):
         """Serving lanes and workspace budget (mlq_serve_limits)."""
         _check(_lib.mlq_serve_limits(self._h, int(lanes), int(max_bytes)), "mlq_serve_limits", self._h)
 
