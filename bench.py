@@ -661,7 +661,14 @@ def main():
         return ctx
 
     ctx = make_ctx(prec)
-    xi_host = [inputs.gaussian_xi(rank, l, 0, LEVEL_N[l], K_MODES) for l in range(len(LEVEL_M))]
+    # one allocation split over the ranks: rank r solves the contiguous sample
+    # indices shard(N_l, r, W) of every level, with the xi of those indices
+    from paper_2105_02007_gb300 import distributed as D
+
+    shards = [D.shard(LEVEL_N[l], rank, world) for l in range(len(LEVEL_M))]
+    if min(c for _, c in shards) < 2:
+        raise SystemExit(f"{world} ranks leave fewer than 2 samples of a level per rank")
+    xi_host = [inputs.gaussian_xi(0, l, f, c, K_MODES) for l, (f, c) in enumerate(shards)]
     xi_dev = [torch.from_numpy(x).to(f"cuda:{local}") for x in xi_host]
     xi_pin = [torch.from_numpy(x).pin_memory() for x in xi_host]
     torch.cuda.synchronize()
@@ -710,14 +717,16 @@ def main():
         t = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{local}")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_all = float(t.item())
-    dof = dof_steps_per_estimate()
-    value = world * dof / (ms_all / 1000.0)
+    dof = dof_steps_per_estimate()          # the whole allocation, over all ranks
+    dof_local = sum(c * (LEVEL_M[l] ** 2 * level_steps(l) + (LEVEL_M[l - 1] ** 2 * level_steps(l - 1) if l else 0))
+                    for l, (_, c) in enumerate(shards))
+    value = dof / (ms_all / 1000.0)
 
     # ---- end to end through the public call, host buffers (pinned) in and
     #      per-sample results out, copies inside the timed region
     e2e_vals = []
     h2d = sum(x.numel() * 8 for x in xi_pin)
-    d2h = sum(LEVEL_N) * 8 + 16 * len(LEVEL_N)
+    d2h = sum(c for _, c in shards) * 8 + 16 * len(LEVEL_N)
     e2e_y = None
     for _ in range(args.e2e_steps):
         barrier()
@@ -729,8 +738,6 @@ def main():
     e2e_s = statistics.mean(e2e_vals) if e2e_vals else None
     combined = None
     if dist is not None:
-        from paper_2105_02007_gb300 import distributed as D
-
         if e2e_s is not None:
             e2e_s = D.max_over_ranks(e2e_s)
         # the one exchange: every rank's Y_l to rank 0, merged in rank order
@@ -808,7 +815,7 @@ def main():
                                          for a, b in zip(y_mixed, ref_y)]}
 
     fp64 = None
-    if args.fp64_steps > 0 and prec == mlq.MLQ_MIXED:
+    if args.fp64_steps > 0 and prec == mlq.MLQ_MIXED and world == 1:
         c64 = make_ctx(mlq.MLQ_FP64)
         ms64, r64 = timed_estimates(c64, args.fp64_steps)
         c64.close()
@@ -817,7 +824,7 @@ def main():
                 "solver": "FP64 Jacobi-PCG from v^n, ||r|| <= 1e-13 ||b|| (the oracle's algorithm)",
                 "mixed_error_vs_fp64": qoi_errors(r64[0], r64[3])}
     jac = None
-    if args.jacobi_steps > 0 and prec == mlq.MLQ_MIXED:
+    if args.jacobi_steps > 0 and prec == mlq.MLQ_MIXED and world == 1:
         cj = make_ctx(mlq.MLQ_MIXED)
         cj.set_options(precond=0)
         msj, rj = timed_estimates(cj, args.jacobi_steps)
@@ -829,13 +836,13 @@ def main():
     # ---- one 3D member (257 x 257 x 65 Kuhn nodes, 16 samples, one block,
     #      mixed path, multigrid): algorithmic bytes over the kernel's time
     roof3d = None
-    if not args.no_3d and prec == mlq.MLQ_MIXED:
+    if not args.no_3d and prec == mlq.MLQ_MIXED and world == 1:
         roof3d = roofline_3d(mlq, inputs, peaks)
 
     # ---- serving: a Poisson stream at the configuration's rate (50/s) over
     #      levels 0-4, through mlq_submit / mlq_poll (continuous batching)
     serving = None
-    if not args.no_serve and prec == mlq.MLQ_MIXED and rank == 0:
+    if not args.no_serve and prec == mlq.MLQ_MIXED and world == 1:
         serving = serve_stream(mlq, inputs, 50.0, 100, 0, 4)
 
     cpu = None
@@ -855,16 +862,16 @@ def main():
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f32+f64" if pkey == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "levels": LEVEL_M, "samples": LEVEL_N, "K": K_MODES,
-                       "dof_steps_per_step": dof, "precision": pkey, "l2": "256 MiB buffer zeroed before each "
+                       "dof_steps_per_step": dof, "dof_steps_per_rank": dof_local, "precision": pkey, "l2": "256 MiB buffer zeroed before each "
                        "timed estimate (inside the timed region, on the same stream)",
-                       "parallelism": f"replicas x{world}, seed = rank",
+                       "parallelism": f"samples x{world} (contiguous index ranges of one allocation)",
                        "cuda_graph": bool(args.graphs and not args.no_graphs),
                        "launch_shapes": {str(l): list(v) for l, v in tuned.items()}},
             "time_to_rmse_s": ms_all / 1000.0, "estimate": mean, "rmse": rmse, "var_l": list(var),
-            "e2e": {"value": world * dof / e2e_s if e2e_s else None, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": dof / e2e_s if e2e_s else None, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": len(e2e_vals)},
             "gpu_launches": launches, "clocks": clk, "roofline": roof, "roofline_3d": roof3d,
             "cpu_baseline": cpu, "fp64": fp64, "mixed_jacobi": jac, "error_vs_oracle": oracle_err,

@@ -211,6 +211,16 @@ int mlq_p1_at_points(int dim, int64_t n, const double *xyz, int64_t ne, const in
  * arguments or counts beyond 4e18. */
 int mlq_mlmc_allocation(int L, const double *var, const double *cost, double eps, int64_t nmin, int64_t *N_out);
 
+/* Host helper: eq. StandardML (Monte Carlo rules) from per-sample level
+ * differences: y[l] (host, N[l] values of Y_l = Q_l - Q_{l-1}, N[l] >= 1)
+ * for l = 0..L.  mean_out = sum_l mean(Y_l); var_out[l] (may be NULL) the
+ * unbiased sample variance of Y_l (0 for N[l] = 1); rmse_out (may be NULL)
+ * = sqrt(sum_l var_l / N[l]).  Sums run in index order, so samples solved on
+ * several processes and gathered back in index order give the same result as
+ * one process, bit for bit. */
+int mlq_mlmc_combine(int L, const int64_t *N, const double *const *y, double *mean_out, double *var_out,
+                     double *rmse_out);
+
 /* Levels on general tetrahedral meshes (non-nested hierarchies; Sec. 4 and
  * the ventricle of Sec. 5.4): a self-contained FP64 member.  One object per
  * mesh; it owns its device arrays and uses the default stream.

@@ -65,3 +65,33 @@ extern "C" int mlq_time_norms(int nt, double T, const double *e, double *l2, dou
     if (h1) *h1 = std::sqrt(a + b);
     return MLQ_OK;
 }
+
+// eq. StandardML with Monte Carlo rules from per-sample level differences:
+// level l contributes the sample mean of Y_l (N[l] values y[l][0..N[l]-1],
+// summed in index order), its unbiased sample variance (two passes), and
+// RMSE_stat = sqrt(sum_l V_l / N_l).  Summing in index order makes the
+// result independent of how the samples were split over processes, as long
+// as they are gathered back in index order.
+extern "C" int mlq_mlmc_combine(int L, const int64_t *N, const double *const *y, double *mean_out, double *var_out,
+                                double *rmse_out)
+{
+    if (L < 0 || !N || !y || !mean_out) return MLQ_EINVAL;
+    for (int l = 0; l <= L; ++l)
+        if (N[l] < 1 || !y[l]) return MLQ_EINVAL;
+    double est = 0.0, mse = 0.0;
+    for (int l = 0; l <= L; ++l) {
+        const int64_t n = N[l];
+        double m = 0.0;
+        for (int64_t i = 0; i < n; ++i) m += y[l][i];
+        m /= (double)n;
+        double s = 0.0;
+        for (int64_t i = 0; i < n; ++i) s += (y[l][i] - m) * (y[l][i] - m);
+        const double v = n > 1 ? s / (double)(n - 1) : 0.0;
+        est += m;
+        mse += v / (double)n;
+        if (var_out) var_out[l] = v;
+    }
+    *mean_out = est;
+    if (rmse_out) *rmse_out = std::sqrt(mse);
+    return MLQ_OK;
+}

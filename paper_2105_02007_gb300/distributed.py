@@ -1,16 +1,25 @@
-"""Multi-rank combination of MLMC estimates (host side, torch.distributed).
+"""Multi-rank MLMC estimate (host side, torch.distributed).
 
-Samples are independent, so N ranks run N replicas of an estimate on their
-own draws (seed = rank) and never exchange data while solving.  The one
-exchange is at the end: every rank's per-sample level differences
-Y_l = Q_l - Q_{l-1} are gathered to rank 0 and the estimator of eq.
-StandardML (sample means per level, unbiased sample variances, RMSE_stat =
-sqrt(sum_l V_l / N_l)) is evaluated over all of them in rank order, so the
-result does not depend on the order in which ranks finish.
+Samples are independent, so the (level, sample index) ranges of one
+allocation are split over the ranks: rank r of W solves the contiguous
+samples shard(N_l, r, W) of every level, drawing exactly the xi a single
+process would draw for those indices (the sample points are a counter-based
+function of (seed, level, index)), and never exchanges data while solving.
+The one exchange is at the end: every rank's per-sample level differences
+Y_l = Q_l - Q_{l-1} are gathered to rank 0 in rank order, which is index
+order, and the estimator of eq. StandardML runs over them in the library
+(mlq_mlmc_combine, sums in index order).  The merged estimate is therefore
+the single-process estimate of the same allocation, bit for bit.
 """
 from __future__ import annotations
 
 import numpy as np
+
+
+def shard(n: int, rank: int, world: int):
+    """The contiguous sample indices [first, first + count) of `rank`."""
+    first = n * rank // world
+    return first, n * (rank + 1) // world - first
 
 
 def _device(group):
@@ -49,32 +58,14 @@ def gather_levels(ys_local, group=None):
     return out if rank == 0 else None
 
 
-def mlmc_from_levels(ys):
-    """Estimate, per-level unbiased variances and RMSE_stat over the samples
-    of each level (sums in index order)."""
-    est, var, mse = 0.0, [], 0.0
-    for y in ys:
-        y = np.asarray(y, dtype=np.float64)
-        n = y.size
-        m = 0.0
-        for v in y:
-            m += float(v)
-        m /= n
-        s = 0.0
-        for v in y:
-            s += (float(v) - m) ** 2
-        v_l = s / (n - 1) if n > 1 else 0.0
-        est += m
-        var.append(v_l)
-        mse += v_l / n
-    return est, var, mse ** 0.5
-
-
 def combine_estimates(ys_local, group=None):
-    """Rank-order merge of every rank's level differences; (estimate, V_l,
-    RMSE_stat) on rank 0, None elsewhere."""
+    """Rank-order merge of every rank's level differences and eq.
+    StandardML over them (mlq_mlmc_combine); (estimate, V_l, RMSE_stat) on
+    rank 0, None elsewhere."""
+    from paper_2105_02007_gb300 import mlq
+
     ys = gather_levels(ys_local, group)
-    return mlmc_from_levels(ys) if ys is not None else None
+    return mlq.mlmc_combine(ys) if ys is not None else None
 
 
 def max_over_ranks(x: float, group=None) -> float:

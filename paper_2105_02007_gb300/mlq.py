@@ -86,6 +86,7 @@ _lib.mlq_set_points.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_d
 _lib.mlq_solve_points.argtypes = [_vp, ctypes.c_int, _i64, _vp, _vp, _vp, _vp, _vp]
 _lib.mlq_trace_prolong.argtypes = [ctypes.c_int, _vp, _vp]
 _lib.mlq_time_norms.argtypes = [ctypes.c_int, ctypes.c_double, _vp, _vp, _vp]
+_lib.mlq_mlmc_combine.argtypes = [ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
 _lib.mlq_estimate.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.mlq_submit.argtypes = [_vp, _vp, _vp]
 _lib.mlq_poll.argtypes = [_vp, ctypes.c_uint64, _vp]
@@ -109,7 +110,7 @@ _lib.mlq_last_cuda_error.argtypes = [_vp]
 EXPORTED = ["mlq_default_options", "mlq_default_model", "mlq_create", "mlq_destroy", "mlq_set_options",
             "mlq_set_model", "mlq_add_level", "mlq_set_initial_state", "mlq_set_initial_disk", "mlq_set_kl",
             "mlq_build_kl", "mlq_centroid_table", "mlq_build_kl_mesh", "mlq_p1_at_points", "mlq_mesh_create",
-            "mlq_mesh_destroy", "mlq_mesh_set_kl", "mlq_mesh_solve", "mlq_mlmc_allocation", "mlq_solve", "mlq_solve_state", "mlq_set_points", "mlq_solve_points", "mlq_trace_prolong",
+            "mlq_mesh_destroy", "mlq_mesh_set_kl", "mlq_mesh_solve", "mlq_mlmc_allocation", "mlq_mlmc_combine", "mlq_solve", "mlq_solve_state", "mlq_set_points", "mlq_solve_points", "mlq_trace_prolong",
             "mlq_time_norms", "mlq_estimate", "mlq_workspace_bytes",
             "mlq_launch_count", "mlq_level_launch", "mlq_strerror", "mlq_last_cuda_error", "mlq_set_profiling",
             "mlq_member_profile", "mlq_autotune", "mlq_solve_noalloc", "mlq_synthesize", "mlq_submit", "mlq_poll", "mlq_serve_limits"]
@@ -551,3 +552,18 @@ def time_norms(e, T: float):
     _check(_lib.mlq_time_norms(a.size - 1, float(T), a.ctypes.data_as(_vp), ctypes.byref(l2), ctypes.byref(h1)),
            "mlq_time_norms")
     return l2.value, h1.value
+
+
+def mlmc_combine(ys):
+    """eq. StandardML over per-sample level differences ys[l] (host arrays),
+    sums in index order (mlq_mlmc_combine).  Returns (mean, var_l, rmse)."""
+    arrs = [np.ascontiguousarray(y, dtype=np.float64) for y in ys]
+    L = len(arrs) - 1
+    N = np.array([a.size for a in arrs], dtype=np.int64)
+    ptrs = (_vp * (L + 1))(*[a.ctypes.data_as(_vp) for a in arrs])
+    mean = ctypes.c_double()
+    var = np.zeros(L + 1)
+    rmse = ctypes.c_double()
+    _check(_lib.mlq_mlmc_combine(L, N.ctypes.data_as(_vp), ptrs, ctypes.byref(mean), var.ctypes.data_as(_vp),
+                                 ctypes.byref(rmse)), "mlq_mlmc_combine")
+    return mean.value, var, rmse.value
