@@ -221,6 +221,21 @@ int mlq_mlmc_allocation(int L, const double *var, const double *cost, double eps
 int mlq_mlmc_combine(int L, const int64_t *N, const double *const *y, double *mean_out, double *var_out,
                      double *rmse_out);
 
+/* Host helpers for field-valued quantities of interest (the state v_h(T) of
+ * mlq_solve_state) on the structured nested levels:
+ * mlq_field_prolong: the P1 interpolant of a coarse field vc (coarse_dims as
+ *   in mlq_add_level; n_c values) at the nodes of the nested fine mesh with
+ *   2m - 1 nodes per axis (vf, n_f values): the intergrid transfer that the
+ *   level differences Y_l = v_l - I v_{l-1} of eq. StandardML need for a
+ *   field QoI.  Fine nodes at coarse nodes keep their value, the others take
+ *   the mean of the two ends of the coarse edge they halve.
+ * mlq_field_norms: ||e||_{L2(D)} and ||e||_{H1(D)} of the P1 function with
+ *   nodal values e on a structured level (lengths as in mlq_add_level, NULL =
+ *   the default box; ignored in 2D): the space norms of the error metric of
+ *   Sec. 5 (eq. space-time-error at one time).  Either output may be NULL. */
+int mlq_field_prolong(int dim, const int32_t *coarse_dims, const double *vc, double *vf);
+int mlq_field_norms(int dim, const int32_t *dims, const double *lengths, const double *e, double *l2, double *h1);
+
 /* Levels on general tetrahedral meshes (non-nested hierarchies; Sec. 4 and
  * the ventricle of Sec. 5.4): a self-contained FP64 member.  One object per
  * mesh; it owns its device arrays and uses the default stream.
@@ -325,6 +340,23 @@ int mlq_time_norms(int nt, double T, const double *e, double *l2, double *h1);
  * may be NULL or contain NULLs) the per-sample Y_l. */
 int mlq_estimate(mlq_ctx *ctx, int L, const int64_t *N, const double *const *xi, double *mean_out,
                  double *var_out, double *rmse_out, double *const *y_out);
+
+/* Adaptive multilevel Monte Carlo (eq. StandardML with the sample numbers of
+ * mlq_mlmc_allocation): solve n_pilot (>= 2) samples of every level pair
+ * 0..L, estimate the variances V_l of Y_l, allocate N_l for the target
+ * statistical error eps with the cost of a sample of pair l taken as its
+ * DOF-steps (n_l nsteps_l + n_{l-1} nsteps_{l-1}), solve the missing samples,
+ * and repeat until the allocation for the latest variances is met.  xi[l]
+ * (host or device, Nmax[l] x K, Nmax[l] >= n_pilot) is the pool of level l,
+ * used in index order; N_l never exceeds Nmax[l] (then rmse_out may stay
+ * above eps).  Outputs (host): N_out[l] the samples used, mean_out, var_out[l]
+ * (may be NULL), rmse_out (may be NULL) = sqrt(sum_l V_l / N_l) over exactly
+ * the samples 0..N_l-1 of each pool (as mlq_mlmc_combine).  The sample
+ * numbers depend only on the values, so a rerun gives the same result.
+ * MLQ_ETIMEOUT if the allocation still grew after 16 rounds. */
+int mlq_estimate_adaptive(mlq_ctx *ctx, int L, double eps, int64_t n_pilot, const int64_t *Nmax,
+                          const double *const *xi, int64_t *N_out, double *mean_out, double *var_out,
+                          double *rmse_out);
 
 /* The KL synthesis step alone (eq. KLlowrank), for verification: for S
  * samples xi (host or device, S x K) write cs2_out[(s*n_elem + e)*2 + {0,1}]

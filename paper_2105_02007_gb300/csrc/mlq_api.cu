@@ -1629,6 +1629,79 @@ int mlq_estimate(mlq_ctx *ctx, int L, const int64_t *N, const double *const *xi,
     return finish_estimate(ctx, L, N, mean_out, var_out, rmse_out);
 }
 
+int mlq_estimate_adaptive(mlq_ctx *ctx, int L, double eps, int64_t n_pilot, const int64_t *Nmax,
+                          const double *const *xi, int64_t *N_out, double *mean_out, double *var_out,
+                          double *rmse_out)
+try {
+    MLQ_GUARD(ctx);
+    if (!ctx || !Nmax || !xi || !N_out || !mean_out || L < 0 || L >= kMaxLevels || !(eps > 0.0) || n_pilot < 2)
+        return MLQ_EINVAL;
+    for (int l = 0; l <= L; ++l) {
+        if (check_level(ctx, l) != MLQ_OK || Nmax[l] < n_pilot || !xi[l]) return MLQ_EINVAL;
+        if (ctx->levels[l].K != ctx->levels[0].K) return MLQ_EINVAL;
+    }
+    const int K = ctx->levels[0].K;
+    // cost per sample of level pair l: the DOF-steps of its members
+    std::vector<double> cost(L + 1), var(L + 1);
+    for (int l = 0; l <= L; ++l) {
+        const Level &F = ctx->levels[l];
+        cost[l] = (double)F.n * F.nsteps;
+        if (l > 0) cost[l] += (double)ctx->levels[l - 1].n * ctx->levels[l - 1].nsteps;
+    }
+    std::vector<std::vector<double>> y(L + 1);
+    std::vector<int64_t> N(L + 1, 0), want(L + 1);
+    for (int l = 0; l <= L; ++l) want[l] = n_pilot;
+    std::vector<double> yb, qf, qc;
+    std::vector<int32_t> stb;
+    // solve samples [N_l, want_l) of every level, in index order and in
+    // pieces of at most 65535
+    auto top_up = [&]() -> int {
+        for (int l = 0; l <= L; ++l) {
+            while (N[l] < want[l]) {
+                const int64_t c = std::min<int64_t>(want[l] - N[l], 65535);
+                yb.assign(c, 0.0);
+                stb.assign(c, 0);
+                const int st = mlq_solve(ctx, l, c, xi[l] + (size_t)N[l] * K, l > 0, nullptr, nullptr, yb.data(),
+                                         stb.data(), nullptr);
+                if (st != MLQ_OK) return st;
+                y[l].insert(y[l].end(), yb.begin(), yb.end());
+                N[l] += c;
+            }
+        }
+        return MLQ_OK;
+    };
+    for (int round = 0; round < 16; ++round) {
+        int st = top_up();
+        if (st != MLQ_OK) return st;
+        std::vector<const double *> yp(L + 1);
+        for (int l = 0; l <= L; ++l) yp[l] = y[l].data();
+        double mean = 0.0, rmse = 0.0;
+        if ((st = mlq_mlmc_combine(L, N.data(), yp.data(), &mean, var.data(), &rmse)) != MLQ_OK) return st;
+        // the allocation for eps from the current variance estimates, within the pools
+        std::vector<double> vpos(var);
+        for (double &v : vpos) v = std::max(v, 1e-300);
+        std::vector<int64_t> alloc(L + 1);
+        if ((st = mlq_mlmc_allocation(L, vpos.data(), cost.data(), eps, n_pilot, alloc.data())) != MLQ_OK) return st;
+        bool grow = false;
+        for (int l = 0; l <= L; ++l) {
+            want[l] = std::min(std::max(alloc[l], N[l]), Nmax[l]);
+            grow = grow || want[l] > N[l];
+        }
+        if (!grow) {
+            for (int l = 0; l <= L; ++l) {
+                N_out[l] = N[l];
+                if (var_out) var_out[l] = var[l];
+            }
+            *mean_out = mean;
+            if (rmse_out) *rmse_out = rmse;
+            return MLQ_OK;
+        }
+    }
+    return MLQ_ETIMEOUT;   // the allocation kept growing: more rounds than the loop allows
+} catch (const std::bad_alloc &) {
+    return MLQ_ENOMEM;
+}
+
 int mlq_set_profiling(mlq_ctx *ctx, int enable)
 {
     MLQ_GUARD(ctx);

@@ -95,3 +95,118 @@ extern "C" int mlq_mlmc_combine(int L, const int64_t *N, const double *const *y,
     if (rmse_out) *rmse_out = std::sqrt(mse);
     return MLQ_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Field-valued quantities of interest (the state v_h(T) of a sample, Sec. 2.4
+// with a field functional; the intergrid transfer of Sec. 4 / Sec. 5 between
+// nested levels).
+// ---------------------------------------------------------------------------
+namespace {
+
+// axis of step q of Kuhn tetrahedron s (the mesh convention of mlq.h: the
+// six axis orders (x,y,z), (x,z,y), (y,x,z), (y,z,x), (z,x,y), (z,y,x))
+int kuhn_step_axis(int s, int q)
+{
+    static const int ax[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    return ax[s][q];
+}
+
+bool dims_ok(int dim, const int32_t *dims)
+{
+    if (!dims || (dim != 2 && dim != 3)) return false;
+    for (int a = 0; a < (dim == 2 ? 1 : 3); ++a)
+        if (dims[a] < 2 || dims[a] > 65536) return false;
+    return true;
+}
+
+}  // namespace
+
+// The P1 interpolant of a coarse field on the nested fine mesh (red
+// refinement in 2D, regular refinement of the Kuhn cubes in 3D: 2m - 1 nodes
+// per axis).  A fine node at a coarse node keeps its value; a fine node
+// halving a coarse edge takes the mean of the edge's two ends.  In 2D the
+// edges are the x, y and (1,1)-diagonal ones of the triangulation; in 3D the
+// seven directions with components in {0, 1} (every such segment of a cube is
+// an edge of its Kuhn tetrahedra).
+extern "C" int mlq_field_prolong(int dim, const int32_t *coarse_dims, const double *vc, double *vf)
+{
+    if (!dims_ok(dim, coarse_dims) || !vc || !vf) return MLQ_EINVAL;
+    if (dim == 2) {
+        const int64_t mc = coarse_dims[0], mf = 2 * mc - 1;
+        for (int64_t J = 0; J < mf; ++J)
+            for (int64_t I = 0; I < mf; ++I) {
+                const int64_t i = I / 2, j = J / 2, a = I & 1, b = J & 1;
+                const double c0 = vc[i + mc * j];
+                vf[I + mf * J] = (a | b) ? 0.5 * (c0 + vc[(i + a) + mc * (j + b)]) : c0;
+            }
+        return MLQ_OK;
+    }
+    const int64_t cx = coarse_dims[0], cy = coarse_dims[1], cz = coarse_dims[2];
+    const int64_t fx = 2 * cx - 1, fy = 2 * cy - 1, fz = 2 * cz - 1;
+    for (int64_t K = 0; K < fz; ++K)
+        for (int64_t J = 0; J < fy; ++J)
+            for (int64_t I = 0; I < fx; ++I) {
+                const int64_t i = I / 2, j = J / 2, k = K / 2, a = I & 1, b = J & 1, c = K & 1;
+                const double c0 = vc[i + cx * (j + cy * k)];
+                vf[I + fx * (J + fy * K)] =
+                    (a | b | c) ? 0.5 * (c0 + vc[(i + a) + cx * ((j + b) + cy * (k + c))]) : c0;
+            }
+    return MLQ_OK;
+}
+
+// ||e||_{L2(D)} and ||e||_{H1(D)} of the P1 function with nodal values e on
+// a structured level (dims and lengths as in mlq_add_level; 2D: the unit
+// square), summed element by element: sum |T| (sum_a e_a^2 + (sum_a e_a)^2)
+// / ((d + 1)(d + 2)) (the consistent mass form) and sum |T| |grad e_h|^2.
+extern "C" int mlq_field_norms(int dim, const int32_t *dims, const double *lengths, const double *e, double *l2,
+                               double *h1)
+{
+    if (!dims_ok(dim, dims) || !e) return MLQ_EINVAL;
+    double m2 = 0.0, g2 = 0.0;
+    if (dim == 2) {
+        const int64_t m = dims[0];
+        const double h = 1.0 / (double)(m - 1), area = 0.5 * h * h;
+        for (int64_t j = 0; j + 1 < m; ++j)
+            for (int64_t i = 0; i + 1 < m; ++i) {
+                const double u00 = e[i + m * j], u10 = e[i + 1 + m * j], u11 = e[i + 1 + m * (j + 1)],
+                             u01 = e[i + m * (j + 1)];
+                // lower (i,j)(i+1,j)(i+1,j+1): grad = ((u10-u00)/h, (u11-u10)/h)
+                // upper (i,j)(i+1,j+1)(i,j+1): grad = ((u11-u01)/h, (u01-u00)/h)
+                const double tri[2][3] = {{u00, u10, u11}, {u00, u11, u01}};
+                const double gx[2] = {(u10 - u00) / h, (u11 - u01) / h}, gy[2] = {(u11 - u10) / h, (u01 - u00) / h};
+                for (int t = 0; t < 2; ++t) {
+                    const double s = tri[t][0] + tri[t][1] + tri[t][2];
+                    m2 += area / 12.0 *
+                          (tri[t][0] * tri[t][0] + tri[t][1] * tri[t][1] + tri[t][2] * tri[t][2] + s * s);
+                    g2 += area * (gx[t] * gx[t] + gy[t] * gy[t]);
+                }
+            }
+    } else {
+        const int64_t mx = dims[0], my = dims[1], mz = dims[2];
+        const double L[3] = {lengths ? lengths[0] : 1.0, lengths ? lengths[1] : 1.0, lengths ? lengths[2] : 0.25};
+        const double h[3] = {L[0] / (mx - 1), L[1] / (my - 1), L[2] / (mz - 1)};
+        const double vol = h[0] * h[1] * h[2] / 6.0;
+        for (int64_t k = 0; k + 1 < mz; ++k)
+            for (int64_t j = 0; j + 1 < my; ++j)
+                for (int64_t i = 0; i + 1 < mx; ++i)
+                    for (int s = 0; s < 6; ++s) {
+                        // vertices: the path from (i,j,k) stepping along the axes of s
+                        int64_t c[3] = {i, j, k};
+                        double u[4];
+                        u[0] = e[c[0] + mx * (c[1] + my * c[2])];
+                        double grad[3];
+                        for (int q = 0; q < 3; ++q) {
+                            const int ax = kuhn_step_axis(s, q);
+                            ++c[ax];
+                            u[q + 1] = e[c[0] + mx * (c[1] + my * c[2])];
+                            grad[ax] = (u[q + 1] - u[q]) / h[ax];
+                        }
+                        const double sum = u[0] + u[1] + u[2] + u[3];
+                        m2 += vol / 20.0 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2] + u[3] * u[3] + sum * sum);
+                        g2 += vol * (grad[0] * grad[0] + grad[1] * grad[1] + grad[2] * grad[2]);
+                    }
+    }
+    if (l2) *l2 = std::sqrt(m2);
+    if (h1) *h1 = std::sqrt(m2 + g2);
+    return MLQ_OK;
+}

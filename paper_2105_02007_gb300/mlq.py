@@ -87,6 +87,9 @@ _lib.mlq_solve_points.argtypes = [_vp, ctypes.c_int, _i64, _vp, _vp, _vp, _vp, _
 _lib.mlq_trace_prolong.argtypes = [ctypes.c_int, _vp, _vp]
 _lib.mlq_time_norms.argtypes = [ctypes.c_int, ctypes.c_double, _vp, _vp, _vp]
 _lib.mlq_mlmc_combine.argtypes = [ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
+_lib.mlq_estimate_adaptive.argtypes = [_vp, ctypes.c_int, ctypes.c_double, _i64, _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.mlq_field_prolong.argtypes = [ctypes.c_int, _vp, _vp, _vp]
+_lib.mlq_field_norms.argtypes = [ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
 _lib.mlq_estimate.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.mlq_submit.argtypes = [_vp, _vp, _vp]
 _lib.mlq_poll.argtypes = [_vp, ctypes.c_uint64, _vp]
@@ -110,7 +113,7 @@ _lib.mlq_last_cuda_error.argtypes = [_vp]
 EXPORTED = ["mlq_default_options", "mlq_default_model", "mlq_create", "mlq_destroy", "mlq_set_options",
             "mlq_set_model", "mlq_add_level", "mlq_set_initial_state", "mlq_set_initial_disk", "mlq_set_kl",
             "mlq_build_kl", "mlq_centroid_table", "mlq_build_kl_mesh", "mlq_p1_at_points", "mlq_mesh_create",
-            "mlq_mesh_destroy", "mlq_mesh_set_kl", "mlq_mesh_solve", "mlq_mlmc_allocation", "mlq_mlmc_combine", "mlq_solve", "mlq_solve_state", "mlq_set_points", "mlq_solve_points", "mlq_trace_prolong",
+            "mlq_mesh_destroy", "mlq_mesh_set_kl", "mlq_mesh_solve", "mlq_mlmc_allocation", "mlq_mlmc_combine", "mlq_estimate_adaptive", "mlq_field_prolong", "mlq_field_norms", "mlq_solve", "mlq_solve_state", "mlq_set_points", "mlq_solve_points", "mlq_trace_prolong",
             "mlq_time_norms", "mlq_estimate", "mlq_workspace_bytes",
             "mlq_launch_count", "mlq_level_launch", "mlq_strerror", "mlq_last_cuda_error", "mlq_set_profiling",
             "mlq_member_profile", "mlq_autotune", "mlq_solve_noalloc", "mlq_synthesize", "mlq_submit", "mlq_poll", "mlq_serve_limits"]
@@ -433,6 +436,23 @@ class Context:
                                      res["status"].ctypes.data_as(_vp)), "mlq_solve_points", self._h)
         return res
 
+    def estimate_adaptive(self, xis, eps: float, n_pilot: int = 16):
+        """Adaptive MLMC over the pools xis[l] (Nmax_l x K) for a target
+        statistical error eps (mlq_estimate_adaptive).  Returns (N_l, mean,
+        var_l, rmse)."""
+        L = len(xis) - 1
+        keep = [_ptr(x, np.float64) for x in xis]
+        Nmax = np.array([int(x.shape[0]) for x in xis], dtype=np.int64)
+        xp = (_vp * (L + 1))(*[k[1] for k in keep])
+        N = np.zeros(L + 1, dtype=np.int64)
+        mean = ctypes.c_double()
+        var = np.zeros(L + 1)
+        rmse = ctypes.c_double()
+        _check(_lib.mlq_estimate_adaptive(self._h, L, float(eps), int(n_pilot), Nmax.ctypes.data_as(_vp), xp,
+                                          N.ctypes.data_as(_vp), ctypes.byref(mean), var.ctypes.data_as(_vp),
+                                          ctypes.byref(rmse)), "mlq_estimate_adaptive", self._h)
+        return N, mean.value, var, rmse.value
+
     def estimate(self, xis, return_y: bool = False):
         """MLMC over levels 0..L with xis[l] (N_l x K).  Returns (mean,
         var_l, rmse[, y_l])."""
@@ -567,3 +587,27 @@ def mlmc_combine(ys):
     _check(_lib.mlq_mlmc_combine(L, N.ctypes.data_as(_vp), ptrs, ctypes.byref(mean), var.ctypes.data_as(_vp),
                                  ctypes.byref(rmse)), "mlq_mlmc_combine")
     return mean.value, var, rmse.value
+
+
+def field_prolong(m_coarse, vc):
+    """The coarse field vc on the nested fine mesh (mlq_field_prolong);
+    m_coarse: nodes per side (2D) or (mx, my, mz) (3D)."""
+    dim, dims = _dims(m_coarse)
+    v = np.ascontiguousarray(vc, dtype=np.float64)
+    nf = int(np.prod([2 * int(d) - 1 for d in dims]) if dim == 3 else (2 * int(dims[0]) - 1) ** 2)
+    out = np.zeros(nf)
+    _check(_lib.mlq_field_prolong(dim, dims.ctypes.data_as(_vp), v.ctypes.data_as(_vp), out.ctypes.data_as(_vp)),
+           "mlq_field_prolong")
+    return out
+
+
+def field_norms(m, e, lengths=None):
+    """(L2(D), H1(D)) norms of the P1 field e on a structured level (mlq_field_norms)."""
+    dim, dims = _dims(m)
+    a = np.ascontiguousarray(e, dtype=np.float64)
+    lg = None if lengths is None else np.ascontiguousarray(lengths, dtype=np.float64)
+    l2 = ctypes.c_double()
+    h1 = ctypes.c_double()
+    _check(_lib.mlq_field_norms(dim, dims.ctypes.data_as(_vp), None if lg is None else lg.ctypes.data_as(_vp),
+                                a.ctypes.data_as(_vp), ctypes.byref(l2), ctypes.byref(h1)), "mlq_field_norms")
+    return l2.value, h1.value

@@ -203,3 +203,37 @@ def test_trace_helpers_match_oracle(mlq):
     # the prolonged coarse trace minus itself is zero in H1 (the level
     # difference of a constant-in-level trace)
     assert mlq.time_norms(mlq.trace_prolong(uc) - np.interp(np.arange(21) / 2.0, np.arange(11.0), uc), 1.0)[1] < 1e-14
+
+
+@pytest.mark.parametrize("m", [(5,), (9,), (5, 4, 3), (3, 5, 3)])
+def test_field_prolong_is_the_p1_interpolant(mlq, m):
+    # the library's transfer against the oracle's point location on the
+    # coarse mesh, evaluated at the fine nodes (exact for nested P1)
+    rng = np.random.default_rng(len(m) * 10 + m[0])
+    if len(m) == 1:
+        coarse, fine = O.mesh2d(m[0]), O.mesh2d(2 * m[0] - 1)
+        arg = m[0]
+    else:
+        coarse = O.mesh3d(*m)
+        fine = O.mesh3d(*[2 * v - 1 for v in m])
+        arg = m
+    vc = rng.normal(size=coarse.n)
+    vf = mlq.field_prolong(arg, vc)
+    ref = O.p1_at_points(coarse, vc[:, None], fine.xyz)[:, 0]
+    assert np.max(np.abs(vf - ref)) < 1e-14
+    # linear fields are reproduced exactly
+    lin = coarse.xyz @ np.arange(1.0, coarse.dim + 1.0) + 0.5
+    assert np.max(np.abs(mlq.field_prolong(arg, lin) - (fine.xyz @ np.arange(1.0, coarse.dim + 1.0) + 0.5))) < 1e-13
+
+
+@pytest.mark.parametrize("m", [9, (5, 4, 3)])
+def test_field_norms_match_assembled_matrices(mlq, m):
+    mesh = O.mesh2d(m) if np.ndim(m) == 0 else O.mesh3d(*m)
+    rng = np.random.default_rng(3)
+    e = rng.normal(size=mesh.n)
+    rp, ci, mv, kv = O.assemble(mesh, None, 1.0, 1.0)      # isotropic: the H1 seminorm's matrix
+    M = O.csr_to_dense(rp, ci, mv, mesh.n)
+    K = O.csr_to_dense(rp, ci, kv, mesh.n)
+    l2, h1 = mlq.field_norms(m, e)
+    assert abs(l2 ** 2 - e @ M @ e) <= 1e-12 * (e @ M @ e)
+    assert abs(h1 ** 2 - e @ (M + K) @ e) <= 1e-12 * (e @ (M + K) @ e)

@@ -1,0 +1,97 @@
+"""Estimators on top of the batched solver (Sec. 4): the adaptive multilevel
+Monte Carlo driver (pilot samples, variances, sample allocation of eq.
+StandardML, top-up) and a field-valued QoI (the state v_h(T)) with the
+nested intergrid transfer, against the oracle on the same seeded inputs."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2105_02007_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mlq():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_02007_gb300 import build
+
+    build.build()
+    from paper_2105_02007_gb300 import mlq as m
+
+    return m
+
+
+MS, DTS, T, K = [9, 17, 33], [0.2, 0.1, 0.05], 4.0, 4
+
+
+def hierarchy():
+    fine = O.mesh2d(MS[-1])
+    modes, _ = O.kl_build(fine, 0.09, 0.04, K)
+    meshes = [O.mesh2d(m) for m in MS]
+    return meshes, [O.centroid_table(fine, modes, mm) for mm in meshes]
+
+
+def test_adaptive_mlmc_meets_the_allocation_and_matches_the_oracle(mlq):
+    meshes, phis = hierarchy()
+    pools = [inputs.gaussian_xi(31, l, 0, n, K) for l, n in enumerate([1200, 400, 120])]
+    eps = 2e-7
+    with mlq.Context(0, mlq.MLQ_MIXED) as ctx:
+        for l, (m, dt, ph) in enumerate(zip(MS, DTS, phis)):
+            ctx.add_level(l, m, dt, int(round(T / dt)))
+            ctx.set_kl(l, ph)
+        N, mean, var, rmse = ctx.estimate_adaptive(pools, eps, n_pilot=16)
+        # the same numbers from direct solves of the first N_l samples of each pool
+        ys = [ctx.solve(l, pools[l][: N[l]], with_coarse=l > 0)["y"] for l in range(3)]
+        again = ctx.estimate_adaptive(pools, eps, n_pilot=16)
+    assert np.all(N >= 16) and np.all(N <= [1200, 400, 120])
+    assert np.any(N > 16)                                      # the pilot was topped up
+    assert rmse <= eps or np.any(N == [1200, 400, 120])
+    m2, v2, r2 = mlq.mlmc_combine(ys)
+    assert m2 == mean and r2 == rmse and np.array_equal(v2, var)
+    assert np.array_equal(again[0], N) and again[1] == mean            # deterministic
+    # the allocation for the final variances is met (the loop's exit rule)
+    cost = [MS[l] ** 2 * round(T / DTS[l]) + (MS[l - 1] ** 2 * round(T / DTS[l - 1]) if l else 0) for l in range(3)]
+    alloc = mlq.mlmc_allocation(var, np.array(cost, dtype=float), eps, 16)
+    assert np.all((alloc <= N) | (N == np.array([1200, 400, 120])))
+    # parity: the oracle's level differences of the same samples
+    yo = []
+    for l in range(3):
+        qf = O.solve_batch(meshes[l], phis[l], pools[l][: N[l]], DTS[l], int(round(T / DTS[l])), nthreads=4)[0]
+        qc = (O.solve_batch(meshes[l - 1], phis[l - 1], pools[l][: N[l]], DTS[l - 1], int(round(T / DTS[l - 1])),
+                            nthreads=4)[0] if l else 0.0)
+        yo.append(qf - qc)
+    mo, vo, ro = O.mlmc_estimate(yo)
+    assert abs(mean - mo) <= 1e-6 * abs(mo)
+    assert abs(rmse - ro) <= 1e-4 * ro
+
+
+def test_field_qoi_multilevel_mean_matches_the_oracle(mlq):
+    # E[v(T)] on the 33 x 33 mesh by eq. StandardML over two levels: the mean
+    # of v_0 prolonged, plus the mean of Y_1 = v_1 - P v_0 (same xi)
+    meshes, phis = hierarchy()
+    xi0 = inputs.gaussian_xi(32, 1, 0, 24, K)
+    xi1 = inputs.gaussian_xi(32, 2, 0, 8, K)
+    with mlq.Context(0, mlq.MLQ_MIXED) as ctx:
+        for l in (1, 2):
+            ctx.add_level(l, MS[l], DTS[l], int(round(T / DTS[l])))
+            ctx.set_kl(l, phis[l])
+        v0 = ctx.solve_state(1, xi0)["v"]
+        f1 = ctx.solve_state(2, xi1)["v"]
+        c1 = ctx.solve_state(1, xi1)["v"]
+    P = lambda v: mlq.field_prolong(MS[1], v)
+    mean = np.mean([P(v) for v in v0], axis=0) + np.mean([f - P(c) for f, c in zip(f1, c1)], axis=0)
+    # the oracle: its own states and its point location for the transfer
+    V0 = O.solve_states(meshes[1], phis[1], xi0, DTS[1], int(round(T / DTS[1])))[1]
+    F1 = O.solve_states(meshes[2], phis[2], xi1, DTS[2], int(round(T / DTS[2])))[1]
+    C1 = O.solve_states(meshes[1], phis[1], xi1, DTS[1], int(round(T / DTS[1])))[1]
+    Po = lambda v: O.p1_at_points(meshes[1], v[:, None], meshes[2].xyz)[:, 0]
+    ref = np.mean([Po(v) for v in V0], axis=0) + np.mean([f - Po(c) for f, c in zip(F1, C1)], axis=0)
+    err = mlq.field_norms(MS[2], mean - ref)[0]
+    assert err <= 1e-6 * mlq.field_norms(MS[2], ref)[0]
+    # the level difference is small against the field in H1(D)
+    y1 = np.mean([f - P(c) for f, c in zip(f1, c1)], axis=0)
+    assert mlq.field_norms(MS[2], y1)[1] < mlq.field_norms(MS[2], mean)[1]
