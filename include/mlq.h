@@ -236,6 +236,15 @@ int mlq_mlmc_combine(int L, const int64_t *N, const double *const *y, double *me
 int mlq_field_prolong(int dim, const int32_t *coarse_dims, const double *vc, double *vf);
 int mlq_field_norms(int dim, const int32_t *dims, const double *lengths, const double *e, double *l2, double *h1);
 
+/* Host helper: eq. PimpedML with nested sample rules, the multilevel
+ * quadrature for levels whose meshes are not nested (Sec. 4, Sec. 5.4):
+ *   est = sum_{l=0}^{L} (Q_l - Q_{l-1})(F_{L-l}),  Q_{-1} = 0,
+ * Q_l the mean over the first N_l points (1 <= N_0 <= ... <= N_L).  F[l]
+ * (host) holds F_{L-l}, the QoI computed on mesh L-l alone, at the first
+ * N_l points; each term needs one mesh, so no transfer between the meshes
+ * of different levels enters.  Sums in index order. */
+int mlq_pimped_ml_combine(int L, const int64_t *N, const double *const *F, double *est_out);
+
 /* Levels on general tetrahedral meshes (non-nested hierarchies; Sec. 4 and
  * the ventricle of Sec. 5.4): a self-contained FP64 member.  One object per
  * mesh; it owns its device arrays and uses the default stream.

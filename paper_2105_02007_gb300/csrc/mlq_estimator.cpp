@@ -210,3 +210,30 @@ extern "C" int mlq_field_norms(int dim, const int32_t *dims, const double *lengt
     if (h1) *h1 = std::sqrt(m2 + g2);
     return MLQ_OK;
 }
+
+// eq. PimpedML with nested sample rules (the non-nested levels of Sec. 5.4):
+//   QoI = sum_{l=0}^{L} (Q_l - Q_{l-1})(F_{L-l}),  Q_{-1} = 0,
+// Q_l the mean over the first N_l points (N_0 <= N_1 <= ... <= N_L).  Term l
+// needs the QoI on one mesh only (mesh L-l) at the first N_l points:
+// F[l][0..N_l-1].  Means are summed in index order.
+extern "C" int mlq_pimped_ml_combine(int L, const int64_t *N, const double *const *F, double *est_out)
+{
+    if (L < 0 || !N || !F || !est_out) return MLQ_EINVAL;
+    for (int l = 0; l <= L; ++l) {
+        if (N[l] < 1 || !F[l]) return MLQ_EINVAL;
+        if (l > 0 && N[l] < N[l - 1]) return MLQ_EINVAL;
+    }
+    double est = 0.0;
+    for (int l = 0; l <= L; ++l) {
+        double a = 0.0;
+        for (int64_t i = 0; i < N[l]; ++i) a += F[l][i];
+        est += a / (double)N[l];
+        if (l > 0) {
+            double b = 0.0;
+            for (int64_t i = 0; i < N[l - 1]; ++i) b += F[l][i];
+            est -= b / (double)N[l - 1];
+        }
+    }
+    *est_out = est;
+    return MLQ_OK;
+}

@@ -90,6 +90,7 @@ _lib.mlq_mlmc_combine.argtypes = [ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
 _lib.mlq_estimate_adaptive.argtypes = [_vp, ctypes.c_int, ctypes.c_double, _i64, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.mlq_field_prolong.argtypes = [ctypes.c_int, _vp, _vp, _vp]
 _lib.mlq_field_norms.argtypes = [ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
+_lib.mlq_pimped_ml_combine.argtypes = [ctypes.c_int, _vp, _vp, _vp]
 _lib.mlq_estimate.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.mlq_submit.argtypes = [_vp, _vp, _vp]
 _lib.mlq_poll.argtypes = [_vp, ctypes.c_uint64, _vp]
@@ -113,7 +114,7 @@ _lib.mlq_last_cuda_error.argtypes = [_vp]
 EXPORTED = ["mlq_default_options", "mlq_default_model", "mlq_create", "mlq_destroy", "mlq_set_options",
             "mlq_set_model", "mlq_add_level", "mlq_set_initial_state", "mlq_set_initial_disk", "mlq_set_kl",
             "mlq_build_kl", "mlq_centroid_table", "mlq_build_kl_mesh", "mlq_p1_at_points", "mlq_mesh_create",
-            "mlq_mesh_destroy", "mlq_mesh_set_kl", "mlq_mesh_solve", "mlq_mlmc_allocation", "mlq_mlmc_combine", "mlq_estimate_adaptive", "mlq_field_prolong", "mlq_field_norms", "mlq_solve", "mlq_solve_state", "mlq_set_points", "mlq_solve_points", "mlq_trace_prolong",
+            "mlq_mesh_destroy", "mlq_mesh_set_kl", "mlq_mesh_solve", "mlq_mlmc_allocation", "mlq_mlmc_combine", "mlq_pimped_ml_combine", "mlq_estimate_adaptive", "mlq_field_prolong", "mlq_field_norms", "mlq_solve", "mlq_solve_state", "mlq_set_points", "mlq_solve_points", "mlq_trace_prolong",
             "mlq_time_norms", "mlq_estimate", "mlq_workspace_bytes",
             "mlq_launch_count", "mlq_level_launch", "mlq_strerror", "mlq_last_cuda_error", "mlq_set_profiling",
             "mlq_member_profile", "mlq_autotune", "mlq_solve_noalloc", "mlq_synthesize", "mlq_submit", "mlq_poll", "mlq_serve_limits"]
@@ -611,3 +612,15 @@ def field_norms(m, e, lengths=None):
     _check(_lib.mlq_field_norms(dim, dims.ctypes.data_as(_vp), None if lg is None else lg.ctypes.data_as(_vp),
                                 a.ctypes.data_as(_vp), ctypes.byref(l2), ctypes.byref(h1)), "mlq_field_norms")
     return l2.value, h1.value
+
+
+def pimped_ml_combine(F_terms, N):
+    """eq. PimpedML over F_terms[l] = F_{L-l} at the first N[l] points
+    (mlq_pimped_ml_combine)."""
+    arrs = [np.ascontiguousarray(f, dtype=np.float64) for f in F_terms]
+    L = len(arrs) - 1
+    n = np.ascontiguousarray(N, dtype=np.int64)
+    ptrs = (_vp * (L + 1))(*[a.ctypes.data_as(_vp) for a in arrs])
+    est = ctypes.c_double()
+    _check(_lib.mlq_pimped_ml_combine(L, n.ctypes.data_as(_vp), ptrs, ctypes.byref(est)), "mlq_pimped_ml_combine")
+    return est.value

@@ -237,3 +237,12 @@ def test_field_norms_match_assembled_matrices(mlq, m):
     l2, h1 = mlq.field_norms(m, e)
     assert abs(l2 ** 2 - e @ M @ e) <= 1e-12 * (e @ M @ e)
     assert abs(h1 ** 2 - e @ (M + K) @ e) <= 1e-12 * (e @ (M + K) @ e)
+
+
+def test_pimped_ml_combine_matches_oracle(mlq):
+    rng = np.random.default_rng(12)
+    N = [3, 9, 27, 40]
+    F = [rng.normal(1.0 + l, 0.1, N[l]) for l in range(4)]
+    assert abs(mlq.pimped_ml_combine(F, N) - O.pimped_ml_estimate(F, N)) < 1e-14
+    with pytest.raises(mlq.MLQError):
+        mlq.pimped_ml_combine(F, [3, 2, 27, 40])            # rules must be nested

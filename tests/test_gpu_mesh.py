@@ -77,3 +77,34 @@ def test_mesh_level_rejects_bad_input(mlq):
     flat[0, 3] = flat[0, 2]                                  # degenerate tetrahedron
     with pytest.raises(mlq.MLQError):
         mlq.MeshLevel(xyz, flat)
+
+
+def test_pimped_ml_over_unrelated_shells_matches_oracle(mlq):
+    # eq. PimpedML over three unrelated shell meshes: term l is the QoI on
+    # mesh L-l alone at the first N_l points; the library's members and
+    # combination against the oracle's solves and combination (FP64 path)
+    meshes = [LV.lv_mesh(*d) for d in ((2, 6, 10), (2, 8, 14), (3, 11, 19))]
+    fine = O.unstructured_mesh(*meshes[-1])
+    modes, _ = O.kl_build(fine, 0.09, 0.15 ** 2, 4)
+    N = [2, 4, 8]
+    xi = inputs.gaussian_xi(40, 0, 0, N[-1], 4)
+    dt, nb = 0.05, 6
+    L = len(meshes) - 1
+    F_lib, F_or = [], []
+    for l in range(L + 1):
+        xyz, conn = meshes[L - l]
+        frames, alpha = LV.lv_fibres(xyz, conn)
+        mesh = O.unstructured_mesh(xyz, conn)
+        phi = O.centroid_table_unrelated(fine, modes, mesh)
+        v0, w0 = LV.stimulus(xyz, radius=0.4)
+        q_or = O.solve_batch(mesh, phi, xi[: N[l]], dt, nb, v0=v0, w0=w0, theta_mean=alpha, frames=frames,
+                             nthreads=2)[0]
+        with mlq.MeshLevel(xyz, conn, frames) as lvl:
+            lvl.set_kl(phi, alpha)
+            q, st, _ = lvl.solve(xi[: N[l]], dt, nb, v0, w0)
+        assert np.all(st == 0)
+        F_lib.append(q)
+        F_or.append(q_or)
+    est = mlq.pimped_ml_combine(F_lib, N)
+    ref = O.pimped_ml_estimate(F_or, N)
+    assert abs(est - ref) <= 1e-10 * abs(ref)
