@@ -116,6 +116,38 @@ typedef struct {
     int precond;
 } mlq_options;
 
+/* Time scheme and ionic model.
+ *   ionic 0  (the default): the two-variable FitzHugh-Nagumo model of
+ *            mlq_model, backward Euler for the diffusion, the reaction
+ *            explicit per block (every block matrix M + dt K is SPD).
+ *   ionic 1  the paper's scheme (Sec. 3.1 eq. st-system with the reaction of
+ *            eq. mono_disc on the new time level): per block
+ *              (M + theta dt K) u + dt M I_ion(u)
+ *                = (M - (1 - theta) dt K) u_k + dt M (theta g(t_{k+1}) + (1 - theta) g(t_k)),
+ *            I_ion(u) = alpha (u - u_rest)(u - u_th)(u - u_peak) (eq. ionic_term),
+ *            g the nodal values of the stimulus I_app(x, t) = (u_rest + amp
+ *            exp(-|x - x0|^2 / sigma^2)) for 0 <= t < t1 (Sec. 5.1);
+ *            theta = 1/2 is Crank-Nicolson, 1 backward Euler.  The nonlinear
+ *            block system is solved by chord-Newton sweeps (the FP64 residual
+ *            of the iterate, CG on M + theta dt K for the correction) to
+ *            ||F|| <= rtol ||rhs||, in both precisions; the start is u_rest
+ *            unless mlq_set_initial_state gives one.  2D levels only
+ *            (MLQ_EUNSUPPORTED with 3D levels); runs in the generic slab
+ *            kernel (Jacobi inner preconditioner).  s_l, s_t come from
+ *            mlq_model.
+ * mlq_default_scheme: ionic 0, theta 1, and the paper's constants alpha
+ * 1.4e-3, u_rest 0, u_th 28, u_peak 115, amp 115, t1 0.005, with sigma 0.1
+ * and x0 the origin (the paper leaves sigma and x0 to the geometry). */
+typedef struct {
+    int ionic;
+    double theta;
+    double alpha, u_rest, u_th, u_peak;
+    double amp, sigma, t1;
+    double x0[3];
+} mlq_scheme;
+int mlq_default_scheme(mlq_scheme *sc);
+int mlq_set_scheme(mlq_ctx *ctx, const mlq_scheme *sc);
+
 /* Fill *opt / *model with the defaults listed above (rtol 1e-13 for FP64,
  * rtol 1e-12 and rtol_inner 1e-5 for MIXED, max_iter 100000, max_sweeps 20,
  * precond 1 (multigrid) for MIXED and 0 for FP64; mlq_solve_noalloc always

@@ -19,7 +19,7 @@ Parity status per function (each is pinned by ``tests/test_oracle_pins.py``
 or, for the fibre frames, point location and eq. PimpedML,
 ``tests/test_oracle_lv.py``):
   mesh2d, mesh3d, assemble, kl_build, centroid_table, solve, solve_batch, solve_states,
-  solve_points, activation_time, time_norms,
+  solve_points, activation_time, time_norms, solve_paper, solve_paper_batch,
   p1_at_points, centroid_table_unrelated, mc_estimate, mlmc_estimate,
   qmc_estimate, pimped_ml_estimate: pinned.
 """
@@ -85,6 +85,9 @@ def _load():
                                        c.c_int64, _f64p, c.c_void_p, c.c_int, _f64p, _i64p, _i32p]
     lib.mlqo_p1_at_points.argtypes = [c.c_int, c.c_int64, _f64p, c.c_int64, _i32p, c.c_int, _f64p, c.c_int64,
                                       _f64p, _f64p, c.c_void_p, c.c_void_p]
+    lib.mlqo_solve_paper.argtypes = [c.c_int, c.c_int64, _f64p, c.c_int64, _i32p, _f64p, _f64p, c.c_double, c.c_int,
+                                     c.c_double, c.c_int64, _f64p, c.POINTER(c.c_double), c.POINTER(c.c_int64),
+                                     c.POINTER(c.c_int32)]
     lib.mlqo_max_threads.restype = c.c_int
     _lib = lib
     return lib
@@ -372,6 +375,55 @@ def time_norms(e: np.ndarray, T: float):
     l2sq = float(np.sum(dt / 6.0 * (e[:-1] ** 2 + 4.0 * mid ** 2 + e[1:] ** 2)))
     h1sq = float(np.sum(((e[1:] - e[:-1]) / dt) ** 2 * dt))
     return np.sqrt(l2sq), np.sqrt(l2sq + h1sq)
+
+
+# The paper's scheme: Crank-Nicolson (theta = 1/2) or backward Euler
+# (theta = 1) slabs, the one-variable ionic current of eq. ionic_term on the
+# new time level, the stimulus I_app of Sec. 5.1, Newton's method.
+PAPER_MODEL = dict(s_l=1.0, s_t=0.2, alpha=1.4e-3, u_rest=0.0, u_th=28.0, u_peak=115.0, theta=0.5,
+                   amp=115.0, sigma=0.1, t1=0.005, x0=(0.0, 0.0, 0.0))
+
+
+def _paper_vec(pm):
+    p = dict(PAPER_MODEL)
+    p.update(pm or {})
+    x0 = list(p["x0"]) + [0.0] * (3 - len(p["x0"]))
+    return np.array([p["s_l"], p["s_t"], p["alpha"], p["u_rest"], p["u_th"], p["u_peak"], p["theta"], p["amp"],
+                     p["sigma"], p["t1"], x0[0], x0[1], x0[2]], dtype=np.float64)
+
+
+def solve_paper(mesh: Mesh, theta, dt: float, nsteps: int, u0=None, pm=None, rtol: float = 1e-13,
+                maxit: int | None = None):
+    """One sample of the paper's scheme (see mlq_oracle.c).  Returns (Q,
+    u_final, Newton steps, status).  u0 defaults to u_rest everywhere."""
+    lib = _load()
+    p = _paper_vec(pm)
+    u = np.full(mesh.n, p[3]) if u0 is None else np.array(u0, dtype=np.float64)
+    q = ctypes.c_double()
+    nw = ctypes.c_int64()
+    st = ctypes.c_int32()
+    maxit = 10 * mesh.n if maxit is None else maxit
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    assert lib.mlqo_solve_paper(mesh.dim, mesh.n, mesh.xyz, mesh.ne, mesh.conn, th, p, dt, nsteps, rtol, maxit, u,
+                                ctypes.byref(q), ctypes.byref(nw), ctypes.byref(st)) == 0
+    return q.value, u, nw.value, st.value
+
+
+def solve_paper_batch(mesh: Mesh, phi: np.ndarray, xi: np.ndarray, dt: float, nsteps: int, u0=None, pm=None,
+                      theta_mean=None, rtol: float = 1e-13):
+    """S samples of the paper's scheme, theta_e = theta_mean_e + sum_k
+    phi[e, k] xi[s, k] (eq. KLlowrank).  Returns (Q[S], u[S, n], status[S])."""
+    xi = np.atleast_2d(np.asarray(xi, dtype=np.float64))
+    S = xi.shape[0]
+    q = np.zeros(S)
+    U = np.zeros((S, mesh.n))
+    st = np.zeros(S, dtype=np.int32)
+    for s in range(S):
+        th = np.asarray(phi, dtype=np.float64) @ xi[s]
+        if theta_mean is not None:
+            th = th + np.asarray(theta_mean, dtype=np.float64)
+        q[s], U[s], _, st[s] = solve_paper(mesh, th, dt, nsteps, u0=u0, pm=pm, rtol=rtol)
+    return q, U, st
 
 
 def p1_at_points(mesh: Mesh, f: np.ndarray, pts: np.ndarray, return_location: bool = False):

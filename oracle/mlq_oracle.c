@@ -938,6 +938,146 @@ int mlqo_solve_batch(int d, int64_t n, const double *xyz, int64_t ne, const int3
                               v0, w0, nthreads, q_out, iters, status);
 }
 
+/* ------------------------------------------------------------------------ */
+/* The paper's time discretization (Sec. 3.1 eq. st-system with the reaction  */
+/* of eq. mono_disc; the model of eq. ionic_term, the stimulus of Sec. 5.1). */
+/* ------------------------------------------------------------------------ */
+
+/* Parameters pm, in this order: s_l, s_t, alpha, u_rest, u_th, u_peak,
+ * theta, amp, sigma, t1, x0, y0, z0.
+ *   I_ion(u)   = alpha (u - u_rest)(u - u_th)(u - u_peak)           (eq. ionic_term)
+ *   I_app(x,t) = (u_rest + amp exp(-|x - x0|^2 / sigma^2)) for 0 <= t < t1, else 0
+ * One time block k -> k+1 (theta = 1/2: Crank-Nicolson, eq. st-system; 1:
+ * backward Euler), the reaction on the new time level (eq. mono_disc):
+ *   F(u) = (M + theta dt K) u + dt M I_ion(u)
+ *          - (M - (1 - theta) dt K) u_k - dt M (theta g(t_{k+1}) + (1 - theta) g(t_k)) = 0
+ * with g(t) the nodal values of I_app(., t), t_k = k dt.  Newton's method
+ * from u_k: J(u) = M + theta dt K + dt M diag(I_ion'(u)) (not symmetric),
+ * J d = -F(u) by BiCGSTAB with a Jacobi preconditioner, until ||F|| <=
+ * rtol ||c||, c the u-independent part. */
+static double ionic(const double *pm, double u) { return pm[2] * (u - pm[3]) * (u - pm[4]) * (u - pm[5]); }
+
+static double ionic_deriv(const double *pm, double u)
+{
+    const double a = pm[3], b = pm[4], c = pm[5];
+    return pm[2] * ((u - b) * (u - c) + (u - a) * (u - c) + (u - a) * (u - b));
+}
+
+static double iapp(int d, const double *x, const double *pm, double t)
+{
+    if (!(t >= 0.0 && t < pm[9])) return 0.0;
+    double r2 = 0.0;
+    for (int c = 0; c < d; ++c) r2 += (x[c] - pm[10 + c]) * (x[c] - pm[10 + c]);
+    return pm[3] + pm[7] * exp(-r2 / (pm[8] * pm[8]));
+}
+
+/* BiCGSTAB (van der Vorst) with right Jacobi preconditioning for the CSR
+ * values jval (pattern P): solve J x = b from x = 0 to ||b - J x|| <=
+ * rtol ||b||.  Work vectors of length n: r rh p v s t y z.  Returns the
+ * iterations (or -1 on breakdown / non-finite values). */
+static int64_t bicgstab(const pattern_t *P, const double *jval, const double *dinv, const double *b, double *x,
+                        double rtol, int64_t maxit, double *r, double *rh, double *p, double *v, double *s, double *t,
+                        double *y, double *z)
+{
+    const int64_t n = P->n;
+    for (int64_t i = 0; i < n; ++i) { x[i] = 0.0; r[i] = b[i]; rh[i] = b[i]; p[i] = 0.0; v[i] = 0.0; }
+    const double bnorm = sqrt(dot(n, b, b));
+    if (bnorm == 0.0) return 0;
+    double rho = 1.0, alpha = 1.0, omega = 1.0;
+    for (int64_t it = 0; it < maxit; ++it) {
+        const double rho_new = dot(n, rh, r);
+        if (rho_new == 0.0 || !isfinite(rho_new)) return -1;
+        const double beta = (rho_new / rho) * (alpha / omega);
+        for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+        for (int64_t i = 0; i < n; ++i) y[i] = dinv[i] * p[i];
+        csr_apply(P, jval, y, v);
+        alpha = rho_new / dot(n, rh, v);
+        for (int64_t i = 0; i < n; ++i) s[i] = r[i] - alpha * v[i];
+        if (sqrt(dot(n, s, s)) <= rtol * bnorm) {
+            for (int64_t i = 0; i < n; ++i) x[i] += alpha * y[i];
+            return it + 1;
+        }
+        for (int64_t i = 0; i < n; ++i) z[i] = dinv[i] * s[i];
+        csr_apply(P, jval, z, t);
+        omega = dot(n, t, s) / dot(n, t, t);
+        for (int64_t i = 0; i < n; ++i) x[i] += alpha * y[i] + omega * z[i];
+        for (int64_t i = 0; i < n; ++i) r[i] = s[i] - omega * t[i];
+        rho = rho_new;
+        const double rn = sqrt(dot(n, r, r));
+        if (!isfinite(rn)) return -1;
+        if (rn <= rtol * bnorm) return it + 1;
+    }
+    return maxit;
+}
+
+/* Public: one sample of the paper's scheme with angle field theta (per
+ * element).  u (length n) holds the initial potential on entry and the
+ * final one on exit; q_out = m^T u(T); newton_out = Newton steps summed over
+ * the blocks (may be NULL); status (may be NULL). */
+int mlqo_solve_paper(int d, int64_t n, const double *xyz, int64_t ne, const int32_t *conn, const double *theta,
+                     const double *pm, double dt, int nsteps, double rtol, int64_t maxit, double *u, double *q_out,
+                     int64_t *newton_out, int32_t *status)
+{
+    problem_t pr;
+    int st = problem_setup(d, n, xyz, ne, conn, &pr);
+    if (st != MLQO_OK) { problem_free(&pr); return st; }
+    const pattern_t *P = &pr.P;
+    const int64_t nnz = P->nnz;
+    const double th = pm[6];
+    double *kval = malloc(sizeof(double) * (size_t)nnz), *aval = malloc(sizeof(double) * (size_t)nnz);
+    double *jval = malloc(sizeof(double) * (size_t)nnz), *dinv = malloc(sizeof(double) * (size_t)n);
+    double *w[14];
+    for (int k = 0; k < 14; ++k) w[k] = malloc(sizeof(double) * (size_t)n);
+    double *c = w[0], *F = w[1], *du = w[2], *gk = w[3], *gk1 = w[4], *tmp = w[5];
+    assemble(d, xyz, ne, conn, theta, NULL, pm[0], pm[1], P, NULL, kval);
+    for (int64_t t = 0; t < nnz; ++t) aval[t] = pr.mval[t] + th * dt * kval[t];
+    int64_t newton = 0;
+    int sst = MLQO_S_CONVERGED;
+    for (int k = 0; k < nsteps && sst != MLQO_S_NONFINITE; ++k) {
+        for (int64_t i = 0; i < n; ++i) {
+            gk[i] = iapp(d, xyz + i * d, pm, k * dt);
+            gk1[i] = iapp(d, xyz + i * d, pm, (k + 1) * dt);
+        }
+        /* c = M u_k - (1 - theta) dt K u_k + dt M (theta g_{k+1} + (1 - theta) g_k) */
+        for (int64_t i = 0; i < n; ++i) tmp[i] = u[i] + dt * (th * gk1[i] + (1.0 - th) * gk[i]);
+        csr_apply(P, pr.mval, tmp, c);
+        csr_apply(P, kval, u, tmp);
+        for (int64_t i = 0; i < n; ++i) c[i] -= (1.0 - th) * dt * tmp[i];
+        const double cnorm = sqrt(dot(n, c, c));
+        int conv = 0;
+        for (int it = 0; it < 100; ++it) {
+            /* F = A u + dt M I(u) - c */
+            csr_apply(P, aval, u, F);
+            for (int64_t i = 0; i < n; ++i) tmp[i] = ionic(pm, u[i]);
+            csr_apply(P, pr.mval, tmp, du);
+            for (int64_t i = 0; i < n; ++i) F[i] += dt * du[i] - c[i];
+            const double fn = sqrt(dot(n, F, F));
+            if (!isfinite(fn)) { sst = MLQO_S_NONFINITE; break; }
+            if (fn <= rtol * cnorm) { conv = 1; break; }
+            /* J = A + dt M diag(I'(u)): column j of M scaled by I'(u_j) */
+            for (int64_t i = 0; i < n; ++i)
+                for (int64_t t = P->rp[i]; t < P->rp[i + 1]; ++t)
+                    jval[t] = aval[t] + dt * pr.mval[t] * ionic_deriv(pm, u[P->ci[t]]);
+            for (int64_t i = 0; i < n; ++i) dinv[i] = 1.0 / jval[find_col(P, i, (int32_t)i)];
+            for (int64_t i = 0; i < n; ++i) F[i] = -F[i];
+            if (bicgstab(P, jval, dinv, F, du, 1e-3 * rtol, maxit, w[6], w[7], w[8], w[9], w[10], w[11], w[12],
+                         w[13]) < 0) { sst = MLQO_S_NONFINITE; break; }
+            for (int64_t i = 0; i < n; ++i) u[i] += du[i];
+            ++newton;
+        }
+        if (!conv && sst == MLQO_S_CONVERGED) sst = MLQO_S_MAXITER;
+    }
+    double Q = dot(n, pr.mlump, u);
+    if (!isfinite(Q)) sst = MLQO_S_NONFINITE;
+    *q_out = Q;
+    if (newton_out) *newton_out = newton;
+    if (status) *status = sst;
+    free(kval); free(aval); free(jval); free(dinv);
+    for (int k = 0; k < 14; ++k) free(w[k]);
+    problem_free(&pr);
+    return MLQO_OK;
+}
+
 /* Public: number of OpenMP threads a parallel region would use. */
 int mlqo_max_threads(void)
 {

@@ -108,6 +108,7 @@ struct mlq_ctx {
     // serving worker, created by the first mlq_submit (under mu) and read by
     // mlq_poll without it
     std::atomic<Server *> server{nullptr};
+    mlq_scheme scheme{};       // time scheme and ionic model (mlq_set_scheme); ionic 0 = FHN
     int serve_lanes = 4;       // mlq_serve_limits (4 measured best of 1, 2, 4, 6 on the 50/s stream)
     size_t serve_budget = 0;
     int device = 0;
@@ -268,7 +269,8 @@ bool uses_mg3(const mlq_ctx *ctx, const Level &L)
 Shape choose_launch(mlq_ctx *ctx, const Level &L, int64_t S = 0)
 {
     if (L.dim == 3) return choose_launch_3d(ctx, L, S);
-    if (ctx->opt.precision == MLQ_MIXED && ctx->opt.precond == 1 && ctx->opt.storage != 2) {
+    const bool paper = ctx->scheme.ionic == 1;   // the paper's scheme runs in the generic slab kernel
+    if (!paper && ctx->opt.precision == MLQ_MIXED && ctx->opt.precond == 1 && ctx->opt.storage != 2) {
         if (L.tuned_cs > 0 && L.tuned_mg && ctx->opt.cluster <= 0 && ctx->opt.threads <= 0) {
             Shape sh{L.tuned_cs, L.tuned_threads, true, (size_t)mlq::mg_plan(L.m, L.tuned_cs).total, L.tuned_npt};
             sh.mg = true;
@@ -285,7 +287,7 @@ Shape choose_launch(mlq_ctx *ctx, const Level &L, int64_t S = 0)
     const int limit = ctx->smem_optin - 2048;  // room for the static reduction buffers
     const bool allow = ctx->opt.storage != 2;
     // mixed path: the register-resident kernel when a shape fits
-    if (ti == 4 && allow) {
+    if (ti == 4 && allow && !paper) {
         if (L.tuned_cs > 0 && !L.tuned_mg && ctx->opt.cluster <= 0 && ctx->opt.threads <= 0) {
             const mlq::RegPlan rp = mlq::reg_plan(L.m, L.tuned_cs);
             return Shape{L.tuned_cs, L.tuned_threads, true, (size_t)rp.total, L.tuned_npt};
@@ -692,7 +694,9 @@ int launch_member_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream_t
     // K2: stencil of A = M + dt K(theta)
     if (phase & kSetup) {
         dim3 blk(256), grd((unsigned)((L.n + 255) / 256), (unsigned)mb.S);
-        mlq::stencil_setup_kernel<<<grd, blk, 0, st>>>(mb.cs2, L.m, L.h, L.dt, ctx->model.s_l, ctx->model.s_t,
+        // A = M + theta dt K (theta = 1 unless the paper's Crank-Nicolson scheme is set)
+        const double dtk = ctx->scheme.ionic == 1 ? ctx->scheme.theta * L.dt : L.dt;
+        mlq::stencil_setup_kernel<<<grd, blk, 0, st>>>(mb.cs2, L.m, L.h, dtk, ctx->model.s_l, ctx->model.s_t,
                                                          (int)mb.S, mb.A64, mixed ? (float *)mb.Ai : nullptr);
         MLQ_CUDA(ctx, cudaGetLastError());
         ctx->launches++;
@@ -731,6 +735,25 @@ int launch_member_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream_t
     a.iters = mb.iters;
     a.status = mb.status;
     a.pq = mb.pq;
+    if (ctx->scheme.ionic == 1) {
+        const mlq_scheme &sc = ctx->scheme;
+        a.scheme = 1;
+        a.theta = sc.theta;
+        a.alpha = sc.alpha;
+        a.u_rest = sc.u_rest;
+        a.u_th = sc.u_th;
+        a.u_peak = sc.u_peak;
+        a.amp = sc.amp;
+        a.sigma2 = sc.sigma * sc.sigma;
+        a.t1 = sc.t1;
+        a.x0 = sc.x0[0];
+        a.y0 = sc.x0[1];
+        // chord-Newton sweeps in both precisions (the FP64 path too)
+        a.max_sweeps = std::max(ctx->opt.max_sweeps, 60);
+    } else {
+        a.scheme = 0;
+        a.theta = 1.0;
+    }
     const Shape sh = choose_launch(ctx, L, mb.S);
     if (ctx->opt.storage == 1 && !sh.resident) return MLQ_EUNSUPPORTED;
     const bool timed = ctx->profile && slot >= 0 && slot < kStreams;
@@ -1010,6 +1033,35 @@ int mlq_set_options(mlq_ctx *ctx, const mlq_options *opt)
     return MLQ_OK;
 }
 
+int mlq_default_scheme(mlq_scheme *sc)
+{
+    if (!sc) return MLQ_EINVAL;
+    sc->ionic = 0;
+    sc->theta = 1.0;
+    sc->alpha = 1.4e-3;
+    sc->u_rest = 0.0;
+    sc->u_th = 28.0;
+    sc->u_peak = 115.0;
+    sc->amp = 115.0;
+    sc->sigma = 0.1;
+    sc->t1 = 0.005;
+    sc->x0[0] = sc->x0[1] = sc->x0[2] = 0.0;
+    return MLQ_OK;
+}
+
+int mlq_set_scheme(mlq_ctx *ctx, const mlq_scheme *sc)
+{
+    MLQ_GUARD(ctx);
+    if (!ctx || !sc || (sc->ionic != 0 && sc->ionic != 1)) return MLQ_EINVAL;
+    if (sc->ionic == 1 && !(sc->theta > 0.0 && sc->theta <= 1.0 && std::isfinite(sc->alpha) && sc->sigma > 0.0))
+        return MLQ_EINVAL;
+    for (const Level &L : ctx->levels)
+        if (L.defined && L.dim == 3 && sc->ionic == 1) return MLQ_EUNSUPPORTED;
+    ctx->scheme = *sc;
+    ctx->generation++;
+    return MLQ_OK;
+}
+
 int mlq_set_model(mlq_ctx *ctx, const mlq_model *m)
 {
     MLQ_GUARD(ctx);
@@ -1027,6 +1079,7 @@ int mlq_add_level(mlq_ctx *ctx, int level, int dim, const int32_t *dims, const d
     if (!ctx || !dims || level < 0 || level >= kMaxLevels) return MLQ_EINVAL;
     if (dim != 2 && dim != 3) return MLQ_EINVAL;
     if (!(dt > 0.0) || nsteps < 0) return MLQ_EINVAL;
+    if (dim == 3 && ctx->scheme.ionic == 1) return MLQ_EUNSUPPORTED;   // the paper's scheme is 2D only
     if (dim == 3) {
         const int64_t nn = (int64_t)dims[0] * dims[1] * dims[2];
         // nine stencil slots of a sample must stay within 32-bit indices

@@ -97,7 +97,39 @@ struct SolveArgs {
     double *q;                    // [S]
     int32_t *iters, *status;      // [S]
     PointArgs pq;                 // point QoIs (npts = 0: none)
+    // time scheme: 0 = the two-variable FHN with the reaction explicit per
+    // block (backward Euler); 1 = the paper's scheme (PaperScheme below)
+    int scheme;
+    double theta;                 // 1 backward Euler, 0.5 Crank-Nicolson (the stencil holds M + theta dt K)
+    double alpha, u_rest, u_th, u_peak;       // I_ion(u) = alpha (u - u_rest)(u - u_th)(u - u_peak)
+    double amp, sigma2, t1, x0, y0;           // I_app = (u_rest + amp exp(-|x - x0|^2 / sigma2)) on [0, t1)
 };
+
+// The paper's time scheme (Sec. 3.1 eq. st-system with eq. mono_disc, the
+// current of eq. ionic_term, the stimulus of Sec. 5.1), per block k -> k+1:
+//   (M + theta dt K) u + dt M I_ion(u) = c,
+//   c = (M - (1 - theta) dt K) u_k + dt M (theta g(t_{k+1}) + (1 - theta) g(t_k)),
+// g the nodal stimulus.  With A = M + theta dt K the kernels form
+// c = M y - ((1 - theta) / theta) A u_k, y = u_k / theta + dt (theta g_{k+1} +
+// (1 - theta) g_k), and solve the nonlinear system by chord-Newton sweeps:
+// the FP64 residual F = c - A u - dt M I_ion(u) of the current iterate, an
+// inner PCG on A d = F, u += d, until ||F|| <= rtol ||c||.  A stays the SPD
+// matrix of the set-up, so the inner solver is CG; the sweeps converge
+// linearly with the factor ~ dt max |I_ion'| (about 0.07 at the paper's
+// dt and constants) to the same root as Newton with the full Jacobian.
+template <typename A>
+__device__ __forceinline__ double paper_ionic(const A &g, double u)
+{
+    return g.alpha * (u - g.u_rest) * (u - g.u_th) * (u - g.u_peak);
+}
+
+template <typename A>
+__device__ __forceinline__ double paper_stimulus(const A &g, double x, double y, double t)
+{
+    if (!(t >= 0.0 && t < g.t1)) return 0.0;
+    const double dx = x - g.x0, dy = y - g.y0;
+    return g.u_rest + g.amp * exp(-(dx * dx + dy * dy) / g.sigma2);
+}
 
 template <typename T>
 __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
@@ -466,6 +498,9 @@ __global__ void __launch_bounds__(512, 1) slab_solve_kernel(SolveArgs<TI> g)
         if (g.v0) {
             v0 = g.v0[node];
             w0 = g.w0 ? g.w0[node] : 0.0;
+        } else if (g.scheme == 1) {
+            v0 = g.u_rest;   // the paper's scheme starts at rest; the stimulus excites
+            w0 = 0.0;
         } else {
             const int j = node / m, i = node - j * m;
             const double xx = (double)i / (double)(m - 1), yy = (double)j / (double)(m - 1);
@@ -479,6 +514,8 @@ __global__ void __launch_bounds__(512, 1) slab_solve_kernel(SolveArgs<TI> g)
     PointState pst;
     const bool pth = rank == 0 && tid < g.pq.npts;   // point QoI threads
     if (pth) point_record(g.pq, sample, g.nsteps, g.dt, v, pst);
+    const bool paper = g.scheme == 1;
+    const double hgrid = 1.0 / (double)(m - 1);
 
     int wpar = 0;
     int64_t total_iters = 0;     // thread 0's count
@@ -490,22 +527,52 @@ __global__ void __launch_bounds__(512, 1) slab_solve_kernel(SolveArgs<TI> g)
         // ---- block load
         const double *wcur = wb0 + wpar * SN;
         double *wnext = wb0 + (wpar ^ 1) * SN;
+        const double cpre = paper ? (1.0 - g.theta) / g.theta : 0.0;
         for (int node = tile0 + tid; node < tile1; node += nt) {
             const double vv = ldcg(v + node), ww = ldcg(wcur + node);
-            ytile[node - tile0] = vv + dt * reaction<mixed>(vv, ww, g.a);
+            if (paper) {
+                const int j = node / m, i = node - j * m;
+                const double x = i * hgrid, y = j * hgrid;
+                ytile[node - tile0] = vv / g.theta + dt * (g.theta * paper_stimulus(g, x, y, (step + 1) * dt) +
+                                                           (1.0 - g.theta) * paper_stimulus(g, x, y, step * dt));
+            } else {
+                ytile[node - tile0] = vv + dt * reaction<mixed>(vv, ww, g.a);
+            }
         }
         __syncthreads();
+        if (paper) {
+            // c = M y - ((1 - theta) / theta) A u_k, then the ionic current of the
+            // iterate (u_k) into the tile for the first residual
+            NodeWalk nw;
+            nw.init(own0 + tid, nt, m);
+            for (int l = tid; l < nown; l += nt, nw.next()) {
+                const int node = own0 + l;
+                double bb = mass_apply(m, nw.i, nw.j, g.h2, ytile, node - tile0);
+                if (cpre != 0.0) bb -= cpre * stencil_apply_global(A64, n, m, node, nw.i, nw.j, v);
+                b[node] = bb;
+            }
+            __syncthreads();
+            for (int node = tile0 + tid; node < tile1; node += nt) ytile[node - tile0] = paper_ionic(g, ldcg(v + node));
+            __syncthreads();
+        }
         {
             double acc[2] = {0.0, 0.0};
             NodeWalk nw;
             nw.init(own0 + tid, nt, m);
             for (int l = tid; l < nown; l += nt, nw.next()) {
                 const int node = own0 + l;
-                const double bb = mass_apply(m, nw.i, nw.j, g.h2, ytile, node - tile0);
-                b[node] = bb;
-                const double vv = v[node], ww = wcur[node];
-                wnext[node] = ww + dt * g.eps * recovery<mixed>(vv, ww, g.gam);
-                const double rr = bb - stencil_apply_global(A64, n, m, node, nw.i, nw.j, v);
+                double bb, rr;
+                if (paper) {
+                    bb = b[node];
+                    rr = bb - stencil_apply_global(A64, n, m, node, nw.i, nw.j, v) -
+                         dt * mass_apply(m, nw.i, nw.j, g.h2, ytile, node - tile0);
+                } else {
+                    bb = mass_apply(m, nw.i, nw.j, g.h2, ytile, node - tile0);
+                    b[node] = bb;
+                    const double vv = v[node], ww = wcur[node];
+                    wnext[node] = ww + dt * g.eps * recovery<mixed>(vv, ww, g.gam);
+                    rr = bb - stencil_apply_global(A64, n, m, node, nw.i, nw.j, v);
+                }
                 R[l] = (TI)rr;
                 acc[0] += bb * bb;
                 acc[1] += rr * rr;
@@ -529,11 +596,19 @@ __global__ void __launch_bounds__(512, 1) slab_solve_kernel(SolveArgs<TI> g)
         for (int sweep = 0; sweep < g.max_sweeps; ++sweep) {
             if (sweep > 0) {
                 double racc[1] = {0.0};
+                if (paper) {
+                    // the ionic current of the iterate (the tile's FP64 slots are
+                    // free between inner solves)
+                    for (int node = tile0 + tid; node < tile1; node += nt)
+                        ytile[node - tile0] = paper_ionic(g, ldcg(v + node));
+                    __syncthreads();
+                }
                 NodeWalk nw;
                 nw.init(own0 + tid, nt, m);
                 for (int l = tid; l < nown; l += nt, nw.next()) {
                     const int node = own0 + l;
-                    const double rr = b[node] - stencil_apply_global(A64, n, m, node, nw.i, nw.j, v);
+                    double rr = b[node] - stencil_apply_global(A64, n, m, node, nw.i, nw.j, v);
+                    if (paper) rr -= dt * mass_apply(m, nw.i, nw.j, g.h2, ytile, node - tile0);
                     R[l] = (TI)rr;
                     racc[0] += rr * rr;
                 }
@@ -543,7 +618,10 @@ __global__ void __launch_bounds__(512, 1) slab_solve_kernel(SolveArgs<TI> g)
                 if (!isfinite(rnorm2)) { nonfinite = true; break; }
             }
             if (rnorm2 <= tol_out2) { solved = true; break; }
-            const double tol_in2 = mixed ? g.rtol_in * g.rtol_in * rnorm2 : tol_out2;
+            // the paper's scheme: each sweep is one chord-Newton step, whose
+            // linear system needs no more than the contraction of the step
+            const double tol_in2 = paper ? fmax((mixed ? g.rtol_in * g.rtol_in : 1e-12) * rnorm2, 0.25 * tol_out2)
+                                         : (mixed ? g.rtol_in * g.rtol_in * rnorm2 : tol_out2);
 
             // ---- inner PCG init: u0 = D^-1 r0 on the tile, w0 = A u0, x = 0
             for (int l = tid; l < nown; l += nt) utile[l + ushift] = R[l] * Dinv[own0 + l];
@@ -659,7 +737,7 @@ __global__ void __launch_bounds__(512, 1) slab_solve_kernel(SolveArgs<TI> g)
             if (nonfinite) break;
             for (int l = tid; l < nown; l += nt) v[own0 + l] = v[own0 + l] + (double)X[l];
             cl.sync();
-            if (!mixed) break;
+            if (!mixed && !paper) break;
         }
         if (nonfinite) {
             status = S_NONFINITE;

@@ -38,6 +38,13 @@ class Model(ctypes.Structure):
                 ("eps", ctypes.c_double), ("gamma", ctypes.c_double), ("T", ctypes.c_double)]
 
 
+class Scheme(ctypes.Structure):
+    _fields_ = [("ionic", ctypes.c_int), ("theta", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("u_rest", ctypes.c_double), ("u_th", ctypes.c_double), ("u_peak", ctypes.c_double),
+                ("amp", ctypes.c_double), ("sigma", ctypes.c_double), ("t1", ctypes.c_double),
+                ("x0", ctypes.c_double * 3)]
+
+
 class Request(ctypes.Structure):
     _fields_ = [("level", ctypes.c_int), ("samples", ctypes.c_int64), ("xi", ctypes.c_void_p),
                 ("target_rmse", ctypes.c_double), ("chunk", ctypes.c_int32)]
@@ -91,6 +98,8 @@ _lib.mlq_estimate_adaptive.argtypes = [_vp, ctypes.c_int, ctypes.c_double, _i64,
 _lib.mlq_field_prolong.argtypes = [ctypes.c_int, _vp, _vp, _vp]
 _lib.mlq_field_norms.argtypes = [ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
 _lib.mlq_pimped_ml_combine.argtypes = [ctypes.c_int, _vp, _vp, _vp]
+_lib.mlq_default_scheme.argtypes = [_vp]
+_lib.mlq_set_scheme.argtypes = [_vp, _vp]
 _lib.mlq_estimate.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.mlq_submit.argtypes = [_vp, _vp, _vp]
 _lib.mlq_poll.argtypes = [_vp, ctypes.c_uint64, _vp]
@@ -111,7 +120,7 @@ _lib.mlq_strerror.argtypes = [ctypes.c_int]
 _lib.mlq_last_cuda_error.restype = ctypes.c_char_p
 _lib.mlq_last_cuda_error.argtypes = [_vp]
 
-EXPORTED = ["mlq_default_options", "mlq_default_model", "mlq_create", "mlq_destroy", "mlq_set_options",
+EXPORTED = ["mlq_default_options", "mlq_default_model", "mlq_default_scheme", "mlq_set_scheme", "mlq_create", "mlq_destroy", "mlq_set_options",
             "mlq_set_model", "mlq_add_level", "mlq_set_initial_state", "mlq_set_initial_disk", "mlq_set_kl",
             "mlq_build_kl", "mlq_centroid_table", "mlq_build_kl_mesh", "mlq_p1_at_points", "mlq_mesh_create",
             "mlq_mesh_destroy", "mlq_mesh_set_kl", "mlq_mesh_solve", "mlq_mlmc_allocation", "mlq_mlmc_combine", "mlq_pimped_ml_combine", "mlq_estimate_adaptive", "mlq_field_prolong", "mlq_field_norms", "mlq_solve", "mlq_solve_state", "mlq_set_points", "mlq_solve_points", "mlq_trace_prolong",
@@ -358,6 +367,20 @@ class Context:
 
     def set_model(self, **kw):
         _check(_lib.mlq_set_model(self._h, ctypes.byref(default_model(**kw))), "mlq_set_model", self._h)
+
+    def set_scheme(self, **kw):
+        """Time scheme and ionic model (mlq_set_scheme): ionic=1 selects the
+        paper's scheme; other keys override mlq_default_scheme's values
+        (x0 as a sequence)."""
+        sc = Scheme()
+        _lib.mlq_default_scheme(ctypes.byref(sc))
+        for k, v in kw.items():
+            if k == "x0":
+                for i, c in enumerate(v):
+                    sc.x0[i] = float(c)
+            else:
+                setattr(sc, k, v)
+        _check(_lib.mlq_set_scheme(self._h, ctypes.byref(sc)), "mlq_set_scheme", self._h)
 
     def add_level(self, level: int, m, dt: float, nsteps: int, lengths=None):
         """Level on m x m nodes (2D) or m = (mx, my, mz) nodes of the box with

@@ -580,3 +580,73 @@ def test_time_norms_match_quadrature_of_the_interpolant():
     # a linear function: |e|_{H1}^2 = slope^2 T, ||e||^2 = T (e0^2 + e0 e1 + e1^2) / 3
     l2, h1 = O.time_norms(np.linspace(1.0, 3.0, 9), 2.0)
     assert abs(l2 ** 2 - 2.0 * (1 + 3 + 9) / 3) < 1e-12 and abs(h1 ** 2 - l2 ** 2 - 2.0) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# the paper's scheme (eq. st-system, eq. mono_disc, eq. ionic_term)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("th", [0.5, 1.0])
+def test_paper_scheme_linear_mode_amplification(th):
+    # alpha = 0, no stimulus: an eigenvector K phi = lam M phi (scipy's
+    # generalised eigensolver) is multiplied per block by the theta-scheme's
+    # amplification factor (1 - (1 - theta) dt lam) / (1 + theta dt lam)
+    mesh = O.mesh2d(7)
+    tfield = np.full(mesh.ne, 0.4)
+    rp, ci, mv, kv = O.assemble(mesh, tfield, SL, ST)
+    M = O.csr_to_dense(rp, ci, mv, mesh.n)
+    K = O.csr_to_dense(rp, ci, kv, mesh.n)
+    lam, vec = scipy.linalg.eigh(K, M)
+    j = 5
+    phi = vec[:, j] / np.max(np.abs(vec[:, j]))
+    dt, nb = 0.05, 7
+    pm = dict(s_l=SL, s_t=ST, alpha=0.0, amp=0.0, theta=th)
+    q, u, nw, st = O.solve_paper(mesh, tfield, dt, nb, u0=phi, pm=pm)
+    rho = (1 - (1 - th) * dt * lam[j]) / (1 + th * dt * lam[j])
+    assert st == 0
+    assert np.max(np.abs(u - rho ** nb * phi)) < 1e-12
+
+
+def test_paper_scheme_uniform_state_is_the_scalar_implicit_recurrence():
+    # no stimulus and a constant state: K 1 = 0 and M c 1 = c M 1, so every
+    # node follows u+ + dt I_ion(u+) = u (whatever theta), solved here by a
+    # scalar Newton iteration
+    mesh = O.mesh2d(9)
+    tfield = np.linspace(-1.0, 1.0, mesh.ne)
+    a, ur, uth, up = 1.4e-3, 0.0, 28.0, 115.0
+    pm = dict(alpha=a, u_rest=ur, u_th=uth, u_peak=up, amp=0.0, theta=0.5)
+    dt, nb = 0.05, 30
+    q, u, nw, st = O.solve_paper(mesh, tfield, dt, nb, u0=np.full(mesh.n, 35.0), pm=pm)
+    x = 35.0
+    for _ in range(nb):
+        y = x
+        for _ in range(60):
+            f = y + dt * a * (y - ur) * (y - uth) * (y - up) - x
+            df = 1 + dt * a * ((y - uth) * (y - up) + (y - ur) * (y - up) + (y - ur) * (y - uth))
+            y -= f / df
+        x = y
+    assert st == 0 and x > 35.0                     # above threshold: the cell activates
+    assert np.max(np.abs(u - x)) < 1e-10 * x
+    assert abs(q - x) < 1e-10 * x                   # |D| = 1
+
+
+@pytest.mark.parametrize("th", [0.5, 1.0])
+def test_paper_scheme_block_balance(th):
+    # summing the block equations (1^T K = 0): m^T u+ + dt m^T I_ion(u+) =
+    # m^T u + dt m^T (theta g(t+) + (1 - theta) g(t)), g the nodal stimulus;
+    # a slip in the reaction's sign or time level, or in the stimulus weights,
+    # breaks it
+    mesh = O.mesh2d(9)
+    rp, ci, mv, _ = O.assemble(mesh)
+    m = O.csr_to_dense(rp, ci, mv, mesh.n).sum(axis=1)
+    rng = np.random.default_rng(8)
+    tfield = rng.normal(size=mesh.ne)
+    u0 = rng.uniform(0, 60, mesh.n)
+    pm = dict(theta=th, sigma=0.3, t1=0.15, amp=115.0, x0=(0.2, 0.3))
+    p = O._paper_vec(pm)
+    dt = 0.1
+    q, u1, nw, st = O.solve_paper(mesh, tfield, dt, 1, u0=u0, pm=pm)
+    ion = lambda u: p[2] * (u - p[3]) * (u - p[4]) * (u - p[5])
+    g = lambda t: (p[3] + p[7] * np.exp(-np.sum((mesh.xyz - p[10:12]) ** 2, axis=1) / p[8] ** 2)) * (t < p[9])
+    lhs = m @ u1 + dt * m @ ion(u1)
+    rhs = m @ u0 + dt * m @ (th * g(dt) + (1 - th) * g(0.0))
+    assert st == 0 and abs(lhs - rhs) < 1e-11 * abs(rhs)
