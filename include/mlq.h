@@ -278,7 +278,7 @@ int mlq_field_norms(int dim, const int32_t *dims, const double *lengths, const d
 int mlq_pimped_ml_combine(int L, const int64_t *N, const double *const *F, double *est_out);
 
 /* Levels on general tetrahedral meshes (non-nested hierarchies; Sec. 4 and
- * the ventricle of Sec. 5.4): a self-contained FP64 member.  One object per
+ * the ventricle of Sec. 5.4): a self-contained member.  One object per
  * mesh; it owns its device arrays and uses the default stream.
  *
  * mlq_mesh_create: n nodes (xyz host, n x 3), ne tetrahedra (conn host,
@@ -294,8 +294,8 @@ int mlq_pimped_ml_combine(int L, const int64_t *N, const double *const *F, doubl
  * (eq. AdmV).
  * mlq_mesh_solve: S samples (xi host, S x K), nsteps time blocks of dt from
  * the initial state v0, w0 (host, n; w0 may be NULL = 0): b = M (v + dt R),
- * (M + dt K) v+ = b by Jacobi-preconditioned CG from v until ||r|| <= rtol
- * ||b|| (at most 10 n iterations per block), w += dt eps (v - gam w);
+ * (M + dt K) v+ = b by Jacobi-preconditioned CG from v until ||b - A v+|| <=
+ * rtol ||b|| (at most 10 n iterations per block), w += dt eps (v - gam w);
  * q_out (host, S) = m^T v(T) with m = M 1; status (mlq_sample_status, worst
  * block) and iters (CG iterations summed over blocks) may be NULL.  Blocks
  * until done. */
@@ -306,6 +306,19 @@ int mlq_mesh_destroy(mlq_mesh *mesh);
 int mlq_mesh_set_kl(mlq_mesh *mesh, int K, const double *phi, const double *theta_mean);
 int mlq_mesh_solve(mlq_mesh *mesh, const mlq_model *model, double dt, int32_t nsteps, double rtol, const double *v0,
                    const double *w0, int64_t S, const double *xi, double *q_out, int32_t *status, int32_t *iters);
+
+/* mlq_mesh_solve with solver options (opt: precision MLQ_FP64 or MLQ_MIXED,
+ * rtol, rtol_inner, max_iter per solve, max_sweeps, cluster 0 (chosen) or
+ * 1..16; the other fields are ignored).  MLQ_FP64: Jacobi-PCG in FP64 to
+ * ||b - A v|| <= rtol ||b||.  MLQ_MIXED: FP32 Jacobi-PCG (FP32 CSR values and
+ * vectors, FP64 sums across threads) inside FP64 iterative refinement with
+ * the FP64 residual, to the same test.  The whole block loop runs in one
+ * launch, one sample per cluster of CTAs (each CTA a band of CSR rows), with
+ * no host synchronisation inside the solve.  mlq_mesh_solve is this call
+ * with FP64 defaults, the given rtol and at most 10 n iterations per block. */
+int mlq_mesh_solve_opts(mlq_mesh *mesh, const mlq_model *model, const mlq_options *opt, double dt, int32_t nsteps,
+                        const double *v0, const double *w0, int64_t S, const double *xi, double *q_out,
+                        int32_t *status, int32_t *iters);
 
 /* Solve S samples (0 <= S <= 65535) on `level`.  xi: host or device, S x K row-major FP64
  * (sample s uses xi[s*K .. s*K+K-1]).  For each sample: synthesise theta

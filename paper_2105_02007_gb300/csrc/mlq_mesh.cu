@@ -9,11 +9,13 @@
 //   A = M + dt K(D) in CSR, b = M (v + dt R(v, w)), w += dt eps (v - gam w),
 //   A v+ = b by Jacobi-preconditioned CG from v (FP64), Q = m^T v, m = M 1.
 // The CSR values of A are gathered per nonzero over the element entries
-// that add to it (a list fixed by the mesh), so every sum has a fixed order;
-// dot products reduce per block in a fixed tree and then over blocks in
-// order.  The CG iteration is driven from the host, one kernel per step
-// with the samples batched; samples that have converged are frozen.
+// that add to it (a list fixed by the mesh), so every sum has a fixed order.
+// The time blocks run in one launch of mesh_slab_kernel (mlq_mesh_solver.cuh):
+// one sample per cluster, FP64 Jacobi-PCG or FP32 inner PCG inside FP64
+// refinement, with no host synchronisation inside the solve.
 #include "mlq.h"
+#include "mlq_launch.cuh"
+#include "mlq_mesh_solver.cuh"
 
 #include <cuda_runtime.h>
 
@@ -74,150 +76,11 @@ __global__ void assemble_kernel(int64_t nnz, int S, const int64_t *__restrict__ 
     aval[(int64_t)s * nnz + t] = mval[t] + dt * acc;
 }
 
-// y[s][i] = sum_t val[t (+ s nnz)] x[s][ci[t]]  (vs = 0: one matrix for all samples)
-__global__ void spmv_kernel(int64_t n, int S, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                            const double *__restrict__ val, int64_t vs, const double *__restrict__ x,
-                            double *__restrict__ y)
+// FP32 copy of the CSR values (the mixed path's inner matrix)
+__global__ void to_f32_kernel(int64_t count, const double *__restrict__ a, float *__restrict__ f)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = blockIdx.y;
-    if (i >= n || s >= S) return;
-    const double *v = val + (int64_t)s * vs;
-    const double *xs = x + (int64_t)s * n;
-    double acc = 0.0;
-    for (int64_t t = rp[i]; t < rp[i + 1]; ++t) acc += v[t] * xs[ci[t]];
-    y[(int64_t)s * n + i] = acc;
-}
-
-// per-block partial sums of u . v (fixed tree), part[s][blockIdx.x]
-__global__ void dot_partial_kernel(int64_t n, int S, const double *__restrict__ u, const double *__restrict__ v,
-                                   int64_t us, double *__restrict__ part)
-{
-    __shared__ double sh[kThreads];
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = blockIdx.y;
-    double x = 0.0;
-    if (i < n && s < S) x = u[(int64_t)s * us + i] * v[(int64_t)s * n + i];
-    sh[threadIdx.x] = x;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0 && s < S) part[(int64_t)s * gridDim.x + blockIdx.x] = sh[0];
-}
-
-__global__ void dot_final_kernel(int S, int nb, const double *__restrict__ part, double *__restrict__ out)
-{
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
-    double acc = 0.0;
-    for (int b = 0; b < nb; ++b) acc += part[(int64_t)s * nb + b];
-    out[s] = acc;
-}
-
-// y = v + dt R(v, w); w <- w + dt eps (v - gam w); x = v
-__global__ void block_load_kernel(int64_t n, int S, double dt, double a, double eps, double gam,
-                                  const double *__restrict__ v, double *__restrict__ w, double *__restrict__ y,
-                                  double *__restrict__ x)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = blockIdx.y;
-    if (i >= n || s >= S) return;
-    const int64_t k = (int64_t)s * n + i;
-    const double vv = v[k], ww = w[k];
-    y[k] = vv + dt * (vv * (vv - a) * (1.0 - vv) - ww);
-    w[k] = ww + dt * eps * (vv - gam * ww);
-    x[k] = vv;
-}
-
-// r = b - q; z = dinv r; p = z
-__global__ void cg_start_kernel(int64_t n, int S, const double *__restrict__ b, const double *__restrict__ q,
-                                const double *__restrict__ dinv, double *__restrict__ r, double *__restrict__ z,
-                                double *__restrict__ p)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = blockIdx.y;
-    if (i >= n || s >= S) return;
-    const int64_t k = (int64_t)s * n + i;
-    const double rr = b[k] - q[k];
-    r[k] = rr;
-    z[k] = dinv[k] * rr;
-    p[k] = z[k];
-}
-
-// x += alpha p; r -= alpha q; z = dinv r
-__global__ void cg_update_kernel(int64_t n, int S, const double *__restrict__ alpha, const double *__restrict__ p,
-                                 const double *__restrict__ q, const double *__restrict__ dinv, double *__restrict__ x,
-                                 double *__restrict__ r, double *__restrict__ z)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = blockIdx.y;
-    if (i >= n || s >= S) return;
-    const double al = alpha[s];
-    if (al == 0.0) return;   // a sample that no longer iterates keeps x, r, z
-    const int64_t k = (int64_t)s * n + i;
-    x[k] += al * p[k];
-    r[k] -= al * q[k];
-    z[k] = dinv[k] * r[k];
-}
-
-__global__ void cg_direction_kernel(int64_t n, int S, const double *__restrict__ beta, const double *__restrict__ z,
-                                    double *__restrict__ p)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = blockIdx.y;
-    if (i >= n || s >= S) return;
-    const int64_t k = (int64_t)s * n + i;
-    p[k] = z[k] + beta[s] * p[k];
-}
-
-__global__ void dinv_kernel(int64_t n, int S, int64_t nnz, const int64_t *__restrict__ diag,
-                            const double *__restrict__ aval, double *__restrict__ dinv)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = blockIdx.y;
-    if (i >= n || s >= S) return;
-    dinv[(int64_t)s * n + i] = 1.0 / aval[(int64_t)s * nnz + diag[i]];
-}
-
-// per-sample scalars of Jacobi-PCG.  st: 0 iterating, 1 converged, 2 iteration
-// cap, 3 not finite.  Phase 0 (start): iterating iff ||r|| > tol ||b||.
-// Phase 1 (after q = A p): alpha = rz / pq.  Phase 2 (after the update):
-// convergence test and beta.  Phase 3: count the iterating samples only.
-struct CgScalars {
-    double *rz, *pq, *rr, *bb, *rzn, *alpha, *beta;
-    int32_t *st, *it;
-};
-
-__global__ void cg_scalar_kernel(int S, int phase, double tol2, int64_t maxit, CgScalars c, int32_t *nactive)
-{
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
-    if (phase == 3) {
-        if (nactive && c.st[s] == 0) atomicAdd(nactive, 1);
-        return;
-    }
-    if (phase == 0) {
-        c.st[s] = (c.rr[s] <= tol2 * c.bb[s]) ? 1 : 0;
-        if (!isfinite(c.rr[s]) || !isfinite(c.bb[s])) c.st[s] = 3;
-        c.alpha[s] = 0.0;
-        c.beta[s] = 0.0;
-    } else if (phase == 1) {
-        const bool run = c.st[s] == 0 && c.pq[s] != 0.0 && isfinite(c.pq[s]);
-        if (c.st[s] == 0 && !run) c.st[s] = isfinite(c.pq[s]) ? 1 : 3;
-        c.alpha[s] = run ? c.rz[s] / c.pq[s] : 0.0;
-    } else {
-        c.beta[s] = 0.0;
-        if (c.st[s] == 0) {
-            c.it[s] += 1;
-            if (!isfinite(c.rr[s])) c.st[s] = 3;
-            else if (c.rr[s] <= tol2 * c.bb[s]) c.st[s] = 1;
-            else if (c.it[s] >= maxit) c.st[s] = 2;
-            if (c.st[s] == 0) c.beta[s] = c.rzn[s] / c.rz[s];
-            c.rz[s] = c.rzn[s];
-        }
-    }
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < count) f[t] = (float)a[t];
 }
 
 struct Csr {
@@ -290,6 +153,69 @@ struct mlq_mesh {
     double *phi = nullptr, *theta_mean = nullptr;
     std::vector<double> lump_h;
 };
+
+namespace {
+
+template <typename TI>
+mlq::MeshArgs<TI> mesh_args(const mlq_mesh *m, const mlq_model *model, const mlq_options &o, double dt, int nsteps,
+                            int64_t S, const double *aval, const TI *ai, const double *v0, const double *w0,
+                            double *v, double *w, double *b, double *y, void *const *vec, double *q, int32_t *it,
+                            int32_t *st)
+{
+    mlq::MeshArgs<TI> a{};
+    a.n = (int)m->n;
+    a.S = (int)S;
+    a.nnz = m->nnz;
+    a.rp = m->rp;
+    a.ci = m->ci;
+    a.diag = m->diag;
+    a.mval = m->mval;
+    a.lump = m->lump;
+    a.A64 = aval;
+    a.Ai = ai;
+    a.dt = dt;
+    a.nsteps = nsteps;
+    a.a = model->a;
+    a.eps = model->eps;
+    a.gam = model->gamma;
+    a.rtol_out = o.rtol;
+    a.rtol_in = o.rtol_inner;
+    a.max_iter = o.max_iter;
+    a.max_sweeps = o.max_sweeps;
+    a.v0 = v0;
+    a.w0 = w0;
+    a.v = v;
+    a.w = w;
+    a.b = b;
+    a.y = y;
+    a.r = (TI *)vec[0];
+    a.u = (TI *)vec[1];
+    a.wv = (TI *)vec[2];
+    a.s = (TI *)vec[3];
+    a.p = (TI *)vec[4];
+    a.x = (TI *)vec[5];
+    a.dinv = (TI *)vec[6];
+    a.q = q;
+    a.iters = it;
+    a.status = st;
+    return a;
+}
+
+template <typename TI>
+cudaError_t launch_mesh(int cs, const mlq::MeshArgs<TI> &a)
+{
+    constexpr int threads = 512;
+    switch (cs) {
+    case 1: return mlq::cluster_launch<1>(mlq::mesh_slab_kernel<TI, 1>, a.S, threads, 0, nullptr, a);
+    case 2: return mlq::cluster_launch<2>(mlq::mesh_slab_kernel<TI, 2>, a.S, threads, 0, nullptr, a);
+    case 4: return mlq::cluster_launch<4>(mlq::mesh_slab_kernel<TI, 4>, a.S, threads, 0, nullptr, a);
+    case 8: return mlq::cluster_launch<8>(mlq::mesh_slab_kernel<TI, 8>, a.S, threads, 0, nullptr, a);
+    case 16: return mlq::cluster_launch<16>(mlq::mesh_slab_kernel<TI, 16>, a.S, threads, 0, nullptr, a);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -405,116 +331,101 @@ int mlq_mesh_set_kl(mlq_mesh *m, int K, const double *phi, const double *theta_m
     return MLQ_OK;
 }
 
-int mlq_mesh_solve(mlq_mesh *m, const mlq_model *model, double dt, int32_t nsteps, double rtol, const double *v0,
-                   const double *w0, int64_t S, const double *xi, double *q_out, int32_t *status, int32_t *iters)
+int mlq_mesh_solve_opts(mlq_mesh *m, const mlq_model *model, const mlq_options *opt, double dt, int32_t nsteps,
+                        const double *v0, const double *w0, int64_t S, const double *xi, double *q_out,
+                        int32_t *status, int32_t *iters)
 {
-    if (!m || !model || !(dt > 0.0) || nsteps < 0 || !(rtol > 0.0) || !v0 || S < 0 || S > 65535 || !q_out)
+    if (!m || !model || !opt || !(dt > 0.0) || nsteps < 0 || !v0 || S < 0 || S > 65535 || !q_out) return MLQ_EINVAL;
+    if (opt->precision != MLQ_FP64 && opt->precision != MLQ_MIXED) return MLQ_EINVAL;
+    if (!(opt->rtol > 0.0) || opt->max_iter < 1 || (opt->precision == MLQ_MIXED && opt->max_sweeps < 1))
+        return MLQ_EINVAL;
+    if (opt->cluster != 0 && opt->cluster != 1 && opt->cluster != 2 && opt->cluster != 4 && opt->cluster != 8 &&
+        opt->cluster != 16)
         return MLQ_EINVAL;
     if (S == 0) return MLQ_OK;
     if (m->K > 0 && !xi) return MLQ_EINVAL;
     if (cudaSetDevice(m->device) != cudaSuccess) return MLQ_ECUDA;
+    const bool mixed = opt->precision == MLQ_MIXED;
     const int64_t n = m->n, ne = m->ne, nnz = m->nnz, sn = S * n;
-    const int nbn = (int)((n + kThreads - 1) / kThreads);
+    const size_t ti = mixed ? 4 : 8;
     std::vector<void *> allocs;
     auto alloc = [&](size_t bytes) -> void * {
         void *p = nullptr;
-        if (cudaMalloc(&p, std::max<size_t>(bytes, 8)) != cudaSuccess) return nullptr;
+        if (cudaMalloc(&p, std::max<size_t>(bytes, 8)) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
         allocs.push_back(p);
         return p;
     };
     auto release = [&]() {
         for (void *p : allocs) cudaFree(p);
     };
-    double *cs2 = (double *)alloc((size_t)S * ne * 2 * 8), *aval = (double *)alloc((size_t)S * nnz * 8);
-    double *dinv = (double *)alloc(sn * 8), *v = (double *)alloc(sn * 8), *w = (double *)alloc(sn * 8);
-    double *y = (double *)alloc(sn * 8), *b = (double *)alloc(sn * 8), *x = (double *)alloc(sn * 8);
-    double *r = (double *)alloc(sn * 8), *z = (double *)alloc(sn * 8), *p = (double *)alloc(sn * 8);
-    double *q = (double *)alloc(sn * 8), *part = (double *)alloc((size_t)S * nbn * 8);
+    double *cs2 = (double *)alloc((size_t)S * ne * 16), *aval = (double *)alloc((size_t)S * nnz * 8);
+    float *a32 = mixed ? (float *)alloc((size_t)S * nnz * 4) : nullptr;
+    double *v = (double *)alloc(sn * 8), *w = (double *)alloc(sn * 8), *b = (double *)alloc(sn * 8),
+           *y = (double *)alloc(sn * 8);
+    void *vec[7];
+    for (void *&p : vec) p = alloc(sn * ti);
+    double *q = (double *)alloc((size_t)S * 8);
+    int32_t *it = (int32_t *)alloc((size_t)S * 4), *st = (int32_t *)alloc((size_t)S * 4);
     double *xi_d = (double *)alloc((size_t)S * std::max(m->K, 1) * 8);
-    double *sc = (double *)alloc((size_t)S * 7 * 8);
-    int32_t *si = (int32_t *)alloc((size_t)S * 2 * 4), *nact = (int32_t *)alloc(4);
-    if (!cs2 || !aval || !dinv || !v || !w || !y || !b || !x || !r || !z || !p || !q || !part || !xi_d || !sc || !si ||
-        !nact) {
+    double *v0_d = (double *)alloc((size_t)n * 8), *w0_d = w0 ? (double *)alloc((size_t)n * 8) : nullptr;
+    bool ok = cs2 && aval && (!mixed || a32) && v && w && b && y && q && it && st && xi_d && v0_d && (!w0 || w0_d);
+    for (void *p : vec) ok = ok && p;
+    if (!ok) {
         release();
         return MLQ_ENOMEM;
     }
-    CgScalars c{sc, sc + S, sc + 2 * S, sc + 3 * S, sc + 4 * S, sc + 5 * S, sc + 6 * S, si, si + S};
-    bool ok = true;
     auto chk = [&](cudaError_t e) { ok = ok && e == cudaSuccess; };
     if (m->K > 0) chk(cudaMemcpy(xi_d, xi, (size_t)S * m->K * 8, cudaMemcpyHostToDevice));
-    // initial state for every sample
-    for (int64_t s = 0; s < S && ok; ++s) {
-        chk(cudaMemcpy(v + s * n, v0, (size_t)n * 8, cudaMemcpyHostToDevice));
-        if (w0) chk(cudaMemcpy(w + s * n, w0, (size_t)n * 8, cudaMemcpyHostToDevice));
-        else chk(cudaMemset(w + s * n, 0, (size_t)n * 8));
-    }
-    chk(cudaMemset(si, 0, (size_t)S * 2 * 4));
-    const dim3 ge((unsigned)((ne + kThreads - 1) / kThreads), (unsigned)S), gz((unsigned)((nnz + kThreads - 1) / kThreads), (unsigned)S);
-    const dim3 gn((unsigned)nbn, (unsigned)S);
-    const unsigned gs = (unsigned)((S + 127) / 128);
+    chk(cudaMemcpy(v0_d, v0, (size_t)n * 8, cudaMemcpyHostToDevice));
+    if (w0) chk(cudaMemcpy(w0_d, w0, (size_t)n * 8, cudaMemcpyHostToDevice));
+    const dim3 ge((unsigned)((ne + kThreads - 1) / kThreads), (unsigned)S);
+    const dim3 gz((unsigned)((nnz + kThreads - 1) / kThreads), (unsigned)S);
     synth_kernel<<<ge, kThreads>>>(m->phi, m->theta_mean, xi_d, m->K, ne, (int)S, cs2);
     assemble_kernel<<<gz, kThreads>>>(nnz, (int)S, m->cstart, m->centry, m->geo, m->frames, cs2, ne, model->s_l,
                                       model->s_t, dt, m->mval, aval);
-    dinv_kernel<<<gn, kThreads>>>(n, (int)S, nnz, m->diag, aval, dinv);
+    if (mixed) to_f32_kernel<<<(unsigned)((S * nnz + kThreads - 1) / kThreads), kThreads>>>(S * nnz, aval, a32);
     chk(cudaGetLastError());
-    auto dot = [&](const double *u, int64_t us, const double *vv, double *outp) {
-        dot_partial_kernel<<<gn, kThreads>>>(n, (int)S, u, vv, us, part);
-        dot_final_kernel<<<gs, 128>>>((int)S, nbn, part, outp);
-    };
-    const int64_t maxit = 10 * n;
-    const double tol2 = rtol * rtol;
-    std::vector<int32_t> it_total((size_t)S, 0), st_worst((size_t)S, 0), it_h((size_t)S), st_h((size_t)S);
-    for (int32_t step = 0; step < nsteps && ok; ++step) {
-        block_load_kernel<<<gn, kThreads>>>(n, (int)S, dt, model->a, model->eps, model->gamma, v, w, y, x);
-        spmv_kernel<<<gn, kThreads>>>(n, (int)S, m->rp, m->ci, m->mval, 0, y, b);      // b = M y
-        spmv_kernel<<<gn, kThreads>>>(n, (int)S, m->rp, m->ci, aval, nnz, x, q);       // q = A x
-        cg_start_kernel<<<gn, kThreads>>>(n, (int)S, b, q, dinv, r, z, p);
-        dot(r, n, z, c.rz);
-        dot(r, n, r, c.rr);
-        dot(b, n, b, c.bb);
-        chk(cudaMemset(c.it, 0, (size_t)S * 4));
-        cg_scalar_kernel<<<gs, 128>>>((int)S, 0, tol2, maxit, c, nullptr);
-        for (int64_t k = 0; ok; ++k) {
-            if (k % 4 == 0) {
-                chk(cudaMemset(nact, 0, 4));
-                cg_scalar_kernel<<<gs, 128>>>((int)S, 3, tol2, maxit, c, nact);
-                int32_t na = 0;
-                chk(cudaMemcpy(&na, nact, 4, cudaMemcpyDeviceToHost));
-                if (na == 0) break;
-            }
-            spmv_kernel<<<gn, kThreads>>>(n, (int)S, m->rp, m->ci, aval, nnz, p, q);   // q = A p
-            dot(p, n, q, c.pq);
-            cg_scalar_kernel<<<gs, 128>>>((int)S, 1, tol2, maxit, c, nullptr);
-            cg_update_kernel<<<gn, kThreads>>>(n, (int)S, c.alpha, p, q, dinv, x, r, z);
-            dot(r, n, z, c.rzn);
-            dot(r, n, r, c.rr);
-            cg_scalar_kernel<<<gs, 128>>>((int)S, 2, tol2, maxit, c, nullptr);
-            cg_direction_kernel<<<gn, kThreads>>>(n, (int)S, c.beta, z, p);
-            chk(cudaGetLastError());
-        }
-        chk(cudaMemcpy(v, x, (size_t)sn * 8, cudaMemcpyDeviceToDevice));
-        chk(cudaMemcpy(it_h.data(), c.it, (size_t)S * 4, cudaMemcpyDeviceToHost));
-        chk(cudaMemcpy(st_h.data(), c.st, (size_t)S * 4, cudaMemcpyDeviceToHost));
-        for (int64_t s = 0; s < S; ++s) {
-            it_total[(size_t)s] += it_h[(size_t)s];
-            const int32_t code = st_h[(size_t)s] == 1 ? MLQ_S_CONVERGED
-                                 : (st_h[(size_t)s] == 2 ? MLQ_S_MAXITER : (st_h[(size_t)s] == 3 ? MLQ_S_NONFINITE : MLQ_S_MAXITER));
-            st_worst[(size_t)s] = std::max(st_worst[(size_t)s], code);
-        }
-    }
-    // Q = m^T v
+    // launch shape: one sample per cluster; the cluster grows while the batch
+    // still fills the SMs twice over and every CTA keeps a few thousand rows
+    int nsm = 1;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device);
+    int cs = 1;
+    while (cs < 16 && (int64_t)(2 * cs) * S <= 2LL * nsm && n / (2 * cs) >= 4096) cs *= 2;
+    if (opt->cluster > 0) cs = opt->cluster;
+    while (cs > 1 && n / cs < 64) cs /= 2;
+    cudaError_t le = cudaSuccess;
     if (ok) {
-        dot(m->lump, 0, v, c.rz);
-        chk(cudaMemcpy(q_out, c.rz, (size_t)S * 8, cudaMemcpyDeviceToHost));
+        if (mixed) {
+            mlq::MeshArgs<float> a = mesh_args<float>(m, model, *opt, dt, nsteps, S, aval, a32, v0_d, w0_d, v, w, b,
+                                                      y, vec, q, it, st);
+            le = launch_mesh<float>(cs, a);
+        } else {
+            mlq::MeshArgs<double> a = mesh_args<double>(m, model, *opt, dt, nsteps, S, aval, aval, v0_d, w0_d, v, w,
+                                                        b, y, vec, q, it, st);
+            le = launch_mesh<double>(cs, a);
+        }
+        chk(le);
+        chk(cudaMemcpy(q_out, q, (size_t)S * 8, cudaMemcpyDeviceToHost));
+        if (status) chk(cudaMemcpy(status, st, (size_t)S * 4, cudaMemcpyDeviceToHost));
+        if (iters) chk(cudaMemcpy(iters, it, (size_t)S * 4, cudaMemcpyDeviceToHost));
         chk(cudaDeviceSynchronize());
     }
     release();
-    if (!ok) return MLQ_ECUDA;
-    for (int64_t s = 0; s < S; ++s) {
-        if (status) status[s] = st_worst[(size_t)s];
-        if (iters) iters[s] = it_total[(size_t)s];
-    }
-    return MLQ_OK;
+    return ok ? MLQ_OK : MLQ_ECUDA;
+}
+
+int mlq_mesh_solve(mlq_mesh *m, const mlq_model *model, double dt, int32_t nsteps, double rtol, const double *v0,
+                   const double *w0, int64_t S, const double *xi, double *q_out, int32_t *status, int32_t *iters)
+{
+    if (!m) return MLQ_EINVAL;
+    mlq_options o;
+    mlq_default_options(&o, MLQ_FP64);
+    o.rtol = rtol;
+    o.max_iter = (int)std::min<int64_t>(10 * m->n, 0x7fffffff);
+    return mlq_mesh_solve_opts(m, model, &o, dt, nsteps, v0, w0, S, xi, q_out, status, iters);
 }
 
 }  // extern "C"

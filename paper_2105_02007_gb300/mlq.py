@@ -85,6 +85,8 @@ _lib.mlq_mlmc_allocation.argtypes = [ctypes.c_int, _vp, _vp, ctypes.c_double, _i
 _lib.mlq_mesh_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, _i64, _vp, _i64, _vp, _vp]
 _lib.mlq_mesh_destroy.argtypes = [_vp]
 _lib.mlq_mesh_set_kl.argtypes = [_vp, ctypes.c_int, _vp, _vp]
+_lib.mlq_mesh_solve_opts.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int32, _vp, _vp, _i64, _vp, _vp,
+                                     _vp, _vp]
 _lib.mlq_mesh_solve.argtypes = [_vp, _vp, ctypes.c_double, ctypes.c_int32, ctypes.c_double, _vp, _vp, _i64, _vp, _vp,
                                 _vp, _vp]
 _lib.mlq_solve.argtypes = [_vp, ctypes.c_int, _i64, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
@@ -123,7 +125,7 @@ _lib.mlq_last_cuda_error.argtypes = [_vp]
 EXPORTED = ["mlq_default_options", "mlq_default_model", "mlq_default_scheme", "mlq_set_scheme", "mlq_create", "mlq_destroy", "mlq_set_options",
             "mlq_set_model", "mlq_add_level", "mlq_set_initial_state", "mlq_set_initial_disk", "mlq_set_kl",
             "mlq_build_kl", "mlq_centroid_table", "mlq_build_kl_mesh", "mlq_p1_at_points", "mlq_mesh_create",
-            "mlq_mesh_destroy", "mlq_mesh_set_kl", "mlq_mesh_solve", "mlq_mlmc_allocation", "mlq_mlmc_combine", "mlq_pimped_ml_combine", "mlq_estimate_adaptive", "mlq_field_prolong", "mlq_field_norms", "mlq_solve", "mlq_solve_state", "mlq_set_points", "mlq_solve_points", "mlq_trace_prolong",
+            "mlq_mesh_destroy", "mlq_mesh_set_kl", "mlq_mesh_solve", "mlq_mesh_solve_opts", "mlq_mlmc_allocation", "mlq_mlmc_combine", "mlq_pimped_ml_combine", "mlq_estimate_adaptive", "mlq_field_prolong", "mlq_field_norms", "mlq_solve", "mlq_solve_state", "mlq_set_points", "mlq_solve_points", "mlq_trace_prolong",
             "mlq_time_norms", "mlq_estimate", "mlq_workspace_bytes",
             "mlq_launch_count", "mlq_level_launch", "mlq_strerror", "mlq_last_cuda_error", "mlq_set_profiling",
             "mlq_member_profile", "mlq_autotune", "mlq_solve_noalloc", "mlq_synthesize", "mlq_submit", "mlq_poll", "mlq_serve_limits"]
@@ -295,7 +297,14 @@ class MeshLevel:
         self.K = phi.shape[1]
 
     def solve(self, xi: np.ndarray, dt: float, nsteps: int, v0: np.ndarray, w0=None, rtol: float = 1e-13,
-              model=None):
+              model=None, precision=None, **opts):
+        """S samples xi (S x K) over nsteps blocks from v0, w0.  precision None:
+        mlq_mesh_solve (FP64, rtol); MLQ_FP64 / MLQ_MIXED: mlq_mesh_solve_opts
+        with the default options of that precision updated by opts (rtol,
+        cluster, max_iter, ...).  Returns (Q, status, iters)."""
+        if precision is not None:
+            o = default_options(precision, **opts)
+            return self._solve_opts(xi, dt, nsteps, v0, w0, model, o)
         xi, px = _host(xi, np.float64)
         S = xi.shape[0]
         v0, pv = _host(v0, np.float64)
@@ -310,6 +319,23 @@ class MeshLevel:
         _check(_lib.mlq_mesh_solve(self._h, ctypes.byref(md), dt, nsteps, rtol, pv, pw, S, px,
                                    q.ctypes.data_as(_vp), st.ctypes.data_as(_vp), it.ctypes.data_as(_vp)),
                "mlq_mesh_solve")
+        return q, st, it
+
+    def _solve_opts(self, xi, dt, nsteps, v0, w0, model, o):
+        xi, px = _host(xi, np.float64)
+        S = xi.shape[0]
+        v0, pv = _host(v0, np.float64)
+        w0a, pw = (None, None) if w0 is None else _host(w0, np.float64)
+        md = Model()
+        _lib.mlq_default_model(ctypes.byref(md))
+        for k, v in (model or {}).items():
+            setattr(md, k, v)
+        q = np.zeros(S)
+        st = np.zeros(S, dtype=np.int32)
+        it = np.zeros(S, dtype=np.int32)
+        _check(_lib.mlq_mesh_solve_opts(self._h, ctypes.byref(md), ctypes.byref(o), dt, nsteps, pv, pw, S, px,
+                                        q.ctypes.data_as(_vp), st.ctypes.data_as(_vp), it.ctypes.data_as(_vp)),
+               "mlq_mesh_solve_opts")
         return q, st, it
 
 

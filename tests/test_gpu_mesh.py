@@ -108,3 +108,25 @@ def test_pimped_ml_over_unrelated_shells_matches_oracle(mlq):
     est = mlq.pimped_ml_combine(F_lib, N)
     ref = O.pimped_ml_estimate(F_or, N)
     assert abs(est - ref) <= 1e-10 * abs(ref)
+
+
+@pytest.mark.parametrize("prec,cluster", [(0, 1), (0, 4), (1, 0), (1, 1), (1, 2), (1, 16)])
+def test_mesh_level_precisions_and_clusters(mlq, prec, cluster):
+    # the device-resident member in both precisions and on every cluster
+    # size (ragged row bands), against the oracle: FP64 1e-10, mixed 1e-6
+    xyz, conn = LV.lv_mesh(*((3, 16, 28) if cluster == 16 else (2, 8, 14)))   # 16 CTAs need >= 1024 rows
+    frames, alpha = LV.lv_fibres(xyz, conn)
+    mesh = O.unstructured_mesh(xyz, conn)
+    modes, _ = O.kl_build(mesh, 0.09, 0.15 ** 2, 4)
+    phi = O.centroid_table_unrelated(mesh, modes, mesh)
+    xi = inputs.gaussian_xi(41, 0, 0, 4, 4)
+    v0, w0 = LV.stimulus(xyz, radius=0.4)
+    dt, nb = 0.05, 10
+    q_ref, _, st = O.solve_batch(mesh, phi, xi, dt, nb, v0=v0, w0=w0, theta_mean=alpha, frames=frames, nthreads=2)
+    assert np.all(st == 0)
+    tol = 1e-10 if prec == 0 else 1e-6
+    with mlq.MeshLevel(xyz, conn, frames) as lvl:
+        lvl.set_kl(phi, alpha)
+        q, status, iters = lvl.solve(xi, dt, nb, v0, w0, precision=prec, cluster=cluster)
+    assert np.all(status == 0) and np.all(iters > 0)
+    assert np.max(np.abs(q - q_ref) / np.abs(q_ref)) < tol
