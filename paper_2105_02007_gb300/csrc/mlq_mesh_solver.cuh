@@ -45,27 +45,52 @@ struct MeshArgs {
     int32_t *iters, *status;      // [S]
 };
 
-// Rows of a CSR product handled by groups of 8 lanes: each group takes one
-// row, its lanes the entries t = rp[row] + lane, + 8, ...; the partial sums
-// meet by butterfly inside the group.  Every lane of a warp runs the same
-// number of rounds (a row past the band contributes zeros), so the shuffles
-// see the whole warp.  f(row, value) consumes a row on lane 0 of its group.
+// Rows of a CSR product handled by groups of 8 lanes: each group takes two
+// rows per round (the loads of both in flight together: the gather of x is
+// bound by L2 latency), its lanes the entries t = rp[row] + lane, + 8, ...;
+// the partial sums meet by butterfly inside the group.  Every lane of a warp
+// runs the same number of rounds (a row past the band contributes zeros), so
+// the shuffles see the whole warp.  The matrix goes through the read-only
+// path (it is not written during the solve), x through L2 (other CTAs write
+// it between cluster barriers).  f(row, value) consumes a row on lane 0 of
+// its group.
 template <typename TV, typename TX, typename F>
 __device__ __forceinline__ void csr_rows(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                          const TV *__restrict__ val, const TX *x, int r0, int r1, F &&f)
 {
     const int lane8 = threadIdx.x & 7, grp = threadIdx.x >> 3, ngrp = blockDim.x >> 3;
-    const int rounds = (r1 - r0 + ngrp - 1) / ngrp;
+    const int rounds = (r1 - r0 + 2 * ngrp - 1) / (2 * ngrp);
     for (int k = 0; k < rounds; ++k) {
-        const int row = r0 + k * ngrp + grp;
-        TV acc = (TV)0;
-        if (row < r1) {
-            const int64_t e = rp[row + 1];
-            for (int64_t t = rp[row] + lane8; t < e; t += 8) acc += val[t] * (TV)__ldcg(x + ci[t]);
+        const int ra = r0 + 2 * k * ngrp + grp, rb = ra + ngrp;
+        TV acca = (TV)0, accb = (TV)0;
+        int64_t ta = 0, ea = 0, tb = 0, eb = 0;
+        if (ra < r1) {
+            ta = __ldg(rp + ra) + lane8;
+            ea = __ldg(rp + ra + 1);
+        }
+        if (rb < r1) {
+            tb = __ldg(rp + rb) + lane8;
+            eb = __ldg(rp + rb + 1);
+        }
+        while (ta < ea || tb < eb) {
+            const bool ha = ta < ea, hb = tb < eb;
+            const int32_t ca = ha ? __ldg(ci + ta) : 0, cb = hb ? __ldg(ci + tb) : 0;
+            const TV va = ha ? __ldg(val + ta) : (TV)0, vb = hb ? __ldg(val + tb) : (TV)0;
+            const TX xa = ha ? __ldcg(x + ca) : (TX)0, xb = hb ? __ldcg(x + cb) : (TX)0;
+            acca += va * (TV)xa;
+            accb += vb * (TV)xb;
+            ta += 8;
+            tb += 8;
         }
 #pragma unroll
-        for (int o = 4; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane8 == 0 && row < r1) f(row, acc);
+        for (int o = 4; o > 0; o >>= 1) {
+            acca += __shfl_xor_sync(0xffffffffu, acca, o);
+            accb += __shfl_xor_sync(0xffffffffu, accb, o);
+        }
+        if (lane8 == 0) {
+            if (ra < r1) f(ra, acca);
+            if (rb < r1) f(rb, accb);
+        }
     }
 }
 

@@ -264,8 +264,8 @@ def mlmc_allocation(var, cost, eps: float, nmin: int = 2) -> np.ndarray:
 
 
 class MeshLevel:
-    """A level on a general tetrahedral mesh (mlq_mesh_*): FP64 Jacobi-PCG
-    member for non-nested hierarchies."""
+    """A level on a general tetrahedral mesh (mlq_mesh_*) for non-nested
+    hierarchies: Jacobi-PCG in FP64, or FP32 inside FP64 refinement."""
 
     def __init__(self, xyz: np.ndarray, conn: np.ndarray, frames=None, device: int = 0):
         self._xyz, px, self._conn, pc = _mesh_args(xyz, conn)
