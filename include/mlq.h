@@ -234,6 +234,17 @@ int mlq_build_kl_mesh(int dim, int64_t n, const double *xyz, int64_t ne, const i
 int mlq_p1_at_points(int dim, int64_t n, const double *xyz, int64_t ne, const int32_t *conn, int K, const double *f,
                      int64_t np, const double *pts, double *out);
 
+/* mlq_p1_at_points on the current CUDA device: the same transfer and the
+ * same rule (the first simplex in element order whose barycentric
+ * coordinates are >= -1e-12; for a point in no simplex the first whose
+ * smallest coordinate is within 1e-12 of the largest over all simplices),
+ * with the bucket grid built, the points located and the fields
+ * interpolated by kernels (each point outside the mesh scans every simplex
+ * in a CTA of its own).  Arguments as mlq_p1_at_points (host arrays);
+ * ne < 2^31.  Blocks until out is written. */
+int mlq_p1_at_points_gpu(int dim, int64_t n, const double *xyz, int64_t ne, const int32_t *conn, int K,
+                         const double *f, int64_t np, const double *pts, double *out);
+
 /* Host helper: numbers of samples per level for eq. StandardML with Monte
  * Carlo rules that minimise the cost sum_l N_l cost[l] subject to the
  * statistical error sqrt(sum_l var[l] / N_l) <= eps:

@@ -81,6 +81,7 @@ _lib.mlq_centroid_table.argtypes = [ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _
 _lib.mlq_build_kl_mesh.argtypes = [ctypes.c_int, _i64, _vp, _i64, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                    _vp, _vp]
 _lib.mlq_p1_at_points.argtypes = [ctypes.c_int, _i64, _vp, _i64, _vp, ctypes.c_int, _vp, _i64, _vp, _vp]
+_lib.mlq_p1_at_points_gpu.argtypes = [ctypes.c_int, _i64, _vp, _i64, _vp, ctypes.c_int, _vp, _i64, _vp, _vp]
 _lib.mlq_mlmc_allocation.argtypes = [ctypes.c_int, _vp, _vp, ctypes.c_double, _i64, _vp]
 _lib.mlq_mesh_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, _i64, _vp, _i64, _vp, _vp]
 _lib.mlq_mesh_destroy.argtypes = [_vp]
@@ -124,7 +125,7 @@ _lib.mlq_last_cuda_error.argtypes = [_vp]
 
 EXPORTED = ["mlq_default_options", "mlq_default_model", "mlq_default_scheme", "mlq_set_scheme", "mlq_create", "mlq_destroy", "mlq_set_options",
             "mlq_set_model", "mlq_add_level", "mlq_set_initial_state", "mlq_set_initial_disk", "mlq_set_kl",
-            "mlq_build_kl", "mlq_centroid_table", "mlq_build_kl_mesh", "mlq_p1_at_points", "mlq_mesh_create",
+            "mlq_build_kl", "mlq_centroid_table", "mlq_build_kl_mesh", "mlq_p1_at_points", "mlq_p1_at_points_gpu", "mlq_mesh_create",
             "mlq_mesh_destroy", "mlq_mesh_set_kl", "mlq_mesh_solve", "mlq_mesh_solve_opts", "mlq_mlmc_allocation", "mlq_mlmc_combine", "mlq_pimped_ml_combine", "mlq_estimate_adaptive", "mlq_field_prolong", "mlq_field_norms", "mlq_solve", "mlq_solve_state", "mlq_set_points", "mlq_solve_points", "mlq_trace_prolong",
             "mlq_time_norms", "mlq_estimate", "mlq_workspace_bytes",
             "mlq_launch_count", "mlq_level_launch", "mlq_strerror", "mlq_last_cuda_error", "mlq_set_profiling",
@@ -237,10 +238,11 @@ def build_kl_mesh(xyz: np.ndarray, conn: np.ndarray, sigma2: float, ell: float, 
     return modes, lam
 
 
-def p1_at_points(xyz: np.ndarray, conn: np.ndarray, f: np.ndarray, pts: np.ndarray) -> np.ndarray:
+def p1_at_points(xyz: np.ndarray, conn: np.ndarray, f: np.ndarray, pts: np.ndarray, device: bool = False) -> np.ndarray:
     """Values at points (np x dim) of the P1 interpolants of nodal fields
     f (n x K) on a general simplicial mesh (the transfer between unrelated
-    meshes)."""
+    meshes); device=True locates the points on the current CUDA device
+    (mlq_p1_at_points_gpu), else on the host cores."""
     xyz, px, conn, pc = _mesh_args(xyz, conn)
     n, dim = xyz.shape
     f2 = np.asarray(f, dtype=np.float64)
@@ -248,8 +250,9 @@ def p1_at_points(xyz: np.ndarray, conn: np.ndarray, f: np.ndarray, pts: np.ndarr
     f2, pf = _host(f2, np.float64)
     pts, pp = _host(pts, np.float64)
     out = np.zeros((pts.shape[0], f2.shape[1]))
-    _check(_lib.mlq_p1_at_points(dim, n, px, conn.shape[0], pc, f2.shape[1], pf, pts.shape[0], pp,
-                                 out.ctypes.data_as(_vp)), "mlq_p1_at_points")
+    fn = _lib.mlq_p1_at_points_gpu if device else _lib.mlq_p1_at_points
+    _check(fn(dim, n, px, conn.shape[0], pc, f2.shape[1], pf, pts.shape[0], pp, out.ctypes.data_as(_vp)),
+           "mlq_p1_at_points_gpu" if device else "mlq_p1_at_points")
     return out
 
 

@@ -130,3 +130,27 @@ def test_mesh_level_precisions_and_clusters(mlq, prec, cluster):
         q, status, iters = lvl.solve(xi, dt, nb, v0, w0, precision=prec, cluster=cluster)
     assert np.all(status == 0) and np.all(iters > 0)
     assert np.max(np.abs(q - q_ref) / np.abs(q_ref)) < tol
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_device_point_location_matches_host_and_oracle(mlq, dim):
+    # the device transfer (bucket grid, location, the global scan of points
+    # outside, interpolation) against the host helper and the oracle, on
+    # unrelated shells with centroids inside and outside the located mesh,
+    # and on a 2D mesh with points on shared edges and outside
+    rng = np.random.default_rng(60 + dim)
+    if dim == 3:
+        fine_xyz, fine_conn = LV.lv_mesh(3, 11, 19)
+        cx, cc = LV.lv_mesh(2, 7, 12)
+        pts = cx[cc].mean(axis=1)
+    else:
+        m = O.mesh2d(9)
+        fine_xyz, fine_conn = m.xyz, m.conn
+        pts = np.vstack([rng.uniform(-0.05, 1.05, size=(200, 2)), m.xyz[::3],
+                         0.5 * (m.xyz[m.conn[:40, 0]] + m.xyz[m.conn[:40, 1]])])
+    f = rng.normal(size=(fine_xyz.shape[0], 5))
+    dev = mlq.p1_at_points(fine_xyz, fine_conn, f, pts, device=True)
+    host = mlq.p1_at_points(fine_xyz, fine_conn, f, pts)
+    ref = O.p1_at_points(O.unstructured_mesh(fine_xyz, fine_conn), f, pts)
+    assert np.max(np.abs(dev - host)) < 1e-12 * np.max(np.abs(host))
+    assert np.max(np.abs(dev - ref)) < 1e-12 * np.max(np.abs(ref))
