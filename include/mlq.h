@@ -86,8 +86,10 @@ typedef struct {
  *                        at rtol_inner times its starting residual.
  *   max_iter   cap on CG iterations per solve (per refinement sweep).
  *   max_sweeps cap on refinement sweeps per block (MLQ_MIXED only).
- *   cluster    CTAs per sample (1,2,4,8,16); 0 = chosen per level.
- *   threads    threads per CTA (64..512, multiple of 32); 0 = chosen.
+ *   cluster    CTAs per sample (1,2,4,6,8,12,16; 2D levels take 6 as 4 and
+ *              12 as 8); 0 = chosen per level.
+ *   threads    threads per CTA (64..512, multiple of 32; 3D levels use at
+ *              most 256); 0 = chosen.
  *   storage    where a sample's PCG vectors live: 0 = on chip (registers and
  *              shared memory of its cluster) when they fit, else global
  *              memory; 1 = on chip (a solve whose level does not fit returns

@@ -19,7 +19,8 @@ LIB = os.path.join(LIBDIR, "libmlq.so")
 INCLUDE = os.path.join(ROOT, "include")
 # (source, extra flags, object name): the slab-solver kernels are compiled
 # once per cluster size / inner precision so that the objects build in parallel
-SOURCES = ([("mlq_api.cu", [], "mlq_api"), ("mlq_kl.cpp", [], "mlq_kl"), ("mlq_3d_inst.cu", [], "mlq_3d"),
+SOURCES = ([("mlq_api.cu", [], "mlq_api"), ("mlq_kl.cpp", [], "mlq_kl"), ("mlq_3d_inst.cu", ["-DMLQ_F64=0"], "mlq_3d_f32"),
+            ("mlq_3d_inst.cu", ["-DMLQ_F64=1"], "mlq_3d_f64"),
             ("mlq_mesh.cu", [], "mlq_mesh"), ("mlq_estimator.cpp", [], "mlq_estimator"),
             ("mlq_locate.cu", [], "mlq_locate")]
            + [("mlq_reg_inst.cu", [f"-DMLQ_CS={cs}"], f"mlq_reg_cs{cs}") for cs in (1, 2, 4, 8, 16)]

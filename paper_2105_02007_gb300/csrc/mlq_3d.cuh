@@ -3,7 +3,9 @@
 // batched time-block solver.
 //
 // Mesh convention (the same as the library's documented mesh, include/mlq.h):
-//   nodes   (i, j, k), node = i + mx (j + my k), x = Lx i / (mx - 1), ...
+//   nodes   (i, j, k), node = i + mx (j + my k), x = Lx i / (mx - 1), ...;
+//           on the device stored at i + px (j + my k) with rows padded to
+//           px (a multiple of 4) and zero pads (Grid3)
 //   cells   c = i + (mx - 1)(j + (my - 1) k), six tetrahedra e = 6 c + s;
 //           tetrahedron s walks from corner (i, j, k) to (i+1, j+1, k+1) along
 //           the unit steps perm[s][0], perm[s][1], perm[s][2] (Kuhn / Freudenthal
@@ -40,6 +42,9 @@ namespace mlq {
 
 constexpr int kMgCoarsestSweeps3D = 6;  // damped Jacobi sweeps on the coarsest 3D level
 
+// The set-up kernels are compiled in one translation unit (MLQ_3D_SETUP).
+#ifdef MLQ_3D_SETUP
+
 // ---------------------------------------------------------------------------
 // Level set-up (sample independent): FP64 mass stencil [8][n] and lumped mass
 // m_P = (incident tetrahedra) |e| / 4.  Gathers over the (up to) 24
@@ -49,11 +54,11 @@ __global__ void level3d_setup_kernel(Grid3 g, double *__restrict__ M3, double *_
 {
     const int64_t P = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (P >= g.n) return;
-    const int i = (int)(P % g.mx), j = (int)((P / g.mx) % g.my), k = (int)(P / ((int64_t)g.mx * g.my));
+    const int i = (int)(P % g.px), j = (int)((P / g.px) % g.my), k = (int)(P / ((int64_t)g.px * g.my));
     const double vol = g.hx * g.hy * g.hz / 6.0;
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int cnt = 0;
-    for (int d = 0; d < 8; ++d) {   // cell with P at corner d
+    for (int d = 0; d < 8 && i < g.mx; ++d) {   // cell with P at corner d (none for a pad entry)
         const int ci = i - (d & 1), cj = j - ((d >> 1) & 1), ck = k - ((d >> 2) & 1);
         if (ci < 0 || cj < 0 || ck < 0 || ci >= g.mx - 1 || cj >= g.my - 1 || ck >= g.mz - 1) continue;
         for (int s = 0; s < 6; ++s) {
@@ -73,14 +78,15 @@ __global__ void level3d_setup_kernel(Grid3 g, double *__restrict__ M3, double *_
 // Gather of the stencil of M + dt K(D) at node P over the (up to) 24
 // tetrahedra at P, in a fixed order; getD(e, d11, d12, d22) gives the
 // in-plane block of D on tetrahedron e (d33 = s_t).
+// A pad entry (i >= mx) gets zeros.
 template <typename GetD>
 __device__ __forceinline__ void stencil3d_gather(const Grid3 &g, int64_t P, double dt, double s_t, GetD getD,
                                                  double (&acc)[8])
 {
-    const int i = (int)(P % g.mx), j = (int)((P / g.mx) % g.my), k = (int)(P / ((int64_t)g.mx * g.my));
+    const int i = (int)(P % g.px), j = (int)((P / g.px) % g.my), k = (int)(P / ((int64_t)g.px * g.my));
     const double vol = g.hx * g.hy * g.hz / 6.0;
     for (int sl = 0; sl < 8; ++sl) acc[sl] = 0.0;
-    for (int d = 0; d < 8; ++d) {
+    for (int d = 0; d < 8 && i < g.mx; ++d) {
         const int ci = i - (d & 1), cj = j - ((d >> 1) & 1), ck = k - ((d >> 2) & 1);
         if (ci < 0 || cj < 0 || ck < 0 || ci >= g.mx - 1 || cj >= g.my - 1 || ck >= g.mz - 1) continue;
         const int64_t cell = ci + (int64_t)(g.mx - 1) * (cj + (int64_t)(g.my - 1) * ck);
@@ -126,13 +132,14 @@ __global__ void stencil3d_setup_kernel(const double *__restrict__ cs2, Grid3 g, 
         d22 = s_t + hds * (1.0 - c);
         d12 = hds * sn;
     }, acc);
+    const double dinv = acc[0] != 0.0 ? 1.0 / acc[0] : 0.0;   // 0 on a pad entry
     double *a = A64 + (size_t)smp * kSlots3D * g.n;
     for (int sl = 0; sl < 8; ++sl) a[(int64_t)sl * g.n + P] = acc[sl];
-    a[8LL * g.n + P] = 1.0 / acc[0];
+    a[8LL * g.n + P] = dinv;
     if (A32) {
         float *f = A32 + (size_t)smp * kSlots3D * g.n;
         for (int sl = 0; sl < 8; ++sl) f[(int64_t)sl * g.n + P] = (float)acc[sl];
-        f[8LL * g.n + P] = (float)(1.0 / acc[0]);
+        f[8LL * g.n + P] = (float)dinv;
     }
 }
 
@@ -202,20 +209,25 @@ __global__ void stencil3d_from_d_kernel(const float *__restrict__ dbar, Grid3 g,
     }, acc);
     float *f = A32 + (size_t)smp * kSlots3D * g.n;
     for (int sl = 0; sl < 8; ++sl) f[(int64_t)sl * g.n + P] = (float)acc[sl];
-    f[8LL * g.n + P] = (float)(1.0 / acc[0]);
+    f[8LL * g.n + P] = acc[0] != 0.0 ? (float)(1.0 / acc[0]) : 0.0f;
 }
 
+#endif  // MLQ_3D_SETUP
+
+// ---------------------------------------------------------------------------
+// Scalar passes (FP64 block work and the FP64 inner path): one stored entry
+// per thread, pads included.
+// ---------------------------------------------------------------------------
+
 // (C x)_P for a symmetric 15-point stencil C [8][n]: slot d at P couples to
-// P + d, slot d at P - d couples to P - d.  x read through L2.
-// One path for every node, so boundary nodes do not split their warp: a
-// coupling that does not exist (P on the boundary, P +- d wrapping to
-// another line or plane) has a zero slot, set up so by the gather over the
-// incident tetrahedra, and adds exactly nothing; a neighbour index outside
-// the array (first and last planes) is replaced by P and its slot by 0.
-// Every load is issued before the first product so that they are in
-// flight together.
+// P + d, slot d at P - d couples to P - d.  x read through L2.  A coupling
+// that does not exist (boundary, pad, P +- d in another line or plane) has a
+// zero slot and adds exactly nothing; a neighbour index outside the array
+// (first and last planes) is replaced by P and its slot by 0, so boundary
+// nodes do not split their warp.  Every load is issued before the first
+// product.
 template <typename T, typename TX>
-__device__ __forceinline__ T apply15(const T *__restrict__ C, const Grid3 &g, const TX *x, int P, int, int, int)
+__device__ __forceinline__ T apply15(const T *__restrict__ C, const Grid3 &g, const TX *x, int P)
 {
     const int n = g.n;
     T c[15], xv[15];
@@ -237,49 +249,49 @@ __device__ __forceinline__ T apply15(const T *__restrict__ C, const Grid3 &g, co
     return acc;
 }
 
-// The nodes a CTA owns on one level: grid lines j0 <= j < j0 + nj of every
-// plane k.  They are visited line by line, j fastest inside the band and
-// then k, so that the nodes a 15-point product reads in the planes k +- 1
-// were visited one band of lines earlier (nj x mx nodes) rather than one
-// whole plane earlier: the reuse stays inside L2 when every SM streams.
+// The entries a CTA owns on one level: grid lines j0 <= j < j0 + nj of every
+// plane k, pads included.  They are visited line by line, j fastest inside
+// the band and then k, so that the entries a 15-point product reads in the
+// planes k +- 1 were visited one band of lines earlier (nj px entries)
+// rather than one whole plane earlier: the reuse stays inside L2.
 struct Band3 {
-    int mx, my, j0, nj;
+    int px, my, j0, nj;
     int cnt;
 };
 
 __device__ __forceinline__ Band3 band3(const Grid3 &g, int rank, int cs)
 {
     Band3 b;
-    b.mx = g.mx;
+    b.px = g.px;
     b.my = g.my;
     b.j0 = (int)(g.my * rank / cs);
     b.nj = (int)(g.my * (rank + 1) / cs) - b.j0;
-    b.cnt = b.nj * g.mx * g.mz;
+    b.cnt = b.nj * g.px * g.mz;
     return b;
 }
 
 // a thread's position (i, j0 + jl, k) in its band, advanced by a fixed
-// stride of band-local indices without a division per node (nj > 0)
+// stride of band-local indices without a division per entry (nj > 0)
 struct Walk3 {
     int i, jl, k, di, dj, dk;
     __device__ void init(const Band3 &b, int f, int stride)
     {
-        i = (int)(f % b.mx);
-        const int line = f / b.mx;
-        jl = (int)(line % b.nj);
-        k = (int)(line / b.nj);
-        di = (int)(stride % b.mx);
-        const int lines = stride / b.mx;
-        dj = (int)(lines % b.nj);
-        dk = (int)(lines / b.nj);
+        i = f % b.px;
+        const int line = f / b.px;
+        jl = line % b.nj;
+        k = line / b.nj;
+        di = stride % b.px;
+        const int lines = stride / b.px;
+        dj = lines % b.nj;
+        dk = lines / b.nj;
     }
     __device__ void next(const Band3 &b)
     {
         i += di;
         jl += dj;
         k += dk;
-        if (i >= b.mx) {
-            i -= b.mx;
+        if (i >= b.px) {
+            i -= b.px;
             ++jl;
         }
         if (jl >= b.nj) {
@@ -288,7 +300,7 @@ struct Walk3 {
         }
     }
     __device__ int j(const Band3 &b) const { return b.j0 + jl; }
-    __device__ int node(const Band3 &b) const { return i + b.mx * (b.j0 + jl + b.my * k); }
+    __device__ int node(const Band3 &b) const { return i + b.px * (b.j0 + jl + b.my * k); }
 };
 
 template <typename T, int N>
@@ -296,41 +308,16 @@ struct Vals {
     T v[N];
 };
 
-// L2 prefetch (one bulk request, TMA unit) of the 16-byte aligned part of
-// elements [lo, hi) of an array
-template <typename T>
-__device__ __forceinline__ void prefetch_l2(const T *a, int lo, int hi)
-{
-    const uintptr_t s = ((uintptr_t)(a + lo) + 15) & ~(uintptr_t)15;
-    const uintptr_t e = (uintptr_t)(a + hi) & ~(uintptr_t)15;
-    if (e > s) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(s), "r"((uint32_t)(e - s)) : "memory");
-}
-
-struct NoPrefetch {
-    __device__ void operator()(int, int) const {}
-};
-
-// For every node of the band: r = ld(P, i, j, k), then st(P, r).  U nodes
-// per thread and round, the loads of all U issued before the first store,
-// so that a pass with few loads per node still keeps U times the bytes in
-// flight (HBM latency, not bandwidth, bounds a pass with one node per round).
-// pf(lo, hi) prefetches the node range [lo, hi) of the pass's streamed
-// arrays into L2: thread 0 hands it the band of the plane after the one it
-// is in (one contiguous range of nj x mx nodes per plane), so the CTA's
-// loads find their lines in L2.
-template <int U, typename Ld, typename St, typename Pf = NoPrefetch>
-__device__ __forceinline__ void sweep3(const Band3 &b, int tid, int nt, Ld &&ld, St &&st, Pf &&pf = Pf{})
+// For every entry of the band: r = ld(P, i, j, k), then st(P, r).  U entries
+// per thread and round, the loads of all U issued before the first store.
+template <int U, typename Ld, typename St>
+__device__ __forceinline__ void sweep3(const Band3 &b, int tid, int nt, Ld &&ld, St &&st)
 {
     if (b.cnt <= 0) return;
     using R = decltype(ld(0, 0, 0, 0));
-    const int plane = b.mx * b.my, band = b.mx * b.nj, base = b.mx * b.j0;
-    const int planes = (int)(b.cnt / band);
-    int ahead = 0;   // planes handed to pf so far (thread 0)
     Walk3 wk;
     wk.init(b, tid, nt);
     for (int f = tid; f < b.cnt; f += U * nt) {
-        if (tid == 0)
-            for (; ahead < planes && ahead <= wk.k + 1; ++ahead) pf(base + plane * ahead, base + plane * ahead + band);
         R r[U];
         int P[U];
 #pragma unroll
@@ -345,12 +332,458 @@ __device__ __forceinline__ void sweep3(const Band3 &b, int tid, int nt, Ld &&ld,
     }
 }
 
-// nodes per thread and round: streaming passes with a few loads per node,
-// and passes with a 15-point product (thirty loads of their own)
-constexpr int kU3 = 4, kU15 = 1;
+// ---------------------------------------------------------------------------
+// Quad passes (the FP32 inner solve): four consecutive stored entries
+// (a 16-byte aligned quad of a padded row) per thread and 16-byte loads and
+// stores.  Quad f of a band lies in band-plane k = f / (nj px / 4), at entry
+// 4 (f mod (nj px / 4)) of that band-plane's contiguous range.
+// ---------------------------------------------------------------------------
 
+struct BandQ {
+    int px, plane, j0, nj, Q;   // Q = px / 4 quads per line
+    int cnt;                    // quads in the band
+};
+
+__device__ __forceinline__ BandQ bandq(const Grid3 &g, int rank, int cs)
+{
+    BandQ b;
+    b.px = g.px;
+    b.plane = g.px * g.my;
+    b.j0 = (int)(g.my * rank / cs);
+    b.nj = (int)(g.my * (rank + 1) / cs) - b.j0;
+    b.Q = g.px >> 2;
+    b.cnt = b.nj * b.Q * g.mz;
+    return b;
+}
+
+// quad position (qi, j0 + jl, k), advanced by a fixed stride of quads
+struct WalkQ {
+    int qi, jl, k, dq, dj, dk;
+    __device__ void init(const BandQ &b, int f, int stride)
+    {
+        qi = f % b.Q;
+        const int line = f / b.Q;
+        jl = line % b.nj;
+        k = line / b.nj;
+        dq = stride % b.Q;
+        const int lines = stride / b.Q;
+        dj = lines % b.nj;
+        dk = lines / b.nj;
+    }
+    __device__ void next(const BandQ &b)
+    {
+        qi += dq;
+        jl += dj;
+        k += dk;
+        if (qi >= b.Q) {
+            qi -= b.Q;
+            ++jl;
+        }
+        if (jl >= b.nj) {
+            jl -= b.nj;
+            ++k;
+        }
+    }
+    __device__ int i() const { return qi << 2; }
+    __device__ int j(const BandQ &b) const { return b.j0 + jl; }
+    __device__ int P(const BandQ &b) const { return (qi << 2) + b.px * (b.j0 + jl) + b.plane * k; }
+};
+
+__device__ __forceinline__ float4 ldq(const float *p) { return __ldcg(reinterpret_cast<const float4 *>(p)); }
+__device__ __forceinline__ void stq(float *p, const float4 &v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ float4 zq() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ float qel(const float4 &v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
+__device__ __forceinline__ float qdot(const float4 &a, const float4 &b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
+// four FP64 entries at a quad (two 16-byte accesses)
+__device__ __forceinline__ void ldq64(const double *p, double (&v)[4])
+{
+    const double2 a = __ldcg(reinterpret_cast<const double2 *>(p)), b = __ldcg(reinterpret_cast<const double2 *>(p) + 1);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+}
+__device__ __forceinline__ void stq64(double *p, const double (&v)[4])
+{
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+}
+
+// For every quad of the band: r = ld(P, wk), then st(P, r); U quads per
+// thread and round, all loads before the first store.
+template <int U, typename Ld, typename St>
+__device__ __forceinline__ void sweepq(const BandQ &b, int tid, int nt, Ld &&ld, St &&st)
+{
+    if (b.cnt <= 0) return;
+    using R = decltype(ld(0, WalkQ{}));
+    WalkQ wk;
+    wk.init(b, tid, nt);
+    for (int f = tid; f < b.cnt; f += U * nt) {
+        R r[U];
+        int P[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            P[u] = wk.P(b);
+            if (f + u * nt < b.cnt) r[u] = ld(P[u], wk);
+            wk.next(b);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (f + u * nt < b.cnt) st(P[u], r[u]);
+    }
+}
+
+// whether the quads of lanes - 1 and + 1 are the ones just before and after
+// this one in memory (then their loads supply the entries -1 and +4)
+struct NbQ {
+    bool hp, hn;
+};
+
+// The 15-point passes: a loop over rounds that every lane of a warp runs
+// (the product exchanges row ends between lanes).  A lane past the band's
+// end works on the band's first quad and does not store.
+template <typename Op>
+__device__ __forceinline__ void sweepq15(const BandQ &b, int tid, int nt, Op &&op)
+{
+    if (b.cnt <= 0) return;
+    const int lane = tid & 31;
+    const int P0 = b.px * b.j0;
+    WalkQ wk;
+    wk.init(b, tid, nt);
+    for (int base = 0; base < b.cnt; base += nt) {
+        const bool act = base + tid < b.cnt;
+        const int P = act ? wk.P(b) : P0;
+        const int Pp = __shfl_up_sync(0xffffffffu, P, 1), Pn = __shfl_down_sync(0xffffffffu, P, 1);
+        NbQ nb;
+        nb.hp = lane > 0 && Pp == P - 4;
+        nb.hn = lane < 31 && Pn == P + 4;
+        op(P, act, nb);
+        wk.next(b);
+    }
+}
+
+// (C x) at the quad P..P+3 of one sample's arrays (C [8][n], x [n], FP32):
+// the eight slots at the quad, the seven slots at the quad shifted by -d,
+// and seven rows of x (the quad's own row and the rows at +-y, +-z, +(y+z),
+// -(y+z)), all 16-byte loads.  The neighbours along x are those rows shifted
+// by one entry: entry -1 comes from lane - 1 (entry +4 from lane + 1) when
+// that lane holds the adjacent quad, else from one 4-byte load.  Rows
+// outside the array read as zero (their slots are zero).  xc returns x at
+// the quad.
+__device__ __forceinline__ float4 apply15q(const float *__restrict__ C, int n, int px, int plane, const float *x,
+                                           int P, NbQ nb, float4 &xc)
+{
+    const unsigned FULL = 0xffffffffu;
+    auto ldx = [&](int idx) -> float4 { return (idx >= 0 && idx <= n - 4) ? ldq(x + idx) : zq(); };
+    auto ldc = [&](int sl, int idx) -> float4 {
+        return (idx >= 0 && idx <= n - 4) ? __ldg(reinterpret_cast<const float4 *>(C + (size_t)sl * n + idx)) : zq();
+    };
+    const float4 x00 = ldx(P), xp0 = ldx(P + px), xm0 = ldx(P - px), x0p = ldx(P + plane), x0m = ldx(P - plane),
+                 xpp = ldx(P + px + plane), xmm = ldx(P - px - plane);
+    float4 cu[8], cd[8];
+#pragma unroll
+    for (int sl = 0; sl < 8; ++sl) cu[sl] = ldc(sl, P);
+#pragma unroll
+    for (int sl = 1; sl < 8; ++sl) {
+        // slot sl of the entries P - d .. P + 3 - d; for d with an x step the
+        // aligned quad starts one entry later and entry -1 is fetched below
+        const int off = (sl & 1) + px * ((sl >> 1) & 1) + plane * ((sl >> 2) & 1);
+        cd[sl] = ldc(sl, P - off + (sl & 1));
+    }
+    // the x-step slots 1, 3, 5, 7 and their rows: 0 (own), +-y, +-z, +-(y+z)
+    float cprev[4], xprev[4], xnext[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int sl = 2 * t + 1;
+        const float4 &dn = t == 0 ? x00 : t == 1 ? xm0 : t == 2 ? x0m : xmm;
+        const float4 &up = t == 0 ? x00 : t == 1 ? xp0 : t == 2 ? x0p : xpp;
+        const int off = 1 + px * ((sl >> 1) & 1) + plane * ((sl >> 2) & 1);
+        const int A = P - off + 1, B = P + off - 1;   // aligned starts of the dn / up rows
+        const float cs = __shfl_up_sync(FULL, cd[sl].w, 1);
+        const float xs = __shfl_up_sync(FULL, dn.w, 1);
+        const float xn = __shfl_down_sync(FULL, up.x, 1);
+        cprev[t] = nb.hp ? cs : (A >= 1 ? __ldg(C + (size_t)sl * n + A - 1) : 0.0f);
+        xprev[t] = nb.hp ? xs : (A >= 1 ? __ldcg(x + A - 1) : 0.0f);
+        xnext[t] = nb.hn ? xn : (B + 4 < n ? __ldcg(x + B + 4) : 0.0f);
+    }
+    float r[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        float a = qel(cu[0], e) * qel(x00, e);
+        a += qel(cu[2], e) * qel(xp0, e) + qel(cd[2], e) * qel(xm0, e);
+        a += qel(cu[4], e) * qel(x0p, e) + qel(cd[4], e) * qel(x0m, e);
+        a += qel(cu[6], e) * qel(xpp, e) + qel(cd[6], e) * qel(xmm, e);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int sl = 2 * t + 1;
+            const float4 &dn = t == 0 ? x00 : t == 1 ? xm0 : t == 2 ? x0m : xmm;
+            const float4 &up = t == 0 ? x00 : t == 1 ? xp0 : t == 2 ? x0p : xpp;
+            const float xu = e < 3 ? qel(up, e + 1) : xnext[t];
+            const float cdn = e > 0 ? qel(cd[sl], e - 1) : cprev[t];
+            const float xd = e > 0 ? qel(dn, e - 1) : xprev[t];
+            a += qel(cu[sl], e) * xu + cdn * xd;
+        }
+        r[e] = a;
+    }
+    xc = x00;
+    return make_float4(r[0], r[1], r[2], r[3]);
+}
+
+// nodes per thread and round of the scalar streaming passes, and quads per
+// thread and round of the FP32 streaming passes
+constexpr int kU3 = 2, kUQ = 2;
+
+// ---------------------------------------------------------------------------
+// The passes of the FP32 inner solve and of the FP64 block work, each its own
+// (not inlined) function: the loop over the band gets the whole register
+// budget, and the solver's live state is saved once per pass instead of being
+// spilled inside the loop.
+// ---------------------------------------------------------------------------
+
+// one level's stencil of one sample (FP32, [9][n]: eight slots, 1 / diagonal)
+struct QLev {
+    const float *A;
+    int n, px, plane;
+};
+
+__device__ __forceinline__ QLev qlev(const float *A, const Grid3 &g) { return QLev{A, g.n, g.px, g.px * g.my}; }
+
+__device__ __forceinline__ float4 dinvq(const QLev &L, int P)
+{
+    return __ldg(reinterpret_cast<const float4 *>(L.A + 8 * (size_t)L.n + P));
+}
+
+// w = A x; returns the thread's part of (w, x)
+static __device__ __noinline__ double qp_product(QLev L, BandQ b, const float *x, float *w)
+{
+    double acc = 0.0;
+    sweepq15(b, threadIdx.x, blockDim.x, [&](int P, bool act, NbQ nb) {
+        float4 xc;
+        const float4 ax = apply15q(L.A, L.n, L.px, L.plane, x, P, nb, xc);
+        if (act) {
+            stq(w + P, ax);
+            acc += (double)qdot(ax, xc);
+        }
+    });
+    return acc;
+}
+
+// rr = bb - A x
+static __device__ __noinline__ void qp_residual(QLev L, BandQ b, const float *x, const float *bb, float *rr)
+{
+    sweepq15(b, threadIdx.x, blockDim.x, [&](int P, bool act, NbQ nb) {
+        float4 xc;
+        const float4 ax = apply15q(L.A, L.n, L.px, L.plane, x, P, nb, xc);
+        const float4 r = ldq(bb + P);
+        if (act) stq(rr + P, make_float4(r.x - ax.x, r.y - ax.y, r.z - ax.z, r.w - ax.w));
+    });
+}
+
+// one damped-Jacobi sweep y = x + om D^-1 (bb - A x); returns the thread's
+// part of (bb, y) and (bb, bb)
+static __device__ __noinline__ double2 qp_smooth(QLev L, BandQ b, float om, const float *x, const float *bb, float *y)
+{
+    double s0 = 0.0, s1 = 0.0;
+    sweepq15(b, threadIdx.x, blockDim.x, [&](int P, bool act, NbQ nb) {
+        float4 xc;
+        const float4 ax = apply15q(L.A, L.n, L.px, L.plane, x, P, nb, xc);
+        const float4 d = dinvq(L, P), r = ldq(bb + P);
+        const float4 o = make_float4(xc.x + om * d.x * (r.x - ax.x), xc.y + om * d.y * (r.y - ax.y),
+                                     xc.z + om * d.z * (r.z - ax.z), xc.w + om * d.w * (r.w - ax.w));
+        if (act) {
+            stq(y + P, o);
+            s0 += (double)qdot(r, o);
+            s1 += (double)qdot(r, r);
+        }
+    });
+    return make_double2(s0, s1);
+}
+
+// xa = om D^-1 bb (the first Jacobi sweep from zero)
+static __device__ __noinline__ void qp_jacobi0(QLev L, BandQ b, float om, const float *bb, float *xa)
+{
+    sweepq<kUQ>(
+        b, threadIdx.x, blockDim.x,
+        [&](int P, const WalkQ &) {
+            const float4 d = dinvq(L, P), r = ldq(bb + P);
+            return make_float4(om * d.x * r.x, om * d.y * r.y, om * d.z * r.z, om * d.w * r.w);
+        },
+        [&](int P, const float4 &x) { stq(xa + P, x); });
+}
+
+// restriction P^T: coarse quad (I..I+3, J, K) of level gq from the fine
+// residual rr of level gf around (2I, 2J, 2K): the fine node plus half of
+// each of its (up to) fourteen edge neighbours; coarse pads get zero
+static __device__ __noinline__ void qp_restrict(Grid3 gf, Grid3 gq, BandQ bq, const float *rr, float *out)
+{
+    sweepq<1>(
+        bq, threadIdx.x, blockDim.x,
+        [&](int, const WalkQ &wk) {
+            const int fj = 2 * wk.j(bq), fk = 2 * wk.k;
+            float o[4];
+#pragma unroll 1
+            for (int e = 0; e < 4; ++e) {
+                const int ci = wk.i() + e;
+                const bool real = ci < gq.mx;
+                const int fi = real ? 2 * ci : 0;
+                const int f = fi + gf.px * (fj + gf.my * fk);
+                // branch-free: a missing neighbour loads the centre and
+                // enters with weight 0
+                float v[15], wgt[15];
+                v[0] = __ldcg(rr + f);
+#pragma unroll
+                for (int sl = 1; sl < 8; ++sl) {
+                    const int dx = sl & 1, dy = (sl >> 1) & 1, dz = (sl >> 2) & 1;
+                    const int off = dir_offset32(gf, sl);
+                    const bool up = fi + dx < gf.mx && fj + dy < gf.my && fk + dz < gf.mz;
+                    const bool dn = fi >= dx && fj >= dy && fk >= dz;
+                    v[2 * sl - 1] = __ldcg(rr + (up ? f + off : f));
+                    v[2 * sl] = __ldcg(rr + (dn ? f - off : f));
+                    wgt[2 * sl - 1] = up ? 1.0f : 0.0f;
+                    wgt[2 * sl] = dn ? 1.0f : 0.0f;
+                }
+                float h = 0.0f;
+#pragma unroll
+                for (int q = 1; q < 15; ++q) h += wgt[q] * v[q];
+                o[e] = real ? v[0] + 0.5f * h : 0.0f;
+            }
+            return make_float4(o[0], o[1], o[2], o[3]);
+        },
+        [&](int Q, const float4 &v) { stq(out + Q, v); });
+}
+
+// xb = xa + P xq: a fine node of level gc takes the mean of the ends of the
+// coarse edge (level gq) it halves; pads stay zero
+static __device__ __noinline__ void qp_prolong(Grid3 gc, Grid3 gq, BandQ bc, const float *xa, const float *xq, float *xb)
+{
+    sweepq<1>(
+        bc, threadIdx.x, blockDim.x,
+        [&](int P, const WalkQ &wk) {
+            const int j = wk.j(bc), k = wk.k;
+            const float4 x = ldq(xa + P);
+            const int ra = gq.px * ((j >> 1) + gq.my * (k >> 1));
+            const int rb = ra + gq.px * ((j & 1) + gq.my * (k & 1));
+            float o[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int i = wk.i() + e;
+                const bool real = i < gc.mx;
+                const int ci = real ? i >> 1 : 0;
+                const int qa = ra + ci, qb = rb + ci + (real ? (i & 1) : 0);
+                o[e] = real ? qel(x, e) + 0.5f * (__ldcg(xq + qa) + __ldcg(xq + qb)) : 0.0f;
+            }
+            return make_float4(o[0], o[1], o[2], o[3]);
+        },
+        [&](int P, const float4 &x) { stq(xb + P, x); });
+}
+
+// start of an inner solve: r = sc r, x = p = s = 0, z = dsc D^-1 r (the
+// Jacobi u, or the multigrid's pre-smoothed XA_0); returns the thread's part
+// of (r, z) and (r, r)
+static __device__ __noinline__ double2 qp_init(BandQ b, float sc, float dsc, float *R, const float *Dinv, float *Z, float *X,
+                                        float *Pv, float *Sv)
+{
+    double g = 0.0, r2 = 0.0;
+    sweepq<kUQ>(
+        b, threadIdx.x, blockDim.x,
+        [&](int P, const WalkQ &) {
+            Vals<float4, 2> o;
+            const float4 r = ldq(R + P);
+            const float4 d = __ldg(reinterpret_cast<const float4 *>(Dinv + P));
+            o.v[0] = make_float4(r.x * sc, r.y * sc, r.z * sc, r.w * sc);
+            o.v[1] = make_float4(dsc * d.x * o.v[0].x, dsc * d.y * o.v[0].y, dsc * d.z * o.v[0].z, dsc * d.w * o.v[0].w);
+            return o;
+        },
+        [&](int P, const Vals<float4, 2> &o) {
+            stq(R + P, o.v[0]);
+            stq(Z + P, o.v[1]);
+            stq(X + P, zq());
+            stq(Pv + P, zq());
+            stq(Sv + P, zq());
+            g += (double)qdot(o.v[0], o.v[1]);
+            r2 += (double)qdot(o.v[0], o.v[0]);
+        });
+    return make_double2(g, r2);
+}
+
+// CG update: s = w + tb s, p = u + tb p (s = w, p = u on the first
+// iteration), x += ta p, r -= ta s, z = dsc D^-1 r; returns the thread's
+// part of (r, r) and (r, z)
+static __device__ __noinline__ double2 qp_update(BandQ b, float ta, float tb, bool first, float dsc, const float *W, const float *U,
+                                          float *Sv, float *Pv, float *X, float *R, const float *Dinv, float *Z)
+{
+    double r2 = 0.0, g = 0.0;
+    sweepq<kUQ>(
+        b, threadIdx.x, blockDim.x,
+        [&](int P, const WalkQ &) {
+            const float4 w = ldq(W + P), u = ldq(U + P);
+            const float4 s0 = first ? zq() : ldq(Sv + P);
+            const float4 p0 = first ? zq() : ldq(Pv + P);
+            const float4 x0 = ldq(X + P), r0 = ldq(R + P);
+            const float4 d = __ldg(reinterpret_cast<const float4 *>(Dinv + P));
+            Vals<float4, 5> o;
+            o.v[0] = make_float4(w.x + tb * s0.x, w.y + tb * s0.y, w.z + tb * s0.z, w.w + tb * s0.w);
+            o.v[1] = make_float4(u.x + tb * p0.x, u.y + tb * p0.y, u.z + tb * p0.z, u.w + tb * p0.w);
+            o.v[2] = make_float4(x0.x + ta * o.v[1].x, x0.y + ta * o.v[1].y, x0.z + ta * o.v[1].z, x0.w + ta * o.v[1].w);
+            o.v[3] = make_float4(r0.x - ta * o.v[0].x, r0.y - ta * o.v[0].y, r0.z - ta * o.v[0].z, r0.w - ta * o.v[0].w);
+            o.v[4] = make_float4(dsc * d.x * o.v[3].x, dsc * d.y * o.v[3].y, dsc * d.z * o.v[3].z, dsc * d.w * o.v[3].w);
+            return o;
+        },
+        [&](int P, const Vals<float4, 5> &o) {
+            stq(Sv + P, o.v[0]);
+            stq(Pv + P, o.v[1]);
+            stq(X + P, o.v[2]);
+            stq(R + P, o.v[3]);
+            stq(Z + P, o.v[4]);
+            r2 += (double)qdot(o.v[3], o.v[3]);
+            g += (double)qdot(o.v[3], o.v[4]);
+        });
+    return make_double2(r2, g);
+}
+
+// FP64 block work: b = M y and r = b - A v (stored in the inner precision);
+// returns the thread's part of (b, b) and (r, r)
+template <typename TI>
+static __device__ __noinline__ double2 sp_load_rhs(Grid3 G, Band3 B, const double *M3, const double *A64, const double *yb,
+                                            const double *v, double *b, TI *R)
+{
+    double bb = 0.0, rr = 0.0;
+    sweep3<1>(
+        B, threadIdx.x, blockDim.x,
+        [&](int P, int, int, int) {
+            Vals<double, 2> o;
+            o.v[0] = apply15<double, double>(M3, G, yb, P);
+            o.v[1] = o.v[0] - apply15<double, double>(A64, G, v, P);
+            return o;
+        },
+        [&](int P, const Vals<double, 2> &o) {
+            b[P] = o.v[0];
+            R[P] = (TI)o.v[1];
+            bb += o.v[0] * o.v[0];
+            rr += o.v[1] * o.v[1];
+        });
+    return make_double2(bb, rr);
+}
+
+// FP64 refinement residual r = b - A v; returns the thread's part of (r, r)
+template <typename TI>
+static __device__ __noinline__ double sp_residual(Grid3 G, Band3 B, const double *A64, const double *b, const double *v, TI *R)
+{
+    double rr = 0.0;
+    sweep3<1>(
+        B, threadIdx.x, blockDim.x, [&](int P, int, int, int) { return b[P] - apply15<double, double>(A64, G, v, P); },
+        [&](int P, double t) {
+            R[P] = (TI)t;
+            rr += t * t;
+        });
+    return rr;
+}
+
+// One sample per cluster of CS CTAs.  256 threads with up to 128 registers
+// each: the 15-point quad product keeps its 22 16-byte loads in flight per
+// thread.
 template <typename TI, int CS>
-__global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
+__global__ void __launch_bounds__(256, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
 {
     __shared__ double wsl[32][4];
     __shared__ double csl[2][4];
@@ -365,6 +798,7 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
     const Grid3 G = g.g;
     const int n = G.n;
     const Band3 B0 = band3(G, rank, CS);
+    const BandQ Q0 = bandq(G, rank, CS);
     const int tid = threadIdx.x, nt = blockDim.x;
     constexpr bool mixed = sizeof(TI) == 4;
 
@@ -372,7 +806,7 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
     const size_t SN = (size_t)g.S * n;
     const double *A64 = g.A64 + (size_t)sample * kSlots3D * n;
     const TI *Ai = g.Ai + (size_t)sample * kSlots3D * n;
-    const TI *__restrict__ Dinv = Ai + 8 * n;
+    const TI *__restrict__ Dinv = Ai + 8 * (size_t)n;
     // v: [kVRing][S][n], the solutions of the last blocks and the guess of the next
     double *vb0 = g.v + so, *wb0 = g.w + so, *b = g.b + so, *yb = g.y + so;
     TI *__restrict__ R = g.r + so;
@@ -381,24 +815,23 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
     TI *__restrict__ Sv = g.s + so;
     TI *__restrict__ Pv = g.p + so;
     TI *__restrict__ X = g.x + so;
-    // L2 prefetch sets of the streaming passes: the eight stencil slots of a
-    // level, and single vectors
-    auto pf_slots = [](const auto *A, int nn, int lo, int hi) {
-#pragma unroll 1
-        for (int sl = 0; sl < 8; ++sl) prefetch_l2(A + sl * nn, lo, hi);
-    };
 
+    // initial state: v0 / w0 (unpadded) or the disk; pads zero
     sweep3<1>(
         B0, tid, nt,
-        [&](int P, int i, int j, int k) {
+        [&](int, int i, int j, int k) {
             Vals<double, 2> s0;
-            if (g.v0) {
-                s0.v[0] = g.v0[P];
-                s0.v[1] = g.w0 ? g.w0[P] : 0.0;
-            } else {
-                const double xx = g.Lx * i / (G.mx - 1), yy = g.Ly * j / (G.my - 1), zz = g.Lz * k / (G.mz - 1);
-                s0.v[0] = (xx * xx + yy * yy + zz * zz <= g.radius2) ? 1.0 : 0.0;
-                s0.v[1] = 0.0;
+            s0.v[0] = 0.0;
+            s0.v[1] = 0.0;
+            if (i < G.mx) {
+                if (g.v0) {
+                    const int64_t node = i + (int64_t)G.mx * (j + (int64_t)G.my * k);
+                    s0.v[0] = g.v0[node];
+                    s0.v[1] = g.w0 ? g.w0[node] : 0.0;
+                } else {
+                    const double xx = g.Lx * i / (G.mx - 1), yy = g.Ly * j / (G.my - 1), zz = g.Lz * k / (G.mz - 1);
+                    s0.v[0] = (xx * xx + yy * yy + zz * zz <= g.radius2) ? 1.0 : 0.0;
+                }
             }
             return s0;
         },
@@ -417,23 +850,19 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
     const double dt = g.dt;
 
     // ---- multigrid preconditioner u = MG(r) (FP32 inner path, nl > 1):
-    // V(1,1) with damped Jacobi, P^T restriction (the fine node 2I plus half
-    // of the fourteen edge midpoints 2I +- d), P1 interpolation (a fine node
-    // takes the mean of the coarse ends of the coarse edge it halves),
-    // Jacobi sweeps on the coarsest level.  Every level is split over the
-    // cluster by grid lines; values of other CTAs are read through L2 after a
-    // cluster barrier.  Input: R (level 0 right-hand side) and its
-    // pre-smoothed XA_0 = omega D^-1 R, written by the pass that formed R;
-    // result in U.  Returns (r, u) and (r, r) (the thread's partial sums),
-    // formed in the level-0 post-smoothing.
+    // V(1,1) with damped Jacobi, P^T restriction, P1 interpolation, Jacobi
+    // sweeps on the coarsest level.  Every level is split over the cluster by
+    // grid lines; values of other CTAs are read through L2 after a cluster
+    // barrier.  Input: R (level 0 right-hand side) and its pre-smoothed
+    // XA_0 = omega D^-1 R, written by the pass that formed R; result in U.
+    // Returns (r, u) and (r, r) (the thread's partial sums), formed in the
+    // level-0 post-smoothing.
     constexpr bool kMg = sizeof(TI) == 4;
     const bool mgp = kMg && g.mg.nl > 1;
     float *const xa0 = mgp ? g.mg.xa[0] + so : nullptr;
-    const TI om0 = (TI)g.mg.omega;
+    const float om0 = g.mg.omega;
     auto vcycle = [&]() {
-        Vals<double, 2> sums;
-        sums.v[0] = 0.0;
-        sums.v[1] = 0.0;
+        double2 sums = make_double2(0.0, 0.0);
         if constexpr (kMg) {
             const Mg3Args &M = sM;
             const int NL = M.nl;
@@ -446,140 +875,46 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
             auto RR = [&](int c) -> float * { return c == 0 ? (float *)U : vec(M.rr, c); };
             for (int c = 0; c < NL - 1; ++c) {
                 const Grid3 &Gc = M.g[c];
-                const Band3 Bc = band3(Gc, rank, CS);
-                const float *A = Aof(c), *Dv = A + 8 * (size_t)Gc.n;
-                float *xa = vec(M.xa, c), *rr = RR(c), *bb = BB(c);
+                const BandQ Bc = bandq(Gc, rank, CS);
+                const QLev Lc = qlev(Aof(c), Gc);
                 // pre-smoothing from zero: XA = omega D^-1 B (level 0: done)
                 if (c > 0) {
-                    sweep3<kU3>(
-                        Bc, tid, nt, [&](int P, int, int, int) { return om * Dv[P] * __ldcg(bb + P); },
-                        [&](int P, float x) { xa[P] = x; },
-                        [&](int lo, int hi) {
-                            prefetch_l2(Dv, lo, hi);
-                            prefetch_l2(bb, lo, hi);
-                        });
+                    qp_jacobi0(Lc, Bc, om, BB(c), vec(M.xa, c));
                     cl.sync();
                 }
-                // residual RR = B - A XA
-                sweep3<kU15>(
-                    Bc, tid, nt,
-                    [&](int P, int i, int j, int k) {
-                        return __ldcg(bb + P) - apply15<float, float>(A, Gc, xa, P, i, j, k);
-                    },
-                    [&](int P, float r) { rr[P] = r; },
-                    [&](int lo, int hi) {
-                        pf_slots(A, Gc.n, lo, hi);
-                        prefetch_l2(xa, lo, hi);
-                        prefetch_l2(bb, lo, hi);
-                    });
+                qp_residual(Lc, Bc, vec(M.xa, c), BB(c), RR(c));
                 cl.sync();
-                // restriction into level c+1
-                const Grid3 &Gq = M.g[c + 1];
-                float *bq = BB(c + 1);
-                sweep3<kU15>(
-                    band3(Gq, rank, CS), tid, nt,
-                    [&](int, int ci, int cj, int ck) {
-                        const int fi = 2 * ci, fj = 2 * cj, fk = 2 * ck;
-                        const int f = fi + Gc.mx * (fj + Gc.my * fk);
-                        // branch-free: a missing neighbour loads the centre
-                        // and enters with weight 0 (h + 0 v = h exactly), so
-                        // boundary nodes do not split their warp
-                        float v[15], wgt[15];
-                        v[0] = __ldcg(rr + f);
-#pragma unroll
-                        for (int sl = 1; sl < 8; ++sl) {
-                            const int dx = sl & 1, dy = (sl >> 1) & 1, dz = (sl >> 2) & 1;
-                            const int off = dir_offset32(Gc, sl);
-                            const bool up = fi + dx < Gc.mx && fj + dy < Gc.my && fk + dz < Gc.mz;
-                            const bool dn = fi >= dx && fj >= dy && fk >= dz;
-                            v[2 * sl - 1] = __ldcg(rr + (up ? f + off : f));
-                            v[2 * sl] = __ldcg(rr + (dn ? f - off : f));
-                            wgt[2 * sl - 1] = up ? 1.0f : 0.0f;
-                            wgt[2 * sl] = dn ? 1.0f : 0.0f;
-                        }
-                        float h = 0.0f;
-#pragma unroll
-                        for (int q = 1; q < 15; ++q) h += wgt[q] * v[q];
-                        return v[0] + 0.5f * h;
-                    },
-                    [&](int Q, float v) { bq[Q] = v; });
+                qp_restrict(Gc, M.g[c + 1], bandq(M.g[c + 1], rank, CS), RR(c), BB(c + 1));
                 cl.sync();
             }
             // coarsest: damped Jacobi sweeps, ping-pong XA / XB
             {
                 const int c = NL - 1;
                 const Grid3 &Gc = M.g[c];
-                const Band3 Bc = band3(Gc, rank, CS);
-                const float *A = Aof(c), *Dv = A + 8 * (size_t)Gc.n;
-                float *X0 = vec(M.xa, c), *Y0 = vec(M.xb, c), *bb = BB(c);
-                sweep3<kU3>(
-                    Bc, tid, nt, [&](int P, int, int, int) { return om * Dv[P] * __ldcg(bb + P); },
-                    [&](int P, float x) { X0[P] = x; });
+                const BandQ Bc = bandq(Gc, rank, CS);
+                const QLev Lc = qlev(Aof(c), Gc);
+                float *X0 = vec(M.xa, c), *Y0 = vec(M.xb, c);
+                qp_jacobi0(Lc, Bc, om, BB(c), X0);
                 for (int k = 1; k < kMgCoarsestSweeps3D; ++k) {
                     cl.sync();
-                    sweep3<kU15>(
-                        Bc, tid, nt,
-                        [&](int P, int i, int j, int kk) {
-                            return __ldcg(X0 + P) +
-                                   om * Dv[P] * (__ldcg(bb + P) - apply15<float, float>(A, Gc, X0, P, i, j, kk));
-                        },
-                        [&](int P, float x) { Y0[P] = x; });
+                    qp_smooth(Lc, Bc, om, X0, BB(c), Y0);
                     float *t = X0;
                     X0 = Y0;
                     Y0 = t;
                 }
                 cl.sync();
             }
-            // ascend
+            // ascend: XB = XA + P X_{c+1}, then post-smoothing
+            // X_c = XB + omega D^-1 (B - A XB) into RR (level 0: U)
             for (int c = NL - 2; c >= 0; --c) {
-                const Grid3 &Gc = M.g[c], &Gq = M.g[c + 1];
-                const Band3 Bc = band3(Gc, rank, CS);
-                const float *A = Aof(c), *Dv = A + 8 * (size_t)Gc.n;
+                const Grid3 &Gc = M.g[c];
+                const BandQ Bc = bandq(Gc, rank, CS);
                 const float *xq = (c + 1 == NL - 1) ? ((kMgCoarsestSweeps3D - 1) % 2 ? vec(M.xb, c + 1) : vec(M.xa, c + 1))
                                                     : RR(c + 1);
-                float *xa = vec(M.xa, c), *xb = vec(M.xb, c), *rr = RR(c), *bb = BB(c);
-                // XB = XA + P X_{c+1}
-                sweep3<kU3>(
-                    Bc, tid, nt,
-                    [&](int P, int i, int j, int k) {
-                        const int ci = i >> 1, cj = j >> 1, ck = k >> 1;
-                        const int qa = ci + Gq.mx * (cj + Gq.my * ck);
-                        const int qb = qa + (i & 1) + Gq.mx * ((j & 1) + Gq.my * (k & 1));
-                        return __ldcg(xa + P) + 0.5f * (__ldcg(xq + qa) + __ldcg(xq + qb));
-                    },
-                    [&](int P, float x) { xb[P] = x; }, [&](int lo, int hi) { prefetch_l2(xa, lo, hi); });
+                qp_prolong(Gc, M.g[c + 1], Bc, vec(M.xa, c), xq, vec(M.xb, c));
                 cl.sync();
-                // post-smoothing X_c = XB + omega D^-1 (B - A XB), into RR
-                auto pf_post = [&](int lo, int hi) {
-                    pf_slots(A, Gc.n, lo, hi);
-                    prefetch_l2(Dv, lo, hi);
-                    prefetch_l2(xb, lo, hi);
-                    prefetch_l2(bb, lo, hi);
-                };
-                if (c > 0) {
-                    sweep3<kU15>(
-                        Bc, tid, nt,
-                        [&](int P, int i, int j, int k) {
-                            return __ldcg(xb + P) +
-                                   om * Dv[P] * (__ldcg(bb + P) - apply15<float, float>(A, Gc, xb, P, i, j, k));
-                        },
-                        [&](int P, float x) { rr[P] = x; }, pf_post);
-                } else {
-                    sweep3<kU15>(
-                        Bc, tid, nt,
-                        [&](int P, int i, int j, int k) {
-                            Vals<float, 2> o;
-                            o.v[1] = __ldcg(bb + P);
-                            o.v[0] = __ldcg(xb + P) + om * Dv[P] * (o.v[1] - apply15<float, float>(A, Gc, xb, P, i, j, k));
-                            return o;
-                        },
-                        [&](int P, const Vals<float, 2> &o) {
-                            rr[P] = o.v[0];
-                            sums.v[0] += (double)(o.v[1] * o.v[0]);
-                            sums.v[1] += (double)(o.v[1] * o.v[1]);
-                        },
-                        pf_post);
-                }
+                const double2 t = qp_smooth(qlev(Aof(c), Gc), Bc, om, vec(M.xb, c), BB(c), RR(c));
+                if (c == 0) sums = t;
                 cl.sync();
             }
         }
@@ -597,7 +932,7 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
         const int gp = guess_order(step);
         const double *wcur = wb0 + wpar * SN;
         double *wnext = wb0 + (wpar ^ 1) * SN;
-        sweep3<2>(
+        sweep3<kU3>(
             B0, tid, nt,
             [&](int P, int, int, int) {
                 const double vv = vcur[P], ww = wcur[P];
@@ -618,21 +953,8 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
         wpar ^= 1;
         cl.sync();
         {
-            double acc[2] = {0.0, 0.0};
-            sweep3<1>(
-                B0, tid, nt,
-                [&](int P, int i, int j, int k) {
-                    Vals<double, 2> o;
-                    o.v[0] = apply15<double, double>(g.M3, G, yb, P, i, j, k);
-                    o.v[1] = o.v[0] - apply15<double, double>(A64, G, v, P, i, j, k);
-                    return o;
-                },
-                [&](int P, const Vals<double, 2> &o) {
-                    b[P] = o.v[0];
-                    R[P] = (TI)o.v[1];
-                    acc[0] += o.v[0] * o.v[0];
-                    acc[1] += o.v[1] * o.v[1];
-                });
+            const double2 t = sp_load_rhs<TI>(G, B0, g.M3, A64, yb, v, b, R);
+            double acc[2] = {t.x, t.y};
             cluster_reduce<2, CS>(acc, wsl, csl, par, [&](double(&t)[2]) {
                 ctl.s0 = t[0];
                 ctl.s1 = t[1];
@@ -650,16 +972,7 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
         const int sweeps = mixed ? g.max_sweeps : 1;
         for (int sweep = 0; sweep < sweeps; ++sweep) {
             if (sweep > 0) {
-                double racc[1] = {0.0};
-                sweep3<1>(
-                    B0, tid, nt,
-                    [&](int P, int i, int j, int k) {
-                        return b[P] - apply15<double, double>(A64, G, v, P, i, j, k);
-                    },
-                    [&](int P, double rr) {
-                        R[P] = (TI)rr;
-                        racc[0] += rr * rr;
-                    });
+                double racc[1] = {sp_residual<TI>(G, B0, A64, b, v, R)};
                 cluster_reduce<1, CS>(racc, wsl, csl, par, [&](double(&t)[1]) { ctl.s1 = t[0]; });
                 par ^= 1;
                 rnorm2 = ctl.s1;
@@ -682,30 +995,38 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
             const double tol_in2 = mixed ? fmax(g.rtol_in * g.rtol_in, 0.25 * need) : need;
 
             // init: r0 normalised, x = p = s = 0; u0 = D^-1 r0 (Jacobi) or the
-            // multigrid's pre-smoothed XA_0 = omega D^-1 r0
-            sweep3<kU3>(
-                B0, tid, nt,
-                [&](int P, int, int, int) {
-                    Vals<TI, 2> o;
-                    o.v[0] = R[P] * rscale;
-                    o.v[1] = mgp ? om0 * Dinv[P] * o.v[0] : Dinv[P] * o.v[0];
-                    return o;
-                },
-                [&](int P, const Vals<TI, 2> &o) {
-                    R[P] = o.v[0];
-                    if (mgp) xa0[P] = (float)o.v[1];
-                    else U[P] = o.v[1];
-                    X[P] = (TI)0;
-                    Pv[P] = (TI)0;
-                    Sv[P] = (TI)0;
-                });
-            cl.sync();
-            // (r, u) and (r, r) of the current iterate
+            // multigrid's pre-smoothed XA_0 = omega D^-1 r0; (r, u), (r, r)
+            // of the Jacobi start
             double gacc = 0.0, racc = 0.0;
+            if constexpr (mixed) {
+                const double2 t = qp_init(Q0, (float)rscale, mgp ? om0 : 1.0f, (float *)R, (const float *)Dinv,
+                                          mgp ? xa0 : (float *)U, (float *)X, (float *)Pv, (float *)Sv);
+                gacc = t.x;
+                racc = t.y;
+            } else {
+                sweep3<kU3>(
+                    B0, tid, nt,
+                    [&](int P, int, int, int) {
+                        Vals<TI, 2> o;
+                        o.v[0] = R[P] * rscale;
+                        o.v[1] = Dinv[P] * o.v[0];
+                        return o;
+                    },
+                    [&](int P, const Vals<TI, 2> &o) {
+                        R[P] = o.v[0];
+                        U[P] = o.v[1];
+                        X[P] = (TI)0;
+                        Pv[P] = (TI)0;
+                        Sv[P] = (TI)0;
+                        gacc += (double)(o.v[0] * o.v[1]);
+                        racc += (double)(o.v[0] * o.v[0]);
+                    });
+            }
+            cl.sync();
             if (mgp) {
-                const Vals<double, 2> t = vcycle();
-                gacc = t.v[0];
-                racc = t.v[1];
+                const double2 t = vcycle();
+                gacc = t.x;
+                racc = t.y;
             }
             double gamma_prev = 1.0, eta_prev = 1.0;
             int it = 0;
@@ -730,43 +1051,25 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                 ctl.beta = beta;
                 ctl.code = code;
             };
-            if (!mgp) {
-                sweep3<kU3>(
-                    B0, tid, nt,
-                    [&](int P, int, int, int) {
-                        Vals<TI, 2> o;
-                        o.v[0] = R[P];
-                        o.v[1] = __ldcg(U + P);
-                        return o;
-                    },
-                    [&](int, const Vals<TI, 2> &o) {
-                        gacc += (double)(o.v[0] * o.v[1]);
-                        racc += (double)(o.v[0] * o.v[0]);
-                    },
-                    [&](int lo, int hi) {
-                        prefetch_l2(R, lo, hi);
-                        prefetch_l2(U, lo, hi);
-                    });
-            }
             while (true) {
                 // w = A u, (w, u); one reduction of (r, u), (w, u), (r, r)
                 double pacc[3] = {gacc, 0.0, racc};
-                sweep3<kU15>(
-                    B0, tid, nt,
-                    [&](int P, int i, int j, int k) {
-                        Vals<TI, 2> o;
-                        o.v[0] = apply15<TI, TI>(Ai, G, U, P, i, j, k);
-                        o.v[1] = __ldcg(U + P);
-                        return o;
-                    },
-                    [&](int P, const Vals<TI, 2> &o) {
-                        W[P] = o.v[0];
-                        pacc[1] += (double)(o.v[0] * o.v[1]);
-                    },
-                    [&](int lo, int hi) {
-                        pf_slots(Ai, n, lo, hi);
-                        prefetch_l2(U, lo, hi);
-                    });
+                if constexpr (mixed) {
+                    pacc[1] = qp_product(qlev((const float *)Ai, G), Q0, (const float *)U, (float *)W);
+                } else {
+                    sweep3<1>(
+                        B0, tid, nt,
+                        [&](int P, int, int, int) {
+                            Vals<TI, 2> o;
+                            o.v[0] = apply15<TI, TI>(Ai, G, U, P);
+                            o.v[1] = __ldcg(U + P);
+                            return o;
+                        },
+                        [&](int P, const Vals<TI, 2> &o) {
+                            W[P] = o.v[0];
+                            pacc[1] += (double)(o.v[0] * o.v[1]);
+                        });
+                }
                 cluster_reduce<3, CS>(pacc, wsl, csl, par, [&](double(&t)[3]) { decide(t[0], t[1], t[2]); });
                 par ^= 1;
                 const int code = ctl.code;
@@ -777,49 +1080,45 @@ __global__ void __launch_bounds__(512, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                 }
                 const TI ta = (TI)ctl.alpha, tb = (TI)ctl.beta;
                 // s = w + b s; p = u + b p; x += a p; r -= a s; u = D^-1 r
-                gacc = 0.0;
-                racc = 0.0;
-                sweep3<2>(
-                    B0, tid, nt,
-                    [&](int P, int, int, int) {
-                        const TI ww = W[P], uu = __ldcg(U + P);
-                        Vals<TI, 5> o;
-                        o.v[0] = it == 0 ? ww : ww + tb * Sv[P];
-                        o.v[1] = it == 0 ? uu : uu + tb * Pv[P];
-                        o.v[2] = X[P] + ta * o.v[1];
-                        o.v[3] = R[P] - ta * o.v[0];
-                        o.v[4] = mgp ? om0 * Dinv[P] * o.v[3] : Dinv[P] * o.v[3];
-                        return o;
-                    },
-                    [&](int P, const Vals<TI, 5> &o) {
-                        Sv[P] = o.v[0];
-                        Pv[P] = o.v[1];
-                        X[P] = o.v[2];
-                        R[P] = o.v[3];
-                        racc += (double)(o.v[3] * o.v[3]);
-                        if (mgp) {
-                            xa0[P] = (float)o.v[4];
-                        } else {
+                // (multigrid: XA_0 = omega D^-1 r, the V-cycle forms u)
+                if constexpr (mixed) {
+                    const double2 t = qp_update(Q0, (float)ta, (float)tb, it == 0, mgp ? om0 : 1.0f, (const float *)W,
+                                                (const float *)U, (float *)Sv, (float *)Pv, (float *)X, (float *)R,
+                                                (const float *)Dinv, mgp ? xa0 : (float *)U);
+                    racc = t.x;
+                    gacc = t.y;
+                } else {
+                    gacc = 0.0;
+                    racc = 0.0;
+                    sweep3<kU3>(
+                        B0, tid, nt,
+                        [&](int P, int, int, int) {
+                            const TI ww = W[P], uu = __ldcg(U + P);
+                            Vals<TI, 5> o;
+                            o.v[0] = it == 0 ? ww : ww + tb * Sv[P];
+                            o.v[1] = it == 0 ? uu : uu + tb * Pv[P];
+                            o.v[2] = X[P] + ta * o.v[1];
+                            o.v[3] = R[P] - ta * o.v[0];
+                            o.v[4] = Dinv[P] * o.v[3];
+                            return o;
+                        },
+                        [&](int P, const Vals<TI, 5> &o) {
+                            Sv[P] = o.v[0];
+                            Pv[P] = o.v[1];
+                            X[P] = o.v[2];
+                            R[P] = o.v[3];
                             U[P] = o.v[4];
+                            racc += (double)(o.v[3] * o.v[3]);
                             gacc += (double)(o.v[3] * o.v[4]);
-                        }
-                    },
-                    [&](int lo, int hi) {
-                        prefetch_l2(W, lo, hi);
-                        prefetch_l2(U, lo, hi);
-                        prefetch_l2(Sv, lo, hi);
-                        prefetch_l2(Pv, lo, hi);
-                        prefetch_l2(X, lo, hi);
-                        prefetch_l2(R, lo, hi);
-                        prefetch_l2(Dinv, lo, hi);
-                    });
+                        });
+                }
                 ++it;
                 cl.sync();
-                if (mgp) gacc = vcycle().v[0];
+                if (mgp) gacc = vcycle().x;
             }
             total_iters += it;
             if (nonfinite) break;
-            sweep3<2>(
+            sweep3<kU3>(
                 B0, tid, nt, [&](int P, int, int, int) { return fma((double)X[P], rnorm, v[P]); },
                 [&](int P, double t) { v[P] = t; });
             cl.sync();

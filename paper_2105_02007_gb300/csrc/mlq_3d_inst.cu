@@ -1,32 +1,74 @@
 // mlq_3d_inst.cu -- instantiations and launchers of the 3D (Kuhn tetrahedra)
-// kernels.
+// kernels.  Compiled twice: MLQ_F64 = 0 (FP32 inner solve, with the level
+// set-up kernels) and MLQ_F64 = 1 (FP64 inner solve), so that the two build
+// in parallel.
+#ifndef MLQ_F64
+#define MLQ_F64 0
+#endif
+#if !MLQ_F64
+#define MLQ_3D_SETUP
+#endif
+
 #include "mlq_3d.cuh"
 #include "mlq_launch.cuh"
 
+#include <type_traits>
+
 namespace mlq {
 
-template <typename TI>
-cudaError_t launch_3d(int cs, const Solve3Args<TI> &a, int nclusters, int threads, cudaStream_t st)
+namespace {
+
+#if MLQ_F64
+using TI3 = double;
+#else
+using TI3 = float;
+#endif
+
+template <typename F>
+cudaError_t with_cs(int cs, F &&f)
 {
     switch (cs) {
-    case 1: return cluster_launch<1>(slab_solve_3d_kernel<TI, 1>, nclusters, threads, 0, st, a);
-    case 2: return cluster_launch<2>(slab_solve_3d_kernel<TI, 2>, nclusters, threads, 0, st, a);
-    case 4: return cluster_launch<4>(slab_solve_3d_kernel<TI, 4>, nclusters, threads, 0, st, a);
-    case 8: return cluster_launch<8>(slab_solve_3d_kernel<TI, 8>, nclusters, threads, 0, st, a);
-    case 16: return cluster_launch<16>(slab_solve_3d_kernel<TI, 16>, nclusters, threads, 0, st, a);
+    case 1: return f(std::integral_constant<int, 1>{});
+    case 2: return f(std::integral_constant<int, 2>{});
+    case 4: return f(std::integral_constant<int, 4>{});
+    case 6: return f(std::integral_constant<int, 6>{});
+    case 8: return f(std::integral_constant<int, 8>{});
+    case 12: return f(std::integral_constant<int, 12>{});
+    case 16: return f(std::integral_constant<int, 16>{});
     default: return cudaErrorInvalidValue;
     }
 }
 
+}  // namespace
+
+#if MLQ_F64
+cudaError_t launch_3d_f64(int cs, const Solve3Args<double> &a, int nclusters, int threads, cudaStream_t st)
+#else
 cudaError_t launch_3d_f32(int cs, const Solve3Args<float> &a, int nclusters, int threads, cudaStream_t st)
+#endif
 {
-    return launch_3d<float>(cs, a, nclusters, threads, st);
+    return with_cs(cs, [&](auto c) {
+        constexpr int CS = decltype(c)::value;
+        return cluster_launch<CS>(slab_solve_3d_kernel<TI3, CS>, nclusters, threads, 0, st, a);
+    });
 }
 
-cudaError_t launch_3d_f64(int cs, const Solve3Args<double> &a, int nclusters, int threads, cudaStream_t st)
+#if MLQ_F64
+int active_3d_f64(int cs, int threads)
+#else
+int active_3d_f32(int cs, int threads)
+#endif
 {
-    return launch_3d<double>(cs, a, nclusters, threads, st);
+    int nc = 0;
+    with_cs(cs, [&](auto c) {
+        constexpr int CS = decltype(c)::value;
+        nc = cluster_occupancy<CS>(slab_solve_3d_kernel<TI3, CS>, threads, 0);
+        return cudaSuccess;
+    });
+    return nc;
 }
+
+#if !MLQ_F64
 
 cudaError_t launch_level3d_setup(const Grid3 &g, double *M3, double *lump, cudaStream_t st)
 {
@@ -55,5 +97,7 @@ cudaError_t launch_mg3_setup(const double *cs2, const float *dfine, const Grid3 
                                                                                                Ac);
     return cudaGetLastError();
 }
+
+#endif
 
 }  // namespace mlq

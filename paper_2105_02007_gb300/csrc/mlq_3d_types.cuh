@@ -11,10 +11,39 @@ namespace mlq {
 
 constexpr int kSlots3D = 9;  // diagonal, seven couplings, 1 / diagonal
 
+// Node (i, j, k) of an mx x my x mz grid is stored at i + px (j + my k): rows
+// are padded to px = mx rounded up to a multiple of 4, so that every row and
+// plane starts on a 16-byte boundary of an FP32 array and the solver moves
+// four consecutive nodes with one 16-byte access.  The pad entries (i >= mx)
+// of every stencil slot, mass and vector are zero; a stencil slot that
+// couples a node to a pad entry is zero as well (no such edge), so the pads
+// take part in the passes and stay zero.  n counts the stored entries.
 struct Grid3 {
-    int mx, my, mz, n;
+    int mx, my, mz;
+    int px;      // row pitch (multiple of 4)
+    int n;       // px * my * mz stored entries
     double hx, hy, hz;
 };
+
+__host__ __device__ inline Grid3 make_grid3(int mx, int my, int mz, double hx, double hy, double hz)
+{
+    Grid3 g;
+    g.mx = mx;
+    g.my = my;
+    g.mz = mz;
+    g.px = (mx + 3) & ~3;
+    g.n = g.px * my * mz;
+    g.hx = hx;
+    g.hy = hy;
+    g.hz = hz;
+    return g;
+}
+
+// stored index of node (i, j, k)
+__host__ __device__ inline int64_t grid3_index(const Grid3 &g, int i, int j, int k)
+{
+    return (int64_t)i + (int64_t)g.px * (j + (int64_t)g.my * k);
+}
 
 // Kuhn steps: tetrahedron s of a cell steps along axes perm[s][0..2]
 __host__ __device__ inline int kuhn_axis(int s, int q)
@@ -40,14 +69,14 @@ __host__ __device__ inline int kuhn_vertex(int s, int q)
 
 __host__ __device__ inline int64_t dir_offset(const Grid3 &g, int slot)
 {
-    return (int64_t)(slot & 1) + (int64_t)g.mx * (((slot >> 1) & 1) + (int64_t)g.my * ((slot >> 2) & 1));
+    return (int64_t)(slot & 1) + (int64_t)g.px * (((slot >> 1) & 1) + (int64_t)g.my * ((slot >> 2) & 1));
 }
 
 // the same in 32 bits: the solver indexes a sample's arrays (at most nine
 // slots of n nodes, n <= 2^27) with int
 __host__ __device__ inline int dir_offset32(const Grid3 &g, int slot)
 {
-    return (slot & 1) + g.mx * (((slot >> 1) & 1) + g.my * ((slot >> 2) & 1));
+    return (slot & 1) + g.px * (((slot >> 1) & 1) + g.my * ((slot >> 2) & 1));
 }
 
 // Element matrices of tetrahedron s (|e| = hx hy hz / 6):
@@ -91,15 +120,7 @@ __host__ __device__ inline int mg3_hierarchy(const Grid3 &g0, Grid3 *out, int ma
     while (nl < max_levels) {
         const Grid3 &f = out[nl - 1];
         if (f.mx < 3 || f.my < 3 || f.mz < 3 || (f.mx - 1) % 2 || (f.my - 1) % 2 || (f.mz - 1) % 2) break;
-        Grid3 c;
-        c.mx = (f.mx + 1) / 2;
-        c.my = (f.my + 1) / 2;
-        c.mz = (f.mz + 1) / 2;
-        c.n = c.mx * c.my * c.mz;
-        c.hx = 2.0 * f.hx;
-        c.hy = 2.0 * f.hy;
-        c.hz = 2.0 * f.hz;
-        out[nl++] = c;
+        out[nl++] = make_grid3((f.mx + 1) / 2, (f.my + 1) / 2, (f.mz + 1) / 2, 2.0 * f.hx, 2.0 * f.hy, 2.0 * f.hz);
     }
     return nl;
 }
@@ -113,12 +134,14 @@ struct Solve3Args {
     double a, eps, gam;
     double rtol_out, rtol_in;
     int max_iter, max_sweeps;
+    // every array below is in the padded layout of Grid3 (n stored entries
+    // per sample and slot), except v0 and w0
     const double *M3, *lump;      // [8][n], [n] (level)
     const double *A64;            // [S][9][n]
     const TI *Ai;                 // [S][9][n] (the FP64 path: A64)
-    double *v, *w, *b, *y;        // [2][S][n], [2][S][n], [S][n], [S][n]
+    double *v, *w, *b, *y;        // [kVRing][S][n], [2][S][n], [S][n], [S][n]
     TI *r, *u, *wv, *s, *p, *x;   // [S][n] each
-    const double *v0, *w0;        // [n] or null
+    const double *v0, *w0;        // [mx my mz] unpadded, node i + mx (j + my k), or null
     double radius2;
     int S;
     double *q;

@@ -81,6 +81,9 @@ struct Member {
 // 3D multigrid in use for a level (FP32 inner path)
 bool uses_mg3(const mlq_ctx *ctx, const Level &L);
 
+// entries per sample of a level's device arrays (3D: rows padded, Grid3)
+inline int64_t stored(const Level &L) { return L.dim == 3 ? (int64_t)L.g3.n : (int64_t)L.n; }
+
 // multigrid levels below the fine one: m_c = (m_{c-1} + 1) / 2 while m_c >= 3
 int mg_coarse_levels(int m)
 {
@@ -134,6 +137,7 @@ struct mlq_ctx {
     bool capturing = false;
     std::string cuda_error;
     int max_cluster = 8;
+    int occ3d[2][32];   // resident clusters of the 3D solver by precision and cluster size (-1: not asked)
     int smem_optin = 48 * 1024;
     int num_sms = 1;
     // optional per-member timing of the slab kernel (CUDA events on the
@@ -243,19 +247,45 @@ std::vector<Shape> mg_candidates(const mlq_ctx *ctx, const Level &L)
     return out;
 }
 
-// 3D: one sample per cluster, vectors in global memory (bandwidth-bound):
-// the cluster grows while the batch still covers the SMs twice (two CTAs
-// resident per SM) and every CTA keeps a few thousand nodes
-Shape choose_launch_3d(const mlq_ctx *ctx, const Level &L, int64_t S = 0)
+// 3D: one sample per cluster of CS CTAs (256 threads), vectors in global
+// memory (bandwidth-bound); a CTA owns my / CS grid lines of every plane (a
+// CTA may own none).  The largest cluster size whose clusters hold every
+// sample of the batch at once, keeping >= 4096 nodes per CTA; when no
+// size holds them all (the batch fills the GPU in any case), one CTA per
+// sample.  Clusters of 16 occupy 8 x 16 = 128 of the 152 SMs, 12 and 6
+// pack the GPCs more densely.
+int active_3d(mlq_ctx *ctx, bool f32, int cs, int threads)
 {
-    const int64_t lines = (int64_t)L.g3.my * L.g3.mz;
+    int &c = ctx->occ3d[f32 ? 0 : 1][cs & 31];
+    if (threads == 256 && c >= 0) return c;
+    const int a = f32 ? mlq::active_3d_f32(cs, threads) : mlq::active_3d_f64(cs, threads);
+    if (threads == 256) c = a;
+    return a;
+}
+
+Shape choose_launch_3d(mlq_ctx *ctx, const Level &L, int64_t S = 0)
+{
+    static const int kCs[] = {16, 12, 8, 6, 4, 2, 1};
+    const bool f32 = ctx->opt.precision == MLQ_MIXED;
+    int threads = ctx->opt.threads > 0 ? ctx->opt.threads / 32 * 32 : 256;
+    threads = std::min(256, std::max(32, threads));
     int cs = 1;
-    const int64_t slots = 2LL * std::max(ctx->num_sms, 1);
-    while (cs < 16 && (int64_t)(2 * cs) * std::max<int64_t>(S, 1) <= slots && L.n / (2 * cs) >= 4096) cs *= 2;
-    if (ctx->opt.cluster > 0) cs = ctx->opt.cluster;
-    while (cs > 1 && (cs > ctx->max_cluster || cs > lines)) cs /= 2;
-    int threads = ctx->opt.threads > 0 ? ctx->opt.threads / 32 * 32 : 512;
-    threads = std::min(512, std::max(32, threads));
+    if (ctx->opt.cluster > 0) {
+        // the built size at or below the requested one that fits the level
+        for (int c : kCs)
+            if (c <= ctx->opt.cluster && c <= ctx->max_cluster) {
+                cs = c;
+                break;
+            }
+    } else {
+        for (int c : kCs) {
+            if (c > 1 && (c > ctx->max_cluster || L.n / c < 4096)) continue;
+            if (active_3d(ctx, f32, c, threads) >= std::max<int64_t>(S, 1)) {
+                cs = c;
+                break;
+            }
+        }
+    }
     return Shape{cs, threads, false, 0, 0};
 }
 
@@ -269,16 +299,19 @@ bool uses_mg3(const mlq_ctx *ctx, const Level &L)
 Shape choose_launch(mlq_ctx *ctx, const Level &L, int64_t S = 0)
 {
     if (L.dim == 3) return choose_launch_3d(ctx, L, S);
+    // 2D kernels are built for clusters of 1, 2, 4, 8, 16: a request of 6 or
+    // 12 takes the power of two below it
+    const int creq = ctx->opt.cluster == 6 ? 4 : ctx->opt.cluster == 12 ? 8 : ctx->opt.cluster;
     const bool paper = ctx->scheme.ionic == 1;   // the paper's scheme runs in the generic slab kernel
     if (!paper && ctx->opt.precision == MLQ_MIXED && ctx->opt.precond == 1 && ctx->opt.storage != 2) {
-        if (L.tuned_cs > 0 && L.tuned_mg && ctx->opt.cluster <= 0 && ctx->opt.threads <= 0) {
+        if (L.tuned_cs > 0 && L.tuned_mg && creq <= 0 && ctx->opt.threads <= 0) {
             Shape sh{L.tuned_cs, L.tuned_threads, true, (size_t)mlq::mg_plan(L.m, L.tuned_cs).total, L.tuned_npt};
             sh.mg = true;
             return sh;
         }
         std::vector<Shape> cand = mg_candidates(ctx, L);
         for (const Shape &c : cand)
-            if (ctx->opt.cluster <= 0 || c.cs == ctx->opt.cluster) return c;
+            if (creq <= 0 || c.cs == creq) return c;
     }
     if (L.tuned_mg && ctx->opt.precond != 1) {
         // a multigrid tuning does not apply to the Jacobi kernel
@@ -288,15 +321,15 @@ Shape choose_launch(mlq_ctx *ctx, const Level &L, int64_t S = 0)
     const bool allow = ctx->opt.storage != 2;
     // mixed path: the register-resident kernel when a shape fits
     if (ti == 4 && allow && !paper) {
-        if (L.tuned_cs > 0 && !L.tuned_mg && ctx->opt.cluster <= 0 && ctx->opt.threads <= 0) {
+        if (L.tuned_cs > 0 && !L.tuned_mg && creq <= 0 && ctx->opt.threads <= 0) {
             const mlq::RegPlan rp = mlq::reg_plan(L.m, L.tuned_cs);
             return Shape{L.tuned_cs, L.tuned_threads, true, (size_t)rp.total, L.tuned_npt};
         }
         std::vector<Shape> cand = reg_candidates(ctx, L);
-        if (ctx->opt.cluster > 0 || ctx->opt.threads > 0) {
+        if (creq > 0 || ctx->opt.threads > 0) {
             // honour explicit overrides when a register shape matches them
             for (const Shape &c : cand) {
-                if (ctx->opt.cluster > 0 && c.cs != ctx->opt.cluster) continue;
+                if (creq > 0 && c.cs != creq) continue;
                 Shape sh = c;
                 if (ctx->opt.threads > 0) {
                     const mlq::RegPlan rp = mlq::reg_plan(L.m, c.cs);
@@ -336,8 +369,8 @@ Shape choose_launch(mlq_ctx *ctx, const Level &L, int64_t S = 0)
         if (c > L.m) return false;
         return mlq::smem_plan(L.m, c, ti, true).total <= limit;
     };
-    if (ctx->opt.cluster > 0) {
-        sh.cs = ctx->opt.cluster;
+    if (creq > 0) {
+        sh.cs = creq;
         sh.resident = allow && fits(sh.cs);
     } else {
         for (int c = 1; allow && c <= ctx->max_cluster; c *= 2) {
@@ -415,7 +448,7 @@ size_t member_bytes(const mlq_ctx *ctx, const Level &L, int64_t S)
 {
     const bool mixed = ctx->opt.precision == MLQ_MIXED;
     const size_t ti = mixed ? 4 : 8;
-    const size_t sn = (size_t)S * L.n;
+    const size_t sn = (size_t)S * stored(L);
     size_t t = 0;
     auto add = [&](size_t bytes) { t += align_up(bytes, 256); };
     if (L.dim == 3) {
@@ -475,7 +508,7 @@ void member_carve(const mlq_ctx *ctx, const Level &L, Member &mb, char *&cur)
 {
     const bool mixed = ctx->opt.precision == MLQ_MIXED;
     const size_t ti = mixed ? 4 : 8;
-    const size_t sn = (size_t)mb.S * L.n;
+    const size_t sn = (size_t)mb.S * stored(L);
     auto take = [&](size_t bytes) {
         char *p = cur;
         cur += align_up(bytes, 256);
@@ -927,8 +960,8 @@ static int validate_options(const mlq_options *o)
 {
     if (o->precision != MLQ_FP64 && o->precision != MLQ_MIXED) return MLQ_EINVAL;
     if (!(o->rtol > 0.0) || !(o->rtol_inner > 0.0) || o->max_iter < 0 || o->max_sweeps < 1) return MLQ_EINVAL;
-    if (o->cluster != 0 && o->cluster != 1 && o->cluster != 2 && o->cluster != 4 && o->cluster != 8 &&
-        o->cluster != 16)
+    if (o->cluster != 0 && o->cluster != 1 && o->cluster != 2 && o->cluster != 4 && o->cluster != 6 &&
+        o->cluster != 8 && o->cluster != 12 && o->cluster != 16)
         return MLQ_EINVAL;
     if (o->threads != 0 && (o->threads < 64 || o->threads > 512 || o->threads % 32)) return MLQ_EINVAL;
     if (o->storage < 0 || o->storage > 2) return MLQ_EINVAL;
@@ -976,6 +1009,8 @@ int mlq_create(mlq_ctx **out, int device, void *cuda_stream, const mlq_options *
     cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
     ctx->max_cluster = mlq::active_reg_cs16(8, 512, 48 * 1024) > 0 ? 16 : 8;
+    for (auto &row : ctx->occ3d)
+        for (int &c : row) c = -1;
     cudaGetLastError();
     (void)nonportable;
     if (o.cluster > ctx->max_cluster) return fail(MLQ_EUNSUPPORTED);
@@ -1109,20 +1144,15 @@ int mlq_add_level(mlq_ctx *ctx, int level, int dim, const int32_t *dims, const d
             L.Ly = lengths[1];
             L.Lz = lengths[2];
         }
-        mlq::Grid3 &g = L.g3;
-        g.mx = dims[0];
-        g.my = dims[1];
-        g.mz = dims[2];
-        g.n = dims[0] * dims[1] * dims[2];
-        g.hx = L.Lx / (g.mx - 1);
-        g.hy = L.Ly / (g.my - 1);
-        g.hz = L.Lz / (g.mz - 1);
-        L.n = g.n;
+        L.g3 = mlq::make_grid3(dims[0], dims[1], dims[2], L.Lx / (dims[0] - 1), L.Ly / (dims[1] - 1),
+                               L.Lz / (dims[2] - 1));
+        const mlq::Grid3 &g = L.g3;
+        L.n = dims[0] * dims[1] * dims[2];   // nodes; the device arrays hold g.n padded entries
         L.ne = 6 * (g.mx - 1) * (g.my - 1) * (g.mz - 1);
         L.dt = dt;
         L.nsteps = nsteps;
-        MLQ_CUDA(ctx, cudaMalloc(&L.d_M3, sizeof(double) * 8 * (size_t)L.n));
-        MLQ_CUDA(ctx, cudaMalloc(&L.d_lump, sizeof(double) * (size_t)L.n));
+        MLQ_CUDA(ctx, cudaMalloc(&L.d_M3, sizeof(double) * 8 * (size_t)g.n));
+        MLQ_CUDA(ctx, cudaMalloc(&L.d_lump, sizeof(double) * (size_t)g.n));
         MLQ_CUDA(ctx, mlq::launch_level3d_setup(g, L.d_M3, L.d_lump, ctx->stream));
         MLQ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         ctx->launches++;
@@ -1370,12 +1400,25 @@ int mlq_solve_state(mlq_ctx *ctx, int level, int64_t S, const double *xi, double
     // where the kernels leave the state after the last block: the ring kernels
     // (multigrid and 3D) keep v_j in buffer j mod kVRing, the others update v
     // in place; w alternates between two buffers, one per block
-    const size_t SN = (size_t)S * L.n;
+    const size_t SN = (size_t)S * stored(L);
     const bool ring = L.dim == 3 || choose_launch(ctx, L, S).mg;
     const double *vfin = mf.v + (ring ? (size_t)(L.nsteps % mlq::kVRing) * SN : 0);
     const double *wfin = mf.w + (size_t)(L.nsteps & 1) * SN;
-    if ((st = copy_out(ctx, v_out, vfin, SN * 8, ctx->stream)) != MLQ_OK) return st;
-    if ((st = copy_out(ctx, w_out, wfin, SN * 8, ctx->stream)) != MLQ_OK) return st;
+    if (L.dim == 3) {
+        // the real entries of every padded row, S x my x mz rows of mx
+        const mlq::Grid3 &g = L.g3;
+        const size_t rows = (size_t)S * g.my * g.mz;
+        for (int t = 0; t < 2; ++t) {
+            double *dst = t == 0 ? v_out : w_out;
+            const double *src = t == 0 ? vfin : wfin;
+            if (!dst) continue;
+            MLQ_CUDA(ctx, cudaMemcpy2DAsync(dst, sizeof(double) * g.mx, src, sizeof(double) * g.px,
+                                            sizeof(double) * g.mx, rows, cudaMemcpyDefault, ctx->stream));
+        }
+    } else {
+        if ((st = copy_out(ctx, v_out, vfin, SN * 8, ctx->stream)) != MLQ_OK) return st;
+        if ((st = copy_out(ctx, w_out, wfin, SN * 8, ctx->stream)) != MLQ_OK) return st;
+    }
     if ((st = copy_out(ctx, q_out, mf.q, S * 8, ctx->stream)) != MLQ_OK) return st;
     if ((st = copy_out(ctx, status, mf.status, S * 4, ctx->stream)) != MLQ_OK) return st;
     MLQ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -1438,7 +1481,7 @@ bool locate_point(const Level &L, const double *x, int *node, double *w)
     const double lam[4] = {1.0 - t[a0], t[a0] - t[a1], t[a1] - t[a2], t[a2]};
     for (int q = 0; q < 4; ++q) {
         const int msk = mlq::kuhn_vertex(s, q);
-        node[q] = (c[0] + (msk & 1)) + g.mx * ((c[1] + ((msk >> 1) & 1)) + g.my * (c[2] + ((msk >> 2) & 1)));
+        node[q] = (int)mlq::grid3_index(g, c[0] + (msk & 1), c[1] + ((msk >> 1) & 1), c[2] + ((msk >> 2) & 1));
         w[q] = lam[q];
     }
     return true;
