@@ -333,33 +333,55 @@ __device__ __forceinline__ void sweep3(const Band3 &b, int tid, int nt, Ld &&ld,
 }
 
 // ---------------------------------------------------------------------------
-// Quad passes (the FP32 inner solve): four consecutive stored entries
-// (a 16-byte aligned quad of a padded row) per thread and 16-byte loads and
-// stores.  Quad f of a band lies in band-plane k = f / (nj px / 4), at entry
-// 4 (f mod (nj px / 4)) of that band-plane's contiguous range.
+// Vector passes: W consecutive stored entries per thread (a 16-byte aligned
+// vector of a padded row: a quad of FP32 entries, W = 4, or a pair of FP64
+// entries, W = 2) and 16-byte loads and stores.  Vector f of a band lies in
+// band-plane k = f / (nj px / W), at entry W (f mod (nj px / W)) of that
+// band-plane's contiguous range.
 // ---------------------------------------------------------------------------
 
-struct BandQ {
-    int px, plane, j0, nj, Q;   // Q = px / 4 quads per line
-    int cnt;                    // quads in the band
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using V = float4;
+    static constexpr int W = 4;
+};
+template <>
+struct Vec16<double> {
+    using V = double2;
+    static constexpr int W = 2;
 };
 
-__device__ __forceinline__ BandQ bandq(const Grid3 &g, int rank, int cs)
+__device__ __forceinline__ float vel(const float4 &v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
+__device__ __forceinline__ double vel(const double2 &v, int e) { return e == 0 ? v.x : v.y; }
+__device__ __forceinline__ float4 vmakef(const float (&a)[4]) { return make_float4(a[0], a[1], a[2], a[3]); }
+__device__ __forceinline__ double2 vmakef(const double (&a)[2]) { return make_double2(a[0], a[1]); }
+
+template <int W>
+struct BandV {
+    int px, plane, j0, nj, Q;   // Q = px / W vectors per line
+    int cnt;                    // vectors in the band
+};
+
+template <int W>
+__device__ __forceinline__ BandV<W> bandv(const Grid3 &g, int rank, int cs)
 {
-    BandQ b;
+    BandV<W> b;
     b.px = g.px;
     b.plane = g.px * g.my;
     b.j0 = (int)(g.my * rank / cs);
     b.nj = (int)(g.my * (rank + 1) / cs) - b.j0;
-    b.Q = g.px >> 2;
+    b.Q = g.px / W;
     b.cnt = b.nj * b.Q * g.mz;
     return b;
 }
 
-// quad position (qi, j0 + jl, k), advanced by a fixed stride of quads
-struct WalkQ {
+// vector position (qi, j0 + jl, k), advanced by a fixed stride of vectors
+template <int W>
+struct WalkV {
     int qi, jl, k, dq, dj, dk;
-    __device__ void init(const BandQ &b, int f, int stride)
+    __device__ void init(const BandV<W> &b, int f, int stride)
     {
         qi = f % b.Q;
         const int line = f / b.Q;
@@ -370,7 +392,7 @@ struct WalkQ {
         dj = lines % b.nj;
         dk = lines / b.nj;
     }
-    __device__ void next(const BandQ &b)
+    __device__ void next(const BandV<W> &b)
     {
         qi += dq;
         jl += dj;
@@ -384,39 +406,40 @@ struct WalkQ {
             ++k;
         }
     }
-    __device__ int i() const { return qi << 2; }
-    __device__ int j(const BandQ &b) const { return b.j0 + jl; }
-    __device__ int P(const BandQ &b) const { return (qi << 2) + b.px * (b.j0 + jl) + b.plane * k; }
+    __device__ int i() const { return qi * W; }
+    __device__ int j(const BandV<W> &b) const { return b.j0 + jl; }
+    __device__ int P(const BandV<W> &b) const { return qi * W + b.px * (b.j0 + jl) + b.plane * k; }
 };
 
-__device__ __forceinline__ float4 ldq(const float *p) { return __ldcg(reinterpret_cast<const float4 *>(p)); }
-__device__ __forceinline__ void stq(float *p, const float4 &v) { *reinterpret_cast<float4 *>(p) = v; }
-__device__ __forceinline__ float4 zq() { return make_float4(0.f, 0.f, 0.f, 0.f); }
-__device__ __forceinline__ float qel(const float4 &v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
-__device__ __forceinline__ float qdot(const float4 &a, const float4 &b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
-// four FP64 entries at a quad (two 16-byte accesses)
-__device__ __forceinline__ void ldq64(const double *p, double (&v)[4])
-{
-    const double2 a = __ldcg(reinterpret_cast<const double2 *>(p)), b = __ldcg(reinterpret_cast<const double2 *>(p) + 1);
-    v[0] = a.x;
-    v[1] = a.y;
-    v[2] = b.x;
-    v[3] = b.y;
-}
-__device__ __forceinline__ void stq64(double *p, const double (&v)[4])
-{
-    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
-    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
-}
+using BandQ = BandV<4>;
+using WalkQ = WalkV<4>;
+__device__ __forceinline__ BandQ bandq(const Grid3 &g, int rank, int cs) { return bandv<4>(g, rank, cs); }
 
-// For every quad of the band: r = ld(P, wk), then st(P, r); U quads per
+__device__ __forceinline__ float4 ldq(const float *p) { return __ldcg(reinterpret_cast<const float4 *>(p)); }
+__device__ __forceinline__ double2 ldq(const double *p) { return __ldcg(reinterpret_cast<const double2 *>(p)); }
+__device__ __forceinline__ void stq(float *p, const float4 &v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ void stq(double *p, const double2 &v) { *reinterpret_cast<double2 *>(p) = v; }
+__device__ __forceinline__ float4 zq() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ float qel(const float4 &v, int e) { return vel(v, e); }
+__device__ __forceinline__ float qdot(const float4 &a, const float4 &b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
+template <typename V>
+__device__ __forceinline__ V vzero();
+template <>
+__device__ __forceinline__ float4 vzero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+template <>
+__device__ __forceinline__ double2 vzero<double2>() { return make_double2(0.0, 0.0); }
+// read-only data (stencils, masses): the non-coherent path
+__device__ __forceinline__ float4 ldro(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+__device__ __forceinline__ double2 ldro(const double *p) { return __ldg(reinterpret_cast<const double2 *>(p)); }
+
+// For every vector of the band: r = ld(P, wk), then st(P, r); U vectors per
 // thread and round, all loads before the first store.
-template <int U, typename Ld, typename St>
-__device__ __forceinline__ void sweepq(const BandQ &b, int tid, int nt, Ld &&ld, St &&st)
+template <int U, int W, typename Ld, typename St>
+__device__ __forceinline__ void sweepv(const BandV<W> &b, int tid, int nt, Ld &&ld, St &&st)
 {
     if (b.cnt <= 0) return;
-    using R = decltype(ld(0, WalkQ{}));
-    WalkQ wk;
+    using R = decltype(ld(0, WalkV<W>{}));
+    WalkV<W> wk;
     wk.init(b, tid, nt);
     for (int f = tid; f < b.cnt; f += U * nt) {
         R r[U];
@@ -433,100 +456,119 @@ __device__ __forceinline__ void sweepq(const BandQ &b, int tid, int nt, Ld &&ld,
     }
 }
 
-// whether the quads of lanes - 1 and + 1 are the ones just before and after
-// this one in memory (then their loads supply the entries -1 and +4)
+template <int U, typename Ld, typename St>
+__device__ __forceinline__ void sweepq(const BandQ &b, int tid, int nt, Ld &&ld, St &&st)
+{
+    sweepv<U, 4>(b, tid, nt, ld, st);
+}
+
+// whether the vectors of lanes - 1 and + 1 are the ones just before and
+// after this one in memory (then their loads supply the entries -1 and +W)
 struct NbQ {
     bool hp, hn;
 };
 
 // The 15-point passes: a loop over rounds that every lane of a warp runs
 // (the product exchanges row ends between lanes).  A lane past the band's
-// end works on the band's first quad and does not store.
-template <typename Op>
-__device__ __forceinline__ void sweepq15(const BandQ &b, int tid, int nt, Op &&op)
+// end works on the band's first vector and does not store.
+template <int W, typename Op>
+__device__ __forceinline__ void sweepv15(const BandV<W> &b, int tid, int nt, Op &&op)
 {
     if (b.cnt <= 0) return;
     const int lane = tid & 31;
     const int P0 = b.px * b.j0;
-    WalkQ wk;
+    WalkV<W> wk;
     wk.init(b, tid, nt);
     for (int base = 0; base < b.cnt; base += nt) {
         const bool act = base + tid < b.cnt;
         const int P = act ? wk.P(b) : P0;
         const int Pp = __shfl_up_sync(0xffffffffu, P, 1), Pn = __shfl_down_sync(0xffffffffu, P, 1);
         NbQ nb;
-        nb.hp = lane > 0 && Pp == P - 4;
-        nb.hn = lane < 31 && Pn == P + 4;
-        op(P, act, nb);
+        nb.hp = lane > 0 && Pp == P - W;
+        nb.hn = lane < 31 && Pn == P + W;
+        op(P, act, nb, wk);
         wk.next(b);
     }
 }
 
-// (C x) at the quad P..P+3 of one sample's arrays (C [8][n], x [n], FP32):
-// the eight slots at the quad, the seven slots at the quad shifted by -d,
-// and seven rows of x (the quad's own row and the rows at +-y, +-z, +(y+z),
-// -(y+z)), all 16-byte loads.  The neighbours along x are those rows shifted
-// by one entry: entry -1 comes from lane - 1 (entry +4 from lane + 1) when
-// that lane holds the adjacent quad, else from one 4-byte load.  Rows
-// outside the array read as zero (their slots are zero).  xc returns x at
-// the quad.
-__device__ __forceinline__ float4 apply15q(const float *__restrict__ C, int n, int px, int plane, const float *x,
-                                           int P, NbQ nb, float4 &xc)
+template <typename Op>
+__device__ __forceinline__ void sweepq15(const BandQ &b, int tid, int nt, Op &&op)
 {
+    sweepv15<4>(b, tid, nt, op);
+}
+
+// (C x) at the vector P..P+W-1 of one sample's arrays (C [8][n], x [n]):
+// the eight slots at the vector, the seven slots at the vector shifted by
+// -d, and seven rows of x (the vector's own row and the rows at +-y, +-z,
+// +(y+z), -(y+z)), all 16-byte loads.  The neighbours along x are those rows
+// shifted by one entry: entry -1 comes from lane - 1 (entry +W from lane + 1)
+// when that lane holds the adjacent vector, else from one scalar load.  Rows
+// outside the array read as zero (their slots are zero).  xc returns x at
+// the vector.
+template <typename T>
+__device__ __forceinline__ typename Vec16<T>::V apply15v(const T *__restrict__ C, int n, int px, int plane, const T *x,
+                                                        int P, NbQ nb, typename Vec16<T>::V &xc)
+{
+    using V = typename Vec16<T>::V;
+    constexpr int W = Vec16<T>::W;
     const unsigned FULL = 0xffffffffu;
-    auto ldx = [&](int idx) -> float4 { return (idx >= 0 && idx <= n - 4) ? ldq(x + idx) : zq(); };
-    auto ldc = [&](int sl, int idx) -> float4 {
-        return (idx >= 0 && idx <= n - 4) ? __ldg(reinterpret_cast<const float4 *>(C + (size_t)sl * n + idx)) : zq();
-    };
-    const float4 x00 = ldx(P), xp0 = ldx(P + px), xm0 = ldx(P - px), x0p = ldx(P + plane), x0m = ldx(P - plane),
-                 xpp = ldx(P + px + plane), xmm = ldx(P - px - plane);
-    float4 cu[8], cd[8];
+    auto ldx = [&](int idx) -> V { return (idx >= 0 && idx <= n - W) ? ldq(x + idx) : vzero<V>(); };
+    auto ldc = [&](int sl, int idx) -> V { return (idx >= 0 && idx <= n - W) ? ldro(C + (size_t)sl * n + idx) : vzero<V>(); };
+    const V x00 = ldx(P), xp0 = ldx(P + px), xm0 = ldx(P - px), x0p = ldx(P + plane), x0m = ldx(P - plane),
+            xpp = ldx(P + px + plane), xmm = ldx(P - px - plane);
+    V cu[8], cd[8];
 #pragma unroll
     for (int sl = 0; sl < 8; ++sl) cu[sl] = ldc(sl, P);
 #pragma unroll
     for (int sl = 1; sl < 8; ++sl) {
-        // slot sl of the entries P - d .. P + 3 - d; for d with an x step the
-        // aligned quad starts one entry later and entry -1 is fetched below
+        // slot sl of the entries P - d .. P + W - 1 - d; for d with an x step
+        // the aligned vector starts one entry later and entry -1 is fetched below
         const int off = (sl & 1) + px * ((sl >> 1) & 1) + plane * ((sl >> 2) & 1);
         cd[sl] = ldc(sl, P - off + (sl & 1));
     }
     // the x-step slots 1, 3, 5, 7 and their rows: 0 (own), +-y, +-z, +-(y+z)
-    float cprev[4], xprev[4], xnext[4];
+    T cprev[4], xprev[4], xnext[4];
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
         const int sl = 2 * t + 1;
-        const float4 &dn = t == 0 ? x00 : t == 1 ? xm0 : t == 2 ? x0m : xmm;
-        const float4 &up = t == 0 ? x00 : t == 1 ? xp0 : t == 2 ? x0p : xpp;
+        const V &dn = t == 0 ? x00 : t == 1 ? xm0 : t == 2 ? x0m : xmm;
+        const V &up = t == 0 ? x00 : t == 1 ? xp0 : t == 2 ? x0p : xpp;
         const int off = 1 + px * ((sl >> 1) & 1) + plane * ((sl >> 2) & 1);
         const int A = P - off + 1, B = P + off - 1;   // aligned starts of the dn / up rows
-        const float cs = __shfl_up_sync(FULL, cd[sl].w, 1);
-        const float xs = __shfl_up_sync(FULL, dn.w, 1);
-        const float xn = __shfl_down_sync(FULL, up.x, 1);
-        cprev[t] = nb.hp ? cs : (A >= 1 ? __ldg(C + (size_t)sl * n + A - 1) : 0.0f);
-        xprev[t] = nb.hp ? xs : (A >= 1 ? __ldcg(x + A - 1) : 0.0f);
-        xnext[t] = nb.hn ? xn : (B + 4 < n ? __ldcg(x + B + 4) : 0.0f);
+        const T cs = __shfl_up_sync(FULL, vel(cd[sl], W - 1), 1);
+        const T xs = __shfl_up_sync(FULL, vel(dn, W - 1), 1);
+        const T xn = __shfl_down_sync(FULL, vel(up, 0), 1);
+        cprev[t] = nb.hp ? cs : (A >= 1 ? __ldg(C + (size_t)sl * n + A - 1) : (T)0);
+        xprev[t] = nb.hp ? xs : (A >= 1 ? __ldcg(x + A - 1) : (T)0);
+        xnext[t] = nb.hn ? xn : (B + W < n ? __ldcg(x + B + W) : (T)0);
     }
-    float r[4];
+    T r[W];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        float a = qel(cu[0], e) * qel(x00, e);
-        a += qel(cu[2], e) * qel(xp0, e) + qel(cd[2], e) * qel(xm0, e);
-        a += qel(cu[4], e) * qel(x0p, e) + qel(cd[4], e) * qel(x0m, e);
-        a += qel(cu[6], e) * qel(xpp, e) + qel(cd[6], e) * qel(xmm, e);
+    for (int e = 0; e < W; ++e) {
+        T a = vel(cu[0], e) * vel(x00, e);
+        a += vel(cu[2], e) * vel(xp0, e) + vel(cd[2], e) * vel(xm0, e);
+        a += vel(cu[4], e) * vel(x0p, e) + vel(cd[4], e) * vel(x0m, e);
+        a += vel(cu[6], e) * vel(xpp, e) + vel(cd[6], e) * vel(xmm, e);
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             const int sl = 2 * t + 1;
-            const float4 &dn = t == 0 ? x00 : t == 1 ? xm0 : t == 2 ? x0m : xmm;
-            const float4 &up = t == 0 ? x00 : t == 1 ? xp0 : t == 2 ? x0p : xpp;
-            const float xu = e < 3 ? qel(up, e + 1) : xnext[t];
-            const float cdn = e > 0 ? qel(cd[sl], e - 1) : cprev[t];
-            const float xd = e > 0 ? qel(dn, e - 1) : xprev[t];
-            a += qel(cu[sl], e) * xu + cdn * xd;
+            const V &dn = t == 0 ? x00 : t == 1 ? xm0 : t == 2 ? x0m : xmm;
+            const V &up = t == 0 ? x00 : t == 1 ? xp0 : t == 2 ? x0p : xpp;
+            const T xu = e < W - 1 ? vel(up, e + 1) : xnext[t];
+            const T cdn = e > 0 ? vel(cd[sl], e - 1) : cprev[t];
+            const T xd = e > 0 ? vel(dn, e - 1) : xprev[t];
+            a += vel(cu[sl], e) * xu + cdn * xd;
         }
         r[e] = a;
     }
     xc = x00;
-    return make_float4(r[0], r[1], r[2], r[3]);
+    return vmakef(r);
+}
+
+__device__ __forceinline__ float4 apply15q(const float *__restrict__ C, int n, int px, int plane, const float *x,
+                                           int P, NbQ nb, float4 &xc)
+{
+    return apply15v<float>(C, n, px, plane, x, P, nb, xc);
 }
 
 // nodes per thread and round of the scalar streaming passes, and quads per
@@ -557,7 +599,7 @@ __device__ __forceinline__ float4 dinvq(const QLev &L, int P)
 static __device__ __noinline__ double qp_product(QLev L, BandQ b, const float *x, float *w)
 {
     double acc = 0.0;
-    sweepq15(b, threadIdx.x, blockDim.x, [&](int P, bool act, NbQ nb) {
+    sweepq15(b, threadIdx.x, blockDim.x, [&](int P, bool act, NbQ nb, const auto &) {
         float4 xc;
         const float4 ax = apply15q(L.A, L.n, L.px, L.plane, x, P, nb, xc);
         if (act) {
@@ -571,7 +613,7 @@ static __device__ __noinline__ double qp_product(QLev L, BandQ b, const float *x
 // rr = bb - A x
 static __device__ __noinline__ void qp_residual(QLev L, BandQ b, const float *x, const float *bb, float *rr)
 {
-    sweepq15(b, threadIdx.x, blockDim.x, [&](int P, bool act, NbQ nb) {
+    sweepq15(b, threadIdx.x, blockDim.x, [&](int P, bool act, NbQ nb, const auto &) {
         float4 xc;
         const float4 ax = apply15q(L.A, L.n, L.px, L.plane, x, P, nb, xc);
         const float4 r = ldq(bb + P);
@@ -584,7 +626,7 @@ static __device__ __noinline__ void qp_residual(QLev L, BandQ b, const float *x,
 static __device__ __noinline__ double2 qp_smooth(QLev L, BandQ b, float om, const float *x, const float *bb, float *y)
 {
     double s0 = 0.0, s1 = 0.0;
-    sweepq15(b, threadIdx.x, blockDim.x, [&](int P, bool act, NbQ nb) {
+    sweepq15(b, threadIdx.x, blockDim.x, [&](int P, bool act, NbQ nb, const auto &) {
         float4 xc;
         const float4 ax = apply15q(L.A, L.n, L.px, L.plane, x, P, nb, xc);
         const float4 d = dinvq(L, P), r = ldq(bb + P);
@@ -613,68 +655,75 @@ static __device__ __noinline__ void qp_jacobi0(QLev L, BandQ b, float om, const 
 
 // restriction P^T: coarse quad (I..I+3, J, K) of level gq from the fine
 // residual rr of level gf around (2I, 2J, 2K): the fine node plus half of
-// each of its (up to) fourteen edge neighbours; coarse pads get zero
+// each of its (up to) fourteen edge neighbours; coarse pads get zero.  The
+// fine entries 2I - 1 .. 2I + 7 of the seven fine rows the stencil touches
+// come as two 16-byte loads per row and entry -1 from lane - 1; a row off
+// the grid (y or z) reads as zero, an x neighbour off the grid is a zero pad.
 static __device__ __noinline__ void qp_restrict(Grid3 gf, Grid3 gq, BandQ bq, const float *rr, float *out)
 {
-    sweepq<1>(
-        bq, threadIdx.x, blockDim.x,
-        [&](int, const WalkQ &wk) {
-            const int fj = 2 * wk.j(bq), fk = 2 * wk.k;
-            float o[4];
-#pragma unroll 1
-            for (int e = 0; e < 4; ++e) {
-                const int ci = wk.i() + e;
-                const bool real = ci < gq.mx;
-                const int fi = real ? 2 * ci : 0;
-                const int f = fi + gf.px * (fj + gf.my * fk);
-                // branch-free: a missing neighbour loads the centre and
-                // enters with weight 0
-                float v[15], wgt[15];
-                v[0] = __ldcg(rr + f);
+    const int nf = gf.n, pxf = gf.px, planef = gf.px * gf.my;
+    sweepv15<4>(bq, threadIdx.x, blockDim.x, [&](int Q, bool act, NbQ nb, const WalkQ &wk) {
+        const int fj = 2 * wk.j(bq), fk = 2 * wk.k, fx = 8 * wk.qi;
+        // rows (dy, dz): 00, +0, -0, 0+, 0-, ++, --
+        const int dys[7] = {0, 1, -1, 0, 0, 1, -1}, dzs[7] = {0, 0, 0, 1, -1, 1, -1};
+        float4 ra[7], rb[7];
+        int base[7];
 #pragma unroll
-                for (int sl = 1; sl < 8; ++sl) {
-                    const int dx = sl & 1, dy = (sl >> 1) & 1, dz = (sl >> 2) & 1;
-                    const int off = dir_offset32(gf, sl);
-                    const bool up = fi + dx < gf.mx && fj + dy < gf.my && fk + dz < gf.mz;
-                    const bool dn = fi >= dx && fj >= dy && fk >= dz;
-                    v[2 * sl - 1] = __ldcg(rr + (up ? f + off : f));
-                    v[2 * sl] = __ldcg(rr + (dn ? f - off : f));
-                    wgt[2 * sl - 1] = up ? 1.0f : 0.0f;
-                    wgt[2 * sl] = dn ? 1.0f : 0.0f;
-                }
-                float h = 0.0f;
+        for (int t = 0; t < 7; ++t) {
+            const int fy = fj + dys[t], fz = fk + dzs[t];
+            const bool ex = fy >= 0 && fy < gf.my && fz >= 0 && fz < gf.mz;
+            base[t] = ex ? pxf * fy + planef * fz + fx : -1;
+            ra[t] = (ex && base[t] + 4 <= nf) ? ldq(rr + base[t]) : zq();
+            rb[t] = (ex && base[t] + 8 <= nf) ? ldq(rr + base[t] + 4) : zq();
+        }
+        // entry -1 of the rows with a -x neighbour: 00, -0, 0-, --
+        float prev[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                for (int q = 1; q < 15; ++q) h += wgt[q] * v[q];
-                o[e] = real ? v[0] + 0.5f * h : 0.0f;
-            }
-            return make_float4(o[0], o[1], o[2], o[3]);
-        },
-        [&](int Q, const float4 &v) { stq(out + Q, v); });
+        for (int t = 0; t < 7; ++t) {
+            if (t == 1 || t == 3 || t == 5) continue;
+            const float pv = __shfl_up_sync(0xffffffffu, rb[t].w, 1);
+            prev[t] = (wk.qi == 0 || base[t] < 0) ? 0.0f : (nb.hp ? pv : (base[t] >= 1 ? __ldcg(rr + base[t] - 1) : 0.0f));
+        }
+        auto at = [&](int t, int m) -> float {   // entry m (-1 .. 7) of row t
+            return m < 0 ? prev[t] : m < 4 ? qel(ra[t], m) : qel(rb[t], m - 4);
+        };
+        float o[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int m = 2 * e;
+            float h = at(0, m - 1) + at(0, m + 1);
+            h += at(1, m) + at(1, m + 1) + at(2, m) + at(2, m - 1);
+            h += at(3, m) + at(3, m + 1) + at(4, m) + at(4, m - 1);
+            h += at(5, m) + at(5, m + 1) + at(6, m) + at(6, m - 1);
+            o[e] = wk.i() + e < gq.mx ? at(0, m) + 0.5f * h : 0.0f;
+        }
+        if (act) stq(out + Q, make_float4(o[0], o[1], o[2], o[3]));
+    });
 }
 
 // xb = xa + P xq: a fine node of level gc takes the mean of the ends of the
-// coarse edge (level gq) it halves; pads stay zero
+// coarse edge (level gq) it halves; pads stay zero.  The fine quad
+// 4q .. 4q + 3 of line (j, k) reads the coarse entries 2q, 2q + 1 of line
+// (j/2, k/2) and 2q .. 2q + 2 of line ((j+1)/2, (k+1)/2).
 static __device__ __noinline__ void qp_prolong(Grid3 gc, Grid3 gq, BandQ bc, const float *xa, const float *xq, float *xb)
 {
-    sweepq<1>(
+    sweepv<kUQ, 4>(
         bc, threadIdx.x, blockDim.x,
         [&](int P, const WalkQ &wk) {
-            const int j = wk.j(bc), k = wk.k;
+            const int j = wk.j(bc), k = wk.k, i0 = wk.i();
             const float4 x = ldq(xa + P);
-            const int ra = gq.px * ((j >> 1) + gq.my * (k >> 1));
+            const int ra = gq.px * ((j >> 1) + gq.my * (k >> 1)) + 2 * wk.qi;
             const int rb = ra + gq.px * ((j & 1) + gq.my * (k & 1));
+            const float2 a = __ldcg(reinterpret_cast<const float2 *>(xq + ra));
+            const float2 b = __ldcg(reinterpret_cast<const float2 *>(xq + rb));
+            const float b2 = i0 + 3 < gc.mx ? __ldcg(xq + rb + 2) : 0.0f;
+            const float c[4] = {a.x + b.x, a.x + b.y, a.y + b.y, a.y + b2};
             float o[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int i = wk.i() + e;
-                const bool real = i < gc.mx;
-                const int ci = real ? i >> 1 : 0;
-                const int qa = ra + ci, qb = rb + ci + (real ? (i & 1) : 0);
-                o[e] = real ? qel(x, e) + 0.5f * (__ldcg(xq + qa) + __ldcg(xq + qb)) : 0.0f;
-            }
+            for (int e = 0; e < 4; ++e) o[e] = i0 + e < gc.mx ? qel(x, e) + 0.5f * c[e] : 0.0f;
             return make_float4(o[0], o[1], o[2], o[3]);
         },
-        [&](int P, const float4 &x) { stq(xb + P, x); });
+        [&](int P, const float4 &v) { stq(xb + P, v); });
 }
 
 // start of an inner solve: r = sc r, x = p = s = 0, z = dsc D^-1 r (the
@@ -741,11 +790,30 @@ static __device__ __noinline__ double2 qp_update(BandQ b, float ta, float tb, bo
     return make_double2(r2, g);
 }
 
-// FP64 block work: b = M y and r = b - A v (stored in the inner precision);
-// returns the thread's part of (b, b) and (r, r)
+// FP64 block work on pairs of entries (16-byte loads and stores)
+
+using BandP = BandV<2>;
+__device__ __forceinline__ BandP bandp(const Grid3 &g, int rank, int cs) { return bandv<2>(g, rank, cs); }
+
+// two entries of the inner precision at an even index
+__device__ __forceinline__ void st2(float *p, double a, double b) { *reinterpret_cast<float2 *>(p) = make_float2((float)a, (float)b); }
+__device__ __forceinline__ void st2(double *p, double a, double b) { *reinterpret_cast<double2 *>(p) = make_double2(a, b); }
+__device__ __forceinline__ double2 ld2(const float *p)
+{
+    const float2 t = __ldcg(reinterpret_cast<const float2 *>(p));
+    return make_double2(t.x, t.y);
+}
+__device__ __forceinline__ double2 ld2(const double *p) { return __ldcg(reinterpret_cast<const double2 *>(p)); }
+
+// The FP64 15-point products run one entry per thread: they are bound by the
+// FP64 rate (15 DFMA per entry; GB300 issues FP64 at 1/64 of the FP32 rate),
+// and the scalar form measured faster than 16-byte pairs.
+
+// b = M y and r = b - A v (r stored in the inner precision); returns the
+// thread's part of (b, b) and (r, r)
 template <typename TI>
-static __device__ __noinline__ double2 sp_load_rhs(Grid3 G, Band3 B, const double *M3, const double *A64, const double *yb,
-                                            const double *v, double *b, TI *R)
+static __device__ __noinline__ double2 sp_load_rhs(Grid3 G, Band3 B, const double *M3, const double *A64,
+                                                   const double *yb, const double *v, double *b, TI *R)
 {
     double bb = 0.0, rr = 0.0;
     sweep3<1>(
@@ -767,7 +835,8 @@ static __device__ __noinline__ double2 sp_load_rhs(Grid3 G, Band3 B, const doubl
 
 // FP64 refinement residual r = b - A v; returns the thread's part of (r, r)
 template <typename TI>
-static __device__ __noinline__ double sp_residual(Grid3 G, Band3 B, const double *A64, const double *b, const double *v, TI *R)
+static __device__ __noinline__ double sp_residual(Grid3 G, Band3 B, const double *A64, const double *b, const double *v,
+                                                  TI *R)
 {
     double rr = 0.0;
     sweep3<1>(
@@ -777,6 +846,50 @@ static __device__ __noinline__ double sp_residual(Grid3 G, Band3 B, const double
             rr += t * t;
         });
     return rr;
+}
+
+// block start: y = v + dt R(v, w), w' = w + dt eps (v - gam w), and the
+// initial guess extrapolated (order gp) from v, v_-1, v_-2, v_-3 and the
+// buffer of the guess (which holds v_-4)
+static __device__ __noinline__ void sp_block_load(BandP B, double dt, double a, double eps, double gam, int gp,
+                                                  const double *vcur, const double *wcur, const double *vm1,
+                                                  const double *vm2, const double *vm3, double *v, double *yb,
+                                                  double *wnext)
+{
+    sweepv<kU3, 2>(
+        B, threadIdx.x, blockDim.x,
+        [&](int P, const WalkV<2> &) {
+            const double2 vv = ldq(vcur + P), ww = ldq(wcur + P);
+            const double2 z = make_double2(0.0, 0.0);
+            const double2 m1 = gp >= 1 ? ldq(vm1 + P) : z, m2 = gp >= 2 ? ldq(vm2 + P) : z, m3 = gp >= 3 ? ldq(vm3 + P) : z,
+                          m4 = gp >= 4 ? ldq(v + P) : z;
+            Vals<double2, 3> o;
+            // FP64 in both paths: the extrapolated guess amplifies the
+            // rounding noise of an FP32 reaction (see reaction())
+            o.v[0] = make_double2(vv.x + dt * reaction<false>(vv.x, ww.x, a), vv.y + dt * reaction<false>(vv.y, ww.y, a));
+            o.v[1] = make_double2(ww.x + dt * eps * recovery<false>(vv.x, ww.x, gam),
+                                  ww.y + dt * eps * recovery<false>(vv.y, ww.y, gam));
+            o.v[2] = make_double2(extrapolate(gp, vv.x, m1.x, m2.x, m3.x, m4.x), extrapolate(gp, vv.y, m1.y, m2.y, m3.y, m4.y));
+            return o;
+        },
+        [&](int P, const Vals<double2, 3> &o) {
+            stq(yb + P, o.v[0]);
+            stq(wnext + P, o.v[1]);
+            stq(v + P, o.v[2]);
+        });
+}
+
+// v += s x (x in the inner precision)
+template <typename TI>
+static __device__ __noinline__ void sp_update_v(BandP B, double s, const TI *X, double *v)
+{
+    sweepv<kU3, 2>(
+        B, threadIdx.x, blockDim.x,
+        [&](int P, const WalkV<2> &) {
+            const double2 x = ld2(X + P), vv = ldq(v + P);
+            return make_double2(fma(x.x, s, vv.x), fma(x.y, s, vv.y));
+        },
+        [&](int P, const double2 &t) { stq(v + P, t); });
 }
 
 // One sample per cluster of CS CTAs.  256 threads with up to 128 registers
@@ -799,6 +912,7 @@ __global__ void __launch_bounds__(256, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
     const int n = G.n;
     const Band3 B0 = band3(G, rank, CS);
     const BandQ Q0 = bandq(G, rank, CS);
+    const BandP P0 = bandp(G, rank, CS);
     const int tid = threadIdx.x, nt = blockDim.x;
     constexpr bool mixed = sizeof(TI) == 4;
 
@@ -932,24 +1046,7 @@ __global__ void __launch_bounds__(256, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
         const int gp = guess_order(step);
         const double *wcur = wb0 + wpar * SN;
         double *wnext = wb0 + (wpar ^ 1) * SN;
-        sweep3<kU3>(
-            B0, tid, nt,
-            [&](int P, int, int, int) {
-                const double vv = vcur[P], ww = wcur[P];
-                Vals<double, 3> o;
-                // FP64 in both paths: the extrapolated guess amplifies the
-                // rounding noise of an FP32 reaction (see reaction())
-                o.v[0] = vv + dt * reaction<false>(vv, ww, g.a);
-                o.v[1] = ww + dt * g.eps * recovery<false>(vv, ww, g.gam);
-                o.v[2] = extrapolate(gp, vv, gp >= 1 ? vm1[P] : 0.0, gp >= 2 ? vm2[P] : 0.0, gp >= 3 ? vm3[P] : 0.0,
-                                     gp >= 4 ? v[P] : 0.0);
-                return o;
-            },
-            [&](int P, const Vals<double, 3> &o) {
-                yb[P] = o.v[0];
-                wnext[P] = o.v[1];
-                v[P] = o.v[2];
-            });
+        sp_block_load(P0, dt, g.a, g.eps, g.gam, gp, vcur, wcur, vm1, vm2, vm3, v, yb, wnext);
         wpar ^= 1;
         cl.sync();
         {
@@ -1118,9 +1215,7 @@ __global__ void __launch_bounds__(256, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
             }
             total_iters += it;
             if (nonfinite) break;
-            sweep3<kU3>(
-                B0, tid, nt, [&](int P, int, int, int) { return fma((double)X[P], rnorm, v[P]); },
-                [&](int P, double t) { v[P] = t; });
+            sp_update_v<TI>(P0, rnorm, X, v);
             cl.sync();
             if (!mixed) solved = true;
         }
@@ -1135,8 +1230,12 @@ __global__ void __launch_bounds__(256, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
 
     double qacc[1] = {0.0};
     const double *vfin = vring(g.nsteps);   // solution of the last block
-    sweep3<1>(
-        B0, tid, nt, [&](int P, int, int, int) { return g.lump[P] * vfin[P]; },
+    sweepv<1, 2>(
+        P0, tid, nt,
+        [&](int P, const WalkV<2> &) {
+            const double2 m = ldro(g.lump + P), vv = ldq(vfin + P);
+            return m.x * vv.x + m.y * vv.y;
+        },
         [&](int, double t) { qacc[0] += t; });
     cluster_reduce<1, CS>(qacc, wsl, csl, par, [&](double(&t)[1]) { ctl.s0 = t[0]; });
     if (rank == 0 && tid == 0) {
