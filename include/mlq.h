@@ -178,6 +178,29 @@ int mlq_set_model(mlq_ctx *ctx, const mlq_model *model);
 int mlq_add_level(mlq_ctx *ctx, int level, int dim, const int32_t *dims, const double *lengths, double dt,
                   int32_t nsteps);
 
+/* A level on a general tetrahedral mesh (the non-nested hierarchies of
+ * Sec. 5.4, eq. PimpedML): n nodes (xyz host, n x 3), ne tetrahedra (conn
+ * host, ne x 4, 0-based node indices), frames as in mlq_mesh_create (host,
+ * ne x 6: the unit vectors e1, e2 of the fibre plane per tetrahedron, or
+ * NULL = the x and y axes), dt and nsteps as mlq_add_level.  The level takes
+ * mlq_set_kl (phi: ne x K, the modes at the tetrahedra, e.g. moved from
+ * another mesh by mlq_p1_at_points), mlq_set_initial_state (n nodes) or
+ * mlq_set_initial_disk (v = 1 where |x|^2 <= radius^2 over the three
+ * coordinates; radius 0.1 until set), and runs in mlq_solve (the coarse
+ * member of with_coarse is level - 1, structured or general, on the same xi)
+ * and mlq_estimate / mlq_estimate_adaptive: a level difference Y_l =
+ * Q_l - Q_{l-1} between unrelated meshes is eq. PimpedML's with both QoIs the
+ * integral of v(T) on their own mesh.  Its members run the general-mesh
+ * solver (as mlq_mesh_solve_opts: Jacobi-PCG, FP64 or FP32 inside FP64
+ * refinement by the context's precision, rtol, rtol_inner, max_iter,
+ * max_sweeps; cluster requests 6 and 12 take 4 and 8; precond, storage and
+ * threads do not apply).  mlq_solve_state, mlq_set_points, mlq_synthesize,
+ * mlq_autotune and mlq_submit return MLQ_EUNSUPPORTED on such a level; the
+ * paper's time discretization (mlq_set_scheme) is for 2D levels.
+ * MLQ_EINVAL for bad sizes, indices or a degenerate tetrahedron. */
+int mlq_add_level_mesh(mlq_ctx *ctx, int level, int64_t n, const double *xyz, int64_t ne, const int32_t *conn,
+                       const double *frames, double dt, int32_t nsteps);
+
 /* Initial state of a level (host arrays of n nodes; w0 may be NULL = 0).
  * Without this call a level starts from v = 1 where x^2 + y^2 <= radius^2,
  * else 0, w = 0, with radius = 0.1 (mlq_set_initial_disk changes radius). */

@@ -9,6 +9,7 @@
 #include "mlq_aux.cuh"
 #include "mlq_kl_tc.cuh"
 #include "mlq_launch.cuh"
+#include "mlq_mesh_member.h"
 
 #include <algorithm>
 #include <atomic>
@@ -57,6 +58,10 @@ struct Level {
     mlq::Grid3 g3{};
     double Lx = 1.0, Ly = 1.0, Lz = 0.25;
     double *d_M3 = nullptr, *d_lump = nullptr;
+    // general simplicial level (mlq_add_level_mesh): the tetrahedral mesh and
+    // its solver, and the node coordinates for the initial disk
+    mlq_mesh *mesh = nullptr;
+    std::vector<double> xyz_h;
     // point QoIs (mlq_set_points): simplex nodes and barycentric weights
     int npts = 0;
     double u_th = 0.0;
@@ -76,6 +81,7 @@ struct Member {
     mlq::D3 *mgD[mlq::kMgMaxLevels] = {};  // coarse-level mean conductivities
     float *mg3v[mlq::kMg3MaxLevels][4] = {};  // 3D multigrid work vectors xa, xb, rr, bb
     mlq::PointArgs pq{};   // point QoIs of this member (npts = 0: none)
+    mlq::MeshWs mws{};     // general-mesh level: the solver's workspace
 };
 
 // 3D multigrid in use for a level (FP32 inner path)
@@ -83,6 +89,41 @@ bool uses_mg3(const mlq_ctx *ctx, const Level &L);
 
 // entries per sample of a level's device arrays (3D: rows padded, Grid3)
 inline int64_t stored(const Level &L) { return L.dim == 3 ? (int64_t)L.g3.n : (int64_t)L.n; }
+
+// the initial disk v = 1 where |x|^2 <= radius^2 (every coordinate of the
+// node), w = 0, of a general level, uploaded to d_v0
+int upload_mesh_disk(Level &L)
+{
+    const int64_t n = (int64_t)L.xyz_h.size() / 3;
+    std::vector<double> v0((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        const double *x = &L.xyz_h[(size_t)i * 3];
+        v0[(size_t)i] = (x[0] * x[0] + x[1] * x[1] + x[2] * x[2] <= L.radius * L.radius) ? 1.0 : 0.0;
+    }
+    cudaFree(L.d_w0);
+    L.d_w0 = nullptr;
+    if (!L.d_v0 && cudaMalloc(&L.d_v0, sizeof(double) * (size_t)n) != cudaSuccess) return MLQ_ECUDA;
+    if (cudaMemcpy(L.d_v0, v0.data(), sizeof(double) * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess)
+        return MLQ_ECUDA;
+    return MLQ_OK;
+}
+
+// free a level's device arrays and its general mesh; the level is undefined after
+void release_level(Level &L)
+{
+    cudaFree(L.d_phi);
+    cudaFree(L.d_phi_hi);
+    cudaFree(L.d_phi_lo);
+    cudaFree(L.d_theta_mean);
+    cudaFree(L.d_v0);
+    cudaFree(L.d_w0);
+    cudaFree(L.d_M3);
+    cudaFree(L.d_lump);
+    cudaFree(L.d_pt_node);
+    cudaFree(L.d_pt_w);
+    if (L.mesh) mlq_mesh_destroy(L.mesh);
+    L = Level();
+}
 
 // multigrid levels below the fine one: m_c = (m_{c-1} + 1) / 2 while m_c >= 3
 int mg_coarse_levels(int m)
@@ -298,6 +339,7 @@ bool uses_mg3(const mlq_ctx *ctx, const Level &L)
 
 Shape choose_launch(mlq_ctx *ctx, const Level &L, int64_t S = 0)
 {
+    if (L.mesh) return Shape{mlq::mesh_member_cluster(L.mesh, std::max<int64_t>(S, 1), ctx->opt.cluster), 512, false, 0, 0};
     if (L.dim == 3) return choose_launch_3d(ctx, L, S);
     // 2D kernels are built for clusters of 1, 2, 4, 8, 16: a request of 6 or
     // 12 takes the power of two below it
@@ -447,6 +489,7 @@ cudaError_t launch_slab_cs(int cs, const mlq::SolveArgs<TI> &a, int nclusters, i
 size_t member_bytes(const mlq_ctx *ctx, const Level &L, int64_t S)
 {
     const bool mixed = ctx->opt.precision == MLQ_MIXED;
+    if (L.mesh) return mlq::mesh_member_bytes(L.mesh, mixed, S);
     const size_t ti = mixed ? 4 : 8;
     const size_t sn = (size_t)S * stored(L);
     size_t t = 0;
@@ -507,6 +550,13 @@ size_t member_bytes(const mlq_ctx *ctx, const Level &L, int64_t S)
 void member_carve(const mlq_ctx *ctx, const Level &L, Member &mb, char *&cur)
 {
     const bool mixed = ctx->opt.precision == MLQ_MIXED;
+    if (L.mesh) {
+        mb.mws = mlq::mesh_member_carve(L.mesh, mixed, mb.S, cur);
+        mb.q = mb.mws.q;
+        mb.iters = mb.mws.iters;
+        mb.status = mb.mws.status;
+        return;
+    }
     const size_t ti = mixed ? 4 : 8;
     const size_t sn = (size_t)mb.S * stored(L);
     auto take = [&](size_t bytes) {
@@ -714,9 +764,32 @@ int launch_member3d_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream
     return MLQ_OK;
 }
 
+// general-mesh member: KL synthesis and CSR assembly, then the block loop
+// of the general-mesh solver (Jacobi-PCG, FP64 or FP32 inside FP64
+// refinement by the context's precision)
+int launch_member_mesh(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream_t st, int slot, int phase)
+{
+    const int cs = mlq::mesh_member_cluster(L.mesh, mb.S, ctx->opt.cluster);
+    const bool timed = ctx->profile && slot >= 0 && slot < kStreams && (phase & kSolve);
+    const unsigned evf = ctx->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if (phase & kSetup) {
+        MLQ_CUDA(ctx, mlq::mesh_member_launch(L.mesh, ctx->model, ctx->opt, L.dt, L.nsteps, L.d_v0, L.d_w0, mb.S, mb.d_xi,
+                                              mb.mws, cs, st, true, false));
+        ctx->launches += ctx->opt.precision == MLQ_MIXED ? 3 : 2;
+    }
+    if (!(phase & kSolve)) return MLQ_OK;
+    if (timed) MLQ_CUDA(ctx, cudaEventRecordWithFlags(ctx->ev_t0[slot], st, evf));
+    MLQ_CUDA(ctx, mlq::mesh_member_launch(L.mesh, ctx->model, ctx->opt, L.dt, L.nsteps, L.d_v0, L.d_w0, mb.S, mb.d_xi,
+                                          mb.mws, cs, st, false, true));
+    if (timed) MLQ_CUDA(ctx, cudaEventRecordWithFlags(ctx->ev_t1[slot], st, evf));
+    ctx->launches++;
+    return MLQ_OK;
+}
+
 template <typename TI>
 int launch_member_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream_t st, int slot, int phase)
 {
+    if (L.mesh) return launch_member_mesh(ctx, L, mb, st, slot, phase);
     if (L.dim == 3) return launch_member3d_t<TI>(ctx, L, mb, st, slot, phase);
     const bool mixed = sizeof(TI) == 4;
     // K1: KL synthesis (theta -> cos 2t, sin 2t)
@@ -869,7 +942,8 @@ int check_err(mlq_ctx *ctx)
 int check_level(const mlq_ctx *ctx, int level)
 {
     if (level < 0 || level >= kMaxLevels || !ctx->levels[level].defined) return MLQ_EINVAL;
-    if (!ctx->levels[level].d_phi) return MLQ_EINVAL;
+    const Level &L = ctx->levels[level];
+    if (L.mesh ? L.K < 1 : !L.d_phi) return MLQ_EINVAL;
     return MLQ_OK;
 }
 
@@ -1041,18 +1115,7 @@ int mlq_destroy(mlq_ctx *ctx)
     cudaFree(ctx->d_err);
     if (ctx->h_sums) cudaFreeHost(ctx->h_sums);
     if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
-    for (auto &L : ctx->levels) {
-        cudaFree(L.d_phi_hi);
-        cudaFree(L.d_phi_lo);
-        cudaFree(L.d_phi);
-        cudaFree(L.d_theta_mean);
-        cudaFree(L.d_v0);
-        cudaFree(L.d_w0);
-        cudaFree(L.d_M3);
-        cudaFree(L.d_lump);
-        cudaFree(L.d_pt_node);
-        cudaFree(L.d_pt_w);
-    }
+    for (auto &L : ctx->levels) release_level(L);
     cudaFree(ctx->ws);
     delete ctx;
     return MLQ_OK;
@@ -1126,17 +1189,7 @@ int mlq_add_level(mlq_ctx *ctx, int level, int dim, const int32_t *dims, const d
     MLQ_CUDA(ctx, cudaSetDevice(ctx->device));
     ctx->generation++;
     Level &L = ctx->levels[level];
-    cudaFree(L.d_phi);
-    cudaFree(L.d_phi_hi);
-    cudaFree(L.d_phi_lo);
-    cudaFree(L.d_theta_mean);
-    cudaFree(L.d_v0);
-    cudaFree(L.d_w0);
-    cudaFree(L.d_M3);
-    cudaFree(L.d_lump);
-    cudaFree(L.d_pt_node);
-    cudaFree(L.d_pt_w);
-    L = Level();
+    release_level(L);
     if (dim == 3) {
         L.dim = 3;
         if (lengths) {
@@ -1172,6 +1225,36 @@ int mlq_add_level(mlq_ctx *ctx, int level, int dim, const int32_t *dims, const d
     return MLQ_OK;
 }
 
+int mlq_add_level_mesh(mlq_ctx *ctx, int level, int64_t n, const double *xyz, int64_t ne, const int32_t *conn,
+                       const double *frames, double dt, int32_t nsteps)
+{
+    MLQ_GUARD(ctx);
+    if (!ctx || !xyz || !conn || level < 0 || level >= kMaxLevels) return MLQ_EINVAL;
+    if (!(dt > 0.0) || nsteps < 0 || n < 4 || ne < 1 || n > ((int64_t)1 << 27)) return MLQ_EINVAL;
+    if (ctx->scheme.ionic == 1) return MLQ_EUNSUPPORTED;   // the paper's scheme runs on 2D levels only
+    MLQ_CUDA(ctx, cudaSetDevice(ctx->device));
+    mlq_mesh *mesh = nullptr;
+    const int st = mlq_mesh_create(&mesh, ctx->device, n, xyz, ne, conn, frames);
+    if (st != MLQ_OK) return st;
+    ctx->generation++;
+    Level &L = ctx->levels[level];
+    release_level(L);
+    L.dim = 3;
+    L.mesh = mesh;
+    L.n = (int)n;
+    L.ne = (int)ne;
+    L.dt = dt;
+    L.nsteps = nsteps;
+    L.xyz_h.assign(xyz, xyz + (size_t)n * 3);
+    const int su = upload_mesh_disk(L);
+    if (su != MLQ_OK) {
+        release_level(L);
+        return su;
+    }
+    L.defined = true;
+    return MLQ_OK;
+}
+
 int mlq_set_initial_state(mlq_ctx *ctx, int level, const double *v0, const double *w0)
 {
     MLQ_GUARD(ctx);
@@ -1202,6 +1285,10 @@ int mlq_set_initial_disk(mlq_ctx *ctx, int level, double radius)
     cudaFree(L.d_w0);
     L.d_v0 = L.d_w0 = nullptr;
     L.radius = radius;
+    if (L.mesh) {
+        MLQ_CUDA(ctx, cudaSetDevice(ctx->device));
+        return upload_mesh_disk(L);
+    }
     return MLQ_OK;
 }
 
@@ -1213,6 +1300,16 @@ int mlq_set_kl(mlq_ctx *ctx, int level, int K, const double *phi, const double *
     ctx->generation++;
     Level &L = ctx->levels[level];
     MLQ_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (L.mesh) {
+        // the general mesh's table (host copies: phi and theta_mean may be device pointers)
+        std::vector<double> ph((size_t)L.ne * K), tm(theta_mean ? (size_t)L.ne : 0);
+        MLQ_CUDA(ctx, cudaMemcpy(ph.data(), phi, sizeof(double) * ph.size(), cudaMemcpyDefault));
+        if (theta_mean) MLQ_CUDA(ctx, cudaMemcpy(tm.data(), theta_mean, sizeof(double) * tm.size(), cudaMemcpyDefault));
+        const int st = mlq_mesh_set_kl(L.mesh, K, ph.data(), theta_mean ? tm.data() : nullptr);
+        if (st != MLQ_OK) return st;
+        L.K = K;
+        return MLQ_OK;
+    }
     cudaFree(L.d_phi);
     cudaFree(L.d_theta_mean);
     L.d_phi = L.d_theta_mean = nullptr;
@@ -1257,6 +1354,7 @@ int mlq_synthesize(mlq_ctx *ctx, int level, int64_t S, const double *xi, double 
     MLQ_GUARD(ctx);
     if (!ctx || !xi || !cs2_out || S < 1 || S > 65535) return MLQ_EINVAL;
     if (check_level(ctx, level) != MLQ_OK) return MLQ_EINVAL;
+    if (ctx->levels[level].mesh) return MLQ_EUNSUPPORTED;
     MLQ_CUDA(ctx, cudaSetDevice(ctx->device));
     const Level &L = ctx->levels[level];
     const size_t out_b = align_up((size_t)S * L.ne * 16, 256), xi_b = align_up((size_t)S * L.K * 8, 256);
@@ -1369,6 +1467,7 @@ int mlq_solve_state(mlq_ctx *ctx, int level, int64_t S, const double *xi, double
     MLQ_GUARD(ctx);
     if (!ctx || !xi || S < 0 || S > 65535) return MLQ_EINVAL;
     if (check_level(ctx, level) != MLQ_OK) return MLQ_EINVAL;
+    if (ctx->levels[level].mesh) return MLQ_EUNSUPPORTED;
     if (S == 0) return MLQ_OK;
     MLQ_CUDA(ctx, cudaSetDevice(ctx->device));
     ctx->nmembers = 0;
@@ -1496,6 +1595,7 @@ int mlq_set_points(mlq_ctx *ctx, int level, int np, const double *pts, double u_
     MLQ_GUARD(ctx);
     if (!ctx || level < 0 || level >= kMaxLevels || !ctx->levels[level].defined) return MLQ_EINVAL;
     if (np < 0 || np > mlq::kMaxPoints || (np > 0 && !pts) || !std::isfinite(u_th)) return MLQ_EINVAL;
+    if (ctx->levels[level].mesh) return MLQ_EUNSUPPORTED;
     Level &L = ctx->levels[level];
     std::vector<int> nd(4 * (size_t)std::max(np, 1));
     std::vector<double> wt(4 * (size_t)std::max(np, 1));
@@ -2574,6 +2674,7 @@ try {
     {
         MLQ_GUARD(ctx);
         if (check_level(ctx, req->level) != MLQ_OK || ctx->levels[req->level].K < 1) return MLQ_EINVAL;
+        if (ctx->levels[req->level].mesh) return MLQ_EUNSUPPORTED;
         r->K = ctx->levels[req->level].K;
         if (!ctx->server.load()) {
             Server *sv = serve_create(ctx);

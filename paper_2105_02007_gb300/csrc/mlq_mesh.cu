@@ -15,6 +15,7 @@
 // refinement, with no host synchronisation inside the solve.
 #include "mlq.h"
 #include "mlq_launch.cuh"
+#include "mlq_mesh_member.h"
 #include "mlq_mesh_solver.cuh"
 
 #include <cuda_runtime.h>
@@ -202,20 +203,109 @@ mlq::MeshArgs<TI> mesh_args(const mlq_mesh *m, const mlq_model *model, const mlq
 }
 
 template <typename TI>
-cudaError_t launch_mesh(int cs, const mlq::MeshArgs<TI> &a)
+cudaError_t launch_mesh(int cs, const mlq::MeshArgs<TI> &a, cudaStream_t st)
 {
     constexpr int threads = 512;
     switch (cs) {
-    case 1: return mlq::cluster_launch<1>(mlq::mesh_slab_kernel<TI, 1>, a.S, threads, 0, nullptr, a);
-    case 2: return mlq::cluster_launch<2>(mlq::mesh_slab_kernel<TI, 2>, a.S, threads, 0, nullptr, a);
-    case 4: return mlq::cluster_launch<4>(mlq::mesh_slab_kernel<TI, 4>, a.S, threads, 0, nullptr, a);
-    case 8: return mlq::cluster_launch<8>(mlq::mesh_slab_kernel<TI, 8>, a.S, threads, 0, nullptr, a);
-    case 16: return mlq::cluster_launch<16>(mlq::mesh_slab_kernel<TI, 16>, a.S, threads, 0, nullptr, a);
+    case 1: return mlq::cluster_launch<1>(mlq::mesh_slab_kernel<TI, 1>, a.S, threads, 0, st, a);
+    case 2: return mlq::cluster_launch<2>(mlq::mesh_slab_kernel<TI, 2>, a.S, threads, 0, st, a);
+    case 4: return mlq::cluster_launch<4>(mlq::mesh_slab_kernel<TI, 4>, a.S, threads, 0, st, a);
+    case 8: return mlq::cluster_launch<8>(mlq::mesh_slab_kernel<TI, 8>, a.S, threads, 0, st, a);
+    case 16: return mlq::cluster_launch<16>(mlq::mesh_slab_kernel<TI, 16>, a.S, threads, 0, st, a);
     default: return cudaErrorInvalidValue;
     }
 }
 
+size_t align256(size_t b) { return (std::max<size_t>(b, 8) + 255) / 256 * 256; }
+
 }  // namespace
+
+namespace mlq {
+
+int64_t mesh_nodes(const mlq_mesh *m) { return m->n; }
+int64_t mesh_elems(const mlq_mesh *m) { return m->ne; }
+int mesh_modes(const mlq_mesh *m) { return m->K; }
+
+size_t mesh_member_bytes(const mlq_mesh *m, bool mixed, int64_t S)
+{
+    const size_t sn = (size_t)S * m->n, ti = mixed ? 4 : 8;
+    size_t t = align256((size_t)S * m->ne * 16) + align256((size_t)S * m->nnz * 8);
+    if (mixed) t += align256((size_t)S * m->nnz * 4);
+    t += 4 * align256(sn * 8) + 7 * align256(sn * ti);
+    t += align256((size_t)S * 8) + 2 * align256((size_t)S * 4);
+    return t;
+}
+
+MeshWs mesh_member_carve(const mlq_mesh *m, bool mixed, int64_t S, char *&base)
+{
+    const size_t sn = (size_t)S * m->n, ti = mixed ? 4 : 8;
+    auto take = [&](size_t bytes) {
+        char *p = base;
+        base += align256(bytes);
+        return (void *)p;
+    };
+    MeshWs w;
+    w.cs2 = (double *)take((size_t)S * m->ne * 16);
+    w.aval = (double *)take((size_t)S * m->nnz * 8);
+    w.a32 = mixed ? (float *)take((size_t)S * m->nnz * 4) : nullptr;
+    w.v = (double *)take(sn * 8);
+    w.w = (double *)take(sn * 8);
+    w.b = (double *)take(sn * 8);
+    w.y = (double *)take(sn * 8);
+    for (void *&p : w.vec) p = take(sn * ti);
+    w.q = (double *)take((size_t)S * 8);
+    w.iters = (int32_t *)take((size_t)S * 4);
+    w.status = (int32_t *)take((size_t)S * 4);
+    return w;
+}
+
+// one sample per cluster; the cluster grows while the batch still fills
+// the SMs twice over and every CTA keeps a few thousand rows
+int mesh_member_cluster(const mlq_mesh *m, int64_t S, int request)
+{
+    int nsm = 1;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device);
+    int cs = 1;
+    while (cs < 16 && (int64_t)(2 * cs) * S <= 2LL * nsm && m->n / (2 * cs) >= 4096) cs *= 2;
+    if (request > 0) {
+        cs = 1;
+        while (cs * 2 <= std::min(request, 16)) cs *= 2;
+    }
+    while (cs > 1 && m->n / cs < 64) cs /= 2;
+    return cs;
+}
+
+cudaError_t mesh_member_launch(const mlq_mesh *m, const mlq_model &model, const mlq_options &opt, double dt,
+                               int nsteps, const double *d_v0, const double *d_w0, int64_t S, const double *d_xi,
+                               const MeshWs &ws, int cs, cudaStream_t st, bool setup, bool solve)
+{
+    if (S <= 0) return cudaSuccess;
+    const bool mixed = opt.precision == MLQ_MIXED;
+    const int64_t ne = m->ne, nnz = m->nnz;
+    if (setup) {
+        const dim3 ge((unsigned)((ne + kThreads - 1) / kThreads), (unsigned)S);
+        const dim3 gz((unsigned)((nnz + kThreads - 1) / kThreads), (unsigned)S);
+        synth_kernel<<<ge, kThreads, 0, st>>>(m->phi, m->theta_mean, d_xi, m->K, ne, (int)S, ws.cs2);
+        assemble_kernel<<<gz, kThreads, 0, st>>>(nnz, (int)S, m->cstart, m->centry, m->geo, m->frames, ws.cs2, ne,
+                                                 model.s_l, model.s_t, dt, m->mval, ws.aval);
+        if (mixed)
+            to_f32_kernel<<<(unsigned)((S * nnz + kThreads - 1) / kThreads), kThreads, 0, st>>>(S * nnz, ws.aval,
+                                                                                               ws.a32);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (!solve) return cudaSuccess;
+    if (mixed) {
+        const mlq::MeshArgs<float> a = mesh_args<float>(m, &model, opt, dt, nsteps, S, ws.aval, ws.a32, d_v0, d_w0, ws.v,
+                                                        ws.w, ws.b, ws.y, ws.vec, ws.q, ws.iters, ws.status);
+        return launch_mesh<float>(cs, a, st);
+    }
+    const mlq::MeshArgs<double> a = mesh_args<double>(m, &model, opt, dt, nsteps, S, ws.aval, ws.aval, d_v0, d_w0, ws.v,
+                                                      ws.w, ws.b, ws.y, ws.vec, ws.q, ws.iters, ws.status);
+    return launch_mesh<double>(cs, a, st);
+}
+
+}  // namespace mlq
 
 extern "C" {
 
@@ -346,74 +436,35 @@ int mlq_mesh_solve_opts(mlq_mesh *m, const mlq_model *model, const mlq_options *
     if (m->K > 0 && !xi) return MLQ_EINVAL;
     if (cudaSetDevice(m->device) != cudaSuccess) return MLQ_ECUDA;
     const bool mixed = opt->precision == MLQ_MIXED;
-    const int64_t n = m->n, ne = m->ne, nnz = m->nnz, sn = S * n;
-    const size_t ti = mixed ? 4 : 8;
-    std::vector<void *> allocs;
-    auto alloc = [&](size_t bytes) -> void * {
-        void *p = nullptr;
-        if (cudaMalloc(&p, std::max<size_t>(bytes, 8)) != cudaSuccess) {
-            cudaGetLastError();
-            return nullptr;
-        }
-        allocs.push_back(p);
-        return p;
-    };
-    auto release = [&]() {
-        for (void *p : allocs) cudaFree(p);
-    };
-    double *cs2 = (double *)alloc((size_t)S * ne * 16), *aval = (double *)alloc((size_t)S * nnz * 8);
-    float *a32 = mixed ? (float *)alloc((size_t)S * nnz * 4) : nullptr;
-    double *v = (double *)alloc(sn * 8), *w = (double *)alloc(sn * 8), *b = (double *)alloc(sn * 8),
-           *y = (double *)alloc(sn * 8);
-    void *vec[7];
-    for (void *&p : vec) p = alloc(sn * ti);
-    double *q = (double *)alloc((size_t)S * 8);
-    int32_t *it = (int32_t *)alloc((size_t)S * 4), *st = (int32_t *)alloc((size_t)S * 4);
-    double *xi_d = (double *)alloc((size_t)S * std::max(m->K, 1) * 8);
-    double *v0_d = (double *)alloc((size_t)n * 8), *w0_d = w0 ? (double *)alloc((size_t)n * 8) : nullptr;
-    bool ok = cs2 && aval && (!mixed || a32) && v && w && b && y && q && it && st && xi_d && v0_d && (!w0 || w0_d);
-    for (void *p : vec) ok = ok && p;
-    if (!ok) {
-        release();
+    const int64_t n = m->n;
+    const size_t ws_b = mlq::mesh_member_bytes(m, mixed, S);
+    const size_t in_b = align256((size_t)S * std::max(m->K, 1) * 8) + 2 * align256((size_t)n * 8);
+    char *blk = nullptr;
+    if (cudaMalloc(&blk, ws_b + in_b) != cudaSuccess) {
+        cudaGetLastError();
         return MLQ_ENOMEM;
     }
+    char *cur = blk;
+    const mlq::MeshWs ws = mlq::mesh_member_carve(m, mixed, S, cur);
+    double *xi_d = (double *)cur;
+    cur += align256((size_t)S * std::max(m->K, 1) * 8);
+    double *v0_d = (double *)cur;
+    cur += align256((size_t)n * 8);
+    double *w0_d = w0 ? (double *)cur : nullptr;
+    bool ok = true;
     auto chk = [&](cudaError_t e) { ok = ok && e == cudaSuccess; };
     if (m->K > 0) chk(cudaMemcpy(xi_d, xi, (size_t)S * m->K * 8, cudaMemcpyHostToDevice));
     chk(cudaMemcpy(v0_d, v0, (size_t)n * 8, cudaMemcpyHostToDevice));
     if (w0) chk(cudaMemcpy(w0_d, w0, (size_t)n * 8, cudaMemcpyHostToDevice));
-    const dim3 ge((unsigned)((ne + kThreads - 1) / kThreads), (unsigned)S);
-    const dim3 gz((unsigned)((nnz + kThreads - 1) / kThreads), (unsigned)S);
-    synth_kernel<<<ge, kThreads>>>(m->phi, m->theta_mean, xi_d, m->K, ne, (int)S, cs2);
-    assemble_kernel<<<gz, kThreads>>>(nnz, (int)S, m->cstart, m->centry, m->geo, m->frames, cs2, ne, model->s_l,
-                                      model->s_t, dt, m->mval, aval);
-    if (mixed) to_f32_kernel<<<(unsigned)((S * nnz + kThreads - 1) / kThreads), kThreads>>>(S * nnz, aval, a32);
-    chk(cudaGetLastError());
-    // launch shape: one sample per cluster; the cluster grows while the batch
-    // still fills the SMs twice over and every CTA keeps a few thousand rows
-    int nsm = 1;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device);
-    int cs = 1;
-    while (cs < 16 && (int64_t)(2 * cs) * S <= 2LL * nsm && n / (2 * cs) >= 4096) cs *= 2;
-    if (opt->cluster > 0) cs = opt->cluster;
-    while (cs > 1 && n / cs < 64) cs /= 2;
-    cudaError_t le = cudaSuccess;
     if (ok) {
-        if (mixed) {
-            mlq::MeshArgs<float> a = mesh_args<float>(m, model, *opt, dt, nsteps, S, aval, a32, v0_d, w0_d, v, w, b,
-                                                      y, vec, q, it, st);
-            le = launch_mesh<float>(cs, a);
-        } else {
-            mlq::MeshArgs<double> a = mesh_args<double>(m, model, *opt, dt, nsteps, S, aval, aval, v0_d, w0_d, v, w,
-                                                        b, y, vec, q, it, st);
-            le = launch_mesh<double>(cs, a);
-        }
-        chk(le);
-        chk(cudaMemcpy(q_out, q, (size_t)S * 8, cudaMemcpyDeviceToHost));
-        if (status) chk(cudaMemcpy(status, st, (size_t)S * 4, cudaMemcpyDeviceToHost));
-        if (iters) chk(cudaMemcpy(iters, it, (size_t)S * 4, cudaMemcpyDeviceToHost));
+        const int cs = mlq::mesh_member_cluster(m, S, opt->cluster);
+        chk(mlq::mesh_member_launch(m, *model, *opt, dt, nsteps, v0_d, w0_d, S, xi_d, ws, cs, nullptr));
+        chk(cudaMemcpy(q_out, ws.q, (size_t)S * 8, cudaMemcpyDeviceToHost));
+        if (status) chk(cudaMemcpy(status, ws.status, (size_t)S * 4, cudaMemcpyDeviceToHost));
+        if (iters) chk(cudaMemcpy(iters, ws.iters, (size_t)S * 4, cudaMemcpyDeviceToHost));
         chk(cudaDeviceSynchronize());
     }
-    release();
+    cudaFree(blk);
     return ok ? MLQ_OK : MLQ_ECUDA;
 }
 

@@ -1,0 +1,42 @@
+// mlq_mesh_member.h -- a general-mesh level as a member of the library's
+// solves and estimates (host side, implemented in mlq_mesh.cu): the device
+// workspace of S samples carved from a caller-owned block, and the
+// stream-ordered launch of the sample's KL synthesis, CSR assembly and block
+// loop (no allocation, no host synchronisation: the calls can be captured
+// into a CUDA graph).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mlq.h"
+
+namespace mlq {
+
+struct MeshWs {
+    double *cs2 = nullptr, *aval = nullptr, *v = nullptr, *w = nullptr, *b = nullptr, *y = nullptr, *q = nullptr;
+    float *a32 = nullptr;
+    void *vec[7] = {};
+    int32_t *iters = nullptr, *status = nullptr;
+};
+
+int64_t mesh_nodes(const mlq_mesh *m);
+int64_t mesh_elems(const mlq_mesh *m);
+int mesh_modes(const mlq_mesh *m);
+
+// bytes of the workspace of S samples (each piece 256-byte aligned)
+size_t mesh_member_bytes(const mlq_mesh *m, bool mixed, int64_t S);
+// the pieces of that workspace starting at base; base advances past it
+MeshWs mesh_member_carve(const mlq_mesh *m, bool mixed, int64_t S, char *&base);
+// cluster size of the block loop for S samples (request 0 = chosen; a
+// request that is not built takes the power of two below it)
+int mesh_member_cluster(const mlq_mesh *m, int64_t S, int request);
+// enqueue the member on stream st: xi (S x K), v0 and w0 (n; w0 may be
+// null) are device pointers; results in ws.q, ws.iters, ws.status.  setup:
+// the KL synthesis and CSR assembly; solve: the block loop (one launch)
+cudaError_t mesh_member_launch(const mlq_mesh *m, const mlq_model &model, const mlq_options &opt, double dt,
+                               int nsteps, const double *d_v0, const double *d_w0, int64_t S, const double *d_xi,
+                               const MeshWs &ws, int cs, cudaStream_t st, bool setup = true, bool solve = true);
+
+}  // namespace mlq

@@ -22,7 +22,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 MLQ_FP64, MLQ_MIXED = 0, 1
-MLQ_EINVAL, MLQ_ENOMEM = -1, -2
+MLQ_EINVAL, MLQ_ENOMEM, MLQ_EUNSUPPORTED = -1, -2, -6
 S_CONVERGED, S_MAXITER, S_NONFINITE, S_CANCELLED = 0, 1, 2, 3
 
 
@@ -73,6 +73,7 @@ _lib.mlq_destroy.argtypes = [_vp]
 _lib.mlq_set_options.argtypes = [_vp, ctypes.POINTER(Options)]
 _lib.mlq_set_model.argtypes = [_vp, ctypes.POINTER(Model)]
 _lib.mlq_add_level.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_double, ctypes.c_int32]
+_lib.mlq_add_level_mesh.argtypes = [_vp, ctypes.c_int, _i64, _vp, _i64, _vp, _vp, ctypes.c_double, ctypes.c_int32]
 _lib.mlq_set_initial_state.argtypes = [_vp, ctypes.c_int, _vp, _vp]
 _lib.mlq_set_initial_disk.argtypes = [_vp, ctypes.c_int, ctypes.c_double]
 _lib.mlq_set_kl.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp]
@@ -124,7 +125,7 @@ _lib.mlq_last_cuda_error.restype = ctypes.c_char_p
 _lib.mlq_last_cuda_error.argtypes = [_vp]
 
 EXPORTED = ["mlq_default_options", "mlq_default_model", "mlq_default_scheme", "mlq_set_scheme", "mlq_create", "mlq_destroy", "mlq_set_options",
-            "mlq_set_model", "mlq_add_level", "mlq_set_initial_state", "mlq_set_initial_disk", "mlq_set_kl",
+            "mlq_set_model", "mlq_add_level", "mlq_add_level_mesh", "mlq_set_initial_state", "mlq_set_initial_disk", "mlq_set_kl",
             "mlq_build_kl", "mlq_centroid_table", "mlq_build_kl_mesh", "mlq_p1_at_points", "mlq_p1_at_points_gpu", "mlq_mesh_create",
             "mlq_mesh_destroy", "mlq_mesh_set_kl", "mlq_mesh_solve", "mlq_mesh_solve_opts", "mlq_mlmc_allocation", "mlq_mlmc_combine", "mlq_pimped_ml_combine", "mlq_estimate_adaptive", "mlq_field_prolong", "mlq_field_norms", "mlq_solve", "mlq_solve_state", "mlq_set_points", "mlq_solve_points", "mlq_trace_prolong",
             "mlq_time_norms", "mlq_estimate", "mlq_workspace_bytes",
@@ -421,6 +422,16 @@ class Context:
                "mlq_add_level", self._h)
         n, ne = _counts(dim, dims)
         self.levels[level] = dict(m=m, dt=dt, nsteps=nsteps, n=n, ne=ne)
+
+    def add_level_mesh(self, level: int, xyz: np.ndarray, conn: np.ndarray, dt: float, nsteps: int, frames=None):
+        """Level on a general tetrahedral mesh (xyz n x 3, conn ne x 4, optional
+        fibre frames ne x 6): a level of mlq_solve / mlq_estimate whose members
+        run the general-mesh solver."""
+        x, px, c, pc = _mesh_args(xyz, conn)
+        fr, pf = (None, None) if frames is None else _host(frames, np.float64)
+        _check(_lib.mlq_add_level_mesh(self._h, level, x.shape[0], px, c.shape[0], pc, pf, dt, nsteps),
+               "mlq_add_level_mesh", self._h)
+        self.levels[level] = dict(m=None, dt=dt, nsteps=nsteps, n=x.shape[0], ne=c.shape[0], mesh=True)
 
     def set_initial_state(self, level: int, v0, w0=None):
         v, pv = _host(v0, np.float64)

@@ -154,3 +154,65 @@ def test_device_point_location_matches_host_and_oracle(mlq, dim):
     ref = O.p1_at_points(O.unstructured_mesh(fine_xyz, fine_conn), f, pts)
     assert np.max(np.abs(dev - host)) < 1e-12 * np.max(np.abs(host))
     assert np.max(np.abs(dev - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_general_levels_in_the_context(mlq, prec):
+    # unrelated shells as levels 0..2 of one context (mlq_add_level_mesh):
+    # mlq_solve with the coarse member equals the standalone general-mesh
+    # solver sample by sample, and mlq_estimate (eq. StandardML with MC rules,
+    # Y_l = Q_l - Q_{l-1} on the same xi, each Q on its own mesh) equals the
+    # oracle's solves on the three meshes: FP64 1e-10, mixed 1e-6
+    meshes = [LV.lv_mesh(*d) for d in ((2, 6, 10), (2, 8, 14), (3, 11, 19))]
+    fine = O.unstructured_mesh(*meshes[-1])
+    modes, _ = O.kl_build(fine, 0.09, 0.15 ** 2, 4)
+    N = [8, 4, 2]
+    xis = [inputs.gaussian_xi(42, l, 0, N[l], 4) for l in range(3)]
+    dt, nb = 0.05, 6
+    tol = 1e-10 if prec == 0 else 1e-6
+    lv = []
+    for l, (xyz, conn) in enumerate(meshes):
+        frames, alpha = LV.lv_fibres(xyz, conn)
+        mesh = O.unstructured_mesh(xyz, conn)
+        phi = O.centroid_table_unrelated(fine, modes, mesh)
+        v0, w0 = LV.stimulus(xyz, radius=0.4)
+        lv.append((xyz, conn, frames, alpha, mesh, phi, v0, w0))
+    with mlq.Context(0, prec) as ctx:
+        for l, (xyz, conn, frames, alpha, mesh, phi, v0, w0) in enumerate(lv):
+            ctx.add_level_mesh(l, xyz, conn, dt, nb, frames=frames)
+            ctx.set_kl(l, phi, alpha)
+            ctx.set_initial_state(l, v0, w0)
+        r = ctx.solve(2, xis[2], with_coarse=True)
+        mean, var, rmse, ys = ctx.estimate(xis, return_y=True)
+        # the structured-only calls refuse a general level
+        with pytest.raises(mlq.MLQError) as e:
+            ctx.solve_state(2, xis[2])
+        assert e.value.code == mlq.MLQ_EUNSUPPORTED
+    assert np.all(r["status"] == 0)
+    for l, key in ((2, "q_fine"), (1, "q_coarse")):
+        xyz, conn, frames, alpha, mesh, phi, v0, w0 = lv[l]
+        with mlq.MeshLevel(xyz, conn, frames) as m:
+            m.set_kl(phi, alpha)
+            q, st, _ = m.solve(xis[2], dt, nb, v0, w0, precision=prec)
+        assert np.all(st == 0)
+        assert np.array_equal(r[key], q), (key, r[key], q)
+    assert np.array_equal(r["y"], r["q_fine"] - r["q_coarse"])
+    ref_y = []
+    for l in range(3):
+        q_f = O.solve_batch(lv[l][4], lv[l][5], xis[l], dt, nb, v0=lv[l][6], w0=lv[l][7], theta_mean=lv[l][3],
+                            frames=lv[l][2], nthreads=2)[0]
+        q_c = 0.0
+        if l > 0:
+            q_c = O.solve_batch(lv[l - 1][4], lv[l - 1][5], xis[l], dt, nb, v0=lv[l - 1][6], w0=lv[l - 1][7],
+                                theta_mean=lv[l - 1][3], frames=lv[l - 1][2], nthreads=2)[0]
+        ref_y.append(q_f - q_c)
+    ref = sum(float(np.mean(y)) for y in ref_y)
+    scale = max(abs(float(np.mean(lv_q))) for lv_q in ref_y)
+    assert abs(mean - ref) <= tol * scale
+    for l in range(3):
+        d = tol * scale   # bound on every per-sample error of Y_l
+        assert np.max(np.abs(ys[l] - ref_y[l])) <= d
+        # a sample variance moves by at most 2 sqrt(var) d + d^2 when every
+        # sample moves by at most d (the unbiased estimator, N_l >= 2)
+        v_ref = float(np.var(ref_y[l], ddof=1))
+        assert abs(var[l] - v_ref) <= 2.0 * np.sqrt(v_ref) * d * N[l] / (N[l] - 1) + 2.0 * d * d * N[l] / (N[l] - 1)
