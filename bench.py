@@ -599,7 +599,7 @@ def run_serve(spec: str):
 
 def run_c5(spec: str):
     """The non-nested multilevel estimate on the synthetic left-ventricle
-    shell: --c5 [T=2][,K=128][,N=4-16-64-256][,precision=mixed|fp64].
+    shell: --c5 [T=0.1][,K=128][,N=1-4-16-64][,precision=fp64|mixed].
     Four unrelated tetrahedral shells (~20k, 80k, 320k, 1.3M nodes) with
     helix fibres (-60 to +60 deg transmurally) turned by a KL field of K modes
     of 0.09 exp(-|x-y|^2 / 0.25^2) built on the finest shell and moved to each
@@ -607,12 +607,14 @@ def run_c5(spec: str):
     interpolation between unrelated meshes); dt_m = 0.1 2^-m on shell m over
     [0, T]; eq. PimpedML
     with nested rules, term l on shell L-l at the first N_l Gaussian points.
-    Prints the estimate, the time of each term's solve and DOF-steps/s."""
+    Prints the estimate, the time of each term's solve and DOF-steps/s.
+    FP64 by default: the shells' thin elements make A ill-conditioned enough
+    that FP32 inner solves stall before the FP64 residual reaches 1e-12."""
     kv = dict(item.split("=") for item in spec.split(",")) if spec else {}
     T = float(kv.get("T", 0.1))
     K = int(kv.get("K", 128))
     N = [int(x) for x in kv.get("N", "1-4-16-64").split("-")]
-    prec_name = kv.get("precision", "mixed")
+    prec_name = kv.get("precision", "fp64")
     from paper_2105_02007_gb300 import build, inputs
     from paper_2105_02007_gb300 import lv_inputs as LV
 

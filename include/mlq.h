@@ -344,8 +344,14 @@ int mlq_mesh_solve(mlq_mesh *mesh, const mlq_model *model, double dt, int32_t ns
                    const double *w0, int64_t S, const double *xi, double *q_out, int32_t *status, int32_t *iters);
 
 /* mlq_mesh_solve with solver options (opt: precision MLQ_FP64 or MLQ_MIXED,
- * rtol, rtol_inner, max_iter per solve, max_sweeps, cluster 0 (chosen) or
- * 1..16; the other fields are ignored).  MLQ_FP64: Jacobi-PCG in FP64 to
+ * rtol, rtol_inner, max_iter per solve, max_sweeps, cluster: CTAs per
+ * sample, 0 = chosen, 1, 2, 4, 8, 16 = one thread-block cluster per sample,
+ * 17..4096 = that many CTAs per sample in one cooperative launch (every CTA
+ * resident at once: MLQ_EUNSUPPORTED when they cannot be; their barriers
+ * wait a bounded time and a wait that runs out returns MLQ_ETIMEOUT with the
+ * samples' status MLQ_S_NONFINITE); the chosen shape is the cooperative one
+ * when a cluster of 16 per sample would leave SMs idle and each CTA keeps
+ * >= 2048 rows; the other fields are ignored).  MLQ_FP64: Jacobi-PCG in FP64 to
  * ||b - A v|| <= rtol ||b||.  MLQ_MIXED: FP32 Jacobi-PCG (FP32 CSR values and
  * vectors, FP64 sums across threads) inside FP64 iterative refinement with
  * the FP64 residual, to the same test.  The whole block loop runs in one

@@ -339,7 +339,11 @@ bool uses_mg3(const mlq_ctx *ctx, const Level &L)
 
 Shape choose_launch(mlq_ctx *ctx, const Level &L, int64_t S = 0)
 {
-    if (L.mesh) return Shape{mlq::mesh_member_cluster(L.mesh, std::max<int64_t>(S, 1), ctx->opt.cluster), 512, false, 0, 0};
+    if (L.mesh) {
+        // CTAs per sample: a cluster, or G CTAs of a cooperative launch
+        const mlq::MeshShape m = mlq::mesh_member_shape(L.mesh, std::max<int64_t>(S, 1), ctx->opt.cluster);
+        return Shape{m.G > 0 ? m.G : m.cs, 512, false, 0, 0};
+    }
     if (L.dim == 3) return choose_launch_3d(ctx, L, S);
     // 2D kernels are built for clusters of 1, 2, 4, 8, 16: a request of 6 or
     // 12 takes the power of two below it
@@ -489,7 +493,7 @@ cudaError_t launch_slab_cs(int cs, const mlq::SolveArgs<TI> &a, int nclusters, i
 size_t member_bytes(const mlq_ctx *ctx, const Level &L, int64_t S)
 {
     const bool mixed = ctx->opt.precision == MLQ_MIXED;
-    if (L.mesh) return mlq::mesh_member_bytes(L.mesh, mixed, S);
+    if (L.mesh) return mlq::mesh_member_bytes(L.mesh, mixed, S, mlq::mesh_member_shape(L.mesh, S, ctx->opt.cluster));
     const size_t ti = mixed ? 4 : 8;
     const size_t sn = (size_t)S * stored(L);
     size_t t = 0;
@@ -551,7 +555,7 @@ void member_carve(const mlq_ctx *ctx, const Level &L, Member &mb, char *&cur)
 {
     const bool mixed = ctx->opt.precision == MLQ_MIXED;
     if (L.mesh) {
-        mb.mws = mlq::mesh_member_carve(L.mesh, mixed, mb.S, cur);
+        mb.mws = mlq::mesh_member_carve(L.mesh, mixed, mb.S, mlq::mesh_member_shape(L.mesh, mb.S, ctx->opt.cluster), cur);
         mb.q = mb.mws.q;
         mb.iters = mb.mws.iters;
         mb.status = mb.mws.status;
@@ -769,18 +773,18 @@ int launch_member3d_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream
 // refinement by the context's precision)
 int launch_member_mesh(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream_t st, int slot, int phase)
 {
-    const int cs = mlq::mesh_member_cluster(L.mesh, mb.S, ctx->opt.cluster);
+    const mlq::MeshShape sh = mlq::mesh_member_shape(L.mesh, mb.S, ctx->opt.cluster);
     const bool timed = ctx->profile && slot >= 0 && slot < kStreams && (phase & kSolve);
     const unsigned evf = ctx->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (phase & kSetup) {
         MLQ_CUDA(ctx, mlq::mesh_member_launch(L.mesh, ctx->model, ctx->opt, L.dt, L.nsteps, L.d_v0, L.d_w0, mb.S, mb.d_xi,
-                                              mb.mws, cs, st, true, false));
+                                              mb.mws, sh, ctx->d_err, st, true, false));
         ctx->launches += ctx->opt.precision == MLQ_MIXED ? 3 : 2;
     }
     if (!(phase & kSolve)) return MLQ_OK;
     if (timed) MLQ_CUDA(ctx, cudaEventRecordWithFlags(ctx->ev_t0[slot], st, evf));
     MLQ_CUDA(ctx, mlq::mesh_member_launch(L.mesh, ctx->model, ctx->opt, L.dt, L.nsteps, L.d_v0, L.d_w0, mb.S, mb.d_xi,
-                                          mb.mws, cs, st, false, true));
+                                          mb.mws, sh, ctx->d_err, st, false, true));
     if (timed) MLQ_CUDA(ctx, cudaEventRecordWithFlags(ctx->ev_t1[slot], st, evf));
     ctx->launches++;
     return MLQ_OK;

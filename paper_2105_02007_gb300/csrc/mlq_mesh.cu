@@ -202,18 +202,59 @@ mlq::MeshArgs<TI> mesh_args(const mlq_mesh *m, const mlq_model *model, const mlq
     return a;
 }
 
+constexpr int kMeshThreads = 512;
+
 template <typename TI>
 cudaError_t launch_mesh(int cs, const mlq::MeshArgs<TI> &a, cudaStream_t st)
 {
-    constexpr int threads = 512;
     switch (cs) {
-    case 1: return mlq::cluster_launch<1>(mlq::mesh_slab_kernel<TI, 1>, a.S, threads, 0, st, a);
-    case 2: return mlq::cluster_launch<2>(mlq::mesh_slab_kernel<TI, 2>, a.S, threads, 0, st, a);
-    case 4: return mlq::cluster_launch<4>(mlq::mesh_slab_kernel<TI, 4>, a.S, threads, 0, st, a);
-    case 8: return mlq::cluster_launch<8>(mlq::mesh_slab_kernel<TI, 8>, a.S, threads, 0, st, a);
-    case 16: return mlq::cluster_launch<16>(mlq::mesh_slab_kernel<TI, 16>, a.S, threads, 0, st, a);
+    case 1: return mlq::cluster_launch<1>(mlq::mesh_slab_kernel<TI, mlq::ClusterGroup<1>>, a.S, kMeshThreads, 0, st, a, mlq::ClusterGroup<1>{});
+    case 2: return mlq::cluster_launch<2>(mlq::mesh_slab_kernel<TI, mlq::ClusterGroup<2>>, a.S, kMeshThreads, 0, st, a, mlq::ClusterGroup<2>{});
+    case 4: return mlq::cluster_launch<4>(mlq::mesh_slab_kernel<TI, mlq::ClusterGroup<4>>, a.S, kMeshThreads, 0, st, a, mlq::ClusterGroup<4>{});
+    case 8: return mlq::cluster_launch<8>(mlq::mesh_slab_kernel<TI, mlq::ClusterGroup<8>>, a.S, kMeshThreads, 0, st, a, mlq::ClusterGroup<8>{});
+    case 16: return mlq::cluster_launch<16>(mlq::mesh_slab_kernel<TI, mlq::ClusterGroup<16>>, a.S, kMeshThreads, 0, st, a, mlq::ClusterGroup<16>{});
     default: return cudaErrorInvalidValue;
     }
+}
+
+// G CTAs per sample in one cooperative launch (every CTA resident at once:
+// the launch fails otherwise)
+template <typename TI>
+cudaError_t launch_mesh_grid(const mlq::MeshArgs<TI> &a, const mlq::GridGroup &grp, cudaStream_t st)
+{
+    auto kern = mlq::mesh_slab_kernel<TI, mlq::GridGroup>;
+    int prio = 0;
+    cudaError_t e = cudaStreamGetPriority(st, &prio);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(a.S * grp.G));
+    cfg.blockDim = dim3((unsigned)kMeshThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    attr[1].id = cudaLaunchAttributePriority;
+    attr[1].val.priority = prio;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelEx(&cfg, kern, a, grp);
+}
+
+// CTAs of the mesh kernel resident at once on the device (both precisions
+// have the same bounds; the larger register count decides)
+int64_t mesh_resident_ctas(int device)
+{
+    int nsm = 1, b32 = 0, b64 = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, mlq::mesh_slab_kernel<float, mlq::GridGroup>,
+                                                      kMeshThreads, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, mlq::mesh_slab_kernel<double, mlq::GridGroup>,
+                                                      kMeshThreads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return (int64_t)std::min(b32, b64) * nsm;
 }
 
 size_t align256(size_t b) { return (std::max<size_t>(b, 8) + 255) / 256 * 256; }
@@ -226,17 +267,47 @@ int64_t mesh_nodes(const mlq_mesh *m) { return m->n; }
 int64_t mesh_elems(const mlq_mesh *m) { return m->ne; }
 int mesh_modes(const mlq_mesh *m) { return m->K; }
 
-size_t mesh_member_bytes(const mlq_mesh *m, bool mixed, int64_t S)
+MeshShape mesh_member_shape(const mlq_mesh *m, int64_t S, int request)
+{
+    MeshShape sh;
+    S = std::max<int64_t>(S, 1);
+    if (request > 16) {
+        sh.G = request;
+        sh.cs = (int64_t)request * S <= mesh_resident_ctas(m->device) ? 1 : 0;
+        return sh;
+    }
+    if (request > 0) {
+        while (sh.cs * 2 <= request) sh.cs *= 2;
+        while (sh.cs > 1 && m->n / sh.cs < 64) sh.cs /= 2;
+        return sh;
+    }
+    int nsm = 1;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device);
+    // one cluster of 16 per sample leaves SMs idle: spread each sample over
+    // the resident CTAs instead, >= 2048 rows per CTA
+    const int64_t res = mesh_resident_ctas(m->device);
+    const int64_t G = std::min<int64_t>(res / S, m->n / 2048);
+    if (16 * S < 2LL * nsm && G > 16) {
+        sh.G = (int)G;
+        return sh;
+    }
+    while (sh.cs < 16 && (int64_t)(2 * sh.cs) * S <= 2LL * nsm && m->n / (2 * sh.cs) >= 4096) sh.cs *= 2;
+    while (sh.cs > 1 && m->n / sh.cs < 64) sh.cs /= 2;
+    return sh;
+}
+
+size_t mesh_member_bytes(const mlq_mesh *m, bool mixed, int64_t S, const MeshShape &sh)
 {
     const size_t sn = (size_t)S * m->n, ti = mixed ? 4 : 8;
     size_t t = align256((size_t)S * m->ne * 16) + align256((size_t)S * m->nnz * 8);
     if (mixed) t += align256((size_t)S * m->nnz * 4);
     t += 4 * align256(sn * 8) + 7 * align256(sn * ti);
     t += align256((size_t)S * 8) + 2 * align256((size_t)S * 4);
+    if (sh.G > 0) t += align256((size_t)S * 2 * sizeof(unsigned)) + align256((size_t)S * 2 * sh.G * 4 * 8);
     return t;
 }
 
-MeshWs mesh_member_carve(const mlq_mesh *m, bool mixed, int64_t S, char *&base)
+MeshWs mesh_member_carve(const mlq_mesh *m, bool mixed, int64_t S, const MeshShape &sh, char *&base)
 {
     const size_t sn = (size_t)S * m->n, ti = mixed ? 4 : 8;
     auto take = [&](size_t bytes) {
@@ -256,29 +327,19 @@ MeshWs mesh_member_carve(const mlq_mesh *m, bool mixed, int64_t S, char *&base)
     w.q = (double *)take((size_t)S * 8);
     w.iters = (int32_t *)take((size_t)S * 4);
     w.status = (int32_t *)take((size_t)S * 4);
-    return w;
-}
-
-// one sample per cluster; the cluster grows while the batch still fills
-// the SMs twice over and every CTA keeps a few thousand rows
-int mesh_member_cluster(const mlq_mesh *m, int64_t S, int request)
-{
-    int nsm = 1;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device);
-    int cs = 1;
-    while (cs < 16 && (int64_t)(2 * cs) * S <= 2LL * nsm && m->n / (2 * cs) >= 4096) cs *= 2;
-    if (request > 0) {
-        cs = 1;
-        while (cs * 2 <= std::min(request, 16)) cs *= 2;
+    if (sh.G > 0) {
+        w.bar = (unsigned *)take((size_t)S * 2 * sizeof(unsigned));
+        w.part = (double *)take((size_t)S * 2 * sh.G * 4 * 8);
     }
-    while (cs > 1 && m->n / cs < 64) cs /= 2;
-    return cs;
+    return w;
 }
 
 cudaError_t mesh_member_launch(const mlq_mesh *m, const mlq_model &model, const mlq_options &opt, double dt,
                                int nsteps, const double *d_v0, const double *d_w0, int64_t S, const double *d_xi,
-                               const MeshWs &ws, int cs, cudaStream_t st, bool setup, bool solve)
+                               const MeshWs &ws, const MeshShape &sh, int *err, cudaStream_t st, bool setup,
+                               bool solve)
 {
+    if (sh.cs < 1 || (sh.G > 0 && (!ws.bar || !ws.part || !err))) return cudaErrorInvalidValue;
     if (S <= 0) return cudaSuccess;
     const bool mixed = opt.precision == MLQ_MIXED;
     const int64_t ne = m->ne, nnz = m->nnz;
@@ -295,14 +356,19 @@ cudaError_t mesh_member_launch(const mlq_mesh *m, const mlq_model &model, const 
         if (e != cudaSuccess) return e;
     }
     if (!solve) return cudaSuccess;
+    mlq::GridGroup grp{sh.G, ws.bar, ws.part, err};
+    if (sh.G > 0) {
+        const cudaError_t e = cudaMemsetAsync(ws.bar, 0, (size_t)S * 2 * sizeof(unsigned), st);
+        if (e != cudaSuccess) return e;
+    }
     if (mixed) {
         const mlq::MeshArgs<float> a = mesh_args<float>(m, &model, opt, dt, nsteps, S, ws.aval, ws.a32, d_v0, d_w0, ws.v,
                                                         ws.w, ws.b, ws.y, ws.vec, ws.q, ws.iters, ws.status);
-        return launch_mesh<float>(cs, a, st);
+        return sh.G > 0 ? launch_mesh_grid<float>(a, grp, st) : launch_mesh<float>(sh.cs, a, st);
     }
     const mlq::MeshArgs<double> a = mesh_args<double>(m, &model, opt, dt, nsteps, S, ws.aval, ws.aval, d_v0, d_w0, ws.v,
                                                       ws.w, ws.b, ws.y, ws.vec, ws.q, ws.iters, ws.status);
-    return launch_mesh<double>(cs, a, st);
+    return sh.G > 0 ? launch_mesh_grid<double>(a, grp, st) : launch_mesh<double>(sh.cs, a, st);
 }
 
 }  // namespace mlq
@@ -429,15 +495,17 @@ int mlq_mesh_solve_opts(mlq_mesh *m, const mlq_model *model, const mlq_options *
     if (opt->precision != MLQ_FP64 && opt->precision != MLQ_MIXED) return MLQ_EINVAL;
     if (!(opt->rtol > 0.0) || opt->max_iter < 1 || (opt->precision == MLQ_MIXED && opt->max_sweeps < 1))
         return MLQ_EINVAL;
-    if (opt->cluster != 0 && opt->cluster != 1 && opt->cluster != 2 && opt->cluster != 4 && opt->cluster != 8 &&
-        opt->cluster != 16)
+    if (!(opt->cluster == 0 || opt->cluster == 1 || opt->cluster == 2 || opt->cluster == 4 || opt->cluster == 8 ||
+          (opt->cluster >= 16 && opt->cluster <= 4096)))
         return MLQ_EINVAL;
     if (S == 0) return MLQ_OK;
     if (m->K > 0 && !xi) return MLQ_EINVAL;
     if (cudaSetDevice(m->device) != cudaSuccess) return MLQ_ECUDA;
     const bool mixed = opt->precision == MLQ_MIXED;
     const int64_t n = m->n;
-    const size_t ws_b = mlq::mesh_member_bytes(m, mixed, S);
+    const mlq::MeshShape sh = mlq::mesh_member_shape(m, S, opt->cluster);
+    if (sh.cs < 1) return MLQ_EUNSUPPORTED;   // the requested CTAs cannot all be resident
+    const size_t ws_b = mlq::mesh_member_bytes(m, mixed, S, sh) + align256(sizeof(int));
     const size_t in_b = align256((size_t)S * std::max(m->K, 1) * 8) + 2 * align256((size_t)n * 8);
     char *blk = nullptr;
     if (cudaMalloc(&blk, ws_b + in_b) != cudaSuccess) {
@@ -445,7 +513,9 @@ int mlq_mesh_solve_opts(mlq_mesh *m, const mlq_model *model, const mlq_options *
         return MLQ_ENOMEM;
     }
     char *cur = blk;
-    const mlq::MeshWs ws = mlq::mesh_member_carve(m, mixed, S, cur);
+    const mlq::MeshWs ws = mlq::mesh_member_carve(m, mixed, S, sh, cur);
+    int *err_d = (int *)cur;
+    cur += align256(sizeof(int));
     double *xi_d = (double *)cur;
     cur += align256((size_t)S * std::max(m->K, 1) * 8);
     double *v0_d = (double *)cur;
@@ -456,16 +526,19 @@ int mlq_mesh_solve_opts(mlq_mesh *m, const mlq_model *model, const mlq_options *
     if (m->K > 0) chk(cudaMemcpy(xi_d, xi, (size_t)S * m->K * 8, cudaMemcpyHostToDevice));
     chk(cudaMemcpy(v0_d, v0, (size_t)n * 8, cudaMemcpyHostToDevice));
     if (w0) chk(cudaMemcpy(w0_d, w0, (size_t)n * 8, cudaMemcpyHostToDevice));
+    int herr = 0;
     if (ok) {
-        const int cs = mlq::mesh_member_cluster(m, S, opt->cluster);
-        chk(mlq::mesh_member_launch(m, *model, *opt, dt, nsteps, v0_d, w0_d, S, xi_d, ws, cs, nullptr));
+        chk(cudaMemset(err_d, 0, sizeof(int)));
+        chk(mlq::mesh_member_launch(m, *model, *opt, dt, nsteps, v0_d, w0_d, S, xi_d, ws, sh, err_d, nullptr));
         chk(cudaMemcpy(q_out, ws.q, (size_t)S * 8, cudaMemcpyDeviceToHost));
         if (status) chk(cudaMemcpy(status, ws.status, (size_t)S * 4, cudaMemcpyDeviceToHost));
         if (iters) chk(cudaMemcpy(iters, ws.iters, (size_t)S * 4, cudaMemcpyDeviceToHost));
+        chk(cudaMemcpy(&herr, err_d, sizeof(int), cudaMemcpyDeviceToHost));
         chk(cudaDeviceSynchronize());
     }
     cudaFree(blk);
-    return ok ? MLQ_OK : MLQ_ECUDA;
+    if (!ok) return MLQ_ECUDA;
+    return herr ? MLQ_ETIMEOUT : MLQ_OK;
 }
 
 int mlq_mesh_solve(mlq_mesh *m, const mlq_model *model, double dt, int32_t nsteps, double rtol, const double *v0,

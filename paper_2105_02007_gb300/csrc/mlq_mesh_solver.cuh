@@ -2,10 +2,12 @@
 // general tetrahedral meshes (the non-nested hierarchies of Sec. 4 and the
 // ventricle of Sec. 5.4).
 //
-// One sample per cluster of CS CTAs; CTA `rank` owns the CSR rows
-// [n rank / CS, n (rank + 1) / CS).  Every vector lives in global memory
+// One sample per group of CTAs (a cluster of CS CTAs, or G CTAs of a
+// cooperative launch when a sample wants more CTAs than a cluster holds;
+// mlq_groups.cuh); CTA `rank` of the group owns the CSR rows
+// [n rank / size, n (rank + 1) / size).  Every vector lives in global memory
 // (sample-major); values of other CTAs' rows are read through L2 after a
-// cluster barrier.  Per time block (Sec. 3.1-3.3, as for the structured
+// group barrier.  Per time block (Sec. 3.1-3.3, as for the structured
 // levels):
 //   y = v + dt R(v, w), w += dt eps (v - gam w)              (own rows)
 //   b = M y, r = b - A v in FP64                             (CSR products)
@@ -18,6 +20,7 @@
 // iteration or per block.
 #pragma once
 
+#include "mlq_groups.cuh"
 #include "mlq_kernels.cuh"
 
 namespace mlq {
@@ -94,17 +97,16 @@ __device__ __forceinline__ void csr_rows(const int64_t *__restrict__ rp, const i
     }
 }
 
-template <typename TI, int CS>
-__global__ void __launch_bounds__(512, 2) mesh_slab_kernel(MeshArgs<TI> g)
+template <typename TI, typename Grp>
+__global__ void __launch_bounds__(512, 2) mesh_slab_kernel(MeshArgs<TI> g, Grp grp)
 {
     __shared__ double wsl[32][4];
     __shared__ double csl[2][4];
     __shared__ Ctl ctl;
-    cg::cluster_group cl = cg::this_cluster();
-    const int rank = (int)cl.block_rank();
-    const int sample = blockIdx.x / CS;
+    const int rank = grp.rank(), gsz = grp.size();
+    const int sample = grp.sample();
     const int n = g.n, tid = threadIdx.x, nt = blockDim.x;
-    const int r0 = (int)(((int64_t)n * rank) / CS), r1 = (int)(((int64_t)n * (rank + 1)) / CS);
+    const int r0 = (int)(((int64_t)n * rank) / gsz), r1 = (int)(((int64_t)n * (rank + 1)) / gsz);
     constexpr bool mixed = sizeof(TI) == 4;
 
     const size_t so = (size_t)sample * n;
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(512, 2) mesh_slab_kernel(MeshArgs<TI> g)
         w[i] = g.w0 ? g.w0[i] : 0.0;
         Dinv[i] = (TI)1 / Ai[g.diag[i]];
     }
-    cl.sync();
+    grp.sync();
 
     int par = 0;
     int64_t total_iters = 0;
@@ -132,7 +134,7 @@ __global__ void __launch_bounds__(512, 2) mesh_slab_kernel(MeshArgs<TI> g)
             y[i] = vv + dt * reaction<mixed>(vv, ww, g.a);
             w[i] = ww + dt * g.eps * recovery<mixed>(vv, ww, g.gam);
         }
-        cl.sync();
+        grp.sync();
         // ---- b = M y (FP64), then r = b - A v (FP64) into R
         {
             double acc[2] = {0.0, 0.0};
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(512, 2) mesh_slab_kernel(MeshArgs<TI> g)
                 R[i] = (TI)rr;
                 acc[1] += rr * rr;
             });
-            cluster_reduce<2, CS>(acc, wsl, csl, par, [&](double(&t)[2]) {
+            grp.template reduce<2>(acc, wsl, csl, par, [&](double(&t)[2]) {
                 ctl.s0 = t[0];
                 ctl.s1 = t[1];
             });
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(512, 2) mesh_slab_kernel(MeshArgs<TI> g)
                     R[i] = (TI)rr;
                     racc[0] += rr * rr;
                 });
-                cluster_reduce<1, CS>(racc, wsl, csl, par, [&](double(&t)[1]) { ctl.s1 = t[0]; });
+                grp.template reduce<1>(racc, wsl, csl, par, [&](double(&t)[1]) { ctl.s1 = t[0]; });
                 par ^= 1;
                 rnorm2 = ctl.s1;
                 if (!isfinite(rnorm2)) {
@@ -203,7 +205,7 @@ __global__ void __launch_bounds__(512, 2) mesh_slab_kernel(MeshArgs<TI> g)
                 gacc += (double)(R[i] * U[i]);
                 racc += (double)(R[i] * R[i]);
             }
-            cl.sync();
+            grp.sync();
             double gamma_prev = 1.0, eta_prev = 1.0;
             int it = 0;
             auto decide = [&](double gamma, double delta, double rr) {
@@ -234,7 +236,7 @@ __global__ void __launch_bounds__(512, 2) mesh_slab_kernel(MeshArgs<TI> g)
                     W[i] = wv;
                     pacc[1] += (double)(wv * U[i]);
                 });
-                cluster_reduce<3, CS>(pacc, wsl, csl, par, [&](double(&t)[3]) { decide(t[0], t[1], t[2]); });
+                grp.template reduce<3>(pacc, wsl, csl, par, [&](double(&t)[3]) { decide(t[0], t[1], t[2]); });
                 par ^= 1;
                 const int code = ctl.code;
                 if (code != 0) {
@@ -261,12 +263,12 @@ __global__ void __launch_bounds__(512, 2) mesh_slab_kernel(MeshArgs<TI> g)
                     racc += (double)(rv * rv);
                 }
                 ++it;
-                cl.sync();
+                grp.sync();
             }
             total_iters += it;
             if (nonfinite) break;
             for (int i = r0 + tid; i < r1; i += nt) v[i] = fma((double)X[i], rnorm, v[i]);
-            cl.sync();
+            grp.sync();
             if (!mixed) solved = true;
         }
         if (nonfinite) {
@@ -278,13 +280,13 @@ __global__ void __launch_bounds__(512, 2) mesh_slab_kernel(MeshArgs<TI> g)
 
     double qacc[1] = {0.0};
     for (int i = r0 + tid; i < r1; i += nt) qacc[0] += g.lump[i] * v[i];
-    cluster_reduce<1, CS>(qacc, wsl, csl, par, [&](double(&t)[1]) { ctl.s0 = t[0]; });
+    grp.template reduce<1>(qacc, wsl, csl, par, [&](double(&t)[1]) { ctl.s0 = t[0]; });
     if (rank == 0 && tid == 0) {
         g.q[sample] = status == S_NONFINITE ? __longlong_as_double(0x7ff8000000000000LL) : ctl.s0;
         g.iters[sample] = (int32_t)(total_iters > 0x7fffffff ? 0x7fffffff : total_iters);
         g.status[sample] = status;
     }
-    cl.sync();
+    grp.sync();
 }
 
 }  // namespace mlq

@@ -110,10 +110,12 @@ def test_pimped_ml_over_unrelated_shells_matches_oracle(mlq):
     assert abs(est - ref) <= 1e-10 * abs(ref)
 
 
-@pytest.mark.parametrize("prec,cluster", [(0, 1), (0, 4), (1, 0), (1, 1), (1, 2), (1, 16)])
+@pytest.mark.parametrize("prec,cluster", [(0, 1), (0, 4), (1, 0), (1, 1), (1, 2), (1, 16), (0, 24), (1, 72)])
 def test_mesh_level_precisions_and_clusters(mlq, prec, cluster):
-    # the device-resident member in both precisions and on every cluster
-    # size (ragged row bands), against the oracle: FP64 1e-10, mixed 1e-6
+    # the device-resident member in both precisions, on every cluster size
+    # (ragged row bands) and as a cooperative launch of 24 / 72 CTAs per
+    # sample (global-memory barriers and sums), against the oracle: FP64
+    # 1e-10, mixed 1e-6
     xyz, conn = LV.lv_mesh(*((3, 16, 28) if cluster == 16 else (2, 8, 14)))   # 16 CTAs need >= 1024 rows
     frames, alpha = LV.lv_fibres(xyz, conn)
     mesh = O.unstructured_mesh(xyz, conn)
@@ -216,3 +218,38 @@ def test_general_levels_in_the_context(mlq, prec):
         # sample moves by at most d (the unbiased estimator, N_l >= 2)
         v_ref = float(np.var(ref_y[l], ddof=1))
         assert abs(var[l] - v_ref) <= 2.0 * np.sqrt(v_ref) * d * N[l] / (N[l] - 1) + 2.0 * d * d * N[l] / (N[l] - 1)
+
+
+def test_mesh_level_cooperative_shape_chosen_and_captured(mlq):
+    # one or two samples on a ~49k-node shell: the chosen shape spreads each
+    # sample over more CTAs than a cluster holds (a cooperative launch); its
+    # Q agrees with clusters of 16 (another summation order) to 1e-10; in a
+    # context the estimate gives the same samples eagerly and replayed from
+    # a captured graph, equal to the standalone solver
+    xyz, conn = LV.lv_mesh(8, 56, 98)
+    frames, alpha = LV.lv_fibres(xyz, conn)
+    rng = np.random.default_rng(70)
+    phi = rng.normal(scale=0.3, size=(conn.shape[0], 4))
+    xi = inputs.gaussian_xi(43, 0, 0, 2, 4)
+    v0, w0 = LV.stimulus(xyz, radius=0.4)
+    dt, nb = 0.05, 3
+    with mlq.MeshLevel(xyz, conn, frames) as lvl:
+        lvl.set_kl(phi, alpha)
+        q_cl, st_cl, it_cl = lvl.solve(xi[:1], dt, nb, v0, w0, precision=0, cluster=16)
+        q_auto, st_a, it_a = lvl.solve(xi[:1], dt, nb, v0, w0, precision=0)
+        q_two, st_two, _ = lvl.solve(xi, dt, nb, v0, w0, precision=0)
+    assert np.all(st_cl == 0) and np.all(st_a == 0) and np.all(st_two == 0)
+    assert abs(q_auto[0] - q_cl[0]) <= 1e-10 * abs(q_cl[0])
+    res = []
+    for graphs in (0, 1):
+        with mlq.Context(0, 0, graphs=graphs) as ctx:
+            ctx.add_level_mesh(0, xyz, conn, dt, nb, frames=frames)
+            ctx.set_kl(0, phi, alpha)
+            ctx.set_initial_state(0, v0, w0)
+            cps = ctx.level_launch(0)[0]
+            for _ in range(2):   # the second call replays the captured graph
+                mean, var, rmse, ys = ctx.estimate([xi], return_y=True)
+            res.append(ys[0])
+    assert cps > 16
+    assert np.array_equal(res[0], res[1])
+    assert np.array_equal(res[0], q_two)
