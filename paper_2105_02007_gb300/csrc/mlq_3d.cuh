@@ -36,6 +36,7 @@
 #pragma once
 
 #include "mlq_3d_types.cuh"
+#include "mlq_groups.cuh"
 #include "mlq_kernels.cuh"
 
 namespace mlq {
@@ -892,11 +893,12 @@ static __device__ __noinline__ void sp_update_v(BandP B, double s, const TI *X, 
         [&](int P, const double2 &t) { stq(v + P, t); });
 }
 
-// One sample per cluster of CS CTAs.  256 threads with up to 128 registers
-// each: the 15-point quad product keeps its 22 16-byte loads in flight per
-// thread.
-template <typename TI, int CS>
-__global__ void __launch_bounds__(256, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
+// One sample per group of CTAs (a cluster of CS CTAs, or G CTAs of a
+// cooperative launch when clusters cannot fill the SMs evenly;
+// mlq_groups.cuh).  256 threads with up to 128 registers each: the
+// 15-point quad product keeps its 22 16-byte loads in flight per thread.
+template <typename TI, typename Grp>
+__global__ void __launch_bounds__(256, 2) slab_solve_3d_kernel(Solve3Args<TI> g, Grp grp)
 {
     __shared__ double wsl[32][4];
     __shared__ double csl[2][4];
@@ -905,9 +907,8 @@ __global__ void __launch_bounds__(256, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
     // shared memory keeps those reads out of local memory
     __shared__ Mg3Args sM;
     if (threadIdx.x == 0) sM = g.mg;
-    cg::cluster_group cl = cg::this_cluster();
-    const int rank = (int)cl.block_rank();
-    const int sample = blockIdx.x / CS;
+    const int rank = grp.rank(), CS = grp.size();
+    const int sample = grp.sample();
     const Grid3 G = g.g;
     const int n = G.n;
     const Band3 B0 = band3(G, rank, CS);
@@ -953,7 +954,7 @@ __global__ void __launch_bounds__(256, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
             vb0[P] = s0.v[0];
             wb0[P] = s0.v[1];
         });
-    cl.sync();
+    grp.sync();
     PointState pst;
     const bool pth = rank == 0 && tid < g.pq.npts;   // point QoI threads
     if (pth) point_record(g.pq, sample, g.nsteps, g.dt, vb0, pst);
@@ -994,12 +995,12 @@ __global__ void __launch_bounds__(256, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                 // pre-smoothing from zero: XA = omega D^-1 B (level 0: done)
                 if (c > 0) {
                     qp_jacobi0(Lc, Bc, om, BB(c), vec(M.xa, c));
-                    cl.sync();
+                    grp.sync();
                 }
                 qp_residual(Lc, Bc, vec(M.xa, c), BB(c), RR(c));
-                cl.sync();
+                grp.sync();
                 qp_restrict(Gc, M.g[c + 1], bandq(M.g[c + 1], rank, CS), RR(c), BB(c + 1));
-                cl.sync();
+                grp.sync();
             }
             // coarsest: damped Jacobi sweeps, ping-pong XA / XB
             {
@@ -1010,13 +1011,13 @@ __global__ void __launch_bounds__(256, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                 float *X0 = vec(M.xa, c), *Y0 = vec(M.xb, c);
                 qp_jacobi0(Lc, Bc, om, BB(c), X0);
                 for (int k = 1; k < kMgCoarsestSweeps3D; ++k) {
-                    cl.sync();
+                    grp.sync();
                     qp_smooth(Lc, Bc, om, X0, BB(c), Y0);
                     float *t = X0;
                     X0 = Y0;
                     Y0 = t;
                 }
-                cl.sync();
+                grp.sync();
             }
             // ascend: XB = XA + P X_{c+1}, then post-smoothing
             // X_c = XB + omega D^-1 (B - A XB) into RR (level 0: U)
@@ -1026,10 +1027,10 @@ __global__ void __launch_bounds__(256, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                 const float *xq = (c + 1 == NL - 1) ? ((kMgCoarsestSweeps3D - 1) % 2 ? vec(M.xb, c + 1) : vec(M.xa, c + 1))
                                                     : RR(c + 1);
                 qp_prolong(Gc, M.g[c + 1], Bc, vec(M.xa, c), xq, vec(M.xb, c));
-                cl.sync();
+                grp.sync();
                 const double2 t = qp_smooth(qlev(Aof(c), Gc), Bc, om, vec(M.xb, c), BB(c), RR(c));
                 if (c == 0) sums = t;
-                cl.sync();
+                grp.sync();
             }
         }
         return sums;
@@ -1048,11 +1049,11 @@ __global__ void __launch_bounds__(256, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
         double *wnext = wb0 + (wpar ^ 1) * SN;
         sp_block_load(P0, dt, g.a, g.eps, g.gam, gp, vcur, wcur, vm1, vm2, vm3, v, yb, wnext);
         wpar ^= 1;
-        cl.sync();
+        grp.sync();
         {
             const double2 t = sp_load_rhs<TI>(G, B0, g.M3, A64, yb, v, b, R);
             double acc[2] = {t.x, t.y};
-            cluster_reduce<2, CS>(acc, wsl, csl, par, [&](double(&t)[2]) {
+            grp.template reduce<2>(acc, wsl, csl, par, [&](double(&t)[2]) {
                 ctl.s0 = t[0];
                 ctl.s1 = t[1];
             });
@@ -1070,7 +1071,7 @@ __global__ void __launch_bounds__(256, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
         for (int sweep = 0; sweep < sweeps; ++sweep) {
             if (sweep > 0) {
                 double racc[1] = {sp_residual<TI>(G, B0, A64, b, v, R)};
-                cluster_reduce<1, CS>(racc, wsl, csl, par, [&](double(&t)[1]) { ctl.s1 = t[0]; });
+                grp.template reduce<1>(racc, wsl, csl, par, [&](double(&t)[1]) { ctl.s1 = t[0]; });
                 par ^= 1;
                 rnorm2 = ctl.s1;
                 if (!isfinite(rnorm2)) {
@@ -1119,7 +1120,7 @@ __global__ void __launch_bounds__(256, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                         racc += (double)(o.v[0] * o.v[0]);
                     });
             }
-            cl.sync();
+            grp.sync();
             if (mgp) {
                 const double2 t = vcycle();
                 gacc = t.x;
@@ -1167,7 +1168,7 @@ __global__ void __launch_bounds__(256, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                             pacc[1] += (double)(o.v[0] * o.v[1]);
                         });
                 }
-                cluster_reduce<3, CS>(pacc, wsl, csl, par, [&](double(&t)[3]) { decide(t[0], t[1], t[2]); });
+                grp.template reduce<3>(pacc, wsl, csl, par, [&](double(&t)[3]) { decide(t[0], t[1], t[2]); });
                 par ^= 1;
                 const int code = ctl.code;
                 if (code != 0) {
@@ -1210,13 +1211,13 @@ __global__ void __launch_bounds__(256, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
                         });
                 }
                 ++it;
-                cl.sync();
+                grp.sync();
                 if (mgp) gacc = vcycle().x;
             }
             total_iters += it;
             if (nonfinite) break;
             sp_update_v<TI>(P0, rnorm, X, v);
-            cl.sync();
+            grp.sync();
             if (!mixed) solved = true;
         }
         if (nonfinite) {
@@ -1237,13 +1238,13 @@ __global__ void __launch_bounds__(256, 2) slab_solve_3d_kernel(Solve3Args<TI> g)
             return m.x * vv.x + m.y * vv.y;
         },
         [&](int, double t) { qacc[0] += t; });
-    cluster_reduce<1, CS>(qacc, wsl, csl, par, [&](double(&t)[1]) { ctl.s0 = t[0]; });
+    grp.template reduce<1>(qacc, wsl, csl, par, [&](double(&t)[1]) { ctl.s0 = t[0]; });
     if (rank == 0 && tid == 0) {
         g.q[sample] = status == S_NONFINITE ? __longlong_as_double(0x7ff8000000000000LL) : ctl.s0;
         g.iters[sample] = (int32_t)(total_iters > 0x7fffffff ? 0x7fffffff : total_iters);
         g.status[sample] = status;
     }
-    cl.sync();
+    grp.sync();
 }
 
 }  // namespace mlq

@@ -39,30 +39,81 @@ cudaError_t with_cs(int cs, F &&f)
     }
 }
 
+// CTAs of the 3D solver resident at once on the device
+int64_t resident_3d(int threads)
+{
+    int dev = 0, nsm = 1, nb = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, slab_solve_3d_kernel<TI3, GridGroup>, threads, 0) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return (int64_t)nb * nsm;
+}
+
 }  // namespace
 
+// cs <= 16: one cluster of cs CTAs per sample; cs > 16: cs CTAs per sample
+// in one cooperative launch (bar: [S][2] zeroed here, part: [S][2][cs][4])
 #if MLQ_F64
-cudaError_t launch_3d_f64(int cs, const Solve3Args<double> &a, int nclusters, int threads, cudaStream_t st)
+cudaError_t launch_3d_f64(int cs, const Solve3Args<double> &a, int nsamples, int threads, cudaStream_t st,
+                          unsigned *bar, double *part, int *err)
 #else
-cudaError_t launch_3d_f32(int cs, const Solve3Args<float> &a, int nclusters, int threads, cudaStream_t st)
+cudaError_t launch_3d_f32(int cs, const Solve3Args<float> &a, int nsamples, int threads, cudaStream_t st,
+                          unsigned *bar, double *part, int *err)
 #endif
 {
+    if (cs > 16) {
+        if (!bar || !part || !err) return cudaErrorInvalidValue;
+        cudaError_t e = cudaMemsetAsync(bar, 0, (size_t)nsamples * 2 * sizeof(unsigned), st);
+        if (e != cudaSuccess) return e;
+        int prio = 0;
+        if ((e = cudaStreamGetPriority(st, &prio)) != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)(nsamples * cs));
+        cfg.blockDim = dim3((unsigned)threads);
+        cfg.stream = st;
+        cudaLaunchAttribute attr[2];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        attr[1].id = cudaLaunchAttributePriority;
+        attr[1].val.priority = prio;
+        cfg.attrs = attr;
+        cfg.numAttrs = 2;
+        const GridGroup grp{cs, bar, part, err};
+        return cudaLaunchKernelEx(&cfg, slab_solve_3d_kernel<TI3, GridGroup>, a, grp);
+    }
     return with_cs(cs, [&](auto c) {
         constexpr int CS = decltype(c)::value;
-        return cluster_launch<CS>(slab_solve_3d_kernel<TI3, CS>, nclusters, threads, 0, st, a);
+        return cluster_launch<CS>(slab_solve_3d_kernel<TI3, ClusterGroup<CS>>, nsamples, threads, 0, st, a,
+                                  ClusterGroup<CS>{});
     });
 }
 
+#if MLQ_F64
+int64_t resident_3d_f64(int threads)
+#else
+int64_t resident_3d_f32(int threads)
+#endif
+{
+    return resident_3d(threads);
+}
+
+// samples whose groups can be resident at once: clusters for cs <= 16, the
+// CTAs of a cooperative launch over cs for cs > 16
 #if MLQ_F64
 int active_3d_f64(int cs, int threads)
 #else
 int active_3d_f32(int cs, int threads)
 #endif
 {
+    if (cs > 16) return (int)(resident_3d(threads) / cs);
     int nc = 0;
     with_cs(cs, [&](auto c) {
         constexpr int CS = decltype(c)::value;
-        nc = cluster_occupancy<CS>(slab_solve_3d_kernel<TI3, CS>, threads, 0);
+        nc = cluster_occupancy<CS>(slab_solve_3d_kernel<TI3, ClusterGroup<CS>>, threads, 0);
         return cudaSuccess;
     });
     return nc;

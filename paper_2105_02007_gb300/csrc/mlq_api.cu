@@ -82,6 +82,8 @@ struct Member {
     float *mg3v[mlq::kMg3MaxLevels][4] = {};  // 3D multigrid work vectors xa, xb, rr, bb
     mlq::PointArgs pq{};   // point QoIs of this member (npts = 0: none)
     mlq::MeshWs mws{};     // general-mesh level: the solver's workspace
+    unsigned *bar3 = nullptr;   // 3D cooperative shape: per-sample barrier words
+    double *part3 = nullptr;    // 3D cooperative shape: per-CTA partial sums
 };
 
 // 3D multigrid in use for a level (FP32 inner path)
@@ -179,6 +181,7 @@ struct mlq_ctx {
     std::string cuda_error;
     int max_cluster = 8;
     int occ3d[2][32];   // resident clusters of the 3D solver by precision and cluster size (-1: not asked)
+    int64_t res3d[2] = {-1, -1};   // resident CTAs of the 3D solver (256 threads) by precision
     int smem_optin = 48 * 1024;
     int num_sms = 1;
     // optional per-member timing of the slab kernel (CUDA events on the
@@ -288,15 +291,19 @@ std::vector<Shape> mg_candidates(const mlq_ctx *ctx, const Level &L)
     return out;
 }
 
-// 3D: one sample per cluster of CS CTAs (256 threads), vectors in global
+// 3D: one sample per group of CS CTAs (256 threads), vectors in global
 // memory (bandwidth-bound); a CTA owns my / CS grid lines of every plane (a
-// CTA may own none).  The largest cluster size whose clusters hold every
+// CTA may own none).  When the resident CTAs over the samples exceed 16
+// (and keep >= 4096 nodes each), that many CTAs per sample in one
+// cooperative launch (every SM holds the same CTAs; cs > 16 below).  Else the
+// largest cluster size whose clusters hold every
 // sample of the batch at once, keeping >= 4096 nodes per CTA; when no
 // size holds them all (the batch fills the GPU in any case), one CTA per
 // sample.  Clusters of 16 occupy 8 x 16 = 128 of the 152 SMs, 12 and 6
 // pack the GPCs more densely.
 int active_3d(mlq_ctx *ctx, bool f32, int cs, int threads)
 {
+    if (cs > 16) return f32 ? mlq::active_3d_f32(cs, threads) : mlq::active_3d_f64(cs, threads);
     int &c = ctx->occ3d[f32 ? 0 : 1][cs & 31];
     if (threads == 256 && c >= 0) return c;
     const int a = f32 ? mlq::active_3d_f32(cs, threads) : mlq::active_3d_f64(cs, threads);
@@ -311,13 +318,29 @@ Shape choose_launch_3d(mlq_ctx *ctx, const Level &L, int64_t S = 0)
     int threads = ctx->opt.threads > 0 ? ctx->opt.threads / 32 * 32 : 256;
     threads = std::min(256, std::max(32, threads));
     int cs = 1;
-    if (ctx->opt.cluster > 0) {
+    const int64_t Sx = std::max<int64_t>(S, 1);
+    int64_t resident;
+    if (threads == 256) {
+        int64_t &res = ctx->res3d[f32 ? 0 : 1];   // cached for the default block size
+        if (res < 0) res = f32 ? mlq::resident_3d_f32(threads) : mlq::resident_3d_f64(threads);
+        resident = res;
+    } else {
+        resident = f32 ? mlq::resident_3d_f32(threads) : mlq::resident_3d_f64(threads);
+    }
+    const int64_t G = resident / Sx;
+    if (ctx->opt.cluster > 16) {
+        cs = ctx->opt.cluster;   // that many CTAs per sample, cooperative launch
+    } else if (ctx->opt.cluster > 0) {
         // the built size at or below the requested one that fits the level
         for (int c : kCs)
             if (c <= ctx->opt.cluster && c <= ctx->max_cluster) {
                 cs = c;
                 break;
             }
+    } else if (G > 16 && L.n / G >= 4096) {
+        // clusters cannot give every SM the same share: spread each sample
+        // over the resident CTAs in one cooperative launch
+        cs = (int)G;
     } else {
         for (int c : kCs) {
             if (c > 1 && (c > ctx->max_cluster || L.n / c < 4096)) continue;
@@ -347,7 +370,7 @@ Shape choose_launch(mlq_ctx *ctx, const Level &L, int64_t S = 0)
     if (L.dim == 3) return choose_launch_3d(ctx, L, S);
     // 2D kernels are built for clusters of 1, 2, 4, 8, 16: a request of 6 or
     // 12 takes the power of two below it
-    const int creq = ctx->opt.cluster == 6 ? 4 : ctx->opt.cluster == 12 ? 8 : ctx->opt.cluster;
+    const int creq = ctx->opt.cluster == 6 ? 4 : ctx->opt.cluster == 12 ? 8 : std::min(ctx->opt.cluster, 16);
     const bool paper = ctx->scheme.ionic == 1;   // the paper's scheme runs in the generic slab kernel
     if (!paper && ctx->opt.precision == MLQ_MIXED && ctx->opt.precond == 1 && ctx->opt.storage != 2) {
         if (L.tuned_cs > 0 && L.tuned_mg && creq <= 0 && ctx->opt.threads <= 0) {
@@ -510,6 +533,11 @@ size_t member_bytes(const mlq_ctx *ctx, const Level &L, int64_t S)
         add((size_t)S * 8);
         add((size_t)S * 4);
         add((size_t)S * 4);
+        const int cs3 = choose_launch_3d(const_cast<mlq_ctx *>(ctx), L, S).cs;
+        if (cs3 > 16) {
+            add((size_t)S * 2 * sizeof(unsigned));
+            add((size_t)S * 2 * cs3 * 4 * 8);
+        }
         if (uses_mg3(ctx, L)) {
             mlq::Grid3 gl[mlq::kMg3MaxLevels];
             const int nl = mlq::mg3_hierarchy(L.g3, gl, mlq::kMg3MaxLevels);
@@ -585,6 +613,11 @@ void member_carve(const mlq_ctx *ctx, const Level &L, Member &mb, char *&cur)
         mb.q = (double *)take((size_t)mb.S * 8);
         mb.iters = (int32_t *)take((size_t)mb.S * 4);
         mb.status = (int32_t *)take((size_t)mb.S * 4);
+        const int cs3 = choose_launch_3d(const_cast<mlq_ctx *>(ctx), L, mb.S).cs;
+        if (cs3 > 16) {
+            mb.bar3 = (unsigned *)take((size_t)mb.S * 2 * sizeof(unsigned));
+            mb.part3 = (double *)take((size_t)mb.S * 2 * cs3 * 4 * 8);
+        }
         if (uses_mg3(ctx, L)) {
             mlq::Grid3 gl[mlq::kMg3MaxLevels];
             const int nl = mlq::mg3_hierarchy(L.g3, gl, mlq::kMg3MaxLevels);
@@ -761,8 +794,10 @@ int launch_member3d_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream
     const bool timed = ctx->profile && slot >= 0 && slot < kStreams;
     const unsigned evf = ctx->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (timed) MLQ_CUDA(ctx, cudaEventRecordWithFlags(ctx->ev_t0[slot], st, evf));
-    if constexpr (sizeof(TI) == 4) MLQ_CUDA(ctx, mlq::launch_3d_f32(sh.cs, a, (int)mb.S, sh.threads, st));
-    else MLQ_CUDA(ctx, mlq::launch_3d_f64(sh.cs, a, (int)mb.S, sh.threads, st));
+    if (sh.cs > 16 && active_3d(ctx, sizeof(TI) == 4, sh.cs, sh.threads) < mb.S) return MLQ_EUNSUPPORTED;
+    if constexpr (sizeof(TI) == 4)
+        MLQ_CUDA(ctx, mlq::launch_3d_f32(sh.cs, a, (int)mb.S, sh.threads, st, mb.bar3, mb.part3, ctx->d_err));
+    else MLQ_CUDA(ctx, mlq::launch_3d_f64(sh.cs, a, (int)mb.S, sh.threads, st, mb.bar3, mb.part3, ctx->d_err));
     if (timed) MLQ_CUDA(ctx, cudaEventRecordWithFlags(ctx->ev_t1[slot], st, evf));
     ctx->launches++;
     return MLQ_OK;
@@ -1039,7 +1074,7 @@ static int validate_options(const mlq_options *o)
     if (o->precision != MLQ_FP64 && o->precision != MLQ_MIXED) return MLQ_EINVAL;
     if (!(o->rtol > 0.0) || !(o->rtol_inner > 0.0) || o->max_iter < 0 || o->max_sweeps < 1) return MLQ_EINVAL;
     if (o->cluster != 0 && o->cluster != 1 && o->cluster != 2 && o->cluster != 4 && o->cluster != 6 &&
-        o->cluster != 8 && o->cluster != 12 && o->cluster != 16)
+        o->cluster != 8 && o->cluster != 12 && !(o->cluster >= 16 && o->cluster <= 1024))
         return MLQ_EINVAL;
     if (o->threads != 0 && (o->threads < 64 || o->threads > 512 || o->threads % 32)) return MLQ_EINVAL;
     if (o->storage < 0 || o->storage > 2) return MLQ_EINVAL;
@@ -1091,7 +1126,7 @@ int mlq_create(mlq_ctx **out, int device, void *cuda_stream, const mlq_options *
         for (int &c : row) c = -1;
     cudaGetLastError();
     (void)nonportable;
-    if (o.cluster > ctx->max_cluster) return fail(MLQ_EUNSUPPORTED);
+    if (o.cluster > ctx->max_cluster && o.cluster <= 16) return fail(MLQ_EUNSUPPORTED);   // sizes above 16 are cooperative launches
     if (cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess || cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess)
         return fail(MLQ_ENOMEM);
     if (cudaMallocHost(&ctx->h_sums, sizeof(double) * 2 * kMaxLevels) != cudaSuccess) return fail(MLQ_ENOMEM);
@@ -1130,7 +1165,7 @@ int mlq_set_options(mlq_ctx *ctx, const mlq_options *opt)
     MLQ_GUARD(ctx);
     if (!ctx || !opt || validate_options(opt) != MLQ_OK) return MLQ_EINVAL;
     ctx->generation++;
-    if (opt->cluster > ctx->max_cluster) return MLQ_EUNSUPPORTED;
+    if (opt->cluster > ctx->max_cluster && opt->cluster <= 16) return MLQ_EUNSUPPORTED;
     ctx->opt = *opt;
     return MLQ_OK;
 }

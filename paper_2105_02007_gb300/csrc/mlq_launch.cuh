@@ -29,12 +29,21 @@ MLQ_DECLARE_REG(16)
 #undef MLQ_DECLARE_REG
 
 // 3D (Kuhn tetrahedra), mlq_3d_inst.cu
-cudaError_t launch_3d_f32(int cs, const Solve3Args<float> &a, int nclusters, int threads, cudaStream_t st);
-cudaError_t launch_3d_f64(int cs, const Solve3Args<double> &a, int nclusters, int threads, cudaStream_t st);
-// clusters of the 3D solver resident at once (0: the size is not built or
-// does not fit); cluster sizes 1, 2, 4, 6, 8, 12, 16
+// cs <= 16: one cluster of cs CTAs per sample (sizes 1, 2, 4, 6, 8, 12,
+// 16); cs > 16: cs CTAs per sample in one cooperative launch whose
+// per-sample barriers live in bar ([S][2], zeroed by the call) and part
+// ([S][2][cs][4]), err set when a barrier wait runs out
+cudaError_t launch_3d_f32(int cs, const Solve3Args<float> &a, int nsamples, int threads, cudaStream_t st,
+                          unsigned *bar = nullptr, double *part = nullptr, int *err = nullptr);
+cudaError_t launch_3d_f64(int cs, const Solve3Args<double> &a, int nsamples, int threads, cudaStream_t st,
+                          unsigned *bar = nullptr, double *part = nullptr, int *err = nullptr);
+// samples of the 3D solver resident at once (clusters for cs <= 16, 0: the
+// size is not built or does not fit; cooperative CTAs / cs for cs > 16)
 int active_3d_f32(int cs, int threads);
 int active_3d_f64(int cs, int threads);
+// CTAs of the 3D solver resident at once
+int64_t resident_3d_f32(int threads);
+int64_t resident_3d_f64(int threads);
 cudaError_t launch_level3d_setup(const Grid3 &g, double *M3, double *lump, cudaStream_t st);
 cudaError_t launch_stencil3d_setup(const double *cs2, const Grid3 &g, double dt, double s_l, double s_t, int S,
                                    double *A64, float *A32, cudaStream_t st);

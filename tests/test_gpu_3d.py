@@ -44,12 +44,14 @@ def setup3d(dims, K, seed, S, radius=0.29):
 
 
 # every built cluster size (a CTA may own no grid line: 9 x 7 x 5 on 8),
+# 20 and 24 CTAs per sample in one cooperative launch (global barriers),
 # ragged line bands, rows padded from 5, 9, 13, 17, 33 to multiples of 4, FP64 and the
 # mixed path with the Jacobi and the multigrid inner preconditioner (meshes
 # with 1..4 multigrid levels; 13 x 11 x 6 cannot be coarsened)
 @pytest.mark.parametrize("dims,cluster", [((5, 5, 3), 1), ((9, 9, 5), 1), ((9, 9, 5), 4), ((9, 7, 5), 8),
                                           ((17, 17, 5), 16), ((17, 17, 5), 12), ((13, 11, 6), 2),
-                                          ((13, 11, 6), 6), ((33, 33, 9), 4)])
+                                          ((13, 11, 6), 6), ((33, 33, 9), 4), ((17, 17, 5), 20),
+                                          ((33, 33, 9), 24)])
 @pytest.mark.parametrize("prec,precond", [(0, 0), (1, 0), (1, 1)])
 def test_3d_parity(mlq, dims, cluster, prec, precond):
     mesh, phi, xi, v0, w0 = setup3d(dims, 6, 11, 5)
@@ -72,7 +74,7 @@ def test_3d_parity(mlq, dims, cluster, prec, precond):
     assert rel(r["q_fine"], q_ref) < TOL[prec]
 
 
-@pytest.mark.parametrize("dims,cluster", [((9, 9, 5), 1), ((17, 17, 5), 4), ((33, 33, 9), 4)])
+@pytest.mark.parametrize("dims,cluster", [((9, 9, 5), 1), ((17, 17, 5), 4), ((33, 33, 9), 4), ((33, 33, 9), 24)])
 @pytest.mark.parametrize("prec,precond", [(0, 0), (1, 0), (1, 1)])
 def test_3d_final_state_parity(mlq, dims, cluster, prec, precond):
     # the field v_h(T), w(T) node by node against the oracle (relative to max |v|)
@@ -225,8 +227,9 @@ def test_3d_full_size_block_conserves_mass_weighted_state(mlq):
         ctx.set_initial_state(0, v0, w0)
         ctx.set_profiling(True)
         r = ctx.solve(0, inputs.gaussian_xi(3, 3, 0, S, 2))
-        # the launch the bench times: 16 samples, every cluster resident at once
-        assert ctx.member_profile()[0]["cluster"] in (12, 16)
+        # the launch the bench times: 16 samples, every group resident at once
+        # (clusters, or > 16 CTAs per sample in one cooperative launch)
+        assert ctx.member_profile()[0]["cluster"] >= 12
     assert np.all(r["status"] == 0)
     assert np.max(np.abs(r["q_fine"] - expect)) < 1e-9 * abs(expect)
 
