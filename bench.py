@@ -240,7 +240,8 @@ def load_peaks():
 KERNEL_SOURCES = {"slab_solve_mg_kernel": ("mlq_mg.cuh", "mlq_kernels.cuh", "mlq_reg_inst.cu"),
                   "slab_solve_reg_kernel": ("mlq_kernels.cuh", "mlq_reg_inst.cu"),
                   "slab_solve_kernel": ("mlq_kernels.cuh", "mlq_slab_inst.cu"),
-                  "slab_solve_3d_kernel": ("mlq_3d.cuh", "mlq_3d_types.cuh", "mlq_kernels.cuh", "mlq_3d_inst.cu")}
+                  "slab_solve_3d_kernel": ("mlq_3d.cuh", "mlq_3d_types.cuh", "mlq_groups.cuh", "mlq_kernels.cuh",
+                                           "mlq_3d_inst.cu")}
 
 
 def kernel_source_hash(kernel_key: str) -> str:
@@ -327,12 +328,14 @@ def roofline_3d(mlq, inputs, peaks):
     sec = prof["kernel_ms"] / 1e3
     algo = n * (it * BYTES3D_PER_DOF_ITER["mg"] + S * steps * BYTES3D_PER_DOF_STEP)
     hbm = peaks.get("hbm_gbs", 6800.0)
-    kname = f"slab_solve_3d_kernel<float,{prof['cluster']}>"
+    coop = prof["cluster"] > 16   # CTAs per sample of a cooperative launch
+    kname = "slab_solve_3d_kernel<float,GridGroup>" if coop else f"slab_solve_3d_kernel<float,ClusterGroup<{prof['cluster']}>>"
     traffic = load_traffic(kname, S, steps)
     out = {"bound": "hbm", "achieved": algo / sec / 1e9, "peak": hbm, "unit": "GB/s", "frac": algo / sec / 1e9 / hbm,
            "traffic": traffic, "kernel": kname, "kernel_ms": prof["kernel_ms"],
            "launch": f"{dims[0]}x{dims[1]}x{dims[2]} nodes, {S} samples, {steps} block, {it} CG iterations, "
-                     f"cluster {prof['cluster']}",
+                     + (f"{prof['cluster']} CTAs per sample in one cooperative launch" if coop
+                        else f"cluster {prof['cluster']}"),
            "bytes": f"{BYTES3D_PER_DOF_ITER['mg']:.0f} B per DOF and CG iteration + {BYTES3D_PER_DOF_STEP:.0f} B "
                     "per DOF and block (the streaming 3D multigrid PCG, every array once per pass)",
            "dof_steps_per_s": n * S * steps / sec}
