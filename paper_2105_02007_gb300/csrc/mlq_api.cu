@@ -1014,6 +1014,12 @@ void launch_member_profile_only(mlq_ctx *ctx, const Member &mb, int slot, int co
 }
 
 // Wait for an estimate and combine the per-level FP64 sums on the host.
+bool same_shape(const Shape &a, const Shape &b)
+{
+    return a.cs == b.cs && a.threads == b.threads && a.resident == b.resident && a.smem == b.smem &&
+           a.npt == b.npt && a.mg == b.mg;
+}
+
 int finish_estimate(mlq_ctx *ctx, int L, const int64_t *N, double *mean_out, double *var_out, double *rmse_out)
 {
     MLQ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -1725,12 +1731,22 @@ int mlq_estimate(mlq_ctx *ctx, int L, const int64_t *N, const double *const *xi,
     MLQ_CUDA(ctx, cudaSetDevice(ctx->device));
     ctx->nmembers = 0;
     const int K = ctx->levels[0].K;
+    // With more members than lanes, the two members on the coarsest mesh
+    // (the fine member of pair 0 and the coarse member of pair 1) run as one
+    // launch of N_0 + N_1 samples, when the launch shape is the same for
+    // each alone and for both (every sample is then solved exactly as in
+    // its own member): no member waits for another's lane.
+    const bool merge0 = L >= 1 && 2 * L + 1 > kLanes && N[0] + N[1] <= 65535 &&
+                        same_shape(choose_launch(ctx, ctx->levels[0], N[0]), choose_launch(ctx, ctx->levels[0], N[1])) &&
+                        same_shape(choose_launch(ctx, ctx->levels[0], N[0]),
+                                   choose_launch(ctx, ctx->levels[0], N[0] + N[1]));
     size_t need = 4096;
     for (int l = 0; l <= L; ++l) {
         need += member_bytes(ctx, ctx->levels[l], N[l]);
         if (l > 0) need += member_bytes(ctx, ctx->levels[l - 1], N[l]);
         need += align_up((size_t)N[l] * 8, 256) * 2 + align_up((size_t)N[l] * K * 8, 256);
     }
+    if (merge0) need += member_bytes(ctx, ctx->levels[0], N[0] + N[1]) + align_up((size_t)(N[0] + N[1]) * K * 8, 256);
     int st = ensure_workspace(ctx, need);
     if (st != MLQ_OK) return st;
     char *cur = (char *)ctx->ws;
@@ -1760,6 +1776,31 @@ int mlq_estimate(mlq_ctx *ctx, int L, const int64_t *N, const double *const *xi,
         }
         fine[l].d_xi = coarse[l].d_xi = d_xi;
     }
+    Member m0;   // the merged coarsest-mesh member: samples of pair 0, then of pair 1
+    double *xi01 = nullptr;
+    if (merge0) {
+        m0.level = 0;
+        m0.S = N[0] + N[1];
+        member_carve(ctx, ctx->levels[0], m0, cur);
+        if ((st = carve_check(ctx, cur, (size_t)m0.S * K * 8)) != MLQ_OK) return st;
+        xi01 = (double *)cur;
+        cur += align_up((size_t)m0.S * K * 8, 256);
+        m0.d_xi = xi01;
+        fine[0].q = m0.q;
+        fine[0].iters = m0.iters;
+        fine[0].status = m0.status;
+        coarse[1].q = m0.q + N[0];
+        coarse[1].iters = m0.iters + N[0];
+        coarse[1].status = m0.status + N[0];
+    }
+    // launch order: largest levels first (slot = lane index)
+    std::vector<std::pair<const Member *, int>> order;
+    for (int l = L; l >= 0; --l)
+        for (int k = 0; k < (l > 0 ? 2 : 1); ++k) {
+            if (merge0 && l == 0) continue;
+            if (merge0 && l == 1 && k == 1) order.push_back({&m0, 1});
+            else order.push_back({k == 0 ? &fine[l] : &coarse[l], k});
+        }
     // CUDA graph: capture the whole estimate once, replay while unchanged
     bool use_graph = ctx->opt.graphs != 0 && ctx->stream != nullptr;
     for (int l = 0; l <= L && use_graph; ++l) {
@@ -1779,9 +1820,8 @@ int mlq_estimate(mlq_ctx *ctx, int L, const int64_t *N, const double *const *xi,
         }
         if (ctx->graph_exec && key == ctx->graph_key) {
             ctx->nmembers = 0;
-            for (int l = L, sid = 0; l >= 0; --l)
-                for (int k = 0; k < (l > 0 ? 2 : 1); ++k, ++sid)
-                    if (ctx->profile) launch_member_profile_only(ctx, k == 0 ? fine[l] : coarse[l], sid, k);
+            for (size_t sid = 0; sid < order.size(); ++sid)
+                if (ctx->profile) launch_member_profile_only(ctx, *order[sid].first, (int)sid, order[sid].second);
             MLQ_CUDA(ctx, cudaGraphLaunch(ctx->graph_exec, ctx->stream));
             ctx->launches += ctx->graph_launches;
             return finish_estimate(ctx, L, N, mean_out, var_out, rmse_out);
@@ -1808,6 +1848,13 @@ int mlq_estimate(mlq_ctx *ctx, int L, const int64_t *N, const double *const *xi,
                                                  ctx->capturing ? cudaEventRecordExternal : cudaEventRecordDefault) !=
                             cudaSuccess)
         return abort_capture(MLQ_ECUDA);
+    if (merge0) {   // the merged member's samples, contiguous (inside the capture: replays recopy)
+        if (cudaMemcpyAsync(xi01, fine[0].d_xi, sizeof(double) * N[0] * K, cudaMemcpyDeviceToDevice, ctx->stream) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(xi01 + (size_t)N[0] * K, coarse[1].d_xi, sizeof(double) * N[1] * K,
+                            cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
+            return abort_capture(MLQ_ECUDA);
+    }
     if (cudaEventRecord(ctx->ev_fork, ctx->stream) != cudaSuccess) return abort_capture(MLQ_ECUDA);
     // every member's set-up first (short kernels), joined, then the solves,
     // largest levels first on the higher-priority streams: the finest level
@@ -1815,21 +1862,17 @@ int mlq_estimate(mlq_ctx *ctx, int L, const int64_t *N, const double *const *xi,
     for (int phase : {kSetup, kSolve}) {
         if (phase == kSolve && cudaEventRecord(ctx->ev_fork, ctx->stream) != cudaSuccess)
             return abort_capture(MLQ_ECUDA);
-        int sid = 0;
-        for (int l = L; l >= 0; --l) {
-            for (int k = 0; k < (l > 0 ? 2 : 1); ++k) {
-                // the device has kLanes hardware queues by default: members
-                // past the last lane (the smallest) run in turn on it instead
-                // of sharing a queue with a large member
-                cudaStream_t s = ctx->pool[std::min(sid, kLanes - 1)];
-                if (cudaStreamWaitEvent(s, ctx->ev_fork, 0) != cudaSuccess) return abort_capture(MLQ_ECUDA);
-                st = launch_member(ctx, k == 0 ? fine[l] : coarse[l], s, sid, k, phase);
-                if (st != MLQ_OK) return abort_capture(st);
-                if (cudaEventRecord(ctx->ev_join[sid], s) != cudaSuccess ||
-                    cudaStreamWaitEvent(ctx->stream, ctx->ev_join[sid], 0) != cudaSuccess)
-                    return abort_capture(MLQ_ECUDA);
-                ++sid;
-            }
+        for (int sid = 0; sid < (int)order.size(); ++sid) {
+            // the device has kLanes hardware queues by default: members
+            // past the last lane (the smallest) run in turn on it instead
+            // of sharing a queue with a large member
+            cudaStream_t s = ctx->pool[std::min(sid, kLanes - 1)];
+            if (cudaStreamWaitEvent(s, ctx->ev_fork, 0) != cudaSuccess) return abort_capture(MLQ_ECUDA);
+            st = launch_member(ctx, *order[sid].first, s, sid, order[sid].second, phase);
+            if (st != MLQ_OK) return abort_capture(st);
+            if (cudaEventRecord(ctx->ev_join[sid], s) != cudaSuccess ||
+                cudaStreamWaitEvent(ctx->stream, ctx->ev_join[sid], 0) != cudaSuccess)
+                return abort_capture(MLQ_ECUDA);
         }
     }
     for (int l = 0; l <= L; ++l) {
