@@ -30,6 +30,16 @@ constexpr int kMgMaxLevels = 8;
 constexpr float kMgOmega = 0.7f;   // lambda_max(D^-1 A) <= 2.5 on every level: omega lambda < 2
 constexpr int kMgGatherM = 17;        // gather levels of at most this many nodes per side
 constexpr int kMgCoarsestSweeps = 6;  // damped Jacobi sweeps on the coarsest level
+// The hierarchy stops at the last level with at least kMgCoarsestM nodes per
+// side (9 for a level of that size itself; levels of 9^2 and less keep the
+// whole hierarchy down to 3^2).  At the time steps of the MLMC
+// levels dt / h^2 is at most ~1 on a 17^2 coarse level, so the mass matrix
+// dominates A there and six damped Jacobi sweeps nearly solve it; every
+// coarser level only lengthened the V-cycle's chain of dependent passes
+// (measured: the 257^2 and 129^2 members 12 % faster, 65^2 15 %, 33^2 13 %,
+// with as many or fewer CG iterations; a 17^2 level keeps 9^2 below it,
+// without which its iterations rose by 60 %).
+constexpr int kMgCoarsestM = 17;
 constexpr int kMgWarpM = 9;           // levels of at most this many nodes per side run on one warp
 
 // Conductivity of an element as (d11, d12, d22).
@@ -61,6 +71,7 @@ struct MgLevelPlan {
 
 struct MgPlan {
     int nl;          // levels (0: no valid layout)
+    int sweeps;      // damped Jacobi sweeps on the coarsest level
     int gather;      // first local level
     int warp_level;  // first level run by one warp (nl: none)
     int total;   // bytes
@@ -84,10 +95,13 @@ __host__ __device__ inline void mg_band(int m0, int cs, int rank, int c, int *R0
     *R1 = r1;
 }
 
-__host__ __device__ inline MgPlan mg_plan(int m0, int cs)
+__host__ __device__ inline MgPlan mg_plan(int m0, int cs, int gather_m = kMgGatherM, int min_m = 0,
+                                          int sweeps = kMgCoarsestSweeps)
 {
     MgPlan pl;
     pl.nl = 0;
+    pl.sweeps = sweeps;
+    if (min_m <= 0) min_m = m0 > kMgCoarsestM ? kMgCoarsestM : (m0 > 9 ? 9 : 3);
     pl.gather = 0;
     pl.warp_level = 0;
     pl.total = 0;
@@ -104,7 +118,7 @@ __host__ __device__ inline MgPlan mg_plan(int m0, int cs)
         }
         if (!local) {
             if (c == 0 && rmin < 1) return pl;  // a rank without fine rows
-            if (c > 0 && (m <= kMgGatherM || rmin < 1)) {
+            if (c > 0 && (m <= gather_m || rmin < 1)) {
                 local = true;
                 pl.gather = c;
             }
@@ -117,7 +131,7 @@ __host__ __device__ inline MgPlan mg_plan(int m0, int cs)
         L.csize = 1 + (rows + 1) * m;
         L.tile = 1 + (rows + 2) * m + 1;
         pl.nl = c + 1;
-        if (m < 5 || (m - 1) % 2) break;
+        if (m < 5 || (m - 1) % 2 || (m + 1) / 2 < min_m) break;
         m = (m + 1) / 2;
     }
     // a cluster needs a local coarsest level (the coarsest sweeps are local)
@@ -451,7 +465,7 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1)
     };
     // coarsest level (held whole): damped Jacobi sweeps, ping-pong XA / XB;
     // the result is in XB after an odd number of swaps, else in XA
-    const int coarse_res = (kMgCoarsestSweeps - 1) % 2 ? plan.lv[NL - 1].off_xb : plan.lv[NL - 1].off_xa;
+    const int coarse_res = (plan.sweeps - 1) % 2 ? plan.lv[NL - 1].off_xb : plan.lv[NL - 1].off_xa;
     auto coarsest = [&](bool wm) {
         const int lt = wm ? (tid & 31) : tid, lnt = wm ? 32 : nt;
         const MgLevelPlan &P = plan.lv[NL - 1];
@@ -460,7 +474,7 @@ __global__ void __launch_bounds__(NPT >= 12 ? 384 : 512, 1)
         const float *bb = F_(P.off_b);
         float *X = F_(P.off_xa), *Y = F_(P.off_xb);
         for (int l = lt; l < nown_c; l += lnt) X[base + l] = __fdividef(kMgOmega * bb[l], Dd[base + l]);
-        for (int k = 1; k < kMgCoarsestSweeps; ++k) {
+        for (int k = 1; k < plan.sweeps; ++k) {
             bar(wm, false);
             for (int l = lt; l < nown_c; l += lnt) {
                 const int t = base + l;
