@@ -362,6 +362,18 @@ int mlq_mesh_solve_opts(mlq_mesh *mesh, const mlq_model *model, const mlq_option
                         const double *v0, const double *w0, int64_t S, const double *xi, double *q_out,
                         int32_t *status, int32_t *iters);
 
+/* Self-test of the barrier and sums that the cooperative launch shapes use
+ * (many CTAs per sample, meeting in global memory): one cooperative launch
+ * of `ctas` CTAs (1..64) on `device` through `rounds` barrier-and-sum rounds
+ * (1..1000), every CTA checking the exact sum; `missing` (0..64) CTAs are
+ * counted in the group but never launched, so with missing > 0 no barrier
+ * completes.  Every wait gives up after `max_polls` polls (>= 1; a poll is
+ * ~0.1-0.2 us): the kernel then records the time-out, returns without
+ * completing, and the device stays usable.  Returns MLQ_OK (every barrier
+ * completed, every sum exact), MLQ_ETIMEOUT (a wait ran out), MLQ_EINVAL
+ * (bad arguments, or a wrong sum), MLQ_ECUDA / MLQ_ENOMEM. */
+int mlq_group_selftest(int device, int ctas, int rounds, int missing, int64_t max_polls);
+
 /* Solve S samples (0 <= S <= 65535) on `level`.  xi: host or device, S x K row-major FP64
  * (sample s uses xi[s*K .. s*K+K-1]).  For each sample: synthesise theta
  * (eq. KLlowrank), set up A = M + dt K(theta), run the nsteps time blocks,

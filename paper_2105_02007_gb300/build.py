@@ -22,7 +22,7 @@ INCLUDE = os.path.join(ROOT, "include")
 SOURCES = ([("mlq_api.cu", [], "mlq_api"), ("mlq_kl.cpp", [], "mlq_kl"), ("mlq_3d_inst.cu", ["-DMLQ_F64=0"], "mlq_3d_f32"),
             ("mlq_3d_inst.cu", ["-DMLQ_F64=1"], "mlq_3d_f64"),
             ("mlq_mesh.cu", [], "mlq_mesh"), ("mlq_estimator.cpp", [], "mlq_estimator"),
-            ("mlq_locate.cu", [], "mlq_locate")]
+            ("mlq_locate.cu", [], "mlq_locate"), ("mlq_selftest.cu", [], "mlq_selftest")]
            + [("mlq_reg_inst.cu", [f"-DMLQ_CS={cs}"], f"mlq_reg_cs{cs}") for cs in (1, 2, 4, 8, 16)]
            + [("mlq_slab_inst.cu", [f"-DMLQ_F64={f}"], f"mlq_slab_f{64 if f else 32}") for f in (0, 1)])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -44,6 +44,7 @@ struct GridGroup {
     unsigned *bar;    // [S][2]: arrivals, generation (zero before the launch)
     double *part;     // [S][2][G][4]: CTA totals of the two alternating sums
     int *err;         // set to 1 when a wait runs out
+    long long limit = kGridWaitLimit;   // polls before a wait gives up
     __device__ int rank() const { return blockIdx.x % G; }
     __device__ int size() const { return G; }
     __device__ int sample() const { return blockIdx.x / G; }
@@ -71,7 +72,7 @@ struct GridGroup {
                 } else {
                     long long it = 0;
                     while (*vgen == g0) {
-                        if (++it > kGridWaitLimit) {
+                        if (++it > limit) {
                             atomicExch(err, 1);
                             atomicExch(gen, 0xffffffffu);
                             ok = 0;

@@ -22,7 +22,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 MLQ_FP64, MLQ_MIXED = 0, 1
-MLQ_EINVAL, MLQ_ENOMEM, MLQ_EUNSUPPORTED = -1, -2, -6
+MLQ_EINVAL, MLQ_ENOMEM, MLQ_ETIMEOUT, MLQ_EUNSUPPORTED = -1, -2, -5, -6
 S_CONVERGED, S_MAXITER, S_NONFINITE, S_CANCELLED = 0, 1, 2, 3
 
 
@@ -74,6 +74,7 @@ _lib.mlq_set_options.argtypes = [_vp, ctypes.POINTER(Options)]
 _lib.mlq_set_model.argtypes = [_vp, ctypes.POINTER(Model)]
 _lib.mlq_add_level.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_double, ctypes.c_int32]
 _lib.mlq_add_level_mesh.argtypes = [_vp, ctypes.c_int, _i64, _vp, _i64, _vp, _vp, ctypes.c_double, ctypes.c_int32]
+_lib.mlq_group_selftest.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i64]
 _lib.mlq_set_initial_state.argtypes = [_vp, ctypes.c_int, _vp, _vp]
 _lib.mlq_set_initial_disk.argtypes = [_vp, ctypes.c_int, ctypes.c_double]
 _lib.mlq_set_kl.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp]
@@ -125,7 +126,7 @@ _lib.mlq_last_cuda_error.restype = ctypes.c_char_p
 _lib.mlq_last_cuda_error.argtypes = [_vp]
 
 EXPORTED = ["mlq_default_options", "mlq_default_model", "mlq_default_scheme", "mlq_set_scheme", "mlq_create", "mlq_destroy", "mlq_set_options",
-            "mlq_set_model", "mlq_add_level", "mlq_add_level_mesh", "mlq_set_initial_state", "mlq_set_initial_disk", "mlq_set_kl",
+            "mlq_set_model", "mlq_add_level", "mlq_add_level_mesh", "mlq_group_selftest", "mlq_set_initial_state", "mlq_set_initial_disk", "mlq_set_kl",
             "mlq_build_kl", "mlq_centroid_table", "mlq_build_kl_mesh", "mlq_p1_at_points", "mlq_p1_at_points_gpu", "mlq_mesh_create",
             "mlq_mesh_destroy", "mlq_mesh_set_kl", "mlq_mesh_solve", "mlq_mesh_solve_opts", "mlq_mlmc_allocation", "mlq_mlmc_combine", "mlq_pimped_ml_combine", "mlq_estimate_adaptive", "mlq_field_prolong", "mlq_field_norms", "mlq_solve", "mlq_solve_state", "mlq_set_points", "mlq_solve_points", "mlq_trace_prolong",
             "mlq_time_norms", "mlq_estimate", "mlq_workspace_bytes",
@@ -219,6 +220,12 @@ def centroid_table(m_fine, modes_f: np.ndarray, m_coarse) -> np.ndarray:
     _check(_lib.mlq_centroid_table(dim, fd.ctypes.data_as(_vp), pm, K, cd.ctypes.data_as(_vp),
                                    phi.ctypes.data_as(_vp)), "mlq_centroid_table")
     return phi
+
+
+def group_selftest(ctas: int, rounds: int, missing: int = 0, max_polls: int = 1 << 16, device: int = 0) -> int:
+    """mlq_group_selftest: the status code (MLQ_OK = 0, MLQ_ETIMEOUT when a
+    barrier wait ran out)."""
+    return int(_lib.mlq_group_selftest(device, ctas, rounds, missing, max_polls))
 
 
 def _mesh_args(xyz, conn):

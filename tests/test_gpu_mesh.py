@@ -253,3 +253,25 @@ def test_mesh_level_cooperative_shape_chosen_and_captured(mlq):
     assert cps > 16
     assert np.array_equal(res[0], res[1])
     assert np.array_equal(res[0], q_two)
+
+
+def test_group_barrier_times_out_and_the_device_stays_usable(mlq):
+    # the global-memory barrier of the cooperative shapes: exact sums over
+    # many rounds; a group that counts a CTA which is never launched makes
+    # the wait run out (nothing sets the flag it waits for): the call reports
+    # MLQ_ETIMEOUT and the next launches and a solve work as before
+    assert mlq.group_selftest(ctas=16, rounds=50) == 0
+    assert mlq.group_selftest(ctas=1, rounds=3) == 0
+    assert mlq.group_selftest(ctas=8, rounds=5, missing=1, max_polls=20000) == mlq.MLQ_ETIMEOUT
+    assert mlq.group_selftest(ctas=16, rounds=10) == 0
+    xyz, conn = LV.lv_mesh(2, 8, 14)
+    frames, alpha = LV.lv_fibres(xyz, conn)
+    mesh = O.unstructured_mesh(xyz, conn)
+    modes, _ = O.kl_build(mesh, 0.09, 0.15 ** 2, 4)
+    phi = O.centroid_table_unrelated(mesh, modes, mesh)
+    v0, w0 = LV.stimulus(xyz, radius=0.4)
+    xi = inputs.gaussian_xi(44, 0, 0, 2, 4)
+    with mlq.MeshLevel(xyz, conn, frames) as lvl:
+        lvl.set_kl(phi, alpha)
+        q, st, _ = lvl.solve(xi, 0.05, 3, v0, w0, precision=0, cluster=24)
+    assert np.all(st == 0) and np.all(np.isfinite(q))
