@@ -284,12 +284,19 @@ MeshShape mesh_member_shape(const mlq_mesh *m, int64_t S, int request)
     int nsm = 1;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device);
     // one cluster of 16 per sample leaves SMs idle: spread each sample over
-    // the resident CTAs instead, >= 2048 rows per CTA
+    // up to min(resident CTAs / S, n / 2048) CTAs; when that many CTAs
+    // outnumber the SMs, take k SMs' worth (k = 2, else 1) so that every SM
+    // holds the same number of CTAs and no barrier waits for a CTA that
+    // shares its SM
     const int64_t res = mesh_resident_ctas(m->device);
-    const int64_t G = std::min<int64_t>(res / S, m->n / 2048);
-    if (16 * S < 2LL * nsm && G > 16) {
-        sh.G = (int)G;
-        return sh;
+    if (16 * S < 2LL * nsm) {
+        const int64_t cap = std::min<int64_t>(res / S, m->n / 2048);
+        int64_t G = cap;
+        if (cap * S > nsm) G = 2LL * nsm / S <= cap ? 2LL * nsm / S : nsm / S;
+        if (G > 16) {
+            sh.G = (int)G;
+            return sh;
+        }
     }
     while (sh.cs < 16 && (int64_t)(2 * sh.cs) * S <= 2LL * nsm && m->n / (2 * sh.cs) >= 4096) sh.cs *= 2;
     while (sh.cs > 1 && m->n / sh.cs < 64) sh.cs /= 2;
