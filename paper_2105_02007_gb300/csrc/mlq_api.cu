@@ -809,6 +809,7 @@ int launch_member3d_t(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream
 int launch_member_mesh(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStream_t st, int slot, int phase)
 {
     const mlq::MeshShape sh = mlq::mesh_member_shape(L.mesh, mb.S, ctx->opt.cluster);
+    if (sh.cs < 1) return MLQ_EUNSUPPORTED;   // the requested CTAs per sample cannot all be resident
     const bool timed = ctx->profile && slot >= 0 && slot < kStreams && (phase & kSolve);
     const unsigned evf = ctx->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (phase & kSetup) {
