@@ -95,3 +95,39 @@ def test_field_qoi_multilevel_mean_matches_the_oracle(mlq):
     # the level difference is small against the field in H1(D)
     y1 = np.mean([f - P(c) for f, c in zip(f1, c1)], axis=0)
     assert mlq.field_norms(MS[2], y1)[1] < mlq.field_norms(MS[2], mean)[1]
+
+
+def test_five_level_estimate_with_the_coarsest_members_merged(mlq):
+    # five levels give nine members on eight lanes: the two members on the
+    # coarsest mesh (pair 0's fine, pair 1's coarse) run as one launch; each
+    # sample must come out exactly as in its own member (mlq_solve per
+    # level), and the estimate as eq. StandardML of the oracle's solves
+    ms, dts, T5 = [5, 9, 17, 33, 65], [0.4, 0.2, 0.1, 0.05, 0.025], 2.0
+    N = [48, 24, 12, 6, 4]
+    fine = O.mesh2d(ms[-1])
+    modes, _ = O.kl_build(fine, 0.09, 0.04, K)
+    meshes = [O.mesh2d(m) for m in ms]
+    phis = [O.centroid_table(fine, modes, mm) for mm in meshes]
+    xis = [inputs.gaussian_xi(46, l, 0, N[l], K) for l in range(5)]
+    with mlq.Context(0, mlq.MLQ_MIXED) as ctx:
+        for l, (m, dt, ph) in enumerate(zip(ms, dts, phis)):
+            ctx.add_level(l, m, dt, int(round(T5 / dt)))
+            ctx.set_kl(l, ph)
+        ctx.set_profiling(True)
+        mean, var, rmse, ys = ctx.estimate(xis, return_y=True)
+        members = ctx.member_profile()
+        ctx.set_profiling(False)
+        direct = [ctx.solve(l, xis[l], with_coarse=l > 0)["y"] for l in range(5)]
+    # eight launches: the 5^2 mesh's two members ran as one of N_0 + N_1 samples
+    assert len(members) == 8
+    assert any(m["level"] == 0 and m["samples"] == N[0] + N[1] for m in members)
+    for l in range(5):
+        assert np.array_equal(ys[l], direct[l]), l
+    yref = []
+    for l in range(5):
+        qf = O.solve_batch(meshes[l], phis[l], xis[l], dts[l], int(round(T5 / dts[l])), nthreads=4)[0]
+        qc = (O.solve_batch(meshes[l - 1], phis[l - 1], xis[l], dts[l - 1], int(round(T5 / dts[l - 1])),
+                            nthreads=4)[0] if l else 0.0)
+        yref.append(qf - qc)
+    est_ref = sum(float(np.mean(y)) for y in yref)
+    assert abs(mean - est_ref) <= 1e-6 * abs(est_ref)
