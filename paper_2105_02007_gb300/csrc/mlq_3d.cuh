@@ -18,20 +18,21 @@
 // couplings to P + d for the seven such directions d (slot = dx + 2 dy + 4 dz);
 // the coupling to P - d is slot d of node P - d (the matrices are symmetric).
 //
-// Solver (one sample per cluster of CS CTAs, everything in global memory and
-// L2; the 3D levels outgrow the shared memory of a cluster):
+// Solver (one sample per group of CTAs: a cluster, or many CTAs of one
+// cooperative launch (mlq_groups.cuh); everything in global memory and L2,
+// the 3D levels outgrow the shared memory of a cluster):
 //   per time block  y = v + dt R(v, w); b = M y; w <- w + dt eps (v - gam w);
 //                   r = b - A v in FP64 from the guess v extrapolated
 //                   from the last block solutions (guess_order)
-//   inner solve     Jacobi-preconditioned CG (Chronopoulos-Gear: one cluster
-//                   reduction per iteration) on A d = r / ||r|| from d = 0 in
-//                   the inner precision TI, v += ||r|| d; the mixed path
-//                   repeats while ||b - A v|| > rtol ||b|| (iterative
-//                   refinement in FP64), the FP64 path runs one sweep to that
-//                   tolerance
+//   inner solve     CG preconditioned by a multigrid V-cycle (mixed path) or
+//                   Jacobi, in Chronopoulos-Gear form (one group reduction
+//                   per iteration), on A d = r / ||r|| from d = 0 in the
+//                   inner precision TI, v += ||r|| d; the mixed path repeats
+//                   while ||b - A v|| > rtol ||b|| (iterative refinement in
+//                   FP64), the FP64 path runs one sweep to that tolerance
 //   QoI             Q = sum_P m_P v_P with the lumped mass m = M 1.
 // CTA `rank` owns the grid lines j0 <= j < j1 of every plane k (on every
-// level); another CTA's values are read through L2 (ld.cg) after a cluster
+// level); another CTA's values are read through L2 (ld.cg) after a group
 // barrier.
 #pragma once
 

@@ -1,6 +1,7 @@
 // mlq_mesh.cu -- levels on general tetrahedral meshes (non-nested
-// hierarchies, Sec. 4 and Sec. 5.4): a first GPU member for meshes that are
-// not structured boxes.
+// hierarchies, Sec. 4 and Sec. 5.4): the GPU member for meshes that are not
+// structured boxes, standalone (mlq_mesh_*) or as a level of a context
+// (mlq_add_level_mesh, through mlq_mesh_member.h).
 //
 // Per sample s and time block, as for the structured levels (Sec. 3.1-3.3):
 //   theta_e = theta_mean_e + sum_k Phi[e, k] xi_k                 (eq. KLlowrank)
@@ -11,8 +12,9 @@
 // The CSR values of A are gathered per nonzero over the element entries
 // that add to it (a list fixed by the mesh), so every sum has a fixed order.
 // The time blocks run in one launch of mesh_slab_kernel (mlq_mesh_solver.cuh):
-// one sample per cluster, FP64 Jacobi-PCG or FP32 inner PCG inside FP64
-// refinement, with no host synchronisation inside the solve.
+// one sample per cluster of CTAs, or per group of many CTAs in one
+// cooperative launch (mlq_groups.cuh), FP64 Jacobi-PCG or FP32 inner PCG
+// inside FP64 refinement, with no host synchronisation inside the solve.
 #include "mlq.h"
 #include "mlq_launch.cuh"
 #include "mlq_mesh_member.h"
