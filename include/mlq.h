@@ -194,9 +194,11 @@ int mlq_add_level(mlq_ctx *ctx, int level, int dim, const int32_t *dims, const d
  * solver (as mlq_mesh_solve_opts: Jacobi-PCG, FP64 or FP32 inside FP64
  * refinement by the context's precision, rtol, rtol_inner, max_iter,
  * max_sweeps; cluster requests 6 and 12 take 4 and 8; precond, storage and
- * threads do not apply).  mlq_solve_state, mlq_set_points, mlq_synthesize,
- * mlq_autotune and mlq_submit return MLQ_EUNSUPPORTED on such a level; the
- * paper's time discretization (mlq_set_scheme) is for 2D levels.
+ * threads do not apply).  mlq_set_points / mlq_solve_points record the point
+ * QoIs on such a level (a point's tetrahedron by the rule of
+ * mlq_p1_at_points).  mlq_solve_state, mlq_synthesize, mlq_autotune and
+ * mlq_submit return MLQ_EUNSUPPORTED on such a level; the paper's time
+ * discretization (mlq_set_scheme) is for 2D levels.
  * MLQ_EINVAL for bad sizes, indices or a degenerate tetrahedron. */
 int mlq_add_level_mesh(mlq_ctx *ctx, int level, int64_t n, const double *xyz, int64_t ne, const int32_t *conn,
                        const double *frames, double dt, int32_t nsteps);
@@ -411,7 +413,10 @@ int mlq_solve_state(mlq_ctx *ctx, int level, int64_t S, const double *xi, double
  * threshold u_th.  Each point is located once: the simplex of the mesh
  * convention holding it (the first of its cell; the cell whose lower corner
  * is floor(x / h)) and its barycentric weights, so u(x_p, t) is the P1 value
- * of v_h(t) there.  MLQ_EINVAL for a point outside the domain.
+ * of v_h(t) there; on a general-mesh level (mlq_add_level_mesh, dim 3) the
+ * first tetrahedron of the mesh holding it (mlq_p1_at_points' rule).
+ * MLQ_EINVAL for a point outside the domain (general mesh: a barycentric
+ * coordinate below -1e-9 in the best tetrahedron).
  *
  * mlq_solve_points: S samples xi (host or device, S x K) on `level`, the
  * same kernels and launch shape as mlq_solve.  Outputs (host or device; any

@@ -9,6 +9,7 @@
 #include "mlq_aux.cuh"
 #include "mlq_kl_tc.cuh"
 #include "mlq_launch.cuh"
+#include "mlq_host.h"
 #include "mlq_mesh_member.h"
 
 #include <algorithm>
@@ -62,6 +63,7 @@ struct Level {
     // its solver, and the node coordinates for the initial disk
     mlq_mesh *mesh = nullptr;
     std::vector<double> xyz_h;
+    std::vector<int32_t> conn_h;   // ne x 4, for point location
     // point QoIs (mlq_set_points): simplex nodes and barycentric weights
     int npts = 0;
     double u_th = 0.0;
@@ -820,7 +822,7 @@ int launch_member_mesh(mlq_ctx *ctx, const Level &L, const Member &mb, cudaStrea
     if (!(phase & kSolve)) return MLQ_OK;
     if (timed) MLQ_CUDA(ctx, cudaEventRecordWithFlags(ctx->ev_t0[slot], st, evf));
     MLQ_CUDA(ctx, mlq::mesh_member_launch(L.mesh, ctx->model, ctx->opt, L.dt, L.nsteps, L.d_v0, L.d_w0, mb.S, mb.d_xi,
-                                          mb.mws, sh, ctx->d_err, st, false, true));
+                                          mb.mws, sh, ctx->d_err, st, false, true, &mb.pq));
     if (timed) MLQ_CUDA(ctx, cudaEventRecordWithFlags(ctx->ev_t1[slot], st, evf));
     ctx->launches++;
     return MLQ_OK;
@@ -1292,6 +1294,7 @@ int mlq_add_level_mesh(mlq_ctx *ctx, int level, int64_t n, const double *xyz, in
     L.dt = dt;
     L.nsteps = nsteps;
     L.xyz_h.assign(xyz, xyz + (size_t)n * 3);
+    L.conn_h.assign(conn, conn + (size_t)ne * 4);
     const int su = upload_mesh_disk(L);
     if (su != MLQ_OK) {
         release_level(L);
@@ -1641,12 +1644,26 @@ int mlq_set_points(mlq_ctx *ctx, int level, int np, const double *pts, double u_
     MLQ_GUARD(ctx);
     if (!ctx || level < 0 || level >= kMaxLevels || !ctx->levels[level].defined) return MLQ_EINVAL;
     if (np < 0 || np > mlq::kMaxPoints || (np > 0 && !pts) || !std::isfinite(u_th)) return MLQ_EINVAL;
-    if (ctx->levels[level].mesh) return MLQ_EUNSUPPORTED;
     Level &L = ctx->levels[level];
     std::vector<int> nd(4 * (size_t)std::max(np, 1));
     std::vector<double> wt(4 * (size_t)std::max(np, 1));
-    for (int p = 0; p < np; ++p)
-        if (!locate_point(L, pts + (size_t)p * L.dim, &nd[4 * p], &wt[4 * p])) return MLQ_EINVAL;
+    if (L.mesh) {
+        // general mesh: the first tetrahedron holding each point; a point
+        // whose best tetrahedron still has a barycentric coordinate below
+        // -1e-9 lies outside the mesh
+        std::vector<int64_t> el((size_t)std::max(np, 1));
+        const int sl = mlq::locate_points(3, (int64_t)L.n, L.xyz_h.data(), (int64_t)L.ne, L.conn_h.data(), np, pts,
+                                          el.data(), wt.data());
+        if (sl != MLQ_OK) return sl;
+        for (int p = 0; p < np; ++p)
+            for (int a = 0; a < 4; ++a) {
+                if (!(wt[4 * p + a] >= -1e-9)) return MLQ_EINVAL;
+                nd[4 * p + a] = L.conn_h[(size_t)el[(size_t)p] * 4 + a];
+            }
+    } else {
+        for (int p = 0; p < np; ++p)
+            if (!locate_point(L, pts + (size_t)p * L.dim, &nd[4 * p], &wt[4 * p])) return MLQ_EINVAL;
+    }
     MLQ_CUDA(ctx, cudaSetDevice(ctx->device));
     MLQ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     cudaFree(L.d_pt_node);

@@ -5,6 +5,7 @@
 // C++ on the host.  The per-sample synthesis from these modes (eq. KLlowrank)
 // is kernel K1.
 #include "mlq.h"
+#include "mlq_host.h"
 
 #include <algorithm>
 #include <array>
@@ -447,10 +448,19 @@ double barycentric_of(const SimplexMesh &m, int64_t e, const double *x, double *
     return mn;
 }
 
-int p1_at_points(int dim, int64_t n, const double *xyz, int64_t ne, const int32_t *conn, int K, const double *f,
-                 int64_t np, const double *pts, double *out)
+}  // namespace
+
+namespace mlq {
+
+// The simplex of a general mesh holding each point and the point's
+// barycentric coordinates there: the first simplex, in element order, that
+// contains the point (bucket grid over the node bounding box); a point in
+// no simplex takes the first simplex whose smallest coordinate is within
+// 1e-12 of the largest over all simplices.  elem: np, lam: np x (dim + 1).
+int locate_points(int dim, int64_t n, const double *xyz, int64_t ne, const int32_t *conn, int64_t np,
+                  const double *pts, int64_t *elem, double *lam_out)
 {
-    if (!mesh_ok(dim, n, xyz, ne, conn) || K < 1 || np < 0 || (np > 0 && (!f || !pts || !out))) return MLQ_EINVAL;
+    if (!mesh_ok(dim, n, xyz, ne, conn) || np < 0 || (np > 0 && (!pts || !elem || !lam_out))) return MLQ_EINVAL;
     const SimplexMesh m{dim, n, ne, xyz, conn};
     const int nv = dim + 1;
     // buckets: a uniform grid over the node bounding box; each lists, in
@@ -529,12 +539,35 @@ int p1_at_points(int dim, int64_t n, const double *xyz, int64_t ne, const int32_
                         std::memcpy(best_lam, lam, sizeof(lam));
                     }
             }
+            elem[p] = best;
+            for (int a = 0; a < nv; ++a) lam_out[p * nv + a] = best_lam[a];
+        }
+    });
+    return MLQ_OK;
+}
+
+}  // namespace mlq
+
+namespace {
+
+int p1_at_points(int dim, int64_t n, const double *xyz, int64_t ne, const int32_t *conn, int K, const double *f,
+                 int64_t np, const double *pts, double *out)
+{
+    if (!mesh_ok(dim, n, xyz, ne, conn) || K < 1 || np < 0 || (np > 0 && (!f || !pts || !out))) return MLQ_EINVAL;
+    const int nv = dim + 1;
+    std::vector<int64_t> elem((size_t)std::max<int64_t>(np, 1));
+    std::vector<double> lam((size_t)std::max<int64_t>(np, 1) * nv);
+    const int st = mlq::locate_points(dim, n, xyz, ne, conn, np, pts, elem.data(), lam.data());
+    if (st != MLQ_OK) return st;
+    parallel_chunks((np + 1023) / 1024, [&](int64_t c) {
+        const int64_t p0 = c * 1024, p1 = std::min(np, p0 + 1024);
+        for (int64_t p = p0; p < p1; ++p)
             for (int k = 0; k < K; ++k) {
                 double v = 0.0;
-                for (int a = 0; a < nv; ++a) v += best_lam[a] * f[(int64_t)conn[best * nv + a] * K + k];
+                for (int a = 0; a < nv; ++a)
+                    v += lam[(size_t)p * nv + a] * f[(int64_t)conn[elem[(size_t)p] * nv + a] * K + k];
                 out[p * K + k] = v;
             }
-        }
     });
     return MLQ_OK;
 }

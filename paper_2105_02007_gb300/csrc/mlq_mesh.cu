@@ -346,7 +346,7 @@ MeshWs mesh_member_carve(const mlq_mesh *m, bool mixed, int64_t S, const MeshSha
 cudaError_t mesh_member_launch(const mlq_mesh *m, const mlq_model &model, const mlq_options &opt, double dt,
                                int nsteps, const double *d_v0, const double *d_w0, int64_t S, const double *d_xi,
                                const MeshWs &ws, const MeshShape &sh, int *err, cudaStream_t st, bool setup,
-                               bool solve)
+                               bool solve, const PointArgs *points)
 {
     if (sh.cs < 1 || (sh.G > 0 && (!ws.bar || !ws.part || !err))) return cudaErrorInvalidValue;
     if (S <= 0) return cudaSuccess;
@@ -370,13 +370,16 @@ cudaError_t mesh_member_launch(const mlq_mesh *m, const mlq_model &model, const 
         const cudaError_t e = cudaMemsetAsync(ws.bar, 0, (size_t)S * 2 * sizeof(unsigned), st);
         if (e != cudaSuccess) return e;
     }
+    const PointArgs pq = points ? *points : PointArgs{0, nullptr, nullptr, 0.0, nullptr, nullptr};
     if (mixed) {
-        const mlq::MeshArgs<float> a = mesh_args<float>(m, &model, opt, dt, nsteps, S, ws.aval, ws.a32, d_v0, d_w0, ws.v,
-                                                        ws.w, ws.b, ws.y, ws.vec, ws.q, ws.iters, ws.status);
+        mlq::MeshArgs<float> a = mesh_args<float>(m, &model, opt, dt, nsteps, S, ws.aval, ws.a32, d_v0, d_w0, ws.v, ws.w,
+                                                  ws.b, ws.y, ws.vec, ws.q, ws.iters, ws.status);
+        a.pq = pq;
         return sh.G > 0 ? launch_mesh_grid<float>(a, grp, st) : launch_mesh<float>(sh.cs, a, st);
     }
-    const mlq::MeshArgs<double> a = mesh_args<double>(m, &model, opt, dt, nsteps, S, ws.aval, ws.aval, d_v0, d_w0, ws.v,
-                                                      ws.w, ws.b, ws.y, ws.vec, ws.q, ws.iters, ws.status);
+    mlq::MeshArgs<double> a = mesh_args<double>(m, &model, opt, dt, nsteps, S, ws.aval, ws.aval, d_v0, d_w0, ws.v, ws.w,
+                                                ws.b, ws.y, ws.vec, ws.q, ws.iters, ws.status);
+    a.pq = pq;
     return sh.G > 0 ? launch_mesh_grid<double>(a, grp, st) : launch_mesh<double>(sh.cs, a, st);
 }
 

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include "mlq.h"
+#include "mlq_points.cuh"
 
 namespace mlq {
 
@@ -51,9 +52,10 @@ MeshWs mesh_member_carve(const mlq_mesh *m, bool mixed, int64_t S, const MeshSha
 // null) are device pointers; results in ws.q, ws.iters, ws.status.  setup:
 // the KL synthesis and CSR assembly; solve: the block loop (one launch).
 // err (device int) is set when a wait of the cooperative shape times out.
+// points (may be null): point QoIs recorded after every block.
 cudaError_t mesh_member_launch(const mlq_mesh *m, const mlq_model &model, const mlq_options &opt, double dt,
                                int nsteps, const double *d_v0, const double *d_w0, int64_t S, const double *d_xi,
                                const MeshWs &ws, const MeshShape &sh, int *err, cudaStream_t st, bool setup = true,
-                               bool solve = true);
+                               bool solve = true, const PointArgs *points = nullptr);
 
 }  // namespace mlq

@@ -46,6 +46,7 @@ struct MeshArgs {
     TI *r, *u, *wv, *s, *p, *x, *dinv;   // [S][n] inner vectors
     double *q;                    // [S]
     int32_t *iters, *status;      // [S]
+    PointArgs pq;                 // point QoIs (npts = 0: none)
 };
 
 // Rows of a CSR product handled by groups of 8 lanes: each group takes two
@@ -122,6 +123,9 @@ __global__ void __launch_bounds__(512, 2) mesh_slab_kernel(MeshArgs<TI> g, Grp g
         Dinv[i] = (TI)1 / Ai[g.diag[i]];
     }
     grp.sync();
+    PointState pst;
+    const bool pth = rank == 0 && tid < g.pq.npts;   // point QoI threads
+    if (pth) point_record(g.pq, sample, g.nsteps, g.dt, v, pst);
 
     int par = 0;
     int64_t total_iters = 0;
@@ -276,7 +280,9 @@ __global__ void __launch_bounds__(512, 2) mesh_slab_kernel(MeshArgs<TI> g, Grp g
             break;
         }
         if (!solved && status == S_CONVERGED) status = S_MAXITER;
+        if (pth) point_record(g.pq, sample, g.nsteps, dt, v, pst);
     }
+    if (pth) point_finish(g.pq, sample, g.nsteps, pst);
 
     double qacc[1] = {0.0};
     for (int i = r0 + tid; i < r1; i += nt) qacc[0] += g.lump[i] * v[i];

@@ -486,8 +486,9 @@ class Context:
 
     def set_points(self, level: int, pts, u_th: float):
         """Point QoIs of `level` at pts (np x dim) with threshold u_th (mlq_set_points)."""
-        p = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3 if isinstance(self.levels[level]["m"],
-                                                                                    (tuple, list)) else 2)
+        lv = self.levels[level]
+        dim = 3 if lv.get("mesh") or isinstance(lv["m"], (tuple, list)) else 2
+        p = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, dim)
         _check(_lib.mlq_set_points(self._h, level, p.shape[0], p.ctypes.data_as(_vp) if p.size else None,
                                    float(u_th)), "mlq_set_points", self._h)
         self.levels[level]["npts"] = p.shape[0]

@@ -220,6 +220,57 @@ def test_general_levels_in_the_context(mlq, prec):
         assert abs(var[l] - v_ref) <= 2.0 * np.sqrt(v_ref) * d * N[l] / (N[l] - 1) + 2.0 * d * d * N[l] / (N[l] - 1)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_point_qois_on_a_general_level(mlq, prec):
+    # the point QoIs of Sec. 2.4 on a shell level of a context: traces
+    # u(x_p, t_n) element by element against the oracle (FP64 1e-10, mixed
+    # 1e-6 of max |u|) and activation times within the bound a trace error
+    # gives them; the points do not change the solve
+    xyz, conn = LV.lv_mesh(2, 8, 14)
+    mesh = O.unstructured_mesh(xyz, conn)
+    rng = np.random.default_rng(71)
+    phi = rng.normal(scale=0.3, size=(conn.shape[0], 4))
+    xi = inputs.gaussian_xi(44, 0, 0, 3, 4)
+    v0, w0 = LV.stimulus(xyz, radius=0.4)
+    # slower diffusion than the default (s_l = 0.01, s_t = 0.002) so that the
+    # excitation travels over the shell within T = 30
+    dt, nb, th = 0.5, 60, 0.5
+    model = dict(s_l=0.01, s_t=0.002)
+    # element centroids: in the stimulus, outside it at rising distance, the
+    # farthest one, and a mesh node
+    cen = xyz[conn].mean(axis=1)
+    vc = v0[conn].mean(axis=1)
+    out = np.nonzero(vc == 0)[0]
+    near = out[np.argsort(np.linalg.norm(cen[out] - cen[np.argmax(vc)], axis=1))]
+    pts = np.vstack([cen[np.argmax(vc)], cen[near[0]], cen[near[len(near) // 8]], cen[near[len(near) // 3]],
+                     cen[near[-1]], xyz[conn[5, 2]]])
+    tr, act, q, st = O.solve_points(mesh, phi, xi, dt, nb, pts, th, v0=v0, w0=w0, model=model)
+    assert np.all(st == 0)
+    assert np.any(act == 0) and np.any(act > 0) and np.any(act < 0)
+    with mlq.Context(0, prec) as ctx:
+        ctx.set_model(**model)
+        ctx.add_level_mesh(0, xyz, conn, dt, nb)
+        ctx.set_kl(0, phi)
+        ctx.set_initial_state(0, v0, w0)
+        ctx.set_points(0, pts, th)
+        r = ctx.solve_points(0, xi)
+        plain = ctx.solve(0, xi)
+        with pytest.raises(mlq.MLQError):
+            ctx.set_points(0, np.array([[9.0, 9.0, 9.0]]), th)
+    assert np.all(r["status"] == 0)
+    assert np.array_equal(r["q"], plain["q_fine"])
+    tol = 1e-10 if prec == 0 else 1e-6
+    scale = np.max(np.abs(tr))
+    assert np.max(np.abs(r["trace"] - tr)) <= tol * scale
+    assert np.array_equal(r["act"] < 0, act < 0) or prec == 1
+    for s_, p_ in zip(*np.nonzero((act >= 0) & (r["act"] >= 0))):
+        u = tr[s_, p_]
+        n = max(1, int(np.ceil(act[s_, p_] / dt - 1e-9)))
+        du = max(u[n] - u[n - 1], 1e-300)
+        assert abs(r["act"][s_, p_] - act[s_, p_]) <= dt * 4 * tol * scale / du + 1e-12 or \
+            abs(u[n] - th) <= 10 * tol * scale, (s_, p_)
+
+
 def test_mesh_level_cooperative_shape_chosen_and_captured(mlq):
     # one or two samples on a ~49k-node shell: the chosen shape spreads each
     # sample over more CTAs than a cluster holds (a cooperative launch); its
