@@ -549,8 +549,7 @@ int mlq_autotune(mlq_ctx *ctx, int level, int64_t S, const double *xi, int probe
  * without waiting; synchronize the stream before reading q.
  *
  * The first call on a device looks up the device address of the scratch
- * array (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture begins.  Every call uses the same array and
+ * array (cudaGetSymbolAddress) with that device current.  Every call uses the same array and
  * leaves its contents behind; the kernels initialise everything they read,
  * so results do not depend on earlier calls.  Calls whose work overlaps on
  * the GPU (other streams, other host threads) race on the array: order them
