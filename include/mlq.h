@@ -196,8 +196,10 @@ int mlq_add_level(mlq_ctx *ctx, int level, int dim, const int32_t *dims, const d
  * max_sweeps; cluster requests 6 and 12 take 4 and 8; precond, storage and
  * threads do not apply).  mlq_set_points / mlq_solve_points record the point
  * QoIs on such a level (a point's tetrahedron by the rule of
- * mlq_p1_at_points).  mlq_solve_state, mlq_synthesize, mlq_autotune and
- * mlq_submit return MLQ_EUNSUPPORTED on such a level; the paper's time
+ * mlq_p1_at_points); mlq_solve_state returns its final state and
+ * mlq_synthesize its KL table (FP64 in both precisions, the general-mesh
+ * solver's synthesis).  mlq_autotune and mlq_submit return
+ * MLQ_EUNSUPPORTED on such a level; the paper's time
  * discretization (mlq_set_scheme) is for 2D levels.
  * MLQ_EINVAL for bad sizes, indices or a degenerate tetrahedron. */
 int mlq_add_level_mesh(mlq_ctx *ctx, int level, int64_t n, const double *xyz, int64_t ne, const int32_t *conn,
@@ -396,7 +398,8 @@ int mlq_solve(mlq_ctx *ctx, int level, int64_t S, const double *xi, int with_coa
  * itself, the P1 nodal values of v_h(T) and of the recovery variable w(T).
  * xi: host or device, S x K.  Outputs (host or device; any may be NULL):
  *   v_out, w_out  S x n FP64, sample-major (v_out[s*n + i], node order of
- *                 the mesh convention above);
+ *                 the mesh convention above; on a general-mesh level the
+ *                 order of its xyz);
  *   q_out         S FP64, Q = m^T v(T) (as mlq_solve's q_fine);
  *   status        S int32 (mlq_sample_status).
  * A sample that met NaN/Inf stops early and its state is undefined.  Blocks
@@ -476,7 +479,9 @@ int mlq_estimate_adaptive(mlq_ctx *ctx, int L, double eps, int64_t n_pilot, cons
  * = (cos 2 theta, sin 2 theta) of element e (host or device, FP64).  The mixed
  * path computes theta on the tensor cores (tcgen05, TF32 operands split into
  * high and low parts, ~21-bit products, FP32 accumulation); the FP64 path on
- * the CUDA cores in FP64.  MLQ_ETIMEOUT if a bounded device wait ran out. */
+ * the CUDA cores in FP64 (on a general-mesh level both paths run the
+ * general-mesh solver's FP64 synthesis).  MLQ_ETIMEOUT if a bounded device
+ * wait ran out. */
 int mlq_synthesize(mlq_ctx *ctx, int level, int64_t S, const double *xi, double *cs2_out);
 
 /* Bytes of device workspace a solve of S samples on `level` (and level-1

@@ -1043,7 +1043,39 @@ int finish_estimate(mlq_ctx *ctx, int L, const int64_t *N, double *mean_out, dou
 
 namespace {
 void serve_stop(mlq_ctx *ctx);  // stops and frees the serving worker (below)
+
+// mlq_synthesize on a general-mesh level: the member's set-up phase (the
+// general-mesh solver's FP64 synthesis kernel, then its CSR assembly) on
+// the context's stream, and a copy of its (cos 2 theta, sin 2 theta) table
+// ([S][n_elem][2] FP64, the layout of the structured levels' output).
+int synthesize_mesh(mlq_ctx *ctx, int level, int64_t S, const double *xi, double *cs2_out)
+{
+    const Level &L = ctx->levels[level];
+    size_t need = 0;
+    int st = mlq_workspace_bytes(ctx, level, S, 0, &need);
+    if (st != MLQ_OK) return st;
+    if ((st = ensure_workspace(ctx, need)) != MLQ_OK) return st;
+    ctx->nmembers = 0;
+    char *cur = (char *)ctx->ws;
+    Member mf;
+    mf.level = level;
+    mf.S = S;
+    member_carve(ctx, L, mf, cur);
+    cur += align_up((size_t)S * 8, 256) + 256 + align_up((size_t)S * 4, 256);  // as mlq_solve's carve
+    const double *d_xi = xi;
+    if ((st = carve_check(ctx, cur, is_device_ptr(xi) ? 0 : (size_t)S * L.K * 8)) != MLQ_OK) return st;
+    if (!is_device_ptr(xi)) {
+        double *dx = (double *)cur;
+        MLQ_CUDA(ctx, cudaMemcpyAsync(dx, xi, sizeof(double) * S * L.K, cudaMemcpyHostToDevice, ctx->stream));
+        d_xi = dx;
+    }
+    mf.d_xi = d_xi;
+    if ((st = launch_member(ctx, mf, ctx->stream, -1, 0, kSetup)) != MLQ_OK) return st;
+    if ((st = copy_out(ctx, cs2_out, mf.mws.cs2, (size_t)S * L.ne * 16, ctx->stream)) != MLQ_OK) return st;
+    MLQ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return check_err(ctx);
 }
+}  // namespace
 
 // ===========================================================================
 // C ABI
@@ -1403,9 +1435,9 @@ int mlq_synthesize(mlq_ctx *ctx, int level, int64_t S, const double *xi, double 
     MLQ_GUARD(ctx);
     if (!ctx || !xi || !cs2_out || S < 1 || S > 65535) return MLQ_EINVAL;
     if (check_level(ctx, level) != MLQ_OK) return MLQ_EINVAL;
-    if (ctx->levels[level].mesh) return MLQ_EUNSUPPORTED;
     MLQ_CUDA(ctx, cudaSetDevice(ctx->device));
     const Level &L = ctx->levels[level];
+    if (L.mesh) return synthesize_mesh(ctx, level, S, xi, cs2_out);
     const size_t out_b = align_up((size_t)S * L.ne * 16, 256), xi_b = align_up((size_t)S * L.K * 8, 256);
     int st = ensure_workspace(ctx, out_b + xi_b);
     if (st != MLQ_OK) return st;
@@ -1516,7 +1548,6 @@ int mlq_solve_state(mlq_ctx *ctx, int level, int64_t S, const double *xi, double
     MLQ_GUARD(ctx);
     if (!ctx || !xi || S < 0 || S > 65535) return MLQ_EINVAL;
     if (check_level(ctx, level) != MLQ_OK) return MLQ_EINVAL;
-    if (ctx->levels[level].mesh) return MLQ_EUNSUPPORTED;
     if (S == 0) return MLQ_OK;
     MLQ_CUDA(ctx, cudaSetDevice(ctx->device));
     ctx->nmembers = 0;
@@ -1547,12 +1578,13 @@ int mlq_solve_state(mlq_ctx *ctx, int level, int64_t S, const double *xi, double
     MLQ_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_join[0], 0));
     // where the kernels leave the state after the last block: the ring kernels
     // (multigrid and 3D) keep v_j in buffer j mod kVRing, the others update v
-    // in place; w alternates between two buffers, one per block
-    const size_t SN = (size_t)S * stored(L);
-    const bool ring = L.dim == 3 || choose_launch(ctx, L, S).mg;
-    const double *vfin = mf.v + (ring ? (size_t)(L.nsteps % mlq::kVRing) * SN : 0);
-    const double *wfin = mf.w + (size_t)(L.nsteps & 1) * SN;
-    if (L.dim == 3) {
+    // in place; w alternates between two buffers, one per block.  The
+    // general-mesh solver updates both in place ([S][n] FP64).
+    const size_t SN = (size_t)S * (L.mesh ? (size_t)L.n : stored(L));
+    const bool ring = !L.mesh && (L.dim == 3 || choose_launch(ctx, L, S).mg);
+    const double *vfin = L.mesh ? mf.mws.v : mf.v + (ring ? (size_t)(L.nsteps % mlq::kVRing) * SN : 0);
+    const double *wfin = L.mesh ? mf.mws.w : mf.w + (size_t)(L.nsteps & 1) * SN;
+    if (L.dim == 3 && !L.mesh) {
         // the real entries of every padded row, S x my x mz rows of mx
         const mlq::Grid3 &g = L.g3;
         const size_t rows = (size_t)S * g.my * g.mz;

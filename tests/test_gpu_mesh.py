@@ -188,7 +188,7 @@ def test_general_levels_in_the_context(mlq, prec):
         mean, var, rmse, ys = ctx.estimate(xis, return_y=True)
         # the structured-only calls refuse a general level
         with pytest.raises(mlq.MLQError) as e:
-            ctx.solve_state(2, xis[2])
+            ctx.autotune(2, xis[2])
         assert e.value.code == mlq.MLQ_EUNSUPPORTED
     assert np.all(r["status"] == 0)
     for l, key in ((2, "q_fine"), (1, "q_coarse")):
@@ -218,6 +218,37 @@ def test_general_levels_in_the_context(mlq, prec):
         # sample moves by at most d (the unbiased estimator, N_l >= 2)
         v_ref = float(np.var(ref_y[l], ddof=1))
         assert abs(var[l] - v_ref) <= 2.0 * np.sqrt(v_ref) * d * N[l] / (N[l] - 1) + 2.0 * d * d * N[l] / (N[l] - 1)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_state_and_synthesis_on_a_general_level(mlq, prec):
+    # the field QoI (v_h(T), w(T) node by node) and the KL table (eq.
+    # KLlowrank, FP64 on this solver in both precisions) of a shell level of
+    # a context, against the oracle; Q of the state call equals mlq_solve's
+    xyz, conn = LV.lv_mesh(2, 8, 14)
+    mesh = O.unstructured_mesh(xyz, conn)
+    rng = np.random.default_rng(72)
+    phi = rng.normal(scale=0.3, size=(conn.shape[0], 4))
+    alpha = rng.uniform(-1.0, 1.0, size=conn.shape[0])
+    xi = inputs.gaussian_xi(45, 0, 0, 4, 4)
+    v0, w0 = LV.stimulus(xyz, radius=0.4)
+    dt, nb = 0.05, 10
+    q_ref, V, W, st = O.solve_states(mesh, phi, xi, dt, nb, v0=v0, w0=w0, theta_mean=alpha)
+    assert np.all(st == 0)
+    with mlq.Context(0, prec) as ctx:
+        ctx.add_level_mesh(0, xyz, conn, dt, nb)
+        ctx.set_kl(0, phi, alpha)
+        ctx.set_initial_state(0, v0, w0)
+        r = ctx.solve_state(0, xi)
+        plain = ctx.solve(0, xi)
+        cs2 = ctx.synthesize(0, xi)
+    assert np.all(r["status"] == 0)
+    assert np.array_equal(r["q"], plain["q_fine"])
+    tol = 1e-10 if prec == 0 else 1e-6
+    assert np.max(np.abs(r["v"] - V)) <= tol * np.max(np.abs(V))
+    assert np.max(np.abs(r["w"] - W)) <= tol * np.max(np.abs(W)) + tol * np.max(np.abs(V))
+    assert np.max(np.abs(r["q"] - q_ref) / np.abs(q_ref)) <= tol
+    assert np.max(np.abs(cs2 - O.kl_synthesis(phi, xi, alpha))) < 1e-13
 
 
 @pytest.mark.parametrize("prec", [0, 1])
