@@ -198,9 +198,9 @@ int mlq_add_level(mlq_ctx *ctx, int level, int dim, const int32_t *dims, const d
  * QoIs on such a level (a point's tetrahedron by the rule of
  * mlq_p1_at_points); mlq_solve_state returns its final state and
  * mlq_synthesize its KL table (FP64 in both precisions, the general-mesh
- * solver's synthesis).  mlq_autotune and mlq_submit return
- * MLQ_EUNSUPPORTED on such a level; the paper's time
- * discretization (mlq_set_scheme) is for 2D levels.
+ * solver's synthesis); mlq_submit serves requests on it beside those of
+ * structured levels.  mlq_autotune returns MLQ_EUNSUPPORTED on such a
+ * level; the paper's time discretization (mlq_set_scheme) is for 2D levels.
  * MLQ_EINVAL for bad sizes, indices or a degenerate tetrahedron. */
 int mlq_add_level_mesh(mlq_ctx *ctx, int level, int64_t n, const double *xyz, int64_t ne, const int32_t *conn,
                        const double *frames, double dt, int32_t nsteps);

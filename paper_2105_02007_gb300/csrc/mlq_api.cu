@@ -2618,7 +2618,7 @@ int64_t serve_form(mlq_ctx *ctx, Server &sv, std::vector<ServePart> &parts, int 
     for (uint64_t id : sv.order) {
         ServeReq &r = *sv.reqs.at(id);
         if (!r.finished && !r.in_flight &&
-            (!ctx->levels[r.level].defined || !ctx->levels[r.level].d_phi || ctx->levels[r.level].K != r.K))
+            (check_level(ctx, r.level) != MLQ_OK || ctx->levels[r.level].K != r.K))
             serve_finish(r, 0, MLQ_EINVAL);
     }
     // one batch per level on the device at a time: a level that already runs
@@ -2806,7 +2806,6 @@ try {
     {
         MLQ_GUARD(ctx);
         if (check_level(ctx, req->level) != MLQ_OK || ctx->levels[req->level].K < 1) return MLQ_EINVAL;
-        if (ctx->levels[req->level].mesh) return MLQ_EUNSUPPORTED;
         r->K = ctx->levels[req->level].K;
         if (!ctx->server.load()) {
             Server *sv = serve_create(ctx);

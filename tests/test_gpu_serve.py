@@ -114,6 +114,39 @@ def test_serve_3d_level(mlq):
     assert abs(r["mean"] - q.mean()) <= 1e-12 * abs(q.mean())
 
 
+def test_serve_general_mesh_level_beside_a_structured_one(mlq):
+    # a level on a general tetrahedral mesh (the shell) and a structured 2D
+    # level in one context: requests on both are served together and each
+    # mean equals the direct solves' (the launch shape follows the batch
+    # size: equal to rounding)
+    from paper_2105_02007_gb300 import lv_inputs as LV
+
+    xyz, conn = LV.lv_mesh(2, 8, 14)
+    frames, alpha = LV.lv_fibres(xyz, conn)
+    rng = np.random.default_rng(73)
+    phi = rng.normal(scale=0.3, size=(conn.shape[0], K))
+    v0, w0 = LV.stimulus(xyz, radius=0.4)
+    fine = O.mesh2d(17)
+    modes, _ = O.kl_build(fine, 0.09, 0.04, K)
+    xs = inputs.gaussian_xi(46, 0, 0, 40, K)
+    xm = inputs.gaussian_xi(47, 1, 0, 24, K)
+    with mlq.Context(0, mlq.MLQ_MIXED) as ctx:
+        ctx.add_level(0, 17, 0.05, 20)
+        ctx.set_kl(0, O.centroid_table(fine, modes, fine))
+        ctx.add_level_mesh(1, xyz, conn, 0.05, 8, frames=frames)
+        ctx.set_kl(1, phi, alpha)
+        ctx.set_initial_state(1, v0, w0)
+        tm = ctx.submit(1, xm, 0.0, 8)
+        ts = ctx.submit(0, xs, 0.0, 8)
+        rm, rs = ctx.wait(tm), ctx.wait(ts)
+        qm = ctx.solve(1, xm)["q_fine"]
+        qs = ctx.solve(0, xs)["q_fine"]
+    assert rm["status"] == 0 and rs["status"] == 0
+    assert rm["samples_used"] == 24 and rs["samples_used"] == 40
+    assert abs(rm["mean"] - qm.mean()) <= 1e-10 * abs(qm.mean())
+    assert abs(rs["mean"] - qs.mean()) <= 1e-10 * abs(qs.mean())
+
+
 def test_serve_rejects_bad_requests(mlq):
     with make_ctx(mlq) as ctx:
         xi = inputs.gaussian_xi(1, 0, 0, 8, K)
