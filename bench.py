@@ -342,8 +342,9 @@ def roofline_3d(mlq, inputs, peaks):
     if traffic:
         out["dram_gbs"] = traffic / sec / 1e9
         out["dram_frac"] = traffic / sec / 1e9 / hbm
-    # the survey's count for a 3D Jacobi-PCG iteration (88 B per DOF, the
-    # upper end of its 64-88 B), which leaves out the multigrid's passes
+    # the streaming count of a matrix-free 3D Jacobi-PCG iteration (88 B per
+    # DOF: 48 B of fibre coefficients, 8 B product, 32 B update), which
+    # leaves out the multigrid's passes
     jac = n * (it * 88.0 + S * steps * BYTES3D_PER_DOF_STEP)
     out["jacobi_pcg_count"] = {"bytes_per_dof_iter": 88.0, "achieved": jac / sec / 1e9, "frac": jac / sec / 1e9 / hbm}
     return out
