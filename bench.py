@@ -433,6 +433,49 @@ def level3_dt(l):
     return 0.05 * 0.5 ** l
 
 
+def run_case_mesh(spec: str):
+    """One general-mesh solve on a synthetic left-ventricle shell:
+    --case-mesh shell=M,samples=S,steps=N[,precision=fp64|mixed][,K=8][,cluster=C].
+    Shell M is one of the four preset resolutions (~20k .. 1.3M nodes) with
+    helix fibres; dt = 0.1 2^-M; a random KL table of K modes (scale 0.2).
+    After a warm-up solve, times one solve on the host clock (the call
+    returns when the results are on the host) and prints the time, CG
+    iterations and time per iteration.  For profiling the general-mesh
+    kernel with ncu."""
+    kv = dict(item.split("=") for item in spec.split(",")) if spec else {}
+    shell = int(kv.get("shell", 3))
+    S = int(kv.get("samples", 1))
+    steps = int(kv.get("steps", 1))
+    K = int(kv.get("K", 8))
+    prec_name = kv.get("precision", "fp64")
+    cluster = int(kv.get("cluster", 0))
+    from paper_2105_02007_gb300 import build, inputs
+    from paper_2105_02007_gb300 import lv_inputs as LV
+
+    build.build()
+    from paper_2105_02007_gb300 import mlq
+
+    prec = mlq.MLQ_MIXED if prec_name == "mixed" else mlq.MLQ_FP64
+    xyz, conn, frames, alpha = LV.lv_level(shell)
+    rng = np.random.default_rng(5)
+    phi = rng.normal(scale=0.2, size=(conn.shape[0], K))
+    v0, w0 = LV.stimulus(xyz, radius=0.4)
+    xi = inputs.gaussian_xi(45, shell, 0, S, K)
+    dt = 0.1 * 2.0 ** -shell
+    with mlq.MeshLevel(xyz, conn, frames) as lvl:
+        lvl.set_kl(phi, alpha)
+        lvl.solve(xi, dt, steps, v0, w0, precision=prec, cluster=cluster)    # warm-up
+        t0 = time.perf_counter()
+        q, st, it = lvl.solve(xi, dt, steps, v0, w0, precision=prec, cluster=cluster)
+        sec = time.perf_counter() - t0
+    iters = int(np.sum(it))
+    print(json.dumps({"case_mesh": spec, "nodes": int(xyz.shape[0]), "tets": int(conn.shape[0]), "seconds": sec,
+                      "cg_iterations": iters, "us_per_iteration": 1e6 * sec / max(iters, 1),
+                      "dof_steps_per_s": xyz.shape[0] * S * steps / sec, "q0": float(q[0]),
+                      "status": [int(x) for x in st[:4]]}))
+    return 0 if np.all(st == 0) else 1
+
+
 def run_case3d(spec: str):
     """One 3D member solve: --case3d level=L,samples=S,steps=N[,precision=mixed|fp64][,K=16].
     KL modes of c = 0.09 exp(-|x-y|^2 / 0.15^2) on the level's own mesh.
@@ -705,6 +748,8 @@ def main():
                          "against 1390 ms per estimate)")
     ap.add_argument("--case", default=None, help="profile one member solve, e.g. level=4,samples=1,steps=4")
     ap.add_argument("--case3d", default=None, help="one 3D member solve, e.g. level=2,samples=8,steps=2")
+    ap.add_argument("--case-mesh", default=None, nargs="?", const="",
+                    help="one general-mesh solve on a ventricle shell, e.g. shell=3,samples=1,steps=1")
     ap.add_argument("--serve", default=None, help="serving stream, e.g. rate=50,requests=200,levels=0-2")
     ap.add_argument("--c5", default=None, nargs="?", const="",
                     help="non-nested estimate on the ventricle shells, e.g. T=0.1,K=128,N=1-4-16-64,precision=fp64")
@@ -715,6 +760,8 @@ def main():
         return run_case(args.case)
     if args.case3d:
         return run_case3d(args.case3d)
+    if args.case_mesh is not None:
+        return run_case_mesh(args.case_mesh)
     if args.serve:
         return run_serve(args.serve)
     if args.c3 is not None:
