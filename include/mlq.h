@@ -608,8 +608,8 @@ int mlq_level_launch(mlq_ctx *ctx, int level, int *cluster, int *threads, int *r
  *
  * Each sample's Q depends only on its own xi, and the stopping rule only on
  * the values in index order, so a request's result does not depend on what
- * it was batched with (bit for bit on the 2D levels; the 3D launch shape
- * follows the batch size, so there to rounding).  xi is copied at submission
+ * it was batched with (bit for bit on the 2D levels; the launch shapes of
+ * 3D and general-mesh levels follow the batch size, so there to rounding).  xi is copied at submission
  * (host pointer).  A request whose level is redefined or gets a KL table of
  * another K before it is served finishes with MLQ_EINVAL.  mlq_submit /
  * mlq_poll may be called from any thread; the worker takes the context's
