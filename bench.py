@@ -371,7 +371,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": desc},
+            "config": {"workload": WORKLOAD, "levels": LEVEL_M, "samples": LEVEL_N, "K": K_MODES,
+                       "dof_steps_per_step": dof_steps_per_estimate(), "precision": "fp64", "sample": desc},
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": smp["threads"], "kind": "oracle", "sample": desc},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
