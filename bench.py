@@ -350,6 +350,47 @@ def roofline_3d(mlq, inputs, peaks):
     return out
 
 
+def run_reference_full(setup):
+    """The reference arm over the whole workload, once: every sample of every
+    level pair over the whole horizon (about 3.7e9 DOF-steps: an hour or more
+    of host time).  Prints the measured rate, the time of each member, and
+    the oracle's estimate of eq. StandardML with its per-level variances."""
+    from paper_2105_02007_gb300 import inputs
+
+    O, meshes, phis = setup
+    threads = O.max_threads()
+    members, ys = [], []
+    t_all = 0.0
+    for l in range(len(LEVEL_M)):
+        xi = inputs.gaussian_xi(0, l, 0, LEVEL_N[l], K_MODES)
+        qs = []
+        for coarse, lm in enumerate([l, l - 1] if l > 0 else [l]):
+            t0 = time.perf_counter()
+            q, it, st = O.solve_batch(meshes[lm], phis[lm], xi, level_dt(lm), level_steps(lm), nthreads=threads)
+            el = time.perf_counter() - t0
+            t_all += el
+            qs.append(q)
+            members.append(dict(level=l, coarse=coarse, mesh=LEVEL_M[lm], samples=LEVEL_N[l],
+                                blocks=level_steps(lm), seconds=el, cg_iterations=int(np.sum(it)),
+                                worst_status=int(np.max(st))))
+            sys.stderr.write(f"[reference full] pair {l} {'coarse' if coarse else 'fine'}: {el:.1f} s\n")
+            sys.stderr.flush()
+        ys.append(qs[0] - qs[1] if l > 0 else qs[0])
+    est, var, rmse = O.mlmc_estimate(ys)
+    dof = dof_steps_per_estimate()
+    desc = "the whole workload: every sample of every level pair over the whole horizon, FP64 CSR Jacobi-PCG, OpenMP over samples"
+    line = {"impl": "reference", "metric": METRIC, "value": dof / t_all, "unit": UNIT, "n_gpus": 1, "steps": 1,
+            "warmup": 0, "ms_per_step": 1000.0 * t_all, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "levels": LEVEL_M, "samples": LEVEL_N, "K": K_MODES,
+                       "dof_steps_per_step": dof, "precision": "fp64", "sample": desc},
+            "cpu_baseline": {"value": dof / t_all, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
+            "e2e": {"value": dof / t_all, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "estimate": est, "var_l": [float(v) for v in var], "rmse": rmse, "members": members}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     """The reference arm: the oracle as it stands on the host cores, every
     step a bounded sample of the workload (one sample per host thread on every
@@ -359,6 +400,8 @@ def run_reference(args):
     if rank != 0:
         return 0
     setup = _oracle_setup()
+    if args.full:
+        return run_reference_full(setup)
     frac = 0.01 * min(1.0, 8.0 / max(1, args.warmup + args.steps))
     vals = []
     for k in range(args.warmup + args.steps):
@@ -732,6 +775,8 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mlq", choices=["mlq", "reference"])
+    ap.add_argument("--full", action="store_true",
+                    help="with --impl reference: the oracle over the whole workload, once (an hour or more)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=1,
                     help="timed plain-FP64 estimates on the same xi (0: skip)")
