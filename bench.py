@@ -426,6 +426,12 @@ def run_reference_full(setup):
     return 0
 
 
+def step_groups(M: int, K: int):
+    """The members (indices 0 .. M-1) each of K timed steps runs: step j
+    takes j, j + K, j + 2K, ... when K <= M, else member j mod M."""
+    return [list(range(j, M, K)) if K <= M else [j % M] for j in range(K)]
+
+
 def run_reference(args):
     """The reference arm: the oracle as it stands on the host cores.  The
     members of the bounded sample (oracle_members) are spread over the timed
@@ -446,8 +452,8 @@ def run_reference(args):
     for k in range(args.warmup):
         time_member(setup, dict(members[k % M]))
     rates, step_s = {}, []
-    for j in range(K):
-        group = [members[i] for i in range(j, M, K)] if K <= M else [members[j % M]]
+    for idx in step_groups(M, K):
+        group = [members[i] for i in idx]
         t = 0.0
         for mb in group:
             r = time_member(setup, dict(mb))

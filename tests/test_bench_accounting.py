@@ -1,7 +1,8 @@
 """The benchmark's bookkeeping, on the CPU: the unit count of the metric
 (DOF-steps of one five-level estimate), the scaling of captured DRAM traffic
-to a launch, the issue-rate ceiling and the clock record parsed from
-nvidia-smi samples.  Each is checked against numbers worked out by hand."""
+to a launch, the issue-rate ceiling, the members and extrapolation of the
+oracle's bounded sample, and the clock record parsed from nvidia-smi
+samples.  Each is checked against numbers worked out by hand."""
 import json
 import os
 
@@ -73,6 +74,34 @@ def test_issue_ceiling(tmp_path, monkeypatch):
     assert r["achieved_inst_per_s"] == pytest.approx(2e9)
     assert r["peak_inst_per_s"] == pytest.approx(1.216e12)
     assert r["frac"] == pytest.approx(2e9 / 1.216e12)
+
+
+def test_oracle_sample_members_and_extrapolation():
+    # nine members (level 0 alone, then fine and coarse of pairs 1-4); pairs
+    # 0-1 over the whole horizon, the others over max(40, 1 %) of their
+    # blocks; with one rate r for every member the extrapolated whole
+    # workload takes its DOF-steps / r
+    pytest.importorskip("oracle")
+    mem = bench.oracle_members(0)
+    assert [(m["level"], m["coarse"], m["mesh"]) for m in mem] == [
+        (0, 0, 0), (1, 0, 1), (1, 1, 0), (2, 0, 2), (2, 1, 1), (3, 0, 3), (3, 1, 2), (4, 0, 4), (4, 1, 3)]
+    assert [m["blocks"] for m in mem] == [100, 200, 100, 40, 40, 40, 40, 40, 40]
+    assert all(m["xi"].shape == (m["samples"], bench.K_MODES) for m in mem)
+    rates = {(m["level"], m["coarse"]): 2.5e6 for m in mem}
+    assert bench.whole_workload_seconds(rates) == pytest.approx(bench.dof_steps_per_estimate() / 2.5e6)
+
+
+@pytest.mark.parametrize("M,K", [(9, 1), (9, 4), (9, 9), (9, 20)])
+def test_reference_steps_cover_every_member(M, K):
+    g = bench.step_groups(M, K)
+    assert len(g) == K
+    seen = sorted(i for idx in g for i in idx)
+    assert set(seen) == set(range(M))
+    if K <= M:
+        assert seen == list(range(M))                       # each member once
+        assert max(map(len, g)) - min(map(len, g)) <= 1     # balanced steps
+    else:
+        assert all(len(idx) == 1 for idx in g)
 
 
 class _Done:
