@@ -1,7 +1,7 @@
 """Test infrastructure: the plain FP64 CPU oracle.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
-leg may import this package.  It shares no code with the CUDA path; the only
+leg and reference arm (``--impl reference``) may import this package.  It shares no code with the CUDA path; the only
 thing both sides take from a common module are the seeded sample points
 (``paper_2105_02007_gb300.inputs``), which hold none of the method's
 arithmetic.

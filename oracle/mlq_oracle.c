@@ -5,8 +5,8 @@
  * the stochastic monodomain equation (Ben Bader, Harbrecht, Krause, Multerer,
  * Quaglino, Schmidlin, "Space-time multilevel quadrature methods and their
  * application for cardiac electrophysiology", arXiv 2105.02007).  Only the
- * test suite, the smoke check and the benchmark's CPU-baseline leg may load
- * this library.  It shares no code, header or table with the CUDA path.
+ * test suite, the smoke check and the benchmark's CPU-baseline leg and
+ * reference arm may load this library.  It shares no code, header or table with the CUDA path.
  *
  * Every step follows the paper's definitions directly:
  *   - P1 Lagrange spaces on nested simplicial meshes            (Sec. 3.1)
