@@ -2,6 +2,8 @@
 Monte Carlo driver (pilot samples, variances, sample allocation of eq.
 StandardML, top-up) and a field-valued QoI (the state v_h(T)) with the
 nested intergrid transfer, against the oracle on the same seeded inputs."""
+import os
+
 import numpy as np
 import pytest
 
@@ -131,3 +133,55 @@ def test_five_level_estimate_with_the_coarsest_members_merged(mlq):
         yref.append(qf - qc)
     est_ref = sum(float(np.mean(y)) for y in yref)
     assert abs(mean - est_ref) <= 1e-6 * abs(est_ref)
+
+
+def read_five_level_golden():
+    """(estimate, V_l, [Y_l per sample]) of tests/golden/mlmc_2d_5levels_oracle_y.txt."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "mlmc_2d_5levels_oracle_y.txt")
+    est, var, ys = None, None, []
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#"):
+                continue
+            w = line.split()
+            if w[0] == "estimate":
+                est = float(w[1])
+            elif w[0] == "var":
+                var = [float(x) for x in w[1:]]
+            elif w[0] == "level":
+                ys.append([])
+            elif w[0] != "rmse":
+                ys[-1].append(float(w[0]))
+    return est, var, [np.array(y) for y in ys]
+
+
+def test_full_five_level_estimate_matches_the_oracle_sample_by_sample(mlq):
+    # the whole five-level 2D workload (17^2 .. 257^2 nodes, 4096 / 1024 /
+    # 256 / 64 / 16 samples, K = 16, dt_l = 0.1 2^-l over T = 10) in the
+    # mixed path, fed the oracle's KL tables: every sample's Y_l against the
+    # oracle's (tests/golden, written from the oracle alone over every
+    # sample and the whole horizon).  Each Q within 1e-6 relative bounds a
+    # Y_l within d = 2e-6 max |Q|; max |Q| is taken from the level-0 values,
+    # which are Q_0 (the coarsest mesh gives the largest Q here), with a 1 %
+    # margin
+    est_ref, var_ref, ys_ref = read_five_level_golden()
+    ms, N = [17, 33, 65, 129, 257], [4096, 1024, 256, 64, 16]
+    assert [y.size for y in ys_ref] == N
+    fine = O.mesh2d(ms[-1])
+    modes, _ = O.kl_build(fine, 0.09, 0.04, 16)
+    phis = [O.centroid_table(fine, modes, O.mesh2d(m)) for m in ms]
+    xis = [inputs.gaussian_xi(0, l, 0, N[l], 16) for l in range(5)]
+    with mlq.Context(0, mlq.MLQ_MIXED) as ctx:
+        for l, m in enumerate(ms):
+            ctx.add_level(l, m, 0.1 * 0.5 ** l, 100 * 2 ** l)
+            ctx.set_kl(l, phis[l])
+        mean, var, rmse, ys = ctx.estimate(xis, return_y=True)
+    d = 2e-6 * 1.01 * float(np.max(np.abs(ys_ref[0])))
+    for l in range(5):
+        assert np.max(np.abs(ys[l] - ys_ref[l])) <= d, l
+        # each deviation from the mean moves by at most 2 d, so the unbiased
+        # sample variance moves by at most (4 d sum |y_i - m| + 4 d^2 n) /
+        # (n - 1) <= (4 d sqrt(n (n - 1) V) + 4 d^2 n) / (n - 1)
+        n = N[l]
+        assert abs(var[l] - var_ref[l]) <= (4 * d * np.sqrt(n * (n - 1) * var_ref[l]) + 4 * d * d * n) / (n - 1)
+    assert abs(mean - est_ref) <= 5 * d
