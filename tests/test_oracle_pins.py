@@ -650,3 +650,39 @@ def test_paper_scheme_block_balance(th):
     lhs = m @ u1 + dt * m @ ion(u1)
     rhs = m @ u0 + dt * m @ (th * g(dt) + (1 - th) * g(0.0))
     assert st == 0 and abs(lhs - rhs) < 1e-11 * abs(rhs)
+
+
+def test_five_level_fixture_reproduces_from_the_oracle():
+    # tests/golden/mlmc_2d_5levels_oracle_y.txt was written by its script
+    # from the oracle alone: its first samples of levels 0 and 1 come out of
+    # the oracle again bit for bit (the oracle's per-sample arithmetic does
+    # not depend on the batch or the thread count), and its estimate and
+    # variances are eq. StandardML of its own Y_l
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "mlmc_2d_5levels_oracle_y.txt")
+    head, ys = {}, []
+    for line in open(path):
+        w = line.split()
+        if line.startswith("#"):
+            continue
+        if w[0] in ("estimate", "var", "rmse"):
+            head[w[0]] = [float(x) for x in w[1:]]
+        elif w[0] == "level":
+            ys.append([])
+        else:
+            ys[-1].append(float(w[0]))
+    ys = [np.array(y) for y in ys]
+    assert [y.size for y in ys] == [4096, 1024, 256, 64, 16]
+    est, var, rmse = O.mlmc_estimate(ys)
+    assert est == head["estimate"][0] and rmse == head["rmse"][0]
+    assert np.array_equal(var, head["var"])
+    fine = O.mesh2d(257)
+    modes, _ = O.kl_build(fine, 0.09, 0.04, 16)
+    m17, m33 = O.mesh2d(17), O.mesh2d(33)
+    p17, p33 = O.centroid_table(fine, modes, m17), O.centroid_table(fine, modes, m33)
+    xi0 = inputs.gaussian_xi(0, 0, 0, 3, 16)
+    assert np.array_equal(O.solve_batch(m17, p17, xi0, 0.1, 100)[0], ys[0][:3])
+    xi1 = inputs.gaussian_xi(0, 1, 0, 2, 16)
+    y1 = O.solve_batch(m33, p33, xi1, 0.05, 200)[0] - O.solve_batch(m17, p17, xi1, 0.1, 100)[0]
+    assert np.array_equal(y1, ys[1][:2])
