@@ -248,6 +248,41 @@ def oracle_single_thread(setup, block_fraction: float = 0.01, seed: int = 0):
     return out
 
 
+def oracle_whole_workload():
+    """The oracle's estimate and level variances of the whole workload (every
+    sample of every level pair over the whole horizon, with its own KL
+    tables), from the header of the fixture its script writes
+    (tests/golden/mlmc_2d_5levels_oracle_y.txt); None without it."""
+    path = os.path.join(ROOT, "tests", "golden", "mlmc_2d_5levels_oracle_y.txt")
+    out = {}
+    try:
+        for line in open(path):
+            w = line.split()
+            if w and w[0] in ("estimate", "var", "rmse"):
+                out[w[0]] = [float(x) for x in w[1:]]
+            elif w and w[0] == "level":
+                break
+    except OSError:
+        return None
+    return out if "estimate" in out and "var" in out else None
+
+
+def compare_with_oracle_whole(mean, var):
+    """Relative differences of the library's estimate (and level variances,
+    when given) from the oracle's whole-workload record; each side with the
+    KL tables of its own builder."""
+    ref = oracle_whole_workload()
+    if ref is None:
+        return None
+    e = ref["estimate"][0]
+    out = {"oracle_estimate": e, "estimate_rel": abs(mean - e) / abs(e),
+           "source": "tests/golden/mlmc_2d_5levels_oracle_y.txt (FP64 oracle, every sample of every level pair "
+                     "over the whole horizon; each side its own KL tables)"}
+    if var is not None:
+        out["var_rel_max"] = max(abs(a - b) / abs(b) for a, b in zip(var, ref["var"]))
+    return out
+
+
 def gpu_vs_oracle(mlq, prec, sample, phis):
     """The library on the oracle sample's members (same xi, same blocks, the
     oracle's mode tables phis as input): the largest relative difference of
@@ -1117,6 +1152,8 @@ def main():
             "serving": serving,
             "estimate_all_ranks": None if combined is None else {"estimate": combined[0], "rmse": combined[2],
                                                                   "ranks": world},
+            "vs_oracle_whole_workload": compare_with_oracle_whole(combined[0], None) if combined is not None
+            else compare_with_oracle_whole(mean, list(var)),
             "members": [{k: d[k] for k in ("level", "coarse", "cluster", "threads", "npt", "resident", "samples",
                                             "kernel_ms", "start_ms", "end_ms", "cg_iterations")}
                         for d in members],

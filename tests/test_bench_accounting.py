@@ -104,6 +104,18 @@ def test_reference_steps_cover_every_member(M, K):
         assert all(len(idx) == 1 for idx in g)
 
 
+def test_estimate_against_the_oracle_whole_workload_record():
+    # the header of the oracle's whole-workload fixture; a library estimate
+    # 1e-10 off reads as 1e-10, and the record compared with itself as 0
+    ref = bench.oracle_whole_workload()
+    assert ref is not None and len(ref["var"]) == 5
+    e = ref["estimate"][0]
+    r = bench.compare_with_oracle_whole(e * (1 + 1e-10), ref["var"])
+    assert r["estimate_rel"] == pytest.approx(1e-10, rel=1e-3)
+    assert r["var_rel_max"] == 0.0
+    assert "var_rel_max" not in bench.compare_with_oracle_whole(e, None)
+
+
 class _Done:
     def terminate(self):
         pass
