@@ -206,17 +206,24 @@ mlq::MeshArgs<TI> mesh_args(const mlq_mesh *m, const mlq_model *model, const mlq
 
 constexpr int kMeshThreads = 512;
 
+template <typename TI, bool PTS>
+cudaError_t launch_mesh_t(int cs, const mlq::MeshArgs<TI> &a, cudaStream_t st)
+{
+    switch (cs) {
+    case 1: return mlq::cluster_launch<1>(mlq::mesh_slab_kernel<TI, mlq::ClusterGroup<1>, PTS>, a.S, kMeshThreads, 0, st, a, mlq::ClusterGroup<1>{});
+    case 2: return mlq::cluster_launch<2>(mlq::mesh_slab_kernel<TI, mlq::ClusterGroup<2>, PTS>, a.S, kMeshThreads, 0, st, a, mlq::ClusterGroup<2>{});
+    case 4: return mlq::cluster_launch<4>(mlq::mesh_slab_kernel<TI, mlq::ClusterGroup<4>, PTS>, a.S, kMeshThreads, 0, st, a, mlq::ClusterGroup<4>{});
+    case 8: return mlq::cluster_launch<8>(mlq::mesh_slab_kernel<TI, mlq::ClusterGroup<8>, PTS>, a.S, kMeshThreads, 0, st, a, mlq::ClusterGroup<8>{});
+    case 16: return mlq::cluster_launch<16>(mlq::mesh_slab_kernel<TI, mlq::ClusterGroup<16>, PTS>, a.S, kMeshThreads, 0, st, a, mlq::ClusterGroup<16>{});
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// the instantiation with point QoIs only when the launch records points
 template <typename TI>
 cudaError_t launch_mesh(int cs, const mlq::MeshArgs<TI> &a, cudaStream_t st)
 {
-    switch (cs) {
-    case 1: return mlq::cluster_launch<1>(mlq::mesh_slab_kernel<TI, mlq::ClusterGroup<1>>, a.S, kMeshThreads, 0, st, a, mlq::ClusterGroup<1>{});
-    case 2: return mlq::cluster_launch<2>(mlq::mesh_slab_kernel<TI, mlq::ClusterGroup<2>>, a.S, kMeshThreads, 0, st, a, mlq::ClusterGroup<2>{});
-    case 4: return mlq::cluster_launch<4>(mlq::mesh_slab_kernel<TI, mlq::ClusterGroup<4>>, a.S, kMeshThreads, 0, st, a, mlq::ClusterGroup<4>{});
-    case 8: return mlq::cluster_launch<8>(mlq::mesh_slab_kernel<TI, mlq::ClusterGroup<8>>, a.S, kMeshThreads, 0, st, a, mlq::ClusterGroup<8>{});
-    case 16: return mlq::cluster_launch<16>(mlq::mesh_slab_kernel<TI, mlq::ClusterGroup<16>>, a.S, kMeshThreads, 0, st, a, mlq::ClusterGroup<16>{});
-    default: return cudaErrorInvalidValue;
-    }
+    return a.pq.npts > 0 ? launch_mesh_t<TI, true>(cs, a, st) : launch_mesh_t<TI, false>(cs, a, st);
 }
 
 // G CTAs per sample in one cooperative launch (every CTA resident at once:
@@ -224,7 +231,8 @@ cudaError_t launch_mesh(int cs, const mlq::MeshArgs<TI> &a, cudaStream_t st)
 template <typename TI>
 cudaError_t launch_mesh_grid(const mlq::MeshArgs<TI> &a, const mlq::GridGroup &grp, cudaStream_t st)
 {
-    auto kern = mlq::mesh_slab_kernel<TI, mlq::GridGroup>;
+    auto kern = a.pq.npts > 0 ? mlq::mesh_slab_kernel<TI, mlq::GridGroup, true>
+                              : mlq::mesh_slab_kernel<TI, mlq::GridGroup, false>;
     int prio = 0;
     cudaError_t e = cudaStreamGetPriority(st, &prio);
     if (e != cudaSuccess) return e;
@@ -243,20 +251,27 @@ cudaError_t launch_mesh_grid(const mlq::MeshArgs<TI> &a, const mlq::GridGroup &g
     return cudaLaunchKernelEx(&cfg, kern, a, grp);
 }
 
-// CTAs of the mesh kernel resident at once on the device (both precisions
-// have the same bounds; the larger register count decides)
+// CTAs of the mesh kernel resident at once on the device (every variant
+// has the same bounds; the smallest count decides)
 int64_t mesh_resident_ctas(int device)
 {
-    int nsm = 1, b32 = 0, b64 = 0;
+    int nsm = 1;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, mlq::mesh_slab_kernel<float, mlq::GridGroup>,
-                                                      kMeshThreads, 0) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, mlq::mesh_slab_kernel<double, mlq::GridGroup>,
-                                                      kMeshThreads, 0) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
+    void (*const kerns[2])(mlq::MeshArgs<float>, mlq::GridGroup) = {
+        mlq::mesh_slab_kernel<float, mlq::GridGroup, false>, mlq::mesh_slab_kernel<float, mlq::GridGroup, true>};
+    void (*const kerns64[2])(mlq::MeshArgs<double>, mlq::GridGroup) = {
+        mlq::mesh_slab_kernel<double, mlq::GridGroup, false>, mlq::mesh_slab_kernel<double, mlq::GridGroup, true>};
+    int best = 1 << 30;
+    for (int k = 0; k < 2; ++k) {
+        int b32 = 0, b64 = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, kerns[k], kMeshThreads, 0) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, kerns64[k], kMeshThreads, 0) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        best = std::min(best, std::min(b32, b64));
     }
-    return (int64_t)std::min(b32, b64) * nsm;
+    return (int64_t)best * nsm;
 }
 
 size_t align256(size_t b) { return (std::max<size_t>(b, 8) + 255) / 256 * 256; }

@@ -98,7 +98,10 @@ __device__ __forceinline__ void csr_rows(const int64_t *__restrict__ rp, const i
     }
 }
 
-template <typename TI, typename Grp>
+// PTS: record the point QoIs of g.pq.  A separate instantiation, so that
+// the solves without points carry none of the point state in registers (at
+// the 64-register cap of 512 threads x 2 CTAs it adds spills).
+template <typename TI, typename Grp, bool PTS>
 __global__ void __launch_bounds__(512, 2) mesh_slab_kernel(MeshArgs<TI> g, Grp grp)
 {
     __shared__ double wsl[32][4];
@@ -124,8 +127,10 @@ __global__ void __launch_bounds__(512, 2) mesh_slab_kernel(MeshArgs<TI> g, Grp g
     }
     grp.sync();
     PointState pst;
-    const bool pth = rank == 0 && tid < g.pq.npts;   // point QoI threads
-    if (pth) point_record(g.pq, sample, g.nsteps, g.dt, v, pst);
+    const bool pth = PTS && rank == 0 && tid < g.pq.npts;   // point QoI threads
+    if constexpr (PTS) {
+        if (pth) point_record(g.pq, sample, g.nsteps, g.dt, v, pst);
+    }
 
     int par = 0;
     int64_t total_iters = 0;
@@ -280,9 +285,13 @@ __global__ void __launch_bounds__(512, 2) mesh_slab_kernel(MeshArgs<TI> g, Grp g
             break;
         }
         if (!solved && status == S_CONVERGED) status = S_MAXITER;
-        if (pth) point_record(g.pq, sample, g.nsteps, dt, v, pst);
+        if constexpr (PTS) {
+            if (pth) point_record(g.pq, sample, g.nsteps, dt, v, pst);
+        }
     }
-    if (pth) point_finish(g.pq, sample, g.nsteps, pst);
+    if constexpr (PTS) {
+        if (pth) point_finish(g.pq, sample, g.nsteps, pst);
+    }
 
     double qacc[1] = {0.0};
     for (int i = r0 + tid; i < r1; i += nt) qacc[0] += g.lump[i] * v[i];
